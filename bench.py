@@ -1,0 +1,384 @@
+#!/usr/bin/env python
+"""Benchmark of the rBKI-TK hot path on GB300 (one JSON line on rank 0).
+
+Workload (default): the single large rBKI-TK problem - a 512x512x512 FP32 tensor, 20^3
+superdiagonal core with power-law mode spectra (sigma_k ~ k^-1/2) x Haar factors + noise
+at SNR 10 dB; ranks (20,20,20), p = 10, q = 3; products in BF16 on the tensor path with
+FP32 accumulation, orthonormalisation and eigensolve in FP64.
+
+A step is one whole rBKI-TK decomposition (staging + Algorithms 1-2 for every mode + the
+core TTM chain).  Metric: X-pass HBM GB/s = algorithmic bytes of the X passes of one step
+(sketch, q+1 Krylov steps per Krylov mode, one pass per Gram mode, the first TTM), each
+counted as one read of X at the streamed BF16 precision (2 B/element), divided by the
+step time.  The oracle arm (--impl reference) reports the same quantity for the FP64 CPU
+oracle on a bounded sample (one mode's Algorithm 1 + Rayleigh-Ritz per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+ELEM_BYTES = 2  # X counted at the streamed BF16 precision
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["tucker512", "tucker64", "video", "htr"], default="tucker512")
+    ap.add_argument("--prec", choices=["bf16", "fp64"], default="bf16")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-compare", action="store_true")
+    return ap.parse_args()
+
+
+def make_workload(name, mc):
+    import synth
+    if name == "tucker512":
+        return synth.config_large(mc=mc)
+    if name == "tucker64":
+        return synth.config_small_fp64(mc=mc)
+    if name == "video":
+        return synth.config_video(mc=mc)
+    if name == "htr":
+        return synth.config_htr(mc=mc)
+    raise ValueError(name)
+
+
+def plan_passes(dims, ranks, p, q):
+    """X passes of one step: per Krylov mode 1 sketch + (q+1) Krylov steps; per Gram mode 1;
+    plus the first TTM of the core chain."""
+    passes, krylov_steps = 1, 0
+    for i_n, r_n in zip(dims, ranks):
+        s = min(r_n + p, i_n)
+        if s * (q + 1) >= i_n:
+            passes += 1
+        else:
+            passes += q + 2
+            krylov_steps += q + 1
+    return passes, krylov_steps
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.uuid = uuid
+        self.proc = None
+        self.path = os.path.join("/tmp", f"rbki_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            cmd = ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.uuid:
+                cmd[1:1] = ["-i", self.uuid]
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            f = [t.strip() for t in line.split(",")]
+            if len(f) < 11:
+                continue
+            rows.append(f)
+        if not rows:
+            return None
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        util = [float(r[5]) for r in rows if r[5].replace(".", "").isdigit()]
+        load = [s for s, u in zip(sm, util) if u > 0] or sm
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[7:11]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(load) if load else None,
+                "sm_max_mhz": float(rows[0][3]) if rows[0][3].replace(".", "").isdigit() else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    elif args.impl == "ours":
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_cpu_baseline(wl, max_seconds=30.0):
+    """The FP64 NumPy oracle as it stands, on this host's cores: full rBKI-TK of the same
+    tensor (bounded: stops after the modes that fit in ~max_seconds)."""
+    import numpy as np
+    from oracle import philox, rbki
+    from oracle.tensor import unfold
+    x = np.asarray(wl.x, dtype=np.float64)
+    t0 = time.perf_counter()
+    done_bytes = 0
+    modes = 0
+    for n in range(x.ndim):
+        s = min(wl.ranks[n] + wl.p, x.shape[n])
+        xn = unfold(x, n)
+        if s * (wl.q + 1) >= x.shape[n]:
+            np.linalg.eigh(xn @ xn.T)
+            done_bytes += x.size * ELEM_BYTES
+        else:
+            om = philox.omega_mode(wl.seed, n, x.shape, s)
+            qb = np.concatenate(rbki.rbki(xn, om, wl.q), axis=1)
+            rbki.rayleigh_ritz(xn, qb, wl.ranks[n])
+            done_bytes += (wl.q + 2) * x.size * ELEM_BYTES
+        modes += 1
+        if time.perf_counter() - t0 > max_seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": done_bytes / dt / 1e9, "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"FP64 NumPy oracle, Algorithm 1 + Rayleigh-Ritz for {modes} of {x.ndim} modes of the "
+                      f"same {'x'.join(map(str, x.shape))} tensor ({dt:.1f} s), X passes counted at "
+                      f"{ELEM_BYTES} B/element"}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import paper_2211_14828_gb300 as rb
+    from paper_2211_14828_gb300 import _binding as B
+
+    world, rank, local = dist_setup(args)
+    wl = make_workload(args.workload, rank)
+    dims = list(wl.x.shape)
+    numel = int(np.prod(dims))
+    passes, krylov_steps = plan_passes(dims, wl.ranks, wl.p, wl.q)
+    step_bytes = passes * numel * ELEM_BYTES
+    prec = args.prec
+    x = torch.from_numpy(wl.x).cuda()
+    stream = torch.cuda.current_stream()
+    out = rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec=prec)
+    ws = out["workspace"]
+    torch.cuda.synchronize()
+    for _ in range(max(0, args.warmup - 1)):
+        rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec=prec, workspace=ws, out=out)
+    torch.cuda.synchronize()
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    rb.rbki_profile_reset()
+    rb.rbki_profile_enable(True)
+    launches0 = rb.rbki_kernel_launches()
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec=prec, workspace=ws, out=out)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    rb.rbki_profile_enable(False)
+    launches = rb.rbki_kernel_launches() - launches0
+    ms_local = ev0.elapsed_time(ev1) / args.steps
+    ms = allreduce_max(ms_local, world)
+    value = world * step_bytes / (ms * 1e-3) / 1e9
+
+    kcount, kms = rb.rbki_profile_read(rb.PROF_KRYLOV)
+    scount, sms = rb.rbki_profile_read(rb.PROF_SKETCH)
+    peak, peak_kind = measured_peaks()
+    per_launch_bytes = numel * ELEM_BYTES if prec != "fp64" else numel * wl.x.itemsize
+    roof = None
+    if kcount:
+        avg = kms / kcount
+        ach = per_launch_bytes / (avg * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(ach / peak, 4), "traffic": None, "kernel": "krylov_step",
+                "avg_launch_ms": round(avg, 4), "launches": kcount, "peak_kind": peak_kind}
+    breakdown = {}
+    for name, cls in (("krylov", rb.PROF_KRYLOV), ("sketch", rb.PROF_SKETCH), ("gram", rb.PROF_GRAM),
+                      ("ttm1", rb.PROF_TTM), ("stage", rb.PROF_STAGE)):
+        c, t = rb.rbki_profile_read(cls)
+        if c:
+            breakdown[name] = {"ms_per_step": round(t / args.steps, 4), "launches_per_step": c / args.steps}
+    rb.rbki_profile_reset()
+
+    norms = out["norms"].cpu().numpy()
+    rel_err = float(np.sqrt(max(norms[0] - norms[1], 0.0) / norms[0]))
+
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.from_numpy(wl.x).pin_memory()
+        oh = B.alloc_outputs(dims, wl.ranks, None, host=True)
+        flags = rb.FLAG_HOST_IO
+        wsh = torch.empty(rb.rbki_tucker_workspace(xh, wl.ranks, wl.p, wl.q, wl.seed, prec, flags),
+                          dtype=torch.uint8, device="cuda")
+        for _ in range(2):
+            rb.rbki_tucker(xh, wl.ranks, wl.p, wl.q, wl.seed, prec=prec, flags=flags, workspace=wsh, out=oh)
+        ke = max(3, min(args.steps, 10))
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            rb.rbki_tucker(xh, wl.ranks, wl.p, wl.q, wl.seed, prec=prec, flags=flags, workspace=wsh, out=oh)
+        te = (time.perf_counter() - t0) / ke
+        te = allreduce_max(te, world)
+        d2h = sum(int(np.prod(v.shape)) * v.element_size() for k, v in oh.items() if k in ("core", "norms", "info"))
+        d2h += sum(f.numel() * 8 for f in oh["factors"]) + sum(e.numel() * 8 for e in oh["eigvals"])
+        e2e = {"value": round(world * step_bytes / te / 1e9, 2), "unit": "GB/s",
+               "h2d_bytes_per_step": int(xh.numel() * xh.element_size()), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": round(te * 1e3, 3)}
+        del wsh
+
+    fp64_cmp = None
+    if not args.no_fp64_compare and prec != "fp64":
+        o64 = rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec="fp64")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec="fp64", workspace=o64["workspace"], out=o64)
+        torch.cuda.synchronize()
+        t64 = time.perf_counter() - t0
+        n64 = o64["norms"].cpu().numpy()
+        rel64 = float(np.sqrt(max(n64[0] - n64[1], 0.0) / n64[0]))
+        fp64_cmp = {"ms_per_step": round(t64 * 1e3, 2), "rel_err": rel64,
+                    "mixed_rel_err": rel_err, "mixed_vs_fp64": (rel_err - rel64) / rel64}
+        del o64
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_cpu_baseline(wl)
+
+    if rank == 0:
+        line = {
+            "metric": "rBKI-TK Krylov-pass HBM GB/s (X-pass bytes of one full decomposition / step time)",
+            "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if prec == "bf16" else "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {'x'.join(map(str, dims))} {wl.x.dtype}, ranks {wl.ranks}, "
+                                   f"p={wl.p}, q={wl.q}, {prec} products",
+                       "passes_per_step": passes, "krylov_steps_per_step": krylov_steps,
+                       "bytes_per_step": step_bytes, "l2": "inputs larger than L2 (no flush)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roof, "breakdown": breakdown, "rel_err": rel_err, "fp64_compare": fp64_cmp,
+            "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """The FP64 NumPy oracle on the host cores, same metric/unit/config; each step = one
+    mode's Algorithm 1 + Rayleigh-Ritz over the full tensor (a bounded sample)."""
+    import numpy as np
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import philox, rbki
+    from oracle.tensor import unfold
+    wl = make_workload(args.workload, 0)
+    x = np.asarray(wl.x, dtype=np.float64)
+    dims = list(x.shape)
+    numel = x.size
+
+    def step(k):
+        n = k % x.ndim
+        s = min(wl.ranks[n] + wl.p, x.shape[n])
+        xn = unfold(x, n)
+        if s * (wl.q + 1) >= x.shape[n]:
+            np.linalg.eigh(xn @ xn.T)
+            return numel * ELEM_BYTES
+        om = philox.omega_mode(wl.seed, n, x.shape, s)
+        qb = np.concatenate(rbki.rbki(xn, om, wl.q), axis=1)
+        rbki.rayleigh_ritz(xn, qb, wl.ranks[n])
+        return (wl.q + 2) * numel * ELEM_BYTES
+
+    for k in range(args.warmup):
+        step(k)
+    t0 = time.perf_counter()
+    tot = 0
+    for k in range(args.steps):
+        tot += step(k)
+    dt = time.perf_counter() - t0
+    value = tot / dt / 1e9
+    line = {
+        "metric": "rBKI-TK Krylov-pass HBM GB/s (X-pass bytes of one full decomposition / step time)",
+        "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(dt / args.steps * 1e3, 2), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": f"{args.workload}: {'x'.join(map(str, dims))}, ranks {wl.ranks}, p={wl.p}, q={wl.q}",
+                   "sample": "one mode's Algorithm 1 + Rayleigh-Ritz per step"},
+        "cpu_baseline": {"value": round(value, 3), "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": "FP64 NumPy oracle, one mode's Algorithm 1 + Rayleigh-Ritz per step, X passes "
+                                   f"counted at {ELEM_BYTES} B/element"},
+        "e2e": {"value": round(value, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

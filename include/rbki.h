@@ -1,0 +1,192 @@
+/*
+ * rbki.h - C ABI of librbki.so: rBKI-TK Tucker decomposition and rBKI-TK-TR
+ * hierarchical tensor-ring decomposition on one GB300 GPU (sm_103a).
+ *
+ * Method: Qiu, Sun, Zhou, Zhao, "Towards Efficient and Accurate Approximation:
+ * Tensor Decomposition Based on Randomized Block Krylov Iteration", arXiv 2211.14828.
+ *   Algorithm 1  tensor sketching by randomized block Krylov iteration (Eq. BKspace)
+ *   Algorithm 2  rBKI-TK (randomized HOSVD with rBKI subspaces, Remark 1, Eq. tensorsketch)
+ *   Algorithm 3  rBKI-TK-TR (TR-ALS on the rBKI-TK core, contraction with the factors)
+ *
+ * Conventions (all entry points):
+ *   - Tensors are dense, C-order (last index fastest).  Mode n is 0-based here
+ *     (the paper's mode n+1).  The mode-n unfolding X_(n) is never materialised;
+ *     its column index is the C-order linear index of the remaining indices.
+ *   - Every pointer in a struct or argument is DEVICE memory on the current CUDA
+ *     device unless RBKI_FLAG_HOST_IO is set (then X and the outputs are host
+ *     memory, preferably pinned, and the call copies them itself and returns
+ *     after the results are back on the host).
+ *   - The caller owns every buffer, including the workspace; the library
+ *     allocates no device memory in these calls.  Buffers must stay alive until
+ *     the work queued on `stream` has finished (or, for the server, until a
+ *     terminal rbki_poll result).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Work is queued on it; rbki_tucker / rbki_htr return without synchronising
+ *     (except with RBKI_FLAG_HOST_IO).
+ *   - Errors never abort the process: a negative rbki_status is returned and
+ *     nothing is written to the outputs if validation fails.  A CUDA launch
+ *     error is reported as RBKI_E_CUDA; rbki_last_error() gives its text.
+ *   - Outputs are FP64 whatever the input dtype and product precision.
+ */
+#ifndef RBKI_H
+#define RBKI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RBKI_MAX_ORDER 8
+
+typedef int32_t rbki_status;
+enum {
+    RBKI_OK = 0,
+    RBKI_PENDING = 1,        /* server: request not finished */
+    RBKI_W_DEFLATED = 2,     /* warning: a Krylov block lost directions (reading c3) */
+    RBKI_E_INVAL = -1,       /* invalid argument (shape, rank, pointer, size) */
+    RBKI_E_NOMEM = -2,       /* workspace too small / server budget exceeded */
+    RBKI_E_CUDA = -3,        /* CUDA runtime or launch error */
+    RBKI_E_UNSUPPORTED = -4, /* valid request outside what this build implements */
+    RBKI_E_TIMEOUT = -5,     /* a bounded device or host wait ran out */
+    RBKI_E_BUSY = -6,        /* server: no slot / queue full */
+    RBKI_E_CANCELLED = -7,   /* server: request cancelled */
+    RBKI_E_NOTFOUND = -8     /* server: unknown ticket */
+};
+
+/* storage dtype of the input tensor */
+enum { RBKI_F64 = 0, RBKI_F32 = 1, RBKI_BF16 = 2, RBKI_F16 = 3 };
+
+/* precision of the X-streaming products (sketch, Krylov step, Gram, first TTM).
+ * Orthonormalisation, the small eigensolve and all outputs are FP64 in every mode. */
+enum { RBKI_PREC_FP64 = 0, RBKI_PREC_BF16 = 1, RBKI_PREC_FP16 = 2 };
+
+/* rbki_params.flags */
+enum {
+    RBKI_FLAG_HOST_IO = 1u,        /* X and outputs in host memory (end-to-end call) */
+    RBKI_FLAG_NO_SPLIT = 2u,       /* mixed path: skip the hi/lo split of the skinny operands */
+    RBKI_FLAG_SERIAL_MODES = 4u    /* run modes one after another on `stream` */
+};
+
+typedef struct {
+    int32_t order;                   /* N, 1..RBKI_MAX_ORDER */
+    int32_t dtype;                   /* RBKI_F64 / RBKI_F32 / RBKI_BF16 / RBKI_F16 */
+    int64_t dims[RBKI_MAX_ORDER];    /* I_1..I_N, each > 0 */
+    const void* data;                /* C-order, 16-byte aligned */
+} rbki_tensor;
+
+/* Algorithm 2 inputs: multilinear rank R_n, oversampling p (S_n = min(R_n + p, I_n)),
+ * Krylov depth q (K has q+1 blocks, Eq. BKspace), seed of the Gaussian sketches. */
+typedef struct {
+    int32_t ranks[RBKI_MAX_ORDER];   /* 1 <= R_n <= I_n */
+    int32_t p;                       /* >= 0 */
+    int32_t q;                       /* >= 0 */
+    uint64_t seed;
+    int32_t prec;                    /* RBKI_PREC_* */
+    uint32_t flags;                  /* RBKI_FLAG_* */
+} rbki_params;
+
+/* Algorithm 2 outputs (caller-owned). */
+typedef struct {
+    double* core;                    /* R_1 x ... x R_N, C-order (required) */
+    double* factors[RBKI_MAX_ORDER]; /* U^(n): I_n x R_n row-major, orthonormal columns,
+                                        descending Ritz values, largest-|.| entry of each
+                                        column positive (required) */
+    double* eigvals[RBKI_MAX_ORDER]; /* optional (NULL): leading R_n eigenvalues of Z^(n) */
+    double* norms;                   /* optional: [0] = |X|_F^2, [1] = |G|_F^2; the
+                                        reconstruction error is |X|^2 - |G|^2 */
+    int32_t* info;                   /* optional, 2N ints: [n] = kept Krylov width of mode n,
+                                        [N+n] = path (0 Krylov, 1 Gram = exact T-SVD mode) */
+} rbki_tucker_out;
+
+/* Bytes of device workspace rbki_tucker needs for this problem. */
+rbki_status rbki_tucker_workspace(const rbki_tensor* X, const rbki_params* prm, size_t* bytes);
+
+/* rBKI-TK, Algorithm 2 (with Algorithm 1 per mode), HOSVD reading: every mode sketches
+ * the original X; G = X x_1 U^(1)T ... x_N U^(N)T (Eq. tensorsketch).
+ * Per mode: S = min(R+p, I), b = S(q+1); b >= I uses the Gram path (Z = X_(n) X_(n)^T,
+ * the exact truncated-HOSVD factor); otherwise W = X_(n) Omega, Q_0 = orth(W),
+ * Q_{j+1} = orth(X_(n) X_(n)^T Q_j) against all earlier blocks, Z = Q^T X X^T Q,
+ * U = Q * leading eigenvectors of Z.  Omega's entries are the Philox4x32-10 +
+ * Box-Muller Gaussians keyed by (seed, n, column, s). */
+rbki_status rbki_tucker(const rbki_tensor* X, const rbki_params* prm, void* workspace,
+                        size_t workspace_bytes, const rbki_tucker_out* out, void* stream);
+
+/* Bytes of device workspace rbki_htr needs. */
+rbki_status rbki_htr_workspace(const rbki_tensor* X, const rbki_params* tk,
+                               const int32_t* tr_ranks, size_t* bytes);
+
+/* rBKI-TK-TR, Algorithm 3.  tr_ranks[n] = r_n (r_0 = r_N, ring closure; Eq. TR).
+ * tr_init[n]: device, initial TR core of the Tucker core, r_{n-1} x R_n x r_n (C-order).
+ * TR-ALS sweeps cores 0..N-1, exact least squares per core (normal equations, FP64),
+ * stops after tr_maxit sweeps or when |Fit_t - Fit_{t-1}| <= tr_tol (Sec. 4 rule).
+ * tr_cores[n]: device output r_{n-1} x I_n x r_n = G_n x_2 U^(n) (Algorithm 3 step 4).
+ * fits: optional device output, tr_maxit doubles (fit per sweep, NaN after the stop);
+ * tucker_out may be NULL or receive the intermediate Tucker result. */
+rbki_status rbki_htr(const rbki_tensor* X, const rbki_params* tk, const int32_t* tr_ranks,
+                     const double* const* tr_init, int32_t tr_maxit, double tr_tol,
+                     double* const* tr_cores, double* fits, const rbki_tucker_out* tucker_out,
+                     void* workspace, size_t workspace_bytes, void* stream);
+
+/* ---- served stream (continuous batching with device-memory admission) ------------- */
+typedef struct rbki_server rbki_server;
+
+/* Creates a server on `device` that admits requests while their workspace fits in
+ * mem_budget bytes and fewer than max_slots are in flight.  The server allocates its
+ * own device memory pool of mem_budget bytes once, here. */
+rbki_status rbki_server_create(int32_t device, size_t mem_budget, int32_t max_slots,
+                               rbki_server** out);
+/* Queues one rBKI-TK request.  X and out must stay valid until a terminal poll. */
+rbki_status rbki_submit(rbki_server* s, const rbki_tensor* X, const rbki_params* prm,
+                        const rbki_tucker_out* out, uint64_t* ticket);
+/* Non-blocking.  *result = RBKI_PENDING while running, else the request's final status;
+ * *latency_s = completion - submission (seconds) once finished. */
+rbki_status rbki_poll(rbki_server* s, uint64_t ticket, rbki_status* result, double* latency_s);
+rbki_status rbki_cancel(rbki_server* s, uint64_t ticket);
+/* Waits (bounded by timeout_s) until every admitted request has finished. */
+rbki_status rbki_server_drain(rbki_server* s, double timeout_s);
+rbki_status rbki_server_destroy(rbki_server* s);
+
+/* ---- step-level entry points (used by the parity tests) --------------------------- */
+
+/* Krylov step of Algorithm 1 / Eq. BKspace on mode n: P = X_(n) (X_(n)^T Q),
+ * Q: I_n x s row-major FP64 (device), P: I_n x s row-major FP64 (device). */
+rbki_status rbki_krylov_product(const rbki_tensor* X, int32_t mode, int32_t prec,
+                                const double* Q, int32_t s, double* P,
+                                void* workspace, size_t workspace_bytes, void* stream);
+rbki_status rbki_krylov_product_workspace(const rbki_tensor* X, int32_t mode, int32_t prec,
+                                          int32_t s, size_t* bytes);
+
+/* Algorithm 1 for one mode: the orthonormal Krylov basis Q = [Q_0..Q_q] (I_n x b,
+ * row-major FP64, deflated columns are zero), b = S(q+1), S = min(R_n+p, I_n). */
+rbki_status rbki_mode_basis(const rbki_tensor* X, const rbki_params* prm, int32_t mode,
+                            double* Q, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Symmetric eigensolver used for Algorithm 2 step 4: A (n x n, FP64, symmetric) ->
+ * eigenvalues descending in w (n) and eigenvectors as columns of V (n x n row-major). */
+rbki_status rbki_syev(const double* A, int32_t n, double* w, double* V,
+                      void* workspace, size_t workspace_bytes, void* stream);
+rbki_status rbki_syev_workspace(int32_t n, size_t* bytes);
+
+/* ---- diagnostics -------------------------------------------------------------------- */
+/* Kernel classes timed by the profiling hook. */
+enum { RBKI_PROF_KRYLOV = 0, RBKI_PROF_SKETCH = 1, RBKI_PROF_GRAM = 2, RBKI_PROF_TTM = 3,
+       RBKI_PROF_STAGE = 4, RBKI_PROF_COUNT = 5 };
+/* When on, each streaming launch (Krylov step, sketch, Gram pass, first TTM, staging) is
+ * bracketed by CUDA events recorded on the stream it runs on.  Off by default. */
+void rbki_profile_enable(int32_t on);
+/* Waits for the recorded events and returns, for class `cls`, the number of timed launches
+ * and their summed duration in milliseconds since the last reset. */
+rbki_status rbki_profile_read(int32_t cls, uint64_t* count, double* total_ms);
+void rbki_profile_reset(void);
+
+const char* rbki_status_str(rbki_status s);
+const char* rbki_last_error(void);
+/* Number of kernels this library has launched in this process (diagnostics). */
+uint64_t rbki_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RBKI_H */

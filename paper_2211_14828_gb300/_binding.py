@@ -1,0 +1,263 @@
+"""Thin ctypes binding of librbki.so (argument marshalling only).
+
+Every computation runs in the library's CUDA kernels; PyTorch only provides device
+memory and the current stream.  The functions keep the C entry points' names.
+If the shared library has not been built, loading fails loudly: there is no CPU
+fallback."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Dict, Optional, Sequence
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librbki.so")
+MAX_ORDER = 8
+
+OK, PENDING, W_DEFLATED = 0, 1, 2
+E_INVAL, E_NOMEM, E_CUDA, E_UNSUPPORTED, E_TIMEOUT, E_BUSY, E_CANCELLED, E_NOTFOUND = range(-1, -9, -1)
+F64, F32, BF16, F16 = 0, 1, 2, 3
+PREC_FP64, PREC_BF16, PREC_FP16 = 0, 1, 2
+FLAG_HOST_IO, FLAG_NO_SPLIT, FLAG_SERIAL_MODES = 1, 2, 4
+
+
+class rbki_tensor(C.Structure):
+    _fields_ = [("order", C.c_int32), ("dtype", C.c_int32), ("dims", C.c_int64 * MAX_ORDER),
+                ("data", C.c_void_p)]
+
+
+class rbki_params(C.Structure):
+    _fields_ = [("ranks", C.c_int32 * MAX_ORDER), ("p", C.c_int32), ("q", C.c_int32),
+                ("seed", C.c_uint64), ("prec", C.c_int32), ("flags", C.c_uint32)]
+
+
+class rbki_tucker_out(C.Structure):
+    _fields_ = [("core", C.c_void_p), ("factors", C.c_void_p * MAX_ORDER),
+                ("eigvals", C.c_void_p * MAX_ORDER), ("norms", C.c_void_p), ("info", C.c_void_p)]
+
+
+class RbkiError(RuntimeError):
+    def __init__(self, status: int, what: str, detail: str):
+        super().__init__(f"{what}: status {status} ({detail})")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                               "(there is no CPU fallback)")
+        L = C.CDLL(LIB_PATH)
+        st = C.c_int32
+        vp = C.c_void_p
+        sz = C.POINTER(C.c_size_t)
+        sig = {
+            "rbki_tucker_workspace": (st, [vp, vp, sz]),
+            "rbki_tucker": (st, [vp, vp, vp, C.c_size_t, vp, vp]),
+            "rbki_htr_workspace": (st, [vp, vp, vp, sz]),
+            "rbki_htr": (st, [vp, vp, vp, vp, C.c_int32, C.c_double, vp, vp, vp, vp, C.c_size_t, vp]),
+            "rbki_server_create": (st, [C.c_int32, C.c_size_t, C.c_int32, C.POINTER(vp)]),
+            "rbki_submit": (st, [vp, vp, vp, vp, C.POINTER(C.c_uint64)]),
+            "rbki_poll": (st, [vp, C.c_uint64, C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
+            "rbki_cancel": (st, [vp, C.c_uint64]),
+            "rbki_server_drain": (st, [vp, C.c_double]),
+            "rbki_server_destroy": (st, [vp]),
+            "rbki_krylov_product": (st, [vp, C.c_int32, C.c_int32, vp, C.c_int32, vp, vp, C.c_size_t, vp]),
+            "rbki_krylov_product_workspace": (st, [vp, C.c_int32, C.c_int32, C.c_int32, sz]),
+            "rbki_mode_basis": (st, [vp, vp, C.c_int32, vp, vp, C.c_size_t, vp]),
+            "rbki_syev": (st, [vp, C.c_int32, vp, vp, vp, C.c_size_t, vp]),
+            "rbki_syev_workspace": (st, [C.c_int32, sz]),
+            "rbki_status_str": (C.c_char_p, [C.c_int32]),
+            "rbki_last_error": (C.c_char_p, []),
+            "rbki_kernel_launches": (C.c_uint64, []),
+            "rbki_profile_enable": (None, [C.c_int32]),
+            "rbki_profile_read": (st, [C.c_int32, C.POINTER(C.c_uint64), C.POINTER(C.c_double)]),
+            "rbki_profile_reset": (None, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(status: int, what: str) -> int:
+    if status < 0:
+        L = lib()
+        raise RbkiError(status, what, f"{L.rbki_status_str(status).decode()}: "
+                                      f"{L.rbki_last_error().decode()}")
+    return status
+
+
+# ---------------- marshalling helpers (torch is used for memory and streams only) ----------------
+def _torch():
+    import torch
+    return torch
+
+
+def dtype_code(t) -> int:
+    torch = _torch()
+    return {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16, torch.float16: F16}[t.dtype]
+
+
+def prec_code(prec) -> int:
+    if isinstance(prec, int):
+        return prec
+    return {"fp64": PREC_FP64, "bf16": PREC_BF16, "fp16": PREC_FP16}[prec]
+
+
+def make_tensor(x, host: bool = False) -> rbki_tensor:
+    if not x.is_contiguous():
+        raise ValueError("X must be C-contiguous")
+    t = rbki_tensor()
+    t.order = x.dim()
+    t.dtype = dtype_code(x)
+    for i, d in enumerate(x.shape):
+        t.dims[i] = int(d)
+    t.data = x.data_ptr()
+    return t
+
+
+def make_params(ranks: Sequence[int], p: int, q: int, seed: int, prec, flags: int = 0) -> rbki_params:
+    prm = rbki_params()
+    for i, r in enumerate(ranks):
+        prm.ranks[i] = int(r)
+    prm.p, prm.q, prm.seed, prm.prec, prm.flags = int(p), int(q), int(seed), prec_code(prec), int(flags)
+    return prm
+
+
+def stream_ptr(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def alloc_outputs(dims, ranks, device, host=False) -> Dict:
+    torch = _torch()
+    kw = dict(dtype=torch.float64, device="cpu" if host else device)
+    if host:
+        kw["pin_memory"] = True
+    out = dict(core=torch.zeros(tuple(ranks), **kw),
+               factors=[torch.zeros((int(d), int(r)), **kw) for d, r in zip(dims, ranks)],
+               eigvals=[torch.zeros(int(r), **kw) for r in ranks],
+               norms=torch.zeros(2, **kw))
+    ikw = dict(dtype=torch.int32, device="cpu" if host else device)
+    if host:
+        ikw["pin_memory"] = True
+    out["info"] = torch.zeros(2 * len(dims), **ikw)
+    return out
+
+
+def make_out(o: Dict) -> rbki_tucker_out:
+    s = rbki_tucker_out()
+    s.core = o["core"].data_ptr()
+    for i, f in enumerate(o["factors"]):
+        s.factors[i] = f.data_ptr()
+    for i, e in enumerate(o.get("eigvals") or []):
+        s.eigvals[i] = e.data_ptr() if e is not None else None
+    s.norms = o["norms"].data_ptr() if o.get("norms") is not None else None
+    s.info = o["info"].data_ptr() if o.get("info") is not None else None
+    return s
+
+
+# ---------------- entry points ----------------
+def rbki_tucker_workspace(x, ranks, p, q, seed=0, prec="bf16", flags=0) -> int:
+    n = C.c_size_t(0)
+    t, prm = make_tensor(x), make_params(ranks, p, q, seed, prec, flags)
+    check(lib().rbki_tucker_workspace(C.byref(t), C.byref(prm), C.byref(n)), "rbki_tucker_workspace")
+    return int(n.value)
+
+
+def rbki_tucker(x, ranks, p, q, seed, prec="bf16", flags=0, workspace=None, out=None, stream=None):
+    """rBKI-TK (Algorithm 2).  x: torch tensor (CUDA, or pinned CPU with FLAG_HOST_IO)."""
+    torch = _torch()
+    host = bool(flags & FLAG_HOST_IO)
+    t, prm = make_tensor(x), make_params(ranks, p, q, seed, prec, flags)
+    need = C.c_size_t(0)
+    check(lib().rbki_tucker_workspace(C.byref(t), C.byref(prm), C.byref(need)), "rbki_tucker_workspace")
+    dev = torch.device("cuda", torch.cuda.current_device()) if host else x.device
+    if workspace is None or workspace.numel() < need.value:
+        workspace = torch.empty(int(need.value), dtype=torch.uint8, device=dev)
+    if out is None:
+        out = alloc_outputs(x.shape, ranks, dev, host=host)
+    o = make_out(out)
+    check(lib().rbki_tucker(C.byref(t), C.byref(prm), C.c_void_p(workspace.data_ptr()),
+                            C.c_size_t(workspace.numel()), C.byref(o), stream_ptr(stream)), "rbki_tucker")
+    out["workspace"] = workspace
+    return out
+
+
+def rbki_krylov_product(x, mode: int, q_mat, prec="fp64", workspace=None, stream=None):
+    """P = X_(n) (X_(n)^T Q) (Algorithm 1 step 3), Q: (I_n, s) float64 CUDA tensor."""
+    torch = _torch()
+    t = make_tensor(x)
+    s = int(q_mat.shape[1])
+    need = C.c_size_t(0)
+    check(lib().rbki_krylov_product_workspace(C.byref(t), mode, prec_code(prec), s, C.byref(need)),
+          "rbki_krylov_product_workspace")
+    if workspace is None or workspace.numel() < need.value:
+        workspace = torch.empty(int(need.value), dtype=torch.uint8, device=x.device)
+    P = torch.empty((x.shape[mode], s), dtype=torch.float64, device=x.device)
+    q_c = q_mat.contiguous()
+    check(lib().rbki_krylov_product(C.byref(t), mode, prec_code(prec), C.c_void_p(q_c.data_ptr()), s,
+                                    C.c_void_p(P.data_ptr()), C.c_void_p(workspace.data_ptr()),
+                                    C.c_size_t(workspace.numel()), stream_ptr(stream)), "rbki_krylov_product")
+    return P
+
+
+def rbki_mode_basis(x, ranks, p, q, seed, mode, prec="fp64", stream=None):
+    """Algorithm 1 basis Q = [Q_0..Q_q] for one mode (I_n x S(q+1), zero deflated columns)."""
+    torch = _torch()
+    t, prm = make_tensor(x), make_params(ranks, p, q, seed, prec)
+    need = C.c_size_t(0)
+    check(lib().rbki_tucker_workspace(C.byref(t), C.byref(prm), C.byref(need)), "rbki_tucker_workspace")
+    ws = torch.empty(int(need.value), dtype=torch.uint8, device=x.device)
+    s = min(ranks[mode] + p, x.shape[mode])
+    Q = torch.empty((x.shape[mode], s * (q + 1)), dtype=torch.float64, device=x.device)
+    check(lib().rbki_mode_basis(C.byref(t), C.byref(prm), mode, C.c_void_p(Q.data_ptr()),
+                                C.c_void_p(ws.data_ptr()), C.c_size_t(ws.numel()), stream_ptr(stream)),
+          "rbki_mode_basis")
+    return Q
+
+
+def rbki_syev(a, stream=None):
+    """Eigen-decomposition of a symmetric FP64 matrix: (w descending, V columns)."""
+    torch = _torch()
+    n = int(a.shape[0])
+    need = C.c_size_t(0)
+    check(lib().rbki_syev_workspace(n, C.byref(need)), "rbki_syev_workspace")
+    ws = torch.empty(int(need.value), dtype=torch.uint8, device=a.device)
+    w = torch.empty(n, dtype=torch.float64, device=a.device)
+    V = torch.empty((n, n), dtype=torch.float64, device=a.device)
+    a_c = a.contiguous()
+    check(lib().rbki_syev(C.c_void_p(a_c.data_ptr()), n, C.c_void_p(w.data_ptr()), C.c_void_p(V.data_ptr()),
+                          C.c_void_p(ws.data_ptr()), C.c_size_t(ws.numel()), stream_ptr(stream)), "rbki_syev")
+    return w, V
+
+
+PROF_KRYLOV, PROF_SKETCH, PROF_GRAM, PROF_TTM, PROF_STAGE = range(5)
+
+
+def rbki_profile_enable(on: bool = True) -> None:
+    lib().rbki_profile_enable(1 if on else 0)
+
+
+def rbki_profile_reset() -> None:
+    lib().rbki_profile_reset()
+
+
+def rbki_profile_read(cls: int):
+    """(launch count, total ms) of kernel class `cls` since the last reset."""
+    n = C.c_uint64(0)
+    ms = C.c_double(0)
+    check(lib().rbki_profile_read(cls, C.byref(n), C.byref(ms)), "rbki_profile_read")
+    return int(n.value), float(ms.value)
+
+
+def rbki_kernel_launches() -> int:
+    return int(lib().rbki_kernel_launches())

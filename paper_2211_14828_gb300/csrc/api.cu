@@ -1,0 +1,510 @@
+// C ABI of librbki: argument validation, planning, workspace carving and the per-mode
+// pipeline of Algorithms 1-2 (rBKI-TK) on the caller's stream.
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "plan.h"
+
+namespace rbki {
+
+static std::atomic<uint64_t> g_launches{0};
+static thread_local std::string g_err;
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+rbki_status set_cuda_error(cudaError_t e, const char* where) {
+    g_err = std::string(where) + ": " + cudaGetErrorString(e);
+    return RBKI_E_CUDA;
+}
+
+rbki_status set_error(rbki_status s, const char* msg) {
+    g_err = msg;
+    return s;
+}
+
+// ---- profiling hook: CUDA events around streaming launches ----
+struct ProfRec { int cls; cudaEvent_t a, b; };
+static std::mutex g_prof_mu;
+static bool g_prof_on = false;
+static std::vector<ProfRec> g_prof;
+static size_t g_prof_used = 0;
+
+int prof_begin(int cls, cudaStream_t st) {
+    if (!g_prof_on) return -1;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (g_prof_used == g_prof.size()) {
+        ProfRec r{cls, nullptr, nullptr};
+        if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) return -1;
+        g_prof.push_back(r);
+    }
+    int tok = (int)g_prof_used++;
+    g_prof[tok].cls = cls;
+    cudaEventRecord(g_prof[tok].a, st);
+    return tok;
+}
+
+void prof_end(int tok, cudaStream_t st) {
+    if (tok < 0) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    cudaEventRecord(g_prof[tok].b, st);
+}
+
+size_t dtype_size(int dt) {
+    switch (dt) {
+        case RBKI_F64: return 8;
+        case RBKI_F32: return 4;
+        case RBKI_BF16: return 2;
+        case RBKI_F16: return 2;
+        default: return 0;
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// validation + plan
+// ---------------------------------------------------------------------------------
+rbki_status validate_tensor(const rbki_tensor* X) {
+    if (!X) return set_error(RBKI_E_INVAL, "X is NULL");
+    if (X->order < 1 || X->order > RBKI_MAX_ORDER) return set_error(RBKI_E_INVAL, "order out of range");
+    if (dtype_size(X->dtype) == 0) return set_error(RBKI_E_INVAL, "unknown dtype");
+    for (int n = 0; n < X->order; ++n)
+        if (X->dims[n] <= 0) return set_error(RBKI_E_INVAL, "dims must be positive");
+    if ((uintptr_t)X->data % 16) return set_error(RBKI_E_INVAL, "X->data must be 16-byte aligned");
+    return RBKI_OK;
+}
+
+rbki_status validate_params(const rbki_tensor* X, const rbki_params* prm) {
+    if (!prm) return set_error(RBKI_E_INVAL, "params is NULL");
+    if (prm->p < 0 || prm->q < 0) return set_error(RBKI_E_INVAL, "p and q must be >= 0");
+    if (prm->prec != RBKI_PREC_FP64 && prm->prec != RBKI_PREC_BF16 && prm->prec != RBKI_PREC_FP16)
+        return set_error(RBKI_E_INVAL, "unknown precision");
+    for (int n = 0; n < X->order; ++n) {
+        if (prm->ranks[n] < 1 || prm->ranks[n] > X->dims[n])
+            return set_error(RBKI_E_INVAL, "ranks must satisfy 1 <= R_n <= I_n");
+    }
+    return RBKI_OK;
+}
+
+rbki_status make_plan(const rbki_tensor* X, const rbki_params* prm, Plan& pl) {
+    RBKI_TRY(validate_tensor(X));
+    RBKI_TRY(validate_params(X, prm));
+    pl = Plan();
+    pl.N = X->order;
+    pl.dtype = X->dtype;
+    pl.prec = prm->prec;
+    pl.numel = 1;
+    for (int n = 0; n < pl.N; ++n) {
+        pl.dims[n] = X->dims[n];
+        pl.numel *= X->dims[n];
+    }
+    pl.mixed = prm->prec != RBKI_PREC_FP64;
+    pl.stream_dtype = pl.mixed ? (prm->prec == RBKI_PREC_BF16 ? RBKI_BF16 : RBKI_F16) : X->dtype;
+    pl.stage = pl.mixed && X->dtype != pl.stream_dtype;
+    for (int n = 0; n < pl.N; ++n) {
+        ModePlan& m = pl.mode[n];
+        m.n = n;
+        m.I = pl.dims[n];
+        m.A = 1;
+        m.C = 1;
+        for (int k = 0; k < n; ++k) m.A *= pl.dims[k];
+        for (int k = n + 1; k < pl.N; ++k) m.C *= pl.dims[k];
+        m.R = prm->ranks[n];
+        m.S = (int)std::min<int64_t>(m.R + prm->p, m.I);
+        m.q = prm->q;
+        int64_t b = (int64_t)m.S * (m.q + 1);
+        m.gram = b >= m.I;
+        m.b = m.gram ? (int)m.I : (int)b;
+        if (m.gram && m.I > 256) return set_error(RBKI_E_UNSUPPORTED, "Gram path with I_n > 256");
+        if (!m.gram && m.b > 256) return set_error(RBKI_E_UNSUPPORTED, "Krylov width S(q+1) > 256");
+        if (!m.gram && m.S > 128) return set_error(RBKI_E_UNSUPPORTED, "sketch size > 128");
+    }
+    // core chain order: largest shrink I_n / R_n first (ties -> lower mode)
+    for (int n = 0; n < pl.N; ++n) pl.order[n] = n;
+    std::stable_sort(pl.order, pl.order + pl.N, [&](int a, int b) {
+        return (double)pl.dims[a] / prm->ranks[a] > (double)pl.dims[b] / prm->ranks[b];
+    });
+    pl.seed = prm->seed;
+    pl.flags = prm->flags;
+    pl.ranks_numel = 1;
+    for (int n = 0; n < pl.N; ++n) pl.ranks_numel *= prm->ranks[n];
+    return RBKI_OK;
+}
+
+// Workspace layout.  carve() with base == nullptr only measures.
+struct Carver {
+    char* base;
+    size_t off = 0;
+    explicit Carver(void* b) : base((char*)b) {}
+    template <typename T> T* take(size_t count) {
+        off = (off + 255) & ~(size_t)255;
+        T* p = base ? (T*)(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+void carve(Plan& pl, void* ws) {
+    Carver c(ws);
+    pl.scal = c.take<double>(4096);
+    if (pl.stage) pl.xs = c.take<char>((size_t)pl.numel * dtype_size(pl.stream_dtype));
+    for (int n = 0; n < pl.N; ++n) {
+        ModePlan& m = pl.mode[n];
+        int64_t d = m.A * m.C;
+        View v{nullptr, pl.stream_dtype, m.A, m.I, m.C};
+        m.nsplit = contract_nsplit(v);
+        m.Z = c.take<double>((size_t)m.b * m.b);
+        m.evec = c.take<double>((size_t)m.b * m.b);
+        m.eval = c.take<double>((size_t)m.b);
+        m.syev_ws = c.take<double>(syev_scratch_doubles(m.b));
+        m.kept = c.take<int32_t>(4);
+        if (m.gram) {
+            m.part = c.take<double>((size_t)m.nsplit * m.I * m.I);
+        } else {
+            m.Qall = c.take<double>((size_t)m.I * m.b);
+            m.Pall = c.take<double>((size_t)m.I * m.b);
+            m.part = c.take<double>((size_t)std::max<int64_t>((int64_t)m.nsplit * m.I * m.S,
+                                                             (int64_t)atb_nchunks(m.I) * m.b * m.b));
+            size_t orth = 0;
+            for (int j = 0; j <= m.q; ++j)
+                orth = std::max(orth, orth_scratch_doubles(m.I, j * m.S, m.S));
+            m.small = c.take<double>(orth);
+            m.Y = c.take<double>((size_t)d * m.S);
+        }
+    }
+    // core chain ping-pong buffers (FP64)
+    size_t maxbuf = 0;
+    {
+        int64_t cur[RBKI_MAX_ORDER];
+        for (int n = 0; n < pl.N; ++n) cur[n] = pl.dims[n];
+        for (int t = 0; t < pl.N; ++t) {
+            int m = pl.order[t];
+            cur[m] = pl.mode[m].R;
+            int64_t sz = 1;
+            for (int n = 0; n < pl.N; ++n) sz *= cur[n];
+            maxbuf = std::max(maxbuf, (size_t)sz);
+        }
+    }
+    pl.tbuf[0] = c.take<double>(maxbuf);
+    pl.tbuf[1] = c.take<double>(maxbuf);
+    pl.ws_bytes = c.off + 256;
+}
+
+// ---------------------------------------------------------------------------------
+// per-mode pipeline
+// ---------------------------------------------------------------------------------
+static const double TAU_DEFLATE = 1e-6;
+
+__global__ void k_symmetrize(double* Z, int n) {
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * n) return;
+    int i = e / n, j = e % n;
+    if (i < j) {
+        double v = 0.5 * (Z[i * n + j] + Z[j * n + i]);
+        Z[i * n + j] = v;
+        Z[j * n + i] = v;
+    }
+}
+
+rbki_status symmetrize_cuda(double* Z, int n, cudaStream_t st) {
+    k_symmetrize<<<(unsigned)cdiv((int64_t)n * n, 256), 256, 0, st>>>(Z, n);
+    RBKI_LAUNCH_CHECK("k_symmetrize");
+    return RBKI_OK;
+}
+
+View mode_view(const Plan& pl, const ModePlan& m) {
+    return View{pl.xstream, pl.stream_dtype, m.A, m.I, m.C};
+}
+
+// P = X_(n) (X_(n)^T Q) for Q (I x S, ld ldq) -> out (ld ldo), out2 (optional copy)
+rbki_status krylov_step(const Plan& pl, const ModePlan& m, const double* Q, int64_t ldq, int S,
+                        double* out, int64_t ldo, double* out2, int64_t ldo2, cudaStream_t st) {
+    View v = mode_view(pl, m);
+    int tok = prof_begin(RBKI_PROF_KRYLOV, st);
+    RBKI_TRY(ttm_cuda(v, Q, ldq, S, m.Y, RBKI_F64, pl.mixed, st));
+    RBKI_TRY(contract_cuda(v, m.Y, RBKI_F64, S, pl.mixed, m.part, m.nsplit, out, ldo, out2, ldo2, st));
+    prof_end(tok, st);
+    return RBKI_OK;
+}
+
+rbki_status orth2(const ModePlan& m, int col0, int32_t* kept, cudaStream_t st) {
+    RBKI_TRY(orth_pass_cuda(m.Qall, m.b, m.I, col0, m.S, TAU_DEFLATE, m.small, nullptr, st));
+    RBKI_TRY(orth_pass_cuda(m.Qall, m.b, m.I, col0, m.S, TAU_DEFLATE, m.small, kept, st));
+    return RBKI_OK;
+}
+
+// Algorithm 1 for mode n: Q = [Q_0 .. Q_q] in m.Qall, P_j = A Q_j in m.Pall
+rbki_status mode_basis(const Plan& pl, const ModePlan& m, int32_t* kept, cudaStream_t st) {
+    View v = mode_view(pl, m);
+    // step 1-2: W = X_(n) Omega  (Omega generated in the [A][S][C] layout)
+    int tok = prof_begin(RBKI_PROF_SKETCH, st);
+    RBKI_TRY(omega_f64_cuda(pl.seed, m.n, m.A, m.C, m.S, m.Y, st));
+    RBKI_TRY(contract_cuda(v, m.Y, RBKI_F64, m.S, pl.mixed, m.part, m.nsplit, m.Qall, m.b,
+                           nullptr, 0, st));
+    prof_end(tok, st);
+    RBKI_TRY(orth2(m, 0, kept, st));
+    // step 3: K = [W, A W, ..., A^q W], orthonormalised block by block (reading c2)
+    for (int j = 0; j <= m.q; ++j) {
+        bool more = j < m.q;
+        RBKI_TRY(krylov_step(pl, m, m.Qall + j * m.S, m.b, m.S, m.Pall + j * m.S, m.b,
+                             more ? m.Qall + (j + 1) * m.S : nullptr, m.b, st));
+        if (more) RBKI_TRY(orth2(m, (j + 1) * m.S, kept, st));
+    }
+    return RBKI_OK;
+}
+
+// Algorithm 2 steps 2-5 for mode n: U^(n) and its Ritz values
+rbki_status mode_factor(const Plan& pl, const ModePlan& m, double* U, double* eigvals,
+                        int32_t* info, cudaStream_t st) {
+    int32_t* kept = info ? info + m.n : m.kept;
+    if (m.gram) {
+        // b >= I: Z = X_(n) X_(n)^T, Q = I (reading c7)
+        View v = mode_view(pl, m);
+        int tok = prof_begin(RBKI_PROF_GRAM, st);
+        RBKI_TRY(contract_cuda(v, pl.xstream, pl.stream_dtype, (int)m.I, pl.mixed, m.part,
+                               m.nsplit, m.Z, m.I, nullptr, 0, st));
+        prof_end(tok, st);
+        RBKI_TRY(symmetrize_cuda(m.Z, (int)m.I, st));
+        RBKI_TRY(syev_cuda(m.Z, (int)m.I, m.eval, m.evec, m.syev_ws, st));
+        RBKI_TRY(form_factor_cuda(nullptr, 0, m.I, m.evec, (int)m.I, m.R, U, st));
+        if (info) RBKI_TRY(fill_i32_cuda(info + m.n, (int32_t)m.I, 1, st));
+    } else {
+        if (info) RBKI_TRY(fill_i32_cuda(info + m.n, 0, 1, st));
+        RBKI_TRY(mode_basis(pl, m, kept, st));
+        // step 3 (Remark 1): Z = Q^T X X^T Q = Q^T [P_0 .. P_q]
+        RBKI_TRY(atb_cuda(m.Qall, m.b, m.b, m.Pall, m.b, m.b, m.I, m.part, m.Z, m.b, st));
+        RBKI_TRY(symmetrize_cuda(m.Z, m.b, st));
+        // step 4: leading eigenvectors of Z; step 5: U = Q U~(:, 1:R)
+        RBKI_TRY(syev_cuda(m.Z, m.b, m.eval, m.evec, m.syev_ws, st));
+        RBKI_TRY(form_factor_cuda(m.Qall, m.b, m.I, m.evec, m.b, m.R, U, st));
+    }
+    if (eigvals) RBKI_TRY(copy_f64_cuda(m.eval, eigvals, m.R, st));
+    if (info) RBKI_TRY(fill_i32_cuda(info + pl.N + m.n, m.gram ? 1 : 0, 1, st));
+    return RBKI_OK;
+}
+
+// step 6: G = X x_1 U^(1)T ... x_N U^(N)T, largest shrink first
+rbki_status core_chain(const Plan& pl, double* const* factors, double* core, cudaStream_t st) {
+    int64_t cur[RBKI_MAX_ORDER];
+    for (int n = 0; n < pl.N; ++n) cur[n] = pl.dims[n];
+    const void* src = pl.xstream;
+    int src_dtype = pl.stream_dtype;
+    for (int t = 0; t < pl.N; ++t) {
+        int m = pl.order[t];
+        int64_t A = 1, C = 1;
+        for (int k = 0; k < m; ++k) A *= cur[k];
+        for (int k = m + 1; k < pl.N; ++k) C *= cur[k];
+        View v{src, src_dtype, A, cur[m], C};
+        double* dst = (t == pl.N - 1) ? core : pl.tbuf[t & 1];
+        int R = pl.mode[m].R;
+        int tok = t == 0 ? prof_begin(RBKI_PROF_TTM, st) : -1;
+        RBKI_TRY(ttm_cuda(v, factors[m], R, R, dst, RBKI_F64, pl.mixed && t == 0, st));
+        prof_end(tok, st);
+        cur[m] = R;
+        src = dst;
+        src_dtype = RBKI_F64;
+    }
+    return RBKI_OK;
+}
+
+rbki_status run_tucker(Plan& pl, const rbki_tucker_out* out, cudaStream_t st) {
+    double* norms = out->norms ? out->norms : pl.scal;
+    int tok = prof_begin(RBKI_PROF_STAGE, st);
+    if (pl.stage) {
+        RBKI_TRY(stage_cuda(pl.xin, pl.dtype, pl.numel, pl.xs, pl.stream_dtype, pl.scal + 64,
+                            norms, st));
+        pl.xstream = pl.xs;
+    } else {
+        pl.xstream = pl.xin;
+        RBKI_TRY(sumsq_cuda(pl.xin, pl.dtype, pl.numel, pl.scal + 64, norms, st));
+    }
+    prof_end(tok, st);
+    for (int n = 0; n < pl.N; ++n) {
+        double* ev = out->eigvals[n];
+        RBKI_TRY(mode_factor(pl, pl.mode[n], out->factors[n], ev, out->info, st));
+    }
+    RBKI_TRY(core_chain(pl, out->factors, out->core, st));
+    RBKI_TRY(sumsq_cuda(out->core, RBKI_F64, pl.ranks_numel, pl.scal + 64, norms + 1, st));
+    return RBKI_OK;
+}
+
+}  // namespace rbki
+
+using namespace rbki;
+
+extern "C" {
+
+const char* rbki_status_str(rbki_status s) {
+    switch (s) {
+        case RBKI_OK: return "ok";
+        case RBKI_PENDING: return "pending";
+        case RBKI_W_DEFLATED: return "warning: Krylov directions deflated";
+        case RBKI_E_INVAL: return "invalid argument";
+        case RBKI_E_NOMEM: return "out of memory / workspace too small";
+        case RBKI_E_CUDA: return "CUDA error";
+        case RBKI_E_UNSUPPORTED: return "unsupported";
+        case RBKI_E_TIMEOUT: return "timeout";
+        case RBKI_E_BUSY: return "busy";
+        case RBKI_E_CANCELLED: return "cancelled";
+        case RBKI_E_NOTFOUND: return "not found";
+        default: return "unknown status";
+    }
+}
+
+const char* rbki_last_error(void) { return g_err.c_str(); }
+
+uint64_t rbki_kernel_launches(void) { return g_launches.load(); }
+
+void rbki_profile_enable(int32_t on) { g_prof_on = on != 0; }
+
+void rbki_profile_reset(void) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_used = 0;
+}
+
+rbki_status rbki_profile_read(int32_t cls, uint64_t* count, double* total_ms) {
+    if (!count || !total_ms) return set_error(RBKI_E_INVAL, "NULL output");
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    uint64_t c = 0;
+    double t = 0.0;
+    for (size_t i = 0; i < g_prof_used; ++i) {
+        if (g_prof[i].cls != cls) continue;
+        RBKI_CUDA_TRY(cudaEventSynchronize(g_prof[i].b));
+        float ms = 0.f;
+        RBKI_CUDA_TRY(cudaEventElapsedTime(&ms, g_prof[i].a, g_prof[i].b));
+        t += ms;
+        ++c;
+    }
+    *count = c;
+    *total_ms = t;
+    return RBKI_OK;
+}
+
+rbki_status rbki_tucker_workspace(const rbki_tensor* X, const rbki_params* prm, size_t* bytes) {
+    if (!bytes) return set_error(RBKI_E_INVAL, "bytes is NULL");
+    Plan pl;
+    RBKI_TRY(make_plan(X, prm, pl));
+    carve(pl, nullptr);
+    size_t extra = 0;
+    if (prm->flags & RBKI_FLAG_HOST_IO) extra = host_io_bytes(pl);
+    *bytes = pl.ws_bytes + extra;
+    return RBKI_OK;
+}
+
+rbki_status rbki_tucker(const rbki_tensor* X, const rbki_params* prm, void* workspace,
+                        size_t workspace_bytes, const rbki_tucker_out* out, void* stream) {
+    Plan pl;
+    RBKI_TRY(make_plan(X, prm, pl));
+    if (!out || !out->core) return set_error(RBKI_E_INVAL, "out->core is NULL");
+    for (int n = 0; n < pl.N; ++n)
+        if (!out->factors[n]) return set_error(RBKI_E_INVAL, "out->factors[n] is NULL");
+    carve(pl, nullptr);
+    size_t need = pl.ws_bytes + ((prm->flags & RBKI_FLAG_HOST_IO) ? host_io_bytes(pl) : 0);
+    if (!workspace || workspace_bytes < need) return set_error(RBKI_E_NOMEM, "workspace too small");
+    cudaStream_t st = (cudaStream_t)stream;
+    carve(pl, workspace);
+    if (prm->flags & RBKI_FLAG_HOST_IO) return run_tucker_host_io(pl, X, out, workspace, st);
+    pl.xin = X->data;
+    return run_tucker(pl, out, st);
+}
+
+rbki_status rbki_krylov_product_workspace(const rbki_tensor* X, int32_t mode, int32_t prec,
+                                          int32_t s, size_t* bytes) {
+    if (!bytes) return set_error(RBKI_E_INVAL, "bytes is NULL");
+    RBKI_TRY(validate_tensor(X));
+    if (mode < 0 || mode >= X->order || s < 1 || s > 128)
+        return set_error(RBKI_E_INVAL, "mode or s out of range");
+    rbki_params prm{};
+    for (int n = 0; n < X->order; ++n) prm.ranks[n] = 1;
+    prm.p = 0;
+    prm.q = 0;
+    prm.prec = prec;
+    Plan pl;
+    RBKI_TRY(make_plan(X, &prm, pl));
+    ModePlan& m = pl.mode[mode];
+    View v{nullptr, pl.stream_dtype, m.A, m.I, m.C};
+    size_t b = 256 + (size_t)m.A * m.C * s * 8 + 256 +
+               (size_t)contract_nsplit(v) * m.I * s * 8 + 256 + 4096 * 8;
+    if (pl.stage) b += (size_t)pl.numel * dtype_size(pl.stream_dtype) + 256;
+    *bytes = b;
+    return RBKI_OK;
+}
+
+rbki_status rbki_krylov_product(const rbki_tensor* X, int32_t mode, int32_t prec, const double* Q,
+                                int32_t s, double* P, void* workspace, size_t workspace_bytes,
+                                void* stream) {
+    size_t need = 0;
+    RBKI_TRY(rbki_krylov_product_workspace(X, mode, prec, s, &need));
+    if (!Q || !P) return set_error(RBKI_E_INVAL, "Q/P NULL");
+    if (!workspace || workspace_bytes < need) return set_error(RBKI_E_NOMEM, "workspace too small");
+    rbki_params prm{};
+    for (int n = 0; n < X->order; ++n) prm.ranks[n] = 1;
+    prm.prec = prec;
+    Plan pl;
+    RBKI_TRY(make_plan(X, &prm, pl));
+    cudaStream_t st = (cudaStream_t)stream;
+    ModePlan m = pl.mode[mode];
+    m.S = s;
+    Carver c(workspace);
+    pl.scal = c.take<double>(4096);
+    View v0{nullptr, pl.stream_dtype, m.A, m.I, m.C};
+    m.nsplit = contract_nsplit(v0);
+    m.Y = c.take<double>((size_t)m.A * m.C * s);
+    m.part = c.take<double>((size_t)m.nsplit * m.I * s);
+    if (pl.stage) {
+        pl.xs = c.take<char>((size_t)pl.numel * dtype_size(pl.stream_dtype));
+        RBKI_TRY(stage_cuda(X->data, X->dtype, pl.numel, pl.xs, pl.stream_dtype, pl.scal + 64,
+                            pl.scal, st));
+        pl.xstream = pl.xs;
+    } else {
+        pl.xstream = X->data;
+    }
+    return krylov_step(pl, m, Q, s, s, P, s, nullptr, 0, st);
+}
+
+rbki_status rbki_mode_basis(const rbki_tensor* X, const rbki_params* prm, int32_t mode, double* Q,
+                            void* workspace, size_t workspace_bytes, void* stream) {
+    Plan pl;
+    RBKI_TRY(make_plan(X, prm, pl));
+    if (mode < 0 || mode >= pl.N) return set_error(RBKI_E_INVAL, "mode out of range");
+    if (pl.mode[mode].gram) return set_error(RBKI_E_INVAL, "mode uses the Gram path (b >= I)");
+    if (!Q) return set_error(RBKI_E_INVAL, "Q is NULL");
+    carve(pl, nullptr);
+    if (!workspace || workspace_bytes < pl.ws_bytes) return set_error(RBKI_E_NOMEM, "workspace too small");
+    carve(pl, workspace);
+    cudaStream_t st = (cudaStream_t)stream;
+    pl.xin = X->data;
+    if (pl.stage) {
+        RBKI_TRY(stage_cuda(pl.xin, pl.dtype, pl.numel, pl.xs, pl.stream_dtype, pl.scal + 64,
+                            pl.scal, st));
+        pl.xstream = pl.xs;
+    } else {
+        pl.xstream = pl.xin;
+    }
+    const ModePlan& m = pl.mode[mode];
+    RBKI_TRY(fill_i32_cuda(m.kept, 0, 1, st));
+    RBKI_TRY(mode_basis(pl, m, m.kept, st));
+    RBKI_TRY(copy_f64_cuda(m.Qall, Q, m.I * m.b, st));
+    return RBKI_OK;
+}
+
+rbki_status rbki_syev_workspace(int32_t n, size_t* bytes) {
+    if (!bytes || n < 1 || n > 256) return set_error(RBKI_E_INVAL, "n out of range");
+    *bytes = syev_scratch_doubles(n) * sizeof(double);
+    return RBKI_OK;
+}
+
+rbki_status rbki_syev(const double* A, int32_t n, double* w, double* V, void* workspace,
+                      size_t workspace_bytes, void* stream) {
+    size_t need = 0;
+    RBKI_TRY(rbki_syev_workspace(n, &need));
+    if (!A || !w || !V) return set_error(RBKI_E_INVAL, "NULL argument");
+    if (!workspace || workspace_bytes < need) return set_error(RBKI_E_NOMEM, "workspace too small");
+    return syev_cuda(A, n, w, V, (double*)workspace, (cudaStream_t)stream);
+}
+
+}  // extern "C"

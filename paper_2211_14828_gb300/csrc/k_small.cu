@@ -1,0 +1,426 @@
+// Small dense FP64 kernels of Algorithms 1-2:
+//   * A^T B with a fixed-order split reduction (block Gram-Schmidt coefficients, Gram
+//     matrices, Z = Q^T P of Remark 1)
+//   * one pass of block orthonormalisation: Pythagorean-inner-product block classical
+//     Gram-Schmidt (BCGS-PIP, Barlow & Smoktunowicz 2013) + Cholesky QR with pivot
+//     deflation (reading c3); two passes give BCGS2 / CholQR2
+//   * cyclic Jacobi eigensolver (Jacobi 1846; Rutishauser's rotation formulas; round-robin
+//     parallel ordering) for Algorithm 2 step 4
+//   * factor formation U = Q U~(:, 1:R) with the sign convention (Algorithm 2 step 5).
+#include "kernels.h"
+
+namespace rbki {
+namespace {
+
+constexpr int AT_T = 32;    // output tile
+constexpr int AT_K = 16;    // rows per sub-chunk
+
+// part[chunk][k][l] = sum_{r in chunk} A[r][k] B[r][l]
+__global__ void __launch_bounds__(256) k_atb_part(const double* __restrict__ A, int64_t lda, int ma,
+                                                  const double* __restrict__ B, int64_t ldb, int mb,
+                                                  int64_t rows, int64_t rows_per_chunk,
+                                                  double* __restrict__ part) {
+    __shared__ double as[AT_K][AT_T + 1];
+    __shared__ double bs[AT_K][AT_T + 1];
+    const int tid = threadIdx.x;
+    const int tk = tid / 16, tl = tid % 16;          // 2 x 2 outputs per thread
+    const int k0 = blockIdx.x * AT_T, l0 = blockIdx.y * AT_T;
+    const int64_t r_lo = (int64_t)blockIdx.z * rows_per_chunk;
+    const int64_t r_hi = min(rows, r_lo + rows_per_chunk);
+    double acc[2][2] = {{0, 0}, {0, 0}};
+    for (int64_t r0 = r_lo; r0 < r_hi; r0 += AT_K) {
+        for (int e = tid; e < AT_K * AT_T; e += 256) {
+            int rr = e / AT_T, cc = e % AT_T;
+            int64_t r = r0 + rr;
+            bool ok = r < r_hi;
+            as[rr][cc] = (ok && k0 + cc < ma) ? A[r * lda + k0 + cc] : 0.0;
+            bs[rr][cc] = (ok && l0 + cc < mb) ? B[r * ldb + l0 + cc] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int rr = 0; rr < AT_K; ++rr) {
+            double a0 = as[rr][tk], a1 = as[rr][tk + 16];
+            double b0 = bs[rr][tl], b1 = bs[rr][tl + 16];
+            acc[0][0] += a0 * b0; acc[0][1] += a0 * b1;
+            acc[1][0] += a1 * b0; acc[1][1] += a1 * b1;
+        }
+        __syncthreads();
+    }
+    double* out = part + (int64_t)blockIdx.z * ma * mb;
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+            int k = k0 + tk + 16 * u, l = l0 + tl + 16 * v;
+            if (k < ma && l < mb) out[(int64_t)k * mb + l] = acc[u][v];
+        }
+}
+
+__global__ void k_atb_reduce(const double* __restrict__ part, int nchunk, int ma, int mb,
+                             double* __restrict__ out, int64_t ldo) {
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ma * mb) return;
+    double acc = 0.0;
+    for (int c = 0; c < nchunk; ++c) acc += part[(int64_t)c * ma * mb + e];
+    out[(int64_t)(e / mb) * ldo + e % mb] = acc;
+}
+
+// G'[k][l] = M[m+k][l] - sum_{r<m} M[r][k] M[r][l]  (Pythagorean Gram of the projected block)
+// nu2[k] = M[m+k][k] (squared column norms before projection).  One CTA per column l.
+__global__ void k_gprime(const double* __restrict__ M, int m, int S, double* __restrict__ Gp,
+                         double* __restrict__ nu2) {
+    int l = blockIdx.x, k = threadIdx.x;
+    if (k >= S) return;
+    double g = M[(int64_t)(m + k) * S + l];
+    double acc = 0.0;
+    for (int r = 0; r < m; ++r) acc += M[(int64_t)r * S + k] * M[(int64_t)r * S + l];
+    Gp[k * S + l] = g - acc;
+    if (k == l) nu2[k] = g;
+}
+
+// Cholesky G' = R^T R with pivot deflation, then Rinv (upper) with zero rows/columns for
+// deflated directions.  Column k is deflated when nu2[k] == 0 or its pivot (squared norm
+// orthogonal to everything accepted) <= tau^2 nu2[k].  Single CTA, S <= blockDim.x.
+__global__ void k_chol_deflate(const double* __restrict__ Gp, const double* __restrict__ nu2,
+                               int S, double tau, double* __restrict__ Rinv,
+                               int32_t* __restrict__ kept) {
+    extern __shared__ double sm[];
+    double* R = sm;              // S x S
+    double* t = sm + S * S;      // S
+    __shared__ int keep_flag;
+    __shared__ int nkept;
+    const int j = threadIdx.x;
+    for (int e = j; e < S * S; e += blockDim.x) R[e] = 0.0;
+    if (j == 0) nkept = 0;
+    __syncthreads();
+    for (int k = 0; k < S; ++k) {
+        if (j >= k && j < S) {
+            double acc = Gp[k * S + j];
+            for (int i = 0; i < k; ++i) acc -= R[i * S + k] * R[i * S + j];
+            t[j] = acc;
+        }
+        __syncthreads();
+        if (j == 0) {
+            double d = t[k], nu = nu2[k];
+            keep_flag = (nu > 0.0 && d > tau * tau * nu) ? 1 : 0;
+            if (keep_flag) { R[k * S + k] = sqrt(d); ++nkept; }
+        }
+        __syncthreads();
+        if (keep_flag && j > k && j < S) R[k * S + j] = t[j] / R[k * S + k];
+        __syncthreads();
+    }
+    // Rinv: column j by back substitution over kept rows
+    if (j < S) {
+        for (int i = 0; i < S; ++i) Rinv[i * S + j] = 0.0;
+        double rjj = R[j * S + j];
+        if (rjj != 0.0) {
+            Rinv[j * S + j] = 1.0 / rjj;
+            for (int i = j - 1; i >= 0; --i) {
+                double rii = R[i * S + i];
+                if (rii == 0.0) continue;
+                double acc = 0.0;
+                for (int tt = i + 1; tt <= j; ++tt) acc += R[i * S + tt] * Rinv[tt * S + j];
+                Rinv[i * S + j] = -acc / rii;
+            }
+        }
+    }
+    if (j == 0 && kept) atomicAdd(kept, nkept);
+}
+
+// Q[i][m+s] = sum_t (Q[i][m+t] - sum_{r<m} Q[i][r] M[r][t]) Rinv[t][s]; ORTH_ROWS rows per CTA
+constexpr int ORTH_ROWS = 8;
+__global__ void k_orth_apply(double* __restrict__ Q, int64_t ldq, int64_t rows, int m, int S,
+                             const double* __restrict__ M, const double* __restrict__ Rinv) {
+    extern __shared__ double tmp[];   // ORTH_ROWS x S
+    const int64_t i0 = (int64_t)blockIdx.x * ORTH_ROWS;
+    for (int e = threadIdx.x; e < ORTH_ROWS * S; e += blockDim.x) {
+        int rr = e / S, s = e % S;
+        int64_t i = i0 + rr;
+        double v = 0.0;
+        if (i < rows) {
+            const double* qi = Q + i * ldq;
+            v = qi[m + s];
+            for (int r = 0; r < m; ++r) v -= qi[r] * M[(int64_t)r * S + s];
+        }
+        tmp[e] = v;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < ORTH_ROWS * S; e += blockDim.x) {
+        int rr = e / S, s = e % S;
+        int64_t i = i0 + rr;
+        if (i >= rows) continue;
+        double acc = 0.0;
+        for (int tt = 0; tt <= s; ++tt) acc += tmp[rr * S + tt] * Rinv[tt * S + s];
+        Q[i * ldq + m + s] = acc;
+    }
+}
+
+// ---- cyclic Jacobi, one CTA ----
+__device__ __forceinline__ void rr_pair(int r, int k, int m, int& p, int& q) {
+    // circle method: position 0 fixed, positions 1..m-1 rotate by r
+    auto idx = [&](int pos) { return pos == 0 ? 0 : ((pos - 1 + r) % (m - 1)) + 1; };
+    p = idx(k);
+    q = idx(m - 1 - k);
+    if (p > q) { int t = p; p = q; q = t; }
+}
+
+__global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ Ain, int n,
+                                                 double* __restrict__ w, double* __restrict__ Vout,
+                                                 double* __restrict__ work, int use_smem,
+                                                 int max_sweeps) {
+    extern __shared__ double sm[];
+    double* a = use_smem ? sm : work;
+    double* v = use_smem ? sm + (size_t)n * n : work + (size_t)n * n;
+    __shared__ double cs[128], sn[128];
+    __shared__ int pp[128], qq[128];
+    __shared__ double red[32];
+    __shared__ int stop;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int e = tid; e < n * n; e += nt) {
+        a[e] = Ain[e];
+        v[e] = (e / n == e % n) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    const int m = n + (n & 1);
+    const int half = m / 2;
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int e = tid; e < n * n; e += nt) {
+            double x = a[e] * a[e];
+            tot += x;
+            if (e / n != e % n) off += x;
+        }
+        off = warp_sum(off);
+        tot = warp_sum(tot);
+        if ((tid & 31) == 0) red[tid >> 5] = off;
+        __syncthreads();
+        if (tid < 32) {
+            double x = tid < (nt >> 5) ? red[tid] : 0.0;
+            x = warp_sum(x);
+            if (tid == 0) red[0] = x;
+        }
+        __syncthreads();
+        off = red[0];
+        __syncthreads();
+        if ((tid & 31) == 0) red[tid >> 5] = tot;
+        __syncthreads();
+        if (tid < 32) {
+            double x = tid < (nt >> 5) ? red[tid] : 0.0;
+            x = warp_sum(x);
+            if (tid == 0) stop = (off <= 1e-30 * x) ? 1 : 0;
+        }
+        __syncthreads();
+        if (stop) break;
+        for (int r = 0; r < m - 1; ++r) {
+            if (tid < half) {
+                int p, q;
+                rr_pair(r, tid, m, p, q);
+                double c = 1.0, s = 0.0;
+                if (q < n) {
+                    double apq = a[p * n + q];
+                    if (apq != 0.0) {
+                        double th = (a[q * n + q] - a[p * n + p]) / (2.0 * apq);
+                        double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                        c = 1.0 / sqrt(t * t + 1.0);
+                        s = t * c;
+                    }
+                }
+                pp[tid] = p; qq[tid] = (q < n) ? q : -1; cs[tid] = c; sn[tid] = s;
+            }
+            __syncthreads();
+            for (int e = tid; e < half * n; e += nt) {     // rows p, q
+                int k = e / n, j = e % n;
+                int q = qq[k];
+                if (q < 0 || sn[k] == 0.0) continue;
+                int p = pp[k];
+                double c = cs[k], s = sn[k];
+                double ap = a[p * n + j], aq = a[q * n + j];
+                a[p * n + j] = c * ap - s * aq;
+                a[q * n + j] = s * ap + c * aq;
+            }
+            __syncthreads();
+            for (int e = tid; e < half * n; e += nt) {     // columns p, q of A and V
+                int k = e / n, j = e % n;
+                int q = qq[k];
+                if (q < 0 || sn[k] == 0.0) continue;
+                int p = pp[k];
+                double c = cs[k], s = sn[k];
+                double ap = a[j * n + p], aq = a[j * n + q];
+                a[j * n + p] = c * ap - s * aq;
+                a[j * n + q] = s * ap + c * aq;
+                double vp = v[j * n + p], vq = v[j * n + q];
+                v[j * n + p] = c * vp - s * vq;
+                v[j * n + q] = s * vp + c * vq;
+            }
+            __syncthreads();
+        }
+    }
+    // descending order: rank_i = #{j : d_j > d_i or (d_j == d_i and j < i)}
+    for (int i = tid; i < n; i += nt) {
+        double di = a[i * n + i];
+        int rank = 0;
+        for (int j = 0; j < n; ++j) {
+            double dj = a[j * n + j];
+            rank += (dj > di || (dj == di && j < i)) ? 1 : 0;
+        }
+        w[rank] = di;
+        for (int j = 0; j < n; ++j) Vout[j * n + rank] = v[j * n + i];
+    }
+}
+
+// U[i][k] = sum_t Q[i][t] V[t][k]  (or V[i][k] when Q == nullptr)
+__global__ void k_form_u(const double* __restrict__ Q, int64_t ldq, int64_t rows,
+                         const double* __restrict__ V, int n, int R, double* __restrict__ U) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= rows * R) return;
+    int64_t i = e / R;
+    int k = (int)(e % R);
+    double acc;
+    if (Q) {
+        acc = 0.0;
+        const double* qi = Q + i * ldq;
+        for (int t = 0; t < n; ++t) acc += qi[t] * V[(int64_t)t * n + k];
+    } else {
+        acc = V[i * n + k];
+    }
+    U[e] = acc;
+}
+
+// largest-|.| entry of column k made positive (lowest row index on ties); one CTA per column
+__global__ void k_sign_fix(double* __restrict__ U, int64_t rows, int R) {
+    const int k = blockIdx.x;
+    double best = -1.0;
+    int64_t bi = 0x7fffffffffffffffLL;
+    for (int64_t i = threadIdx.x; i < rows; i += blockDim.x) {
+        double x = fabs(U[i * R + k]);
+        if (x > best) { best = x; bi = i; }
+    }
+    __shared__ double sb[1024];
+    __shared__ int64_t si[1024];
+    sb[threadIdx.x] = best;
+    si[threadIdx.x] = bi;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o; o >>= 1) {
+        if (threadIdx.x < o) {
+            double b2 = sb[threadIdx.x + o];
+            int64_t i2 = si[threadIdx.x + o];
+            if (b2 > sb[threadIdx.x] || (b2 == sb[threadIdx.x] && i2 < si[threadIdx.x])) {
+                sb[threadIdx.x] = b2;
+                si[threadIdx.x] = i2;
+            }
+        }
+        __syncthreads();
+    }
+    int64_t piv = si[0];
+    if (piv >= rows) return;
+    bool flip = U[piv * R + k] < 0.0;
+    __syncthreads();
+    if (flip)
+        for (int64_t i = threadIdx.x; i < rows; i += blockDim.x) U[i * R + k] = -U[i * R + k];
+}
+
+__global__ void k_copy(const double* __restrict__ s, double* __restrict__ d, int64_t n) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) d[e] = s[e];
+}
+__global__ void k_fill_i32(int32_t* d, int32_t v, int n) {
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) d[e] = v;
+}
+
+}  // namespace
+
+int atb_nchunks(int64_t rows) {
+    int64_t n = cdiv(rows, 32);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(n, 64));
+}
+
+rbki_status atb_cuda(const double* A, int64_t lda, int ma, const double* B, int64_t ldb, int mb,
+                     int64_t rows, double* part, double* out, int64_t ldo, cudaStream_t st) {
+    int nch = atb_nchunks(rows);
+    int64_t rpc = cdiv(rows, nch);
+    dim3 grid((unsigned)cdiv(ma, AT_T), (unsigned)cdiv(mb, AT_T), (unsigned)nch);
+    k_atb_part<<<grid, 256, 0, st>>>(A, lda, ma, B, ldb, mb, rows, rpc, part);
+    RBKI_LAUNCH_CHECK("k_atb_part");
+    k_atb_reduce<<<(unsigned)cdiv((int64_t)ma * mb, 256), 256, 0, st>>>(part, nch, ma, mb, out, ldo);
+    RBKI_LAUNCH_CHECK("k_atb_reduce");
+    return RBKI_OK;
+}
+
+size_t orth_scratch_doubles(int64_t rows, int m, int S) {
+    size_t mp = (size_t)(m + S) * S;
+    return (size_t)atb_nchunks(rows) * mp + mp + 2 * (size_t)S * S + S + 64;
+}
+
+rbki_status orth_pass_cuda(double* Q, int64_t ldq, int64_t rows, int m, int S, double tau,
+                           double* scratch, int32_t* kept, cudaStream_t st) {
+    if (S > 128) return set_error(RBKI_E_UNSUPPORTED, "orth: block width > 128");
+    size_t mp = (size_t)(m + S) * S;
+    double* part = scratch;
+    double* M = part + (size_t)atb_nchunks(rows) * mp;
+    double* Gp = M + mp;
+    double* Rinv = Gp + (size_t)S * S;
+    double* nu2 = Rinv + (size_t)S * S;
+    RBKI_TRY(atb_cuda(Q, ldq, m + S, Q + m, ldq, S, rows, part, M, S, st));
+    k_gprime<<<S, 128, 0, st>>>(M, m, S, Gp, nu2);
+    RBKI_LAUNCH_CHECK("k_gprime");
+    size_t sm = ((size_t)S * S + S) * sizeof(double);
+    static bool attr_done = false;
+    if (!attr_done) {
+        RBKI_CUDA_TRY(cudaFuncSetAttribute(k_chol_deflate, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           160 * 1024));
+        attr_done = true;
+    }
+    k_chol_deflate<<<1, 128, sm, st>>>(Gp, nu2, S, tau, Rinv, kept);
+    RBKI_LAUNCH_CHECK("k_chol_deflate");
+    k_orth_apply<<<(unsigned)cdiv(rows, ORTH_ROWS), 256, ORTH_ROWS * S * sizeof(double), st>>>(
+        Q, ldq, rows, m, S, M, Rinv);
+    RBKI_LAUNCH_CHECK("k_orth_apply");
+    return RBKI_OK;
+}
+
+size_t syev_scratch_doubles(int n) { return 2 * (size_t)n * n + 64; }
+
+rbki_status syev_cuda(const double* A, int n, double* w, double* V, double* scratch,
+                      cudaStream_t st) {
+    if (n > 256) return set_error(RBKI_E_UNSUPPORTED, "syev: n > 256");
+    size_t need = 2 * (size_t)n * n * sizeof(double);
+    int use_smem = need <= 200 * 1024;
+    if (use_smem) {
+        static bool attr_done = false;
+        if (!attr_done) {
+            RBKI_CUDA_TRY(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               200 * 1024));
+            attr_done = true;
+        }
+    }
+    k_jacobi<<<1, 1024, use_smem ? need : 0, st>>>(A, n, w, V, scratch, use_smem, 40);
+    RBKI_LAUNCH_CHECK("k_jacobi");
+    return RBKI_OK;
+}
+
+rbki_status form_factor_cuda(const double* Q, int64_t ldq, int64_t rows, const double* V, int n,
+                             int R, double* U, cudaStream_t st) {
+    int64_t tot = rows * R;
+    k_form_u<<<(unsigned)cdiv(tot, 256), 256, 0, st>>>(Q, ldq, rows, V, n, R, U);
+    RBKI_LAUNCH_CHECK("k_form_u");
+    k_sign_fix<<<R, 256, 0, st>>>(U, rows, R);
+    RBKI_LAUNCH_CHECK("k_sign_fix");
+    return RBKI_OK;
+}
+
+rbki_status copy_f64_cuda(const double* src, double* dst, int64_t n, cudaStream_t st) {
+    if (n <= 0) return RBKI_OK;
+    k_copy<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(src, dst, n);
+    RBKI_LAUNCH_CHECK("k_copy");
+    return RBKI_OK;
+}
+
+rbki_status fill_i32_cuda(int32_t* dst, int32_t v, int n, cudaStream_t st) {
+    if (n <= 0) return RBKI_OK;
+    k_fill_i32<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(dst, v, n);
+    RBKI_LAUNCH_CHECK("k_fill_i32");
+    return RBKI_OK;
+}
+
+}  // namespace rbki

@@ -1,0 +1,260 @@
+// CUDA-core streaming products over the strided mode-n view X = [A][I][C]:
+//   * TTM     Y = X x_n M^T             (Algorithm 2 step 6; Krylov half-step X_(n)^T Q)
+//   * contract P = X_(n) Y_(n)^T        (Algorithm 1 steps 2-3: sketch W = X Omega and the
+//                                        Krylov product X (X^T Q); Gram X X^T when Y == X)
+// These are the FP64 comparator path (FP64 accumulate) and the FP32-accumulate CUDA-core
+// path for small-I Gram passes.  The unfolding is never materialised: element (i, col) of
+// X_(n) is X[(col / C) * I * C + i * C + col % C].
+#include "kernels.h"
+
+namespace rbki {
+namespace {
+
+constexpr int TT_COLS = 64;   // columns of X_(n) per TTM tile
+constexpr int TT_K = 16;      // rows of X_(n) per k-chunk
+constexpr int MAXS = 64;      // s per tile
+
+template <typename T, typename Acc, typename To>
+__global__ void __launch_bounds__(256) k_ttm(const T* __restrict__ X, int64_t A, int64_t I,
+                                             int64_t C, const double* __restrict__ M, int64_t ldm,
+                                             int S, To* __restrict__ Y) {
+    __shared__ Acc xs[TT_K][TT_COLS + 1];
+    __shared__ Acc ms[TT_K][MAXS + 1];
+    const int tid = threadIdx.x;
+    const int tx = tid % 16, ty = tid / 16;
+    const int s0 = blockIdx.y * MAXS;
+    // tile -> columns
+    int64_t a0, c0;
+    const bool cfast = C > 1;
+    if (cfast) {
+        int64_t ctiles = cdiv(C, TT_COLS);
+        a0 = blockIdx.x / ctiles;
+        c0 = (blockIdx.x % ctiles) * TT_COLS;
+    } else {
+        a0 = (int64_t)blockIdx.x * TT_COLS;
+        c0 = 0;
+    }
+    Acc acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = 0;
+
+    for (int64_t i0 = 0; i0 < I; i0 += TT_K) {
+        // load X chunk [TT_K][TT_COLS]
+        for (int e = tid; e < TT_K * TT_COLS; e += 256) {
+            int ii, jj;
+            if (cfast) { ii = e / TT_COLS; jj = e % TT_COLS; }
+            else { jj = e / TT_K; ii = e % TT_K; }
+            int64_t i = i0 + ii;
+            Acc v = 0;
+            if (i < I) {
+                if (cfast) {
+                    int64_t c = c0 + jj;
+                    if (c < C) v = (Acc)ld_f64(X + (a0 * I + i) * C + c);
+                } else {
+                    int64_t a = a0 + jj;
+                    if (a < A) v = (Acc)ld_f64(X + a * I + i);
+                }
+            }
+            xs[ii][jj] = v;
+        }
+        for (int e = tid; e < TT_K * MAXS; e += 256) {
+            int ii = e / MAXS, ss = e % MAXS;
+            int64_t i = i0 + ii;
+            int s = s0 + ss;
+            ms[ii][ss] = (i < I && s < S) ? (Acc)M[i * ldm + s] : (Acc)0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < TT_K; ++kk) {
+            Acc xv[4], mv[4];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) xv[v] = xs[kk][tx * 4 + v];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) mv[u] = ms[kk][ty + 16 * u];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] += mv[u] * xv[v];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        int s = s0 + ty + 16 * u;
+        if (s >= S) continue;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            int jj = tx * 4 + v;
+            if (cfast) {
+                int64_t c = c0 + jj;
+                if (c < C) Y[(a0 * S + s) * C + c] = (To)acc[u][v];
+            } else {
+                int64_t a = a0 + jj;
+                if (a < A) Y[a * S + s] = (To)acc[u][v];
+            }
+        }
+    }
+}
+
+constexpr int CT_ROWS = 64;   // rows of X_(n) (i) per contraction tile
+constexpr int CT_K = 16;      // columns per chunk
+
+// P_part[split][i][s] = sum over the split's columns of X[i][col] * Y[s][col]
+template <typename T, typename TY, typename Acc>
+__global__ void __launch_bounds__(256) k_contract(const T* __restrict__ X, int64_t A, int64_t I,
+                                                  int64_t C, const TY* __restrict__ Y, int S,
+                                                  int64_t cols_per_split, double* __restrict__ part) {
+    __shared__ Acc xs[CT_K][CT_ROWS + 1];
+    __shared__ Acc ys[CT_K][MAXS + 1];
+    const int tid = threadIdx.x;
+    const int tx = tid % 16, ty = tid / 16;
+    const int64_t i0 = (int64_t)blockIdx.x * CT_ROWS;
+    const int s0 = blockIdx.y * MAXS;
+    const int64_t d = A * C;
+    const int64_t col_lo = (int64_t)blockIdx.z * cols_per_split;
+    const int64_t col_hi = min(d, col_lo + cols_per_split);
+    Acc acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = 0;
+
+    for (int64_t k0 = col_lo; k0 < col_hi; k0 += CT_K) {
+        for (int e = tid; e < CT_K * CT_ROWS; e += 256) {
+            int kk, ii;
+            if (C > 1) { ii = e / CT_K; kk = e % CT_K; }     // consecutive columns: coalesced in c
+            else { kk = e / CT_ROWS; ii = e % CT_ROWS; }      // C == 1: coalesced in i
+            int64_t col = k0 + kk, i = i0 + ii;
+            Acc v = 0;
+            if (col < col_hi && i < I) {
+                int64_t a = col / C, c = col - a * C;
+                v = (Acc)ld_f64(X + (a * I + i) * C + c);
+            }
+            xs[kk][ii] = v;
+        }
+        for (int e = tid; e < CT_K * MAXS; e += 256) {
+            int kk, ss;
+            if (C > 1) { ss = e / CT_K; kk = e % CT_K; }
+            else { kk = e / MAXS; ss = e % MAXS; }
+            int64_t col = k0 + kk;
+            int s = s0 + ss;
+            Acc v = 0;
+            if (col < col_hi && s < S) {
+                int64_t a = col / C, c = col - a * C;
+                v = (Acc)ld_f64(Y + (a * S + s) * C + c);
+            }
+            ys[kk][ss] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < CT_K; ++kk) {
+            Acc xv[4], yv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) xv[u] = xs[kk][ty + 16 * u];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) yv[v] = ys[kk][tx + 16 * v];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] += xv[u] * yv[v];
+        }
+        __syncthreads();
+    }
+    double* out = part + (int64_t)blockIdx.z * I * S;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        int64_t i = i0 + ty + 16 * u;
+        if (i >= I) continue;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            int s = s0 + tx + 16 * v;
+            if (s < S) out[i * S + s] = (double)acc[u][v];
+        }
+    }
+}
+
+// out[i*ld + s] = sum_{k < nsplit} part[k][i][s]   (fixed order: deterministic)
+__global__ void k_reduce_parts(const double* __restrict__ part, int nsplit, int64_t I, int S,
+                               double* __restrict__ out, int64_t ld, double* __restrict__ out2,
+                               int64_t ld2) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= I * S) return;
+    double acc = 0.0;
+    for (int k = 0; k < nsplit; ++k) acc += part[(int64_t)k * I * S + e];
+    int64_t i = e / S, s = e % S;
+    out[i * ld + s] = acc;
+    if (out2) out2[i * ld2 + s] = acc;
+}
+
+template <typename T>
+const T* as(const void* p) { return static_cast<const T*>(p); }
+
+}  // namespace
+
+rbki_status ttm_cuda(const View& x, const double* M, int64_t ldm, int S, void* Y, int y_dtype,
+                     bool acc32, cudaStream_t st) {
+    int64_t ntiles = x.C > 1 ? x.A * cdiv(x.C, TT_COLS) : cdiv(x.A, TT_COLS);
+    if (ntiles > 0x7fffffff) return set_error(RBKI_E_UNSUPPORTED, "ttm: too many tiles");
+    dim3 grid((unsigned)ntiles, (unsigned)cdiv(S, MAXS));
+#define TTM_L(T, ACC, TO)                                                                   \
+    k_ttm<T, ACC, TO><<<grid, 256, 0, st>>>(as<T>(x.data), x.A, x.I, x.C, M, ldm, S,        \
+                                            static_cast<TO*>(Y))
+#define TTM_D(T)                                                                            \
+    if (y_dtype == RBKI_F64) { if (acc32) TTM_L(T, float, double); else TTM_L(T, double, double); } \
+    else if (y_dtype == RBKI_F32) { if (acc32) TTM_L(T, float, float); else TTM_L(T, double, float); } \
+    else return set_error(RBKI_E_INVAL, "ttm: output dtype");
+    switch (x.dtype) {
+        case RBKI_F64: TTM_D(double); break;
+        case RBKI_F32: TTM_D(float); break;
+        case RBKI_BF16: TTM_D(__nv_bfloat16); break;
+        case RBKI_F16: TTM_D(__half); break;
+        default: return set_error(RBKI_E_INVAL, "ttm: dtype");
+    }
+#undef TTM_D
+#undef TTM_L
+    RBKI_LAUNCH_CHECK("k_ttm");
+    return RBKI_OK;
+}
+
+int contract_nsplit(const View& x) {
+    int64_t d = x.A * x.C;
+    int64_t itiles = cdiv(x.I, CT_ROWS);
+    int64_t want = cdiv(4 * 152, itiles);
+    int64_t maxs = cdiv(d, 256);
+    int64_t n = want < maxs ? want : maxs;
+    return (int)(n < 1 ? 1 : n);
+}
+
+rbki_status contract_cuda(const View& x, const void* Y, int y_dtype, int S, bool acc32,
+                          double* part, int nsplit, double* out, int64_t ld_out, double* out2,
+                          int64_t ld_out2, cudaStream_t st) {
+    int64_t d = x.A * x.C;
+    int64_t cps = rup(cdiv(d, nsplit), CT_K);
+    dim3 grid((unsigned)cdiv(x.I, CT_ROWS), (unsigned)cdiv(S, MAXS), (unsigned)nsplit);
+#define CT_L(T, TY, ACC)                                                                   \
+    k_contract<T, TY, ACC><<<grid, 256, 0, st>>>(as<T>(x.data), x.A, x.I, x.C, as<TY>(Y), S, \
+                                                 cps, part)
+#define CT_D(T)                                                                            \
+    if (y_dtype == RBKI_F64) { if (acc32) CT_L(T, double, float); else CT_L(T, double, double); } \
+    else if (y_dtype == x.dtype) { if (acc32) CT_L(T, T, float); else CT_L(T, T, double); }  \
+    else return set_error(RBKI_E_INVAL, "contract: Y dtype");
+    switch (x.dtype) {
+        case RBKI_F64: CT_D(double); break;
+        case RBKI_F32: CT_D(float); break;
+        case RBKI_BF16: CT_D(__nv_bfloat16); break;
+        case RBKI_F16: CT_D(__half); break;
+        default: return set_error(RBKI_E_INVAL, "contract: dtype");
+    }
+#undef CT_D
+#undef CT_L
+    RBKI_LAUNCH_CHECK("k_contract");
+    int64_t n = x.I * S;
+    k_reduce_parts<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(part, nsplit, x.I, S, out, ld_out,
+                                                            out2, ld_out2);
+    RBKI_LAUNCH_CHECK("k_reduce_parts");
+    return RBKI_OK;
+}
+
+}  // namespace rbki

@@ -1,0 +1,66 @@
+// Internal launch wrappers of librbki (host side).  Not part of the C ABI.
+#pragma once
+
+#include "common.cuh"
+
+namespace rbki {
+
+// View of the streamed tensor for mode n: X as [A][I][C] (A = prod of dims before n,
+// C = prod of dims after n).  Column `col` of X_(n) is (a, c) = (col / C, col % C).
+struct View {
+    const void* data;
+    int dtype;  // RBKI_F64 / F32 / BF16 / F16
+    int64_t A, I, C;
+};
+
+// ---- FP64/FP32 CUDA-core streaming products (k_stream.cu) ----
+// TTM: Y[a][s][c] = sum_i M[i*ldm + s] X[a][i][c],  s < S.  Y is [A][S][C] (Tout).
+// `acc32` = accumulate in FP32 (mixed path), else FP64.
+rbki_status ttm_cuda(const View& x, const double* M, int64_t ldm, int S, void* Y, int y_dtype,
+                     bool acc32, cudaStream_t st);
+// Contraction: P[i][s] = sum_{a,c} X[a][i][c] Y[a][s][c] (split over columns into nsplit
+// partials `part` [nsplit][I][S], then a fixed-order reduce into out (ld_out) and out2).
+// Y has element type y_dtype (RBKI_F64 or the tensor's dtype).  Gram: Y == X, S == I.
+rbki_status contract_cuda(const View& x, const void* Y, int y_dtype, int S, bool acc32,
+                          double* part, int nsplit, double* out, int64_t ld_out,
+                          double* out2, int64_t ld_out2, cudaStream_t st);
+int contract_nsplit(const View& x);
+
+// FP64 Omega in the [A][S][C] layout of a TTM result (k_omega.cu).
+rbki_status omega_f64_cuda(uint64_t seed, int mode, int64_t A, int64_t C, int S, double* Y,
+                           cudaStream_t st);
+
+// sum of squares of n elements (FP64 result into *out) - partials in `part` (>= 1024 doubles)
+rbki_status sumsq_cuda(const void* x, int dtype, int64_t n, double* part, double* out,
+                       cudaStream_t st);
+// cast to bf16/f16 (dst_dtype) + sum of squares of the source
+rbki_status stage_cuda(const void* x, int dtype, int64_t n, void* dst, int dst_dtype,
+                       double* part, double* norm2, cudaStream_t st);
+
+// ---- small dense FP64 kernels (k_small.cu) ----
+// out (ma x mb, ld ldo) = A^T B over `rows` rows; A: rows x ma (lda), B: rows x mb (ldb).
+int atb_nchunks(int64_t rows);
+rbki_status atb_cuda(const double* A, int64_t lda, int ma, const double* B, int64_t ldb, int mb,
+                     int64_t rows, double* part, double* out, int64_t ldo, cudaStream_t st);
+// One pass of block orthonormalisation (Pythagorean-inner-product block Gram-Schmidt
+// followed by Cholesky QR with pivot deflation).  Q: rows x ldq, block = columns
+// [m, m+S); earlier columns [0, m) are orthonormal.  In place.
+rbki_status orth_pass_cuda(double* Q, int64_t ldq, int64_t rows, int m, int S, double tau,
+                           double* scratch, int32_t* kept, cudaStream_t st);
+size_t orth_scratch_doubles(int64_t rows, int m, int S);
+// symmetric eigensolver, descending; V columns are eigenvectors (n x n row-major)
+rbki_status syev_cuda(const double* A, int n, double* w, double* V, double* scratch,
+                      cudaStream_t st);
+size_t syev_scratch_doubles(int n);
+// U[i][k] = sum_t Q[i*ldq + t] V[t*n + k] (k < R); then sign-normalise each column.
+// Q == nullptr means identity (Gram path): U = V[:, :R].
+rbki_status form_factor_cuda(const double* Q, int64_t ldq, int64_t rows, const double* V, int n,
+                             int R, double* U, cudaStream_t st);
+rbki_status copy_f64_cuda(const double* src, double* dst, int64_t n, cudaStream_t st);
+rbki_status fill_i32_cuda(int32_t* dst, int32_t v, int n, cudaStream_t st);
+
+// profiling hook (api.cu): returns a token for prof_end, or -1 when profiling is off
+int prof_begin(int cls, cudaStream_t st);
+void prof_end(int token, cudaStream_t st);
+
+}  // namespace rbki

@@ -1,0 +1,52 @@
+// Host-side plan of one rBKI-TK call (sizes per mode + carved workspace pointers).
+#pragma once
+
+#include "kernels.h"
+
+namespace rbki {
+
+struct ModePlan {
+    int n = 0;
+    int64_t I = 0, A = 1, C = 1;   // X viewed as [A][I][C] for this mode
+    int R = 0, S = 0, q = 0, b = 0;
+    bool gram = false;             // b >= I: exact Gram path (reading c7)
+    int nsplit = 1;
+    // workspace (device)
+    double* Qall = nullptr;        // I x b, blocks Q_0..Q_q (ld b)
+    double* Pall = nullptr;        // I x b, P_j = X X^T Q_j
+    double* Y = nullptr;           // [A][S][C]: Omega, or X x_n Q_j^T
+    double* part = nullptr;        // split partials
+    double* small = nullptr;       // orthonormalisation scratch
+    double* Z = nullptr;           // b x b
+    double* evec = nullptr;        // b x b
+    double* eval = nullptr;        // b
+    double* syev_ws = nullptr;
+    int32_t* kept = nullptr;
+};
+
+struct Plan {
+    int N = 0, dtype = 0, prec = 0, stream_dtype = 0;
+    bool mixed = false, stage = false;
+    int64_t dims[RBKI_MAX_ORDER] = {0};
+    int64_t numel = 0, ranks_numel = 0;
+    int order[RBKI_MAX_ORDER] = {0};
+    uint64_t seed = 0;
+    uint32_t flags = 0;
+    ModePlan mode[RBKI_MAX_ORDER];
+    // workspace
+    double* scal = nullptr;        // scalars + reduction partials
+    char* xs = nullptr;            // staged low-precision copy of X
+    double* tbuf[2] = {nullptr, nullptr};
+    size_t ws_bytes = 0;
+    // bound at run time
+    const void* xin = nullptr;
+    const void* xstream = nullptr;
+};
+
+size_t dtype_size(int dt);
+size_t host_io_bytes(const Plan& pl);
+rbki_status run_tucker(Plan& pl, const rbki_tucker_out* out, cudaStream_t st);
+rbki_status run_tucker_host_io(Plan& pl, const rbki_tensor* X, const rbki_tucker_out* out,
+                               void* workspace, cudaStream_t st);
+
+}  // namespace rbki

@@ -1,0 +1,64 @@
+"""CPU checks of the C ABI: the library builds, loads and exports every symbol that
+include/rbki.h declares; argument validation needs no GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2211_14828_gb300 import _build
+    import paper_2211_14828_gb300 as rb
+    if not os.path.exists(rb.LIB_PATH):
+        _build.build()
+    return rb.lib()
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "rbki.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(rbki_[a-z_0-9]+)\s*\(", txt)))
+
+
+def test_header_symbols_exported(L):
+    names = _declared()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_status_strings(L):
+    assert L.rbki_status_str(0) == b"ok"
+    assert L.rbki_status_str(-2).startswith(b"out of memory")
+
+
+def test_validation_without_gpu(L):
+    import torch
+    import paper_2211_14828_gb300 as rb
+    from paper_2211_14828_gb300 import _binding as B
+    x = torch.zeros((8, 9, 10), dtype=torch.float32)
+    assert rb.rbki_tucker_workspace(x, [2, 3, 4], 2, 1, prec="bf16") > 0
+    with pytest.raises(rb.RbkiError) as e:
+        rb.rbki_tucker_workspace(x, [2, 30, 4], 2, 1)        # R > I
+    assert e.value.status == B.E_INVAL
+    with pytest.raises(rb.RbkiError):
+        rb.rbki_tucker_workspace(x, [2, 3, 4], -1, 1)        # p < 0
+    t = B.make_tensor(x)
+    t.order = 9
+    n = ctypes.c_size_t(0)
+    prm = B.make_params([1] * 8, 0, 0, 0, "fp64")
+    assert L.rbki_tucker_workspace(ctypes.byref(t), ctypes.byref(prm), ctypes.byref(n)) == B.E_INVAL
+    # a call with a too-small workspace is rejected before any device work
+    t = B.make_tensor(x)
+    prm = B.make_params([2, 3, 4], 2, 1, 0, "fp64")
+    out = B.rbki_tucker_out()
+    out.core = 16
+    for i in range(3):
+        out.factors[i] = 16
+    st = L.rbki_tucker(ctypes.byref(t), ctypes.byref(prm), ctypes.c_void_p(16), ctypes.c_size_t(8),
+                       ctypes.byref(out), None)
+    assert st == B.E_NOMEM

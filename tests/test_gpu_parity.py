@@ -1,0 +1,146 @@
+"""GPU parity of the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+FP64 path bar: principal-angle sines <= 1e-10 per mode and reconstruction error agreeing
+to 1e-12 relative (same seeded Omega and input).  Mixed (BF16 products / FP32 accumulate,
+FP64 orthonormalisation and eigensolve) bar: relative reconstruction error within 1% of
+the oracle's."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import metrics, rbki
+from oracle.tensor import unfold
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def rb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2211_14828_gb300 as rb
+    rb.lib()
+    return rb
+
+
+def _err_from_norms(norms):
+    n = norms.cpu().numpy()
+    return float(np.sqrt(max(n[0] - n[1], 0.0)))
+
+
+@pytest.mark.parametrize("dims", [(20, 30, 40), (37, 23, 41), (5, 130, 7), (64, 64, 64), (6, 5, 4, 7)])
+@pytest.mark.parametrize("s", [1, 7, 16, 30])
+def test_krylov_product_fp64(rb, dims, s):
+    g = np.random.default_rng(sum(dims) + s)
+    x = g.standard_normal(dims)
+    xt = torch.from_numpy(x).cuda()
+    for mode in range(len(dims)):
+        q = g.standard_normal((dims[mode], s))
+        p = rb.rbki_krylov_product(xt, mode, torch.from_numpy(q).cuda(), prec="fp64")
+        xn = unfold(x, mode)
+        want = xn @ (xn.T @ q)
+        np.testing.assert_allclose(p.cpu().numpy(), want, rtol=1e-12, atol=1e-12 * np.abs(want).max())
+
+
+@pytest.mark.parametrize("dims", [(20, 30, 40), (64, 64, 64)])
+def test_krylov_product_bf16_cuda_cores(rb, dims):
+    g = np.random.default_rng(1)
+    x = g.standard_normal(dims).astype(np.float32)
+    q = g.standard_normal((dims[0], 12))
+    xt = torch.from_numpy(x).cuda()
+    xb = xt.bfloat16().double().cpu().numpy()          # the staged operand, exactly
+    p = rb.rbki_krylov_product(xt, 0, torch.from_numpy(q).cuda(), prec="bf16").cpu().numpy()
+    xn = unfold(xb, 0)
+    want = xn @ (xn.T @ q)
+    rel = np.linalg.norm(p - want) / np.linalg.norm(want)
+    assert rel < 2e-5
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 36, 48, 97, 120])
+def test_syev(rb, n):
+    g = np.random.default_rng(n)
+    a = g.standard_normal((n, n))
+    a = a @ a.T + np.diag(np.linspace(0, 1, n))
+    w, V = rb.rbki_syev(torch.from_numpy(a).cuda())
+    w, V = w.cpu().numpy(), V.cpu().numpy()
+    wr = np.sort(np.linalg.eigvalsh(a))[::-1]
+    np.testing.assert_allclose(w, wr, rtol=1e-12, atol=1e-12 * wr[0])
+    np.testing.assert_allclose(a @ V, V * w[None, :], atol=1e-11 * wr[0])
+    np.testing.assert_allclose(V.T @ V, np.eye(n), atol=1e-13)
+
+
+def test_mode_basis_span_fp64(rb):
+    wl = synth.config_small_fp64(mc=0)
+    x = torch.from_numpy(wl.x).cuda()
+    for n in range(3):
+        q_gpu = rb.rbki_mode_basis(x, wl.ranks, wl.p, wl.q, wl.seed, n, prec="fp64").cpu().numpy()
+        q_ref = rbki.krylov_basis(wl.x, n, wl.ranks[n] + wl.p, wl.q, wl.seed)
+        assert np.linalg.norm(q_gpu.T @ q_gpu - np.eye(q_gpu.shape[1])) <= 1e-13
+        assert metrics.max_principal_sine(q_ref, q_gpu) <= 1e-10
+        assert metrics.max_principal_sine(q_gpu, q_ref) <= 1e-10
+
+
+def _check_fp64(rb, wl, sine_tol=1e-10, err_rtol=1e-12):
+    ref = rbki.rbki_tucker(wl.x, wl.ranks, wl.p, wl.q, wl.seed)
+    x = torch.from_numpy(np.ascontiguousarray(wl.x)).cuda()
+    out = rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec="fp64")
+    torch.cuda.synchronize()
+    err_ref = metrics.fnorm(wl.x - rbki.reconstruct(ref["core"], ref["factors"]))
+    for n in range(x.dim()):
+        u = out["factors"][n].cpu().numpy()
+        assert np.linalg.norm(u.T @ u - np.eye(u.shape[1])) <= 1e-12
+        assert metrics.max_principal_sine(ref["factors"][n], u) <= sine_tol
+        np.testing.assert_allclose(out["eigvals"][n].cpu().numpy(), ref["eigvals"][n], rtol=1e-11,
+                                   atol=1e-12 * ref["eigvals"][n][0])
+    info = out["info"].cpu().numpy()
+    assert list(info[x.dim():]) == [1 if p == "gram" else 0 for p in ref["path"]]
+    assert list(info[: x.dim()]) == ref["kept"]
+    # reconstruction error: identity |X|^2 - |G|^2, and explicit from the returned factors
+    g = out["core"].cpu().numpy()
+    us = [f.cpu().numpy() for f in out["factors"]]
+    err = metrics.fnorm(wl.x - rbki.reconstruct(g, us))
+    assert abs(err - err_ref) <= err_rtol * max(err_ref, 1e-300) + 1e-13 * metrics.fnorm(wl.x)
+    return out, ref
+
+
+def test_tucker_fp64_small_config(rb):
+    _check_fp64(rb, synth.config_small_fp64(mc=0))
+
+
+def test_tucker_fp64_ragged_and_order4(rb):
+    _check_fp64(rb, synth.config_small_fp64(mc=1, dims=(37, 23, 41), core=(5, 4, 6), p=3, q=1))
+    _check_fp64(rb, synth.config_small_fp64(mc=2, dims=(12, 30, 9, 25), core=(3, 4, 2, 5), p=2, q=2))
+
+
+def test_tucker_fp64_exact_recovery(rb):
+    wl = synth.config_small_fp64(mc=3, snr_db=None)
+    out, _ = _check_fp64(rb, wl)
+    g = out["core"].cpu().numpy()
+    us = [f.cpu().numpy() for f in out["factors"]]
+    assert metrics.fnorm(wl.x - rbki.reconstruct(g, us)) / metrics.fnorm(wl.x) <= 1e-12
+
+
+def test_tucker_fp64_gram_path_equals_tsvd(rb):
+    g = synth.rng(7)
+    x = synth.gaussian_tucker(g, 3, 10, 3) + 0.3 * g.standard_normal((10, 10, 10))
+    wl = synth.Workload("tiny", np.ascontiguousarray(x), None, [3, 3, 3], 2, 1, 11)
+    out, ref = _check_fp64(rb, wl)
+    ts = rbki.tsvd(x, [3, 3, 3])
+    for n in range(3):
+        assert metrics.max_principal_sine(ts["factors"][n], out["factors"][n].cpu().numpy()) <= 1e-12
+
+
+def test_tucker_mixed_small_config(rb):
+    wl = synth.config_small_fp64(mc=0)
+    ref = rbki.rbki_tucker(wl.x, wl.ranks, wl.p, wl.q, wl.seed)
+    x = torch.from_numpy(wl.x.astype(np.float32)).cuda()
+    out = rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec="bf16")
+    torch.cuda.synchronize()
+    err_ref = np.sqrt(ref["x_norm2"] - ref["core_norm2"])
+    g = out["core"].cpu().numpy()
+    us = [f.cpu().numpy() for f in out["factors"]]
+    err = metrics.fnorm(wl.x - rbki.reconstruct(g, us))
+    assert abs(err - err_ref) <= 0.01 * err_ref
+    assert abs(_err_from_norms(out["norms"]) - err_ref) <= 0.01 * err_ref
