@@ -65,7 +65,8 @@ enum { RBKI_PREC_FP64 = 0, RBKI_PREC_BF16 = 1, RBKI_PREC_FP16 = 2 };
 /* rbki_params.flags */
 enum {
     RBKI_FLAG_HOST_IO = 1u,        /* X and outputs in host memory (end-to-end call) */
-    RBKI_FLAG_NO_SPLIT = 2u,       /* mixed path: skip the hi/lo split of the skinny operands */
+    RBKI_FLAG_SPLIT = 2u,          /* mixed path: carry the skinny operands (Q, Y, Omega, U) as
+                                      hi + lo BF16 pairs: ~FP32-accurate products, 2x MMA work */
     RBKI_FLAG_SERIAL_MODES = 4u    /* run modes one after another on `stream` */
 };
 
@@ -96,8 +97,10 @@ typedef struct {
     double* eigvals[RBKI_MAX_ORDER]; /* optional (NULL): leading R_n eigenvalues of Z^(n) */
     double* norms;                   /* optional: [0] = |X|_F^2, [1] = |G|_F^2; the
                                         reconstruction error is |X|^2 - |G|^2 */
-    int32_t* info;                   /* optional, 2N ints: [n] = kept Krylov width of mode n,
-                                        [N+n] = path (0 Krylov, 1 Gram = exact T-SVD mode) */
+    int32_t* info;                   /* optional, 2N+1 ints: [n] = kept Krylov width of mode n,
+                                        [N+n] = path (0 Krylov, 1 Gram = exact T-SVD mode),
+                                        [2N] = device error flags (nonzero: a bounded wait inside
+                                        a kernel expired; the results are not valid) */
 } rbki_tucker_out;
 
 /* Bytes of device workspace rbki_tucker needs for this problem. */
@@ -151,7 +154,10 @@ rbki_status rbki_server_destroy(rbki_server* s);
 /* ---- step-level entry points (used by the parity tests) --------------------------- */
 
 /* Krylov step of Algorithm 1 / Eq. BKspace on mode n: P = X_(n) (X_(n)^T Q),
- * Q: I_n x s row-major FP64 (device), P: I_n x s row-major FP64 (device). */
+ * Q: I_n x s row-major FP64 (device), P: I_n x s row-major FP64 (device).
+ * prec = RBKI_PREC_*; a negative value -RBKI_PREC_BF16 / -RBKI_PREC_FP16 selects the split
+ * (hi + lo) operand variant.  BF16/FP16 run on the tensor-core kernel when the shape allows
+ * (contiguous extent a multiple of 8, I_n <= 512 for s <= 32), else on CUDA cores. */
 rbki_status rbki_krylov_product(const rbki_tensor* X, int32_t mode, int32_t prec,
                                 const double* Q, int32_t s, double* P,
                                 void* workspace, size_t workspace_bytes, void* stream);

@@ -18,7 +18,7 @@ OK, PENDING, W_DEFLATED = 0, 1, 2
 E_INVAL, E_NOMEM, E_CUDA, E_UNSUPPORTED, E_TIMEOUT, E_BUSY, E_CANCELLED, E_NOTFOUND = range(-1, -9, -1)
 F64, F32, BF16, F16 = 0, 1, 2, 3
 PREC_FP64, PREC_BF16, PREC_FP16 = 0, 1, 2
-FLAG_HOST_IO, FLAG_NO_SPLIT, FLAG_SERIAL_MODES = 1, 2, 4
+FLAG_HOST_IO, FLAG_SPLIT, FLAG_SERIAL_MODES = 1, 2, 4
 
 
 class rbki_tensor(C.Structure):
@@ -106,6 +106,7 @@ def dtype_code(t) -> int:
 
 
 def prec_code(prec) -> int:
+    """'fp64' | 'bf16' | 'fp16', or the C code; a negative code selects the split variant."""
     if isinstance(prec, int):
         return prec
     return {"fp64": PREC_FP64, "bf16": PREC_BF16, "fp16": PREC_FP16}[prec]
@@ -149,7 +150,7 @@ def alloc_outputs(dims, ranks, device, host=False) -> Dict:
     ikw = dict(dtype=torch.int32, device="cpu" if host else device)
     if host:
         ikw["pin_memory"] = True
-    out["info"] = torch.zeros(2 * len(dims), **ikw)
+    out["info"] = torch.zeros(2 * len(dims) + 1, **ikw)
     return out
 
 

@@ -10,6 +10,7 @@
 
 #include "kernels.h"
 #include "plan.h"
+#include "tc.h"
 
 namespace rbki {
 
@@ -103,6 +104,7 @@ rbki_status make_plan(const rbki_tensor* X, const rbki_params* prm, Plan& pl) {
         pl.numel *= X->dims[n];
     }
     pl.mixed = prm->prec != RBKI_PREC_FP64;
+    pl.split = pl.mixed && (prm->flags & RBKI_FLAG_SPLIT);
     pl.stream_dtype = pl.mixed ? (prm->prec == RBKI_PREC_BF16 ? RBKI_BF16 : RBKI_F16) : X->dtype;
     pl.stage = pl.mixed && X->dtype != pl.stream_dtype;
     for (int n = 0; n < pl.N; ++n) {
@@ -151,6 +153,7 @@ struct Carver {
 void carve(Plan& pl, void* ws) {
     Carver c(ws);
     pl.scal = c.take<double>(4096);
+    pl.err = c.take<int32_t>(64);
     if (pl.stage) pl.xs = c.take<char>((size_t)pl.numel * dtype_size(pl.stream_dtype));
     for (int n = 0; n < pl.N; ++n) {
         ModePlan& m = pl.mode[n];
@@ -173,7 +176,16 @@ void carve(Plan& pl, void* ws) {
             for (int j = 0; j <= m.q; ++j)
                 orth = std::max(orth, orth_scratch_doubles(m.I, j * m.S, m.S));
             m.small = c.take<double>(orth);
-            m.Y = c.take<double>((size_t)d * m.S);
+            m.N = (int)rup(pl.split ? 2 * m.S : m.S, 16);
+            m.tc = pl.mixed && tc::supported(v, tc::KRYLOV, m.N) && tc::supported(v, tc::SKETCH, m.N);
+            if (m.tc) {
+                m.tgrid = tc::grid_size(v);
+                m.qimg = c.take<char>(tc::image_bytes_skinny(v, m.N));
+                m.omg = c.take<char>(tc::image_bytes_omega(v, m.N));
+                m.tpart = c.take<float>((size_t)m.tgrid * m.I * m.N);
+            } else {
+                m.Y = c.take<double>((size_t)d * m.S);
+            }
         }
     }
     // core chain ping-pong buffers (FP64)
@@ -191,6 +203,15 @@ void carve(Plan& pl, void* ws) {
     }
     pl.tbuf[0] = c.take<double>(maxbuf);
     pl.tbuf[1] = c.take<double>(maxbuf);
+    {
+        const int m0 = pl.order[0];
+        const ModePlan& m = pl.mode[m0];
+        View v{nullptr, pl.stream_dtype, m.A, m.I, m.C};
+        // the core carries the reconstruction error |X|^2 - |G|^2: always hi + lo operands
+        pl.ttm_N = (int)rup(2 * m.R, 16);
+        pl.ttm_tc = pl.mixed && m.R <= 32 && tc::supported(v, tc::TTM, pl.ttm_N);
+        if (pl.ttm_tc) pl.ttm_img = c.take<char>(tc::image_bytes_skinny(v, pl.ttm_N));
+    }
     pl.ws_bytes = c.off + 256;
 }
 
@@ -224,6 +245,13 @@ View mode_view(const Plan& pl, const ModePlan& m) {
 rbki_status krylov_step(const Plan& pl, const ModePlan& m, const double* Q, int64_t ldq, int S,
                         double* out, int64_t ldo, double* out2, int64_t ldo2, cudaStream_t st) {
     View v = mode_view(pl, m);
+    if (m.tc) {
+        RBKI_TRY(tc::skinny_image(Q, ldq, m.I, S, m.N, pl.split, pl.stream_dtype == RBKI_F16, m.qimg, st));
+        int tok = prof_begin(RBKI_PROF_KRYLOV, st);
+        RBKI_TRY(tc::stream_tc(tc::KRYLOV, v, m.N, S, pl.split, m.qimg, nullptr, m.tpart, nullptr, pl.err, st));
+        prof_end(tok, st);
+        return tc::reduce_parts(m.tpart, m.tgrid, m.I, m.N, S, pl.split, out, ldo, out2, ldo2, st);
+    }
     int tok = prof_begin(RBKI_PROF_KRYLOV, st);
     RBKI_TRY(ttm_cuda(v, Q, ldq, S, m.Y, RBKI_F64, pl.mixed, st));
     RBKI_TRY(contract_cuda(v, m.Y, RBKI_F64, S, pl.mixed, m.part, m.nsplit, out, ldo, out2, ldo2, st));
@@ -241,11 +269,19 @@ rbki_status orth2(const ModePlan& m, int col0, int32_t* kept, cudaStream_t st) {
 rbki_status mode_basis(const Plan& pl, const ModePlan& m, int32_t* kept, cudaStream_t st) {
     View v = mode_view(pl, m);
     // step 1-2: W = X_(n) Omega  (Omega generated in the [A][S][C] layout)
-    int tok = prof_begin(RBKI_PROF_SKETCH, st);
-    RBKI_TRY(omega_f64_cuda(pl.seed, m.n, m.A, m.C, m.S, m.Y, st));
-    RBKI_TRY(contract_cuda(v, m.Y, RBKI_F64, m.S, pl.mixed, m.part, m.nsplit, m.Qall, m.b,
-                           nullptr, 0, st));
-    prof_end(tok, st);
+    if (m.tc) {
+        RBKI_TRY(tc::omega_images(pl.seed, m.n, v, m.S, m.N, pl.split, m.omg, st));
+        int tok = prof_begin(RBKI_PROF_SKETCH, st);
+        RBKI_TRY(tc::stream_tc(tc::SKETCH, v, m.N, m.S, pl.split, nullptr, m.omg, m.tpart, nullptr, pl.err, st));
+        prof_end(tok, st);
+        RBKI_TRY(tc::reduce_parts(m.tpart, m.tgrid, m.I, m.N, m.S, pl.split, m.Qall, m.b, nullptr, 0, st));
+    } else {
+        int tok = prof_begin(RBKI_PROF_SKETCH, st);
+        RBKI_TRY(omega_f64_cuda(pl.seed, m.n, m.A, m.C, m.S, m.Y, st));
+        RBKI_TRY(contract_cuda(v, m.Y, RBKI_F64, m.S, pl.mixed, m.part, m.nsplit, m.Qall, m.b,
+                               nullptr, 0, st));
+        prof_end(tok, st);
+    }
     RBKI_TRY(orth2(m, 0, kept, st));
     // step 3: K = [W, A W, ..., A^q W], orthonormalised block by block (reading c2)
     for (int j = 0; j <= m.q; ++j) {
@@ -269,8 +305,8 @@ rbki_status mode_factor(const Plan& pl, const ModePlan& m, double* U, double* ei
                                m.nsplit, m.Z, m.I, nullptr, 0, st));
         prof_end(tok, st);
         RBKI_TRY(symmetrize_cuda(m.Z, (int)m.I, st));
-        RBKI_TRY(syev_cuda(m.Z, (int)m.I, m.eval, m.evec, m.syev_ws, st));
-        RBKI_TRY(form_factor_cuda(nullptr, 0, m.I, m.evec, (int)m.I, m.R, U, st));
+        RBKI_TRY(syev_top_cuda(m.Z, (int)m.I, m.R, m.eval, m.evec, m.syev_ws, st));
+        RBKI_TRY(form_factor_cuda(nullptr, 0, m.I, m.evec, (int)m.I, m.R, m.R, U, st));
         if (info) RBKI_TRY(fill_i32_cuda(info + m.n, (int32_t)m.I, 1, st));
     } else {
         if (info) RBKI_TRY(fill_i32_cuda(info + m.n, 0, 1, st));
@@ -279,8 +315,8 @@ rbki_status mode_factor(const Plan& pl, const ModePlan& m, double* U, double* ei
         RBKI_TRY(atb_cuda(m.Qall, m.b, m.b, m.Pall, m.b, m.b, m.I, m.part, m.Z, m.b, st));
         RBKI_TRY(symmetrize_cuda(m.Z, m.b, st));
         // step 4: leading eigenvectors of Z; step 5: U = Q U~(:, 1:R)
-        RBKI_TRY(syev_cuda(m.Z, m.b, m.eval, m.evec, m.syev_ws, st));
-        RBKI_TRY(form_factor_cuda(m.Qall, m.b, m.I, m.evec, m.b, m.R, U, st));
+        RBKI_TRY(syev_top_cuda(m.Z, m.b, m.R, m.eval, m.evec, m.syev_ws, st));
+        RBKI_TRY(form_factor_cuda(m.Qall, m.b, m.I, m.evec, m.b, m.R, m.R, U, st));
     }
     if (eigvals) RBKI_TRY(copy_f64_cuda(m.eval, eigvals, m.R, st));
     if (info) RBKI_TRY(fill_i32_cuda(info + pl.N + m.n, m.gram ? 1 : 0, 1, st));
@@ -302,6 +338,18 @@ rbki_status core_chain(const Plan& pl, double* const* factors, double* core, cud
         double* dst = (t == pl.N - 1) ? core : pl.tbuf[t & 1];
         int R = pl.mode[m].R;
         int tok = t == 0 ? prof_begin(RBKI_PROF_TTM, st) : -1;
+        if (t == 0 && pl.ttm_tc && t != pl.N - 1) {
+            // first mode product on tcgen05: FP32 result [A][R][C] in the ping-pong buffer
+            RBKI_TRY(tc::skinny_image(factors[m], R, cur[m], R, pl.ttm_N, true, pl.stream_dtype == RBKI_F16,
+                                      pl.ttm_img, st));
+            RBKI_TRY(tc::stream_tc(tc::TTM, v, pl.ttm_N, R, true, pl.ttm_img, nullptr, nullptr, (float*)dst,
+                                   pl.err, st));
+            prof_end(tok, st);
+            cur[m] = R;
+            src = dst;
+            src_dtype = RBKI_F32;
+            continue;
+        }
         RBKI_TRY(ttm_cuda(v, factors[m], R, R, dst, RBKI_F64, pl.mixed && t == 0, st));
         prof_end(tok, st);
         cur[m] = R;
@@ -313,6 +361,7 @@ rbki_status core_chain(const Plan& pl, double* const* factors, double* core, cud
 
 rbki_status run_tucker(Plan& pl, const rbki_tucker_out* out, cudaStream_t st) {
     double* norms = out->norms ? out->norms : pl.scal;
+    RBKI_CUDA_TRY(cudaMemsetAsync(pl.err, 0, sizeof(int32_t), st));
     int tok = prof_begin(RBKI_PROF_STAGE, st);
     if (pl.stage) {
         RBKI_TRY(stage_cuda(pl.xin, pl.dtype, pl.numel, pl.xs, pl.stream_dtype, pl.scal + 64,
@@ -329,6 +378,8 @@ rbki_status run_tucker(Plan& pl, const rbki_tucker_out* out, cudaStream_t st) {
     }
     RBKI_TRY(core_chain(pl, out->factors, out->core, st));
     RBKI_TRY(sumsq_cuda(out->core, RBKI_F64, pl.ranks_numel, pl.scal + 64, norms + 1, st));
+    if (out->info)
+        RBKI_CUDA_TRY(cudaMemcpyAsync(out->info + 2 * pl.N, pl.err, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
     return RBKI_OK;
 }
 
@@ -412,51 +463,65 @@ rbki_status rbki_tucker(const rbki_tensor* X, const rbki_params* prm, void* work
     return run_tucker(pl, out, st);
 }
 
-rbki_status rbki_krylov_product_workspace(const rbki_tensor* X, int32_t mode, int32_t prec,
-                                          int32_t s, size_t* bytes) {
-    if (!bytes) return set_error(RBKI_E_INVAL, "bytes is NULL");
+// Workspace of the step-level Krylov product: staging copy, FP64 intermediates of the
+// CUDA-core path or the operand image + partials of the tensor-core path.
+static rbki_status krylov_product_plan(const rbki_tensor* X, int32_t mode, int32_t prec, int32_t s,
+                                       uint32_t flags, Plan& pl, ModePlan& m, void* ws, size_t* bytes) {
     RBKI_TRY(validate_tensor(X));
     if (mode < 0 || mode >= X->order || s < 1 || s > 128)
         return set_error(RBKI_E_INVAL, "mode or s out of range");
     rbki_params prm{};
     for (int n = 0; n < X->order; ++n) prm.ranks[n] = 1;
-    prm.p = 0;
-    prm.q = 0;
     prm.prec = prec;
-    Plan pl;
+    prm.flags = flags;
     RBKI_TRY(make_plan(X, &prm, pl));
-    ModePlan& m = pl.mode[mode];
+    m = pl.mode[mode];
+    m.S = s;
+    Carver c(ws);
+    pl.scal = c.take<double>(4096);
+    pl.err = c.take<int32_t>(64);
+    if (pl.stage) pl.xs = c.take<char>((size_t)pl.numel * dtype_size(pl.stream_dtype));
     View v{nullptr, pl.stream_dtype, m.A, m.I, m.C};
-    size_t b = 256 + (size_t)m.A * m.C * s * 8 + 256 +
-               (size_t)contract_nsplit(v) * m.I * s * 8 + 256 + 4096 * 8;
-    if (pl.stage) b += (size_t)pl.numel * dtype_size(pl.stream_dtype) + 256;
-    *bytes = b;
+    m.N = (int)rup(pl.split ? 2 * s : s, 16);
+    m.tc = pl.mixed && tc::supported(v, tc::KRYLOV, m.N);
+    if (m.tc) {
+        m.tgrid = tc::grid_size(v);
+        m.qimg = c.take<char>(tc::image_bytes_skinny(v, m.N));
+        m.tpart = c.take<float>((size_t)m.tgrid * m.I * m.N);
+    } else {
+        m.nsplit = contract_nsplit(v);
+        m.Y = c.take<double>((size_t)m.A * m.C * s);
+        m.part = c.take<double>((size_t)m.nsplit * m.I * s);
+    }
+    if (bytes) *bytes = c.off + 256;
     return RBKI_OK;
 }
 
+rbki_status rbki_krylov_product_workspace(const rbki_tensor* X, int32_t mode, int32_t prec,
+                                          int32_t s, size_t* bytes) {
+    if (!bytes) return set_error(RBKI_E_INVAL, "bytes is NULL");
+    Plan pl;
+    ModePlan m;
+    uint32_t flags = prec < 0 ? RBKI_FLAG_SPLIT : 0u;
+    return krylov_product_plan(X, mode, prec < 0 ? -prec : prec, s, flags, pl, m, nullptr, bytes);
+}
+
+// prec < 0 selects the split (hi + lo) operand variant of precision -prec.
 rbki_status rbki_krylov_product(const rbki_tensor* X, int32_t mode, int32_t prec, const double* Q,
                                 int32_t s, double* P, void* workspace, size_t workspace_bytes,
                                 void* stream) {
     size_t need = 0;
-    RBKI_TRY(rbki_krylov_product_workspace(X, mode, prec, s, &need));
+    Plan pl;
+    ModePlan m;
+    uint32_t flags = prec < 0 ? RBKI_FLAG_SPLIT : 0u;
+    int32_t pr = prec < 0 ? -prec : prec;
+    RBKI_TRY(krylov_product_plan(X, mode, pr, s, flags, pl, m, nullptr, &need));
     if (!Q || !P) return set_error(RBKI_E_INVAL, "Q/P NULL");
     if (!workspace || workspace_bytes < need) return set_error(RBKI_E_NOMEM, "workspace too small");
-    rbki_params prm{};
-    for (int n = 0; n < X->order; ++n) prm.ranks[n] = 1;
-    prm.prec = prec;
-    Plan pl;
-    RBKI_TRY(make_plan(X, &prm, pl));
+    RBKI_TRY(krylov_product_plan(X, mode, pr, s, flags, pl, m, workspace, nullptr));
     cudaStream_t st = (cudaStream_t)stream;
-    ModePlan m = pl.mode[mode];
-    m.S = s;
-    Carver c(workspace);
-    pl.scal = c.take<double>(4096);
-    View v0{nullptr, pl.stream_dtype, m.A, m.I, m.C};
-    m.nsplit = contract_nsplit(v0);
-    m.Y = c.take<double>((size_t)m.A * m.C * s);
-    m.part = c.take<double>((size_t)m.nsplit * m.I * s);
+    RBKI_CUDA_TRY(cudaMemsetAsync(pl.err, 0, sizeof(int32_t), st));
     if (pl.stage) {
-        pl.xs = c.take<char>((size_t)pl.numel * dtype_size(pl.stream_dtype));
         RBKI_TRY(stage_cuda(X->data, X->dtype, pl.numel, pl.xs, pl.stream_dtype, pl.scal + 64,
                             pl.scal, st));
         pl.xstream = pl.xs;

@@ -26,7 +26,7 @@ HostIoLayout layout(const Plan& pl) {
         L.eig_off[n] = take((size_t)pl.mode[n].R * 8);
     }
     L.norms_off = take(2 * 8);
-    L.info_off = take(2 * RBKI_MAX_ORDER * 4);
+    L.info_off = take((2 * RBKI_MAX_ORDER + 1) * 4);
     L.total = off - pl.ws_bytes + 256;
     return L;
 }
@@ -63,7 +63,7 @@ rbki_status run_tucker_host_io(Plan& pl, const rbki_tensor* X, const rbki_tucker
     if (out->norms)
         RBKI_CUDA_TRY(cudaMemcpyAsync(out->norms, dout.norms, 16, cudaMemcpyDeviceToHost, st));
     if (out->info)
-        RBKI_CUDA_TRY(cudaMemcpyAsync(out->info, dout.info, 2 * pl.N * 4, cudaMemcpyDeviceToHost, st));
+        RBKI_CUDA_TRY(cudaMemcpyAsync(out->info, dout.info, (2 * pl.N + 1) * 4, cudaMemcpyDeviceToHost, st));
     RBKI_CUDA_TRY(cudaStreamSynchronize(st));
     return RBKI_OK;
 }

@@ -4,8 +4,6 @@
 //   * one pass of block orthonormalisation: Pythagorean-inner-product block classical
 //     Gram-Schmidt (BCGS-PIP, Barlow & Smoktunowicz 2013) + Cholesky QR with pivot
 //     deflation (reading c3); two passes give BCGS2 / CholQR2
-//   * cyclic Jacobi eigensolver (Jacobi 1846; Rutishauser's rotation formulas; round-robin
-//     parallel ordering) for Algorithm 2 step 4
 //   * factor formation U = Q U~(:, 1:R) with the sign convention (Algorithm 2 step 5).
 #include "kernels.h"
 
@@ -155,122 +153,9 @@ __global__ void k_orth_apply(double* __restrict__ Q, int64_t ldq, int64_t rows, 
     }
 }
 
-// ---- cyclic Jacobi, one CTA ----
-__device__ __forceinline__ void rr_pair(int r, int k, int m, int& p, int& q) {
-    // circle method: position 0 fixed, positions 1..m-1 rotate by r
-    auto idx = [&](int pos) { return pos == 0 ? 0 : ((pos - 1 + r) % (m - 1)) + 1; };
-    p = idx(k);
-    q = idx(m - 1 - k);
-    if (p > q) { int t = p; p = q; q = t; }
-}
-
-__global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ Ain, int n,
-                                                 double* __restrict__ w, double* __restrict__ Vout,
-                                                 double* __restrict__ work, int use_smem,
-                                                 int max_sweeps) {
-    extern __shared__ double sm[];
-    double* a = use_smem ? sm : work;
-    double* v = use_smem ? sm + (size_t)n * n : work + (size_t)n * n;
-    __shared__ double cs[128], sn[128];
-    __shared__ int pp[128], qq[128];
-    __shared__ double red[32];
-    __shared__ int stop;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    for (int e = tid; e < n * n; e += nt) {
-        a[e] = Ain[e];
-        v[e] = (e / n == e % n) ? 1.0 : 0.0;
-    }
-    __syncthreads();
-    const int m = n + (n & 1);
-    const int half = m / 2;
-    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-        double off = 0.0, tot = 0.0;
-        for (int e = tid; e < n * n; e += nt) {
-            double x = a[e] * a[e];
-            tot += x;
-            if (e / n != e % n) off += x;
-        }
-        off = warp_sum(off);
-        tot = warp_sum(tot);
-        if ((tid & 31) == 0) red[tid >> 5] = off;
-        __syncthreads();
-        if (tid < 32) {
-            double x = tid < (nt >> 5) ? red[tid] : 0.0;
-            x = warp_sum(x);
-            if (tid == 0) red[0] = x;
-        }
-        __syncthreads();
-        off = red[0];
-        __syncthreads();
-        if ((tid & 31) == 0) red[tid >> 5] = tot;
-        __syncthreads();
-        if (tid < 32) {
-            double x = tid < (nt >> 5) ? red[tid] : 0.0;
-            x = warp_sum(x);
-            if (tid == 0) stop = (off <= 1e-30 * x) ? 1 : 0;
-        }
-        __syncthreads();
-        if (stop) break;
-        for (int r = 0; r < m - 1; ++r) {
-            if (tid < half) {
-                int p, q;
-                rr_pair(r, tid, m, p, q);
-                double c = 1.0, s = 0.0;
-                if (q < n) {
-                    double apq = a[p * n + q];
-                    if (apq != 0.0) {
-                        double th = (a[q * n + q] - a[p * n + p]) / (2.0 * apq);
-                        double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-                        c = 1.0 / sqrt(t * t + 1.0);
-                        s = t * c;
-                    }
-                }
-                pp[tid] = p; qq[tid] = (q < n) ? q : -1; cs[tid] = c; sn[tid] = s;
-            }
-            __syncthreads();
-            for (int e = tid; e < half * n; e += nt) {     // rows p, q
-                int k = e / n, j = e % n;
-                int q = qq[k];
-                if (q < 0 || sn[k] == 0.0) continue;
-                int p = pp[k];
-                double c = cs[k], s = sn[k];
-                double ap = a[p * n + j], aq = a[q * n + j];
-                a[p * n + j] = c * ap - s * aq;
-                a[q * n + j] = s * ap + c * aq;
-            }
-            __syncthreads();
-            for (int e = tid; e < half * n; e += nt) {     // columns p, q of A and V
-                int k = e / n, j = e % n;
-                int q = qq[k];
-                if (q < 0 || sn[k] == 0.0) continue;
-                int p = pp[k];
-                double c = cs[k], s = sn[k];
-                double ap = a[j * n + p], aq = a[j * n + q];
-                a[j * n + p] = c * ap - s * aq;
-                a[j * n + q] = s * ap + c * aq;
-                double vp = v[j * n + p], vq = v[j * n + q];
-                v[j * n + p] = c * vp - s * vq;
-                v[j * n + q] = s * vp + c * vq;
-            }
-            __syncthreads();
-        }
-    }
-    // descending order: rank_i = #{j : d_j > d_i or (d_j == d_i and j < i)}
-    for (int i = tid; i < n; i += nt) {
-        double di = a[i * n + i];
-        int rank = 0;
-        for (int j = 0; j < n; ++j) {
-            double dj = a[j * n + j];
-            rank += (dj > di || (dj == di && j < i)) ? 1 : 0;
-        }
-        w[rank] = di;
-        for (int j = 0; j < n; ++j) Vout[j * n + rank] = v[j * n + i];
-    }
-}
-
 // U[i][k] = sum_t Q[i][t] V[t][k]  (or V[i][k] when Q == nullptr)
 __global__ void k_form_u(const double* __restrict__ Q, int64_t ldq, int64_t rows,
-                         const double* __restrict__ V, int n, int R, double* __restrict__ U) {
+                         const double* __restrict__ V, int n, int ldv, int R, double* __restrict__ U) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= rows * R) return;
     int64_t i = e / R;
@@ -279,9 +164,9 @@ __global__ void k_form_u(const double* __restrict__ Q, int64_t ldq, int64_t rows
     if (Q) {
         acc = 0.0;
         const double* qi = Q + i * ldq;
-        for (int t = 0; t < n; ++t) acc += qi[t] * V[(int64_t)t * n + k];
+        for (int t = 0; t < n; ++t) acc += qi[t] * V[(int64_t)t * ldv + k];
     } else {
-        acc = V[i * n + k];
+        acc = V[i * ldv + k];
     }
     U[e] = acc;
 }
@@ -365,12 +250,9 @@ rbki_status orth_pass_cuda(double* Q, int64_t ldq, int64_t rows, int m, int S, d
     k_gprime<<<S, 128, 0, st>>>(M, m, S, Gp, nu2);
     RBKI_LAUNCH_CHECK("k_gprime");
     size_t sm = ((size_t)S * S + S) * sizeof(double);
-    static bool attr_done = false;
-    if (!attr_done) {
-        RBKI_CUDA_TRY(cudaFuncSetAttribute(k_chol_deflate, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           160 * 1024));
-        attr_done = true;
-    }
+    static size_t smax = 0;
+    if (!smax) smax = max_dyn_smem(k_chol_deflate);
+    if (sm > smax) return set_error(RBKI_E_UNSUPPORTED, "orth: block too wide for shared memory");
     k_chol_deflate<<<1, 128, sm, st>>>(Gp, nu2, S, tau, Rinv, kept);
     RBKI_LAUNCH_CHECK("k_chol_deflate");
     k_orth_apply<<<(unsigned)cdiv(rows, ORTH_ROWS), 256, ORTH_ROWS * S * sizeof(double), st>>>(
@@ -379,30 +261,10 @@ rbki_status orth_pass_cuda(double* Q, int64_t ldq, int64_t rows, int m, int S, d
     return RBKI_OK;
 }
 
-size_t syev_scratch_doubles(int n) { return 2 * (size_t)n * n + 64; }
-
-rbki_status syev_cuda(const double* A, int n, double* w, double* V, double* scratch,
-                      cudaStream_t st) {
-    if (n > 256) return set_error(RBKI_E_UNSUPPORTED, "syev: n > 256");
-    size_t need = 2 * (size_t)n * n * sizeof(double);
-    int use_smem = need <= 200 * 1024;
-    if (use_smem) {
-        static bool attr_done = false;
-        if (!attr_done) {
-            RBKI_CUDA_TRY(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               200 * 1024));
-            attr_done = true;
-        }
-    }
-    k_jacobi<<<1, 1024, use_smem ? need : 0, st>>>(A, n, w, V, scratch, use_smem, 40);
-    RBKI_LAUNCH_CHECK("k_jacobi");
-    return RBKI_OK;
-}
-
 rbki_status form_factor_cuda(const double* Q, int64_t ldq, int64_t rows, const double* V, int n,
-                             int R, double* U, cudaStream_t st) {
+                             int ldv, int R, double* U, cudaStream_t st) {
     int64_t tot = rows * R;
-    k_form_u<<<(unsigned)cdiv(tot, 256), 256, 0, st>>>(Q, ldq, rows, V, n, R, U);
+    k_form_u<<<(unsigned)cdiv(tot, 256), 256, 0, st>>>(Q, ldq, rows, V, n, ldv, R, U);
     RBKI_LAUNCH_CHECK("k_form_u");
     k_sign_fix<<<R, 256, 0, st>>>(U, rows, R);
     RBKI_LAUNCH_CHECK("k_sign_fix");

@@ -1,0 +1,631 @@
+// Tensor-core (tcgen05 / TMEM / TMA) streaming kernels for the mixed path on sm_103a.
+//
+// One kernel template streams X once per launch over the native C-order layout, viewed
+// per mode as [A][I][C], in tiles of 128 unfolding columns x all I rows:
+//   KRYLOV  P += X_tile (X_tile^T Q)      Algorithm 1 step 3 / Eq. BKspace: one X read per step
+//   SKETCH  P += X_tile Omega_tile        Algorithm 1 step 2 (W = X Omega)
+//   TTM     Y  = X_tile^T U  (stored)     Algorithm 2 step 6, first mode product of the core
+// Operands are BF16 (or FP16) with FP32 accumulation in tensor memory.  With `split`, the
+// skinny operand is carried as a hi + lo pair of BF16 values (N doubles), which makes the
+// products accurate to ~FP32 against BF16-exact X.
+//
+// Data movement: TMA tiled loads with 128-byte swizzle, boxes of 64 (contiguous dim) x
+// 128 rows; a "slab" is 128 rows x 128 columns = two boxes = 32 KB.  Three layouts of X in
+// shared memory are consumed directly by the tensor core:
+//   C > 1 ("CFAST", columns contiguous): GEMM1 reads X^T as an MN-major operand, GEMM2 reads
+//        X as a K-major operand;  C == 1 ("IFAST", rows contiguous): the roles swap.
+// Warp roles (192 threads): warp 0 TMA producer, warp 1 MMA issuer + TMEM owner, warps 2-5
+// epilogue (TMEM -> registers -> BF16 operand image in shared memory / global stores).
+// Every mbarrier wait is bounded; on expiry the CTA sets an abort flag, drains, frees its
+// TMEM and reports through an error word.
+#include <cuda.h>
+
+#include "kernels.h"
+#include "tc.h"
+
+namespace rbki {
+namespace tc {
+namespace {
+
+constexpr int SLAB_BYTES = 32768;
+constexpr int BOX_BYTES = 16384;
+constexpr int NTHREADS = 192;
+constexpr uint32_t WAIT_LIMIT = 1u << 25;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+__device__ __forceinline__ uint32_t mbar_try(uint32_t a, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return ok;
+}
+// bounded wait: false on timeout (abort raised) or when another role already aborted
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort_flag) {
+    for (uint32_t it = 0; it < WAIT_LIMIT; ++it) {
+        if (mbar_try(a, parity)) return true;
+        if (*abort_flag) return false;
+    }
+    *abort_flag = 1;
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t mbar, int c0,
+                                            int c1, int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
+        "l"(map), "r"(mbar), "r"(c0), "r"(c1), "r"(c2)
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t mbar, int c0, int c1) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+        "l"(map), "r"(mbar), "r"(c0), "r"(c1)
+        : "memory");
+}
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void umma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 32 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// shared-memory matrix descriptor (sm_100 family): start, leading / stride byte offsets,
+// version 1, layout type in bits 61-63 (0 = no swizzle, 2 = 128-byte swizzle)
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo, uint32_t layout) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | ((uint64_t)layout << 61);
+}
+constexpr uint32_t LAYOUT_SW128 = 2, LAYOUT_NONE = 0;
+
+// instruction descriptor of kind::f16: D = F32, A = B = BF16 (or F16), M = 128, N
+__device__ __forceinline__ uint32_t idesc_f16(int N, bool a_mn, bool b_mn, bool fp16) {
+    const uint32_t fmt = fp16 ? 0u : 1u;
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((a_mn ? 1u : 0u) << 15) | ((b_mn ? 1u : 0u) << 16) |
+           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ uint32_t pack2(float a, float b, bool fp16) {
+    if (fp16) {
+        __half2 h = __floats2half2_rn(a, b);
+        return *reinterpret_cast<uint32_t*>(&h);
+    }
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+__device__ __forceinline__ float round_lo(float v, bool fp16) {
+    return fp16 ? __half2float(__float2half_rn(v)) : __bfloat162float(__float2bfloat16_rn(v));
+}
+
+template <int MODE, bool IFAST>
+__global__ void __launch_bounds__(NTHREADS, 1) k_stream_tc(const __grid_constant__ CUtensorMap tmap, const Params p) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t sbase = smem_u32(smem);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nslot = p.nslot, NS = p.NS, N = p.N;
+    uint64_t* bars = (uint64_t*)(smem + p.smem_bar);
+    const uint32_t b_full = smem_u32(bars), b_empty = b_full + 8 * nslot;
+    const uint32_t b_yfull = b_empty + 8 * nslot, b_yready = b_yfull + 16, b_ysfree = b_yready + 16;
+    const uint32_t b_omfull = b_ysfree + 16, b_qfull = b_omfull + 16, b_pdone = b_qfull + 8;
+    uint32_t* tmem_slot = (uint32_t*)(bars + 2 * nslot + 10);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < nslot; ++i) {
+            mbar_init(b_full + 8 * i, 1);
+            mbar_init(b_empty + 8 * i, 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(b_yfull + 8 * i, 1);
+            mbar_init(b_yready + 8 * i, 128);
+            mbar_init(b_ysfree + 8 * i, 1);
+            mbar_init(b_omfull + 8 * i, 1);
+        }
+        mbar_init(b_qfull, 1);
+        mbar_init(b_pdone, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_async_smem();
+    }
+    if (warp == 1) {
+        tmem_alloc(smem_u32(tmem_slot), p.tmem_cols);
+        tmem_relinquish();
+    }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tmem_slot;
+    const int64_t my_tiles = (p.tiles - blockIdx.x + gridDim.x - 1) / gridDim.x;
+    const uint32_t X0 = sbase + p.smem_x, Q0 = sbase + p.smem_q, Y0 = sbase + p.smem_y;
+    const uint32_t ycol0 = (MODE == TTM) ? 0u : (uint32_t)(NS * N);
+    const bool fp16 = p.fp16 != 0;
+
+    if (warp == 0) {
+        // ------------------------------ TMA producer ------------------------------
+        if (lane == 0) {
+            if (MODE != SKETCH) {
+                mbar_expect_tx(b_qfull, p.qimg_bytes);
+                for (uint32_t off = 0; off < p.qimg_bytes; off += 32768) {
+                    uint32_t sz = min(32768u, p.qimg_bytes - off);
+                    bulk_load(Q0 + off, (const uint8_t*)p.qimg + off, sz, b_qfull);
+                }
+            }
+            uint32_t slot = 0, phase = 0;
+            for (int64_t k = 0; k < my_tiles && !*abort_flag; ++k) {
+                const int64_t t = blockIdx.x + k * gridDim.x;
+                int ca = 0, cc = 0;   // TMA coordinates of the tile
+                if (!IFAST) {
+                    ca = (int)(t / p.ctiles);
+                    cc = (int)((t % p.ctiles) * 128);
+                } else {
+                    ca = (int)(t * 128);
+                }
+                if (MODE == SKETCH) {
+                    const int b = (int)(k & 1);
+                    if (k >= 2 && !mbar_wait(b_ysfree + 8 * b, (uint32_t)(((k - 2) >> 1) & 1), abort_flag)) break;
+                    mbar_expect_tx(b_omfull + 8 * b, p.yimg_bytes);
+                    bulk_load(Y0 + b * p.yimg_bytes, (const uint8_t*)p.omg + (size_t)t * p.yimg_bytes, p.yimg_bytes,
+                              b_omfull + 8 * b);
+                }
+                for (int s = 0; s < NS; ++s) {
+                    if (!mbar_wait(b_empty + 8 * slot, phase ^ 1, abort_flag)) break;
+                    mbar_expect_tx(b_full + 8 * slot, SLAB_BYTES);
+                    const uint32_t dst = X0 + slot * SLAB_BYTES;
+                    if (!IFAST) {
+                        tma_load_3d(dst, &tmap, b_full + 8 * slot, cc, 128 * s, ca);
+                        tma_load_3d(dst + BOX_BYTES, &tmap, b_full + 8 * slot, cc + 64, 128 * s, ca);
+                    } else {
+                        tma_load_2d(dst, &tmap, b_full + 8 * slot, 128 * s, ca);
+                        tma_load_2d(dst + BOX_BYTES, &tmap, b_full + 8 * slot, 128 * s + 64, ca);
+                    }
+                    if (++slot == (uint32_t)nslot) { slot = 0; phase ^= 1; }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------ MMA issuer ------------------------------
+        if (lane == 0) {
+            const uint32_t id1 = idesc_f16(N, /*a_mn=*/!IFAST, /*b_mn=*/true, fp16);   // Y = X^T Q
+            const uint32_t id2 = idesc_f16(N, /*a_mn=*/IFAST, /*b_mn=*/true, fp16);    // P += X Y
+            const uint32_t qlbo = (uint32_t)(N / 8) * 128u;
+            bool ok = true;
+            if (MODE != SKETCH) ok = mbar_wait(b_qfull, 0, abort_flag);
+            uint32_t slot = 0, phase = 0;
+            for (int64_t k = 0; ok && k < my_tiles; ++k) {
+                const int b = (int)(k & 1);
+                const uint32_t slot0 = slot, phase0 = phase;
+                if (MODE != SKETCH) {
+                    if (MODE == TTM && k >= 2 && !mbar_wait(b_yready + 8 * b, (uint32_t)(((k - 2) >> 1) & 1), abort_flag)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t ytm = tbase + ycol0 + (uint32_t)(b * N);
+                    for (int s = 0; s < NS && ok; ++s) {
+                        if (!mbar_wait(b_full + 8 * slot, phase, abort_flag)) { ok = false; break; }
+                        tc_fence_after();
+                        const uint32_t xs = X0 + slot * SLAB_BYTES;
+#pragma unroll
+                        for (int kk = 0; kk < 8; ++kk) {
+                            const uint64_t ad = IFAST ? sdesc(xs + (kk >> 2) * BOX_BYTES + (kk & 3) * 32, 16, 1024, LAYOUT_SW128)
+                                                      : sdesc(xs + kk * 2048, BOX_BYTES, 1024, LAYOUT_SW128);
+                            const uint64_t bd = sdesc(Q0 + (uint32_t)(s * 8 + kk) * 2u * qlbo, qlbo, 128, LAYOUT_NONE);
+                            umma_f16(ytm, ad, bd, id1, (s | kk) != 0 ? 1u : 0u);
+                        }
+                        if (MODE == TTM) umma_commit(b_empty + 8 * slot);
+                        if (++slot == (uint32_t)nslot) { slot = 0; phase ^= 1; }
+                    }
+                    if (!ok) break;
+                    umma_commit(b_yfull + 8 * b);
+                }
+                if (MODE != TTM) {
+                    const uint32_t rb = (MODE == KRYLOV) ? b_yready + 8 * b : b_omfull + 8 * b;
+                    if (!mbar_wait(rb, (uint32_t)((k >> 1) & 1), abort_flag)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t yimg = Y0 + (uint32_t)b * p.yimg_bytes;
+                    uint32_t sl = slot0, ph = phase0;
+                    for (int s = 0; s < NS; ++s) {
+                        if (MODE == SKETCH) {
+                            if (!mbar_wait(b_full + 8 * sl, ph, abort_flag)) { ok = false; break; }
+                            tc_fence_after();
+                        }
+                        const uint32_t xs = X0 + sl * SLAB_BYTES;
+                        const uint32_t ptm = tbase + (uint32_t)(s * N);
+#pragma unroll
+                        for (int kk = 0; kk < 8; ++kk) {
+                            const uint64_t ad = IFAST ? sdesc(xs + kk * 2048, BOX_BYTES, 1024, LAYOUT_SW128)
+                                                      : sdesc(xs + (kk >> 2) * BOX_BYTES + (kk & 3) * 32, 16, 1024, LAYOUT_SW128);
+                            const uint64_t bd = sdesc(yimg + kk * 256, 128, 2048, LAYOUT_NONE);
+                            umma_f16(ptm, ad, bd, id2, (k > 0 || kk > 0) ? 1u : 0u);
+                        }
+                        umma_commit(b_empty + 8 * sl);
+                        if (++sl == (uint32_t)nslot) { sl = 0; ph ^= 1; }
+                    }
+                    if (!ok) break;
+                    umma_commit(b_ysfree + 8 * b);
+                    if (MODE == SKETCH) { slot = sl; phase = ph; }
+                }
+            }
+            if (MODE != TTM) umma_commit(b_pdone);
+        }
+    } else {
+        // ------------------------------ epilogue (warps 2-5) ------------------------------
+        const int q = warp & 3;
+        const int row = q * 32 + lane;                  // tile column (TMEM lane)
+        const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+        float v[64];
+        if (MODE != SKETCH) {
+            for (int64_t k = 0; k < my_tiles; ++k) {
+                const int b = (int)(k & 1);
+                if (!mbar_wait(b_yfull + 8 * b, (uint32_t)((k >> 1) & 1), abort_flag)) break;
+                tc_fence_after();
+                const uint32_t ytm = tbase + ycol0 + (uint32_t)(b * N) + lane_off;
+                tmem_ld32(ytm, v);
+                if (N > 32) tmem_ld32(ytm + 32, v + 32);
+                const int Sh = p.Sh;
+                if (p.split)
+                    for (int s = 0; s < Sh; ++s) v[s] += v[Sh + s];
+                if (MODE == TTM) {
+                    tc_fence_before();
+                    mbar_arrive(b_yready + 8 * b);
+                    const int64_t t = blockIdx.x + k * gridDim.x;
+                    if (!IFAST) {
+                        const int64_t a = t / p.ctiles, c = (t % p.ctiles) * 128 + row;
+                        if (c < p.C)
+                            for (int s = 0; s < Sh; ++s) p.yout[(a * Sh + s) * p.C + c] = v[s];
+                    } else {
+                        const int64_t a = t * 128 + row;
+                        if (a < p.A)
+                            for (int s = 0; s < Sh; ++s) p.yout[a * Sh + s] = v[s];
+                    }
+                } else {
+                    if (k >= 2 && !mbar_wait(b_ysfree + 8 * b, (uint32_t)(((k - 2) >> 1) & 1), abort_flag)) break;
+                    // BF16 operand image of Y (MN-major, no swizzle): element (c, n) at
+                    // (n/8)*2048 + c*16 + (n%8)*2
+                    uint8_t* img = smem + p.smem_y + (size_t)b * p.yimg_bytes;
+                    if (p.split) {
+                        for (int s = 0; s < Sh; ++s) {
+                            float hi = round_lo(v[s], fp16);
+                            v[Sh + s] = v[s] - hi;
+                            v[s] = hi;
+                        }
+                    }
+                    for (int g = 0; g < N / 8; ++g) {
+                        uint4 w;
+                        w.x = pack2(v[8 * g + 0], v[8 * g + 1], fp16);
+                        w.y = pack2(v[8 * g + 2], v[8 * g + 3], fp16);
+                        w.z = pack2(v[8 * g + 4], v[8 * g + 5], fp16);
+                        w.w = pack2(v[8 * g + 6], v[8 * g + 7], fp16);
+                        *reinterpret_cast<uint4*>(img + g * 2048 + row * 16) = w;
+                    }
+                    fence_async_smem();
+                    tc_fence_before();
+                    mbar_arrive(b_yready + 8 * b);
+                }
+            }
+        }
+        if (MODE != TTM) {
+            if (mbar_wait(b_pdone, 0, abort_flag)) {
+                tc_fence_after();
+                float* out = p.part + (size_t)blockIdx.x * p.I * N;
+                for (int s = 0; s < NS; ++s) {
+                    const uint32_t ptm = tbase + (uint32_t)(s * N) + lane_off;
+                    tmem_ld32(ptm, v);
+                    if (N > 32) tmem_ld32(ptm + 32, v + 32);
+                    const int64_t i = (int64_t)s * 128 + row;
+                    if (i < p.I) {
+                        float4* o = reinterpret_cast<float4*>(out + i * N);
+                        for (int g = 0; g < N / 4; ++g) o[g] = make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tbase, p.tmem_cols);
+    }
+    if (threadIdx.x == 0 && *abort_flag) atomicOr(p.err, 1);
+}
+
+// ---- operand images ----
+// B image of a skinny FP64 matrix M (rows x S, ld ldm) for GEMM1: MN-major no-swizzle,
+// element (i, n) at (i/8)*(N/8)*128 + (n/8)*128 + (i%8)*16 + (n%8)*2; rows padded to
+// rows_pad; columns n < S hold hi (or the value), S <= n < 2S the lo part when split.
+__global__ void k_skinny_image(const double* __restrict__ M, int64_t ldm, int64_t rows, int S,
+                               int64_t rows_pad, int N, int split, int fp16, uint16_t* __restrict__ img) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= rows_pad * N) return;
+    int64_t i = e / N;
+    int n = (int)(e % N);
+    float val = 0.f;
+    int s = (split && n >= S) ? n - S : n;
+    if (i < rows && s < S) {
+        double x = M[i * ldm + s];
+        float hi = fp16 ? __half2float(__double2half(x)) : __bfloat162float(__double2bfloat16(x));
+        val = (split && n >= S) ? (float)(x - (double)hi) : hi;
+    }
+    uint16_t bits;
+    if (fp16) { __half h = __float2half_rn(val); bits = *reinterpret_cast<uint16_t*>(&h); }
+    else { __nv_bfloat16 h = __float2bfloat16_rn(val); bits = *reinterpret_cast<uint16_t*>(&h); }
+    int64_t off = (i / 8) * (N / 8) * 64 + (n / 8) * 64 + (i % 8) * 8 + (n % 8);   // in elements
+    img[off] = bits;
+}
+
+// Per-tile Omega images for SKETCH: tile t covers 128 unfolding columns; element (c, n) of
+// tile t at t*128*N + (n/8)*1024 + c*8 + n%8 (elements).  Columns outside the tensor are 0.
+__global__ void k_omega_images(uint64_t seed, int mode, int64_t A, int64_t C, int ifast, int64_t ctiles,
+                               int64_t tiles, int S, int N, int split, int fp16, uint16_t* __restrict__ img) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // (tile, c, pair)
+    const int npair = (S + 1) / 2;
+    if (e >= tiles * 128 * npair) return;
+    int pair = (int)(e % npair);
+    int64_t tc_ = e / npair;
+    int c = (int)(tc_ % 128);
+    int64_t t = tc_ / 128;
+    int64_t col;
+    bool valid;
+    if (!ifast) {
+        int64_t a = t / ctiles, cc = (t % ctiles) * 128 + c;
+        valid = cc < C;
+        col = a * C + cc;
+    } else {
+        int64_t a = t * 128 + c;
+        valid = a < A;
+        col = a;
+    }
+    double z[2] = {0.0, 0.0};
+    if (valid) omega_pair_f64(seed, (uint32_t)mode, (uint64_t)col, (uint32_t)pair, z[0], z[1]);
+    uint16_t* base = img + (size_t)t * 128 * N;
+    for (int u = 0; u < 2; ++u) {
+        int s = 2 * pair + u;
+        if (s >= S) break;
+        double x = z[u];
+        float hi = fp16 ? __half2float(__double2half(x)) : __bfloat162float(__double2bfloat16(x));
+        float lo = (float)(x - (double)hi);
+        int ns[2] = {s, split ? S + s : -1};
+        float vs[2] = {hi, lo};
+        for (int w = 0; w < 2; ++w) {
+            int n = ns[w];
+            if (n < 0) continue;
+            uint16_t bits;
+            if (fp16) { __half h = __float2half_rn(vs[w]); bits = *reinterpret_cast<uint16_t*>(&h); }
+            else { __nv_bfloat16 h = __float2bfloat16_rn(vs[w]); bits = *reinterpret_cast<uint16_t*>(&h); }
+            base[(n / 8) * 1024 + c * 8 + n % 8] = bits;
+        }
+    }
+}
+
+// out[i*ld + s] = sum_b (part[b][i][s] + split * part[b][i][Sh + s]), FP64, fixed order
+__global__ void k_reduce_tc(const float* __restrict__ part, int nb, int64_t I, int N, int Sh, int split,
+                            double* __restrict__ out, int64_t ld, double* __restrict__ out2, int64_t ld2) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= I * Sh) return;
+    int64_t i = e / Sh;
+    int s = (int)(e % Sh);
+    double acc = 0.0;
+    for (int b = 0; b < nb; ++b) {
+        const float* pb = part + ((size_t)b * I + i) * N;
+        acc += (double)pb[s];
+        if (split) acc += (double)pb[Sh + s];
+    }
+    out[i * ld + s] = acc;
+    if (out2) out2[i * ld2 + s] = acc;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)ptr;
+    }
+    return fn;
+}
+
+template <int MODE, bool IFAST>
+size_t smem_limit() {
+    static size_t mx = 0;
+    if (!mx) mx = max_dyn_smem(k_stream_tc<MODE, IFAST>);
+    return mx;
+}
+
+}  // namespace
+
+bool supported(const View& v, int mode, int N) {
+    if (v.dtype != RBKI_BF16 && v.dtype != RBKI_F16) return false;
+    if (N < 16 || N > 64 || N % 16) return false;
+    const bool ifast = v.C == 1;
+    if (ifast ? (v.I % 8) : (v.C % 8)) return false;
+    if (v.A > 0x7fffffffLL || v.I > 0x7fffffffLL || v.C > 0x7fffffffLL) return false;
+    const int NS = (int)cdiv(v.I, 128);
+    const uint32_t tm = (uint32_t)((mode == TTM ? 0 : NS * N) + (mode == SKETCH ? 0 : 2 * N));
+    if (tm > 512) return false;
+    const size_t qimg = mode == SKETCH ? 0 : (size_t)NS * 128 * N * 2;
+    const size_t yimg = mode == TTM ? 0 : (size_t)2 * 128 * N * 2;
+    const size_t avail = 227 * 1024 - 2048 - qimg - yimg;
+    const int nslot = (int)std::min<size_t>(8, avail / SLAB_BYTES);
+    if (mode == KRYLOV ? nslot < NS : nslot < 2) return false;
+    return true;
+}
+
+int64_t num_tiles(const View& v) { return v.C > 1 ? v.A * cdiv(v.C, 128) : cdiv(v.A, 128); }
+
+size_t image_bytes_skinny(const View& v, int N) { return (size_t)cdiv(v.I, 128) * 128 * N * 2; }
+size_t image_bytes_omega(const View& v, int N) { return (size_t)num_tiles(v) * 128 * N * 2; }
+int grid_size(const View& v) {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    return (int)std::min<int64_t>(num_tiles(v), sms);
+}
+
+rbki_status skinny_image(const double* M, int64_t ldm, int64_t rows, int S, int N, bool split, bool fp16,
+                         void* img, cudaStream_t st) {
+    int64_t rows_pad = cdiv(rows, 128) * 128;
+    int64_t tot = rows_pad * N;
+    k_skinny_image<<<(unsigned)cdiv(tot, 256), 256, 0, st>>>(M, ldm, rows, S, rows_pad, N, split ? 1 : 0,
+                                                             fp16 ? 1 : 0, (uint16_t*)img);
+    RBKI_LAUNCH_CHECK("k_skinny_image");
+    return RBKI_OK;
+}
+
+rbki_status omega_images(uint64_t seed, int mode, const View& v, int S, int N, bool split, void* img,
+                         cudaStream_t st) {
+    const bool ifast = v.C == 1;
+    int64_t ctiles = ifast ? 1 : cdiv(v.C, 128);
+    int64_t tiles = num_tiles(v);
+    RBKI_CUDA_TRY(cudaMemsetAsync(img, 0, image_bytes_omega(v, N), st));
+    int64_t tot = tiles * 128 * ((S + 1) / 2);
+    k_omega_images<<<(unsigned)cdiv(tot, 256), 256, 0, st>>>(seed, mode, v.A, v.C, ifast ? 1 : 0, ctiles, tiles, S,
+                                                             N, split ? 1 : 0, v.dtype == RBKI_F16 ? 1 : 0,
+                                                             (uint16_t*)img);
+    RBKI_LAUNCH_CHECK("k_omega_images");
+    return RBKI_OK;
+}
+
+rbki_status stream_tc(int mode, const View& v, int N, int Sh, bool split, const void* qimg, const void* omg,
+                      float* part, float* yout, int* err, cudaStream_t st) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return set_error(RBKI_E_CUDA, "cuTensorMapEncodeTiled unavailable");
+    const bool ifast = v.C == 1;
+    CUtensorMap map;
+    const CUtensorMapDataType dt = v.dtype == RBKI_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    CUresult r;
+    if (!ifast) {
+        cuuint64_t dims[3] = {(cuuint64_t)v.C, (cuuint64_t)v.I, (cuuint64_t)v.A};
+        cuuint64_t strides[2] = {(cuuint64_t)v.C * 2, (cuuint64_t)v.I * v.C * 2};
+        cuuint32_t box[3] = {64, 128, 1};
+        cuuint32_t es[3] = {1, 1, 1};
+        r = enc(&map, dt, 3, const_cast<void*>(v.data), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    } else {
+        cuuint64_t dims[2] = {(cuuint64_t)v.I, (cuuint64_t)v.A};
+        cuuint64_t strides[1] = {(cuuint64_t)v.I * 2};
+        cuuint32_t box[2] = {64, 128};
+        cuuint32_t es[2] = {1, 1};
+        r = enc(&map, dt, 2, const_cast<void*>(v.data), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    }
+    if (r != CUDA_SUCCESS) return set_error(RBKI_E_CUDA, "cuTensorMapEncodeTiled failed");
+
+    Params p{};
+    p.A = v.A; p.I = v.I; p.C = v.C;
+    p.NS = (int)cdiv(v.I, 128);
+    p.N = N; p.Sh = Sh; p.split = split ? 1 : 0;
+    p.tiles = num_tiles(v);
+    p.ctiles = ifast ? 1 : cdiv(v.C, 128);
+    p.qimg = qimg; p.omg = omg;
+    p.qimg_bytes = mode == SKETCH ? 0 : (uint32_t)image_bytes_skinny(v, N);
+    p.yimg_bytes = (uint32_t)(128 * N * 2);
+    p.part = part; p.yout = yout; p.err = err;
+    p.fp16 = v.dtype == RBKI_F16 ? 1 : 0;
+    uint32_t tm = (uint32_t)((mode == TTM ? 0 : p.NS * N) + (mode == SKETCH ? 0 : 2 * N));
+    uint32_t cols = 32;
+    while (cols < tm) cols <<= 1;
+    p.tmem_cols = cols;
+    const size_t yimg_total = mode == TTM ? 0 : 2 * (size_t)p.yimg_bytes;
+    const size_t bar_bytes = 256;
+    size_t limit = 0;
+#define LIM(M_, F_) limit = smem_limit<M_, F_>()
+    if (mode == KRYLOV) { if (ifast) LIM(KRYLOV, true); else LIM(KRYLOV, false); }
+    else if (mode == SKETCH) { if (ifast) LIM(SKETCH, true); else LIM(SKETCH, false); }
+    else { if (ifast) LIM(TTM, true); else LIM(TTM, false); }
+#undef LIM
+    if (!limit) return set_error(RBKI_E_CUDA, "stream_tc: shared-memory attribute");
+    const size_t fixed = 1024 + p.qimg_bytes + yimg_total + bar_bytes;
+    if (limit < fixed + 2 * SLAB_BYTES) return set_error(RBKI_E_UNSUPPORTED, "stream_tc: shared memory");
+    p.nslot = (int)std::min<size_t>(8, (limit - fixed) / SLAB_BYTES);
+    if (mode == KRYLOV && p.nslot < p.NS) return set_error(RBKI_E_UNSUPPORTED, "stream_tc: tile does not fit");
+    p.smem_x = 0;
+    p.smem_q = (uint32_t)(p.nslot * SLAB_BYTES);
+    p.smem_y = p.smem_q + p.qimg_bytes;
+    p.smem_bar = (uint32_t)(p.smem_y + yimg_total);
+    const size_t smem = 1024 + p.smem_bar + bar_bytes;
+    const int grid = grid_size(v);
+#define LAUNCH(M_, F_) k_stream_tc<M_, F_><<<grid, NTHREADS, smem, st>>>(map, p)
+    if (mode == KRYLOV) { if (ifast) LAUNCH(KRYLOV, true); else LAUNCH(KRYLOV, false); }
+    else if (mode == SKETCH) { if (ifast) LAUNCH(SKETCH, true); else LAUNCH(SKETCH, false); }
+    else { if (ifast) LAUNCH(TTM, true); else LAUNCH(TTM, false); }
+#undef LAUNCH
+    RBKI_LAUNCH_CHECK("k_stream_tc");
+    return RBKI_OK;
+}
+
+rbki_status reduce_parts(const float* part, int nb, int64_t I, int N, int Sh, bool split, double* out, int64_t ld,
+                         double* out2, int64_t ld2, cudaStream_t st) {
+    int64_t tot = I * Sh;
+    k_reduce_tc<<<(unsigned)cdiv(tot, 256), 256, 0, st>>>(part, nb, I, N, Sh, split ? 1 : 0, out, ld, out2, ld2);
+    RBKI_LAUNCH_CHECK("k_reduce_tc");
+    return RBKI_OK;
+}
+
+}  // namespace tc
+}  // namespace rbki

@@ -48,16 +48,34 @@ rbki_status atb_cuda(const double* A, int64_t lda, int ma, const double* B, int6
 rbki_status orth_pass_cuda(double* Q, int64_t ldq, int64_t rows, int m, int S, double tau,
                            double* scratch, int32_t* kept, cudaStream_t st);
 size_t orth_scratch_doubles(int64_t rows, int m, int S);
-// symmetric eigensolver, descending; V columns are eigenvectors (n x n row-major)
+// symmetric eigensolver (k_eig.cu), descending; V (n x n row-major) columns are eigenvectors
 rbki_status syev_cuda(const double* A, int n, double* w, double* V, double* scratch,
                       cudaStream_t st);
+// leading nwant eigenpairs only: w (nwant), V (n x nwant row-major)
+rbki_status syev_top_cuda(const double* A, int n, int nwant, double* w, double* V, double* scratch,
+                          cudaStream_t st);
 size_t syev_scratch_doubles(int n);
-// U[i][k] = sum_t Q[i*ldq + t] V[t*n + k] (k < R); then sign-normalise each column.
+// U[i][k] = sum_t Q[i*ldq + t] V[t*ldv + k] (k < R); then sign-normalise each column.
 // Q == nullptr means identity (Gram path): U = V[:, :R].
 rbki_status form_factor_cuda(const double* Q, int64_t ldq, int64_t rows, const double* V, int n,
-                             int R, double* U, cudaStream_t st);
+                             int ldv, int R, double* U, cudaStream_t st);
 rbki_status copy_f64_cuda(const double* src, double* dst, int64_t n, cudaStream_t st);
 rbki_status fill_i32_cuda(int32_t* dst, int32_t v, int n, cudaStream_t st);
+
+// Opt a kernel into the largest dynamic shared memory the device allows next to its static
+// shared memory; returns that maximum (bytes) or 0 on error.
+template <typename K>
+inline size_t max_dyn_smem(K kernel) {
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) return 0;
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    size_t mx = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx) != cudaSuccess)
+        return 0;
+    return mx;
+}
 
 // profiling hook (api.cu): returns a token for prof_end, or -1 when profiling is off
 int prof_begin(int cls, cudaStream_t st);

@@ -22,11 +22,18 @@ struct ModePlan {
     double* eval = nullptr;        // b
     double* syev_ws = nullptr;
     int32_t* kept = nullptr;
+    // tensor-core path (mixed precision)
+    bool tc = false;               // sketch + Krylov steps on tcgen05
+    int N = 0;                     // MMA width (includes the lo half when split)
+    void* qimg = nullptr;          // BF16 operand image of Q_j
+    void* omg = nullptr;           // per-tile Omega images
+    float* tpart = nullptr;        // [grid][I][N] partials
+    int tgrid = 0;
 };
 
 struct Plan {
     int N = 0, dtype = 0, prec = 0, stream_dtype = 0;
-    bool mixed = false, stage = false;
+    bool mixed = false, stage = false, split = false;
     int64_t dims[RBKI_MAX_ORDER] = {0};
     int64_t numel = 0, ranks_numel = 0;
     int order[RBKI_MAX_ORDER] = {0};
@@ -37,6 +44,10 @@ struct Plan {
     double* scal = nullptr;        // scalars + reduction partials
     char* xs = nullptr;            // staged low-precision copy of X
     double* tbuf[2] = {nullptr, nullptr};
+    int32_t* err = nullptr;        // device error word (bounded waits)
+    bool ttm_tc = false;           // first core TTM on tcgen05
+    int ttm_N = 0;
+    void* ttm_img = nullptr;
     size_t ws_bytes = 0;
     // bound at run time
     const void* xin = nullptr;

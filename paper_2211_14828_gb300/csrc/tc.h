@@ -1,0 +1,46 @@
+// Tensor-core streaming kernels (k_tc.cu): host interface.
+#pragma once
+
+#include "kernels.h"
+
+namespace rbki {
+namespace tc {
+
+enum { KRYLOV = 0, SKETCH = 1, TTM = 2 };
+
+struct Params {
+    int64_t A, I, C;        // X viewed as [A][I][C]
+    int NS;                 // 128-row slabs: cdiv(I, 128)
+    int N;                  // MMA N (includes the lo half when split)
+    int Sh;                 // logical width (N/2 when split, else the used columns)
+    int split;
+    int64_t tiles, ctiles;
+    int nslot;
+    uint32_t smem_x, smem_q, smem_y, smem_bar;
+    uint32_t tmem_cols;
+    const void* qimg;       // GEMM1 B image (global)
+    uint32_t qimg_bytes;
+    const void* omg;        // per-tile Omega images (SKETCH)
+    uint32_t yimg_bytes;    // 128 * N * 2
+    float* part;            // [grid][I][N] partial products (KRYLOV, SKETCH)
+    float* yout;            // [A][Sh][C] TTM output
+    int* err;               // error word (bounded wait expired)
+    int fp16;
+};
+
+bool supported(const View& v, int mode, int N);
+int64_t num_tiles(const View& v);
+int grid_size(const View& v);
+size_t image_bytes_skinny(const View& v, int N);
+size_t image_bytes_omega(const View& v, int N);
+rbki_status skinny_image(const double* M, int64_t ldm, int64_t rows, int S, int N, bool split, bool fp16,
+                         void* img, cudaStream_t st);
+rbki_status omega_images(uint64_t seed, int mode, const View& v, int S, int N, bool split, void* img,
+                         cudaStream_t st);
+rbki_status stream_tc(int mode, const View& v, int N, int Sh, bool split, const void* qimg, const void* omg,
+                      float* part, float* yout, int* err, cudaStream_t st);
+rbki_status reduce_parts(const float* part, int nb, int64_t I, int N, int Sh, bool split, double* out,
+                         int64_t ld, double* out2, int64_t ld2, cudaStream_t st);
+
+}  // namespace tc
+}  // namespace rbki

@@ -44,8 +44,10 @@ def test_krylov_product_fp64(rb, dims, s):
         np.testing.assert_allclose(p.cpu().numpy(), want, rtol=1e-12, atol=1e-12 * np.abs(want).max())
 
 
-@pytest.mark.parametrize("dims", [(20, 30, 40), (64, 64, 64)])
+@pytest.mark.parametrize("dims", [(21, 30, 37), (33, 17, 45)])
 def test_krylov_product_bf16_cuda_cores(rb, dims):
+    """Shapes the TMA path cannot take (contiguous extent not a multiple of 8) run the
+    FP32-accumulate CUDA-core kernels."""
     g = np.random.default_rng(1)
     x = g.standard_normal(dims).astype(np.float32)
     q = g.standard_normal((dims[0], 12))
@@ -95,7 +97,8 @@ def _check_fp64(rb, wl, sine_tol=1e-10, err_rtol=1e-12):
         np.testing.assert_allclose(out["eigvals"][n].cpu().numpy(), ref["eigvals"][n], rtol=1e-11,
                                    atol=1e-12 * ref["eigvals"][n][0])
     info = out["info"].cpu().numpy()
-    assert list(info[x.dim():]) == [1 if p == "gram" else 0 for p in ref["path"]]
+    assert list(info[x.dim(): 2 * x.dim()]) == [1 if p == "gram" else 0 for p in ref["path"]]
+    assert info[2 * x.dim()] == 0
     assert list(info[: x.dim()]) == ref["kept"]
     # reconstruction error: identity |X|^2 - |G|^2, and explicit from the returned factors
     g = out["core"].cpu().numpy()
@@ -144,3 +147,36 @@ def test_tucker_mixed_small_config(rb):
     err = metrics.fnorm(wl.x - rbki.reconstruct(g, us))
     assert abs(err - err_ref) <= 0.01 * err_ref
     assert abs(_err_from_norms(out["norms"]) - err_ref) <= 0.01 * err_ref
+    assert out["info"].cpu().numpy()[6] == 0
+
+
+def _bf16(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).bfloat16().double().numpy()
+
+
+@pytest.mark.parametrize("dims", [(200, 48, 40), (64, 64, 64), (512, 24, 136), (96, 136, 16), (8, 384, 24)])
+@pytest.mark.parametrize("s", [12, 30])
+def test_krylov_product_tensor_core(rb, dims, s):
+    """tcgen05 Krylov step vs FP64 products of the BF16-exact operands.
+    split: Q and Y carried as hi + lo BF16 pairs -> FP32-level agreement; plain BF16: the
+    reference rounds Q and Y to BF16 the same way (a few elements may round the other way)."""
+    g = np.random.default_rng(sum(dims) * 7 + s)
+    x = g.standard_normal(dims).astype(np.float32)
+    xt = torch.from_numpy(x).cuda()
+    xb = _bf16(x)
+    for mode in range(len(dims)):
+        if dims[mode] > 512:
+            continue
+        q = g.standard_normal((dims[mode], s))
+        qt = torch.from_numpy(q).cuda()
+        xn = unfold(xb, mode)
+        exact = xn @ (xn.T @ q)
+        p_split = rb.rbki_krylov_product(xt, mode, qt, prec=-1).cpu().numpy()
+        rel = np.linalg.norm(p_split - exact) / np.linalg.norm(exact)
+        assert rel < 2e-5, (mode, rel)
+        p = rb.rbki_krylov_product(xt, mode, qt, prec="bf16").cpu().numpy()
+        yb = _bf16(xn.T @ _bf16(q))
+        want = xn @ yb
+        rel = np.linalg.norm(p - want) / np.linalg.norm(want)
+        assert rel < 2e-3, (mode, rel)
+        assert np.linalg.norm(p - exact) / np.linalg.norm(exact) < 1e-2
