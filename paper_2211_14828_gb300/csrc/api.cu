@@ -123,7 +123,7 @@ rbki_status make_plan(const rbki_tensor* X, const rbki_params* prm, Plan& pl) {
         m.b = m.gram ? (int)m.I : (int)b;
         if (m.gram && m.I > 256) return set_error(RBKI_E_UNSUPPORTED, "Gram path with I_n > 256");
         if (!m.gram && m.b > 256) return set_error(RBKI_E_UNSUPPORTED, "Krylov width S(q+1) > 256");
-        if (!m.gram && m.S > 128) return set_error(RBKI_E_UNSUPPORTED, "sketch size > 128");
+        if (!m.gram && m.S > 96) return set_error(RBKI_E_UNSUPPORTED, "sketch size > 96");
     }
     // core chain order: largest shrink I_n / R_n first (ties -> lower mode)
     for (int n = 0; n < pl.N; ++n) pl.order[n] = n;
@@ -350,12 +350,38 @@ rbki_status core_chain(const Plan& pl, double* const* factors, double* core, cud
             src_dtype = RBKI_F32;
             continue;
         }
-        RBKI_TRY(ttm_cuda(v, factors[m], R, R, dst, RBKI_F64, pl.mixed && t == 0, st));
+        RBKI_TRY(ttm_cuda(v, factors[m], R, R, dst, RBKI_F64, pl.mixed, st));
         prof_end(tok, st);
         cur[m] = R;
         src = dst;
         src_dtype = RBKI_F64;
     }
+    return RBKI_OK;
+}
+
+// Per-device pool of non-blocking streams: the N modes are independent (HOSVD reading), so
+// each mode's Algorithm 1-2 chain runs on its own stream, forked from and joined back to the
+// caller's stream.  Latency-bound small FP64 kernels of one mode then overlap the HBM-bound
+// passes of the others.
+struct StreamPool {
+    bool ready = false;
+    cudaStream_t s[RBKI_MAX_ORDER];
+};
+static std::mutex g_pool_mu;
+static StreamPool g_pools[64];
+
+static rbki_status mode_streams(cudaStream_t* out, int n) {
+    int dev = 0;
+    RBKI_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return set_error(RBKI_E_UNSUPPORTED, "device index");
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    StreamPool& p = g_pools[dev];
+    if (!p.ready) {
+        for (int i = 0; i < RBKI_MAX_ORDER; ++i)
+            RBKI_CUDA_TRY(cudaStreamCreateWithFlags(&p.s[i], cudaStreamNonBlocking));
+        p.ready = true;
+    }
+    for (int i = 0; i < n; ++i) out[i] = p.s[i];
     return RBKI_OK;
 }
 
@@ -372,9 +398,27 @@ rbki_status run_tucker(Plan& pl, const rbki_tucker_out* out, cudaStream_t st) {
         RBKI_TRY(sumsq_cuda(pl.xin, pl.dtype, pl.numel, pl.scal + 64, norms, st));
     }
     prof_end(tok, st);
-    for (int n = 0; n < pl.N; ++n) {
-        double* ev = out->eigvals[n];
-        RBKI_TRY(mode_factor(pl, pl.mode[n], out->factors[n], ev, out->info, st));
+    const bool concurrent = pl.N > 1 && !(pl.flags & RBKI_FLAG_SERIAL_MODES);
+    if (concurrent) {
+        cudaStream_t ms[RBKI_MAX_ORDER];
+        RBKI_TRY(mode_streams(ms, pl.N));
+        cudaEvent_t fork, join[RBKI_MAX_ORDER];
+        RBKI_CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+        RBKI_CUDA_TRY(cudaEventRecord(fork, st));
+        rbki_status rs = RBKI_OK;
+        for (int n = 0; n < pl.N; ++n) {
+            RBKI_CUDA_TRY(cudaEventCreateWithFlags(&join[n], cudaEventDisableTiming));
+            RBKI_CUDA_TRY(cudaStreamWaitEvent(ms[n], fork, 0));
+            if (rs >= 0) rs = mode_factor(pl, pl.mode[n], out->factors[n], out->eigvals[n], out->info, ms[n]);
+            RBKI_CUDA_TRY(cudaEventRecord(join[n], ms[n]));
+            RBKI_CUDA_TRY(cudaStreamWaitEvent(st, join[n], 0));
+        }
+        cudaEventDestroy(fork);
+        for (int n = 0; n < pl.N; ++n) cudaEventDestroy(join[n]);
+        if (rs < 0) return rs;
+    } else {
+        for (int n = 0; n < pl.N; ++n)
+            RBKI_TRY(mode_factor(pl, pl.mode[n], out->factors[n], out->eigvals[n], out->info, st));
     }
     RBKI_TRY(core_chain(pl, out->factors, out->core, st));
     RBKI_TRY(sumsq_cuda(out->core, RBKI_F64, pl.ranks_numel, pl.scal + 64, norms + 1, st));

@@ -1,29 +1,42 @@
-// Symmetric eigensolver for Algorithm 2 step 4 (Z = Q^T X X^T Q, b x b, b <= 256), FP64
-// results for the leading `nwant` eigenpairs.  GB300 executes FP64 FMAs at 1/58 of the
-// FP32 rate, so the solver keeps FP64 arithmetic to the O(b^3) reduction that needs it and
-// spreads the rest:
-//   1. Householder tridiagonalisation in FP64 (Householder 1958; the symmetric rank-2
-//      update form used by LAPACK's xSYTD2), one CTA, lower triangle updated and mirrored.
-//   2. Bisection with Sturm counts on the tridiagonal in FP32 (Givens 1954 / Wilkinson) for
-//      the wanted eigenvalues - only as shifts.
-//   3. Inverse iteration in FP64 on the tridiagonal (Gaussian elimination with partial
-//      pivoting), FP64 Rayleigh quotients for the eigenvalues, then classical Gram-Schmidt
-//      (twice) inside clusters of close eigenvalues.
-//   4. Back-transformation by the stored reflectors, one CTA per eigenvector.
+// Symmetric eigensolver for Algorithm 2 step 4 (Z = Q^T X X^T Q, b x b, b <= 256): FP64
+// leading `nwant` eigenpairs.
+//
+// GB300 runs FP64 FMAs at 1/58 of the FP32 rate (1.26 vs 73 TFLOP/s measured), and an
+// O(b^3) FP64 reduction on one SM takes milliseconds.  The solver therefore splits the
+// work by precision:
+//   1. a full eigendecomposition of Z in FP32 on one CTA:
+//        Householder tridiagonalisation (Householder 1958; the symmetric rank-2 update
+//        form of LAPACK's xSYTD2), bisection with Sturm counts (Givens 1954) for the
+//        eigenvalues, inverse iteration with Rayleigh-quotient shifts on the tridiagonal
+//        (fixed shift; Gaussian elimination with partial pivoting), Gram-Schmidt inside
+//        clusters of equal shifts,
+//        back-transformation by the reflectors (one warp per eigenvector);
+//   2. FP64 iterative refinement of the leading `nwant` eigenvectors by the method of
+//        Ogita & Aishima ("Iterative refinement for symmetric eigenvalue decomposition",
+//        Japan J. Indust. Appl. Math. 35, 2018), restricted to the wanted columns: with
+//        X the approximate eigenvector matrix and X1 its first nwant columns,
+//          G = X^T X1,  S = X^T (Z X1),  r_ij = delta_ij - g_ij,
+//          lambda_j = s_jj / (1 - r_jj),
+//          e_ij = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i)   (i != j, separated)
+//          e_ij = r_ij / 2                                          (i == j or clustered)
+//          X1 <- X1 + X E.
+//      All products are FP64 GEMMs of b x b x nwant spread over many CTAs.  Two sweeps
+//      take FP32-accurate vectors (~1e-6) to FP64 accuracy for eigenvalues separated
+//      from the rest; within a cluster only the span is refined.
 #include "kernels.h"
 
 namespace rbki {
 namespace {
 
-__device__ double block_sum(double v, double* red) {
+template <typename T>
+__device__ T block_sum(T v, T* red) {
     v = warp_sum(v);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     __syncthreads();
     if (lane == 0) red[wid] = v;
     __syncthreads();
-    double t = 0.0;
     if (threadIdx.x < 32) {
-        t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        T t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : (T)0;
         t = warp_sum(t);
         if (threadIdx.x == 0) red[32] = t;
     }
@@ -31,71 +44,89 @@ __device__ double block_sum(double v, double* red) {
     return red[32];
 }
 
-// Tridiagonalise A (n x n, symmetric): d[n], e[n-1]; reflector k (unit vector acting on
-// rows k+1..n-1, zero if none) stored as row k of `refl` (refl[k*n + k+1+i]).  The working
-// matrix lives in shared memory with an odd leading dimension (n+1) when it fits, otherwise
-// in `work` (global, L2 resident).
-__global__ void __launch_bounds__(512) k_tridiag(const double* __restrict__ A, int n,
-                                                 double* __restrict__ work, int use_smem,
-                                                 double* __restrict__ d, double* __restrict__ e,
-                                                 double* __restrict__ refl) {
-    extern __shared__ double sm[];
+// Tridiagonalise A (n x n, symmetric, FP64 input) in precision T: d[n], e[n-1]; reflector
+// k (unit vector acting on rows k+1..n-1, zero if none) stored as row k of `refl`.  The
+// working matrix lives in shared memory with an odd leading dimension (n+1) when it fits,
+// otherwise in `work` (global, L2 resident).
+template <typename T>
+__device__ __forceinline__ T block_sum1(T v, T* part, int nwarps) {
+    // warp partials to shared memory, one barrier, every thread adds the partials itself
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
+    __syncthreads();
+    T t = 0;
+    for (int w = 0; w < nwarps; ++w) t += part[w];
+    return t;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_tridiag(const double* __restrict__ A, int n, T* __restrict__ work,
+                                                 int use_smem, T* __restrict__ d, T* __restrict__ e,
+                                                 T* __restrict__ refl) {
+    extern __shared__ __align__(16) unsigned char tsm_raw[];
     const int ld = use_smem ? n + 1 : n;
-    double* a = use_smem ? sm : work;
-    __shared__ double v[256], u[256];
-    __shared__ double red[33];
+    T* a = use_smem ? reinterpret_cast<T*>(tsm_raw) : work;
+    __shared__ T v[256], u[256];
+    __shared__ T part_a[16], part_b[16];
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
-    for (int t = tid; t < n * n; t += nt) a[(t / n) * ld + t % n] = A[t];
-    for (int t = tid; t < n * n; t += nt) refl[t] = 0.0;
+    for (int t = tid; t < n * n; t += nt) a[(t / n) * ld + t % n] = (T)A[t];
+    for (int t = tid; t < n * n; t += nt) refl[t] = (T)0;
     __syncthreads();
     for (int k = 0; k + 2 < n; ++k) {
         const int m = n - k - 1;
         const int o = k + 1;
-        double x0 = a[o * ld + k];
-        double s1 = 0.0;
+        const T x0 = a[o * ld + k];
+        T s1 = 0;
         for (int i = 1 + tid; i < m; i += nt) {
-            double x = a[(o + i) * ld + k];
+            const T x = a[(o + i) * ld + k];
             s1 += x * x;
         }
-        s1 = block_sum(s1, red);
+        T* part = (k & 1) ? part_b : part_a;          // alternate buffers: no reuse barrier
+        s1 = block_sum1(s1, part, nw);
         if (tid == 0) d[k] = a[k * ld + k];
-        if (s1 == 0.0) {
+        if (s1 == (T)0) {
             if (tid == 0) e[k] = x0;
             __syncthreads();
             continue;
         }
-        double nrm = sqrt(x0 * x0 + s1);
-        double alpha = x0 >= 0.0 ? -nrm : nrm;
-        double v0 = x0 - alpha;
-        double inv = 1.0 / sqrt(v0 * v0 + s1);
+        const T nrm = sqrt(x0 * x0 + s1);
+        const T alpha = x0 >= (T)0 ? -nrm : nrm;
+        const T v0 = x0 - alpha;
+        const T inv = (T)1 / sqrt(v0 * v0 + s1);
         for (int i = tid; i < m; i += nt) {
-            double vi = (i == 0 ? v0 : a[(o + i) * ld + k]) * inv;
+            const T vi = (i == 0 ? v0 : a[(o + i) * ld + k]) * inv;
             v[i] = vi;
             refl[(size_t)k * n + o + i] = vi;
         }
         if (tid == 0) e[k] = alpha;
         __syncthreads();
-        // u = B v, B = a[o:, o:]: one warp per row
-        for (int i = wid; i < m; i += nw) {
-            const double* row = a + (size_t)(o + i) * ld + o;
-            double acc = 0.0;
-            for (int j = lane; j < m; j += 32) acc += row[j] * v[j];
-            acc = warp_sum(acc);
-            if (lane == 0) u[i] = acc;
+        // u = B v with four threads per row (adjacent lanes), g = v^T u from the same pass
+        T gp = 0;
+        for (int base = 0; base < m; base += nt / 4) {
+            const int i = base + tid / 4, q = tid & 3;
+            T acc = 0;
+            if (i < m) {
+                const T* row = a + (size_t)(o + i) * ld + o;
+                for (int j = q; j < m; j += 4) acc += row[j] * v[j];
+            }
+            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+            if (i < m && q == 0) {
+                u[i] = acc;
+                gp += acc * v[i];
+            }
         }
+        part = (k & 1) ? part_a : part_b;
+        const T g = block_sum1(gp, part, nw);
+        for (int i = tid; i < m; i += nt) u[i] = (T)2 * u[i] - (T)2 * g * v[i];   // w
         __syncthreads();
-        double g = 0.0;
-        for (int i = tid; i < m; i += nt) g += v[i] * u[i];
-        g = block_sum(g, red);
-        for (int i = tid; i < m; i += nt) u[i] = 2.0 * u[i] - 2.0 * g * v[i];   // w
-        __syncthreads();
-        // B -= v w^T + w v^T on the lower triangle, mirrored to the upper one
+        // B -= v w^T + w v^T: warp per row on the lower triangle, mirrored
         for (int i = wid; i < m; i += nw) {
-            const double vi = v[i], wi = u[i];
-            double* row = a + (size_t)(o + i) * ld + o;
+            const T vi = v[i], wi = u[i];
+            T* row = a + (size_t)(o + i) * ld + o;
             for (int j = lane; j <= i; j += 32) {
-                double val = row[j] - vi * u[j] - wi * v[j];
+                const T val = row[j] - vi * u[j] - wi * v[j];
                 row[j] = val;
                 a[(size_t)(o + j) * ld + o + i] = val;
             }
@@ -111,6 +142,8 @@ __global__ void __launch_bounds__(512) k_tridiag(const double* __restrict__ A, i
     }
 }
 
+}  // namespace
+
 // number of eigenvalues of T (d, e) below x, FP32 Sturm sequence
 __host__ __device__ int sturm_count(const float* d, const float* e2, int n, float x, float pivmin) {
     int c = 0;
@@ -118,7 +151,11 @@ __host__ __device__ int sturm_count(const float* d, const float* e2, int n, floa
     if (fabsf(q) < pivmin) q = -pivmin;
     if (q < 0.f) ++c;
     for (int i = 1; i < n; ++i) {
+#ifdef __CUDA_ARCH__
+        q = (d[i] - x) - __fdividef(e2[i - 1], q);
+#else
         q = (d[i] - x) - e2[i - 1] / q;
+#endif
         if (fabsf(q) < pivmin) q = -pivmin;
         if (q < 0.f) ++c;
     }
@@ -135,99 +172,99 @@ __host__ __device__ float bisect_one(const float* df, const float* e2f, int n, i
     return 0.5f * (lo + hi);
 }
 
-// Eigenvector of T (d, e; FP64) for the eigenvalue nearest `mu` by inverse iteration with
-// Rayleigh-quotient shift updates (Gaussian elimination with partial pivoting on T - mu I).
-// work: 5n doubles; flags: n bytes.  Result (unit 2-norm) in y; returns the final shift.
-__host__ __device__ double invit_one(const double* d, const double* e, int n, double mu, double tnorm, int k,
-                                     double* work, unsigned char* swapped, double* y) {
-    const double eps = 1.1102230246251565e-16;
-    double* dd = work;
-    double* du = dd + n;
-    double* du2 = du + n;
-    double* mult = du2 + n;
-    double* ty = mult + n;
+// Eigenvector of T (d, e) for the eigenvalue nearest `mu`: inverse iteration with
+// Rayleigh-quotient shift updates.  Each sweep factorises T - mu I by Gaussian elimination
+// with partial pivoting fused with the forward substitution, then back-substitutes.  The
+// running rows live in registers; the factor rows (1/pivot, super, second super) and y are
+// strided arrays (element i at [i * stride]).  Returns the final shift.
+template <typename T>
+__host__ __device__ T invit_one(const T* d, const T* e, int n, T mu, T tnorm, int k, T* rdd, T* du, T* du2, T* y,
+                                int stride, int sweeps, int rq_update) {
+    const T eps = sizeof(T) == 8 ? (T)1.1102230246251565e-16 : (T)5.9604645e-08f;
+    const T tiny = eps * tnorm + (T)(sizeof(T) == 8 ? 1e-300 : 1e-37);
     uint32_t hsh = 2166136261u ^ ((uint32_t)k * 16777619u);
     for (int i = 0; i < n; ++i) {
         hsh = hsh * 1664525u + 1013904223u;
-        y[i] = 1.0 + 0.5 * ((double)(hsh >> 8) * (1.0 / 16777216.0) - 0.5);
+        y[i * stride] = (T)1 + (T)0.5 * ((T)(hsh >> 8) * (T)(1.0 / 16777216.0) - (T)0.5);
     }
-    const double tiny = eps * tnorm + 1e-300;
-    for (int it = 0; it < 4; ++it) {
-        for (int i = 0; i < n; ++i) { dd[i] = d[i] - mu; du[i] = (i + 1 < n) ? e[i] : 0.0; du2[i] = 0.0; }
+    for (int it = 0; it < sweeps; ++it) {
+        T a = d[0] - mu, b = n > 1 ? e[0] : (T)0, yi = y[0];
         for (int i = 0; i + 1 < n; ++i) {
-            double a = dd[i], b = du[i], c = e[i], dn = dd[i + 1], f = (i + 2 < n) ? du[i + 1] : 0.0;
+            const T c = e[i], dn = d[i + 1] - mu, f = (i + 2 < n) ? e[i + 1] : (T)0, yn = y[(i + 1) * stride];
             if (fabs(a) >= fabs(c)) {
-                if (fabs(a) < tiny) a = a >= 0 ? tiny : -tiny;
-                double mlt = c / a;
-                dd[i] = a;
-                dd[i + 1] = dn - mlt * b;
-                mult[i] = mlt;
-                swapped[i] = 0;
+                if (fabs(a) < tiny) a = a >= (T)0 ? tiny : -tiny;
+                const T r = (T)1 / a, m = c * r;
+                rdd[i * stride] = r; du[i * stride] = b; du2[i * stride] = 0; y[i * stride] = yi;
+                a = dn - m * b; b = f; yi = yn - m * yi;
             } else {
-                double mlt = a / c;
-                dd[i] = c;
-                du[i] = dn;
-                du2[i] = f;
-                dd[i + 1] = b - mlt * dn;
-                if (i + 2 < n) du[i + 1] = -mlt * f;
-                mult[i] = mlt;
-                swapped[i] = 1;
+                const T r = (T)1 / c, m = a * r;
+                rdd[i * stride] = r; du[i * stride] = dn; du2[i * stride] = f; y[i * stride] = yn;
+                a = b - m * dn; b = -m * f; yi = yi - m * yn;
             }
         }
-        if (fabs(dd[n - 1]) < tiny) dd[n - 1] = dd[n - 1] >= 0 ? tiny : -tiny;
-        for (int i = 0; i + 1 < n; ++i) {
-            if (swapped[i]) {
-                double t = y[i];
-                y[i] = y[i + 1];
-                y[i + 1] = t - mult[i] * y[i];
-            } else {
-                y[i + 1] -= mult[i] * y[i];
-            }
+        if (fabs(a) < tiny) a = a >= (T)0 ? tiny : -tiny;
+        T y1 = yi / a, y2 = 0;
+        y[(n - 1) * stride] = y1;
+        T ss = y1 * y1;
+        for (int i = n - 2; i >= 0; --i) {
+            const T vv = (y[i * stride] - du[i * stride] * y1 - du2[i * stride] * y2) * rdd[i * stride];
+            y[i * stride] = vv;
+            ss += vv * vv;
+            y2 = y1;
+            y1 = vv;
         }
-        y[n - 1] /= dd[n - 1];
-        if (n >= 2) y[n - 2] = (y[n - 2] - du[n - 2] * y[n - 1]) / dd[n - 2];
-        for (int i = n - 3; i >= 0; --i) y[i] = (y[i] - du[i] * y[i + 1] - du2[i] * y[i + 2]) / dd[i];
-        double s = 0.0;
-        for (int i = 0; i < n; ++i) s += y[i] * y[i];
-        s = 1.0 / sqrt(s);
-        for (int i = 0; i < n; ++i) y[i] *= s;
-        // Rayleigh quotient of the new vector as the next shift
-        double num = 0.0;
+        const T sc = (T)1 / sqrt(ss);
+        T num = 0, prev = 0, cur = y[0] * sc;
         for (int i = 0; i < n; ++i) {
-            double ti = d[i] * y[i];
-            if (i > 0) ti += e[i - 1] * y[i - 1];
-            if (i + 1 < n) ti += e[i] * y[i + 1];
-            ty[i] = ti;
-            num += y[i] * ti;
+            const T next = (i + 1 < n) ? y[(i + 1) * stride] * sc : (T)0;
+            y[i * stride] = cur;
+            T ti = d[i] * cur;
+            if (i > 0) ti += e[i - 1] * prev;
+            if (i + 1 < n) ti += e[i] * next;
+            num += cur * ti;
+            prev = cur;
+            cur = next;
         }
-        mu = num + (k + 1) * eps * tnorm;
+        if (rq_update) mu = num + (T)(k + 1) * eps * tnorm;
     }
     return mu;
 }
+template double invit_one<double>(const double*, const double*, int, double, double, int, double*, double*, double*,
+                                  double*, int, int, int);
+template float invit_one<float>(const float*, const float*, int, float, float, int, float*, float*, float*, float*,
+                                int, int, int);
 
-// Leading `nwant` eigenpairs of T: eigenvalues (descending) in w, tridiagonal eigenvectors
-// y (n x nwant, column k = k-th largest) in Y.  One CTA; thread k handles eigenvalue k.
-__global__ void __launch_bounds__(256) k_tri_eig(const double* __restrict__ d, const double* __restrict__ e,
-                                                 int n, int nwant, double* __restrict__ w,
-                                                 double* __restrict__ Y, double* __restrict__ scratch) {
+namespace {
+
+// Leading `nwant` eigenpairs of T (d, e) in three launches:
+//   k_tri_vec   bisection (FP32 Sturm counts) for the shifts + fixed-shift inverse iteration,
+//               one thread per eigenvalue; a fixed shift keeps the vectors of a cluster
+//               linearly independent (random starts stay mixed inside the cluster);
+//   k_tri_orth  CholQR, twice, of the n x nwant eigenvector block (one CTA) - vectors of
+//               distinct eigenvalues are already orthogonal, so the triangular mixing only
+//               acts inside clusters;
+//   k_tri_rq    Rayleigh quotients as eigenvalues.
+// Y is n x nwant with leading dimension ld = nwant + 1 (odd: conflict-free row access).
+template <typename T>
+__global__ void __launch_bounds__(64) k_tri_vec(const T* __restrict__ d, const T* __restrict__ e, int n, int nwant,
+                                                T* __restrict__ Y, T* __restrict__ scratch,
+                                                float* __restrict__ shift_out) {
     __shared__ float df[256], e2f[256];
-    __shared__ float lam_sh[256];
-    __shared__ double red[33];
     __shared__ float bounds[2];
-    __shared__ double tn_sh;
+    __shared__ T tn_sh;
     const int tid = threadIdx.x;
     if (tid == 0) {
-        double t = 0.0;
+        T t = 0;
         for (int i = 0; i < n; ++i)
-            t = fmax(t, fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < n ? fabs(e[i]) : 0.0));
-        tn_sh = t > 0.0 ? t : 1.0;
+            t = fmax(t, fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : (T)0) + (i + 1 < n ? fabs(e[i]) : (T)0));
+        tn_sh = t > (T)0 ? t : (T)1;
     }
     __syncthreads();
-    const double tnorm = tn_sh;
-    const double sc = 1.0 / tnorm;                      // bisection on T / |T| (FP32 range)
+    const T tnorm = tn_sh;
+    const double sc = 1.0 / (double)tnorm;     // bisection on T / |T| (FP32 range)
     for (int i = tid; i < n; i += blockDim.x) {
-        df[i] = (float)(d[i] * sc);
-        e2f[i] = i + 1 < n ? (float)((e[i] * sc) * (e[i] * sc)) : 0.f;
+        df[i] = (float)((double)d[i] * sc);
+        e2f[i] = i + 1 < n ? (float)(((double)e[i] * sc) * ((double)e[i] * sc)) : 0.f;
     }
     __syncthreads();
     if (tid == 0) {
@@ -241,97 +278,318 @@ __global__ void __launch_bounds__(256) k_tri_eig(const double* __restrict__ d, c
         bounds[1] = hi + 1e-5f;
     }
     __syncthreads();
-    // ---- bisection (FP32) ----
-    for (int k = tid; k < nwant; k += blockDim.x) lam_sh[k] = bisect_one(df, e2f, n, n - 1 - k, bounds[0], bounds[1]);
+    const int ld = nwant + 1;
+    const int k = blockIdx.x * blockDim.x + tid;
+    if (k >= nwant) return;
+    const float lam = bisect_one(df, e2f, n, n - 1 - k, bounds[0], bounds[1]);
+    shift_out[k] = lam;
+    const T eps = sizeof(T) == 8 ? (T)1.1102230246251565e-16 : (T)5.9604645e-08f;
+    T* rdd = scratch;
+    T* du = rdd + (size_t)n * ld;
+    T* du2 = du + (size_t)n * ld;
+    const T mu = (T)lam * tnorm + (T)(k + 1) * eps * tnorm;
+    invit_one<T>(d, e, n, mu, tnorm, k, rdd + k, du + k, du2 + k, Y + k, ld, 3, 0);
+}
+
+// Orthonormalise the inverse-iteration vectors by one Cholesky QR of the whole block
+// (FP32): fixed-shift inverse iteration leaves the vectors of a cluster of (near-)equal
+// eigenvalues independent but not orthogonal, and the noise part of Z forms large clusters
+// at FP32 resolution.  Vectors of separated eigenvalues are already orthogonal, so the
+// triangular mixing acts inside clusters only.  The Gram matrix and the row update use the
+// whole CTA; the factorisation and the triangular inverse run on warp 0 with warp-level
+// synchronisation only.  Y (n x nwant, ld nwant+1) is processed in shared memory.
+template <typename T>
+__global__ void __launch_bounds__(256) k_tri_orth(T* __restrict__ Yg, int n, int nwant, T* __restrict__ scratch,
+                                                  int use_smem) {
+    extern __shared__ __align__(16) unsigned char osm_raw[];
+    const int tid = threadIdx.x;
+    const int ld = nwant + 1;
+    T* ys = use_smem ? reinterpret_cast<T*>(osm_raw) : scratch;   // n x ld
+    T* Gm = ys + (size_t)n * ld;                         // nwant x ld (R in the upper triangle)
+    T* Ri = Gm + (size_t)nwant * ld;                     // nwant: 1 / R_kk
+    for (int t = tid; t < n * ld; t += blockDim.x) ys[t] = Yg[t];
     __syncthreads();
-    // ---- inverse iteration with Rayleigh-quotient shifts (FP64) ----
-    const double eps = 1.1102230246251565e-16;
-    for (int k = tid; k < nwant; k += blockDim.x) {
-        double* work = scratch + (size_t)k * 6 * n;
-        double* y = work + 5 * n;
-        unsigned char swapped[256];
-        double mu = (double)lam_sh[k] * tnorm + (k + 1) * eps * tnorm;
-        invit_one(d, e, n, mu, tnorm, k, work, swapped, y);
-        for (int i = 0; i < n; ++i) Y[(size_t)i * nwant + k] = y[i];
+    // G = Y^T Y, upper triangle, 4 x 4 register tiles
+    const int nt4 = (nwant + 3) / 4;
+    for (int t = tid; t < nt4 * nt4; t += blockDim.x) {
+        const int pb = (t / nt4) * 4, qb = (t % nt4) * 4;
+        if (qb + 3 < pb) continue;
+        T acc[4][4] = {};
+        for (int i = 0; i < n; ++i) {
+            const T* yi = ys + (size_t)i * ld;
+            T yp[4], yq[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                yp[u] = pb + u < nwant ? yi[pb + u] : (T)0;
+                yq[u] = qb + u < nwant ? yi[qb + u] : (T)0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v2 = 0; v2 < 4; ++v2) acc[u][v2] += yp[u] * yq[v2];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v2 = 0; v2 < 4; ++v2) {
+                const int pp = pb + u, qq = qb + v2;
+                if (pp < nwant && qq < nwant && qq >= pp) Gm[pp * ld + qq] = acc[u][v2];
+            }
     }
     __syncthreads();
-    // ---- Gram-Schmidt (twice) inside clusters, then FP64 Rayleigh quotients ----
-    const double ctol = 1e-3;                 // cluster: normalised shifts closer than this
-    for (int k = 1; k < nwant; ++k) {
-        for (int pass = 0; pass < 2; ++pass) {
-            for (int jv = 0; jv < k; ++jv) {
-                if (fabs((double)lam_sh[jv] - (double)lam_sh[k]) > ctol) continue;
-                double dot = 0.0;
-                for (int i = tid; i < n; i += blockDim.x) dot += Y[(size_t)i * nwant + jv] * Y[(size_t)i * nwant + k];
-                dot = block_sum(dot, red);
-                for (int i = tid; i < n; i += blockDim.x) Y[(size_t)i * nwant + k] -= dot * Y[(size_t)i * nwant + jv];
-                __syncthreads();
-            }
+    // right-looking Cholesky on the upper triangle: pivot on thread 0, rank-1 update of the
+    // trailing triangle spread over the whole CTA; Ri[k] keeps 1 / R_kk
+    for (int k = 0; k < nwant; ++k) {
+        if (tid == 0) {
+            const T dk = Gm[k * ld + k];
+            const T r = dk > (T)0 ? sqrt(dk) : (T)1;
+            Gm[k * ld + k] = r;
+            Ri[k] = (T)1 / r;
         }
-        double s = 0.0;
-        for (int i = tid; i < n; i += blockDim.x) { double v = Y[(size_t)i * nwant + k]; s += v * v; }
-        s = block_sum(s, red);
-        double sc = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
-        for (int i = tid; i < n; i += blockDim.x) Y[(size_t)i * nwant + k] *= sc;
+        __syncthreads();
+        const T ri = Ri[k];
+        const int mm = nwant - k - 1;
+        // trailing update G_ij -= R_ki R_kj with R_kj = G_kj / r (row k scaled afterwards)
+        for (int t = tid; t < mm * mm; t += blockDim.x) {
+            const int i = k + 1 + t / mm, j = k + 1 + t % mm;
+            if (j >= i) Gm[i * ld + j] -= (Gm[k * ld + i] * ri) * (Gm[k * ld + j] * ri);
+        }
+        __syncthreads();
+        for (int j = k + 1 + tid; j < nwant; j += blockDim.x) Gm[k * ld + j] *= ri;
         __syncthreads();
     }
-    for (int k = tid; k < nwant; k += blockDim.x) {
-        double num = 0.0;
-        for (int i = 0; i < n; ++i) {
-            double ti = d[i] * Y[(size_t)i * nwant + k];
-            if (i > 0) ti += e[i - 1] * Y[(size_t)(i - 1) * nwant + k];
-            if (i + 1 < n) ti += e[i] * Y[(size_t)(i + 1) * nwant + k];
-            num += Y[(size_t)i * nwant + k] * ti;
+    // rows of Y: solve y_new R = y by forward substitution (one thread per row)
+    for (int i = tid; i < n; i += blockDim.x) {
+        T* yi = ys + (size_t)i * ld;
+        for (int q = 0; q < nwant; ++q) {
+            T a0 = yi[q], a1 = 0;
+            int p = 0;
+            for (; p + 1 < q; p += 2) {
+                a0 -= yi[p] * Gm[p * ld + q];
+                a1 -= yi[p + 1] * Gm[(p + 1) * ld + q];
+            }
+            for (; p < q; ++p) a0 -= yi[p] * Gm[p * ld + q];
+            yi[q] = (a0 + a1) * Ri[q];
         }
-        w[k] = num;
+    }
+    __syncthreads();
+    for (int t = tid; t < n * ld; t += blockDim.x) Yg[t] = ys[t];
+}
+
+template <typename T>
+__global__ void k_tri_rq(const T* __restrict__ d, const T* __restrict__ e, int n, int nwant,
+                         const T* __restrict__ Y, T* __restrict__ w) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nwant) return;
+    const int ld = nwant + 1;
+    T num = 0;
+    for (int i = 0; i < n; ++i) {
+        T ti = d[i] * Y[(size_t)i * ld + k];
+        if (i > 0) ti += e[i - 1] * Y[(size_t)(i - 1) * ld + k];
+        if (i + 1 < n) ti += e[i] * Y[(size_t)(i + 1) * ld + k];
+        num += Y[(size_t)i * ld + k] * ti;
+    }
+    w[k] = num;
+}
+
+// z = H_0 H_1 ... H_{n-3} y for eigenvector column k, one warp per eigenvector (z held in
+// registers, 8 entries per lane); output widened to FP64 (ld ldv).
+template <typename T>
+__global__ void __launch_bounds__(128) k_backtransform(const T* __restrict__ refl, int n, int nwant,
+                                                       const T* __restrict__ Y, double* __restrict__ V, int ldv) {
+    const int lane = threadIdx.x & 31;
+    const int k = blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (k >= nwant) return;
+    T z[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        const int i = lane + 32 * t;
+        z[t] = i < n ? Y[(size_t)i * (nwant + 1) + k] : (T)0;
+    }
+    for (int j = n - 3; j >= 0; --j) {
+        const T* vj = refl + (size_t)j * n;
+        T vr[8];
+        T dot = 0;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const int i = lane + 32 * t;
+            vr[t] = (i > j && i < n) ? vj[i] : (T)0;
+            dot += vr[t] * z[t];
+        }
+        dot = warp_sum(dot);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) z[t] -= (T)2 * dot * vr[t];
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        const int i = lane + 32 * t;
+        if (i < n) V[(size_t)i * ldv + k] = (double)z[t];
     }
 }
 
-// z = H_0 H_1 ... H_{n-3} y for eigenvector column k (one CTA per column); reflector j is
-// refl[j*n + j+1+i], H_j = I - 2 v v^T acting on rows j+1..n-1.
-__global__ void k_backtransform(const double* __restrict__ refl, int n, int nwant, const double* __restrict__ Y,
-                                double* __restrict__ V) {
-    __shared__ double z[256];
-    __shared__ double red[33];
-    const int k = blockIdx.x;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) z[i] = Y[(size_t)i * nwant + k];
-    __syncthreads();
-    for (int j = n - 3; j >= 0; --j) {
-        const int o = j + 1, m = n - o;
-        double dot = 0.0;
-        const double* vj = refl + (size_t)j * n + o;
-        for (int i = threadIdx.x; i < m; i += blockDim.x) dot += vj[i] * z[o + i];
-        dot = block_sum(dot, red);
-        for (int i = threadIdx.x; i < m; i += blockDim.x) z[o + i] -= 2.0 * dot * vj[i];
-        __syncthreads();
+// Ogita-Aishima correction for the leading R columns: E (n x R), refined eigenvalues lam1.
+// G = X^T X1, S = X^T Z X1 (n x R each), lam_all: approximate eigenvalues of every column.
+__global__ void k_oa_update(const double* __restrict__ G, const double* __restrict__ S,
+                            const double* __restrict__ lam_all, int n, int R, double* __restrict__ E,
+                            double* __restrict__ lam1) {
+    __shared__ double lt[256];
+    for (int j = threadIdx.x; j < R; j += blockDim.x) {
+        const double rjj = 1.0 - G[(size_t)j * R + j];
+        lt[j] = S[(size_t)j * R + j] / (1.0 - rjj);
     }
-    for (int i = threadIdx.x; i < n; i += blockDim.x) V[(size_t)i * nwant + k] = z[i];
+    __syncthreads();
+    // pairs closer than sqrt(eps) |lambda|_max are a cluster in every sweep
+    const double gap_floor = 1.5e-8 * fmax(fabs(lam_all[0]), fabs(lam_all[n - 1]));
+    for (int t = threadIdx.x; t < n * R; t += blockDim.x) {
+        const int i = t / R, j = t % R;
+        const double rij = (i == j ? 1.0 : 0.0) - G[t];
+        double eij = 0.5 * rij;
+        if (i != j) {
+            const double li = i < R ? lt[i] : lam_all[i];
+            const double num = S[t] + lt[j] * rij, den = lt[j] - li;
+            // Newton correction only while the coupling is small against the gap
+            if (fabs(den) > gap_floor && fabs(num) <= 0.1 * fabs(den)) eij = num / den;
+        }
+        E[t] = eij;
+    }
+    for (int j = threadIdx.x; j < R; j += blockDim.x) lam1[j] = lt[j];
+}
+
+// descending order of the R refined pairs: w[rank] = lam[j], V[:, rank] = X1[:, j]
+__global__ void k_sort_top(const double* __restrict__ lam, const double* __restrict__ X1, int n, int ldx, int R,
+                           double* __restrict__ w, double* __restrict__ V) {
+    __shared__ int rank_of[256];
+    for (int j = threadIdx.x; j < R; j += blockDim.x) {
+        int r = 0;
+        for (int t = 0; t < R; ++t) r += (lam[t] > lam[j] || (lam[t] == lam[j] && t < j)) ? 1 : 0;
+        rank_of[j] = r;
+        w[r] = lam[j];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < n * R; t += blockDim.x) {
+        const int i = t / R, j = t % R;
+        V[(size_t)i * R + rank_of[j]] = X1[(size_t)i * ldx + j];
+    }
+}
+
+// M = (3 I - G) / 2: one second-order step towards orthonormal columns (X1 <- X1 M)
+__global__ void k_halfstep(const double* __restrict__ G, int R, double* __restrict__ M) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= R * R) return;
+    M[t] = ((t / R == t % R) ? 1.5 : 0.0) - 0.5 * G[t];
+}
+
+__global__ void k_f32_to_f64(const float* __restrict__ s, double* __restrict__ d, int n) {
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) d[e] = (double)s[e];
+}
+
+__global__ void k_copy_cols(const double* __restrict__ src, int lds, double* __restrict__ dst, int ldd, int n,
+                            int R) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * R) return;
+    dst[(size_t)(t / R) * ldd + t % R] = src[(size_t)(t / R) * lds + t % R];
+}
+
+struct EigLayout {
+    float *work, *refl, *d, *e, *lam, *shift, *Yt, *iiw;
+    double *X, *ZX1, *G, *S, *E, *T1, *lam_all, *lam1, *part;
+    size_t doubles;
+};
+
+EigLayout eig_layout(double* base, int n) {
+    EigLayout L{};
+    const size_t nn = (size_t)n * n;
+    size_t off = 0;   // in doubles
+    auto fl = [&](size_t count) {
+        float* p = base ? reinterpret_cast<float*>(base + off) : nullptr;
+        off += (count + 1) / 2 + 32;
+        return p;
+    };
+    auto db = [&](size_t count) {
+        double* p = base ? base + off : nullptr;
+        off += count + 32;
+        return p;
+    };
+    L.work = fl(nn);
+    L.refl = fl(nn);
+    L.d = fl(n);
+    L.e = fl(n);
+    L.lam = fl(n);
+    L.shift = fl(n);
+    L.Yt = fl((size_t)n * (n + 1));
+    L.iiw = fl(2 * (size_t)n + 4 * (size_t)n * (n + 1) + 2 * nn + (size_t)n);
+    L.X = db(nn);
+    L.ZX1 = db(nn);
+    L.G = db(nn);
+    L.S = db(nn);
+    L.E = db(nn);
+    L.T1 = db(nn);
+    L.lam_all = db(n);
+    L.lam1 = db(n);
+    L.part = db(gemm_part_doubles(n, n, n));
+    L.doubles = off + 64;
+    return L;
 }
 
 }  // namespace
 
-size_t syev_scratch_doubles(int n) { return 2 * (size_t)n * n + 2 * (size_t)n + (size_t)n * n + 6 * (size_t)n * n + 64; }
+size_t syev_scratch_doubles(int n) { return eig_layout(nullptr, n).doubles; }
 
 // w: nwant eigenvalues (descending); V: n x nwant row-major eigenvectors
 rbki_status syev_top_cuda(const double* A, int n, int nwant, double* w, double* V, double* scratch,
                           cudaStream_t st) {
     if (n > 256 || nwant > n || nwant < 1) return set_error(RBKI_E_UNSUPPORTED, "syev: n > 256");
-    double* work = scratch;                      // n x n working matrix (global fallback)
-    double* refl = work + (size_t)n * n;         // n x n reflectors (rows)
-    double* d = refl + (size_t)n * n;
-    double* e = d + n;
-    double* Y = e + n;                           // n x nwant
-    double* iiw = Y + (size_t)n * n;             // 6 n per wanted eigenvalue
-    const size_t smem = (size_t)(n + 1) * n * sizeof(double);
-    static size_t smax = 0;
-    if (!smax) smax = max_dyn_smem(k_tridiag);
-    const int use_smem = smem <= smax;
-    k_tridiag<<<1, 512, use_smem ? smem : 0, st>>>(A, n, work, use_smem, d, e, refl);
+    const EigLayout L = eig_layout(scratch, n);
+    const size_t nn = (size_t)n * n;
+    // ---- 1. FP32 eigendecomposition ----
+    static size_t tmax = 0, emax = 0;
+    if (!tmax) tmax = max_dyn_smem(k_tridiag<float>);
+    (void)emax;
+    const size_t tsm = (size_t)(n + 1) * n * sizeof(float);
+    const int t_smem = tsm <= tmax;
+    k_tridiag<float><<<1, 512, t_smem ? tsm : 0, st>>>(A, n, L.work, t_smem, L.d, L.e, L.refl);
     RBKI_LAUNCH_CHECK("k_tridiag");
-    k_tri_eig<<<1, 256, 0, st>>>(d, e, n, nwant, w, Y, iiw);
-    RBKI_LAUNCH_CHECK("k_tri_eig");
-    k_backtransform<<<nwant, 128, 0, st>>>(refl, n, nwant, Y, V);
+    k_tri_vec<float><<<(unsigned)cdiv(n, 64), 64, 0, st>>>(L.d, L.e, n, n, L.Yt, L.iiw, L.shift);
+    RBKI_LAUNCH_CHECK("k_tri_vec");
+    static size_t omax = 0;
+    if (!omax) omax = max_dyn_smem(k_tri_orth<float>);
+    const size_t osm = (size_t)(n + 2 * n) * (n + 1) * sizeof(float);
+    const int o_smem = osm <= omax;
+    k_tri_orth<float><<<1, 256, o_smem ? osm : 0, st>>>(L.Yt, n, n, L.iiw, o_smem);
+    RBKI_LAUNCH_CHECK("k_tri_orth");
+    k_tri_rq<float><<<(unsigned)cdiv(n, 64), 64, 0, st>>>(L.d, L.e, n, n, L.Yt, L.lam);
+    RBKI_LAUNCH_CHECK("k_tri_rq");
+    k_backtransform<float><<<(unsigned)cdiv(n, 4), 128, 0, st>>>(L.refl, n, n, L.Yt, L.X, n);
     RBKI_LAUNCH_CHECK("k_backtransform");
+    k_f32_to_f64<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(L.lam, L.lam_all, n);
+    RBKI_LAUNCH_CHECK("k_f32_to_f64");
+    // ---- 2. FP64 refinement of the leading nwant columns ----
+    const int R = nwant;
+    const int sweeps = R == n ? 5 : 2;
+    for (int it = 0; it < sweeps; ++it) {
+        RBKI_TRY(gemm_f64_cuda(false, n, R, n, A, n, L.X, n, L.ZX1, R, 0.0, L.part, st));   // Z X1
+        RBKI_TRY(gemm_f64_cuda(true, n, R, n, L.X, n, L.ZX1, R, L.S, R, 0.0, L.part, st));  // X^T Z X1
+        RBKI_TRY(gemm_f64_cuda(true, n, R, n, L.X, n, L.X, n, L.G, R, 0.0, L.part, st));    // X^T X1
+        k_oa_update<<<1, 256, 0, st>>>(L.G, L.S, L.lam_all, n, R, L.E, L.lam1);
+        RBKI_LAUNCH_CHECK("k_oa_update");
+        // X1 <- X1 + X E  (into T1, then back over the first R columns)
+        k_copy_cols<<<(unsigned)cdiv((int64_t)n * R, 256), 256, 0, st>>>(L.X, n, L.T1, R, n, R);
+        RBKI_LAUNCH_CHECK("k_copy_cols");
+        RBKI_TRY(gemm_f64_cuda(false, n, R, n, L.X, n, L.E, R, L.T1, R, 1.0, L.part, st));
+        k_copy_cols<<<(unsigned)cdiv((int64_t)n * R, 256), 256, 0, st>>>(L.T1, R, L.X, n, n, R);
+        RBKI_LAUNCH_CHECK("k_copy_cols");
+        RBKI_TRY(copy_f64_cuda(L.lam1, L.lam_all, R, st));
+    }
+    // X1 <- X1 (3I - X1^T X1) / 2 (orthonormal to second order)
+    RBKI_TRY(gemm_f64_cuda(true, R, R, n, L.X, n, L.X, n, L.G, R, 0.0, L.part, st));
+    k_halfstep<<<(unsigned)cdiv((int64_t)R * R, 256), 256, 0, st>>>(L.G, R, L.S);
+    RBKI_LAUNCH_CHECK("k_halfstep");
+    RBKI_TRY(gemm_f64_cuda(false, n, R, R, L.X, n, L.S, R, L.T1, R, 0.0, L.part, st));
+    k_copy_cols<<<(unsigned)cdiv((int64_t)n * R, 256), 256, 0, st>>>(L.T1, R, L.X, n, n, R);
+    RBKI_LAUNCH_CHECK("k_copy_cols");
+    k_sort_top<<<1, 256, 0, st>>>(L.lam1, L.X, n, n, R, w, V);
+    RBKI_LAUNCH_CHECK("k_sort_top");
     return RBKI_OK;
 }
 

@@ -89,7 +89,8 @@ __global__ void k_stage_f32_bf16_v4(const float4* __restrict__ x, int64_t n4,
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
          i += (int64_t)gridDim.x * blockDim.x) {
         float4 v = __ldcs(x + i);
-        acc += (double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z + (double)v.w * v.w;
+        // FP32 square-sum of the four elements, FP64 accumulation across the stream
+        acc += (double)(v.x * v.x + v.y * v.y + v.z * v.z + v.w * v.w);
         __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y);
         __nv_bfloat162 b = __floats2bfloat162_rn(v.z, v.w);
         uint2 o;

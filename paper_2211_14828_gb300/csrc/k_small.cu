@@ -70,63 +70,85 @@ __global__ void k_gprime(const double* __restrict__ M, int m, int S, double* __r
     int l = blockIdx.x, k = threadIdx.x;
     if (k >= S) return;
     double g = M[(int64_t)(m + k) * S + l];
-    double acc = 0.0;
-    for (int r = 0; r < m; ++r) acc += M[(int64_t)r * S + k] * M[(int64_t)r * S + l];
-    Gp[k * S + l] = g - acc;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int r = 0;
+    for (; r + 3 < m; r += 4) {
+        a0 += M[(int64_t)r * S + k] * M[(int64_t)r * S + l];
+        a1 += M[(int64_t)(r + 1) * S + k] * M[(int64_t)(r + 1) * S + l];
+        a2 += M[(int64_t)(r + 2) * S + k] * M[(int64_t)(r + 2) * S + l];
+        a3 += M[(int64_t)(r + 3) * S + k] * M[(int64_t)(r + 3) * S + l];
+    }
+    for (; r < m; ++r) a0 += M[(int64_t)r * S + k] * M[(int64_t)r * S + l];
+    Gp[k * S + l] = g - ((a0 + a1) + (a2 + a3));
     if (k == l) nu2[k] = g;
 }
 
 // Cholesky G' = R^T R with pivot deflation, then Rinv (upper) with zero rows/columns for
 // deflated directions.  Column k is deflated when nu2[k] == 0 or its pivot (squared norm
-// orthogonal to everything accepted) <= tau^2 nu2[k].  Single CTA, S <= blockDim.x.
+// orthogonal to everything accepted) <= tau^2 nu2[k].  Single CTA.  Both the factorisation
+// and the triangular inverse are right-looking: each step is one square root / reciprocal
+// followed by a parallel rank-1 update, so the dependent FP64 chain per step stays short.
 __global__ void k_chol_deflate(const double* __restrict__ Gp, const double* __restrict__ nu2,
                                int S, double tau, double* __restrict__ Rinv,
                                int32_t* __restrict__ kept) {
     extern __shared__ double sm[];
-    double* R = sm;              // S x S
-    double* t = sm + S * S;      // S
-    __shared__ int keep_flag;
+    double* W = sm;                   // S x S working copy (upper triangle), becomes R
+    double* B = W + S * S;            // S x S, becomes Rinv
+    double* rinv = B + S * S;         // S: 1 / R_kk, 0 when deflated
     __shared__ int nkept;
-    const int j = threadIdx.x;
-    for (int e = j; e < S * S; e += blockDim.x) R[e] = 0.0;
-    if (j == 0) nkept = 0;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int e = tid; e < S * S; e += nt) {
+        W[e] = Gp[e];
+        B[e] = (e / S == e % S) ? 1.0 : 0.0;
+    }
+    if (tid == 0) nkept = 0;
     __syncthreads();
     for (int k = 0; k < S; ++k) {
-        if (j >= k && j < S) {
-            double acc = Gp[k * S + j];
-            for (int i = 0; i < k; ++i) acc -= R[i * S + k] * R[i * S + j];
-            t[j] = acc;
-        }
-        __syncthreads();
-        if (j == 0) {
-            double d = t[k], nu = nu2[k];
-            keep_flag = (nu > 0.0 && d > tau * tau * nu) ? 1 : 0;
-            if (keep_flag) { R[k * S + k] = sqrt(d); ++nkept; }
-        }
-        __syncthreads();
-        if (keep_flag && j > k && j < S) R[k * S + j] = t[j] / R[k * S + k];
-        __syncthreads();
-    }
-    // Rinv: column j by back substitution over kept rows
-    if (j < S) {
-        for (int i = 0; i < S; ++i) Rinv[i * S + j] = 0.0;
-        double rjj = R[j * S + j];
-        if (rjj != 0.0) {
-            Rinv[j * S + j] = 1.0 / rjj;
-            for (int i = j - 1; i >= 0; --i) {
-                double rii = R[i * S + i];
-                if (rii == 0.0) continue;
-                double acc = 0.0;
-                for (int tt = i + 1; tt <= j; ++tt) acc += R[i * S + tt] * Rinv[tt * S + j];
-                Rinv[i * S + j] = -acc / rii;
+        if (tid == 0) {
+            const double d = W[k * S + k], nu = nu2[k];
+            if (nu > 0.0 && d > tau * tau * nu) {
+                // 1/sqrt(d): FP32 estimate + two FP64 Newton steps (full FP64 accuracy with a
+                // much shorter dependent chain than a correctly rounded divide and root)
+                double y = (double)rsqrtf((float)d);
+                y = y * (1.5 - 0.5 * d * y * y);
+                y = y * (1.5 - 0.5 * d * y * y);
+                W[k * S + k] = d * y;
+                rinv[k] = y;
+                ++nkept;
+            } else {
+                W[k * S + k] = 0.0;
+                rinv[k] = 0.0;
             }
         }
+        __syncthreads();
+        const double ri = rinv[k];
+        for (int j = k + 1 + tid; j < S; j += nt) W[k * S + j] = W[k * S + j] * ri;   // row k of R
+        __syncthreads();
+        // trailing update G'_ij -= R_ki R_kj, k < i <= j
+        const int m = S - k - 1;
+        for (int t = tid; t < m * m; t += nt) {
+            const int i = k + 1 + t / m, j = k + 1 + t % m;
+            if (j >= i) W[i * S + j] -= W[k * S + i] * W[k * S + j];
+        }
+        __syncthreads();
     }
-    if (j == 0 && kept) atomicAdd(kept, nkept);
+    // Rinv: R X = I from the bottom row up; row i = B_i / R_ii, then B_r -= R_ri X_i (r < i)
+    for (int i = S - 1; i >= 0; --i) {
+        const double ri = rinv[i];
+        for (int j = tid; j < S; j += nt) B[i * S + j] = ri != 0.0 ? B[i * S + j] * ri : 0.0;
+        __syncthreads();
+        for (int t = tid; t < i * S; t += nt) {
+            const int r = t / S, j = t % S;
+            B[r * S + j] -= W[r * S + i] * B[i * S + j];
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < S * S; e += nt) Rinv[e] = B[e];
+    if (tid == 0 && kept) atomicAdd(kept, nkept);
 }
 
 // Q[i][m+s] = sum_t (Q[i][m+t] - sum_{r<m} Q[i][r] M[r][t]) Rinv[t][s]; ORTH_ROWS rows per CTA
-constexpr int ORTH_ROWS = 8;
+constexpr int ORTH_ROWS = 4;
 __global__ void k_orth_apply(double* __restrict__ Q, int64_t ldq, int64_t rows, int m, int S,
                              const double* __restrict__ M, const double* __restrict__ Rinv) {
     extern __shared__ double tmp[];   // ORTH_ROWS x S
@@ -137,8 +159,16 @@ __global__ void k_orth_apply(double* __restrict__ Q, int64_t ldq, int64_t rows, 
         double v = 0.0;
         if (i < rows) {
             const double* qi = Q + i * ldq;
-            v = qi[m + s];
-            for (int r = 0; r < m; ++r) v -= qi[r] * M[(int64_t)r * S + s];
+            double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+            int r = 0;
+            for (; r + 3 < m; r += 4) {
+                a0 += qi[r] * M[(int64_t)r * S + s];
+                a1 += qi[r + 1] * M[(int64_t)(r + 1) * S + s];
+                a2 += qi[r + 2] * M[(int64_t)(r + 2) * S + s];
+                a3 += qi[r + 3] * M[(int64_t)(r + 3) * S + s];
+            }
+            for (; r < m; ++r) a0 += qi[r] * M[(int64_t)r * S + s];
+            v = qi[m + s] - ((a0 + a1) + (a2 + a3));
         }
         tmp[e] = v;
     }
@@ -147,9 +177,14 @@ __global__ void k_orth_apply(double* __restrict__ Q, int64_t ldq, int64_t rows, 
         int rr = e / S, s = e % S;
         int64_t i = i0 + rr;
         if (i >= rows) continue;
-        double acc = 0.0;
-        for (int tt = 0; tt <= s; ++tt) acc += tmp[rr * S + tt] * Rinv[tt * S + s];
-        Q[i * ldq + m + s] = acc;
+        double a0 = 0.0, a1 = 0.0;
+        int tt = 0;
+        for (; tt + 1 <= s; tt += 2) {
+            a0 += tmp[rr * S + tt] * Rinv[tt * S + s];
+            a1 += tmp[rr * S + tt + 1] * Rinv[(tt + 1) * S + s];
+        }
+        for (; tt <= s; ++tt) a0 += tmp[rr * S + tt] * Rinv[tt * S + s];
+        Q[i * ldq + m + s] = a0 + a1;
     }
 }
 
@@ -249,7 +284,7 @@ rbki_status orth_pass_cuda(double* Q, int64_t ldq, int64_t rows, int m, int S, d
     RBKI_TRY(atb_cuda(Q, ldq, m + S, Q + m, ldq, S, rows, part, M, S, st));
     k_gprime<<<S, 128, 0, st>>>(M, m, S, Gp, nu2);
     RBKI_LAUNCH_CHECK("k_gprime");
-    size_t sm = ((size_t)S * S + S) * sizeof(double);
+    size_t sm = (2 * (size_t)S * S + S) * sizeof(double);
     static size_t smax = 0;
     if (!smax) smax = max_dyn_smem(k_chol_deflate);
     if (sm > smax) return set_error(RBKI_E_UNSUPPORTED, "orth: block too wide for shared memory");
@@ -282,6 +317,85 @@ rbki_status fill_i32_cuda(int32_t* dst, int32_t v, int n, cudaStream_t st) {
     if (n <= 0) return RBKI_OK;
     k_fill_i32<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(dst, v, n);
     RBKI_LAUNCH_CHECK("k_fill_i32");
+    return RBKI_OK;
+}
+
+}  // namespace rbki
+
+// ---- general small FP64 GEMM: C = op(A) B + beta C with a split over K ----
+namespace rbki {
+namespace {
+
+template <bool TRANSA>
+__global__ void __launch_bounds__(256) k_gemm_part(const double* __restrict__ A, int64_t lda,
+                                                   const double* __restrict__ B, int64_t ldb, int M, int N, int K,
+                                                   int kpc, double* __restrict__ part) {
+    __shared__ double as[AT_K][AT_T + 1];
+    __shared__ double bs[AT_K][AT_T + 1];
+    const int tid = threadIdx.x;
+    const int tk = tid / 16, tl = tid % 16;
+    const int m0 = blockIdx.x * AT_T, n0 = blockIdx.y * AT_T;
+    const int k_lo = blockIdx.z * kpc, k_hi = min(K, k_lo + kpc);
+    double acc[2][2] = {{0, 0}, {0, 0}};
+    for (int k0 = k_lo; k0 < k_hi; k0 += AT_K) {
+        for (int e = tid; e < AT_K * AT_T; e += 256) {
+            const int kk = e / AT_T, cc = e % AT_T;
+            const int k = k0 + kk;
+            const bool ok = k < k_hi;
+            as[kk][cc] = (ok && m0 + cc < M) ? (TRANSA ? A[(int64_t)k * lda + m0 + cc] : A[(int64_t)(m0 + cc) * lda + k]) : 0.0;
+            bs[kk][cc] = (ok && n0 + cc < N) ? B[(int64_t)k * ldb + n0 + cc] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < AT_K; ++kk) {
+            const double a0 = as[kk][tk], a1 = as[kk][tk + 16];
+            const double b0 = bs[kk][tl], b1 = bs[kk][tl + 16];
+            acc[0][0] += a0 * b0; acc[0][1] += a0 * b1;
+            acc[1][0] += a1 * b0; acc[1][1] += a1 * b1;
+        }
+        __syncthreads();
+    }
+    double* out = part + (int64_t)blockIdx.z * M * N;
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+            const int m = m0 + tk + 16 * u, n = n0 + tl + 16 * v;
+            if (m < M && n < N) out[(int64_t)m * N + n] = acc[u][v];
+        }
+}
+
+__global__ void k_gemm_reduce(const double* __restrict__ part, int nchunk, int M, int N, double* __restrict__ C,
+                              int64_t ldc, double beta) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= M * N) return;
+    double acc = 0.0;
+    for (int c = 0; c < nchunk; ++c) acc += part[(int64_t)c * M * N + e];
+    double* cp = C + (int64_t)(e / N) * ldc + e % N;
+    *cp = beta != 0.0 ? acc + beta * *cp : acc;
+}
+
+int gemm_nchunk(int M, int N, int K) {
+    const int tiles = (int)(cdiv(M, AT_T) * cdiv(N, AT_T));
+    const int want = (int)cdiv(256, tiles);
+    const int maxc = (int)cdiv(K, AT_K);
+    return std::max(1, std::min(want, maxc));
+}
+
+}  // namespace
+
+size_t gemm_part_doubles(int M, int N, int K) { return (size_t)gemm_nchunk(M, N, K) * M * N; }
+
+rbki_status gemm_f64_cuda(bool transA, int M, int N, int K, const double* A, int64_t lda, const double* B,
+                          int64_t ldb, double* C, int64_t ldc, double beta, double* part, cudaStream_t st) {
+    const int nch = gemm_nchunk(M, N, K);
+    const int kpc = (int)rup(cdiv(K, nch), AT_K);
+    dim3 grid((unsigned)cdiv(M, AT_T), (unsigned)cdiv(N, AT_T), (unsigned)nch);
+    if (transA) k_gemm_part<true><<<grid, 256, 0, st>>>(A, lda, B, ldb, M, N, K, kpc, part);
+    else k_gemm_part<false><<<grid, 256, 0, st>>>(A, lda, B, ldb, M, N, K, kpc, part);
+    RBKI_LAUNCH_CHECK("k_gemm_part");
+    k_gemm_reduce<<<(unsigned)cdiv((int64_t)M * N, 256), 256, 0, st>>>(part, nch, M, N, C, ldc, beta);
+    RBKI_LAUNCH_CHECK("k_gemm_reduce");
     return RBKI_OK;
 }
 

@@ -431,15 +431,15 @@ __global__ void k_omega_images(uint64_t seed, int mode, int64_t A, int64_t C, in
         valid = a < A;
         col = a;
     }
-    double z[2] = {0.0, 0.0};
-    if (valid) omega_pair_f64(seed, (uint32_t)mode, (uint64_t)col, (uint32_t)pair, z[0], z[1]);
+    float z[2] = {0.f, 0.f};
+    if (valid) omega_pair_f32(seed, (uint32_t)mode, (uint64_t)col, (uint32_t)pair, z[0], z[1]);
     uint16_t* base = img + (size_t)t * 128 * N;
     for (int u = 0; u < 2; ++u) {
         int s = 2 * pair + u;
         if (s >= S) break;
-        double x = z[u];
-        float hi = fp16 ? __half2float(__double2half(x)) : __bfloat162float(__double2bfloat16(x));
-        float lo = (float)(x - (double)hi);
+        const float x = z[u];
+        float hi = fp16 ? __half2float(__float2half_rn(x)) : __bfloat162float(__float2bfloat16_rn(x));
+        float lo = x - hi;
         int ns[2] = {s, split ? S + s : -1};
         float vs[2] = {hi, lo};
         for (int w = 0; w < 2; ++w) {
@@ -453,21 +453,35 @@ __global__ void k_omega_images(uint64_t seed, int mode, int64_t A, int64_t C, in
     }
 }
 
-// out[i*ld + s] = sum_b (part[b][i][s] + split * part[b][i][Sh + s]), FP64, fixed order
-__global__ void k_reduce_tc(const float* __restrict__ part, int nb, int64_t I, int N, int Sh, int split,
-                            double* __restrict__ out, int64_t ld, double* __restrict__ out2, int64_t ld2) {
-    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= I * Sh) return;
-    int64_t i = e / Sh;
-    int s = (int)(e % Sh);
+// out[i*ld + s] = sum_b (part[b][i][s] + split * part[b][i][Sh + s]), FP64, fixed order:
+// 32 outputs per CTA; warp w sums partials b = w, w+8, ...; warps combined in order.
+__global__ void __launch_bounds__(256) k_reduce_tc(const float* __restrict__ part, int nb, int64_t I, int N, int Sh,
+                                                   int split, double* __restrict__ out, int64_t ld,
+                                                   double* __restrict__ out2, int64_t ld2) {
+    __shared__ double acc_sh[8][33];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t e = (int64_t)blockIdx.x * 32 + lane;
+    const int64_t tot = I * Sh;
     double acc = 0.0;
-    for (int b = 0; b < nb; ++b) {
-        const float* pb = part + ((size_t)b * I + i) * N;
-        acc += (double)pb[s];
-        if (split) acc += (double)pb[Sh + s];
+    if (e < tot) {
+        const int64_t i = e / Sh;
+        const int s = (int)(e % Sh);
+        for (int b = w; b < nb; b += 8) {
+            const float* pb = part + ((size_t)b * I + i) * N;
+            acc += (double)pb[s];
+            if (split) acc += (double)pb[Sh + s];
+        }
     }
-    out[i * ld + s] = acc;
-    if (out2) out2[i * ld2 + s] = acc;
+    acc_sh[w][lane] = acc;
+    __syncthreads();
+    if (w == 0 && e < tot) {
+        double t = 0.0;
+        for (int k = 0; k < 8; ++k) t += acc_sh[k][lane];
+        const int64_t i = e / Sh;
+        const int s = (int)(e % Sh);
+        out[i * ld + s] = t;
+        if (out2) out2[i * ld2 + s] = t;
+    }
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -622,7 +636,7 @@ rbki_status stream_tc(int mode, const View& v, int N, int Sh, bool split, const 
 rbki_status reduce_parts(const float* part, int nb, int64_t I, int N, int Sh, bool split, double* out, int64_t ld,
                          double* out2, int64_t ld2, cudaStream_t st) {
     int64_t tot = I * Sh;
-    k_reduce_tc<<<(unsigned)cdiv(tot, 256), 256, 0, st>>>(part, nb, I, N, Sh, split ? 1 : 0, out, ld, out2, ld2);
+    k_reduce_tc<<<(unsigned)cdiv(tot, 32), 256, 0, st>>>(part, nb, I, N, Sh, split ? 1 : 0, out, ld, out2, ld2);
     RBKI_LAUNCH_CHECK("k_reduce_tc");
     return RBKI_OK;
 }

@@ -48,6 +48,11 @@ rbki_status atb_cuda(const double* A, int64_t lda, int ma, const double* B, int6
 rbki_status orth_pass_cuda(double* Q, int64_t ldq, int64_t rows, int m, int S, double tau,
                            double* scratch, int32_t* kept, cudaStream_t st);
 size_t orth_scratch_doubles(int64_t rows, int m, int S);
+// C (M x N, ld ldc) = op(A) B + beta C; op(A) = A^T (A: K x M, ld lda) when transA, else A
+// (M x K); B: K x N (ld ldb).  Split over K into `part` (gemm_part_doubles), fixed-order reduce.
+size_t gemm_part_doubles(int M, int N, int K);
+rbki_status gemm_f64_cuda(bool transA, int M, int N, int K, const double* A, int64_t lda, const double* B,
+                          int64_t ldb, double* C, int64_t ldc, double beta, double* part, cudaStream_t st);
 // symmetric eigensolver (k_eig.cu), descending; V (n x n row-major) columns are eigenvectors
 rbki_status syev_cuda(const double* A, int n, double* w, double* V, double* scratch,
                       cudaStream_t st);
