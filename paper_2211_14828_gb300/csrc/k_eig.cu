@@ -179,36 +179,36 @@ __host__ __device__ float bisect_one(const float* df, const float* e2f, int n, i
 // strided arrays (element i at [i * stride]).  Returns the final shift.
 template <typename T>
 __host__ __device__ T invit_one(const T* d, const T* e, int n, T mu, T tnorm, int k, T* rdd, T* du, T* du2, T* y,
-                                int stride, int sweeps, int rq_update) {
+                                int stride, int sweeps, int rq_update, int ystride) {
     const T eps = sizeof(T) == 8 ? (T)1.1102230246251565e-16 : (T)5.9604645e-08f;
     const T tiny = eps * tnorm + (T)(sizeof(T) == 8 ? 1e-300 : 1e-37);
     uint32_t hsh = 2166136261u ^ ((uint32_t)k * 16777619u);
     for (int i = 0; i < n; ++i) {
         hsh = hsh * 1664525u + 1013904223u;
-        y[i * stride] = (T)1 + (T)0.5 * ((T)(hsh >> 8) * (T)(1.0 / 16777216.0) - (T)0.5);
+        y[i * ystride] = (T)1 + (T)0.5 * ((T)(hsh >> 8) * (T)(1.0 / 16777216.0) - (T)0.5);
     }
     for (int it = 0; it < sweeps; ++it) {
         T a = d[0] - mu, b = n > 1 ? e[0] : (T)0, yi = y[0];
         for (int i = 0; i + 1 < n; ++i) {
-            const T c = e[i], dn = d[i + 1] - mu, f = (i + 2 < n) ? e[i + 1] : (T)0, yn = y[(i + 1) * stride];
+            const T c = e[i], dn = d[i + 1] - mu, f = (i + 2 < n) ? e[i + 1] : (T)0, yn = y[(i + 1) * ystride];
             if (fabs(a) >= fabs(c)) {
                 if (fabs(a) < tiny) a = a >= (T)0 ? tiny : -tiny;
                 const T r = (T)1 / a, m = c * r;
-                rdd[i * stride] = r; du[i * stride] = b; du2[i * stride] = 0; y[i * stride] = yi;
+                rdd[i * stride] = r; du[i * stride] = b; du2[i * stride] = 0; y[i * ystride] = yi;
                 a = dn - m * b; b = f; yi = yn - m * yi;
             } else {
                 const T r = (T)1 / c, m = a * r;
-                rdd[i * stride] = r; du[i * stride] = dn; du2[i * stride] = f; y[i * stride] = yn;
+                rdd[i * stride] = r; du[i * stride] = dn; du2[i * stride] = f; y[i * ystride] = yn;
                 a = b - m * dn; b = -m * f; yi = yi - m * yn;
             }
         }
         if (fabs(a) < tiny) a = a >= (T)0 ? tiny : -tiny;
         T y1 = yi / a, y2 = 0;
-        y[(n - 1) * stride] = y1;
+        y[(n - 1) * ystride] = y1;
         T ss = y1 * y1;
         for (int i = n - 2; i >= 0; --i) {
-            const T vv = (y[i * stride] - du[i * stride] * y1 - du2[i * stride] * y2) * rdd[i * stride];
-            y[i * stride] = vv;
+            const T vv = (y[i * ystride] - du[i * stride] * y1 - du2[i * stride] * y2) * rdd[i * stride];
+            y[i * ystride] = vv;
             ss += vv * vv;
             y2 = y1;
             y1 = vv;
@@ -216,8 +216,8 @@ __host__ __device__ T invit_one(const T* d, const T* e, int n, T mu, T tnorm, in
         const T sc = (T)1 / sqrt(ss);
         T num = 0, prev = 0, cur = y[0] * sc;
         for (int i = 0; i < n; ++i) {
-            const T next = (i + 1 < n) ? y[(i + 1) * stride] * sc : (T)0;
-            y[i * stride] = cur;
+            const T next = (i + 1 < n) ? y[(i + 1) * ystride] * sc : (T)0;
+            y[i * ystride] = cur;
             T ti = d[i] * cur;
             if (i > 0) ti += e[i - 1] * prev;
             if (i + 1 < n) ti += e[i] * next;
@@ -230,9 +230,9 @@ __host__ __device__ T invit_one(const T* d, const T* e, int n, T mu, T tnorm, in
     return mu;
 }
 template double invit_one<double>(const double*, const double*, int, double, double, int, double*, double*, double*,
-                                  double*, int, int, int);
+                                  double*, int, int, int, int);
 template float invit_one<float>(const float*, const float*, int, float, float, int, float*, float*, float*, float*,
-                                int, int, int);
+                                int, int, int, int);
 
 namespace {
 
@@ -284,11 +284,13 @@ __global__ void __launch_bounds__(64) k_tri_vec(const T* __restrict__ d, const T
     const float lam = bisect_one(df, e2f, n, n - 1 - k, bounds[0], bounds[1]);
     shift_out[k] = lam;
     const T eps = sizeof(T) == 8 ? (T)1.1102230246251565e-16 : (T)5.9604645e-08f;
-    T* rdd = scratch;
-    T* du = rdd + (size_t)n * ld;
-    T* du2 = du + (size_t)n * ld;
+    // elimination rows of this thread in shared memory ([i][thread], conflict-free)
+    extern __shared__ __align__(16) unsigned char vsm_raw[];
+    T* rdd = reinterpret_cast<T*>(vsm_raw);
+    T* du = rdd + (size_t)n * blockDim.x;
+    T* du2 = du + (size_t)n * blockDim.x;
     const T mu = (T)lam * tnorm + (T)(k + 1) * eps * tnorm;
-    invit_one<T>(d, e, n, mu, tnorm, k, rdd + k, du + k, du2 + k, Y + k, ld, 3, 0);
+    invit_one<T>(d, e, n, mu, tnorm, k, rdd + tid, du + tid, du2 + tid, Y + k, (int)blockDim.x, 3, 0, ld);
 }
 
 // Orthonormalise the inverse-iteration vectors by one Cholesky QR of the whole block
@@ -337,27 +339,26 @@ __global__ void __launch_bounds__(256) k_tri_orth(T* __restrict__ Yg, int n, int
             }
     }
     __syncthreads();
-    // right-looking Cholesky on the upper triangle: pivot on thread 0, rank-1 update of the
-    // trailing triangle spread over the whole CTA; Ri[k] keeps 1 / R_kk
+    // right-looking Cholesky on the upper triangle, one barrier per step: each thread takes
+    // the pivot itself; the trailing update (warp per row, lanes over columns) uses the
+    // unscaled row k; rows are scaled to R after the loop.  Ri[k] keeps 1 / R_kk.
+    const int lane = tid & 31, wid = tid >> 5, nwp = blockDim.x >> 5;
     for (int k = 0; k < nwant; ++k) {
-        if (tid == 0) {
-            const T dk = Gm[k * ld + k];
-            const T r = dk > (T)0 ? sqrt(dk) : (T)1;
-            Gm[k * ld + k] = r;
-            Ri[k] = (T)1 / r;
+        const T dk = Gm[k * ld + k];
+        const T ri = dk > (T)0 ? (T)1 / sqrt(dk) : (T)1;
+        if (tid == 0) Ri[k] = ri;
+        const T r2 = ri * ri;
+        for (int i = k + 1 + wid; i < nwant; i += nwp) {
+            const T gki = Gm[k * ld + i] * r2;
+            for (int j = i + lane; j < nwant; j += 32) Gm[i * ld + j] -= gki * Gm[k * ld + j];
         }
-        __syncthreads();
-        const T ri = Ri[k];
-        const int mm = nwant - k - 1;
-        // trailing update G_ij -= R_ki R_kj with R_kj = G_kj / r (row k scaled afterwards)
-        for (int t = tid; t < mm * mm; t += blockDim.x) {
-            const int i = k + 1 + t / mm, j = k + 1 + t % mm;
-            if (j >= i) Gm[i * ld + j] -= (Gm[k * ld + i] * ri) * (Gm[k * ld + j] * ri);
-        }
-        __syncthreads();
-        for (int j = k + 1 + tid; j < nwant; j += blockDim.x) Gm[k * ld + j] *= ri;
         __syncthreads();
     }
+    for (int t = tid; t < nwant * nwant; t += blockDim.x) {
+        const int p = t / nwant, q = t % nwant;
+        if (q >= p) Gm[p * ld + q] *= Ri[p];
+    }
+    __syncthreads();
     // rows of Y: solve y_new R = y by forward substitution (one thread per row)
     for (int i = tid; i < n; i += blockDim.x) {
         T* yi = ys + (size_t)i * ld;
@@ -550,7 +551,12 @@ rbki_status syev_top_cuda(const double* A, int n, int nwant, double* w, double* 
     const int t_smem = tsm <= tmax;
     k_tridiag<float><<<1, 512, t_smem ? tsm : 0, st>>>(A, n, L.work, t_smem, L.d, L.e, L.refl);
     RBKI_LAUNCH_CHECK("k_tridiag");
-    k_tri_vec<float><<<(unsigned)cdiv(n, 64), 64, 0, st>>>(L.d, L.e, n, n, L.Yt, L.iiw, L.shift);
+    static size_t vmax = 0;
+    if (!vmax) vmax = max_dyn_smem(k_tri_vec<float>);
+    const int vthr = 32;
+    const size_t vsm = 3 * (size_t)n * vthr * sizeof(float);
+    if (vsm > vmax) return set_error(RBKI_E_UNSUPPORTED, "syev: inverse-iteration rows exceed shared memory");
+    k_tri_vec<float><<<(unsigned)cdiv(n, vthr), vthr, vsm, st>>>(L.d, L.e, n, n, L.Yt, L.iiw, L.shift);
     RBKI_LAUNCH_CHECK("k_tri_vec");
     static size_t omax = 0;
     if (!omax) omax = max_dyn_smem(k_tri_orth<float>);

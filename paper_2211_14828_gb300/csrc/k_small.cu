@@ -85,66 +85,59 @@ __global__ void k_gprime(const double* __restrict__ M, int m, int S, double* __r
 
 // Cholesky G' = R^T R with pivot deflation, then Rinv (upper) with zero rows/columns for
 // deflated directions.  Column k is deflated when nu2[k] == 0 or its pivot (squared norm
-// orthogonal to everything accepted) <= tau^2 nu2[k].  Single CTA.  Both the factorisation
-// and the triangular inverse are right-looking: each step is one square root / reciprocal
-// followed by a parallel rank-1 update, so the dependent FP64 chain per step stays short.
+// orthogonal to everything accepted) <= tau^2 nu2[k].  Single CTA, right-looking with one
+// barrier per step: every thread evaluates the pivot itself (same inputs, same decision), the
+// trailing update uses the unscaled row k times the pivot reciprocal, and the rows of R and
+// of Rinv are scaled in one final pass.
+__device__ __forceinline__ double rsqrt_f64(double d) {
+    // FP32 estimate + two FP64 Newton steps: full FP64 accuracy with a short dependent chain
+    double y = (double)rsqrtf((float)d);
+    y = y * (1.5 - 0.5 * d * y * y);
+    y = y * (1.5 - 0.5 * d * y * y);
+    return y;
+}
+
 __global__ void k_chol_deflate(const double* __restrict__ Gp, const double* __restrict__ nu2,
                                int S, double tau, double* __restrict__ Rinv,
                                int32_t* __restrict__ kept) {
     extern __shared__ double sm[];
-    double* W = sm;                   // S x S working copy (upper triangle), becomes R
+    double* W = sm;                   // S x S (upper triangle: unscaled rows of R)
     double* B = W + S * S;            // S x S, becomes Rinv
     double* rinv = B + S * S;         // S: 1 / R_kk, 0 when deflated
-    __shared__ int nkept;
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int e = tid; e < S * S; e += nt) {
         W[e] = Gp[e];
         B[e] = (e / S == e % S) ? 1.0 : 0.0;
     }
-    if (tid == 0) nkept = 0;
     __syncthreads();
+    int nk = 0;
     for (int k = 0; k < S; ++k) {
-        if (tid == 0) {
-            const double d = W[k * S + k], nu = nu2[k];
-            if (nu > 0.0 && d > tau * tau * nu) {
-                // 1/sqrt(d): FP32 estimate + two FP64 Newton steps (full FP64 accuracy with a
-                // much shorter dependent chain than a correctly rounded divide and root)
-                double y = (double)rsqrtf((float)d);
-                y = y * (1.5 - 0.5 * d * y * y);
-                y = y * (1.5 - 0.5 * d * y * y);
-                W[k * S + k] = d * y;
-                rinv[k] = y;
-                ++nkept;
-            } else {
-                W[k * S + k] = 0.0;
-                rinv[k] = 0.0;
-            }
-        }
-        __syncthreads();
-        const double ri = rinv[k];
-        for (int j = k + 1 + tid; j < S; j += nt) W[k * S + j] = W[k * S + j] * ri;   // row k of R
-        __syncthreads();
-        // trailing update G'_ij -= R_ki R_kj, k < i <= j
-        const int m = S - k - 1;
-        for (int t = tid; t < m * m; t += nt) {
-            const int i = k + 1 + t / m, j = k + 1 + t % m;
-            if (j >= i) W[i * S + j] -= W[k * S + i] * W[k * S + j];
+        const double d = W[k * S + k], nu = nu2[k];
+        const bool keep = nu > 0.0 && d > tau * tau * nu;
+        const double ri = keep ? rsqrt_f64(d) : 0.0;
+        nk += keep ? 1 : 0;
+        if (tid == 0) rinv[k] = ri;
+        // G_ij -= (G_ki ri)(G_kj ri) for k < i <= j
+        const double r2 = ri * ri;
+        const int mm = S - k - 1;
+        for (int t = tid; t < mm * mm; t += nt) {
+            const int i = k + 1 + t / mm, j = k + 1 + t % mm;
+            if (j >= i) W[i * S + j] -= W[k * S + i] * W[k * S + j] * r2;
         }
         __syncthreads();
     }
-    // Rinv: R X = I from the bottom row up; row i = B_i / R_ii, then B_r -= R_ri X_i (r < i)
+    // Rinv: R X = I from the bottom row up.  With unscaled rows (R_ri = W_ri rinv_r), row i
+    // of X is B_i rinv_i and B_r -= R_ri X_i for r < i; rows are scaled at the end.
     for (int i = S - 1; i >= 0; --i) {
         const double ri = rinv[i];
-        for (int j = tid; j < S; j += nt) B[i * S + j] = ri != 0.0 ? B[i * S + j] * ri : 0.0;
-        __syncthreads();
         for (int t = tid; t < i * S; t += nt) {
             const int r = t / S, j = t % S;
-            B[r * S + j] -= W[r * S + i] * B[i * S + j];
+            B[r * S + j] -= (W[r * S + i] * rinv[r]) * (B[i * S + j] * ri);
         }
         __syncthreads();
     }
-    for (int e = tid; e < S * S; e += nt) Rinv[e] = B[e];
-    if (tid == 0 && kept) atomicAdd(kept, nkept);
+    for (int e = tid; e < S * S; e += nt) Rinv[e] = B[e] * rinv[e / S];
+    if (tid == 0 && kept) atomicAdd(kept, nk);
 }
 
 // Q[i][m+s] = sum_t (Q[i][m+t] - sum_{r<m} Q[i][r] M[r][t]) Rinv[t][s]; ORTH_ROWS rows per CTA
@@ -284,7 +277,7 @@ rbki_status orth_pass_cuda(double* Q, int64_t ldq, int64_t rows, int m, int S, d
     RBKI_TRY(atb_cuda(Q, ldq, m + S, Q + m, ldq, S, rows, part, M, S, st));
     k_gprime<<<S, 128, 0, st>>>(M, m, S, Gp, nu2);
     RBKI_LAUNCH_CHECK("k_gprime");
-    size_t sm = (2 * (size_t)S * S + S) * sizeof(double);
+    size_t sm = (2 * (size_t)S * S + S) * sizeof(double);   // W, B, rinv
     static size_t smax = 0;
     if (!smax) smax = max_dyn_smem(k_chol_deflate);
     if (sm > smax) return set_error(RBKI_E_UNSUPPORTED, "orth: block too wide for shared memory");
