@@ -164,6 +164,28 @@ rbki_status rbki_krylov_product(const rbki_tensor* X, int32_t mode, int32_t prec
 rbki_status rbki_krylov_product_workspace(const rbki_tensor* X, int32_t mode, int32_t prec,
                                           int32_t s, size_t* bytes);
 
+/* Size of the device array that rbki_krylov_product_noalloc uses instead of a workspace. */
+#define RBKI_NOALLOC_SCRATCH_BYTES (20u * 1024u * 1024u)
+
+/* The Krylov step of rbki_krylov_product, for callers that cannot allocate device memory:
+ * some host applications give all device memory to their own allocator up front, or call
+ * this step from code where cudaMalloc is not allowed or too slow, so they cannot pass a
+ * workspace.  This variant takes none: its scratch (BF16 operand image, per-CTA partial
+ * products, error word) is a fixed array of RBKI_NOALLOC_SCRATCH_BYTES compiled into the
+ * library, which every GPU that loads the library keeps until the process exits.  The
+ * paper has no counterpart of this entry point.
+ *   X: device, already stored in the product precision (RBKI_BF16 for RBKI_PREC_BF16,
+ *      RBKI_F16 for RBKI_PREC_FP16); prec < 0 selects the split (hi + lo) variant.
+ *   Q: I_n x s row-major FP64 (device), 1 <= s <= 32;  P: I_n x s row-major FP64 (device).
+ * Shapes the tensor-core kernel takes (contiguous extent a multiple of 8, I_n <= 512) fit
+ * the array on GB300; RBKI_E_UNSUPPORTED is returned for other shapes and RBKI_E_NOMEM if a
+ * shape would ever need more scratch than the array holds.  It allocates nothing.
+ * All calls share the array: calls that overlap on the GPU race on it and must be ordered
+ * by the caller.  The first call on a device looks up the array's address
+ * (cudaGetSymbolAddress, once per device); make that call before any stream capture. */
+rbki_status rbki_krylov_product_noalloc(const rbki_tensor* X, int32_t mode, int32_t prec,
+                                        const double* Q, int32_t s, double* P, void* stream);
+
 /* Algorithm 1 for one mode: the orthonormal Krylov basis Q = [Q_0..Q_q] (I_n x b,
  * row-major FP64, deflated columns are zero), b = S(q+1), S = min(R_n+p, I_n). */
 rbki_status rbki_mode_basis(const rbki_tensor* X, const rbki_params* prm, int32_t mode,

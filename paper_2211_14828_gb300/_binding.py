@@ -69,6 +69,7 @@ def lib():
             "rbki_krylov_product": (st, [vp, C.c_int32, C.c_int32, vp, C.c_int32, vp, vp, C.c_size_t, vp]),
             "rbki_krylov_product_workspace": (st, [vp, C.c_int32, C.c_int32, C.c_int32, sz]),
             "rbki_mode_basis": (st, [vp, vp, C.c_int32, vp, vp, C.c_size_t, vp]),
+            "rbki_krylov_product_noalloc": (st, [vp, C.c_int32, C.c_int32, vp, C.c_int32, vp, vp]),
             "rbki_syev": (st, [vp, C.c_int32, vp, vp, vp, C.c_size_t, vp]),
             "rbki_syev_workspace": (st, [C.c_int32, sz]),
             "rbki_status_str": (C.c_char_p, [C.c_int32]),
@@ -208,6 +209,21 @@ def rbki_krylov_product(x, mode: int, q_mat, prec="fp64", workspace=None, stream
     check(lib().rbki_krylov_product(C.byref(t), mode, prec_code(prec), C.c_void_p(q_c.data_ptr()), s,
                                     C.c_void_p(P.data_ptr()), C.c_void_p(workspace.data_ptr()),
                                     C.c_size_t(workspace.numel()), stream_ptr(stream)), "rbki_krylov_product")
+    return P
+
+
+def rbki_krylov_product_noalloc(x, mode: int, q_mat, prec="bf16", stream=None):
+    """Krylov step without a workspace (static device scratch inside the library).
+    x must already be BF16 (prec 'bf16') or FP16 (prec 'fp16'); a negative prec code selects
+    the split variant.  Returns P = X_(n) (X_(n)^T Q) as an (I_n, s) float64 CUDA tensor."""
+    torch = _torch()
+    t = make_tensor(x)
+    s = int(q_mat.shape[1])
+    P = torch.empty((x.shape[mode], s), dtype=torch.float64, device=x.device)
+    q_c = q_mat.contiguous()
+    check(lib().rbki_krylov_product_noalloc(C.byref(t), mode, prec_code(prec), C.c_void_p(q_c.data_ptr()), s,
+                                            C.c_void_p(P.data_ptr()), stream_ptr(stream)),
+          "rbki_krylov_product_noalloc")
     return P
 
 

@@ -55,6 +55,7 @@ struct Plan {
 };
 
 size_t dtype_size(int dt);
+rbki_status validate_tensor(const rbki_tensor* X);
 size_t host_io_bytes(const Plan& pl);
 rbki_status run_tucker(Plan& pl, const rbki_tucker_out* out, cudaStream_t st);
 rbki_status run_tucker_host_io(Plan& pl, const rbki_tensor* X, const rbki_tucker_out* out,

@@ -1,0 +1,48 @@
+"""The Krylov step without a workspace (rbki_krylov_product_noalloc), for callers that cannot
+allocate device memory.  Its scratch is a fixed device array inside the library, shared by
+every call, so two calls in a row must each match the regular entry point (which uses a
+caller-provided workspace).  Collected last on purpose: it must pass both alone in a fresh
+process and after every other test."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def rb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2211_14828_gb300 as rb
+    rb.lib()
+    return rb
+
+
+@pytest.mark.parametrize("prec", ["bf16", -1])
+def test_noalloc_matches_workspace_entry_point_twice(rb, prec):
+    g = np.random.default_rng(2024)
+    dims = (96, 64, 80)
+    x = torch.from_numpy(g.standard_normal(dims).astype(np.float32)).cuda().bfloat16()
+    for call, (mode, s) in enumerate([(0, 30), (2, 12)]):       # two calls in a row
+        q = torch.from_numpy(g.standard_normal((dims[mode], s))).cuda()
+        p_ws = rb.rbki_krylov_product(x, mode, q, prec=prec)
+        p_na = rb.rbki_krylov_product_noalloc(x, mode, q, prec=prec)
+        torch.cuda.synchronize()
+        a, b = p_ws.cpu().numpy(), p_na.cpu().numpy()
+        np.testing.assert_allclose(b, a, rtol=1e-12, atol=1e-12 * np.abs(a).max(), err_msg=f"call {call}")
+
+
+def test_noalloc_rejects_unsupported_and_wrong_dtype(rb):
+    from paper_2211_14828_gb300 import _binding as B
+    x = torch.zeros((8, 8, 8), dtype=torch.float32, device="cuda")
+    q = torch.zeros((8, 4), dtype=torch.float64, device="cuda")
+    with pytest.raises(rb.RbkiError) as e:
+        rb.rbki_krylov_product_noalloc(x, 0, q, prec="bf16")          # X not stored in BF16
+    assert e.value.status == B.E_INVAL
+    tall = torch.zeros((600, 8, 16), dtype=torch.bfloat16, device="cuda")
+    qt = torch.zeros((600, 32), dtype=torch.float64, device="cuda")
+    with pytest.raises(rb.RbkiError) as e:
+        rb.rbki_krylov_product_noalloc(tall, 0, qt, prec=-1)           # tile exceeds shared memory
+    assert e.value.status == B.E_UNSUPPORTED
