@@ -194,6 +194,33 @@ def rbki_tucker(x, ranks, p, q, seed, prec="bf16", flags=0, workspace=None, out=
     return out
 
 
+def rbki_htr(x, tucker_ranks, p, q, seed, tr_ranks, tr_init, maxit=20, tol=1e-3, prec="fp64", flags=0,
+             workspace=None, tucker_out=None, stream=None):
+    """rBKI-TK-TR (Algorithm 3).  tr_init: list of float64 CUDA tensors (r_{n-1}, R_n, r_n).
+    Returns dict(cores=[(r_{n-1}, I_n, r_n)], fits=(maxit,) NaN after the stop, tucker=...)."""
+    torch = _torch()
+    N = x.dim()
+    t, prm = make_tensor(x), make_params(tucker_ranks, p, q, seed, prec, flags)
+    trr = (C.c_int32 * 8)(*[int(r) for r in tr_ranks])
+    need = C.c_size_t(0)
+    check(lib().rbki_htr_workspace(C.byref(t), C.byref(prm), trr, C.byref(need)), "rbki_htr_workspace")
+    if workspace is None or workspace.numel() < need.value:
+        workspace = torch.empty(int(need.value), dtype=torch.uint8, device=x.device)
+    init = [z.contiguous() for z in tr_init]
+    init_p = (C.c_void_p * 8)(*[z.data_ptr() for z in init])
+    cores = [torch.zeros((int(tr_ranks[(n + N - 1) % N]), int(x.shape[n]), int(tr_ranks[n])),
+                         dtype=torch.float64, device=x.device) for n in range(N)]
+    cores_p = (C.c_void_p * 8)(*[z.data_ptr() for z in cores])
+    fits = torch.zeros(int(maxit), dtype=torch.float64, device=x.device)
+    if tucker_out is None:
+        tucker_out = alloc_outputs(x.shape, tucker_ranks, x.device)
+    o = make_out(tucker_out)
+    check(lib().rbki_htr(C.byref(t), C.byref(prm), trr, init_p, C.c_int32(int(maxit)), C.c_double(float(tol)),
+                         cores_p, C.c_void_p(fits.data_ptr()), C.byref(o), C.c_void_p(workspace.data_ptr()),
+                         C.c_size_t(workspace.numel()), stream_ptr(stream)), "rbki_htr")
+    return dict(cores=cores, fits=fits, tucker=tucker_out, workspace=workspace)
+
+
 def rbki_krylov_product(x, mode: int, q_mat, prec="fp64", workspace=None, stream=None):
     """P = X_(n) (X_(n)^T Q) (Algorithm 1 step 3), Q: (I_n, s) float64 CUDA tensor."""
     torch = _torch()

@@ -601,6 +601,118 @@ rbki_status rbki_mode_basis(const rbki_tensor* X, const rbki_params* prm, int32_
     return RBKI_OK;
 }
 
+// ---- rBKI-TK-TR (Algorithm 3) ----------------------------------------------------
+struct HtrLayout {
+    size_t tucker, core, fac[RBKI_MAX_ORDER], eig[RBKI_MAX_ORDER], norms, info, trc[RBKI_MAX_ORDER], table, trws,
+        total;
+};
+
+static rbki_status htr_layout(const Plan& pl, const rbki_params* tk, const int32_t* tr, HtrLayout& L) {
+    size_t off = (pl.ws_bytes + 255) & ~(size_t)255;
+    auto take = [&](size_t bytes) {
+        off = (off + 255) & ~(size_t)255;
+        size_t r = off;
+        off += bytes;
+        return r;
+    };
+    L.tucker = 0;
+    L.core = take((size_t)pl.ranks_numel * 8);
+    int64_t cdims[RBKI_MAX_ORDER];
+    for (int n = 0; n < pl.N; ++n) {
+        L.fac[n] = take((size_t)pl.dims[n] * tk->ranks[n] * 8);
+        L.eig[n] = take((size_t)tk->ranks[n] * 8);
+        cdims[n] = tk->ranks[n];
+    }
+    L.norms = take(16);
+    L.info = take((2 * RBKI_MAX_ORDER + 1) * 4);
+    for (int n = 0; n < pl.N; ++n)
+        L.trc[n] = take((size_t)tr[(n + pl.N - 1) % pl.N] * tk->ranks[n] * tr[n] * 8);
+    L.table = take(RBKI_MAX_ORDER * sizeof(double*));
+    L.trws = take(tr_workspace_doubles_for(pl.N, cdims, tr) * 8);
+    L.total = off + 256;
+    return RBKI_OK;
+}
+
+static rbki_status htr_validate(const rbki_tensor* X, const rbki_params* tk, const int32_t* tr_ranks, Plan& pl) {
+    RBKI_TRY(make_plan(X, tk, pl));
+    if (!tr_ranks) return set_error(RBKI_E_INVAL, "tr_ranks is NULL");
+    for (int n = 0; n < pl.N; ++n)
+        if (tr_ranks[n] < 1 || tr_ranks[n] > 8) return set_error(RBKI_E_UNSUPPORTED, "TR ranks must be in [1, 8]");
+    if (pl.N < 2) return set_error(RBKI_E_INVAL, "a tensor ring needs order >= 2");
+    if (tk->flags & RBKI_FLAG_HOST_IO) return set_error(RBKI_E_UNSUPPORTED, "rbki_htr takes device buffers");
+    carve(pl, nullptr);
+    return RBKI_OK;
+}
+
+rbki_status rbki_htr_workspace(const rbki_tensor* X, const rbki_params* tk, const int32_t* tr_ranks,
+                               size_t* bytes) {
+    if (!bytes) return set_error(RBKI_E_INVAL, "bytes is NULL");
+    Plan pl;
+    RBKI_TRY(htr_validate(X, tk, tr_ranks, pl));
+    HtrLayout L;
+    RBKI_TRY(htr_layout(pl, tk, tr_ranks, L));
+    *bytes = L.total;
+    return RBKI_OK;
+}
+
+// Algorithm 3: rBKI-TK, TR-ALS on the core, contraction of each TR core with its factor.
+// Synchronises `stream` once per TR-ALS sweep (the stopping rule is evaluated on the host).
+rbki_status rbki_htr(const rbki_tensor* X, const rbki_params* tk, const int32_t* tr_ranks,
+                     const double* const* tr_init, int32_t tr_maxit, double tr_tol, double* const* tr_cores,
+                     double* fits, const rbki_tucker_out* tucker_out, void* workspace, size_t workspace_bytes,
+                     void* stream) {
+    Plan pl;
+    RBKI_TRY(htr_validate(X, tk, tr_ranks, pl));
+    if (!tr_init || !tr_cores || tr_maxit < 1) return set_error(RBKI_E_INVAL, "tr_init / tr_cores / tr_maxit");
+    for (int n = 0; n < pl.N; ++n)
+        if (!tr_init[n] || !tr_cores[n]) return set_error(RBKI_E_INVAL, "NULL TR core pointer");
+    HtrLayout L;
+    RBKI_TRY(htr_layout(pl, tk, tr_ranks, L));
+    if (!workspace || workspace_bytes < L.total) return set_error(RBKI_E_NOMEM, "workspace too small");
+    carve(pl, workspace);
+    char* base = static_cast<char*>(workspace);
+    cudaStream_t st = (cudaStream_t)stream;
+    rbki_tucker_out o{};
+    if (tucker_out && tucker_out->core) {
+        o = *tucker_out;
+    } else {
+        o.core = reinterpret_cast<double*>(base + L.core);
+        for (int n = 0; n < pl.N; ++n) o.factors[n] = reinterpret_cast<double*>(base + L.fac[n]);
+    }
+    for (int n = 0; n < pl.N; ++n)
+        if (!o.eigvals[n]) o.eigvals[n] = reinterpret_cast<double*>(base + L.eig[n]);
+    if (!o.norms) o.norms = reinterpret_cast<double*>(base + L.norms);
+    if (!o.info) o.info = reinterpret_cast<int32_t*>(base + L.info);
+    pl.xin = X->data;
+    RBKI_TRY(run_tucker(pl, &o, st));
+    // working TR cores (initial values copied in) and their pointer table
+    double* cores[RBKI_MAX_ORDER];
+    int64_t cdims[RBKI_MAX_ORDER];
+    for (int n = 0; n < pl.N; ++n) {
+        cores[n] = reinterpret_cast<double*>(base + L.trc[n]);
+        cdims[n] = tk->ranks[n];
+        const size_t cnt = (size_t)tr_ranks[(n + pl.N - 1) % pl.N] * tk->ranks[n] * tr_ranks[n];
+        RBKI_CUDA_TRY(cudaMemcpyAsync(cores[n], tr_init[n], cnt * 8, cudaMemcpyDeviceToDevice, st));
+    }
+    double** table = reinterpret_cast<double**>(base + L.table);
+    RBKI_CUDA_TRY(cudaMemcpyAsync(table, cores, pl.N * sizeof(double*), cudaMemcpyHostToDevice, st));
+    double norms[2];
+    RBKI_CUDA_TRY(cudaMemcpyAsync(norms, o.norms, sizeof(norms), cudaMemcpyDeviceToHost, st));
+    RBKI_CUDA_TRY(cudaStreamSynchronize(st));
+    std::vector<double> hf(tr_maxit, std::nan(""));
+    int sweeps = 0;
+    RBKI_TRY(tr_run(pl.N, cdims, tr_ranks, o.core, norms[1], cores, table, tr_maxit, tr_tol,
+                    reinterpret_cast<double*>(base + L.trws), hf.data(), &sweeps, st));
+    for (int n = 0; n < pl.N; ++n)
+        RBKI_TRY(tr_contract_cuda(cores[n], o.factors[n], tr_ranks[(n + pl.N - 1) % pl.N], tk->ranks[n], tr_ranks[n],
+                                  pl.dims[n], tr_cores[n], st));
+    if (fits) {
+        RBKI_CUDA_TRY(cudaMemcpyAsync(fits, hf.data(), tr_maxit * sizeof(double), cudaMemcpyHostToDevice, st));
+        RBKI_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    return RBKI_OK;
+}
+
 rbki_status rbki_syev_workspace(int32_t n, size_t* bytes) {
     if (!bytes || n < 1 || n > 256) return set_error(RBKI_E_INVAL, "n out of range");
     *bytes = syev_scratch_doubles(n) * sizeof(double);

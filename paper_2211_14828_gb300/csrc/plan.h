@@ -54,6 +54,15 @@ struct Plan {
     const void* xstream = nullptr;
 };
 
+// TR-ALS (k_tr.cu)
+struct TrPlan;
+size_t tr_workspace_doubles_for(int N, const int64_t* core_dims, const int32_t* ranks);
+rbki_status tr_run(int N, const int64_t* core_dims, const int32_t* ranks, const double* G, double g_norm2,
+                   double* const* cores_dev, const double* const* cores_table_dev, int maxit, double tol,
+                   double* ws, double* fits_host, int* sweeps, cudaStream_t st);
+rbki_status tr_contract_cuda(const double* Z, const double* U, int r0, int64_t Rn, int r1, int64_t In, double* X,
+                             cudaStream_t st);
+
 size_t dtype_size(int dt);
 rbki_status validate_tensor(const rbki_tensor* X);
 size_t host_io_bytes(const Plan& pl);

@@ -5,14 +5,6 @@
 using namespace rbki;
 
 extern "C" {
-rbki_status rbki_htr_workspace(const rbki_tensor*, const rbki_params*, const int32_t*, size_t*) {
-    return set_error(RBKI_E_UNSUPPORTED, "rbki_htr not built");
-}
-rbki_status rbki_htr(const rbki_tensor*, const rbki_params*, const int32_t*, const double* const*,
-                     int32_t, double, double* const*, double*, const rbki_tucker_out*, void*, size_t,
-                     void*) {
-    return set_error(RBKI_E_UNSUPPORTED, "rbki_htr not built");
-}
 rbki_status rbki_server_create(int32_t, size_t, int32_t, rbki_server**) {
     return set_error(RBKI_E_UNSUPPORTED, "server not built");
 }
