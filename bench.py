@@ -37,16 +37,18 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["tucker512", "tucker64", "video", "htr"], default="tucker512")
     ap.add_argument("--prec", choices=["bf16", "fp64"], default="bf16")
+    ap.add_argument("--size", type=int, default=0,
+                    help="cube edge for tucker512 (0 = 512); smaller cases for profiler captures")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
     return ap.parse_args()
 
 
-def make_workload(name, mc):
+def make_workload(name, mc, size=0):
     import synth
     if name == "tucker512":
-        return synth.config_large(mc=mc)
+        return synth.config_large(mc=mc, size=size or 512)
     if name == "tucker64":
         return synth.config_small_fp64(mc=mc)
     if name == "video":
@@ -196,7 +198,7 @@ def run_ours(args):
     from paper_2211_14828_gb300 import _binding as B
 
     world, rank, local = dist_setup(args)
-    wl = make_workload(args.workload, rank)
+    wl = make_workload(args.workload, rank, args.size)
     dims = list(wl.x.shape)
     numel = int(np.prod(dims))
     passes, krylov_steps = plan_passes(dims, wl.ranks, wl.p, wl.q)
@@ -332,7 +334,7 @@ def run_reference(args):
         return
     from oracle import philox, rbki
     from oracle.tensor import unfold
-    wl = make_workload(args.workload, 0)
+    wl = make_workload(args.workload, 0, args.size)
     x = np.asarray(wl.x, dtype=np.float64)
     dims = list(x.shape)
     numel = x.size

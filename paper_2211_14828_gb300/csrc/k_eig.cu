@@ -7,9 +7,9 @@
 //   1. a full eigendecomposition of Z in FP32 on one CTA:
 //        Householder tridiagonalisation (Householder 1958; the symmetric rank-2 update
 //        form of LAPACK's xSYTD2), bisection with Sturm counts (Givens 1954) for the
-//        eigenvalues, inverse iteration with Rayleigh-quotient shifts on the tridiagonal
-//        (fixed shift; Gaussian elimination with partial pivoting), Gram-Schmidt inside
-//        clusters of equal shifts,
+//        eigenvalues, fixed-shift inverse iteration on the tridiagonal (Gaussian
+//        elimination with partial pivoting), one Cholesky QR of the eigenvector block
+//        (mixes vectors only inside clusters),
 //        back-transformation by the reflectors (one warp per eigenvector);
 //   2. FP64 iterative refinement of the leading `nwant` eigenvectors by the method of
 //        Ogita & Aishima ("Iterative refinement for symmetric eigenvalue decomposition",
@@ -172,47 +172,63 @@ __host__ __device__ float bisect_one(const float* df, const float* e2f, int n, i
     return 0.5f * (lo + hi);
 }
 
-// Eigenvector of T (d, e) for the eigenvalue nearest `mu`: inverse iteration with
-// Rayleigh-quotient shift updates.  Each sweep factorises T - mu I by Gaussian elimination
+// Inverse iteration on T (d, e).  Each solve factorises T - mu I by Gaussian elimination
 // with partial pivoting fused with the forward substitution, then back-substitutes.  The
 // running rows live in registers; the factor rows (1/pivot, super, second super) and y are
-// strided arrays (element i at [i * stride]).  Returns the final shift.
+// strided arrays (element i at [i * stride]).
+//
+// Seeded start vector of eigenvector k (entries in [0.75, 1.25]).
 template <typename T>
-__host__ __device__ T invit_one(const T* d, const T* e, int n, T mu, T tnorm, int k, T* rdd, T* du, T* du2, T* y,
-                                int stride, int sweeps, int rq_update, int ystride) {
-    const T eps = sizeof(T) == 8 ? (T)1.1102230246251565e-16 : (T)5.9604645e-08f;
-    const T tiny = eps * tnorm + (T)(sizeof(T) == 8 ? 1e-300 : 1e-37);
+__host__ __device__ void invit_start(int n, int k, T* y, int ystride) {
     uint32_t hsh = 2166136261u ^ ((uint32_t)k * 16777619u);
     for (int i = 0; i < n; ++i) {
         hsh = hsh * 1664525u + 1013904223u;
         y[i * ystride] = (T)1 + (T)0.5 * ((T)(hsh >> 8) * (T)(1.0 / 16777216.0) - (T)0.5);
     }
+}
+
+// One inverse-iteration solve y <- (T - mu I)^{-1} y, unnormalised; returns |y|^2.
+template <typename T>
+__host__ __device__ T invit_solve(const T* d, const T* e, int n, T mu, T tiny, T* rdd, T* du, T* du2, T* y,
+                                  int stride, int ystride) {
+    T a = d[0] - mu, b = n > 1 ? e[0] : (T)0, yi = y[0];
+    for (int i = 0; i + 1 < n; ++i) {
+        const T c = e[i], dn = d[i + 1] - mu, f = (i + 2 < n) ? e[i + 1] : (T)0, yn = y[(i + 1) * ystride];
+        if (fabs(a) >= fabs(c)) {
+            if (fabs(a) < tiny) a = a >= (T)0 ? tiny : -tiny;
+            const T r = (T)1 / a, m = c * r;
+            rdd[i * stride] = r; du[i * stride] = b; du2[i * stride] = 0; y[i * ystride] = yi;
+            a = dn - m * b; b = f; yi = yn - m * yi;
+        } else {
+            const T r = (T)1 / c, m = a * r;
+            rdd[i * stride] = r; du[i * stride] = dn; du2[i * stride] = f; y[i * ystride] = yn;
+            a = b - m * dn; b = -m * f; yi = yi - m * yn;
+        }
+    }
+    if (fabs(a) < tiny) a = a >= (T)0 ? tiny : -tiny;
+    T y1 = yi / a, y2 = 0;
+    y[(n - 1) * ystride] = y1;
+    T ss = y1 * y1;
+    for (int i = n - 2; i >= 0; --i) {
+        const T vv = (y[i * ystride] - du[i * stride] * y1 - du2[i * stride] * y2) * rdd[i * stride];
+        y[i * ystride] = vv;
+        ss += vv * vv;
+        y2 = y1;
+        y1 = vv;
+    }
+    return ss;
+}
+
+// Eigenvector of T for the eigenvalue nearest `mu` (optionally with Rayleigh-quotient shift
+// updates); returns the final shift.
+template <typename T>
+__host__ __device__ T invit_one(const T* d, const T* e, int n, T mu, T tnorm, int k, T* rdd, T* du, T* du2, T* y,
+                                int stride, int sweeps, int rq_update, int ystride) {
+    const T eps = sizeof(T) == 8 ? (T)1.1102230246251565e-16 : (T)5.9604645e-08f;
+    const T tiny = eps * tnorm + (T)(sizeof(T) == 8 ? 1e-300 : 1e-37);
+    invit_start<T>(n, k, y, ystride);
     for (int it = 0; it < sweeps; ++it) {
-        T a = d[0] - mu, b = n > 1 ? e[0] : (T)0, yi = y[0];
-        for (int i = 0; i + 1 < n; ++i) {
-            const T c = e[i], dn = d[i + 1] - mu, f = (i + 2 < n) ? e[i + 1] : (T)0, yn = y[(i + 1) * ystride];
-            if (fabs(a) >= fabs(c)) {
-                if (fabs(a) < tiny) a = a >= (T)0 ? tiny : -tiny;
-                const T r = (T)1 / a, m = c * r;
-                rdd[i * stride] = r; du[i * stride] = b; du2[i * stride] = 0; y[i * ystride] = yi;
-                a = dn - m * b; b = f; yi = yn - m * yi;
-            } else {
-                const T r = (T)1 / c, m = a * r;
-                rdd[i * stride] = r; du[i * stride] = dn; du2[i * stride] = f; y[i * ystride] = yn;
-                a = b - m * dn; b = -m * f; yi = yi - m * yn;
-            }
-        }
-        if (fabs(a) < tiny) a = a >= (T)0 ? tiny : -tiny;
-        T y1 = yi / a, y2 = 0;
-        y[(n - 1) * ystride] = y1;
-        T ss = y1 * y1;
-        for (int i = n - 2; i >= 0; --i) {
-            const T vv = (y[i * ystride] - du[i * stride] * y1 - du2[i * stride] * y2) * rdd[i * stride];
-            y[i * ystride] = vv;
-            ss += vv * vv;
-            y2 = y1;
-            y1 = vv;
-        }
+        const T ss = invit_solve<T>(d, e, n, mu, tiny, rdd, du, du2, y, stride, ystride);
         const T sc = (T)1 / sqrt(ss);
         T num = 0, prev = 0, cur = y[0] * sc;
         for (int i = 0; i < n; ++i) {
@@ -225,7 +241,7 @@ __host__ __device__ T invit_one(const T* d, const T* e, int n, T mu, T tnorm, in
             prev = cur;
             cur = next;
         }
-        if (rq_update) mu = num + (T)(k + 1) * eps * tnorm;
+        if (rq_update) mu = num;
     }
     return mu;
 }
@@ -236,32 +252,45 @@ template float invit_one<float>(const float*, const float*, int, float, float, i
 
 namespace {
 
-// Leading `nwant` eigenpairs of T (d, e) in three launches:
+// Leading `nwant` eigenpairs of T (d, e):
 //   k_tri_vec   bisection (FP32 Sturm counts) for the shifts + fixed-shift inverse iteration,
-//               one thread per eigenvalue; a fixed shift keeps the vectors of a cluster
-//               linearly independent (random starts stay mixed inside the cluster);
-//   k_tri_orth  CholQR, twice, of the n x nwant eigenvector block (one CTA) - vectors of
-//               distinct eigenvalues are already orthogonal, so the triangular mixing only
-//               acts inside clusters;
+//               one thread per eigenvalue;
+//   k_tri_runs  runs of tied shifts (consecutive shifts closer than TIE_EPS FP32 ulps of |T|:
+//               a multiple eigenvalue or one FP32 cannot split): equal shifts give equal
+//               factorisations, and inverse iteration then drives every start vector of the run
+//               to the same direction.  The members after the first are computed in order, each
+//               iterate re-orthogonalised (classical Gram-Schmidt, twice) against the earlier
+//               members of its run, as in LAPACK's xSTEIN;
+//   k_tri_orth  one Cholesky QR of the n x nwant eigenvector block (mixes vectors inside
+//               clusters only: vectors of separated eigenvalues are already orthogonal);
 //   k_tri_rq    Rayleigh quotients as eigenvalues.
 // Y is n x nwant with leading dimension ld = nwant + 1 (odd: conflict-free row access).
+constexpr float TIE_EPS = 4.f;
+constexpr float EPS32 = 5.9604645e-08f;
+
+__device__ __forceinline__ bool tied(const float* shift, int k) {
+    return k > 0 && fabsf(shift[k] - shift[k - 1]) <= TIE_EPS * EPS32;
+}
+
 template <typename T>
-__global__ void __launch_bounds__(64) k_tri_vec(const T* __restrict__ d, const T* __restrict__ e, int n, int nwant,
-                                                T* __restrict__ Y, T* __restrict__ scratch,
-                                                float* __restrict__ shift_out) {
+__device__ T tri_norm(const T* d, const T* e, int n) {
+    T t = 0;
+    for (int i = 0; i < n; ++i)
+        t = fmax(t, fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : (T)0) + (i + 1 < n ? fabs(e[i]) : (T)0));
+    return t > (T)0 ? t : (T)1;
+}
+
+// shifts (normalised by |T|) of the nwant largest eigenvalues, one thread each
+template <typename T>
+__global__ void __launch_bounds__(64) k_tri_shift(const T* __restrict__ d, const T* __restrict__ e, int n,
+                                                  int nwant, float* __restrict__ shift_out) {
     __shared__ float df[256], e2f[256];
     __shared__ float bounds[2];
     __shared__ T tn_sh;
     const int tid = threadIdx.x;
-    if (tid == 0) {
-        T t = 0;
-        for (int i = 0; i < n; ++i)
-            t = fmax(t, fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : (T)0) + (i + 1 < n ? fabs(e[i]) : (T)0));
-        tn_sh = t > (T)0 ? t : (T)1;
-    }
+    if (tid == 0) tn_sh = tri_norm(d, e, n);
     __syncthreads();
-    const T tnorm = tn_sh;
-    const double sc = 1.0 / (double)tnorm;     // bisection on T / |T| (FP32 range)
+    const double sc = 1.0 / (double)tn_sh;     // bisection on T / |T| (FP32 range)
     for (int i = tid; i < n; i += blockDim.x) {
         df[i] = (float)((double)d[i] * sc);
         e2f[i] = i + 1 < n ? (float)(((double)e[i] * sc) * ((double)e[i] * sc)) : 0.f;
@@ -278,19 +307,88 @@ __global__ void __launch_bounds__(64) k_tri_vec(const T* __restrict__ d, const T
         bounds[1] = hi + 1e-5f;
     }
     __syncthreads();
+    const int k = blockIdx.x * blockDim.x + tid;
+    if (k < nwant) shift_out[k] = bisect_one(df, e2f, n, n - 1 - k, bounds[0], bounds[1]);
+}
+
+// fixed-shift inverse iteration (3 solves) for every eigenvalue that does not continue a run
+template <typename T>
+__global__ void __launch_bounds__(64) k_tri_vec(const T* __restrict__ d, const T* __restrict__ e, int n, int nwant,
+                                                const float* __restrict__ shift, T* __restrict__ Y) {
+    __shared__ T tn_sh;
+    const int tid = threadIdx.x;
+    if (tid == 0) tn_sh = tri_norm(d, e, n);
+    __syncthreads();
+    const T tnorm = tn_sh;
     const int ld = nwant + 1;
     const int k = blockIdx.x * blockDim.x + tid;
-    if (k >= nwant) return;
-    const float lam = bisect_one(df, e2f, n, n - 1 - k, bounds[0], bounds[1]);
-    shift_out[k] = lam;
-    const T eps = sizeof(T) == 8 ? (T)1.1102230246251565e-16 : (T)5.9604645e-08f;
+    if (k >= nwant || tied(shift, k)) return;
     // elimination rows of this thread in shared memory ([i][thread], conflict-free)
     extern __shared__ __align__(16) unsigned char vsm_raw[];
     T* rdd = reinterpret_cast<T*>(vsm_raw);
     T* du = rdd + (size_t)n * blockDim.x;
     T* du2 = du + (size_t)n * blockDim.x;
-    const T mu = (T)lam * tnorm + (T)(k + 1) * eps * tnorm;
+    // the bisection value itself: an offset that grows with k would move the shifts of a
+    // dense cluster onto neighbouring eigenvalues
+    const T mu = (T)shift[k] * tnorm;
     invit_one<T>(d, e, n, mu, tnorm, k, rdd + tid, du + tid, du2 + tid, Y + k, (int)blockDim.x, 3, 0, ld);
+}
+
+// One CTA per run of tied shifts starting at column blockIdx.x (CTAs whose column does not
+// start a run with at least one follower return at once).  y lives in shared memory; the
+// serial tridiagonal solve runs on thread 0.
+template <typename T>
+__global__ void __launch_bounds__(256) k_tri_runs(const T* __restrict__ d, const T* __restrict__ e, int n,
+                                                  int nwant, const float* __restrict__ shift, T* __restrict__ Y) {
+    const int L = blockIdx.x;
+    if (L >= nwant || tied(shift, L) || L + 1 >= nwant || !tied(shift, L + 1)) return;
+    int end = L + 1;
+    while (end < nwant && tied(shift, end)) ++end;   // members L .. end-1
+    __shared__ T y[256], c[256], rdd[256], du[256], du2[256];
+    __shared__ T red[33];
+    __shared__ T tn_sh;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int ld = nwant + 1;
+    if (tid == 0) tn_sh = tri_norm(d, e, n);
+    __syncthreads();
+    const T tnorm = tn_sh;
+    const T tiny = (T)EPS32 * tnorm + (T)1e-37;
+    // y -= Y[:, L..k-1] (Y[:, L..k-1]^T y), twice, then y /= |y|
+    auto cgs2 = [&](int k) {
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int j = L + tid; j < k; j += nt) {
+                T acc = 0;
+                for (int i = 0; i < n; ++i) acc += Y[(size_t)i * ld + j] * y[i];
+                c[j - L] = acc;
+            }
+            __syncthreads();
+            for (int i = tid; i < n; i += nt) {
+                T acc = y[i];
+                for (int j = L; j < k; ++j) acc -= c[j - L] * Y[(size_t)i * ld + j];
+                y[i] = acc;
+            }
+            __syncthreads();
+        }
+        T ss = 0;
+        for (int i = tid; i < n; i += nt) ss += y[i] * y[i];
+        ss = block_sum(ss, red);
+        const T sc = ss > (T)0 ? (T)1 / sqrt(ss) : (T)0;
+        for (int i = tid; i < n; i += nt) y[i] *= sc;
+        __syncthreads();
+    };
+    for (int k = L + 1; k < end; ++k) {
+        if (tid == 0) invit_start<T>(n, k, y, 1);
+        __syncthreads();
+        const T mu = (T)shift[k] * tnorm;
+        for (int sweep = 0; sweep < 3; ++sweep) {
+            cgs2(k);
+            if (tid == 0) invit_solve<T>(d, e, n, mu, tiny, rdd, du, du2, y, 1, 1);
+            __syncthreads();
+        }
+        cgs2(k);
+        for (int i = tid; i < n; i += nt) Y[(size_t)i * ld + k] = y[i];
+        __syncthreads();
+    }
 }
 
 // Orthonormalise the inverse-iteration vectors by one Cholesky QR of the whole block
@@ -343,9 +441,11 @@ __global__ void __launch_bounds__(256) k_tri_orth(T* __restrict__ Yg, int n, int
     // the pivot itself; the trailing update (warp per row, lanes over columns) uses the
     // unscaled row k; rows are scaled to R after the loop.  Ri[k] keeps 1 / R_kk.
     const int lane = tid & 31, wid = tid >> 5, nwp = blockDim.x >> 5;
+    // the columns are unit vectors: a pivot below 1e-6 marks a (numerically) dependent
+    // column, which is left unscaled instead of being blown up to inf
     for (int k = 0; k < nwant; ++k) {
         const T dk = Gm[k * ld + k];
-        const T ri = dk > (T)0 ? (T)1 / sqrt(dk) : (T)1;
+        const T ri = dk > (T)1e-6 ? (T)1 / sqrt(dk) : (T)1;
         if (tid == 0) Ri[k] = ri;
         const T r2 = ri * ri;
         for (int i = k + 1 + wid; i < nwant; i += nwp) {
@@ -439,8 +539,9 @@ __global__ void k_oa_update(const double* __restrict__ G, const double* __restri
         lt[j] = S[(size_t)j * R + j] / (1.0 - rjj);
     }
     __syncthreads();
-    // pairs closer than sqrt(eps) |lambda|_max are a cluster in every sweep
-    const double gap_floor = 1.5e-8 * fmax(fabs(lam_all[0]), fabs(lam_all[n - 1]));
+    // pairs closer than 16 FP32 ulps of |lambda|_max are a cluster in every sweep: the FP32
+    // stage does not resolve them, and a Newton step across such a gap amplifies its error
+    const double gap_floor = 1e-6 * fmax(fabs(lam_all[0]), fabs(lam_all[n - 1]));
     for (int t = threadIdx.x; t < n * R; t += blockDim.x) {
         const int i = t / R, j = t % R;
         const double rij = (i == j ? 1.0 : 0.0) - G[t];
@@ -556,8 +657,12 @@ rbki_status syev_top_cuda(const double* A, int n, int nwant, double* w, double* 
     const int vthr = 32;
     const size_t vsm = 3 * (size_t)n * vthr * sizeof(float);
     if (vsm > vmax) return set_error(RBKI_E_UNSUPPORTED, "syev: inverse-iteration rows exceed shared memory");
-    k_tri_vec<float><<<(unsigned)cdiv(n, vthr), vthr, vsm, st>>>(L.d, L.e, n, n, L.Yt, L.iiw, L.shift);
+    k_tri_shift<float><<<(unsigned)cdiv(n, 64), 64, 0, st>>>(L.d, L.e, n, n, L.shift);
+    RBKI_LAUNCH_CHECK("k_tri_shift");
+    k_tri_vec<float><<<(unsigned)cdiv(n, vthr), vthr, vsm, st>>>(L.d, L.e, n, n, L.shift, L.Yt);
     RBKI_LAUNCH_CHECK("k_tri_vec");
+    k_tri_runs<float><<<(unsigned)n, 256, 0, st>>>(L.d, L.e, n, n, L.shift, L.Yt);
+    RBKI_LAUNCH_CHECK("k_tri_runs");
     static size_t omax = 0;
     if (!omax) omax = max_dyn_smem(k_tri_orth<float>);
     const size_t osm = (size_t)(n + 2 * n) * (n + 1) * sizeof(float);

@@ -73,6 +73,42 @@ def test_syev(rb, n):
     np.testing.assert_allclose(V.T @ V, np.eye(n), atol=1e-13)
 
 
+def _sym_with_spectrum(lam, seed):
+    g = np.random.default_rng(seed)
+    q, r = np.linalg.qr(g.standard_normal((len(lam), len(lam))))
+    q *= np.sign(np.diag(r))[None, :]
+    return (q * lam[None, :]) @ q.T, q
+
+
+@pytest.mark.parametrize("kind", ["noise_cluster", "multiple", "eps32_spacing"])
+def test_syev_clustered(rb, kind):
+    """Spectra of Z on low-rank + noise data: a few separated leading eigenvalues above a
+    cluster far narrower than FP32 resolution allows to split.  The separated pairs must
+    come out to FP64 accuracy and the cluster as an orthonormal basis of its eigenspace."""
+    n = 120
+    if kind == "noise_cluster":       # the shape of Z for 512^3, R = 20, p = 10, q = 3
+        top = 1.0 / np.arange(1, 21)
+        rest = np.sort(np.random.default_rng(1).uniform(6.5e-4, 7.6e-4, n - 20))[::-1]
+    elif kind == "multiple":          # an exactly repeated eigenvalue
+        top = np.linspace(2.0, 1.0, 10)
+        rest = np.full(n - 10, 1e-3)
+    else:                             # spacing of a few FP32 ulps
+        top = np.linspace(3.0, 2.0, 20)
+        rest = 0.5 + 1e-7 * np.arange(n - 20)[::-1]
+    lam = np.concatenate([top, rest])
+    a, q = _sym_with_spectrum(lam, seed=len(kind))
+    w, V = rb.rbki_syev(torch.from_numpy(a).cuda())
+    w, V = w.cpu().numpy(), V.cpu().numpy()
+    assert np.all(np.isfinite(w)) and np.all(np.isfinite(V))
+    k = len(top)
+    np.testing.assert_allclose(w[:k], top, rtol=1e-12, atol=1e-13 * lam[0])
+    np.testing.assert_allclose(a @ V[:, :k], V[:, :k] * w[None, :k], atol=1e-11 * lam[0])
+    np.testing.assert_allclose(V.T @ V, np.eye(n), atol=1e-12)
+    width = rest.max() - rest.min()
+    assert np.all(np.abs(w[k:] - rest) <= width + 1e-12 * lam[0])
+    assert metrics.max_principal_sine(q[:, k:], V[:, k:]) <= 1e-9
+
+
 def test_mode_basis_span_fp64(rb):
     wl = synth.config_small_fp64(mc=0)
     x = torch.from_numpy(wl.x).cuda()
@@ -123,6 +159,18 @@ def test_tucker_fp64_exact_recovery(rb):
     g = out["core"].cpu().numpy()
     us = [f.cpu().numpy() for f in out["factors"]]
     assert metrics.fnorm(wl.x - rbki.reconstruct(g, us)) / metrics.fnorm(wl.x) <= 1e-12
+
+
+def test_tucker_power_law_256(rb):
+    """512^3 workload's spectrum shape at 256^3 (R = 20, p = 10, q = 3: b = 120, 100 noise
+    eigenvalues in a narrow cluster): FP64 path at the FP64 bar, mixed path within 1%."""
+    wl = synth.config_large(size=256)
+    _, ref = _check_fp64(rb, wl)
+    e_ref = np.sqrt(max(ref["x_norm2"] - ref["core_norm2"], 0.0))
+    x = torch.from_numpy(wl.x).cuda()
+    out = rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec="bf16")
+    e = _err_from_norms(out["norms"])
+    assert np.isfinite(e) and abs(e - e_ref) <= 0.01 * e_ref
 
 
 def test_tucker_fp64_gram_path_equals_tsvd(rb):
