@@ -58,6 +58,13 @@ def make_workload(name, mc, size=0):
     raise ValueError(name)
 
 
+# DRAM bytes (read + write) per X element of one tensor-core Krylov-step launch, from the
+# ncu capture summarised in profiles/k_stream_tc_krylov_448cube_bf16.md (183.4 MB for
+# 448^3 elements); traffic grows in proportion to the elements streamed.  Set to None when
+# k_stream_tc changes until a new capture is taken.
+KRYLOV_TC_DRAM_BYTES_PER_ELEM = (179.947776e6 + 3.468032e6) / 448 ** 3
+
+
 def plan_passes(dims, ranks, p, q):
     """X passes of one step: per Krylov mode 1 sketch + (q+1) Krylov steps; per Gram mode 1;
     plus the first TTM of the core chain."""
@@ -249,7 +256,11 @@ def run_ours(args):
         avg = kms / kcount
         ach = per_launch_bytes / (avg * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(ach / peak, 4), "traffic": None, "kernel": "krylov_step",
+                "frac": round(ach / peak, 4),
+                "traffic": (round(KRYLOV_TC_DRAM_BYTES_PER_ELEM * numel) if prec == "bf16"
+                            and KRYLOV_TC_DRAM_BYTES_PER_ELEM else None),
+                "traffic_unit": "bytes per launch (ncu at 448^3, scaled by elements)",
+                "kernel": "krylov_step",
                 "avg_launch_ms": round(avg, 4), "launches": kcount, "peak_kind": peak_kind}
     breakdown = {}
     for name, cls in (("krylov", rb.PROF_KRYLOV), ("sketch", rb.PROF_SKETCH), ("gram", rb.PROF_GRAM),
