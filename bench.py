@@ -158,13 +158,21 @@ def barrier(world):
 
 
 def allreduce_max(v, world):
+    """Max of a per-rank float over all ranks (NCCL on the GPU, gloo on the CPU)."""
     if world == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_throughput(step_bytes, ms_max, world):
+    """Whole-job GB/s of `world` independent replicas: every rank streams `step_bytes` per
+    step, and the job's step time is the slowest rank's."""
+    return world * step_bytes / (ms_max * 1e-3) / 1e9
 
 
 def oracle_cpu_baseline(wl, max_seconds=30.0):
@@ -245,7 +253,7 @@ def run_ours(args):
     launches = rb.rbki_kernel_launches() - launches0
     ms_local = ev0.elapsed_time(ev1) / args.steps
     ms = allreduce_max(ms_local, world)
-    value = world * step_bytes / (ms * 1e-3) / 1e9
+    value = replica_throughput(step_bytes, ms, world)
 
     kcount, kms = rb.rbki_profile_read(rb.PROF_KRYLOV)
     scount, sms = rb.rbki_profile_read(rb.PROF_SKETCH)
