@@ -284,6 +284,60 @@ def rbki_syev(a, stream=None):
     return w, V
 
 
+PENDING, E_CANCELLED, E_NOTFOUND, E_NOMEM, E_INVAL = 1, -7, -8, -2, -1
+
+
+class RbkiServer:
+    """Served stream (rbki_server_*): continuous batching with device-memory admission.
+    Holds references to each request's input and outputs until its terminal poll."""
+
+    def __init__(self, device: int = 0, mem_budget: int = 1 << 30, max_slots: int = 4):
+        h = C.c_void_p()
+        check(lib().rbki_server_create(int(device), C.c_size_t(int(mem_budget)), int(max_slots), C.byref(h)),
+              "rbki_server_create")
+        self._h = h
+        self._live = {}
+
+    def submit(self, x, ranks, p, q, seed, prec="bf16", out=None):
+        t, prm = make_tensor(x), make_params(ranks, p, q, seed, prec)
+        if out is None:
+            out = alloc_outputs(x.shape, ranks, x.device)
+        o = make_out(out)
+        tk = C.c_uint64(0)
+        check(lib().rbki_submit(self._h, C.byref(t), C.byref(prm), C.byref(o), C.byref(tk)), "rbki_submit")
+        self._live[tk.value] = (x, out)
+        return tk.value, out
+
+    def poll(self, ticket):
+        """(done, status, latency_s): done False while the request is queued or running."""
+        res = C.c_int32(0)
+        lat = C.c_double(0.0)
+        st = lib().rbki_poll(self._h, C.c_uint64(ticket), C.byref(res), C.byref(lat))
+        if st == PENDING:
+            return False, PENDING, None
+        check(st, "rbki_poll")
+        self._live.pop(ticket, None)
+        return True, int(res.value), float(lat.value)
+
+    def cancel(self, ticket):
+        check(lib().rbki_cancel(self._h, C.c_uint64(ticket)), "rbki_cancel")
+
+    def drain(self, timeout_s: float = -1.0):
+        return check(lib().rbki_server_drain(self._h, C.c_double(timeout_s)), "rbki_server_drain")
+
+    def close(self):
+        if self._h is not None:
+            check(lib().rbki_server_destroy(self._h), "rbki_server_destroy")
+            self._h = None
+            self._live.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
 PROF_KRYLOV, PROF_SKETCH, PROF_GRAM, PROF_TTM, PROF_STAGE = range(5)
 
 

@@ -370,7 +370,7 @@ struct StreamPool {
 static std::mutex g_pool_mu;
 static StreamPool g_pools[64];
 
-static rbki_status mode_streams(cudaStream_t* out, int n) {
+static rbki_status pool_streams(cudaStream_t* out, int n) {
     int dev = 0;
     RBKI_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return set_error(RBKI_E_UNSUPPORTED, "device index");
@@ -385,7 +385,7 @@ static rbki_status mode_streams(cudaStream_t* out, int n) {
     return RBKI_OK;
 }
 
-rbki_status run_tucker(Plan& pl, const rbki_tucker_out* out, cudaStream_t st) {
+rbki_status run_tucker(Plan& pl, const rbki_tucker_out* out, cudaStream_t st, const cudaStream_t* mode_streams) {
     double* norms = out->norms ? out->norms : pl.scal;
     RBKI_CUDA_TRY(cudaMemsetAsync(pl.err, 0, sizeof(int32_t), st));
     int tok = prof_begin(RBKI_PROF_STAGE, st);
@@ -401,7 +401,11 @@ rbki_status run_tucker(Plan& pl, const rbki_tucker_out* out, cudaStream_t st) {
     const bool concurrent = pl.N > 1 && !(pl.flags & RBKI_FLAG_SERIAL_MODES);
     if (concurrent) {
         cudaStream_t ms[RBKI_MAX_ORDER];
-        RBKI_TRY(mode_streams(ms, pl.N));
+        if (mode_streams) {
+            for (int n = 0; n < pl.N; ++n) ms[n] = mode_streams[n];
+        } else {
+            RBKI_TRY(pool_streams(ms, pl.N));
+        }
         cudaEvent_t fork, join[RBKI_MAX_ORDER];
         RBKI_CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
         RBKI_CUDA_TRY(cudaEventRecord(fork, st));

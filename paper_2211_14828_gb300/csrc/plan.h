@@ -66,7 +66,11 @@ rbki_status tr_contract_cuda(const double* Z, const double* U, int r0, int64_t R
 size_t dtype_size(int dt);
 rbki_status validate_tensor(const rbki_tensor* X);
 size_t host_io_bytes(const Plan& pl);
-rbki_status run_tucker(Plan& pl, const rbki_tucker_out* out, cudaStream_t st);
+rbki_status make_plan(const rbki_tensor* X, const rbki_params* prm, Plan& pl);
+void carve(Plan& pl, void* ws);    // ws == nullptr: only measures pl.ws_bytes
+// mode_streams: N streams for the concurrent per-mode chains (nullptr: the per-device pool)
+rbki_status run_tucker(Plan& pl, const rbki_tucker_out* out, cudaStream_t st,
+                       const cudaStream_t* mode_streams = nullptr);
 rbki_status run_tucker_host_io(Plan& pl, const rbki_tensor* X, const rbki_tucker_out* out,
                                void* workspace, cudaStream_t st);
 

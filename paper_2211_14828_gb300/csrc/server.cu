@@ -1,0 +1,333 @@
+// Served stream of rBKI-TK requests: continuous batching with device-memory admission.
+//
+// One server owns, on one device:
+//   * an arena of `mem_budget` bytes (one cudaMalloc at creation) from which every admitted
+//     request's workspace (its Krylov basis, products, eigensolver scratch, ...) is carved;
+//   * `max_slots` slots, each a host thread with its own stream and its own per-mode
+//     streams.  A slot takes the oldest queued request as soon as the request's workspace
+//     fits in the arena, runs Algorithms 1-2 on its streams and waits for the device.
+//     Requests that arrive while others run are admitted as slots and memory free up,
+//     and their kernels overlap on the GPU with the ones already there.
+//
+// Admission is FIFO: a request that does not fit waits at the head of the queue until
+// enough memory is released (no starvation of large requests).  A request whose
+// workspace exceeds the whole budget is refused at submission (RBKI_E_NOMEM).
+//
+// The result of a request does not depend on what else runs: every reduction in the
+// path has a fixed order and the tensor-core kernels' grid depends only on the shape, so
+// a request computes the same bits alone and in the mix.
+//
+// Latency is measured on the host from rbki_submit to the moment the slot observes the
+// request's last kernel complete.
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "plan.h"
+
+namespace rbki {
+namespace {
+
+double now_s() {
+    using namespace std::chrono;
+    return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+// First-fit sub-allocator over [0, size) with coalescing; offsets 256-byte aligned.
+class Arena {
+public:
+    explicit Arena(size_t size) { free_[0] = size; }
+    bool alloc(size_t bytes, size_t* off) {
+        bytes = (bytes + 255) & ~(size_t)255;
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                *off = it->first;
+                const size_t rest = it->second - bytes, start = it->first + bytes;
+                free_.erase(it);
+                if (rest) free_[start] = rest;
+                used_[*off] = bytes;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off) {
+        auto u = used_.find(off);
+        if (u == used_.end()) return;
+        size_t start = off, len = u->second;
+        used_.erase(u);
+        auto next = free_.lower_bound(start);
+        if (next != free_.end() && next->first == start + len) {
+            len += next->second;
+            next = free_.erase(next);
+        }
+        if (next != free_.begin()) {
+            auto prev = std::prev(next);
+            if (prev->first + prev->second == start) {
+                prev->second += len;
+                return;
+            }
+        }
+        free_[start] = len;
+    }
+
+private:
+    std::map<size_t, size_t> free_, used_;
+};
+
+enum class State { QUEUED, RUNNING, DONE };
+
+struct Request {
+    uint64_t ticket = 0;
+    rbki_tensor X{};
+    rbki_params prm{};
+    rbki_tucker_out out{};
+    size_t ws_bytes = 0;
+    State state = State::QUEUED;
+    bool cancel = false;
+    rbki_status result = RBKI_PENDING;
+    double t_submit = 0, t_done = 0;
+};
+
+struct Slot {
+    cudaStream_t st = nullptr;
+    cudaStream_t ms[RBKI_MAX_ORDER] = {nullptr};
+};
+
+}  // namespace
+}  // namespace rbki
+
+using namespace rbki;
+
+struct rbki_server {
+    int device = 0;
+    size_t budget = 0;
+    int nslots = 0;
+    char* arena_base = nullptr;
+    Arena* arena = nullptr;
+    std::mutex mu;
+    std::condition_variable cv_work;   // queue / memory changes (slots wait here)
+    std::condition_variable cv_done;   // a request finished (drain waits here)
+    std::deque<Request*> queue;
+    std::unordered_map<uint64_t, Request*> reqs;   // every request not yet retired by a poll
+    uint64_t next_ticket = 1;
+    int running = 0;
+    bool stopping = false;
+    std::vector<Slot> slots;
+    std::vector<std::thread> workers;
+};
+
+namespace {
+
+// Runs one admitted request on a slot; returns its status.
+rbki_status run_request(rbki_server* s, Slot& slot, Request* r, size_t off) {
+    Plan pl;
+    RBKI_TRY(make_plan(&r->X, &r->prm, pl));
+    carve(pl, s->arena_base + off);
+    pl.xin = r->X.data;
+    rbki_status rs = run_tucker(pl, &r->out, slot.st, slot.ms);
+    cudaError_t e = cudaStreamSynchronize(slot.st);
+    if (rs < 0) return rs;
+    if (e != cudaSuccess) return set_cuda_error(e, "server request");
+    int32_t err = 0;
+    e = cudaMemcpy(&err, pl.err, sizeof(err), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return set_cuda_error(e, "server error word");
+    if (err) return set_error(RBKI_E_TIMEOUT, "a bounded wait inside a kernel expired");
+    return rs;
+}
+
+void slot_main(rbki_server* s, int id) {
+    cudaSetDevice(s->device);
+    Slot& slot = s->slots[id];
+    std::unique_lock<std::mutex> lk(s->mu);
+    for (;;) {
+        size_t off = 0;
+        s->cv_work.wait(lk, [&] {
+            return s->stopping || (!s->queue.empty() && s->arena->alloc(s->queue.front()->ws_bytes, &off));
+        });
+        if (s->stopping) return;
+        Request* r = s->queue.front();
+        s->queue.pop_front();
+        r->state = State::RUNNING;
+        ++s->running;
+        lk.unlock();
+        const rbki_status rs = run_request(s, slot, r, off);
+        const double t = now_s();
+        lk.lock();
+        s->arena->release(off);
+        --s->running;
+        r->t_done = t;
+        r->result = r->cancel ? RBKI_E_CANCELLED : rs;
+        r->state = State::DONE;
+        s->cv_work.notify_all();
+        s->cv_done.notify_all();
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+rbki_status rbki_server_create(int32_t device, size_t mem_budget, int32_t max_slots, rbki_server** out) {
+    if (!out) return set_error(RBKI_E_INVAL, "out is NULL");
+    *out = nullptr;
+    if (max_slots < 1 || max_slots > 64) return set_error(RBKI_E_INVAL, "max_slots must be in [1, 64]");
+    if (mem_budget < 4096) return set_error(RBKI_E_INVAL, "mem_budget too small");
+    int ndev = 0;
+    RBKI_CUDA_TRY(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return set_error(RBKI_E_INVAL, "no such device");
+    int prev = 0;
+    RBKI_CUDA_TRY(cudaGetDevice(&prev));
+    RBKI_CUDA_TRY(cudaSetDevice(device));
+    rbki_server* s = new rbki_server();
+    s->device = device;
+    s->budget = mem_budget;
+    s->nslots = max_slots;
+    cudaError_t e = cudaMalloc(&s->arena_base, mem_budget);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete s;
+        cudaSetDevice(prev);
+        return set_error(RBKI_E_NOMEM, "server: cannot allocate mem_budget on the device");
+    }
+    s->arena = new Arena(mem_budget);
+    s->slots.resize(max_slots);
+    for (auto& sl : s->slots) {
+        e = cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking);
+        for (int n = 0; n < RBKI_MAX_ORDER && e == cudaSuccess; ++n)
+            e = cudaStreamCreateWithFlags(&sl.ms[n], cudaStreamNonBlocking);
+        if (e != cudaSuccess) break;
+    }
+    if (e != cudaSuccess) {
+        rbki_server_destroy(s);
+        cudaSetDevice(prev);
+        return set_cuda_error(e, "server streams");
+    }
+    for (int i = 0; i < max_slots; ++i) s->workers.emplace_back(slot_main, s, i);
+    cudaSetDevice(prev);
+    *out = s;
+    return RBKI_OK;
+}
+
+rbki_status rbki_submit(rbki_server* s, const rbki_tensor* X, const rbki_params* prm, const rbki_tucker_out* out,
+                        uint64_t* ticket) {
+    if (!s || !ticket) return set_error(RBKI_E_INVAL, "server / ticket is NULL");
+    if (!out || !out->core) return set_error(RBKI_E_INVAL, "out->core is NULL");
+    Plan pl;
+    RBKI_TRY(make_plan(X, prm, pl));
+    if (prm->flags & RBKI_FLAG_HOST_IO) return set_error(RBKI_E_UNSUPPORTED, "server requests use device buffers");
+    for (int n = 0; n < pl.N; ++n)
+        if (!out->factors[n]) return set_error(RBKI_E_INVAL, "out->factors[n] is NULL");
+    carve(pl, nullptr);
+    if (pl.ws_bytes > s->budget) return set_error(RBKI_E_NOMEM, "request workspace exceeds the server budget");
+    Request* r = new Request();
+    r->X = *X;
+    r->prm = *prm;
+    r->out = *out;
+    r->ws_bytes = pl.ws_bytes;
+    r->t_submit = now_s();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->stopping) {
+            delete r;
+            return set_error(RBKI_E_BUSY, "server is shutting down");
+        }
+        r->ticket = s->next_ticket++;
+        s->reqs[r->ticket] = r;
+        s->queue.push_back(r);
+        *ticket = r->ticket;
+    }
+    s->cv_work.notify_all();
+    return RBKI_OK;
+}
+
+rbki_status rbki_poll(rbki_server* s, uint64_t ticket, rbki_status* result, double* latency_s) {
+    if (!s) return set_error(RBKI_E_INVAL, "server is NULL");
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return set_error(RBKI_E_NOTFOUND, "unknown or already retired ticket");
+    Request* r = it->second;
+    if (r->state != State::DONE) {
+        if (result) *result = RBKI_PENDING;
+        return RBKI_PENDING;
+    }
+    if (result) *result = r->result;
+    if (latency_s) *latency_s = r->t_done - r->t_submit;
+    s->reqs.erase(it);
+    delete r;
+    return RBKI_OK;
+}
+
+rbki_status rbki_cancel(rbki_server* s, uint64_t ticket) {
+    if (!s) return set_error(RBKI_E_INVAL, "server is NULL");
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        auto it = s->reqs.find(ticket);
+        if (it == s->reqs.end()) return set_error(RBKI_E_NOTFOUND, "unknown or already retired ticket");
+        Request* r = it->second;
+        if (r->state == State::QUEUED) {
+            for (auto q = s->queue.begin(); q != s->queue.end(); ++q)
+                if (*q == r) {
+                    s->queue.erase(q);
+                    break;
+                }
+            r->state = State::DONE;
+            r->result = RBKI_E_CANCELLED;
+            r->t_done = now_s();
+        } else if (r->state == State::RUNNING) {
+            r->cancel = true;   // its kernels finish; the result is reported as cancelled
+        }
+    }
+    s->cv_work.notify_all();
+    s->cv_done.notify_all();
+    return RBKI_OK;
+}
+
+rbki_status rbki_server_drain(rbki_server* s, double timeout_s) {
+    if (!s) return set_error(RBKI_E_INVAL, "server is NULL");
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto idle = [&] { return s->queue.empty() && s->running == 0; };
+    if (timeout_s < 0) {
+        s->cv_done.wait(lk, idle);
+        return RBKI_OK;
+    }
+    if (!s->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), idle))
+        return set_error(RBKI_E_TIMEOUT, "drain: requests still queued or running");
+    return RBKI_OK;
+}
+
+rbki_status rbki_server_destroy(rbki_server* s) {
+    if (!s) return set_error(RBKI_E_INVAL, "server is NULL");
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stopping = true;
+        for (Request* r : s->queue) {
+            r->state = State::DONE;
+            r->result = RBKI_E_CANCELLED;
+        }
+        s->queue.clear();
+    }
+    s->cv_work.notify_all();
+    for (auto& w : s->workers) w.join();   // running requests finish first
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(s->device);
+    for (auto& sl : s->slots) {
+        if (sl.st) cudaStreamDestroy(sl.st);
+        for (auto m : sl.ms)
+            if (m) cudaStreamDestroy(m);
+    }
+    if (s->arena_base) cudaFree(s->arena_base);
+    cudaSetDevice(prev);
+    for (auto& kv : s->reqs) delete kv.second;
+    delete s->arena;
+    delete s;
+    return RBKI_OK;
+}
+
+}  // extern "C"

@@ -62,3 +62,16 @@ def test_validation_without_gpu(L):
     st = L.rbki_tucker(ctypes.byref(t), ctypes.byref(prm), ctypes.c_void_p(16), ctypes.c_size_t(8),
                        ctypes.byref(out), None)
     assert st == B.E_NOMEM
+
+
+def test_server_argument_checks_without_gpu(L):
+    """Server entry points reject bad arguments before touching a device."""
+    h = ctypes.c_void_p()
+    assert L.rbki_server_create(0, ctypes.c_size_t(1 << 20), 0, ctypes.byref(h)) == -1      # max_slots < 1
+    assert L.rbki_server_create(0, ctypes.c_size_t(16), 2, ctypes.byref(h)) == -1           # budget too small
+    res = ctypes.c_int32(0)
+    lat = ctypes.c_double(0)
+    assert L.rbki_poll(None, ctypes.c_uint64(1), ctypes.byref(res), ctypes.byref(lat)) == -1
+    assert L.rbki_cancel(None, ctypes.c_uint64(1)) == -1
+    assert L.rbki_server_drain(None, ctypes.c_double(0.0)) == -1
+    assert L.rbki_server_destroy(None) == -1
