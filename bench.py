@@ -35,7 +35,11 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["tucker512", "tucker64", "video", "htr"], default="tucker512")
+    ap.add_argument("--workload", choices=["tucker512", "tucker64", "video", "htr", "serve"], default="tucker512")
+    ap.add_argument("--requests", type=int, default=4096, help="served stream length (--workload serve)")
+    ap.add_argument("--slots", type=int, default=16, help="server slots (--workload serve)")
+    ap.add_argument("--fp64-requests", type=int, default=256,
+                    help="prefix of the served stream also run on the FP64 GPU path (--workload serve)")
     ap.add_argument("--prec", choices=["bf16", "fp64"], default="bf16")
     ap.add_argument("--size", type=int, default=0,
                     help="cube edge for tucker512 (0 = 512); smaller cases for profiler captures")
@@ -353,6 +357,29 @@ def run_reference(args):
         return
     from oracle import philox, rbki
     from oracle.tensor import unfold
+    if args.workload == "serve":
+        import synth
+        reqs = synth.serve_stream(n_requests=args.requests, seed=5000)
+        for r in reqs[:args.warmup]:
+            wl = synth.serve_request_tensor(r, dtype=np.float64)
+            rbki.rbki_tucker(wl.x, wl.ranks, wl.p, wl.q, wl.seed)
+        t0 = time.perf_counter()
+        for r in reqs[args.warmup:args.warmup + args.steps]:
+            wl = synth.serve_request_tensor(r, dtype=np.float64)
+            rbki.rbki_tucker(wl.x, wl.ranks, wl.p, wl.q, wl.seed)
+        dt = time.perf_counter() - t0
+        value = args.steps / dt
+        print(json.dumps({
+            "metric": "served rBKI-TK solves/s (closed loop; p50/p99 latency under Poisson arrivals)",
+            "value": round(value, 3), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 2), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": "serve: requests of the served stream, one per step, solved one after another"},
+            "cpu_baseline": {"value": round(value, 3), "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"FP64 NumPy oracle, {args.steps} requests of the stream"},
+            "e2e": {"value": round(value, 3), "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }))
+        return
     wl = make_workload(args.workload, 0, args.size)
     x = np.asarray(wl.x, dtype=np.float64)
     dims = list(x.shape)
@@ -393,10 +420,167 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def serve_passes(dims, ranks, p, q):
+    """X passes of one served request (same rule as `plan_passes`)."""
+    return plan_passes(dims, ranks, p, q)[0]
+
+
+def _serve_closed_loop(rb, srv, items, outs, prec):
+    """Submit every request at once and wait for all: (seconds, latencies, statuses)."""
+    t0 = time.perf_counter()
+    tickets = [srv.submit(x, rk, p, q, sd, prec=prec, out=o)[0] for (x, rk, p, q, sd), o in zip(items, outs)]
+    pending = set(tickets)
+    lat, status = {}, {}
+    while pending:
+        for t in list(pending):
+            ok, st, l = srv.poll(t)
+            if ok:
+                pending.discard(t)
+                lat[t], status[t] = l, st
+        if pending:
+            time.sleep(2e-4)
+    return time.perf_counter() - t0, [lat[t] for t in tickets], [status[t] for t in tickets]
+
+
+def _serve_poisson(rb, srv, items, outs, prec, rate, seed):
+    """Open loop: request i is submitted at its Poisson arrival time; latency = completion
+    - arrival (any lateness of the submitter counts against the server)."""
+    import numpy as np
+    g = np.random.default_rng(seed)
+    arrivals = np.cumsum(g.exponential(1.0 / rate, len(items)))
+    t0 = time.perf_counter()
+    pending, lat, i = {}, [], 0
+    while i < len(items) or pending:
+        now = time.perf_counter() - t0
+        while i < len(items) and arrivals[i] <= now:
+            x, rk, p, q, sd = items[i]
+            t, _ = srv.submit(x, rk, p, q, sd, prec=prec, out=outs[i])
+            pending[t] = (arrivals[i], now)
+            i += 1
+        for t in list(pending):
+            ok, st, l = srv.poll(t)
+            if ok:
+                arr, sub = pending.pop(t)
+                lat.append((sub - arr) + l)
+        time.sleep(1e-4)
+    return time.perf_counter() - t0, lat
+
+
+def run_serve(args):
+    """Served stream: --requests rBKI-TK requests (3rd order, dims in [32, 256], ranks in
+    [4, 32], q in {1, 2, 3}, p = 5, SNR in [5, 25] dB, BF16 products) through the server.
+    value = closed-loop solves/s; p50/p99 latency under Poisson arrivals at 0.5/0.8/0.95 of
+    that rate; the FP64 GPU path on a prefix of the same stream for the matched-error check."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_2211_14828_gb300 as rb
+    from paper_2211_14828_gb300 import _binding as B
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:
+        raise SystemExit("--workload serve runs on one GPU")
+    torch.cuda.set_device(0)
+    reqs = synth.serve_stream(n_requests=args.requests, seed=5000)
+    items, outs, x32 = [], [], []
+    numel_passes = 0
+    for i, r in enumerate(reqs):
+        x, rk, p, q, sd = synth.serve_request_device(r)
+        items.append((x, rk, p, q, sd))
+        outs.append(B.alloc_outputs(x.shape, rk, x.device))
+        numel_passes += serve_passes(x.shape, rk, p, q) * x.numel()
+        if i < args.fp64_requests:
+            x32.append(x.float())
+    torch.cuda.synchronize()
+    budget = 8 << 30
+    launches0 = rb.rbki_kernel_launches()
+    with rb.RbkiServer(0, mem_budget=budget, max_slots=args.slots) as srv:
+        nw = min(len(items), max(args.warmup, 1) * args.slots)
+        _serve_closed_loop(rb, srv, items[:nw], outs[:nw], "bf16")
+        clocks = ClockSampler()
+        clocks.start()
+        launches0 = rb.rbki_kernel_launches()
+        torch.cuda.synchronize()
+        secs, lat, status = _serve_closed_loop(rb, srv, items, outs, "bf16")
+        torch.cuda.synchronize()
+        launches = rb.rbki_kernel_launches() - launches0
+        clk = clocks.stop()
+        assert all(s == 0 for s in status), "served request failed"
+        sat = len(items) / secs
+        errs_mixed = []
+        for o in outs:
+            n = o["norms"].cpu().numpy()
+            errs_mixed.append(float(np.sqrt(max(n[0] - n[1], 0.0) / n[0])))
+        latency = {"closed_loop": {"p50_ms": round(1e3 * float(np.percentile(lat, 50)), 3),
+                                   "p99_ms": round(1e3 * float(np.percentile(lat, 99)), 3)}}
+        for rho in (0.5, 0.8, 0.95):
+            t, l = _serve_poisson(rb, srv, items, outs, "bf16", rho * sat, seed=int(rho * 1000))
+            latency[f"poisson_rho_{rho}"] = {"offered_per_s": round(rho * sat, 1),
+                                             "achieved_per_s": round(len(items) / t, 1),
+                                             "p50_ms": round(1e3 * float(np.percentile(l, 50)), 3),
+                                             "p99_ms": round(1e3 * float(np.percentile(l, 99)), 3)}
+        # FP64 GPU path on a prefix of the same stream
+        f64 = None
+        if x32:
+            its = [(x32[i],) + items[i][1:] for i in range(len(x32))]
+            o64 = [B.alloc_outputs(x.shape, it[1], x.device) for x, it in zip(x32, its)]
+            secs64, lat64, st64 = _serve_closed_loop(rb, srv, its, o64, "fp64")
+            e64 = []
+            for o in o64:
+                n = o["norms"].cpu().numpy()
+                e64.append(float(np.sqrt(max(n[0] - n[1], 0.0) / n[0])))
+            dev = [abs(a - b) / b for a, b in zip(errs_mixed[:len(e64)], e64)]
+            f64 = {"requests": len(its), "solves_per_s": round(len(its) / secs64, 1),
+                   "p50_ms": round(1e3 * float(np.percentile(lat64, 50)), 3),
+                   "p99_ms": round(1e3 * float(np.percentile(lat64, 99)), 3),
+                   "mixed_solves_per_s_same_prefix": None,
+                   "max_rel_err_dev_mixed_vs_fp64": max(dev), "all_within_1pct": bool(max(dev) <= 0.01)}
+            secs_m, _, _ = _serve_closed_loop(rb, srv, items[:len(its)], outs[:len(its)], "bf16")
+            f64["mixed_solves_per_s_same_prefix"] = round(len(its) / secs_m, 1)
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = serve_cpu_baseline(reqs)
+    line = {
+        "metric": "served rBKI-TK solves/s (closed loop; p50/p99 latency under Poisson arrivals)",
+        "value": round(sat, 2), "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": args.warmup,
+        "ms_per_step": round(secs * 1e3, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": f"serve: {len(items)} requests, dims U[32,256]^3, ranks U[4,32], p=5, q in {{1,2,3}}, "
+                               f"SNR U[5,25] dB, BF16 products", "slots": args.slots, "budget_bytes": budget,
+                   "x_pass_bytes": int(2 * numel_passes),
+                   "x_pass_gbs": round(2 * numel_passes / secs / 1e9, 2),
+                   "l2": "requests are mostly smaller than L2; throughput is latency-bound"},
+        "latency": latency, "fp64_compare": f64,
+        "rel_err_mixed": {"median": float(np.median(errs_mixed)), "max": float(np.max(errs_mixed))},
+        "e2e": None, "gpu_launches": int(launches), "clocks": clk, "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+
+
+def serve_cpu_baseline(reqs, max_seconds=20.0):
+    """The FP64 oracle on the host cores over a bounded prefix of the served stream."""
+    import numpy as np
+    import synth
+    from oracle import rbki
+    t0 = time.perf_counter()
+    n = 0
+    for r in reqs:
+        wl = synth.serve_request_tensor(r, dtype=np.float64)
+        rbki.rbki_tucker(wl.x, wl.ranks, wl.p, wl.q, wl.seed)
+        n += 1
+        if time.perf_counter() - t0 > max_seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": round(n / dt, 3), "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"FP64 NumPy oracle, the first {n} requests of the stream ({dt:.1f} s, NumPy-generated "
+                      f"tensors of the same recipe)"}
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

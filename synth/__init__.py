@@ -26,7 +26,7 @@ __all__ = [
     "rng", "haar_factor", "dct_factor", "tucker_full", "tr_full",
     "add_noise_snr", "power_functional", "gaussian_tucker",
     "Workload", "config_small_fp64", "config_large", "config_video",
-    "config_htr", "serve_stream", "tr_init_cores",
+    "config_htr", "serve_stream", "serve_request_tensor", "serve_request_device", "tr_init_cores",
 ]
 
 
@@ -194,6 +194,27 @@ def serve_stream(n_requests: int = 4096, seed: int = 5000, dim_lo: int = 32, dim
         snr = float(g.uniform(snr_lo, snr_hi))
         reqs.append(dict(id=i, dims=dims, ranks=ranks, p=p, q=q, snr_db=snr, seed=seed * 10 + i))
     return reqs
+
+
+def serve_request_device(req, device="cuda", dtype=None):
+    """Device-side version of `serve_request_tensor` for large streams: the same recipe
+    (Gaussian core and Haar factors drawn with NumPy from the request's seed; the dense
+    tensor formed on the device; Gaussian noise from torch's generator seeded with the
+    request's seed, scaled to the request's SNR by the realised norms).  The noise draws
+    differ from the NumPy version's, so values are not identical to it.  Returns
+    (x on `device` in `dtype` (default bfloat16), ranks, p, q, omega_seed)."""
+    import torch
+    g = rng(req["seed"])
+    c = torch.from_numpy(g.standard_normal(req["ranks"]).astype(np.float32)).to(device)
+    facs = [torch.from_numpy(haar_factor(g, i, r).astype(np.float32)).to(device)
+            for i, r in zip(req["dims"], req["ranks"])]
+    clean = torch.einsum("abc,ia,jb,kc->ijk", c, facs[0], facs[1], facs[2])
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(req["seed"]))
+    noise = torch.randn(clean.shape, generator=gen, device=device, dtype=torch.float32)
+    lam = torch.linalg.vector_norm(clean) / (torch.linalg.vector_norm(noise) * 10.0 ** (req["snr_db"] / 20.0))
+    x = (clean + lam * noise).to(dtype or torch.bfloat16).contiguous()
+    return x, list(req["ranks"]), req["p"], req["q"], req["seed"] + 17
 
 
 def serve_request_tensor(req, dtype=np.float32) -> Workload:
