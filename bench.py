@@ -36,6 +36,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["tucker512", "tucker64", "video", "htr", "serve"], default="tucker512")
+    ap.add_argument("--inflight", type=int, default=3,
+                    help="decompositions in flight on separate streams (throughput mode); 1 = one at a time")
     ap.add_argument("--requests", type=int, default=4096, help="served stream length (--workload serve)")
     ap.add_argument("--slots", type=int, default=16, help="server slots (--workload serve)")
     ap.add_argument("--fp64-requests", type=int, default=256,
@@ -225,12 +227,41 @@ def run_ours(args):
     prec = args.prec
     x = torch.from_numpy(wl.x).cuda()
     stream = torch.cuda.current_stream()
-    out = rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec=prec)
-    ws = out["workspace"]
+    # K decompositions in flight: stream j runs steps j, j+K, ...; each has its own workspace
+    # and outputs (the steps are independent decompositions of the input)
+    K = max(1, args.inflight)
+    streams = [torch.cuda.Stream() for _ in range(K)]
+    outs = []
+    for j in range(K):
+        with torch.cuda.stream(streams[j]):
+            outs.append(rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec=prec, stream=streams[j]))
     torch.cuda.synchronize()
-    for _ in range(max(0, args.warmup - 1)):
-        rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec=prec, workspace=ws, out=out)
+    out = outs[0]
+
+    def run_steps(nsteps):
+        ev = torch.cuda.Event()
+        ev.record(stream)
+        for j in range(K):
+            streams[j].wait_event(ev)
+        for t in range(nsteps):
+            j = t % K
+            o = outs[j]
+            rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec=prec, workspace=o["workspace"], out=o,
+                           stream=streams[j])
+        for j in range(K):
+            e = torch.cuda.Event()
+            e.record(streams[j])
+            stream.wait_event(e)
+
+    run_steps(max(0, args.warmup - 1) * K + K)
     torch.cuda.synchronize()
+    # one decomposition alone (latency)
+    e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e_a.record(stream)
+    rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec=prec, workspace=out["workspace"], out=out, stream=stream)
+    e_b.record(stream)
+    torch.cuda.synchronize()
+    single_ms = e_a.elapsed_time(e_b)
 
     uuid = None
     try:
@@ -247,8 +278,7 @@ def run_ours(args):
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    for _ in range(args.steps):
-        rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec=prec, workspace=ws, out=out)
+    run_steps(args.steps)
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier(world)
@@ -335,6 +365,7 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": f"{args.workload}: {'x'.join(map(str, dims))} {wl.x.dtype}, ranks {wl.ranks}, "
                                    f"p={wl.p}, q={wl.q}, {prec} products",
+                       "inflight": K, "single_decomposition_ms": round(single_ms, 4),
                        "passes_per_step": passes, "krylov_steps_per_step": krylov_steps,
                        "bytes_per_step": step_bytes, "l2": "inputs larger than L2 (no flush)",
                        "parallelism": f"replicas x{world}"},

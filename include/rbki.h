@@ -140,9 +140,15 @@ typedef struct rbki_server rbki_server;
  * own device memory pool of mem_budget bytes once, here. */
 rbki_status rbki_server_create(int32_t device, size_t mem_budget, int32_t max_slots,
                                rbki_server** out);
-/* Queues one rBKI-TK request.  X and out must stay valid until a terminal poll. */
+/* Queues one rBKI-TK request (device buffers; RBKI_FLAG_HOST_IO is refused).  X and out
+ * must stay valid until a terminal poll.  The server runs requests on its own streams: work
+ * already queued on `after_stream` (a cudaStream_t as void*, typically the stream that
+ * produced X) is waited for before the request's first kernel - an event is recorded on
+ * it here.  Pass NULL only when X is complete on the device (e.g. after a synchronize).
+ * Refused at submission: invalid arguments (RBKI_E_INVAL), a workspace larger than the
+ * whole budget (RBKI_E_NOMEM), a server shutting down (RBKI_E_BUSY). */
 rbki_status rbki_submit(rbki_server* s, const rbki_tensor* X, const rbki_params* prm,
-                        const rbki_tucker_out* out, uint64_t* ticket);
+                        const rbki_tucker_out* out, void* after_stream, uint64_t* ticket);
 /* Non-blocking.  *result = RBKI_PENDING while running, else the request's final status;
  * *latency_s = completion - submission (seconds) once finished. */
 rbki_status rbki_poll(rbki_server* s, uint64_t ticket, rbki_status* result, double* latency_s);

@@ -61,7 +61,7 @@ def lib():
             "rbki_htr_workspace": (st, [vp, vp, vp, sz]),
             "rbki_htr": (st, [vp, vp, vp, vp, C.c_int32, C.c_double, vp, vp, vp, vp, C.c_size_t, vp]),
             "rbki_server_create": (st, [C.c_int32, C.c_size_t, C.c_int32, C.POINTER(vp)]),
-            "rbki_submit": (st, [vp, vp, vp, vp, C.POINTER(C.c_uint64)]),
+            "rbki_submit": (st, [vp, vp, vp, vp, vp, C.POINTER(C.c_uint64)]),
             "rbki_poll": (st, [vp, C.c_uint64, C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
             "rbki_cancel": (st, [vp, C.c_uint64]),
             "rbki_server_drain": (st, [vp, C.c_double]),
@@ -298,13 +298,18 @@ class RbkiServer:
         self._h = h
         self._live = {}
 
-    def submit(self, x, ranks, p, q, seed, prec="bf16", out=None):
+    def submit(self, x, ranks, p, q, seed, prec="bf16", out=None, after_stream=None):
+        """Queues a request; its kernels wait for the work already queued on `after_stream`
+        (default: torch's current stream, where x and out were made)."""
+        torch = _torch()
         t, prm = make_tensor(x), make_params(ranks, p, q, seed, prec)
         if out is None:
             out = alloc_outputs(x.shape, ranks, x.device)
         o = make_out(out)
         tk = C.c_uint64(0)
-        check(lib().rbki_submit(self._h, C.byref(t), C.byref(prm), C.byref(o), C.byref(tk)), "rbki_submit")
+        st = after_stream if after_stream is not None else torch.cuda.current_stream()
+        check(lib().rbki_submit(self._h, C.byref(t), C.byref(prm), C.byref(o), stream_ptr(st), C.byref(tk)),
+              "rbki_submit")
         self._live[tk.value] = (x, out)
         return tk.value, out
 

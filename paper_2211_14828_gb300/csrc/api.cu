@@ -350,7 +350,10 @@ rbki_status core_chain(const Plan& pl, double* const* factors, double* core, cud
             src_dtype = RBKI_F32;
             continue;
         }
-        RBKI_TRY(ttm_cuda(v, factors[m], R, R, dst, RBKI_F64, pl.mixed, st));
+        if (t > 0 && R <= 32 && (src_dtype == RBKI_F64 || src_dtype == RBKI_F32))
+            RBKI_TRY(ttm_small_cuda(v, factors[m], R, R, dst, pl.mixed, st));
+        else
+            RBKI_TRY(ttm_cuda(v, factors[m], R, R, dst, RBKI_F64, pl.mixed, st));
         prof_end(tok, st);
         cur[m] = R;
         src = dst;
@@ -359,29 +362,40 @@ rbki_status core_chain(const Plan& pl, double* const* factors, double* core, cud
     return RBKI_OK;
 }
 
-// Per-device pool of non-blocking streams: the N modes are independent (HOSVD reading), so
+// Per-device pools of non-blocking streams: the N modes are independent (HOSVD reading), so
 // each mode's Algorithm 1-2 chain runs on its own stream, forked from and joined back to the
 // caller's stream.  Latency-bound small FP64 kernels of one mode then overlap the HBM-bound
-// passes of the others.
+// passes of the others.  Each caller stream gets its own set, so that calls issued on
+// different streams (decompositions in flight together) do not queue behind one another on
+// shared mode streams.  A device keeps at most MAX_POOLS sets; callers beyond that share
+// the last one.
 struct StreamPool {
-    bool ready = false;
+    cudaStream_t owner = nullptr;
     cudaStream_t s[RBKI_MAX_ORDER];
 };
+constexpr int MAX_POOLS = 32;
 static std::mutex g_pool_mu;
-static StreamPool g_pools[64];
+static std::vector<StreamPool> g_pools[64];
 
-static rbki_status pool_streams(cudaStream_t* out, int n) {
+static rbki_status pool_streams(cudaStream_t caller, cudaStream_t* out, int n) {
     int dev = 0;
     RBKI_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return set_error(RBKI_E_UNSUPPORTED, "device index");
     std::lock_guard<std::mutex> lk(g_pool_mu);
-    StreamPool& p = g_pools[dev];
-    if (!p.ready) {
+    std::vector<StreamPool>& pools = g_pools[dev];
+    StreamPool* p = nullptr;
+    for (auto& q : pools)
+        if (q.owner == caller) p = &q;
+    if (!p && (int)pools.size() < MAX_POOLS) {
+        StreamPool q;
+        q.owner = caller;
         for (int i = 0; i < RBKI_MAX_ORDER; ++i)
-            RBKI_CUDA_TRY(cudaStreamCreateWithFlags(&p.s[i], cudaStreamNonBlocking));
-        p.ready = true;
+            RBKI_CUDA_TRY(cudaStreamCreateWithFlags(&q.s[i], cudaStreamNonBlocking));
+        pools.push_back(q);
+        p = &pools.back();
     }
-    for (int i = 0; i < n; ++i) out[i] = p.s[i];
+    if (!p) p = &pools.back();
+    for (int i = 0; i < n; ++i) out[i] = p->s[i];
     return RBKI_OK;
 }
 
@@ -404,7 +418,7 @@ rbki_status run_tucker(Plan& pl, const rbki_tucker_out* out, cudaStream_t st, co
         if (mode_streams) {
             for (int n = 0; n < pl.N; ++n) ms[n] = mode_streams[n];
         } else {
-            RBKI_TRY(pool_streams(ms, pl.N));
+            RBKI_TRY(pool_streams(st, ms, pl.N));
         }
         cudaEvent_t fork, join[RBKI_MAX_ORDER];
         RBKI_CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));

@@ -58,6 +58,17 @@ template <> __device__ __forceinline__ float ld_f32<__nv_bfloat16>(const __nv_bf
 }
 template <> __device__ __forceinline__ float ld_f32<__half>(const __half* p) { return __half2float(*p); }
 
+// load converted straight to the accumulation type: FP32 paths never touch the FP64 pipe
+// (a float <-> double conversion has 64-100 cycles of latency and FP64 throughput on GB300)
+template <typename Acc> struct LdAcc;
+template <> struct LdAcc<float> {
+    template <typename T> __device__ __forceinline__ static float ld(const T* p) { return ld_f32(p); }
+};
+template <> struct LdAcc<double> {
+    template <typename T> __device__ __forceinline__ static double ld(const T* p) { return ld_f64(p); }
+};
+template <typename Acc, typename T> __device__ __forceinline__ Acc ld_acc(const T* p) { return LdAcc<Acc>::ld(p); }
+
 // ---- Philox4x32-10 (Salmon et al., SC'11) and the Box-Muller Gaussian of Omega ----
 struct U4 { uint32_t x, y, z, w; };
 

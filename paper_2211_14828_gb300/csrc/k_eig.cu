@@ -142,6 +142,124 @@ __global__ void __launch_bounds__(512) k_tridiag(const double* __restrict__ A, i
     }
 }
 
+// Register-resident variant for n <= 32 * NC (and n <= 16 * NR): the working matrix is
+// distributed over 16 warps, element (i, j) held by warp i % 16 (slot i / 16) and lane
+// j % 32 (slot j / 32).  Per Householder step: the owners of column k publish it through
+// shared memory (barrier 1); every thread forms the reflector v from it; u = B v is
+// reduced across the lanes of each warp with shuffles and published with g = v^T u
+// (barrier 2); the rank-2 update B -= v w^T + w v^T, w = 2u - 2 g v, runs in registers.
+// Entries in rows or columns <= k are dead: v and w are zero there.
+template <int NR, int NC>
+__global__ void __launch_bounds__(512) k_tridiag_reg(const double* __restrict__ A, int n, float* __restrict__ d,
+                                                     float* __restrict__ e, float* __restrict__ refl) {
+    constexpr int NW = 16;
+    __shared__ float xv[2][NR * NW];   // column k below the diagonal, double-buffered by k
+    __shared__ float uv[NR * NW];
+    __shared__ float part[NW], part2[NW];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    float a[NR][NC];
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const int i = r * NW + w, j = c * 32 + lane;
+            a[r][c] = (i < n && j < n) ? (float)A[(size_t)i * n + j] : 0.f;
+        }
+    for (int t = tid; t < n * n; t += blockDim.x) refl[t] = 0.f;
+    for (int k = 0; k + 2 < n; ++k) {
+        float* x = xv[k & 1];
+        const int ck = k >> 5, lk = k & 31;
+        if (lane == lk) {
+            float ss = 0.f;
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+                if (c == ck) {
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) {
+                        const int i = r * NW + w;
+                        const float val = a[r][c];
+                        if (i > k && i < n) {
+                            x[i] = val;
+                            if (i > k + 1) ss += val * val;
+                        }
+                        if (i == k) d[k] = val;
+                    }
+                }
+            part[w] = ss;
+        }
+        __syncthreads();
+        float s1 = part[lane & (NW - 1)];
+#pragma unroll
+        for (int o = NW / 2; o; o >>= 1) s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        const float x0 = x[k + 1];
+        if (s1 == 0.f) {                 // already reduced: no reflector (uniform branch)
+            if (tid == 0) e[k] = x0;
+            __syncthreads();
+            continue;
+        }
+        const float nrm = sqrtf(x0 * x0 + s1);
+        const float alpha = x0 >= 0.f ? -nrm : nrm;
+        const float v0 = x0 - alpha;
+        const float inv = 1.f / sqrtf(v0 * v0 + s1);
+        auto vval = [&](int i) -> float { return (i <= k || i >= n) ? 0.f : (i == k + 1 ? v0 : x[i]) * inv; };
+        if (tid == 0) e[k] = alpha;
+        for (int i = k + 1 + tid; i < n; i += blockDim.x) refl[(size_t)k * n + i] = vval(i);
+        float vc[NC], vr[NR];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) vc[c] = vval(c * 32 + lane);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) vr[r] = vval(r * NW + w);
+        // rows with i <= k and column slots with every column <= k are dead: skipped
+        // (the row test is uniform over a warp, the slot test over the whole block)
+        float gp = 0.f;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const int i = r * NW + w;
+            if (i > k && i < n) {
+                float p = 0.f;
+#pragma unroll
+                for (int c = 0; c < NC; ++c)
+                    if (c * 32 + 31 > k) p += a[r][c] * vc[c];
+                p = warp_sum(p);
+                if (lane == 0) uv[i] = p;
+                gp += p * vr[r];
+            }
+        }
+        if (lane == 0) part2[w] = gp;
+        __syncthreads();
+        float g = part2[lane & (NW - 1)];
+#pragma unroll
+        for (int o = NW / 2; o; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+        float wc[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const int j = c * 32 + lane;
+            wc[c] = (j > k && j < n) ? 2.f * uv[j] - 2.f * g * vc[c] : 0.f;
+        }
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const int i = r * NW + w;
+            if (i > k && i < n) {
+                const float wr = 2.f * uv[i] - 2.f * g * vr[r];
+#pragma unroll
+                for (int c = 0; c < NC; ++c)
+                    if (c * 32 + 31 > k) a[r][c] -= vr[r] * wc[c] + wr * vc[c];
+            }
+        }
+    }
+    // the last 2 x 2 block
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const int i = r * NW + w, j = c * 32 + lane;
+            if (i < n && j < n) {
+                if (i == j && i >= n - 2) d[i] = a[r][c];
+                if (i == n - 1 && j == n - 2) e[n - 2] = a[r][c];
+            }
+        }
+}
+
 }  // namespace
 
 // number of eigenvalues of T (d, e) below x, FP32 Sturm sequence
@@ -187,6 +305,13 @@ __host__ __device__ void invit_start(int n, int k, T* y, int ystride) {
     }
 }
 
+// reciprocal on the serial elimination chain: the hardware reciprocal for FP32 (this
+// stage only needs FP32 accuracy), IEEE division otherwise
+template <typename T> __host__ __device__ __forceinline__ T chain_rcp(T a) { return (T)1 / a; }
+#ifdef __CUDA_ARCH__
+template <> __device__ __forceinline__ float chain_rcp<float>(float a) { return __frcp_rn(a); }
+#endif
+
 // One inverse-iteration solve y <- (T - mu I)^{-1} y, unnormalised; returns |y|^2.
 template <typename T>
 __host__ __device__ T invit_solve(const T* d, const T* e, int n, T mu, T tiny, T* rdd, T* du, T* du2, T* y,
@@ -196,11 +321,11 @@ __host__ __device__ T invit_solve(const T* d, const T* e, int n, T mu, T tiny, T
         const T c = e[i], dn = d[i + 1] - mu, f = (i + 2 < n) ? e[i + 1] : (T)0, yn = y[(i + 1) * ystride];
         if (fabs(a) >= fabs(c)) {
             if (fabs(a) < tiny) a = a >= (T)0 ? tiny : -tiny;
-            const T r = (T)1 / a, m = c * r;
+            const T r = chain_rcp(a), m = c * r;
             rdd[i * stride] = r; du[i * stride] = b; du2[i * stride] = 0; y[i * ystride] = yi;
             a = dn - m * b; b = f; yi = yn - m * yi;
         } else {
-            const T r = (T)1 / c, m = a * r;
+            const T r = chain_rcp(c), m = a * r;
             rdd[i * stride] = r; du[i * stride] = dn; du2[i * stride] = f; y[i * ystride] = yn;
             a = b - m * dn; b = -m * f; yi = yi - m * yn;
         }
@@ -230,6 +355,10 @@ __host__ __device__ T invit_one(const T* d, const T* e, int n, T mu, T tnorm, in
     for (int it = 0; it < sweeps; ++it) {
         const T ss = invit_solve<T>(d, e, n, mu, tiny, rdd, du, du2, y, stride, ystride);
         const T sc = (T)1 / sqrt(ss);
+        if (!rq_update) {
+            for (int i = 0; i < n; ++i) y[i * ystride] *= sc;
+            continue;
+        }
         T num = 0, prev = 0, cur = y[0] * sc;
         for (int i = 0; i < n; ++i) {
             const T next = (i + 1 < n) ? y[(i + 1) * ystride] * sc : (T)0;
@@ -280,17 +409,20 @@ __device__ T tri_norm(const T* d, const T* e, int n) {
     return t > (T)0 ? t : (T)1;
 }
 
-// shifts (normalised by |T|) of the nwant largest eigenvalues, one thread each
+// shifts (normalised by |T|) of the nwant largest eigenvalues by multisection: one warp per
+// eigenvalue, each round splits the bracketing interval at 32 points (one FP32 Sturm count
+// per lane) and keeps the sub-interval where the count crosses the eigenvalue's index.
+constexpr int SHIFT_WARPS = 8;
 template <typename T>
-__global__ void __launch_bounds__(64) k_tri_shift(const T* __restrict__ d, const T* __restrict__ e, int n,
-                                                  int nwant, float* __restrict__ shift_out) {
+__global__ void __launch_bounds__(32 * SHIFT_WARPS) k_tri_shift(const T* __restrict__ d, const T* __restrict__ e,
+                                                                int n, int nwant, float* __restrict__ shift_out) {
     __shared__ float df[256], e2f[256];
     __shared__ float bounds[2];
     __shared__ T tn_sh;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31;
     if (tid == 0) tn_sh = tri_norm(d, e, n);
     __syncthreads();
-    const double sc = 1.0 / (double)tn_sh;     // bisection on T / |T| (FP32 range)
+    const double sc = 1.0 / (double)tn_sh;     // on T / |T| (FP32 range)
     for (int i = tid; i < n; i += blockDim.x) {
         df[i] = (float)((double)d[i] * sc);
         e2f[i] = i + 1 < n ? (float)(((double)e[i] * sc) * ((double)e[i] * sc)) : 0.f;
@@ -307,8 +439,22 @@ __global__ void __launch_bounds__(64) k_tri_shift(const T* __restrict__ d, const
         bounds[1] = hi + 1e-5f;
     }
     __syncthreads();
-    const int k = blockIdx.x * blockDim.x + tid;
-    if (k < nwant) shift_out[k] = bisect_one(df, e2f, n, n - 1 - k, bounds[0], bounds[1]);
+    const int k = blockIdx.x * SHIFT_WARPS + (tid >> 5);
+    if (k >= nwant) return;
+    const int j = n - 1 - k;                    // index from below
+    float lo = bounds[0], hi = bounds[1];
+    for (int round = 0; round < 12; ++round) {
+        const float h = (hi - lo) * (1.f / 33.f);
+        const float p = lo + h * (float)(lane + 1);
+        const unsigned above = __ballot_sync(0xffffffffu, p > lo && p < hi && sturm_count(df, e2f, n, p, 1e-30f) > j);
+        const int first = above ? __ffs(above) - 1 : 32;
+        const float nlo = first == 0 ? lo : lo + h * (float)first;
+        const float nhi = first == 32 ? hi : lo + h * (float)(first + 1);
+        if (!(nhi - nlo < hi - lo)) break;      // the interval no longer shrinks in FP32
+        lo = nlo;
+        hi = nhi;
+    }
+    if (lane == 0) shift_out[k] = 0.5f * (lo + hi);
 }
 
 // fixed-shift inverse iteration (3 solves) for every eigenvalue that does not continue a run
@@ -477,6 +623,98 @@ __global__ void __launch_bounds__(256) k_tri_orth(T* __restrict__ Yg, int n, int
     for (int t = tid; t < n * ld; t += blockDim.x) Yg[t] = ys[t];
 }
 
+// Cholesky QR of the eigenvector block for n <= 32 * NC (n <= 16 * NR), 512 threads.
+// Y (n x n, ld n+1) is staged in shared memory; G = Y^T Y is accumulated into the same
+// register distribution as k_tridiag_reg; the right-looking Cholesky publishes row k
+// (double-buffered, one barrier per step) and keeps R in shared memory; then each row of
+// Y is solved against R by four threads (partial sums over p = sub mod 4, two shuffles per
+// column).  Same pivot guard as k_tri_orth: a pivot <= 1e-6 (the columns are unit
+// vectors) leaves its column unscaled.
+template <int NR, int NC>
+__global__ void __launch_bounds__(512) k_tri_orth_reg(float* __restrict__ Yg, int n) {
+    constexpr int NW = 16;
+    extern __shared__ __align__(16) unsigned char or_raw[];
+    const int ld = n + 1;
+    float* ys = reinterpret_cast<float*>(or_raw);        // n x ld
+    float* Rm = ys + (size_t)n * ld;                       // n x ld, upper triangle of R
+    float* ri_s = Rm + (size_t)n * ld;                     // n: multiplier of column q
+    __shared__ float rowbuf[2][NC * 32];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    for (int t = tid; t < n * ld; t += blockDim.x) ys[t] = Yg[t];
+    __syncthreads();
+    float G[NR][NC];
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) G[r][c] = 0.f;
+    for (int l = 0; l < n; ++l) {
+        const float* yl = ys + (size_t)l * ld;
+        float yi[NR], yj[NC];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) { const int i = r * NW + w; yi[r] = i < n ? yl[i] : 0.f; }
+#pragma unroll
+        for (int c = 0; c < NC; ++c) { const int j = c * 32 + lane; yj[c] = j < n ? yl[j] : 0.f; }
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) G[r][c] += yi[r] * yj[c];
+    }
+    for (int k = 0; k < n; ++k) {
+        float* rb = rowbuf[k & 1];
+        if (w == k % NW) {
+            const int rk = k / NW;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                float val = 0.f;
+#pragma unroll
+                for (int r = 0; r < NR; ++r) val = (r == rk) ? G[r][c] : val;
+                rb[c * 32 + lane] = val;
+            }
+        }
+        __syncthreads();
+        const float dk = rb[k];
+        const float ri = dk > 1e-6f ? 1.f / sqrtf(dk) : 1.f;
+        const float r2 = ri * ri;
+        for (int j = k + tid; j < n; j += blockDim.x) Rm[(size_t)k * ld + j] = rb[j] * ri;
+        if (tid == 0) ri_s[k] = ri;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const int i = r * NW + w;
+            if (i > k && i < n) {
+                const float gi = rb[i] * r2;
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    const int j = c * 32 + lane;
+                    if (c * 32 + 31 > k && j > k) G[r][c] -= gi * rb[j];
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // rows of Y: y_new R = y, four threads per row.  The row loop runs to a multiple of
+    // 8 rows so that every lane of a warp takes part in the shuffles; lanes past row n-1
+    // contribute zeros and write nothing.
+    const int sub = tid & 3;
+    const int n8 = (n + 7) & ~7;
+    for (int i = tid >> 2; i < n8; i += blockDim.x >> 2) {
+        const bool act = i < n;
+        float* yi = ys + (size_t)(act ? i : 0) * ld;
+        for (int q = 0; q < n; ++q) {
+            float acc = 0.f;
+            if (act)
+                for (int p = sub; p < q; p += 4) acc += yi[p] * Rm[(size_t)p * ld + q];
+            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+            const float v = act ? (yi[q] - acc) * ri_s[q] : 0.f;
+            __syncwarp();
+            if (act && (q & 3) == sub) yi[q] = v;
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    for (int t = tid; t < n * ld; t += blockDim.x) Yg[t] = ys[t];
+}
+
 template <typename T>
 __global__ void k_tri_rq(const T* __restrict__ d, const T* __restrict__ e, int n, int nwant,
                          const T* __restrict__ Y, T* __restrict__ w) {
@@ -494,12 +732,24 @@ __global__ void k_tri_rq(const T* __restrict__ d, const T* __restrict__ e, int n
 }
 
 // z = H_0 H_1 ... H_{n-3} y for eigenvector column k, one warp per eigenvector (z held in
-// registers, 8 entries per lane); output widened to FP64 (ld ldv).
+// registers, 8 entries per lane); output widened to FP64 (ld ldv).  BT_WARPS eigenvectors
+// per CTA; the reflectors are staged once per CTA in shared memory when they fit
+// (use_smem), otherwise read from global memory.
+constexpr int BT_WARPS = 16;
 template <typename T>
-__global__ void __launch_bounds__(128) k_backtransform(const T* __restrict__ refl, int n, int nwant,
-                                                       const T* __restrict__ Y, double* __restrict__ V, int ldv) {
+__global__ void __launch_bounds__(32 * BT_WARPS) k_backtransform(const T* __restrict__ refl, int n, int nwant,
+                                                                 const T* __restrict__ Y, double* __restrict__ V,
+                                                                 int ldv, int use_smem) {
+    extern __shared__ __align__(16) unsigned char bt_raw[];
+    const T* rf = refl;
+    if (use_smem) {
+        T* s = reinterpret_cast<T*>(bt_raw);
+        for (int t = threadIdx.x; t < n * n; t += blockDim.x) s[t] = refl[t];
+        __syncthreads();
+        rf = s;
+    }
     const int lane = threadIdx.x & 31;
-    const int k = blockIdx.x * 4 + (threadIdx.x >> 5);
+    const int k = blockIdx.x * BT_WARPS + (threadIdx.x >> 5);
     if (k >= nwant) return;
     T z[8];
 #pragma unroll
@@ -508,7 +758,7 @@ __global__ void __launch_bounds__(128) k_backtransform(const T* __restrict__ ref
         z[t] = i < n ? Y[(size_t)i * (nwant + 1) + k] : (T)0;
     }
     for (int j = n - 3; j >= 0; --j) {
-        const T* vj = refl + (size_t)j * n;
+        const T* vj = rf + (size_t)j * n;
         T vr[8];
         T dot = 0;
 #pragma unroll
@@ -645,33 +895,62 @@ rbki_status syev_top_cuda(const double* A, int n, int nwant, double* w, double* 
     const EigLayout L = eig_layout(scratch, n);
     const size_t nn = (size_t)n * n;
     // ---- 1. FP32 eigendecomposition ----
-    static size_t tmax = 0, emax = 0;
-    if (!tmax) tmax = max_dyn_smem(k_tridiag<float>);
-    (void)emax;
-    const size_t tsm = (size_t)(n + 1) * n * sizeof(float);
-    const int t_smem = tsm <= tmax;
-    k_tridiag<float><<<1, 512, t_smem ? tsm : 0, st>>>(A, n, L.work, t_smem, L.d, L.e, L.refl);
+    if (n <= 32) {
+        k_tridiag_reg<2, 1><<<1, 512, 0, st>>>(A, n, L.d, L.e, L.refl);
+    } else if (n <= 64) {
+        k_tridiag_reg<4, 2><<<1, 512, 0, st>>>(A, n, L.d, L.e, L.refl);
+    } else if (n <= 128) {
+        k_tridiag_reg<8, 4><<<1, 512, 0, st>>>(A, n, L.d, L.e, L.refl);
+    } else if (n <= 192) {
+        k_tridiag_reg<12, 6><<<1, 512, 0, st>>>(A, n, L.d, L.e, L.refl);
+    } else {
+        static size_t tmax = 0;
+        if (!tmax) tmax = max_dyn_smem(k_tridiag<float>);
+        const size_t tsm = (size_t)(n + 1) * n * sizeof(float);
+        const int t_smem = tsm <= tmax;
+        k_tridiag<float><<<1, 512, t_smem ? tsm : 0, st>>>(A, n, L.work, t_smem, L.d, L.e, L.refl);
+    }
     RBKI_LAUNCH_CHECK("k_tridiag");
     static size_t vmax = 0;
     if (!vmax) vmax = max_dyn_smem(k_tri_vec<float>);
     const int vthr = 32;
     const size_t vsm = 3 * (size_t)n * vthr * sizeof(float);
     if (vsm > vmax) return set_error(RBKI_E_UNSUPPORTED, "syev: inverse-iteration rows exceed shared memory");
-    k_tri_shift<float><<<(unsigned)cdiv(n, 64), 64, 0, st>>>(L.d, L.e, n, n, L.shift);
+    k_tri_shift<float><<<(unsigned)cdiv(n, SHIFT_WARPS), 32 * SHIFT_WARPS, 0, st>>>(L.d, L.e, n, n, L.shift);
     RBKI_LAUNCH_CHECK("k_tri_shift");
     k_tri_vec<float><<<(unsigned)cdiv(n, vthr), vthr, vsm, st>>>(L.d, L.e, n, n, L.shift, L.Yt);
     RBKI_LAUNCH_CHECK("k_tri_vec");
     k_tri_runs<float><<<(unsigned)n, 256, 0, st>>>(L.d, L.e, n, n, L.shift, L.Yt);
     RBKI_LAUNCH_CHECK("k_tri_runs");
-    static size_t omax = 0;
-    if (!omax) omax = max_dyn_smem(k_tri_orth<float>);
-    const size_t osm = (size_t)(n + 2 * n) * (n + 1) * sizeof(float);
-    const int o_smem = osm <= omax;
-    k_tri_orth<float><<<1, 256, o_smem ? osm : 0, st>>>(L.Yt, n, n, L.iiw, o_smem);
+    const size_t rsm = (2 * (size_t)n * (n + 1) + n) * sizeof(float);
+    if (n <= 128) {
+        static size_t rmax[3] = {0, 0, 0};
+        if (n <= 32) {
+            if (!rmax[0]) rmax[0] = max_dyn_smem(k_tri_orth_reg<2, 1>);
+            k_tri_orth_reg<2, 1><<<1, 512, rsm, st>>>(L.Yt, n);
+        } else if (n <= 64) {
+            if (!rmax[1]) rmax[1] = max_dyn_smem(k_tri_orth_reg<4, 2>);
+            k_tri_orth_reg<4, 2><<<1, 512, rsm, st>>>(L.Yt, n);
+        } else {
+            if (!rmax[2]) rmax[2] = max_dyn_smem(k_tri_orth_reg<8, 4>);
+            k_tri_orth_reg<8, 4><<<1, 512, rsm, st>>>(L.Yt, n);
+        }
+    } else {
+        static size_t omax = 0;
+        if (!omax) omax = max_dyn_smem(k_tri_orth<float>);
+        const size_t osm = (size_t)(n + 2 * n) * (n + 1) * sizeof(float);
+        const int o_smem = osm <= omax;
+        k_tri_orth<float><<<1, 256, o_smem ? osm : 0, st>>>(L.Yt, n, n, L.iiw, o_smem);
+    }
     RBKI_LAUNCH_CHECK("k_tri_orth");
     k_tri_rq<float><<<(unsigned)cdiv(n, 64), 64, 0, st>>>(L.d, L.e, n, n, L.Yt, L.lam);
     RBKI_LAUNCH_CHECK("k_tri_rq");
-    k_backtransform<float><<<(unsigned)cdiv(n, 4), 128, 0, st>>>(L.refl, n, n, L.Yt, L.X, n);
+    static size_t bmax = 0;
+    if (!bmax) bmax = max_dyn_smem(k_backtransform<float>);
+    const size_t bsm = (size_t)n * n * sizeof(float);
+    const int b_smem = bsm <= bmax;
+    k_backtransform<float><<<(unsigned)cdiv(n, BT_WARPS), 32 * BT_WARPS, b_smem ? bsm : 0, st>>>(
+        L.refl, n, n, L.Yt, L.X, n, b_smem);
     RBKI_LAUNCH_CHECK("k_backtransform");
     k_f32_to_f64<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(L.lam, L.lam_all, n);
     RBKI_LAUNCH_CHECK("k_f32_to_f64");

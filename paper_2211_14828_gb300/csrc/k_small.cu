@@ -83,12 +83,19 @@ __global__ void k_gprime(const double* __restrict__ M, int m, int S, double* __r
     if (k == l) nu2[k] = g;
 }
 
-// Cholesky G' = R^T R with pivot deflation, then Rinv (upper) with zero rows/columns for
-// deflated directions.  Column k is deflated when nu2[k] == 0 or its pivot (squared norm
-// orthogonal to everything accepted) <= tau^2 nu2[k].  Single CTA, right-looking with one
-// barrier per step: every thread evaluates the pivot itself (same inputs, same decision), the
-// trailing update uses the unscaled row k times the pivot reciprocal, and the rows of R and
-// of Rinv are scaled in one final pass.
+// Cholesky G' = R^T R with pivot deflation, and Rinv (upper, zero rows/columns for
+// deflated directions).  Column k is deflated when nu2[k] == 0 or its pivot (squared norm
+// orthogonal to everything accepted) <= tau^2 nu2[k].  Single CTA.
+//
+// G' = L D L^T by elimination without square roots, carrying M = L^{-1} along (the same row
+// operations applied to an identity), so that R = D^{1/2} L^T and Rinv = M^T D^{-1/2} come
+// out of one loop with one barrier per step.  FP64 on GB300 has 64 cycles of dependent
+// latency and 2 FMA/clk/SM, so the serial chain is kept short and the FP64 instructions
+// full:
+//   * thread 0 updates d_{k+1} first and computes 1 / d_{k+1} (FP32 estimate + two FP64
+//     Newton steps) while the other threads update the rest (lookahead);
+//   * the trailing upper triangle and the rows of M are walked as one packed index list;
+//   * 1 / sqrt(d_k) for all k in parallel afterwards.
 __device__ __forceinline__ double rsqrt_f64(double d) {
     // FP32 estimate + two FP64 Newton steps: full FP64 accuracy with a short dependent chain
     double y = (double)rsqrtf((float)d);
@@ -96,54 +103,81 @@ __device__ __forceinline__ double rsqrt_f64(double d) {
     y = y * (1.5 - 0.5 * d * y * y);
     return y;
 }
+__device__ __forceinline__ double rcp_f64(double d) {
+    double y = (double)__frcp_rn((float)d);
+    y = y * (2.0 - d * y);
+    y = y * (2.0 - d * y);
+    return y;
+}
 
 __global__ void k_chol_deflate(const double* __restrict__ Gp, const double* __restrict__ nu2,
                                int S, double tau, double* __restrict__ Rinv,
                                int32_t* __restrict__ kept) {
     extern __shared__ double sm[];
-    double* W = sm;                   // S x S (upper triangle: unscaled rows of R)
-    double* B = W + S * S;            // S x S, becomes Rinv
-    double* rinv = B + S * S;         // S: 1 / R_kk, 0 when deflated
+    double* W = sm;                   // S x S, upper triangle: row k = d_k L_{:,k}^T after step k
+    double* Mi = W + S * S;           // S x S, lower triangle: L^{-1}
+    double* inv_d = Mi + S * S;       // S: 1 / d_k, 0 when deflated
+    double* rinv = inv_d + S;         // S: 1 / sqrt(d_k), 0 when deflated
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int e = tid; e < S * S; e += nt) {
         W[e] = Gp[e];
-        B[e] = (e / S == e % S) ? 1.0 : 0.0;
+        Mi[e] = (e / S == e % S) ? 1.0 : 0.0;
     }
     __syncthreads();
-    int nk = 0;
-    for (int k = 0; k < S; ++k) {
+    auto pivot = [&](int k) {
         const double d = W[k * S + k], nu = nu2[k];
-        const bool keep = nu > 0.0 && d > tau * tau * nu;
-        const double ri = keep ? rsqrt_f64(d) : 0.0;
-        nk += keep ? 1 : 0;
-        if (tid == 0) rinv[k] = ri;
-        // G_ij -= (G_ki ri)(G_kj ri) for k < i <= j
-        const double r2 = ri * ri;
+        inv_d[k] = (nu > 0.0 && d > tau * tau * nu) ? rcp_f64(d) : 0.0;
+    };
+    if (tid == 0) pivot(0);
+    __syncthreads();
+    for (int k = 0; k < S; ++k) {
+        const double ik = inv_d[k];
         const int mm = S - k - 1;
-        for (int t = tid; t < mm * mm; t += nt) {
-            const int i = k + 1 + t / mm, j = k + 1 + t % mm;
-            if (j >= i) W[i * S + j] -= W[k * S + i] * W[k * S + j] * r2;
+        if (ik != 0.0) {                       // uniform: a deflated column eliminates nothing
+            if (tid == 0 && mm > 0) {          // d_{k+1} first, then its reciprocal
+                const double wk = W[k * S + k + 1];
+                W[(k + 1) * S + k + 1] -= wk * wk * ik;
+            }
+            const int ntri = mm * (mm + 1) / 2;      // trailing upper triangle (a <= b)
+            const int nm = mm * (k + 1);             // rows k+1.. of M, columns 0..k
+            for (int t = tid + 1; t < ntri + nm; t += nt) {
+                if (t < ntri) {
+                    // t = b (b + 1) / 2 + a, 0 <= a <= b < mm
+                    int bb = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+                    if ((bb + 1) * (bb + 2) / 2 <= t) ++bb;
+                    if (bb * (bb + 1) / 2 > t) --bb;
+                    const int aa = t - bb * (bb + 1) / 2;
+                    const int i = k + 1 + aa, j = k + 1 + bb;
+                    W[i * S + j] -= W[k * S + i] * W[k * S + j] * ik;
+                } else {
+                    const int u = t - ntri;
+                    const int i = k + 1 + u / (k + 1), c = u % (k + 1);
+                    Mi[i * S + c] -= (W[k * S + i] * ik) * Mi[k * S + c];
+                }
+            }
         }
+        if (tid == 0 && mm > 0) pivot(k + 1);
         __syncthreads();
     }
-    // Rinv: R X = I from the bottom row up.  With unscaled rows (R_ri = W_ri rinv_r), row i
-    // of X is B_i rinv_i and B_r -= R_ri X_i for r < i; rows are scaled at the end.
-    for (int i = S - 1; i >= 0; --i) {
-        const double ri = rinv[i];
-        for (int t = tid; t < i * S; t += nt) {
-            const int r = t / S, j = t % S;
-            B[r * S + j] -= (W[r * S + i] * rinv[r]) * (B[i * S + j] * ri);
-        }
-        __syncthreads();
+    for (int k = tid; k < S; k += nt) rinv[k] = inv_d[k] != 0.0 ? rsqrt_f64(W[k * S + k]) : 0.0;
+    __syncthreads();
+    // Rinv[t][s] = L^{-1}[s][t] / sqrt(d_s) for t <= s
+    for (int e = tid; e < S * S; e += nt) {
+        const int t = e / S, c = e % S;
+        Rinv[e] = t <= c ? Mi[c * S + t] * rinv[c] : 0.0;
     }
-    for (int e = tid; e < S * S; e += nt) Rinv[e] = B[e] * rinv[e / S];
-    if (tid == 0 && kept) atomicAdd(kept, nk);
+    if (tid == 0 && kept) {
+        int nk = 0;
+        for (int k = 0; k < S; ++k) nk += inv_d[k] != 0.0 ? 1 : 0;
+        atomicAdd(kept, nk);
+    }
 }
 
 // Q[i][m+s] = sum_t (Q[i][m+t] - sum_{r<m} Q[i][r] M[r][t]) Rinv[t][s]; ORTH_ROWS rows per CTA
 constexpr int ORTH_ROWS = 4;
-__global__ void k_orth_apply(double* __restrict__ Q, int64_t ldq, int64_t rows, int m, int S,
-                             const double* __restrict__ M, const double* __restrict__ Rinv) {
+__global__ void __launch_bounds__(128) k_orth_apply(double* __restrict__ Q, int64_t ldq, int64_t rows, int m,
+                                                    int S, const double* __restrict__ M,
+                                                    const double* __restrict__ Rinv) {
     extern __shared__ double tmp[];   // ORTH_ROWS x S
     const int64_t i0 = (int64_t)blockIdx.x * ORTH_ROWS;
     for (int e = threadIdx.x; e < ORTH_ROWS * S; e += blockDim.x) {
@@ -170,14 +204,16 @@ __global__ void k_orth_apply(double* __restrict__ Q, int64_t ldq, int64_t rows, 
         int rr = e / S, s = e % S;
         int64_t i = i0 + rr;
         if (i >= rows) continue;
-        double a0 = 0.0, a1 = 0.0;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
         int tt = 0;
-        for (; tt + 1 <= s; tt += 2) {
+        for (; tt + 3 <= s; tt += 4) {
             a0 += tmp[rr * S + tt] * Rinv[tt * S + s];
             a1 += tmp[rr * S + tt + 1] * Rinv[(tt + 1) * S + s];
+            a2 += tmp[rr * S + tt + 2] * Rinv[(tt + 2) * S + s];
+            a3 += tmp[rr * S + tt + 3] * Rinv[(tt + 3) * S + s];
         }
         for (; tt <= s; ++tt) a0 += tmp[rr * S + tt] * Rinv[tt * S + s];
-        Q[i * ldq + m + s] = a0 + a1;
+        Q[i * ldq + m + s] = (a0 + a1) + (a2 + a3);
     }
 }
 
@@ -277,13 +313,13 @@ rbki_status orth_pass_cuda(double* Q, int64_t ldq, int64_t rows, int m, int S, d
     RBKI_TRY(atb_cuda(Q, ldq, m + S, Q + m, ldq, S, rows, part, M, S, st));
     k_gprime<<<S, 128, 0, st>>>(M, m, S, Gp, nu2);
     RBKI_LAUNCH_CHECK("k_gprime");
-    size_t sm = (2 * (size_t)S * S + S) * sizeof(double);   // W, B, rinv
+    size_t sm = (2 * (size_t)S * S + 2 * S) * sizeof(double);   // W, B, 1/d, 1/sqrt(d)
     static size_t smax = 0;
     if (!smax) smax = max_dyn_smem(k_chol_deflate);
     if (sm > smax) return set_error(RBKI_E_UNSUPPORTED, "orth: block too wide for shared memory");
     k_chol_deflate<<<1, 128, sm, st>>>(Gp, nu2, S, tau, Rinv, kept);
     RBKI_LAUNCH_CHECK("k_chol_deflate");
-    k_orth_apply<<<(unsigned)cdiv(rows, ORTH_ROWS), 256, ORTH_ROWS * S * sizeof(double), st>>>(
+    k_orth_apply<<<(unsigned)cdiv(rows, ORTH_ROWS), 32 * ORTH_ROWS, ORTH_ROWS * S * sizeof(double), st>>>(
         Q, ldq, rows, m, S, M, Rinv);
     RBKI_LAUNCH_CHECK("k_orth_apply");
     return RBKI_OK;

@@ -51,10 +51,10 @@ __global__ void __launch_bounds__(256) k_ttm(const T* __restrict__ X, int64_t A,
             if (i < I) {
                 if (cfast) {
                     int64_t c = c0 + jj;
-                    if (c < C) v = (Acc)ld_f64(X + (a0 * I + i) * C + c);
+                    if (c < C) v = ld_acc<Acc>(X + (a0 * I + i) * C + c);
                 } else {
                     int64_t a = a0 + jj;
-                    if (a < A) v = (Acc)ld_f64(X + a * I + i);
+                    if (a < A) v = ld_acc<Acc>(X + a * I + i);
                 }
             }
             xs[ii][jj] = v;
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(256) k_contract(const T* __restrict__ X, int64
             Acc v = 0;
             if (col < col_hi && i < I) {
                 int64_t a = col / C, c = col - a * C;
-                v = (Acc)ld_f64(X + (a * I + i) * C + c);
+                v = ld_acc<Acc>(X + (a * I + i) * C + c);
             }
             xs[kk][ii] = v;
         }
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(256) k_contract(const T* __restrict__ X, int64
             Acc v = 0;
             if (col < col_hi && s < S) {
                 int64_t a = col / C, c = col - a * C;
-                v = (Acc)ld_f64(Y + (a * S + s) * C + c);
+                v = ld_acc<Acc>(Y + (a * S + s) * C + c);
             }
             ys[kk][ss] = v;
         }
@@ -215,6 +215,115 @@ rbki_status ttm_cuda(const View& x, const double* M, int64_t ldm, int S, void* Y
 #undef TTM_D
 #undef TTM_L
     RBKI_LAUNCH_CHECK("k_ttm");
+    return RBKI_OK;
+}
+
+// Small mode products (the core chain after the first contraction): Y = X x_n M^T with
+// S <= NSB <= 32 outputs per column.  M is staged in shared memory in chunks of TS_MI rows,
+// converted to the accumulation type once.
+//   C > 1: one thread per (a, c) column with NSB accumulators; X reads coalesced over c.
+//   C = 1: one warp per a, lanes over i, butterfly reduction of the NSB partial sums.
+constexpr int TS_MI = 128;
+template <typename T, typename Acc, int NSB>
+__global__ void __launch_bounds__(256) k_ttm_small_c(const T* __restrict__ X, int64_t A, int64_t I, int64_t C,
+                                                     const double* __restrict__ M, int64_t ldm, int S,
+                                                     double* __restrict__ Y) {
+    __shared__ __align__(16) Acc ms[TS_MI][NSB];
+    const int64_t cblocks = cdiv(C, (int64_t)blockDim.x);
+    const int64_t a = blockIdx.x / cblocks;
+    const int64_t c = (blockIdx.x % cblocks) * blockDim.x + threadIdx.x;
+    Acc acc[NSB];
+#pragma unroll
+    for (int q = 0; q < NSB; ++q) acc[q] = 0;
+    for (int64_t i0 = 0; i0 < I; i0 += TS_MI) {
+        const int ni = (int)((I - i0) < TS_MI ? (I - i0) : TS_MI);
+        __syncthreads();
+        for (int e = threadIdx.x; e < TS_MI * NSB; e += blockDim.x) {
+            const int ii = e / NSB, q = e % NSB;
+            ms[ii][q] = (ii < ni && q < S) ? (Acc)M[(i0 + ii) * ldm + q] : (Acc)0;
+        }
+        __syncthreads();
+        if (c < C) {
+            const T* xp = X + (a * I + i0) * C + c;
+            for (int ii = 0; ii < ni; ++ii) {
+                const Acc x = ld_acc<Acc>(xp + (int64_t)ii * C);
+                // the row of M is the same for every lane: 16-byte broadcast reads
+                const uint4* mr = reinterpret_cast<const uint4*>(&ms[ii][0]);
+#pragma unroll
+                for (int v = 0; v < NSB * (int)sizeof(Acc) / 16; ++v) {
+                    const uint4 u = mr[v];
+                    if constexpr (sizeof(Acc) == 4) {
+                        acc[4 * v + 0] += x * __uint_as_float(u.x);
+                        acc[4 * v + 1] += x * __uint_as_float(u.y);
+                        acc[4 * v + 2] += x * __uint_as_float(u.z);
+                        acc[4 * v + 3] += x * __uint_as_float(u.w);
+                    } else {
+                        acc[2 * v + 0] += x * __hiloint2double((int)u.y, (int)u.x);
+                        acc[2 * v + 1] += x * __hiloint2double((int)u.w, (int)u.z);
+                    }
+                }
+            }
+        }
+    }
+    if (c < C)
+#pragma unroll
+        for (int q = 0; q < NSB; ++q)
+            if (q < S) Y[(a * S + q) * C + c] = (double)acc[q];
+}
+
+template <typename T, typename Acc, int NSB>
+__global__ void __launch_bounds__(256) k_ttm_small_i(const T* __restrict__ X, int64_t A, int64_t I,
+                                                     const double* __restrict__ M, int64_t ldm, int S,
+                                                     double* __restrict__ Y) {
+    __shared__ Acc ms[TS_MI][NSB + 1];   // odd stride: the lanes of a warp read different rows
+    const int lane = threadIdx.x & 31;
+    const int64_t a = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    Acc acc[NSB];
+#pragma unroll
+    for (int q = 0; q < NSB; ++q) acc[q] = 0;
+    for (int64_t i0 = 0; i0 < I; i0 += TS_MI) {
+        const int ni = (int)((I - i0) < TS_MI ? (I - i0) : TS_MI);
+        __syncthreads();
+        for (int e = threadIdx.x; e < TS_MI * NSB; e += blockDim.x) {
+            const int ii = e / NSB, q = e % NSB;
+            ms[ii][q] = (ii < ni && q < S) ? (Acc)M[(i0 + ii) * ldm + q] : (Acc)0;
+        }
+        __syncthreads();
+        if (a < A)
+            for (int ii = lane; ii < ni; ii += 32) {
+                const Acc x = ld_acc<Acc>(X + a * I + i0 + ii);
+#pragma unroll
+                for (int q = 0; q < NSB; ++q) acc[q] += x * ms[ii][q];
+            }
+    }
+    if (a >= A) return;   // whole warp
+#pragma unroll
+    for (int q = 0; q < NSB; ++q) {
+        const Acc v = warp_sum(acc[q]);
+        if (lane == 0 && q < S) Y[a * S + q] = (double)v;
+    }
+}
+
+rbki_status ttm_small_cuda(const View& x, const double* M, int64_t ldm, int S, double* Y, bool acc32,
+                           cudaStream_t st) {
+    if (S < 1 || S > 32) return set_error(RBKI_E_UNSUPPORTED, "ttm_small: S > 32");
+    if (x.dtype != RBKI_F64 && x.dtype != RBKI_F32) return set_error(RBKI_E_UNSUPPORTED, "ttm_small: dtype");
+    const bool ifast = x.C == 1;
+    const int64_t blocks = ifast ? cdiv(x.A, (int64_t)8) : x.A * cdiv(x.C, (int64_t)256);
+    if (blocks > 0x7fffffff) return set_error(RBKI_E_UNSUPPORTED, "ttm_small: too many blocks");
+#define TS_L(T, ACC, NSB)                                                                              \
+    if (ifast) k_ttm_small_i<T, ACC, NSB><<<(unsigned)blocks, 256, 0, st>>>(as<T>(x.data), x.A, x.I, M, ldm, S, Y); \
+    else k_ttm_small_c<T, ACC, NSB><<<(unsigned)blocks, 256, 0, st>>>(as<T>(x.data), x.A, x.I, x.C, M, ldm, S, Y)
+#define TS_B(T, ACC)                                                                                   \
+    if (S <= 8) { TS_L(T, ACC, 8); } else if (S <= 16) { TS_L(T, ACC, 16); } else { TS_L(T, ACC, 32); }
+    if (x.dtype == RBKI_F64) {
+        if (acc32) { TS_B(double, float) } else { TS_B(double, double) }
+    } else {
+        if (acc32) { TS_B(float, float) } else { TS_B(float, double) }
+    }
+#undef TS_B
+#undef TS_L
+    RBKI_LAUNCH_CHECK("k_ttm_small");
     return RBKI_OK;
 }
 

@@ -16,6 +16,9 @@ struct View {
 // ---- FP64/FP32 CUDA-core streaming products (k_stream.cu) ----
 // TTM: Y[a][s][c] = sum_i M[i*ldm + s] X[a][i][c],  s < S.  Y is [A][S][C] (Tout).
 // `acc32` = accumulate in FP32 (mixed path), else FP64.
+// Y (FP64, [A][S][C]) = X x_n M^T for S <= 32 (F64/F32 input): the small core-chain products
+rbki_status ttm_small_cuda(const View& x, const double* M, int64_t ldm, int S, double* Y, bool acc32,
+                           cudaStream_t st);
 rbki_status ttm_cuda(const View& x, const double* M, int64_t ldm, int S, void* Y, int y_dtype,
                      bool acc32, cudaStream_t st);
 // Contraction: P[i][s] = sum_{a,c} X[a][i][c] Y[a][s][c] (split over columns into nsplit

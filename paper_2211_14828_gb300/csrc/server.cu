@@ -92,6 +92,7 @@ struct Request {
     bool cancel = false;
     rbki_status result = RBKI_PENDING;
     double t_submit = 0, t_done = 0;
+    cudaEvent_t ready = nullptr;   // recorded on the submitter's stream (or null)
 };
 
 struct Slot {
@@ -130,6 +131,7 @@ rbki_status run_request(rbki_server* s, Slot& slot, Request* r, size_t off) {
     RBKI_TRY(make_plan(&r->X, &r->prm, pl));
     carve(pl, s->arena_base + off);
     pl.xin = r->X.data;
+    if (r->ready) RBKI_CUDA_TRY(cudaStreamWaitEvent(slot.st, r->ready, 0));
     rbki_status rs = run_tucker(pl, &r->out, slot.st, slot.ms);
     cudaError_t e = cudaStreamSynchronize(slot.st);
     if (rs < 0) return rs;
@@ -215,7 +217,7 @@ rbki_status rbki_server_create(int32_t device, size_t mem_budget, int32_t max_sl
 }
 
 rbki_status rbki_submit(rbki_server* s, const rbki_tensor* X, const rbki_params* prm, const rbki_tucker_out* out,
-                        uint64_t* ticket) {
+                        void* after_stream, uint64_t* ticket) {
     if (!s || !ticket) return set_error(RBKI_E_INVAL, "server / ticket is NULL");
     if (!out || !out->core) return set_error(RBKI_E_INVAL, "out->core is NULL");
     Plan pl;
@@ -226,6 +228,19 @@ rbki_status rbki_submit(rbki_server* s, const rbki_tensor* X, const rbki_params*
     carve(pl, nullptr);
     if (pl.ws_bytes > s->budget) return set_error(RBKI_E_NOMEM, "request workspace exceeds the server budget");
     Request* r = new Request();
+    if (after_stream) {
+        int prev = 0;
+        cudaGetDevice(&prev);
+        cudaSetDevice(s->device);
+        cudaError_t e = cudaEventCreateWithFlags(&r->ready, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(r->ready, (cudaStream_t)after_stream);
+        cudaSetDevice(prev);
+        if (e != cudaSuccess) {
+            if (r->ready) cudaEventDestroy(r->ready);
+            delete r;
+            return set_cuda_error(e, "rbki_submit: event on after_stream");
+        }
+    }
     r->X = *X;
     r->prm = *prm;
     r->out = *out;
@@ -234,6 +249,7 @@ rbki_status rbki_submit(rbki_server* s, const rbki_tensor* X, const rbki_params*
     {
         std::lock_guard<std::mutex> lk(s->mu);
         if (s->stopping) {
+            if (r->ready) cudaEventDestroy(r->ready);
             delete r;
             return set_error(RBKI_E_BUSY, "server is shutting down");
         }
@@ -259,6 +275,7 @@ rbki_status rbki_poll(rbki_server* s, uint64_t ticket, rbki_status* result, doub
     if (result) *result = r->result;
     if (latency_s) *latency_s = r->t_done - r->t_submit;
     s->reqs.erase(it);
+    if (r->ready) cudaEventDestroy(r->ready);
     delete r;
     return RBKI_OK;
 }
@@ -324,7 +341,10 @@ rbki_status rbki_server_destroy(rbki_server* s) {
     }
     if (s->arena_base) cudaFree(s->arena_base);
     cudaSetDevice(prev);
-    for (auto& kv : s->reqs) delete kv.second;
+    for (auto& kv : s->reqs) {
+        if (kv.second->ready) cudaEventDestroy(kv.second->ready);
+        delete kv.second;
+    }
     delete s->arena;
     delete s;
     return RBKI_OK;

@@ -45,12 +45,15 @@ def _run_both(rb, x, tucker_ranks, p, q, seed, tr_ranks, maxit=20, tol=1e-3, ini
 
 def _check(want, got, maxit, unique=True):
     """unique=False: some ALS update is underdetermined (prod_{j!=k} R_j < r_{k-1} r_k), so
-    the cores are not unique; then only the fits and the reconstruction are compared."""
+    the cores are not unique; then only the fits and the reconstruction are compared, and
+    the fits to 1e-7: the GPU solves the singular normal equations with a diagonal shift of
+    1e-12 trace/S, which leaves a residual of about 1e-9 |G| where the oracle's
+    minimum-norm least squares leaves rounding."""
     fits = got["fits"].cpu().numpy()
     nsweeps = int(np.sum(~np.isnan(fits)))
     assert nsweeps == len(want["fits"]), (fits, want["fits"])
     assert np.all(np.isnan(fits[nsweeps:]))
-    np.testing.assert_allclose(fits[:nsweeps], want["fits"], rtol=0, atol=1e-9)
+    np.testing.assert_allclose(fits[:nsweeps], want["fits"], rtol=0, atol=1e-9 if unique else 1e-7)
     cores = [c.cpu().numpy() for c in got["cores"]]
     for c, w in zip(cores, want["cores"]):
         assert c.shape == w.shape
