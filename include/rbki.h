@@ -144,7 +144,8 @@ rbki_status rbki_server_create(int32_t device, size_t mem_budget, int32_t max_sl
  * must stay valid until a terminal poll.  The server runs requests on its own streams: work
  * already queued on `after_stream` (a cudaStream_t as void*, typically the stream that
  * produced X) is waited for before the request's first kernel - an event is recorded on
- * it here.  Pass NULL only when X is complete on the device (e.g. after a synchronize).
+ * it here.  NULL means "nothing to wait for": pass it only when X is complete on the device
+ * (e.g. after a synchronize); the legacy default stream is passed as cudaStreamLegacy.
  * Refused at submission: invalid arguments (RBKI_E_INVAL), a workspace larger than the
  * whole budget (RBKI_E_NOMEM), a server shutting down (RBKI_E_BUSY). */
 rbki_status rbki_submit(rbki_server* s, const rbki_tensor* X, const rbki_params* prm,

@@ -308,7 +308,10 @@ class RbkiServer:
         o = make_out(out)
         tk = C.c_uint64(0)
         st = after_stream if after_stream is not None else torch.cuda.current_stream()
-        check(lib().rbki_submit(self._h, C.byref(t), C.byref(prm), C.byref(o), stream_ptr(st), C.byref(tk)),
+        # the legacy default stream has handle 0, which the C ABI reads as "no stream to wait
+        # for": pass its explicit handle (cudaStreamLegacy) instead
+        handle = st.cuda_stream or 0x1
+        check(lib().rbki_submit(self._h, C.byref(t), C.byref(prm), C.byref(o), C.c_void_p(handle), C.byref(tk)),
               "rbki_submit")
         self._live[tk.value] = (x, out)
         return tk.value, out
