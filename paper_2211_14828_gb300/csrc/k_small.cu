@@ -113,16 +113,16 @@ __device__ __forceinline__ double rcp_f64(double d) {
 __global__ void k_chol_deflate(const double* __restrict__ Gp, const double* __restrict__ nu2,
                                int S, double tau, double* __restrict__ Rinv,
                                int32_t* __restrict__ kept) {
+    // one S x S array holds both factors: the upper triangle (with the diagonal) is W, row k
+    // = d_k L_{:,k}^T after step k; the strict lower triangle is L^{-1} (unit diagonal
+    // implied).  Keeping the shared memory small (S = 30: 7.5 KB) lets this kernel share an
+    // SM with the tensor-core streaming kernel running on another stream.
     extern __shared__ double sm[];
-    double* W = sm;                   // S x S, upper triangle: row k = d_k L_{:,k}^T after step k
-    double* Mi = W + S * S;           // S x S, lower triangle: L^{-1}
-    double* inv_d = Mi + S * S;       // S: 1 / d_k, 0 when deflated
+    double* W = sm;
+    double* inv_d = W + S * S;        // S: 1 / d_k, 0 when deflated
     double* rinv = inv_d + S;         // S: 1 / sqrt(d_k), 0 when deflated
     const int tid = threadIdx.x, nt = blockDim.x;
-    for (int e = tid; e < S * S; e += nt) {
-        W[e] = Gp[e];
-        Mi[e] = (e / S == e % S) ? 1.0 : 0.0;
-    }
+    for (int e = tid; e < S * S; e += nt) W[e] = (e % S >= e / S) ? Gp[e] : 0.0;
     __syncthreads();
     auto pivot = [&](int k) {
         const double d = W[k * S + k], nu = nu2[k];
@@ -139,7 +139,7 @@ __global__ void k_chol_deflate(const double* __restrict__ Gp, const double* __re
                 W[(k + 1) * S + k + 1] -= wk * wk * ik;
             }
             const int ntri = mm * (mm + 1) / 2;      // trailing upper triangle (a <= b)
-            const int nm = mm * (k + 1);             // rows k+1.. of M, columns 0..k
+            const int nm = mm * (k + 1);             // rows k+1.. of L^{-1}, columns 0..k
             for (int t = tid + 1; t < ntri + nm; t += nt) {
                 if (t < ntri) {
                     // t = b (b + 1) / 2 + a, 0 <= a <= b < mm
@@ -152,7 +152,8 @@ __global__ void k_chol_deflate(const double* __restrict__ Gp, const double* __re
                 } else {
                     const int u = t - ntri;
                     const int i = k + 1 + u / (k + 1), c = u % (k + 1);
-                    Mi[i * S + c] -= (W[k * S + i] * ik) * Mi[k * S + c];
+                    const double mkc = c == k ? 1.0 : W[k * S + c];   // L^{-1}[k][c]
+                    W[i * S + c] -= (W[k * S + i] * ik) * mkc;
                 }
             }
         }
@@ -161,10 +162,10 @@ __global__ void k_chol_deflate(const double* __restrict__ Gp, const double* __re
     }
     for (int k = tid; k < S; k += nt) rinv[k] = inv_d[k] != 0.0 ? rsqrt_f64(W[k * S + k]) : 0.0;
     __syncthreads();
-    // Rinv[t][s] = L^{-1}[s][t] / sqrt(d_s) for t <= s
+    // Rinv[t][c] = L^{-1}[c][t] / sqrt(d_c) for t <= c
     for (int e = tid; e < S * S; e += nt) {
         const int t = e / S, c = e % S;
-        Rinv[e] = t <= c ? Mi[c * S + t] * rinv[c] : 0.0;
+        Rinv[e] = t < c ? W[c * S + t] * rinv[c] : (t == c ? rinv[c] : 0.0);
     }
     if (tid == 0 && kept) {
         int nk = 0;
@@ -313,7 +314,7 @@ rbki_status orth_pass_cuda(double* Q, int64_t ldq, int64_t rows, int m, int S, d
     RBKI_TRY(atb_cuda(Q, ldq, m + S, Q + m, ldq, S, rows, part, M, S, st));
     k_gprime<<<S, 128, 0, st>>>(M, m, S, Gp, nu2);
     RBKI_LAUNCH_CHECK("k_gprime");
-    size_t sm = (2 * (size_t)S * S + 2 * S) * sizeof(double);   // W, B, 1/d, 1/sqrt(d)
+    size_t sm = ((size_t)S * S + 2 * S) * sizeof(double);   // W | L^{-1}, 1/d, 1/sqrt(d)
     static size_t smax = 0;
     if (!smax) smax = max_dyn_smem(k_chol_deflate);
     if (sm > smax) return set_error(RBKI_E_UNSUPPORTED, "orth: block too wide for shared memory");
