@@ -165,6 +165,41 @@ def rbki_tucker(x: np.ndarray, ranks: Sequence[int], p: int, q: int, seed: int,
                 x_norm2=float(np.sum(x * x)), core_norm2=float(np.sum(core * core)))
 
 
+def rbki_st_tucker(x: np.ndarray, ranks: Sequence[int], p: int, q: int, seed: int,
+                   tau: float = TAU_DEFLATE) -> Dict:
+    """Algorithm 2 read literally (sequential truncation, the other reading of step 6): the
+    modes are taken in order n = 1..N, and mode n is sketched from the tensor already
+    contracted by the earlier factors, Y_n = X x_1 U^(1)T ... x_{n-1} U^(n-1)T; after U^(n)
+    the tensor is contracted once more, and the last contraction is the core.  Omega^(n) is
+    keyed by the column index of Y_n's mode-n unfolding (reading c6 applied to Y_n).
+    Returns the same fields as rbki_tucker, plus `step_res2[n]` = |Y_n - Y_n x_n U U^T|^2."""
+    y = np.asarray(x, dtype=np.float64)
+    x_norm2 = float(np.sum(y * y))
+    factors, eigvals, kept, paths, res2 = [], [], [], [], []
+    for n in range(y.ndim):
+        s, b, path = sketch_plan(y.shape, ranks, p, q)[n]
+        yn = unfold(y, n)
+        if path == "gram":
+            lam, vec = np.linalg.eigh(yn @ yn.T)
+            order = np.argsort(-lam, kind="stable")
+            u = sign_fix(vec[:, order[: ranks[n]]])
+            lam = lam[order[: ranks[n]]]
+            kept.append(y.shape[n])
+        else:
+            om = philox.omega_mode(seed, n, y.shape, s)
+            qb = np.concatenate(rbki(yn, om, q, tau), axis=1)
+            u, lam, _ = rayleigh_ritz(yn, qb, ranks[n])
+            kept.append(qb.shape[1])
+        factors.append(u)
+        eigvals.append(lam)
+        paths.append(path)
+        nxt = ttm(y, u.T, n)                              # step 6, inside the mode loop
+        res2.append(float(np.sum(y * y) - np.sum(nxt * nxt)))
+        y = nxt
+    return dict(core=y, factors=factors, eigvals=eigvals, kept=kept, path=paths, step_res2=res2,
+                x_norm2=x_norm2, core_norm2=float(np.sum(y * y)))
+
+
 def krylov_basis(x: np.ndarray, n: int, s: int, q: int, seed: int, tau: float = TAU_DEFLATE):
     """Q^(n) of Algorithm 1 for mode n (all blocks concatenated)."""
     x = np.asarray(x, dtype=np.float64)
