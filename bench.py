@@ -45,6 +45,9 @@ def parse_args():
     ap.add_argument("--prec", choices=["bf16", "fp64"], default="bf16")
     ap.add_argument("--size", type=int, default=0,
                     help="cube edge for tucker512 (0 = 512); smaller cases for profiler captures")
+    ap.add_argument("--sequential", action="store_true",
+                    help="sequentially truncated reading (each mode sketched on the contracted tensor)")
+    ap.add_argument("--no-sequential-compare", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
@@ -83,6 +86,29 @@ def plan_passes(dims, ranks, p, q):
             passes += q + 2
             krylov_steps += q + 1
     return passes, krylov_steps
+
+
+def plan_sequential(dims, ranks, p, q, elem0, elem_rest):
+    """Sequential reading: per step n the passes over Y_n (dims R_1..R_{n-1}, I_n..I_N) of
+    Algorithm 1 (1 sketch + q+1 Krylov steps, or 1 Gram pass) plus the product
+    Y_n x_n U^(n)T.  Returns (bytes per decomposition, Krylov-step bytes, Krylov steps)."""
+    cur = list(dims)
+    total = kbytes = ksteps = 0
+    for n, (i_n, r_n) in enumerate(zip(dims, ranks)):
+        e = 1
+        for v in cur:
+            e *= v
+        eb = elem0 if n == 0 else elem_rest
+        s = min(r_n + p, i_n)
+        if s * (q + 1) >= i_n:
+            m = 1
+        else:
+            m = q + 2
+            kbytes += (q + 1) * e * eb
+            ksteps += q + 1
+        total += (m + 1) * e * eb
+        cur[n] = r_n
+    return total, kbytes, ksteps
 
 
 def measured_peaks():
@@ -222,9 +248,17 @@ def run_ours(args):
     wl = make_workload(args.workload, rank, args.size)
     dims = list(wl.x.shape)
     numel = int(np.prod(dims))
-    passes, krylov_steps = plan_passes(dims, wl.ranks, wl.p, wl.q)
-    step_bytes = passes * numel * ELEM_BYTES
     prec = args.prec
+    flags = rb.FLAG_SEQUENTIAL if args.sequential else 0
+    if args.sequential:
+        passes = None
+        e0 = ELEM_BYTES if prec != "fp64" else wl.x.itemsize
+        step_bytes, krylov_bytes, krylov_steps = plan_sequential(dims, wl.ranks, wl.p, wl.q, e0,
+                                                                 ELEM_BYTES if prec != "fp64" else 8)
+    else:
+        passes, krylov_steps = plan_passes(dims, wl.ranks, wl.p, wl.q)
+        step_bytes = passes * numel * ELEM_BYTES
+        krylov_bytes = krylov_steps * numel * (ELEM_BYTES if prec != "fp64" else wl.x.itemsize)
     x = torch.from_numpy(wl.x).cuda()
     stream = torch.cuda.current_stream()
     # K decompositions in flight: stream j runs steps j, j+K, ...; each has its own workspace
@@ -234,7 +268,8 @@ def run_ours(args):
     outs = []
     for j in range(K):
         with torch.cuda.stream(streams[j]):
-            outs.append(rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec=prec, stream=streams[j]))
+            outs.append(rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec=prec, flags=flags,
+                                       stream=streams[j]))
     torch.cuda.synchronize()
     out = outs[0]
 
@@ -246,8 +281,8 @@ def run_ours(args):
         for t in range(nsteps):
             j = t % K
             o = outs[j]
-            rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec=prec, workspace=o["workspace"], out=o,
-                           stream=streams[j])
+            rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec=prec, flags=flags, workspace=o["workspace"],
+                           out=o, stream=streams[j])
         for j in range(K):
             e = torch.cuda.Event()
             e.record(streams[j])
@@ -258,7 +293,8 @@ def run_ours(args):
     # one decomposition alone (latency)
     e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e_a.record(stream)
-    rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec=prec, workspace=out["workspace"], out=out, stream=stream)
+    rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec=prec, flags=flags, workspace=out["workspace"], out=out,
+                   stream=stream)
     e_b.record(stream)
     torch.cuda.synchronize()
     single_ms = e_a.elapsed_time(e_b)
@@ -292,15 +328,15 @@ def run_ours(args):
     kcount, kms = rb.rbki_profile_read(rb.PROF_KRYLOV)
     scount, sms = rb.rbki_profile_read(rb.PROF_SKETCH)
     peak, peak_kind = measured_peaks()
-    per_launch_bytes = numel * ELEM_BYTES if prec != "fp64" else numel * wl.x.itemsize
     roof = None
     if kcount:
+        # algorithmic bytes of all timed Krylov-step launches / their summed duration
         avg = kms / kcount
-        ach = per_launch_bytes / (avg * 1e-3) / 1e9
+        ach = krylov_bytes * args.steps / (kms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(ach / peak, 4),
                 "traffic": (round(KRYLOV_TC_DRAM_BYTES_PER_ELEM * numel) if prec == "bf16"
-                            and KRYLOV_TC_DRAM_BYTES_PER_ELEM else None),
+                            and KRYLOV_TC_DRAM_BYTES_PER_ELEM and not args.sequential else None),
                 "traffic_unit": "bytes per launch (ncu at 448^3, scaled by elements)",
                 "kernel": "krylov_step",
                 "avg_launch_ms": round(avg, 4), "launches": kcount, "peak_kind": peak_kind}
@@ -319,16 +355,16 @@ def run_ours(args):
     if not args.no_e2e:
         xh = torch.from_numpy(wl.x).pin_memory()
         oh = B.alloc_outputs(dims, wl.ranks, None, host=True)
-        flags = rb.FLAG_HOST_IO
-        wsh = torch.empty(rb.rbki_tucker_workspace(xh, wl.ranks, wl.p, wl.q, wl.seed, prec, flags),
+        hflags = flags | rb.FLAG_HOST_IO
+        wsh = torch.empty(rb.rbki_tucker_workspace(xh, wl.ranks, wl.p, wl.q, wl.seed, prec, hflags),
                           dtype=torch.uint8, device="cuda")
         for _ in range(2):
-            rb.rbki_tucker(xh, wl.ranks, wl.p, wl.q, wl.seed, prec=prec, flags=flags, workspace=wsh, out=oh)
+            rb.rbki_tucker(xh, wl.ranks, wl.p, wl.q, wl.seed, prec=prec, flags=hflags, workspace=wsh, out=oh)
         ke = max(3, min(args.steps, 10))
         barrier(world)
         t0 = time.perf_counter()
         for _ in range(ke):
-            rb.rbki_tucker(xh, wl.ranks, wl.p, wl.q, wl.seed, prec=prec, flags=flags, workspace=wsh, out=oh)
+            rb.rbki_tucker(xh, wl.ranks, wl.p, wl.q, wl.seed, prec=prec, flags=hflags, workspace=wsh, out=oh)
         te = (time.perf_counter() - t0) / ke
         te = allreduce_max(te, world)
         d2h = sum(int(np.prod(v.shape)) * v.element_size() for k, v in oh.items() if k in ("core", "norms", "info"))
@@ -340,10 +376,11 @@ def run_ours(args):
 
     fp64_cmp = None
     if not args.no_fp64_compare and prec != "fp64":
-        o64 = rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec="fp64")
+        o64 = rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec="fp64", flags=flags)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec="fp64", workspace=o64["workspace"], out=o64)
+        rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec="fp64", flags=flags, workspace=o64["workspace"],
+                       out=o64)
         torch.cuda.synchronize()
         t64 = time.perf_counter() - t0
         n64 = o64["norms"].cpu().numpy()
@@ -351,6 +388,26 @@ def run_ours(args):
         fp64_cmp = {"ms_per_step": round(t64 * 1e3, 2), "rel_err": rel64,
                     "mixed_rel_err": rel_err, "mixed_vs_fp64": (rel_err - rel64) / rel64}
         del o64
+
+    seq_cmp = None
+    if not args.sequential and not args.no_sequential_compare:
+        # the sequentially truncated reading on the same input: one decomposition alone
+        osq = rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec=prec, flags=rb.FLAG_SEQUENTIAL)
+        times = []
+        for _ in range(4):
+            e_a.record(stream)
+            rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec=prec, flags=rb.FLAG_SEQUENTIAL,
+                           workspace=osq["workspace"], out=osq, stream=stream)
+            e_b.record(stream)
+            torch.cuda.synchronize()
+            times.append(e_a.elapsed_time(e_b))
+        nsq = osq["norms"].cpu().numpy()
+        e_sq = 2 if prec != "fp64" else wl.x.itemsize
+        sq_bytes = plan_sequential(dims, wl.ranks, wl.p, wl.q, e_sq, 2 if prec != "fp64" else 8)[0]
+        seq_cmp = {"single_decomposition_ms": round(min(times[1:]), 4),
+                   "rel_err": float(np.sqrt(max(nsq[0] - nsq[1], 0.0) / nsq[0])),
+                   "bytes_per_decomposition": sq_bytes}
+        del osq
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -364,12 +421,14 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if prec == "bf16" else "f64",
             "data": "synthetic",
             "config": {"workload": f"{args.workload}: {'x'.join(map(str, dims))} {wl.x.dtype}, ranks {wl.ranks}, "
-                                   f"p={wl.p}, q={wl.q}, {prec} products",
+                                   f"p={wl.p}, q={wl.q}, {prec} products"
+                                   + (", sequential truncation" if args.sequential else ""),
                        "inflight": K, "single_decomposition_ms": round(single_ms, 4),
                        "passes_per_step": passes, "krylov_steps_per_step": krylov_steps,
                        "bytes_per_step": step_bytes, "l2": "inputs larger than L2 (no flush)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roof, "breakdown": breakdown, "rel_err": rel_err, "fp64_compare": fp64_cmp,
+            "sequential_compare": seq_cmp,
             "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "cpu_baseline": cpu,
         }
         print(json.dumps(line))
@@ -417,6 +476,9 @@ def run_reference(args):
     numel = x.size
 
     def step(k):
+        if args.sequential:
+            rbki.rbki_st_tucker(x, wl.ranks, wl.p, wl.q, wl.seed)
+            return plan_sequential(dims, wl.ranks, wl.p, wl.q, ELEM_BYTES, ELEM_BYTES)[0]
         n = k % x.ndim
         s = min(wl.ranks[n] + wl.p, x.shape[n])
         xn = unfold(x, n)
@@ -441,8 +503,10 @@ def run_reference(args):
         "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(dt / args.steps * 1e3, 2), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": {"workload": f"{args.workload}: {'x'.join(map(str, dims))}, ranks {wl.ranks}, p={wl.p}, q={wl.q}",
-                   "sample": "one mode's Algorithm 1 + Rayleigh-Ritz per step"},
+        "config": {"workload": f"{args.workload}: {'x'.join(map(str, dims))}, ranks {wl.ranks}, p={wl.p}, q={wl.q}"
+                               + (", sequential truncation" if args.sequential else ""),
+                   "sample": ("one full sequentially truncated decomposition per step" if args.sequential
+                              else "one mode's Algorithm 1 + Rayleigh-Ritz per step")},
         "cpu_baseline": {"value": round(value, 3), "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle",
                          "sample": "FP64 NumPy oracle, one mode's Algorithm 1 + Rayleigh-Ritz per step, X passes "
                                    f"counted at {ELEM_BYTES} B/element"},

@@ -67,7 +67,11 @@ enum {
     RBKI_FLAG_HOST_IO = 1u,        /* X and outputs in host memory (end-to-end call) */
     RBKI_FLAG_SPLIT = 2u,          /* mixed path: carry the skinny operands (Q, Y, Omega, U) as
                                       hi + lo BF16 pairs: ~FP32-accurate products, 2x MMA work */
-    RBKI_FLAG_SERIAL_MODES = 4u    /* run modes one after another on `stream` */
+    RBKI_FLAG_SERIAL_MODES = 4u,   /* run modes one after another on `stream` */
+    RBKI_FLAG_SEQUENTIAL = 8u      /* sequentially truncated reading of Algorithm 2 (ST-HOSVD):
+                                      mode n is sketched on Y_n = X x_1 U^(1)T .. x_{n-1} U^(n-1)T,
+                                      modes in the order 1..N; the default (HOSVD reading)
+                                      sketches every mode on X itself */
 };
 
 typedef struct {
@@ -112,7 +116,11 @@ rbki_status rbki_tucker_workspace(const rbki_tensor* X, const rbki_params* prm, 
  * the exact truncated-HOSVD factor); otherwise W = X_(n) Omega, Q_0 = orth(W),
  * Q_{j+1} = orth(X_(n) X_(n)^T Q_j) against all earlier blocks, Z = Q^T X X^T Q,
  * U = Q * leading eigenvectors of Z.  Omega's entries are the Philox4x32-10 +
- * Box-Muller Gaussians keyed by (seed, n, column, s). */
+ * Box-Muller Gaussians keyed by (seed, n, column, s).
+ * RBKI_FLAG_SEQUENTIAL: the sequentially truncated reading - the same per-mode steps on
+ * Y_n (dims R_1..R_{n-1}, I_n..I_N; Omega keyed by Y_n's unfolding columns), modes taken in
+ * the order 1..N, Y_{n+1} = Y_n x_n U^(n)T, G = Y_{N+1}.  Works with every other flag and
+ * with rbki_htr and the server; the workspace adds two buffers of the largest Y_n. */
 rbki_status rbki_tucker(const rbki_tensor* X, const rbki_params* prm, void* workspace,
                         size_t workspace_bytes, const rbki_tucker_out* out, void* stream);
 

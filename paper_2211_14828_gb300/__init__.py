@@ -5,5 +5,5 @@ from ._binding import (  # noqa: F401
     rbki_syev, rbki_tucker, rbki_htr, RbkiServer, rbki_tucker_workspace, rbki_profile_enable, rbki_profile_reset,
     rbki_profile_read, PROF_KRYLOV, PROF_SKETCH, PROF_GRAM, PROF_TTM, PROF_STAGE,
     F64, F32, BF16, F16, PREC_FP64, PREC_BF16, PREC_FP16, FLAG_HOST_IO, FLAG_SPLIT,
-    FLAG_SERIAL_MODES,
+    FLAG_SERIAL_MODES, FLAG_SEQUENTIAL,
 )

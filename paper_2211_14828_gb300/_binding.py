@@ -18,7 +18,7 @@ OK, PENDING, W_DEFLATED = 0, 1, 2
 E_INVAL, E_NOMEM, E_CUDA, E_UNSUPPORTED, E_TIMEOUT, E_BUSY, E_CANCELLED, E_NOTFOUND = range(-1, -9, -1)
 F64, F32, BF16, F16 = 0, 1, 2, 3
 PREC_FP64, PREC_BF16, PREC_FP16 = 0, 1, 2
-FLAG_HOST_IO, FLAG_SPLIT, FLAG_SERIAL_MODES = 1, 2, 4
+FLAG_HOST_IO, FLAG_SPLIT, FLAG_SERIAL_MODES, FLAG_SEQUENTIAL = 1, 2, 4, 8
 
 
 class rbki_tensor(C.Structure):
@@ -298,11 +298,11 @@ class RbkiServer:
         self._h = h
         self._live = {}
 
-    def submit(self, x, ranks, p, q, seed, prec="bf16", out=None, after_stream=None):
+    def submit(self, x, ranks, p, q, seed, prec="bf16", out=None, after_stream=None, flags=0):
         """Queues a request; its kernels wait for the work already queued on `after_stream`
         (default: torch's current stream, where x and out were made)."""
         torch = _torch()
-        t, prm = make_tensor(x), make_params(ranks, p, q, seed, prec)
+        t, prm = make_tensor(x), make_params(ranks, p, q, seed, prec, flags)
         if out is None:
             out = alloc_outputs(x.shape, ranks, x.device)
         o = make_out(out)

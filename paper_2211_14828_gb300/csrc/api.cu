@@ -132,9 +132,35 @@ rbki_status make_plan(const rbki_tensor* X, const rbki_params* prm, Plan& pl) {
     });
     pl.seed = prm->seed;
     pl.flags = prm->flags;
+    pl.prm = *prm;
     pl.ranks_numel = 1;
     for (int n = 0; n < pl.N; ++n) pl.ranks_numel *= prm->ranks[n];
+    pl.sequential = (prm->flags & RBKI_FLAG_SEQUENTIAL) != 0;
+    if (pl.sequential) {
+        // every step's plan must exist (modes already truncated take the Gram path on R_k)
+        int64_t cur[RBKI_MAX_ORDER];
+        for (int n = 0; n < pl.N; ++n) cur[n] = pl.dims[n];
+        for (int n = 0; n < pl.N; ++n) {
+            Plan sp;
+            RBKI_TRY(step_plan(pl, n, cur, n == 0 ? pl.dtype : (pl.mixed ? RBKI_F32 : RBKI_F64), sp));
+            cur[n] = pl.mode[n].R;
+        }
+    }
     return RBKI_OK;
+}
+
+// Plan of step n of the sequential reading: the tensor Y_n of dims `cur` (modes < n already
+// truncated to R_k), the caller's parameters without the sequential flag.
+rbki_status step_plan(const Plan& pl, int n, const int64_t* cur, int dtype, Plan& sp) {
+    (void)n;
+    rbki_tensor t{};
+    t.order = pl.N;
+    t.dtype = dtype;
+    for (int k = 0; k < pl.N; ++k) t.dims[k] = cur[k];
+    t.data = nullptr;
+    rbki_params p = pl.prm;
+    p.flags &= ~(uint32_t)RBKI_FLAG_SEQUENTIAL;
+    return make_plan(&t, &p, sp);
 }
 
 // Workspace layout.  carve() with base == nullptr only measures.
@@ -150,7 +176,57 @@ struct Carver {
     }
 };
 
+// Sequential reading: the step plans share the front of the workspace (each carves from
+// the base; the largest sets the size), then the two Y buffers, then the operand image of
+// the first mode product when it runs on the tensor cores.
+static void carve_sequential(Plan& pl, void* ws) {
+    pl.ydtype = pl.mixed ? RBKI_F32 : RBKI_F64;
+    int64_t cur[RBKI_MAX_ORDER];
+    for (int n = 0; n < pl.N; ++n) cur[n] = pl.dims[n];
+    size_t front = 0, ymax = 0;
+    for (int n = 0; n < pl.N; ++n) {
+        Plan sp;
+        if (step_plan(pl, n, cur, n == 0 ? pl.dtype : pl.ydtype, sp) != RBKI_OK) continue;  // checked in make_plan
+        carve(sp, nullptr);
+        front = std::max(front, sp.ws_bytes);
+        cur[n] = pl.mode[n].R;
+        if (n < pl.N - 1) {
+            size_t e = 1;
+            for (int k = 0; k < pl.N; ++k) e *= (size_t)cur[k];
+            ymax = std::max(ymax, e);
+        }
+    }
+    Carver c(ws);
+    c.take<char>(front);
+    pl.ybuf[0] = c.take<char>(ymax * dtype_size(pl.ydtype));
+    pl.ybuf[1] = c.take<char>(ymax * dtype_size(pl.ydtype));
+    {
+        const ModePlan& m = pl.mode[0];
+        View v{nullptr, pl.stream_dtype, m.A, m.I, m.C};
+        pl.ttm_N = (int)rup(2 * m.R, 16);
+        pl.ttm_tc = pl.mixed && pl.N > 1 && m.R <= 32 && tc::supported(v, tc::TTM, pl.ttm_N);
+        if (pl.ttm_tc) pl.ttm_img = c.take<char>(tc::image_bytes_skinny(v, pl.ttm_N));
+    }
+    pl.ws_bytes = c.off + 256;
+    pl.ws_base = ws;
+    pl.scal = nullptr;
+    pl.err = nullptr;
+    if (ws) {
+        // the scalars and the error word sit at the same offsets in every step plan
+        Plan sp;
+        if (step_plan(pl, 0, pl.dims, pl.dtype, sp) == RBKI_OK) {
+            carve(sp, ws);
+            pl.scal = sp.scal;
+            pl.err = sp.err;
+        }
+    }
+}
+
 void carve(Plan& pl, void* ws) {
+    if (pl.sequential) {
+        carve_sequential(pl, ws);
+        return;
+    }
     Carver c(ws);
     pl.scal = c.take<double>(4096);
     pl.err = c.take<int32_t>(64);
@@ -399,7 +475,70 @@ static rbki_status pool_streams(cudaStream_t caller, cudaStream_t* out, int n) {
     return RBKI_OK;
 }
 
+// Algorithm 2, sequentially truncated reading: for n = 1..N, U^(n) from Algorithm 1 on
+// Y_n (Y_1 = X), then Y_{n+1} = Y_n x_n U^(n)T; the last product is the core G.  Every step
+// depends on the previous one, so all of it runs on the caller's stream.  Mixed precision:
+// Y_n is kept in FP32 and streamed as BF16/FP16 (staged per step); the first product runs
+// on the tensor cores from the staged X when the shape allows.
+static rbki_status run_sequential(Plan& pl, const rbki_tucker_out* out, cudaStream_t st) {
+    if (!pl.ws_base || !pl.scal || !pl.err) return set_error(RBKI_E_INVAL, "sequential plan not carved");
+    double* norms = out->norms ? out->norms : pl.scal;
+    RBKI_CUDA_TRY(cudaMemsetAsync(pl.err, 0, sizeof(int32_t), st));
+    int64_t cur[RBKI_MAX_ORDER];
+    for (int n = 0; n < pl.N; ++n) cur[n] = pl.dims[n];
+    const void* src = pl.xin;
+    int src_dtype = pl.dtype;
+    for (int n = 0; n < pl.N; ++n) {
+        Plan sp;
+        RBKI_TRY(step_plan(pl, n, cur, src_dtype, sp));
+        carve(sp, pl.ws_base);
+        if (sp.err != pl.err) return set_error(RBKI_E_INVAL, "sequential plan: error word moved");
+        sp.xin = src;
+        const int64_t numel = sp.numel;
+        double* nrm = n == 0 ? norms : sp.scal + 8;
+        int tok = prof_begin(RBKI_PROF_STAGE, st);
+        if (sp.stage) {
+            RBKI_TRY(stage_cuda(src, src_dtype, numel, sp.xs, sp.stream_dtype, sp.scal + 64, nrm, st));
+            sp.xstream = sp.xs;
+        } else {
+            sp.xstream = src;
+            if (n == 0) RBKI_TRY(sumsq_cuda(src, src_dtype, numel, sp.scal + 64, nrm, st));
+        }
+        prof_end(tok, st);
+        const ModePlan& m = sp.mode[n];
+        RBKI_TRY(mode_factor(sp, m, out->factors[n], out->eigvals[n], out->info, st));
+        // Y_{n+1} = Y_n x_n U^(n)T
+        const bool last = n == pl.N - 1;
+        void* dst = last ? (void*)out->core : pl.ybuf[n & 1];
+        const int dst_dtype = last ? RBKI_F64 : pl.ydtype;
+        const int R = m.R;
+        tok = prof_begin(RBKI_PROF_TTM, st);
+        if (n == 0 && pl.ttm_tc && !last) {
+            View v{sp.xstream, sp.stream_dtype, m.A, m.I, m.C};
+            RBKI_TRY(tc::skinny_image(out->factors[0], R, m.I, R, pl.ttm_N, true, sp.stream_dtype == RBKI_F16,
+                                      pl.ttm_img, st));
+            RBKI_TRY(tc::stream_tc(tc::TTM, v, pl.ttm_N, R, true, pl.ttm_img, nullptr, nullptr, (float*)dst,
+                                   pl.err, st));
+        } else {
+            View v{src, src_dtype, m.A, m.I, m.C};
+            if (n > 0 && dst_dtype == RBKI_F64 && R <= 32 && (src_dtype == RBKI_F64 || src_dtype == RBKI_F32))
+                RBKI_TRY(ttm_small_cuda(v, out->factors[n], R, R, (double*)dst, pl.mixed, st));
+            else
+                RBKI_TRY(ttm_cuda(v, out->factors[n], R, R, dst, dst_dtype, pl.mixed, st));
+        }
+        prof_end(tok, st);
+        cur[n] = R;
+        src = dst;
+        src_dtype = dst_dtype;
+    }
+    RBKI_TRY(sumsq_cuda(out->core, RBKI_F64, pl.ranks_numel, pl.scal + 64, norms + 1, st));
+    if (out->info)
+        RBKI_CUDA_TRY(cudaMemcpyAsync(out->info + 2 * pl.N, pl.err, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+    return RBKI_OK;
+}
+
 rbki_status run_tucker(Plan& pl, const rbki_tucker_out* out, cudaStream_t st, const cudaStream_t* mode_streams) {
+    if (pl.sequential) return run_sequential(pl, out, st);
     double* norms = out->norms ? out->norms : pl.scal;
     RBKI_CUDA_TRY(cudaMemsetAsync(pl.err, 0, sizeof(int32_t), st));
     int tok = prof_begin(RBKI_PROF_STAGE, st);
@@ -598,6 +737,7 @@ rbki_status rbki_mode_basis(const rbki_tensor* X, const rbki_params* prm, int32_
     Plan pl;
     RBKI_TRY(make_plan(X, prm, pl));
     if (mode < 0 || mode >= pl.N) return set_error(RBKI_E_INVAL, "mode out of range");
+    if (pl.sequential) return set_error(RBKI_E_INVAL, "the basis is defined on X: no RBKI_FLAG_SEQUENTIAL");
     if (pl.mode[mode].gram) return set_error(RBKI_E_INVAL, "mode uses the Gram path (b >= I)");
     if (!Q) return set_error(RBKI_E_INVAL, "Q is NULL");
     carve(pl, nullptr);

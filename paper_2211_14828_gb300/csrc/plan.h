@@ -49,6 +49,13 @@ struct Plan {
     int ttm_N = 0;
     void* ttm_img = nullptr;
     size_t ws_bytes = 0;
+    // sequential truncation (RBKI_FLAG_SEQUENTIAL): step n works on Y_n = X x_1 U^(1)T ..
+    // x_{n-1} U^(n-1)T through a plan of its own carved at the front of the workspace
+    bool sequential = false;
+    rbki_params prm{};
+    void* ws_base = nullptr;
+    void* ybuf[2] = {nullptr, nullptr};  // Y_1 .. Y_{N-1}, ping-pong (FP64, FP32 when mixed)
+    int ydtype = 0;
     // bound at run time
     const void* xin = nullptr;
     const void* xstream = nullptr;
@@ -68,6 +75,7 @@ rbki_status validate_tensor(const rbki_tensor* X);
 size_t host_io_bytes(const Plan& pl);
 rbki_status make_plan(const rbki_tensor* X, const rbki_params* prm, Plan& pl);
 void carve(Plan& pl, void* ws);    // ws == nullptr: only measures pl.ws_bytes
+rbki_status step_plan(const Plan& pl, int n, const int64_t* cur, int dtype, Plan& sp);
 // mode_streams: N streams for the concurrent per-mode chains (nullptr: the per-device pool)
 rbki_status run_tucker(Plan& pl, const rbki_tucker_out* out, cudaStream_t st,
                        const cudaStream_t* mode_streams = nullptr);

@@ -75,3 +75,22 @@ def test_server_argument_checks_without_gpu(L):
     assert L.rbki_cancel(None, ctypes.c_uint64(1)) == -1
     assert L.rbki_server_drain(None, ctypes.c_double(0.0)) == -1
     assert L.rbki_server_destroy(None) == -1
+
+
+def test_sequential_flag_without_gpu(L):
+    """The sequentially truncated reading adds two buffers of the largest Y_n to the
+    workspace; the step-level basis call (defined on X) refuses the flag."""
+    import torch
+    import paper_2211_14828_gb300 as rb
+    from paper_2211_14828_gb300 import _binding as B
+    x = torch.zeros((64, 48, 40), dtype=torch.float64)
+    ranks = [5, 6, 7]
+    ws = rb.rbki_tucker_workspace(x, ranks, 2, 1, prec="fp64")
+    ws_seq = rb.rbki_tucker_workspace(x, ranks, 2, 1, prec="fp64", flags=rb.FLAG_SEQUENTIAL)
+    assert ws_seq >= 2 * 5 * 48 * 40 * 8
+    assert ws_seq < ws + 2 * 5 * 48 * 40 * 8 + (1 << 20)
+    t = B.make_tensor(x)
+    prm = B.make_params(ranks, 2, 1, 0, "fp64", rb.FLAG_SEQUENTIAL)
+    st = L.rbki_mode_basis(ctypes.byref(t), ctypes.byref(prm), 0, ctypes.c_void_p(16), ctypes.c_void_p(16),
+                           ctypes.c_size_t(1 << 30), None)
+    assert st == B.E_INVAL
