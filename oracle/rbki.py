@@ -39,7 +39,7 @@ from typing import Dict, List, Sequence
 
 import numpy as np
 
-from . import philox
+from . import philox, sampling
 from .tensor import ttm, unfold
 
 TAU_DEFLATE = 1e-6
@@ -136,9 +136,26 @@ def rayleigh_ritz(xn: np.ndarray, q_basis: np.ndarray, r: int):
     return sign_fix(u), lam[:r], z
 
 
+def krylov_mode(xn: np.ndarray, x: np.ndarray, n: int, s: int, r: int, q: int, seed: int, omega: float,
+                tau: float = TAU_DEFLATE):
+    """Algorithms 1-2 for a Krylov-path mode of tensor x (unfolding xn): (U, lambda, kept).
+    0 < omega < 1: the Krylov space and Z come from the sampled Y (oracle.sampling)."""
+    if 0.0 < omega < 1.0:
+        y, _ = sampling.sampled_mode(x, n, seed, omega)
+        om = philox.omega(seed, n, np.arange(y.shape[1], dtype=np.uint64), s)
+        qb = np.concatenate(rbki(y, om, q, tau), axis=1)
+        u, lam, _ = rayleigh_ritz(y, qb, r)
+    else:
+        om = philox.omega_mode(seed, n, x.shape, s)
+        qb = np.concatenate(rbki(xn, om, q, tau), axis=1)
+        u, lam, _ = rayleigh_ritz(xn, qb, r)
+    return u, lam, qb.shape[1]
+
+
 def rbki_tucker(x: np.ndarray, ranks: Sequence[int], p: int, q: int, seed: int,
-                tau: float = TAU_DEFLATE) -> Dict:
-    """Algorithm 2 (rBKI-TK), HOSVD reading: every mode sketches the original X."""
+                tau: float = TAU_DEFLATE, omega: float = 1.0) -> Dict:
+    """Algorithm 2 (rBKI-TK), HOSVD reading: every mode sketches the original X.
+    0 < omega < 1: partial column sampling of the Krylov construction (oracle.sampling)."""
     x = np.asarray(x, dtype=np.float64)
     plan = sketch_plan(x.shape, ranks, p, q)
     factors, eigvals, kept, paths = [], [], [], []
@@ -151,10 +168,8 @@ def rbki_tucker(x: np.ndarray, ranks: Sequence[int], p: int, q: int, seed: int,
             lam = lam[order[: ranks[n]]]
             kept.append(x.shape[n])
         else:
-            om = philox.omega_mode(seed, n, x.shape, s)
-            qb = np.concatenate(rbki(xn, om, q, tau), axis=1)
-            u, lam, _ = rayleigh_ritz(xn, qb, ranks[n])
-            kept.append(qb.shape[1])
+            u, lam, k = krylov_mode(xn, x, n, s, ranks[n], q, seed, omega, tau)
+            kept.append(k)
         factors.append(u)
         eigvals.append(lam)
         paths.append(path)
@@ -166,7 +181,7 @@ def rbki_tucker(x: np.ndarray, ranks: Sequence[int], p: int, q: int, seed: int,
 
 
 def rbki_st_tucker(x: np.ndarray, ranks: Sequence[int], p: int, q: int, seed: int,
-                   tau: float = TAU_DEFLATE) -> Dict:
+                   tau: float = TAU_DEFLATE, omega: float = 1.0) -> Dict:
     """Algorithm 2 read literally (sequential truncation, the other reading of step 6): the
     modes are taken in order n = 1..N, and mode n is sketched from the tensor already
     contracted by the earlier factors, Y_n = X x_1 U^(1)T ... x_{n-1} U^(n-1)T; after U^(n)
@@ -186,10 +201,8 @@ def rbki_st_tucker(x: np.ndarray, ranks: Sequence[int], p: int, q: int, seed: in
             lam = lam[order[: ranks[n]]]
             kept.append(y.shape[n])
         else:
-            om = philox.omega_mode(seed, n, y.shape, s)
-            qb = np.concatenate(rbki(yn, om, q, tau), axis=1)
-            u, lam, _ = rayleigh_ritz(yn, qb, ranks[n])
-            kept.append(qb.shape[1])
+            u, lam, k = krylov_mode(yn, y, n, s, ranks[n], q, seed, omega, tau)
+            kept.append(k)
         factors.append(u)
         eigvals.append(lam)
         paths.append(path)
