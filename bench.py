@@ -17,6 +17,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -48,6 +49,8 @@ def parse_args():
     ap.add_argument("--sequential", action="store_true",
                     help="sequentially truncated reading (each mode sketched on the contracted tensor)")
     ap.add_argument("--no-sequential-compare", action="store_true")
+    ap.add_argument("--omega", type=float, default=0.0,
+                    help="column sampling rate of the Krylov construction (0 < omega < 1)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
@@ -86,6 +89,39 @@ def plan_passes(dims, ranks, p, q):
             passes += q + 2
             krylov_steps += q + 1
     return passes, krylov_steps
+
+
+def sampled_columns(dims, n, omega):
+    """Columns of the sampled unfolding Y of mode n (128-column units, ragged ones padded)."""
+    a = 1
+    for v in dims[:n]:
+        a *= v
+    c = 1
+    for v in dims[n + 1:]:
+        c *= v
+    nu = a * -(-c // 128) if c > 1 else -(-a // 128)
+    return 128 * int(min(max(math.ceil(omega * nu), 1), nu))
+
+
+def plan_sampled(dims, ranks, p, q, omega, elem):
+    """Bytes of one decomposition with partial column sampling: per Krylov mode the gather
+    (read the kept columns, write Y) and 1 sketch + (q+1) Krylov passes over Y; per Gram
+    mode one pass of X; the first core product reads X.  Returns (bytes, Krylov bytes,
+    Krylov steps)."""
+    numel = 1
+    for v in dims:
+        numel *= v
+    total, kbytes, ksteps = numel * elem, 0, 0
+    for n, (i_n, r_n) in enumerate(zip(dims, ranks)):
+        s = min(r_n + p, i_n)
+        if s * (q + 1) >= i_n:
+            total += numel * elem
+            continue
+        y = sampled_columns(dims, n, omega) * i_n * elem
+        total += 2 * y + (q + 2) * y
+        kbytes += (q + 1) * y
+        ksteps += q + 1
+    return total, kbytes, ksteps
 
 
 def plan_sequential(dims, ranks, p, q, elem0, elem_rest):
@@ -250,7 +286,13 @@ def run_ours(args):
     numel = int(np.prod(dims))
     prec = args.prec
     flags = rb.FLAG_SEQUENTIAL if args.sequential else 0
-    if args.sequential:
+    if args.omega > 0 and args.sequential:
+        raise SystemExit("--omega and --sequential: byte accounting of the combination is not implemented")
+    if args.omega > 0:
+        passes = None
+        step_bytes, krylov_bytes, krylov_steps = plan_sampled(dims, wl.ranks, wl.p, wl.q, args.omega,
+                                                              ELEM_BYTES if prec != "fp64" else wl.x.itemsize)
+    elif args.sequential:
         passes = None
         e0 = ELEM_BYTES if prec != "fp64" else wl.x.itemsize
         step_bytes, krylov_bytes, krylov_steps = plan_sequential(dims, wl.ranks, wl.p, wl.q, e0,
@@ -269,6 +311,7 @@ def run_ours(args):
     for j in range(K):
         with torch.cuda.stream(streams[j]):
             outs.append(rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec=prec, flags=flags,
+                                       omega=args.omega,
                                        stream=streams[j]))
     torch.cuda.synchronize()
     out = outs[0]
@@ -281,8 +324,8 @@ def run_ours(args):
         for t in range(nsteps):
             j = t % K
             o = outs[j]
-            rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec=prec, flags=flags, workspace=o["workspace"],
-                           out=o, stream=streams[j])
+            rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec=prec, flags=flags, omega=args.omega,
+                           workspace=o["workspace"], out=o, stream=streams[j])
         for j in range(K):
             e = torch.cuda.Event()
             e.record(streams[j])
@@ -293,8 +336,8 @@ def run_ours(args):
     # one decomposition alone (latency)
     e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e_a.record(stream)
-    rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec=prec, flags=flags, workspace=out["workspace"], out=out,
-                   stream=stream)
+    rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec=prec, flags=flags, omega=args.omega,
+                   workspace=out["workspace"], out=out, stream=stream)
     e_b.record(stream)
     torch.cuda.synchronize()
     single_ms = e_a.elapsed_time(e_b)
@@ -336,13 +379,15 @@ def run_ours(args):
         roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(ach / peak, 4),
                 "traffic": (round(KRYLOV_TC_DRAM_BYTES_PER_ELEM * numel) if prec == "bf16"
-                            and KRYLOV_TC_DRAM_BYTES_PER_ELEM and not args.sequential else None),
+                            and KRYLOV_TC_DRAM_BYTES_PER_ELEM and not args.sequential
+                            and args.omega <= 0 else None),
                 "traffic_unit": "bytes per launch (ncu at 448^3, scaled by elements)",
                 "kernel": "krylov_step",
                 "avg_launch_ms": round(avg, 4), "launches": kcount, "peak_kind": peak_kind}
     breakdown = {}
     for name, cls in (("krylov", rb.PROF_KRYLOV), ("sketch", rb.PROF_SKETCH), ("gram", rb.PROF_GRAM),
-                      ("ttm1", rb.PROF_TTM), ("stage", rb.PROF_STAGE)):
+                      ("ttm1", rb.PROF_TTM), ("stage", rb.PROF_STAGE),
+                      ("sample", rb.PROF_SAMPLE)):
         c, t = rb.rbki_profile_read(cls)
         if c:
             breakdown[name] = {"ms_per_step": round(t / args.steps, 4), "launches_per_step": c / args.steps}
@@ -356,15 +401,17 @@ def run_ours(args):
         xh = torch.from_numpy(wl.x).pin_memory()
         oh = B.alloc_outputs(dims, wl.ranks, None, host=True)
         hflags = flags | rb.FLAG_HOST_IO
-        wsh = torch.empty(rb.rbki_tucker_workspace(xh, wl.ranks, wl.p, wl.q, wl.seed, prec, hflags),
+        wsh = torch.empty(rb.rbki_tucker_workspace(xh, wl.ranks, wl.p, wl.q, wl.seed, prec, hflags, args.omega),
                           dtype=torch.uint8, device="cuda")
         for _ in range(2):
-            rb.rbki_tucker(xh, wl.ranks, wl.p, wl.q, wl.seed, prec=prec, flags=hflags, workspace=wsh, out=oh)
+            rb.rbki_tucker(xh, wl.ranks, wl.p, wl.q, wl.seed, prec=prec, flags=hflags, omega=args.omega,
+                           workspace=wsh, out=oh)
         ke = max(3, min(args.steps, 10))
         barrier(world)
         t0 = time.perf_counter()
         for _ in range(ke):
-            rb.rbki_tucker(xh, wl.ranks, wl.p, wl.q, wl.seed, prec=prec, flags=hflags, workspace=wsh, out=oh)
+            rb.rbki_tucker(xh, wl.ranks, wl.p, wl.q, wl.seed, prec=prec, flags=hflags, omega=args.omega,
+                           workspace=wsh, out=oh)
         te = (time.perf_counter() - t0) / ke
         te = allreduce_max(te, world)
         d2h = sum(int(np.prod(v.shape)) * v.element_size() for k, v in oh.items() if k in ("core", "norms", "info"))
@@ -376,11 +423,11 @@ def run_ours(args):
 
     fp64_cmp = None
     if not args.no_fp64_compare and prec != "fp64":
-        o64 = rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec="fp64", flags=flags)
+        o64 = rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec="fp64", flags=flags, omega=args.omega)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec="fp64", flags=flags, workspace=o64["workspace"],
-                       out=o64)
+        rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec="fp64", flags=flags, omega=args.omega,
+                       workspace=o64["workspace"], out=o64)
         torch.cuda.synchronize()
         t64 = time.perf_counter() - t0
         n64 = o64["norms"].cpu().numpy()
@@ -390,7 +437,7 @@ def run_ours(args):
         del o64
 
     seq_cmp = None
-    if not args.sequential and not args.no_sequential_compare:
+    if not args.sequential and not args.no_sequential_compare and args.omega <= 0:
         # the sequentially truncated reading on the same input: one decomposition alone
         osq = rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec=prec, flags=rb.FLAG_SEQUENTIAL)
         times = []
@@ -422,7 +469,8 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": f"{args.workload}: {'x'.join(map(str, dims))} {wl.x.dtype}, ranks {wl.ranks}, "
                                    f"p={wl.p}, q={wl.q}, {prec} products"
-                                   + (", sequential truncation" if args.sequential else ""),
+                                   + (", sequential truncation" if args.sequential else "")
+                                   + (f", column sampling omega={args.omega}" if args.omega > 0 else ""),
                        "inflight": K, "single_decomposition_ms": round(single_ms, 4),
                        "passes_per_step": passes, "krylov_steps_per_step": krylov_steps,
                        "bytes_per_step": step_bytes, "l2": "inputs larger than L2 (no flush)",
@@ -485,6 +533,9 @@ def run_reference(args):
         if s * (wl.q + 1) >= x.shape[n]:
             np.linalg.eigh(xn @ xn.T)
             return numel * ELEM_BYTES
+        if args.omega > 0:
+            rbki.krylov_mode(xn, x, n, s, wl.ranks[n], wl.q, wl.seed, args.omega)
+            return (wl.q + 4) * sampled_columns(dims, n, args.omega) * x.shape[n] * ELEM_BYTES
         om = philox.omega_mode(wl.seed, n, x.shape, s)
         qb = np.concatenate(rbki.rbki(xn, om, wl.q), axis=1)
         rbki.rayleigh_ritz(xn, qb, wl.ranks[n])
@@ -504,7 +555,8 @@ def run_reference(args):
         "ms_per_step": round(dt / args.steps * 1e3, 2), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
         "config": {"workload": f"{args.workload}: {'x'.join(map(str, dims))}, ranks {wl.ranks}, p={wl.p}, q={wl.q}"
-                               + (", sequential truncation" if args.sequential else ""),
+                               + (", sequential truncation" if args.sequential else "")
+                               + (f", column sampling omega={args.omega}" if args.omega > 0 else ""),
                    "sample": ("one full sequentially truncated decomposition per step" if args.sequential
                               else "one mode's Algorithm 1 + Rayleigh-Ritz per step")},
         "cpu_baseline": {"value": round(value, 3), "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle",

@@ -90,6 +90,14 @@ typedef struct {
     uint64_t seed;
     int32_t prec;                    /* RBKI_PREC_* */
     uint32_t flags;                  /* RBKI_FLAG_* */
+    double omega;                    /* column sampling rate of the Krylov construction
+                                        (Sec. 3.2 after Table 2, Fig. 5): 0 < omega < 1
+                                        builds Krylov-path modes from ceil(omega U_n) of the
+                                        U_n 128-column units of X_(n) (units with the
+                                        smallest Philox4x32-10 keys, counter (u lo, u hi, n,
+                                        0x53414D50), key = seed); Z = Q^T Y Y^T Q on the
+                                        sampled Y; the core uses all of X.  <= 0 or >= 1:
+                                        no sampling.  Must be finite. */
 } rbki_params;
 
 /* Algorithm 2 outputs (caller-owned). */
@@ -206,6 +214,12 @@ rbki_status rbki_krylov_product_noalloc(const rbki_tensor* X, int32_t mode, int3
 rbki_status rbki_mode_basis(const rbki_tensor* X, const rbki_params* prm, int32_t mode,
                             double* Q, void* workspace, size_t workspace_bytes, void* stream);
 
+/* Partial column sampling, the choice of units alone: units[0..kept-1] (device int32) =
+ * the `kept` of n_units units with the smallest keys of rbki_params.omega's rule for mode
+ * `mode`, ascending.  1 <= kept <= n_units < 2^31, else RBKI_E_INVAL. */
+rbki_status rbki_sample_units(uint64_t seed, int32_t mode, int64_t n_units, int64_t kept,
+                              int32_t* units, void* stream);
+
 /* Symmetric eigensolver used for Algorithm 2 step 4: A (n x n, FP64, symmetric) ->
  * eigenvalues descending in w (n) and eigenvectors as columns of V (n x n row-major). */
 rbki_status rbki_syev(const double* A, int32_t n, double* w, double* V,
@@ -215,7 +229,7 @@ rbki_status rbki_syev_workspace(int32_t n, size_t* bytes);
 /* ---- diagnostics -------------------------------------------------------------------- */
 /* Kernel classes timed by the profiling hook. */
 enum { RBKI_PROF_KRYLOV = 0, RBKI_PROF_SKETCH = 1, RBKI_PROF_GRAM = 2, RBKI_PROF_TTM = 3,
-       RBKI_PROF_STAGE = 4, RBKI_PROF_COUNT = 5 };
+       RBKI_PROF_STAGE = 4, RBKI_PROF_SAMPLE = 5, RBKI_PROF_COUNT = 6 };
 /* When on, each streaming launch (Krylov step, sketch, Gram pass, first TTM, staging) is
  * bracketed by CUDA events recorded on the stream it runs on.  Off by default. */
 void rbki_profile_enable(int32_t on);

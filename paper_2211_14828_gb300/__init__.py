@@ -3,7 +3,8 @@ C ABI in include/rbki.h, with a thin ctypes binding."""
 from ._binding import (  # noqa: F401
     LIB_PATH, RbkiError, lib, rbki_kernel_launches, rbki_krylov_product, rbki_krylov_product_noalloc, rbki_mode_basis,
     rbki_syev, rbki_tucker, rbki_htr, RbkiServer, rbki_tucker_workspace, rbki_profile_enable, rbki_profile_reset,
-    rbki_profile_read, PROF_KRYLOV, PROF_SKETCH, PROF_GRAM, PROF_TTM, PROF_STAGE,
+    rbki_profile_read, PROF_KRYLOV, PROF_SKETCH, PROF_GRAM, PROF_TTM, PROF_STAGE, PROF_SAMPLE,
+    rbki_sample_units,
     F64, F32, BF16, F16, PREC_FP64, PREC_BF16, PREC_FP16, FLAG_HOST_IO, FLAG_SPLIT,
     FLAG_SERIAL_MODES, FLAG_SEQUENTIAL,
 )

@@ -28,7 +28,7 @@ class rbki_tensor(C.Structure):
 
 class rbki_params(C.Structure):
     _fields_ = [("ranks", C.c_int32 * MAX_ORDER), ("p", C.c_int32), ("q", C.c_int32),
-                ("seed", C.c_uint64), ("prec", C.c_int32), ("flags", C.c_uint32)]
+                ("seed", C.c_uint64), ("prec", C.c_int32), ("flags", C.c_uint32), ("omega", C.c_double)]
 
 
 class rbki_tucker_out(C.Structure):
@@ -72,6 +72,7 @@ def lib():
             "rbki_krylov_product_noalloc": (st, [vp, C.c_int32, C.c_int32, vp, C.c_int32, vp, vp]),
             "rbki_syev": (st, [vp, C.c_int32, vp, vp, vp, C.c_size_t, vp]),
             "rbki_syev_workspace": (st, [C.c_int32, sz]),
+            "rbki_sample_units": (st, [C.c_uint64, C.c_int32, C.c_int64, C.c_int64, vp, vp]),
             "rbki_status_str": (C.c_char_p, [C.c_int32]),
             "rbki_last_error": (C.c_char_p, []),
             "rbki_kernel_launches": (C.c_uint64, []),
@@ -125,11 +126,14 @@ def make_tensor(x, host: bool = False) -> rbki_tensor:
     return t
 
 
-def make_params(ranks: Sequence[int], p: int, q: int, seed: int, prec, flags: int = 0) -> rbki_params:
+def make_params(ranks: Sequence[int], p: int, q: int, seed: int, prec, flags: int = 0,
+                omega: float = 0.0) -> rbki_params:
+    """omega: column sampling rate of the Krylov construction (0 < omega < 1), else none."""
     prm = rbki_params()
     for i, r in enumerate(ranks):
         prm.ranks[i] = int(r)
     prm.p, prm.q, prm.seed, prm.prec, prm.flags = int(p), int(q), int(seed), prec_code(prec), int(flags)
+    prm.omega = float(omega)
     return prm
 
 
@@ -168,18 +172,19 @@ def make_out(o: Dict) -> rbki_tucker_out:
 
 
 # ---------------- entry points ----------------
-def rbki_tucker_workspace(x, ranks, p, q, seed=0, prec="bf16", flags=0) -> int:
+def rbki_tucker_workspace(x, ranks, p, q, seed=0, prec="bf16", flags=0, omega=0.0) -> int:
     n = C.c_size_t(0)
-    t, prm = make_tensor(x), make_params(ranks, p, q, seed, prec, flags)
+    t, prm = make_tensor(x), make_params(ranks, p, q, seed, prec, flags, omega)
     check(lib().rbki_tucker_workspace(C.byref(t), C.byref(prm), C.byref(n)), "rbki_tucker_workspace")
     return int(n.value)
 
 
-def rbki_tucker(x, ranks, p, q, seed, prec="bf16", flags=0, workspace=None, out=None, stream=None):
-    """rBKI-TK (Algorithm 2).  x: torch tensor (CUDA, or pinned CPU with FLAG_HOST_IO)."""
+def rbki_tucker(x, ranks, p, q, seed, prec="bf16", flags=0, workspace=None, out=None, stream=None, omega=0.0):
+    """rBKI-TK (Algorithm 2).  x: torch tensor (CUDA, or pinned CPU with FLAG_HOST_IO).
+    omega: column sampling rate of the Krylov construction (0 < omega < 1), else none."""
     torch = _torch()
     host = bool(flags & FLAG_HOST_IO)
-    t, prm = make_tensor(x), make_params(ranks, p, q, seed, prec, flags)
+    t, prm = make_tensor(x), make_params(ranks, p, q, seed, prec, flags, omega)
     need = C.c_size_t(0)
     check(lib().rbki_tucker_workspace(C.byref(t), C.byref(prm), C.byref(need)), "rbki_tucker_workspace")
     dev = torch.device("cuda", torch.cuda.current_device()) if host else x.device
@@ -195,12 +200,12 @@ def rbki_tucker(x, ranks, p, q, seed, prec="bf16", flags=0, workspace=None, out=
 
 
 def rbki_htr(x, tucker_ranks, p, q, seed, tr_ranks, tr_init, maxit=20, tol=1e-3, prec="fp64", flags=0,
-             workspace=None, tucker_out=None, stream=None):
+             workspace=None, tucker_out=None, stream=None, omega=0.0):
     """rBKI-TK-TR (Algorithm 3).  tr_init: list of float64 CUDA tensors (r_{n-1}, R_n, r_n).
     Returns dict(cores=[(r_{n-1}, I_n, r_n)], fits=(maxit,) NaN after the stop, tucker=...)."""
     torch = _torch()
     N = x.dim()
-    t, prm = make_tensor(x), make_params(tucker_ranks, p, q, seed, prec, flags)
+    t, prm = make_tensor(x), make_params(tucker_ranks, p, q, seed, prec, flags, omega)
     trr = (C.c_int32 * 8)(*[int(r) for r in tr_ranks])
     need = C.c_size_t(0)
     check(lib().rbki_htr_workspace(C.byref(t), C.byref(prm), trr, C.byref(need)), "rbki_htr_workspace")
@@ -254,10 +259,10 @@ def rbki_krylov_product_noalloc(x, mode: int, q_mat, prec="bf16", stream=None):
     return P
 
 
-def rbki_mode_basis(x, ranks, p, q, seed, mode, prec="fp64", stream=None):
+def rbki_mode_basis(x, ranks, p, q, seed, mode, prec="fp64", stream=None, omega=0.0):
     """Algorithm 1 basis Q = [Q_0..Q_q] for one mode (I_n x S(q+1), zero deflated columns)."""
     torch = _torch()
-    t, prm = make_tensor(x), make_params(ranks, p, q, seed, prec)
+    t, prm = make_tensor(x), make_params(ranks, p, q, seed, prec, 0, omega)
     need = C.c_size_t(0)
     check(lib().rbki_tucker_workspace(C.byref(t), C.byref(prm), C.byref(need)), "rbki_tucker_workspace")
     ws = torch.empty(int(need.value), dtype=torch.uint8, device=x.device)
@@ -267,6 +272,15 @@ def rbki_mode_basis(x, ranks, p, q, seed, mode, prec="fp64", stream=None):
                                 C.c_void_p(ws.data_ptr()), C.c_size_t(ws.numel()), stream_ptr(stream)),
           "rbki_mode_basis")
     return Q
+
+
+def rbki_sample_units(seed, mode, n_units, kept, device=None, stream=None):
+    """Kept units of partial column sampling (int32 device tensor, ascending)."""
+    torch = _torch()
+    units = torch.empty(int(kept), dtype=torch.int32, device=device or "cuda")
+    check(lib().rbki_sample_units(int(seed), int(mode), int(n_units), int(kept), C.c_void_p(units.data_ptr()),
+                                  stream_ptr(stream)), "rbki_sample_units")
+    return units
 
 
 def rbki_syev(a, stream=None):
@@ -298,11 +312,11 @@ class RbkiServer:
         self._h = h
         self._live = {}
 
-    def submit(self, x, ranks, p, q, seed, prec="bf16", out=None, after_stream=None, flags=0):
+    def submit(self, x, ranks, p, q, seed, prec="bf16", out=None, after_stream=None, flags=0, omega=0.0):
         """Queues a request; its kernels wait for the work already queued on `after_stream`
         (default: torch's current stream, where x and out were made)."""
         torch = _torch()
-        t, prm = make_tensor(x), make_params(ranks, p, q, seed, prec, flags)
+        t, prm = make_tensor(x), make_params(ranks, p, q, seed, prec, flags, omega)
         if out is None:
             out = alloc_outputs(x.shape, ranks, x.device)
         o = make_out(out)
@@ -346,7 +360,7 @@ class RbkiServer:
         self.close()
 
 
-PROF_KRYLOV, PROF_SKETCH, PROF_GRAM, PROF_TTM, PROF_STAGE = range(5)
+PROF_KRYLOV, PROF_SKETCH, PROF_GRAM, PROF_TTM, PROF_STAGE, PROF_SAMPLE = range(6)
 
 
 def rbki_profile_enable(on: bool = True) -> None:

@@ -84,6 +84,7 @@ rbki_status validate_params(const rbki_tensor* X, const rbki_params* prm) {
     if (prm->p < 0 || prm->q < 0) return set_error(RBKI_E_INVAL, "p and q must be >= 0");
     if (prm->prec != RBKI_PREC_FP64 && prm->prec != RBKI_PREC_BF16 && prm->prec != RBKI_PREC_FP16)
         return set_error(RBKI_E_INVAL, "unknown precision");
+    if (!std::isfinite(prm->omega)) return set_error(RBKI_E_INVAL, "omega must be finite");
     for (int n = 0; n < X->order; ++n) {
         if (prm->ranks[n] < 1 || prm->ranks[n] > X->dims[n])
             return set_error(RBKI_E_INVAL, "ranks must satisfy 1 <= R_n <= I_n");
@@ -124,6 +125,23 @@ rbki_status make_plan(const rbki_tensor* X, const rbki_params* prm, Plan& pl) {
         if (m.gram && m.I > 256) return set_error(RBKI_E_UNSUPPORTED, "Gram path with I_n > 256");
         if (!m.gram && m.b > 256) return set_error(RBKI_E_UNSUPPORTED, "Krylov width S(q+1) > 256");
         if (!m.gram && m.S > 96) return set_error(RBKI_E_UNSUPPORTED, "sketch size > 96");
+        // partial column sampling (Krylov-path modes, 0 < omega < 1): 128-column units
+        if (!m.gram && prm->omega > 0.0 && prm->omega < 1.0) {
+            m.sampled = true;
+            m.A0 = m.A;
+            m.C0 = m.C;
+            m.nunits = m.C > 1 ? m.A * cdiv(m.C, 128) : cdiv(m.A, 128);
+            if (m.nunits > 0x7fffffff) return set_error(RBKI_E_UNSUPPORTED, "too many sampling units");
+            double k = std::ceil(prm->omega * (double)m.nunits);
+            m.kunits = (int64_t)std::min(std::max(k, 1.0), (double)m.nunits);
+            if (m.C0 > 1) {
+                m.A = m.kunits;
+                m.C = 128;
+            } else {
+                m.A = m.kunits * 128;
+                m.C = 1;
+            }
+        }
     }
     // core chain order: largest shrink I_n / R_n first (ties -> lower mode)
     for (int n = 0; n < pl.N; ++n) pl.order[n] = n;
@@ -202,7 +220,7 @@ static void carve_sequential(Plan& pl, void* ws) {
     pl.ybuf[1] = c.take<char>(ymax * dtype_size(pl.ydtype));
     {
         const ModePlan& m = pl.mode[0];
-        View v{nullptr, pl.stream_dtype, m.A, m.I, m.C};
+        View v{nullptr, pl.stream_dtype, m.sampled ? m.A0 : m.A, m.I, m.sampled ? m.C0 : m.C};
         pl.ttm_N = (int)rup(2 * m.R, 16);
         pl.ttm_tc = pl.mixed && pl.N > 1 && m.R <= 32 && tc::supported(v, tc::TTM, pl.ttm_N);
         if (pl.ttm_tc) pl.ttm_img = c.take<char>(tc::image_bytes_skinny(v, pl.ttm_N));
@@ -241,6 +259,10 @@ void carve(Plan& pl, void* ws) {
         m.eval = c.take<double>((size_t)m.b);
         m.syev_ws = c.take<double>(syev_scratch_doubles(m.b));
         m.kept = c.take<int32_t>(4);
+        if (m.sampled) {
+            m.units = c.take<int32_t>((size_t)m.kunits);
+            m.ysamp = c.take<char>((size_t)m.A * m.I * m.C * dtype_size(pl.stream_dtype));
+        }
         if (m.gram) {
             m.part = c.take<double>((size_t)m.nsplit * m.I * m.I);
         } else {
@@ -282,7 +304,8 @@ void carve(Plan& pl, void* ws) {
     {
         const int m0 = pl.order[0];
         const ModePlan& m = pl.mode[m0];
-        View v{nullptr, pl.stream_dtype, m.A, m.I, m.C};
+        // the first core product streams all of X (not a mode's column sample)
+        View v{nullptr, pl.stream_dtype, m.sampled ? m.A0 : m.A, m.I, m.sampled ? m.C0 : m.C};
         // the core carries the reconstruction error |X|^2 - |G|^2: always hi + lo operands
         pl.ttm_N = (int)rup(2 * m.R, 16);
         pl.ttm_tc = pl.mixed && m.R <= 32 && tc::supported(v, tc::TTM, pl.ttm_N);
@@ -314,7 +337,16 @@ rbki_status symmetrize_cuda(double* Z, int n, cudaStream_t st) {
 }
 
 View mode_view(const Plan& pl, const ModePlan& m) {
-    return View{pl.xstream, pl.stream_dtype, m.A, m.I, m.C};
+    return View{m.sampled ? m.ysamp : pl.xstream, pl.stream_dtype, m.A, m.I, m.C};
+}
+
+// Partial column sampling: choose the kept units of mode n and gather Y from the streamed X.
+static rbki_status sample_mode(const Plan& pl, const ModePlan& m, cudaStream_t st) {
+    RBKI_TRY(sample_units_cuda(pl.seed, m.n, m.nunits, m.kunits, m.units, st));
+    int tok = prof_begin(RBKI_PROF_SAMPLE, st);
+    RBKI_TRY(gather_units_cuda(pl.xstream, pl.stream_dtype, m.A0, m.I, m.C0, m.units, m.kunits, m.ysamp, st));
+    prof_end(tok, st);
+    return RBKI_OK;
 }
 
 // P = X_(n) (X_(n)^T Q) for Q (I x S, ld ldq) -> out (ld ldo), out2 (optional copy)
@@ -386,6 +418,7 @@ rbki_status mode_factor(const Plan& pl, const ModePlan& m, double* U, double* ei
         if (info) RBKI_TRY(fill_i32_cuda(info + m.n, (int32_t)m.I, 1, st));
     } else {
         if (info) RBKI_TRY(fill_i32_cuda(info + m.n, 0, 1, st));
+        if (m.sampled) RBKI_TRY(sample_mode(pl, m, st));
         RBKI_TRY(mode_basis(pl, m, kept, st));
         // step 3 (Remark 1): Z = Q^T X X^T Q = Q^T [P_0 .. P_q]
         RBKI_TRY(atb_cuda(m.Qall, m.b, m.b, m.Pall, m.b, m.b, m.I, m.part, m.Z, m.b, st));
@@ -512,15 +545,17 @@ static rbki_status run_sequential(Plan& pl, const rbki_tucker_out* out, cudaStre
         void* dst = last ? (void*)out->core : pl.ybuf[n & 1];
         const int dst_dtype = last ? RBKI_F64 : pl.ydtype;
         const int R = m.R;
+        // the product runs over all of Y_n (a sampled mode's m.A, m.C describe the sample)
+        const int64_t fa = m.sampled ? m.A0 : m.A, fc = m.sampled ? m.C0 : m.C;
         tok = prof_begin(RBKI_PROF_TTM, st);
         if (n == 0 && pl.ttm_tc && !last) {
-            View v{sp.xstream, sp.stream_dtype, m.A, m.I, m.C};
+            View v{sp.xstream, sp.stream_dtype, fa, m.I, fc};
             RBKI_TRY(tc::skinny_image(out->factors[0], R, m.I, R, pl.ttm_N, true, sp.stream_dtype == RBKI_F16,
                                       pl.ttm_img, st));
             RBKI_TRY(tc::stream_tc(tc::TTM, v, pl.ttm_N, R, true, pl.ttm_img, nullptr, nullptr, (float*)dst,
                                    pl.err, st));
         } else {
-            View v{src, src_dtype, m.A, m.I, m.C};
+            View v{src, src_dtype, fa, m.I, fc};
             if (n > 0 && dst_dtype == RBKI_F64 && R <= 32 && (src_dtype == RBKI_F64 || src_dtype == RBKI_F32))
                 RBKI_TRY(ttm_small_cuda(v, out->factors[n], R, R, (double*)dst, pl.mixed, st));
             else
@@ -754,6 +789,7 @@ rbki_status rbki_mode_basis(const rbki_tensor* X, const rbki_params* prm, int32_
     }
     const ModePlan& m = pl.mode[mode];
     RBKI_TRY(fill_i32_cuda(m.kept, 0, 1, st));
+    if (m.sampled) RBKI_TRY(sample_mode(pl, m, st));
     RBKI_TRY(mode_basis(pl, m, m.kept, st));
     RBKI_TRY(copy_f64_cuda(m.Qall, Q, m.I * m.b, st));
     return RBKI_OK;
@@ -869,6 +905,12 @@ rbki_status rbki_htr(const rbki_tensor* X, const rbki_params* tk, const int32_t*
         RBKI_CUDA_TRY(cudaStreamSynchronize(st));
     }
     return RBKI_OK;
+}
+
+rbki_status rbki_sample_units(uint64_t seed, int32_t mode, int64_t n_units, int64_t kept, int32_t* units,
+                              void* stream) {
+    if (!units) return set_error(RBKI_E_INVAL, "units is NULL");
+    return sample_units_cuda(seed, mode, n_units, kept, units, (cudaStream_t)stream);
 }
 
 rbki_status rbki_syev_workspace(int32_t n, size_t* bytes) {

@@ -13,6 +13,14 @@ struct View {
     int64_t A, I, C;
 };
 
+// ---- partial column sampling (k_sample.cu) ----
+// the `kept` units (of nu) with the smallest Philox keys, ascending, into units[kept]
+rbki_status sample_units_cuda(uint64_t seed, int mode, int64_t nu, int64_t kept, int32_t* units,
+                              cudaStream_t st);
+// sampled unfolding Y of the kept units: [kept][I][128] (C > 1) or [kept * 128][I] (C = 1)
+rbki_status gather_units_cuda(const void* x, int dtype, int64_t A, int64_t I, int64_t C, const int32_t* units,
+                              int64_t kept, void* y, cudaStream_t st);
+
 // ---- FP64/FP32 CUDA-core streaming products (k_stream.cu) ----
 // TTM: Y[a][s][c] = sum_i M[i*ldm + s] X[a][i][c],  s < S.  Y is [A][S][C] (Tout).
 // `acc32` = accumulate in FP32 (mixed path), else FP64.

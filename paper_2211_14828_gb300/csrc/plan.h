@@ -11,6 +11,12 @@ struct ModePlan {
     int R = 0, S = 0, q = 0, b = 0;
     bool gram = false;             // b >= I: exact Gram path (reading c7)
     int nsplit = 1;
+    // partial column sampling: A, C above describe the sampled unfolding Y ([kept][I][128]
+    // or [kept*128][I][1]); A0, C0 the full view of X it is gathered from
+    bool sampled = false;
+    int64_t A0 = 1, C0 = 1, nunits = 0, kunits = 0;
+    int32_t* units = nullptr;      // kept unit indices, ascending
+    void* ysamp = nullptr;         // Y in the streamed dtype
     // workspace (device)
     double* Qall = nullptr;        // I x b, blocks Q_0..Q_q (ld b)
     double* Pall = nullptr;        // I x b, P_j = X X^T Q_j
