@@ -45,12 +45,13 @@ from .tensor import ttm, unfold
 TAU_DEFLATE = 1e-6
 
 
-def sketch_plan(dims: Sequence[int], ranks: Sequence[int], p: int, q: int):
-    """Per mode: (S_n, b_n, path) with path 'krylov' or 'gram' (readings c4, c7)."""
+def sketch_plan(dims: Sequence[int], ranks: Sequence[int], p: int, q: int, variant: str = "krylov"):
+    """Per mode: (S_n, b_n, path) with path 'krylov' or 'gram' (readings c4, c7).  The
+    power-iteration variant keeps one block of width S_n (b_n = S_n)."""
     plan = []
     for i_n, r_n in zip(dims, ranks):
         s = min(r_n + p, i_n)
-        b = s * (q + 1)
+        b = s if variant == "power" else s * (q + 1)
         plan.append((s, b, "gram" if b >= i_n else "krylov"))
     return plan
 
@@ -91,6 +92,40 @@ def rbki(xn: np.ndarray, om: np.ndarray, q: int, tau: float = TAU_DEFLATE) -> Li
         v = xn @ (xn.T @ blocks[-1])                     # (X X^T) Q_j
         blocks.append(orth_block(v, prev, tau))
     return blocks
+
+
+def power_basis(xn: np.ndarray, om: np.ndarray, q: int, tau: float = TAU_DEFLATE) -> np.ndarray:
+    """Power-iteration baseline (the "P-iter" / GRpi comparison of Sec. 3.1: K = (X X^T)^q W
+    instead of Eq. BKspace): Q_0 = orth(X Omega), Q_{j+1} = orth((X X^T) Q_j), and the
+    basis is the last block Q_q alone (width S)."""
+    qb = orth_block(xn @ om, np.zeros((xn.shape[0], 0)), tau)
+    for _ in range(q):
+        qb = orth_block(xn @ (xn.T @ qb), np.zeros((xn.shape[0], 0)), tau)
+    return qb
+
+
+def mode_fit(lam: np.ndarray, x_norm2: float) -> float:
+    """Fit (as a fraction, 1 - |X - X^|/|X|) of the rank-R projection U U^T X_(n) whose
+    Rayleigh-Ritz values are lam: |X - U U^T X|^2 = |X|^2 - sum(lam) (reading c27)."""
+    return 1.0 - np.sqrt(max(x_norm2 - float(np.sum(lam)), 0.0) / x_norm2)
+
+
+def krylov_adaptive(xn: np.ndarray, om: np.ndarray, r: int, q_max: int, q_tol: float,
+                    tau: float = TAU_DEFLATE):
+    """Adaptive depth (reading c26): after block j the Rayleigh-Ritz step runs on Q_0..Q_j;
+    stop at the first j >= 1 with |Fit_j - Fit_{j-1}| <= q_tol, or at j = q_max.
+    Returns (U, lambda, kept width, q used, fits)."""
+    x_norm2 = float(np.sum(xn * xn))
+    blocks = [orth_block(xn @ om, np.zeros((xn.shape[0], 0)), tau)]
+    fits = []
+    for j in range(q_max + 1):
+        qb = np.concatenate(blocks, axis=1)
+        u, lam, _ = rayleigh_ritz(xn, qb, r)
+        fits.append(mode_fit(lam, x_norm2))
+        if j == q_max or (j >= 1 and abs(fits[j] - fits[j - 1]) <= q_tol):
+            return u, lam, qb.shape[1], j, fits
+        blocks.append(orth_block(xn @ (xn.T @ blocks[-1]), qb, tau))
+    raise AssertionError("unreachable")
 
 
 def complete_basis(u: np.ndarray, r: int) -> np.ndarray:
@@ -137,28 +172,37 @@ def rayleigh_ritz(xn: np.ndarray, q_basis: np.ndarray, r: int):
 
 
 def krylov_mode(xn: np.ndarray, x: np.ndarray, n: int, s: int, r: int, q: int, seed: int, omega: float,
-                tau: float = TAU_DEFLATE):
-    """Algorithms 1-2 for a Krylov-path mode of tensor x (unfolding xn): (U, lambda, kept).
-    0 < omega < 1: the Krylov space and Z come from the sampled Y (oracle.sampling)."""
+                tau: float = TAU_DEFLATE, variant: str = "krylov", q_tol=None):
+    """Algorithms 1-2 for a Krylov-path mode of tensor x (unfolding xn): (U, lambda, kept, q used).
+    0 < omega < 1: the Krylov space and Z come from the sampled Y (oracle.sampling).
+    variant "power": the power-iteration basis; q_tol: adaptive depth with q as the bound."""
     if 0.0 < omega < 1.0:
+        if q_tol is not None:
+            raise ValueError("adaptive q with column sampling is not defined")
         y, _ = sampling.sampled_mode(x, n, seed, omega)
         om = philox.omega(seed, n, np.arange(y.shape[1], dtype=np.uint64), s)
-        qb = np.concatenate(rbki(y, om, q, tau), axis=1)
-        u, lam, _ = rayleigh_ritz(y, qb, r)
+        a = y
     else:
         om = philox.omega_mode(seed, n, x.shape, s)
-        qb = np.concatenate(rbki(xn, om, q, tau), axis=1)
-        u, lam, _ = rayleigh_ritz(xn, qb, r)
-    return u, lam, qb.shape[1]
+        a = xn
+    if q_tol is not None:
+        if variant != "krylov":
+            raise ValueError("adaptive q applies to the block Krylov space")
+        u, lam, k, qu, _ = krylov_adaptive(a, om, r, q, q_tol, tau)
+        return u, lam, k, qu
+    qb = power_basis(a, om, q, tau) if variant == "power" else np.concatenate(rbki(a, om, q, tau), axis=1)
+    u, lam, _ = rayleigh_ritz(a, qb, r)
+    return u, lam, qb.shape[1], q
 
 
 def rbki_tucker(x: np.ndarray, ranks: Sequence[int], p: int, q: int, seed: int,
-                tau: float = TAU_DEFLATE, omega: float = 1.0) -> Dict:
+                tau: float = TAU_DEFLATE, omega: float = 1.0, variant: str = "krylov", q_tol=None) -> Dict:
     """Algorithm 2 (rBKI-TK), HOSVD reading: every mode sketches the original X.
-    0 < omega < 1: partial column sampling of the Krylov construction (oracle.sampling)."""
+    0 < omega < 1: partial column sampling of the Krylov construction (oracle.sampling).
+    variant "power": the power-iteration baseline; q_tol: adaptive depth, q the bound."""
     x = np.asarray(x, dtype=np.float64)
-    plan = sketch_plan(x.shape, ranks, p, q)
-    factors, eigvals, kept, paths = [], [], [], []
+    plan = sketch_plan(x.shape, ranks, p, q, variant)
+    factors, eigvals, kept, paths, q_used = [], [], [], [], []
     for n, (s, b, path) in enumerate(plan):
         xn = unfold(x, n)
         if path == "gram":
@@ -167,21 +211,23 @@ def rbki_tucker(x: np.ndarray, ranks: Sequence[int], p: int, q: int, seed: int,
             u = sign_fix(vec[:, order[: ranks[n]]])
             lam = lam[order[: ranks[n]]]
             kept.append(x.shape[n])
+            q_used.append(0)
         else:
-            u, lam, k = krylov_mode(xn, x, n, s, ranks[n], q, seed, omega, tau)
+            u, lam, k, qu = krylov_mode(xn, x, n, s, ranks[n], q, seed, omega, tau, variant, q_tol)
             kept.append(k)
+            q_used.append(qu)
         factors.append(u)
         eigvals.append(lam)
         paths.append(path)
     core = x
     for n, u in enumerate(factors):
         core = ttm(core, u.T, n)                         # step 6
-    return dict(core=core, factors=factors, eigvals=eigvals, kept=kept, path=paths,
+    return dict(core=core, factors=factors, eigvals=eigvals, kept=kept, path=paths, q_used=q_used,
                 x_norm2=float(np.sum(x * x)), core_norm2=float(np.sum(core * core)))
 
 
 def rbki_st_tucker(x: np.ndarray, ranks: Sequence[int], p: int, q: int, seed: int,
-                   tau: float = TAU_DEFLATE, omega: float = 1.0) -> Dict:
+                   tau: float = TAU_DEFLATE, omega: float = 1.0, variant: str = "krylov") -> Dict:
     """Algorithm 2 read literally (sequential truncation, the other reading of step 6): the
     modes are taken in order n = 1..N, and mode n is sketched from the tensor already
     contracted by the earlier factors, Y_n = X x_1 U^(1)T ... x_{n-1} U^(n-1)T; after U^(n)
@@ -192,7 +238,7 @@ def rbki_st_tucker(x: np.ndarray, ranks: Sequence[int], p: int, q: int, seed: in
     x_norm2 = float(np.sum(y * y))
     factors, eigvals, kept, paths, res2 = [], [], [], [], []
     for n in range(y.ndim):
-        s, b, path = sketch_plan(y.shape, ranks, p, q)[n]
+        s, b, path = sketch_plan(y.shape, ranks, p, q, variant)[n]
         yn = unfold(y, n)
         if path == "gram":
             lam, vec = np.linalg.eigh(yn @ yn.T)
@@ -201,7 +247,7 @@ def rbki_st_tucker(x: np.ndarray, ranks: Sequence[int], p: int, q: int, seed: in
             lam = lam[order[: ranks[n]]]
             kept.append(y.shape[n])
         else:
-            u, lam, k = krylov_mode(yn, y, n, s, ranks[n], q, seed, omega, tau)
+            u, lam, k, _ = krylov_mode(yn, y, n, s, ranks[n], q, seed, omega, tau, variant)
             kept.append(k)
         factors.append(u)
         eigvals.append(lam)
