@@ -49,6 +49,9 @@ def parse_args():
     ap.add_argument("--sequential", action="store_true",
                     help="sequentially truncated reading (each mode sketched on the contracted tensor)")
     ap.add_argument("--no-sequential-compare", action="store_true")
+    ap.add_argument("--power", action="store_true", help="power-iteration baseline instead of block Krylov")
+    ap.add_argument("--q-tol", type=float, default=None,
+                    help="adaptive Krylov depth: stop a mode when its fit changes by at most this (q is the bound)")
     ap.add_argument("--omega", type=float, default=0.0,
                     help="column sampling rate of the Krylov construction (0 < omega < 1)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -286,6 +289,11 @@ def run_ours(args):
     numel = int(np.prod(dims))
     prec = args.prec
     flags = rb.FLAG_SEQUENTIAL if args.sequential else 0
+    if args.power:
+        flags |= rb.FLAG_POWER
+    if args.q_tol is not None:
+        flags |= rb.FLAG_ADAPTIVE_Q
+    qtol = args.q_tol or 0.0
     if args.omega > 0 and args.sequential:
         raise SystemExit("--omega and --sequential: byte accounting of the combination is not implemented")
     if args.omega > 0:
@@ -311,10 +319,23 @@ def run_ours(args):
     for j in range(K):
         with torch.cuda.stream(streams[j]):
             outs.append(rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec=prec, flags=flags,
-                                       omega=args.omega,
+                                       omega=args.omega, q_tol=qtol,
                                        stream=streams[j]))
     torch.cuda.synchronize()
     out = outs[0]
+    if args.q_tol is not None:
+        # the adaptive depths decide the passes: 1 sketch + (q_used + 1) Krylov steps per mode
+        qu = out["q_used"].cpu().numpy().tolist()
+        step_bytes, krylov_bytes, krylov_steps = numel * ELEM_BYTES, 0, 0
+        for n, (i_n, r_n) in enumerate(zip(dims, wl.ranks)):
+            s_n = min(r_n + wl.p, i_n)
+            if s_n * (wl.q + 1) >= i_n:
+                step_bytes += numel * ELEM_BYTES
+            else:
+                step_bytes += (qu[n] + 2) * numel * ELEM_BYTES
+                krylov_bytes += (qu[n] + 1) * numel * (ELEM_BYTES if prec != "fp64" else wl.x.itemsize)
+                krylov_steps += qu[n] + 1
+        passes = step_bytes // (numel * ELEM_BYTES)
 
     def run_steps(nsteps):
         ev = torch.cuda.Event()
@@ -324,7 +345,7 @@ def run_ours(args):
         for t in range(nsteps):
             j = t % K
             o = outs[j]
-            rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec=prec, flags=flags, omega=args.omega,
+            rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec=prec, flags=flags, omega=args.omega, q_tol=qtol,
                            workspace=o["workspace"], out=o, stream=streams[j])
         for j in range(K):
             e = torch.cuda.Event()
@@ -336,7 +357,7 @@ def run_ours(args):
     # one decomposition alone (latency)
     e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e_a.record(stream)
-    rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec=prec, flags=flags, omega=args.omega,
+    rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec=prec, flags=flags, omega=args.omega, q_tol=qtol,
                    workspace=out["workspace"], out=out, stream=stream)
     e_b.record(stream)
     torch.cuda.synchronize()
@@ -380,7 +401,7 @@ def run_ours(args):
                 "frac": round(ach / peak, 4),
                 "traffic": (round(KRYLOV_TC_DRAM_BYTES_PER_ELEM * numel) if prec == "bf16"
                             and KRYLOV_TC_DRAM_BYTES_PER_ELEM and not args.sequential
-                            and args.omega <= 0 else None),
+                            and args.omega <= 0 and args.q_tol is None else None),
                 "traffic_unit": "bytes per launch (ncu at 448^3, scaled by elements)",
                 "kernel": "krylov_step",
                 "avg_launch_ms": round(avg, 4), "launches": kcount, "peak_kind": peak_kind}
@@ -401,16 +422,16 @@ def run_ours(args):
         xh = torch.from_numpy(wl.x).pin_memory()
         oh = B.alloc_outputs(dims, wl.ranks, None, host=True)
         hflags = flags | rb.FLAG_HOST_IO
-        wsh = torch.empty(rb.rbki_tucker_workspace(xh, wl.ranks, wl.p, wl.q, wl.seed, prec, hflags, args.omega),
+        wsh = torch.empty(rb.rbki_tucker_workspace(xh, wl.ranks, wl.p, wl.q, wl.seed, prec, hflags, args.omega, qtol),
                           dtype=torch.uint8, device="cuda")
         for _ in range(2):
-            rb.rbki_tucker(xh, wl.ranks, wl.p, wl.q, wl.seed, prec=prec, flags=hflags, omega=args.omega,
+            rb.rbki_tucker(xh, wl.ranks, wl.p, wl.q, wl.seed, prec=prec, flags=hflags, omega=args.omega, q_tol=qtol,
                            workspace=wsh, out=oh)
         ke = max(3, min(args.steps, 10))
         barrier(world)
         t0 = time.perf_counter()
         for _ in range(ke):
-            rb.rbki_tucker(xh, wl.ranks, wl.p, wl.q, wl.seed, prec=prec, flags=hflags, omega=args.omega,
+            rb.rbki_tucker(xh, wl.ranks, wl.p, wl.q, wl.seed, prec=prec, flags=hflags, omega=args.omega, q_tol=qtol,
                            workspace=wsh, out=oh)
         te = (time.perf_counter() - t0) / ke
         te = allreduce_max(te, world)
@@ -426,7 +447,7 @@ def run_ours(args):
         o64 = rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec="fp64", flags=flags, omega=args.omega)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec="fp64", flags=flags, omega=args.omega,
+        rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec="fp64", flags=flags, omega=args.omega, q_tol=qtol,
                        workspace=o64["workspace"], out=o64)
         torch.cuda.synchronize()
         t64 = time.perf_counter() - t0
@@ -437,7 +458,8 @@ def run_ours(args):
         del o64
 
     seq_cmp = None
-    if not args.sequential and not args.no_sequential_compare and args.omega <= 0:
+    if (not args.sequential and not args.no_sequential_compare and args.omega <= 0 and not args.power
+            and args.q_tol is None):
         # the sequentially truncated reading on the same input: one decomposition alone
         osq = rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec=prec, flags=rb.FLAG_SEQUENTIAL)
         times = []
@@ -470,7 +492,10 @@ def run_ours(args):
             "config": {"workload": f"{args.workload}: {'x'.join(map(str, dims))} {wl.x.dtype}, ranks {wl.ranks}, "
                                    f"p={wl.p}, q={wl.q}, {prec} products"
                                    + (", sequential truncation" if args.sequential else "")
-                                   + (f", column sampling omega={args.omega}" if args.omega > 0 else ""),
+                                   + (f", column sampling omega={args.omega}" if args.omega > 0 else "")
+                                   + (", power iteration" if args.power else "")
+                                   + (f", adaptive q (q_tol={args.q_tol}, depths "
+                                      f"{out['q_used'].cpu().numpy().tolist()})" if args.q_tol is not None else ""),
                        "inflight": K, "single_decomposition_ms": round(single_ms, 4),
                        "passes_per_step": passes, "krylov_steps_per_step": krylov_steps,
                        "bytes_per_step": step_bytes, "l2": "inputs larger than L2 (no flush)",

@@ -68,10 +68,20 @@ enum {
     RBKI_FLAG_SPLIT = 2u,          /* mixed path: carry the skinny operands (Q, Y, Omega, U) as
                                       hi + lo BF16 pairs: ~FP32-accurate products, 2x MMA work */
     RBKI_FLAG_SERIAL_MODES = 4u,   /* run modes one after another on `stream` */
-    RBKI_FLAG_SEQUENTIAL = 8u      /* sequentially truncated reading of Algorithm 2 (ST-HOSVD):
+    RBKI_FLAG_SEQUENTIAL = 8u,     /* sequentially truncated reading of Algorithm 2 (ST-HOSVD):
                                       mode n is sketched on Y_n = X x_1 U^(1)T .. x_{n-1} U^(n-1)T,
                                       modes in the order 1..N; the default (HOSVD reading)
                                       sketches every mode on X itself */
+    RBKI_FLAG_POWER = 16u,         /* power-iteration baseline (Sec. 3.1 "P-iter", GRpi):
+                                      Q_{j+1} = orth(X X^T Q_j) replaces the block instead of
+                                      extending it; the basis is Q_q alone (width S_n); a mode
+                                      takes the Gram path when S_n >= I_n */
+    RBKI_FLAG_ADAPTIVE_Q = 32u     /* adaptive Krylov depth: q is the bound; after block j the
+                                      mode's fit F_j = 1 - sqrt(|X|^2 - sum of its R_n Ritz
+                                      values)/|X| is evaluated, and the mode stops at the first
+                                      j >= 1 with |F_j - F_{j-1}| <= q_tol (or at j = q).  The
+                                      call then synchronises `stream` once per block.  Not with
+                                      RBKI_FLAG_POWER, RBKI_FLAG_SEQUENTIAL or omega sampling */
 };
 
 typedef struct {
@@ -98,6 +108,7 @@ typedef struct {
                                         0x53414D50), key = seed); Z = Q^T Y Y^T Q on the
                                         sampled Y; the core uses all of X.  <= 0 or >= 1:
                                         no sampling.  Must be finite. */
+    double q_tol;                    /* RBKI_FLAG_ADAPTIVE_Q: fit-change threshold, >= 0 */
 } rbki_params;
 
 /* Algorithm 2 outputs (caller-owned). */
@@ -113,6 +124,8 @@ typedef struct {
                                         [N+n] = path (0 Krylov, 1 Gram = exact T-SVD mode),
                                         [2N] = device error flags (nonzero: a bounded wait inside
                                         a kernel expired; the results are not valid) */
+    int32_t* q_used;                 /* optional, N ints: Krylov depth used per mode (q, or
+                                        the adaptive choice; 0 on the Gram path) */
 } rbki_tucker_out;
 
 /* Bytes of device workspace rbki_tucker needs for this problem. */

@@ -18,7 +18,7 @@ OK, PENDING, W_DEFLATED = 0, 1, 2
 E_INVAL, E_NOMEM, E_CUDA, E_UNSUPPORTED, E_TIMEOUT, E_BUSY, E_CANCELLED, E_NOTFOUND = range(-1, -9, -1)
 F64, F32, BF16, F16 = 0, 1, 2, 3
 PREC_FP64, PREC_BF16, PREC_FP16 = 0, 1, 2
-FLAG_HOST_IO, FLAG_SPLIT, FLAG_SERIAL_MODES, FLAG_SEQUENTIAL = 1, 2, 4, 8
+FLAG_HOST_IO, FLAG_SPLIT, FLAG_SERIAL_MODES, FLAG_SEQUENTIAL, FLAG_POWER, FLAG_ADAPTIVE_Q = 1, 2, 4, 8, 16, 32
 
 
 class rbki_tensor(C.Structure):
@@ -28,12 +28,14 @@ class rbki_tensor(C.Structure):
 
 class rbki_params(C.Structure):
     _fields_ = [("ranks", C.c_int32 * MAX_ORDER), ("p", C.c_int32), ("q", C.c_int32),
-                ("seed", C.c_uint64), ("prec", C.c_int32), ("flags", C.c_uint32), ("omega", C.c_double)]
+                ("seed", C.c_uint64), ("prec", C.c_int32), ("flags", C.c_uint32), ("omega", C.c_double),
+                ("q_tol", C.c_double)]
 
 
 class rbki_tucker_out(C.Structure):
     _fields_ = [("core", C.c_void_p), ("factors", C.c_void_p * MAX_ORDER),
-                ("eigvals", C.c_void_p * MAX_ORDER), ("norms", C.c_void_p), ("info", C.c_void_p)]
+                ("eigvals", C.c_void_p * MAX_ORDER), ("norms", C.c_void_p), ("info", C.c_void_p),
+                ("q_used", C.c_void_p)]
 
 
 class RbkiError(RuntimeError):
@@ -127,13 +129,15 @@ def make_tensor(x, host: bool = False) -> rbki_tensor:
 
 
 def make_params(ranks: Sequence[int], p: int, q: int, seed: int, prec, flags: int = 0,
-                omega: float = 0.0) -> rbki_params:
-    """omega: column sampling rate of the Krylov construction (0 < omega < 1), else none."""
+                omega: float = 0.0, q_tol: float = 0.0) -> rbki_params:
+    """omega: column sampling rate of the Krylov construction (0 < omega < 1), else none;
+    q_tol: fit-change threshold of FLAG_ADAPTIVE_Q."""
     prm = rbki_params()
     for i, r in enumerate(ranks):
         prm.ranks[i] = int(r)
     prm.p, prm.q, prm.seed, prm.prec, prm.flags = int(p), int(q), int(seed), prec_code(prec), int(flags)
     prm.omega = float(omega)
+    prm.q_tol = float(q_tol)
     return prm
 
 
@@ -156,6 +160,7 @@ def alloc_outputs(dims, ranks, device, host=False) -> Dict:
     if host:
         ikw["pin_memory"] = True
     out["info"] = torch.zeros(2 * len(dims) + 1, **ikw)
+    out["q_used"] = torch.zeros(len(dims), **ikw)
     return out
 
 
@@ -168,23 +173,26 @@ def make_out(o: Dict) -> rbki_tucker_out:
         s.eigvals[i] = e.data_ptr() if e is not None else None
     s.norms = o["norms"].data_ptr() if o.get("norms") is not None else None
     s.info = o["info"].data_ptr() if o.get("info") is not None else None
+    s.q_used = o["q_used"].data_ptr() if o.get("q_used") is not None else None
     return s
 
 
 # ---------------- entry points ----------------
-def rbki_tucker_workspace(x, ranks, p, q, seed=0, prec="bf16", flags=0, omega=0.0) -> int:
+def rbki_tucker_workspace(x, ranks, p, q, seed=0, prec="bf16", flags=0, omega=0.0, q_tol=0.0) -> int:
     n = C.c_size_t(0)
-    t, prm = make_tensor(x), make_params(ranks, p, q, seed, prec, flags, omega)
+    t, prm = make_tensor(x), make_params(ranks, p, q, seed, prec, flags, omega, q_tol)
     check(lib().rbki_tucker_workspace(C.byref(t), C.byref(prm), C.byref(n)), "rbki_tucker_workspace")
     return int(n.value)
 
 
-def rbki_tucker(x, ranks, p, q, seed, prec="bf16", flags=0, workspace=None, out=None, stream=None, omega=0.0):
+def rbki_tucker(x, ranks, p, q, seed, prec="bf16", flags=0, workspace=None, out=None, stream=None, omega=0.0,
+                q_tol=0.0):
     """rBKI-TK (Algorithm 2).  x: torch tensor (CUDA, or pinned CPU with FLAG_HOST_IO).
-    omega: column sampling rate of the Krylov construction (0 < omega < 1), else none."""
+    omega: column sampling rate of the Krylov construction (0 < omega < 1), else none;
+    q_tol: fit-change threshold with FLAG_ADAPTIVE_Q (q is then the bound)."""
     torch = _torch()
     host = bool(flags & FLAG_HOST_IO)
-    t, prm = make_tensor(x), make_params(ranks, p, q, seed, prec, flags, omega)
+    t, prm = make_tensor(x), make_params(ranks, p, q, seed, prec, flags, omega, q_tol)
     need = C.c_size_t(0)
     check(lib().rbki_tucker_workspace(C.byref(t), C.byref(prm), C.byref(need)), "rbki_tucker_workspace")
     dev = torch.device("cuda", torch.cuda.current_device()) if host else x.device
@@ -312,11 +320,12 @@ class RbkiServer:
         self._h = h
         self._live = {}
 
-    def submit(self, x, ranks, p, q, seed, prec="bf16", out=None, after_stream=None, flags=0, omega=0.0):
+    def submit(self, x, ranks, p, q, seed, prec="bf16", out=None, after_stream=None, flags=0, omega=0.0,
+               q_tol=0.0):
         """Queues a request; its kernels wait for the work already queued on `after_stream`
         (default: torch's current stream, where x and out were made)."""
         torch = _torch()
-        t, prm = make_tensor(x), make_params(ranks, p, q, seed, prec, flags, omega)
+        t, prm = make_tensor(x), make_params(ranks, p, q, seed, prec, flags, omega, q_tol)
         if out is None:
             out = alloc_outputs(x.shape, ranks, x.device)
         o = make_out(out)

@@ -85,6 +85,15 @@ rbki_status validate_params(const rbki_tensor* X, const rbki_params* prm) {
     if (prm->prec != RBKI_PREC_FP64 && prm->prec != RBKI_PREC_BF16 && prm->prec != RBKI_PREC_FP16)
         return set_error(RBKI_E_INVAL, "unknown precision");
     if (!std::isfinite(prm->omega)) return set_error(RBKI_E_INVAL, "omega must be finite");
+    if (prm->flags & RBKI_FLAG_ADAPTIVE_Q) {
+        if (!std::isfinite(prm->q_tol) || prm->q_tol < 0.0) return set_error(RBKI_E_INVAL, "q_tol must be >= 0");
+        if (prm->flags & RBKI_FLAG_POWER)
+            return set_error(RBKI_E_INVAL, "adaptive q applies to the block Krylov space, not power iteration");
+        if (prm->flags & RBKI_FLAG_SEQUENTIAL)
+            return set_error(RBKI_E_UNSUPPORTED, "adaptive q with the sequential reading");
+        if (prm->omega > 0.0 && prm->omega < 1.0)
+            return set_error(RBKI_E_UNSUPPORTED, "adaptive q with column sampling");
+    }
     for (int n = 0; n < X->order; ++n) {
         if (prm->ranks[n] < 1 || prm->ranks[n] > X->dims[n])
             return set_error(RBKI_E_INVAL, "ranks must satisfy 1 <= R_n <= I_n");
@@ -119,7 +128,8 @@ rbki_status make_plan(const rbki_tensor* X, const rbki_params* prm, Plan& pl) {
         m.R = prm->ranks[n];
         m.S = (int)std::min<int64_t>(m.R + prm->p, m.I);
         m.q = prm->q;
-        int64_t b = (int64_t)m.S * (m.q + 1);
+        // power iteration keeps one block of width S (RBKI_FLAG_POWER)
+        int64_t b = (prm->flags & RBKI_FLAG_POWER) ? (int64_t)m.S : (int64_t)m.S * (m.q + 1);
         m.gram = b >= m.I;
         m.b = m.gram ? (int)m.I : (int)b;
         if (m.gram && m.I > 256) return set_error(RBKI_E_UNSUPPORTED, "Gram path with I_n > 256");
@@ -390,6 +400,19 @@ rbki_status mode_basis(const Plan& pl, const ModePlan& m, int32_t* kept, cudaStr
                                nullptr, 0, st));
         prof_end(tok, st);
     }
+    if (pl.flags & RBKI_FLAG_POWER) {
+        // power iteration: each product replaces the block, orthonormalised on its own
+        RBKI_TRY(orth2(m, 0, kept, st));
+        for (int j = 0; j <= m.q; ++j) {
+            const bool more = j < m.q;
+            RBKI_TRY(krylov_step(pl, m, m.Qall, m.b, m.S, m.Pall, m.b, more ? m.Qall : nullptr, m.b, st));
+            if (more) {
+                RBKI_TRY(fill_i32_cuda(kept, 0, 1, st));
+                RBKI_TRY(orth2(m, 0, kept, st));
+            }
+        }
+        return RBKI_OK;
+    }
     RBKI_TRY(orth2(m, 0, kept, st));
     // step 3: K = [W, A W, ..., A^q W], orthonormalised block by block (reading c2)
     for (int j = 0; j <= m.q; ++j) {
@@ -429,6 +452,101 @@ rbki_status mode_factor(const Plan& pl, const ModePlan& m, double* U, double* ei
     }
     if (eigvals) RBKI_TRY(copy_f64_cuda(m.eval, eigvals, m.R, st));
     if (info) RBKI_TRY(fill_i32_cuda(info + pl.N + m.n, m.gram ? 1 : 0, 1, st));
+    return RBKI_OK;
+}
+
+// Adaptive Krylov depth (RBKI_FLAG_ADAPTIVE_Q): the Krylov-path modes advance block by
+// block in lockstep, each on its own stream.  After block j every active mode has the
+// Rayleigh-Ritz values of Z_j = Q_{<=j}^T [P_0 .. P_j]; the host reads them (one
+// synchronisation per block), forms F_j = 1 - sqrt(max(|X|^2 - sum lambda, 0) / |X|^2) in
+// FP64 and stops the mode at the first j >= 1 with |F_j - F_{j-1}| <= q_tol, or at j = q.
+// A stopped mode forms U from the eigenvectors of its last Z_j; a continuing one
+// orthonormalises block j+1 (already written by the Krylov step).  Gram-path modes run as
+// usual.  q_used[n] receives the depth.
+static rbki_status run_modes_adaptive(const Plan& pl, const rbki_tucker_out* out, const double* norms,
+                                      const cudaStream_t* ms, int32_t* q_used_host) {
+    const double tol = pl.prm.q_tol;
+    bool active[RBKI_MAX_ORDER] = {false};
+    double prev_fit[RBKI_MAX_ORDER] = {0.0};
+    int qmax = 0;
+    for (int n = 0; n < pl.N; ++n) {
+        const ModePlan& m = pl.mode[n];
+        q_used_host[n] = 0;
+        if (m.gram) {
+            RBKI_TRY(mode_factor(pl, m, out->factors[n], out->eigvals[n], out->info, ms[n]));
+            continue;
+        }
+        int32_t* kept = out->info ? out->info + n : m.kept;
+        RBKI_TRY(fill_i32_cuda(kept, 0, 1, ms[n]));
+        // Algorithm 1 steps 1-2 and Q_0 (the sketch part of mode_basis)
+        View v = mode_view(pl, m);
+        if (m.tc) {
+            RBKI_TRY(tc::omega_images(pl.seed, m.n, v, m.S, m.N, pl.split, m.omg, ms[n]));
+            int tok = prof_begin(RBKI_PROF_SKETCH, ms[n]);
+            RBKI_TRY(tc::stream_tc(tc::SKETCH, v, m.N, m.S, pl.split, nullptr, m.omg, m.tpart, nullptr, pl.err, ms[n]));
+            prof_end(tok, ms[n]);
+            RBKI_TRY(tc::reduce_parts(m.tpart, m.tgrid, m.I, m.N, m.S, pl.split, m.Qall, m.b, nullptr, 0, ms[n]));
+        } else {
+            int tok = prof_begin(RBKI_PROF_SKETCH, ms[n]);
+            RBKI_TRY(omega_f64_cuda(pl.seed, m.n, m.A, m.C, m.S, m.Y, ms[n]));
+            RBKI_TRY(contract_cuda(v, m.Y, RBKI_F64, m.S, pl.mixed, m.part, m.nsplit, m.Qall, m.b, nullptr, 0, ms[n]));
+            prof_end(tok, ms[n]);
+        }
+        RBKI_TRY(orth2(m, 0, kept, ms[n]));
+        active[n] = true;
+        qmax = std::max(qmax, m.q);
+    }
+    std::vector<double> lam[RBKI_MAX_ORDER];
+    double x2 = -1.0;
+    for (int j = 0; j <= qmax; ++j) {
+        bool any = false;
+        for (int n = 0; n < pl.N; ++n) {
+            if (!active[n]) continue;
+            any = true;
+            const ModePlan& m = pl.mode[n];
+            const int bj = (j + 1) * m.S;
+            RBKI_TRY(krylov_step(pl, m, m.Qall + j * m.S, m.b, m.S, m.Pall + j * m.S, m.b,
+                                 j < m.q ? m.Qall + (j + 1) * m.S : nullptr, m.b, ms[n]));
+            RBKI_TRY(atb_cuda(m.Qall, m.b, bj, m.Pall, m.b, bj, m.I, m.part, m.Z, bj, ms[n]));
+            RBKI_TRY(symmetrize_cuda(m.Z, bj, ms[n]));
+            RBKI_TRY(syev_top_cuda(m.Z, bj, m.R, m.eval, m.evec, m.syev_ws, ms[n]));
+        }
+        if (!any) break;
+        // the Ritz values (and |X|^2, written before the fork) come back on the mode streams
+        bool want_x2 = x2 < 0.0;
+        for (int n = 0; n < pl.N; ++n) {
+            if (!active[n]) continue;
+            lam[n].resize(pl.mode[n].R);
+            RBKI_CUDA_TRY(cudaMemcpyAsync(lam[n].data(), pl.mode[n].eval, pl.mode[n].R * sizeof(double),
+                                          cudaMemcpyDeviceToHost, ms[n]));
+            if (want_x2) {
+                RBKI_CUDA_TRY(cudaMemcpyAsync(&x2, norms, sizeof(double), cudaMemcpyDeviceToHost, ms[n]));
+                want_x2 = false;
+            }
+        }
+        for (int n = 0; n < pl.N; ++n)
+            if (active[n]) RBKI_CUDA_TRY(cudaStreamSynchronize(ms[n]));
+        for (int n = 0; n < pl.N; ++n) {
+            if (!active[n]) continue;
+            const ModePlan& m = pl.mode[n];
+            double sum = 0.0;
+            for (int k = 0; k < m.R; ++k) sum += lam[n][k];
+            const double fit = x2 > 0.0 ? 1.0 - std::sqrt(std::max(x2 - sum, 0.0) / x2) : 1.0;
+            const bool stop = j == m.q || (j >= 1 && std::fabs(fit - prev_fit[n]) <= tol);
+            prev_fit[n] = fit;
+            if (stop) {
+                const int bj = (j + 1) * m.S;
+                RBKI_TRY(form_factor_cuda(m.Qall, m.b, m.I, m.evec, bj, m.R, m.R, out->factors[n], ms[n]));
+                if (out->eigvals[n]) RBKI_TRY(copy_f64_cuda(m.eval, out->eigvals[n], m.R, ms[n]));
+                if (out->info) RBKI_TRY(fill_i32_cuda(out->info + pl.N + n, 0, 1, ms[n]));
+                q_used_host[n] = j;
+                active[n] = false;
+            } else {
+                int32_t* kept = out->info ? out->info + n : m.kept;
+                RBKI_TRY(orth2(m, (j + 1) * m.S, kept, ms[n]));
+            }
+        }
+    }
     return RBKI_OK;
 }
 
@@ -569,6 +687,9 @@ static rbki_status run_sequential(Plan& pl, const rbki_tucker_out* out, cudaStre
     RBKI_TRY(sumsq_cuda(out->core, RBKI_F64, pl.ranks_numel, pl.scal + 64, norms + 1, st));
     if (out->info)
         RBKI_CUDA_TRY(cudaMemcpyAsync(out->info + 2 * pl.N, pl.err, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+    if (out->q_used)
+        for (int n = 0; n < pl.N; ++n)
+            RBKI_TRY(fill_i32_cuda(out->q_used + n, pl.mode[n].gram ? 0 : pl.mode[n].q, 1, st));
     return RBKI_OK;
 }
 
@@ -587,7 +708,29 @@ rbki_status run_tucker(Plan& pl, const rbki_tucker_out* out, cudaStream_t st, co
     }
     prof_end(tok, st);
     const bool concurrent = pl.N > 1 && !(pl.flags & RBKI_FLAG_SERIAL_MODES);
-    if (concurrent) {
+    int32_t q_used[RBKI_MAX_ORDER];
+    for (int n = 0; n < pl.N; ++n) q_used[n] = pl.mode[n].gram ? 0 : pl.mode[n].q;
+    if (pl.flags & RBKI_FLAG_ADAPTIVE_Q) {
+        cudaStream_t ms[RBKI_MAX_ORDER];
+        if (!concurrent) {
+            for (int n = 0; n < pl.N; ++n) ms[n] = st;
+        } else if (mode_streams) {
+            for (int n = 0; n < pl.N; ++n) ms[n] = mode_streams[n];
+        } else {
+            RBKI_TRY(pool_streams(st, ms, pl.N));
+        }
+        cudaEvent_t ev;
+        RBKI_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        RBKI_CUDA_TRY(cudaEventRecord(ev, st));
+        for (int n = 0; n < pl.N; ++n) RBKI_CUDA_TRY(cudaStreamWaitEvent(ms[n], ev, 0));
+        rbki_status rs = run_modes_adaptive(pl, out, norms, ms, q_used);
+        for (int n = 0; n < pl.N && concurrent; ++n) {
+            RBKI_CUDA_TRY(cudaEventRecord(ev, ms[n]));
+            RBKI_CUDA_TRY(cudaStreamWaitEvent(st, ev, 0));
+        }
+        cudaEventDestroy(ev);
+        if (rs < 0) return rs;
+    } else if (concurrent) {
         cudaStream_t ms[RBKI_MAX_ORDER];
         if (mode_streams) {
             for (int n = 0; n < pl.N; ++n) ms[n] = mode_streams[n];
@@ -612,6 +755,8 @@ rbki_status run_tucker(Plan& pl, const rbki_tucker_out* out, cudaStream_t st, co
         for (int n = 0; n < pl.N; ++n)
             RBKI_TRY(mode_factor(pl, pl.mode[n], out->factors[n], out->eigvals[n], out->info, st));
     }
+    if (out->q_used)
+        for (int n = 0; n < pl.N; ++n) RBKI_TRY(fill_i32_cuda(out->q_used + n, q_used[n], 1, st));
     RBKI_TRY(core_chain(pl, out->factors, out->core, st));
     RBKI_TRY(sumsq_cuda(out->core, RBKI_F64, pl.ranks_numel, pl.scal + 64, norms + 1, st));
     if (out->info)

@@ -7,7 +7,7 @@ namespace rbki {
 
 namespace {
 struct HostIoLayout {
-    size_t x_off, core_off, fac_off[RBKI_MAX_ORDER], eig_off[RBKI_MAX_ORDER], norms_off, info_off, total;
+    size_t x_off, core_off, fac_off[RBKI_MAX_ORDER], eig_off[RBKI_MAX_ORDER], norms_off, info_off, q_off, total;
 };
 
 HostIoLayout layout(const Plan& pl) {
@@ -27,6 +27,7 @@ HostIoLayout layout(const Plan& pl) {
     }
     L.norms_off = take(2 * 8);
     L.info_off = take((2 * RBKI_MAX_ORDER + 1) * 4);
+    L.q_off = take(RBKI_MAX_ORDER * 4);
     L.total = off - pl.ws_bytes + 256;
     return L;
 }
@@ -49,6 +50,7 @@ rbki_status run_tucker_host_io(Plan& pl, const rbki_tensor* X, const rbki_tucker
     }
     dout.norms = (double*)(base + L.norms_off);
     dout.info = (int32_t*)(base + L.info_off);
+    dout.q_used = (int32_t*)(base + L.q_off);
     pl.xin = xdev;
     RBKI_TRY(run_tucker(pl, &dout, st));
     RBKI_CUDA_TRY(cudaMemcpyAsync(out->core, dout.core, (size_t)pl.ranks_numel * 8,
@@ -64,6 +66,8 @@ rbki_status run_tucker_host_io(Plan& pl, const rbki_tensor* X, const rbki_tucker
         RBKI_CUDA_TRY(cudaMemcpyAsync(out->norms, dout.norms, 16, cudaMemcpyDeviceToHost, st));
     if (out->info)
         RBKI_CUDA_TRY(cudaMemcpyAsync(out->info, dout.info, (2 * pl.N + 1) * 4, cudaMemcpyDeviceToHost, st));
+    if (out->q_used)
+        RBKI_CUDA_TRY(cudaMemcpyAsync(out->q_used, dout.q_used, pl.N * 4, cudaMemcpyDeviceToHost, st));
     RBKI_CUDA_TRY(cudaStreamSynchronize(st));
     return RBKI_OK;
 }
