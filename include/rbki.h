@@ -145,6 +145,23 @@ rbki_status rbki_tucker_workspace(const rbki_tensor* X, const rbki_params* prm, 
 rbki_status rbki_tucker(const rbki_tensor* X, const rbki_params* prm, void* workspace,
                         size_t workspace_bytes, const rbki_tucker_out* out, void* stream);
 
+/* ---- batches and divide-and-conquer (Sec. 4.1.2) ----------------------------------- */
+/* Workspace of a batch: the items' workspaces one after another (256-byte aligned). */
+rbki_status rbki_tucker_batch_workspace(int32_t count, const rbki_tensor* X, const rbki_params* prm,
+                                        size_t* bytes);
+/* `count` independent rBKI-TK decompositions (arrays X[count], prm[count], out[count];
+ * device buffers, RBKI_FLAG_HOST_IO refused) run concurrently: item k on its own stream
+ * (forked from and joined back to `stream`), with its own mode streams.  Results equal
+ * the items' rbki_tucker calls bit for bit. */
+rbki_status rbki_tucker_batch(int32_t count, const rbki_tensor* X, const rbki_params* prm,
+                              void* workspace, size_t workspace_bytes, const rbki_tucker_out* out,
+                              void* stream);
+/* Divide-and-conquer split: dst[k] (device, dense C-order, dims of X with I_mode replaced by
+ * hi_k - lo_k) = X restricted to mode indices [lo_k, hi_k), lo_k = floor(k I_mode / parts),
+ * hi_k = floor((k+1) I_mode / parts); 1 <= parts <= I_mode.  Same dtype as X. */
+rbki_status rbki_split_mode(const rbki_tensor* X, int32_t mode, int32_t parts, void* const* dst,
+                            void* stream);
+
 /* Bytes of device workspace rbki_htr needs. */
 rbki_status rbki_htr_workspace(const rbki_tensor* X, const rbki_params* tk,
                                const int32_t* tr_ranks, size_t* bytes);

@@ -75,6 +75,9 @@ def lib():
             "rbki_syev": (st, [vp, C.c_int32, vp, vp, vp, C.c_size_t, vp]),
             "rbki_syev_workspace": (st, [C.c_int32, sz]),
             "rbki_sample_units": (st, [C.c_uint64, C.c_int32, C.c_int64, C.c_int64, vp, vp]),
+            "rbki_tucker_batch_workspace": (st, [C.c_int32, vp, vp, sz]),
+            "rbki_tucker_batch": (st, [C.c_int32, vp, vp, vp, C.c_size_t, vp, vp]),
+            "rbki_split_mode": (st, [vp, C.c_int32, C.c_int32, vp, vp]),
             "rbki_status_str": (C.c_char_p, [C.c_int32]),
             "rbki_last_error": (C.c_char_p, []),
             "rbki_kernel_launches": (C.c_uint64, []),
@@ -205,6 +208,52 @@ def rbki_tucker(x, ranks, p, q, seed, prec="bf16", flags=0, workspace=None, out=
                             C.c_size_t(workspace.numel()), C.byref(o), stream_ptr(stream)), "rbki_tucker")
     out["workspace"] = workspace
     return out
+
+
+def rbki_split_mode(x, mode, parts, stream=None):
+    """Consecutive parts of x along `mode` (part k: [floor(k I / K), floor((k+1) I / K))) as
+    dense device tensors, copied by the library's split kernel."""
+    torch = _torch()
+    size = x.shape[mode]
+    outs = []
+    for k in range(parts):
+        shape = list(x.shape)
+        shape[mode] = (k + 1) * size // parts - k * size // parts
+        outs.append(torch.empty(shape, dtype=x.dtype, device=x.device))
+    ptrs = (C.c_void_p * parts)(*[o.data_ptr() for o in outs])
+    check(lib().rbki_split_mode(C.byref(make_tensor(x)), int(mode), int(parts), ptrs, stream_ptr(stream)),
+          "rbki_split_mode")
+    return outs
+
+
+def rbki_tucker_batch(xs, ranks, p, q, seeds, prec="bf16", flags=0, omega=0.0, q_tol=0.0, workspace=None,
+                      outs=None, stream=None):
+    """Independent rBKI-TK decompositions run concurrently (one call).  ranks[k], seeds[k]
+    per item; returns the list of output dicts (the first also holds the workspace)."""
+    torch = _torch()
+    n = len(xs)
+    ts = (rbki_tensor * n)(*[make_tensor(x) for x in xs])
+    ps = (rbki_params * n)(*[make_params(ranks[k], p, q, seeds[k], prec, flags, omega, q_tol) for k in range(n)])
+    need = C.c_size_t(0)
+    check(lib().rbki_tucker_batch_workspace(n, ts, ps, C.byref(need)), "rbki_tucker_batch_workspace")
+    if workspace is None or workspace.numel() < need.value:
+        workspace = torch.empty(int(need.value), dtype=torch.uint8, device=xs[0].device)
+    if outs is None:
+        outs = [alloc_outputs(x.shape, ranks[k], x.device) for k, x in enumerate(xs)]
+    os_ = (rbki_tucker_out * n)(*[make_out(o) for o in outs])
+    check(lib().rbki_tucker_batch(n, ts, ps, C.c_void_p(workspace.data_ptr()), C.c_size_t(workspace.numel()),
+                                  os_, stream_ptr(stream)), "rbki_tucker_batch")
+    outs[0]["workspace"] = workspace
+    return outs
+
+
+def rbki_divide_and_conquer(x, mode, parts, ranks, p, q, seed, prec="bf16", flags=0, stream=None):
+    """Divide-and-conquer decomposition along `mode`: split into `parts` consecutive parts,
+    decompose them as one batch (part k with ranks[k] and seed + k).  Returns (parts, outs)."""
+    xs = rbki_split_mode(x, mode, parts, stream=stream)
+    outs = rbki_tucker_batch(xs, ranks, p, q, [seed + k for k in range(parts)], prec=prec, flags=flags,
+                             stream=stream)
+    return xs, outs
 
 
 def rbki_htr(x, tucker_ranks, p, q, seed, tr_ranks, tr_init, maxit=20, tol=1e-3, prec="fp64", flags=0,

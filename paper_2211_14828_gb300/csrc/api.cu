@@ -285,8 +285,11 @@ void carve(Plan& pl, void* ws) {
                 orth = std::max(orth, orth_scratch_doubles(m.I, j * m.S, m.S));
             m.small = c.take<double>(orth);
             m.N = (int)rup(pl.split ? 2 * m.S : m.S, 16);
-            m.tc = pl.mixed && tc::supported(v, tc::KRYLOV, m.N) && tc::supported(v, tc::SKETCH, m.N);
-            if (m.tc) {
+            const bool kr = tc::supported(v, tc::KRYLOV, m.N), sk = tc::supported(v, tc::SKETCH, m.N);
+            m.tc = pl.mixed && kr && sk;
+            // two-pass Krylov step when the fused one does not fit (I_n > 640); plain operands
+            m.tc2 = pl.mixed && !m.tc && !pl.split && sk && tc::supported(v, tc::TTM, m.N);
+            if (m.tc || m.tc2) {
                 m.tgrid = tc::grid_size(v);
                 m.qimg = c.take<char>(tc::image_bytes_skinny(v, m.N));
                 m.omg = c.take<char>(tc::image_bytes_omega(v, m.N));
@@ -363,6 +366,16 @@ static rbki_status sample_mode(const Plan& pl, const ModePlan& m, cudaStream_t s
 rbki_status krylov_step(const Plan& pl, const ModePlan& m, const double* Q, int64_t ldq, int S,
                         double* out, int64_t ldo, double* out2, int64_t ldo2, cudaStream_t st) {
     View v = mode_view(pl, m);
+    if (m.tc2) {
+        // pass 1 writes Y = X_(n)^T Q as per-tile operand images (into the Omega image buffer,
+        // free after the sketch); pass 2 is the sketch kernel with Y in place of Omega
+        RBKI_TRY(tc::skinny_image(Q, ldq, m.I, S, m.N, false, pl.stream_dtype == RBKI_F16, m.qimg, st));
+        int tok = prof_begin(RBKI_PROF_KRYLOV, st);
+        RBKI_TRY(tc::stream_tc(tc::TTM, v, m.N, S, false, m.qimg, nullptr, nullptr, nullptr, pl.err, st, m.omg));
+        RBKI_TRY(tc::stream_tc(tc::SKETCH, v, m.N, S, false, nullptr, m.omg, m.tpart, nullptr, pl.err, st));
+        prof_end(tok, st);
+        return tc::reduce_parts(m.tpart, m.tgrid, m.I, m.N, S, false, out, ldo, out2, ldo2, st);
+    }
     if (m.tc) {
         RBKI_TRY(tc::skinny_image(Q, ldq, m.I, S, m.N, pl.split, pl.stream_dtype == RBKI_F16, m.qimg, st));
         int tok = prof_begin(RBKI_PROF_KRYLOV, st);
@@ -387,7 +400,7 @@ rbki_status orth2(const ModePlan& m, int col0, int32_t* kept, cudaStream_t st) {
 rbki_status mode_basis(const Plan& pl, const ModePlan& m, int32_t* kept, cudaStream_t st) {
     View v = mode_view(pl, m);
     // step 1-2: W = X_(n) Omega  (Omega generated in the [A][S][C] layout)
-    if (m.tc) {
+    if (m.tc || m.tc2) {
         RBKI_TRY(tc::omega_images(pl.seed, m.n, v, m.S, m.N, pl.split, m.omg, st));
         int tok = prof_begin(RBKI_PROF_SKETCH, st);
         RBKI_TRY(tc::stream_tc(tc::SKETCH, v, m.N, m.S, pl.split, nullptr, m.omg, m.tpart, nullptr, pl.err, st));
@@ -432,8 +445,11 @@ rbki_status mode_factor(const Plan& pl, const ModePlan& m, double* U, double* ei
         // b >= I: Z = X_(n) X_(n)^T, Q = I (reading c7)
         View v = mode_view(pl, m);
         int tok = prof_begin(RBKI_PROF_GRAM, st);
-        RBKI_TRY(contract_cuda(v, pl.xstream, pl.stream_dtype, (int)m.I, pl.mixed, m.part,
-                               m.nsplit, m.Z, m.I, nullptr, 0, st));
+        if (m.I <= 8)
+            RBKI_TRY(gram_small_cuda(v, pl.mixed, m.part, m.nsplit, m.Z, m.I, st));
+        else
+            RBKI_TRY(contract_cuda(v, pl.xstream, pl.stream_dtype, (int)m.I, pl.mixed, m.part,
+                                   m.nsplit, m.Z, m.I, nullptr, 0, st));
         prof_end(tok, st);
         RBKI_TRY(symmetrize_cuda(m.Z, (int)m.I, st));
         RBKI_TRY(syev_top_cuda(m.Z, (int)m.I, m.R, m.eval, m.evec, m.syev_ws, st));
@@ -480,7 +496,7 @@ static rbki_status run_modes_adaptive(const Plan& pl, const rbki_tucker_out* out
         RBKI_TRY(fill_i32_cuda(kept, 0, 1, ms[n]));
         // Algorithm 1 steps 1-2 and Q_0 (the sketch part of mode_basis)
         View v = mode_view(pl, m);
-        if (m.tc) {
+        if (m.tc || m.tc2) {
             RBKI_TRY(tc::omega_images(pl.seed, m.n, v, m.S, m.N, pl.split, m.omg, ms[n]));
             int tok = prof_begin(RBKI_PROF_SKETCH, ms[n]);
             RBKI_TRY(tc::stream_tc(tc::SKETCH, v, m.N, m.S, pl.split, nullptr, m.omg, m.tpart, nullptr, pl.err, ms[n]));
@@ -600,7 +616,7 @@ struct StreamPool {
     cudaStream_t owner = nullptr;
     cudaStream_t s[RBKI_MAX_ORDER];
 };
-constexpr int MAX_POOLS = 32;
+constexpr int MAX_POOLS = 64;
 static std::mutex g_pool_mu;
 static std::vector<StreamPool> g_pools[64];
 
@@ -690,6 +706,38 @@ static rbki_status run_sequential(Plan& pl, const rbki_tucker_out* out, cudaStre
     if (out->q_used)
         for (int n = 0; n < pl.N; ++n)
             RBKI_TRY(fill_i32_cuda(out->q_used + n, pl.mode[n].gram ? 0 : pl.mode[n].q, 1, st));
+    return RBKI_OK;
+}
+
+// Per-caller item streams of a batch (rbki_tucker_batch): item k of a batch issued on
+// `caller` runs on item stream k mod MAX_ITEMS, which then owns its own mode-stream set.
+constexpr int MAX_ITEMS = 32;
+struct ItemPool {
+    cudaStream_t owner = nullptr;
+    std::vector<cudaStream_t> s;
+};
+static std::vector<ItemPool> g_items[64];
+
+static rbki_status item_streams(cudaStream_t caller, int count, std::vector<cudaStream_t>& out) {
+    int dev = 0;
+    RBKI_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return set_error(RBKI_E_UNSUPPORTED, "device index");
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    ItemPool* p = nullptr;
+    for (auto& q : g_items[dev])
+        if (q.owner == caller) p = &q;
+    if (!p) {
+        g_items[dev].push_back(ItemPool{caller, {}});
+        p = &g_items[dev].back();
+    }
+    const int want = std::min(count, MAX_ITEMS);
+    while ((int)p->s.size() < want) {
+        cudaStream_t s;
+        RBKI_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        p->s.push_back(s);
+    }
+    out.resize(count);
+    for (int k = 0; k < count; ++k) out[k] = p->s[k % MAX_ITEMS];
     return RBKI_OK;
 }
 
@@ -865,10 +913,12 @@ static rbki_status krylov_product_plan(const rbki_tensor* X, int32_t mode, int32
     View v{nullptr, pl.stream_dtype, m.A, m.I, m.C};
     m.N = (int)rup(pl.split ? 2 * s : s, 16);
     m.tc = pl.mixed && tc::supported(v, tc::KRYLOV, m.N);
-    if (m.tc) {
+    m.tc2 = pl.mixed && !m.tc && !pl.split && tc::supported(v, tc::SKETCH, m.N) && tc::supported(v, tc::TTM, m.N);
+    if (m.tc || m.tc2) {
         m.tgrid = tc::grid_size(v);
         m.qimg = c.take<char>(tc::image_bytes_skinny(v, m.N));
         m.tpart = c.take<float>((size_t)m.tgrid * m.I * m.N);
+        if (m.tc2) m.omg = c.take<char>(tc::image_bytes_omega(v, m.N));
     } else {
         m.nsplit = contract_nsplit(v);
         m.Y = c.take<double>((size_t)m.A * m.C * s);
@@ -1050,6 +1100,78 @@ rbki_status rbki_htr(const rbki_tensor* X, const rbki_params* tk, const int32_t*
         RBKI_CUDA_TRY(cudaStreamSynchronize(st));
     }
     return RBKI_OK;
+}
+
+// ---- batches and divide-and-conquer (Sec. 4.1.2) ----
+static rbki_status batch_plans(int32_t count, const rbki_tensor* X, const rbki_params* prm, std::vector<Plan>& pls,
+                               std::vector<size_t>& off, size_t* total) {
+    if (count < 1 || !X || !prm) return set_error(RBKI_E_INVAL, "batch: count < 1 or NULL arrays");
+    pls.resize(count);
+    off.resize(count);
+    size_t t = 0;
+    for (int k = 0; k < count; ++k) {
+        if (prm[k].flags & RBKI_FLAG_HOST_IO) return set_error(RBKI_E_UNSUPPORTED, "batch items use device buffers");
+        RBKI_TRY(make_plan(&X[k], &prm[k], pls[k]));
+        carve(pls[k], nullptr);
+        off[k] = t;
+        t += (pls[k].ws_bytes + 255) & ~(size_t)255;
+    }
+    *total = t + 256;
+    return RBKI_OK;
+}
+
+rbki_status rbki_tucker_batch_workspace(int32_t count, const rbki_tensor* X, const rbki_params* prm, size_t* bytes) {
+    if (!bytes) return set_error(RBKI_E_INVAL, "bytes is NULL");
+    std::vector<Plan> pls;
+    std::vector<size_t> off;
+    return batch_plans(count, X, prm, pls, off, bytes);
+}
+
+rbki_status rbki_tucker_batch(int32_t count, const rbki_tensor* X, const rbki_params* prm, void* workspace,
+                              size_t workspace_bytes, const rbki_tucker_out* out, void* stream) {
+    std::vector<Plan> pls;
+    std::vector<size_t> off;
+    size_t need = 0;
+    RBKI_TRY(batch_plans(count, X, prm, pls, off, &need));
+    if (!out) return set_error(RBKI_E_INVAL, "out is NULL");
+    for (int k = 0; k < count; ++k) {
+        if (!out[k].core) return set_error(RBKI_E_INVAL, "out[k].core is NULL");
+        for (int n = 0; n < pls[k].N; ++n)
+            if (!out[k].factors[n]) return set_error(RBKI_E_INVAL, "out[k].factors[n] is NULL");
+    }
+    if (!workspace || workspace_bytes < need) return set_error(RBKI_E_NOMEM, "workspace too small");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<cudaStream_t> items;
+    RBKI_TRY(item_streams(st, count, items));
+    cudaEvent_t ev;
+    RBKI_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    RBKI_CUDA_TRY(cudaEventRecord(ev, st));
+    for (int k = 0; k < count && k < MAX_ITEMS; ++k) RBKI_CUDA_TRY(cudaStreamWaitEvent(items[k], ev, 0));
+    rbki_status rs = RBKI_OK;
+    for (int k = 0; k < count && rs >= 0; ++k) {
+        carve(pls[k], static_cast<char*>(workspace) + off[k]);
+        pls[k].xin = X[k].data;
+        rs = run_tucker(pls[k], &out[k], items[k]);
+    }
+    for (int k = 0; k < count && k < MAX_ITEMS; ++k) {
+        RBKI_CUDA_TRY(cudaEventRecord(ev, items[k]));
+        RBKI_CUDA_TRY(cudaStreamWaitEvent(st, ev, 0));
+    }
+    cudaEventDestroy(ev);
+    return rs;
+}
+
+rbki_status rbki_split_mode(const rbki_tensor* X, int32_t mode, int32_t parts, void* const* dst, void* stream) {
+    RBKI_TRY(validate_tensor(X));
+    if (mode < 0 || mode >= X->order) return set_error(RBKI_E_INVAL, "mode out of range");
+    if (parts < 1 || parts > X->dims[mode]) return set_error(RBKI_E_INVAL, "need 1 <= parts <= I_mode");
+    if (!dst) return set_error(RBKI_E_INVAL, "dst is NULL");
+    for (int k = 0; k < parts; ++k)
+        if (!dst[k]) return set_error(RBKI_E_INVAL, "dst[k] is NULL");
+    int64_t A = 1, C = 1;
+    for (int k = 0; k < mode; ++k) A *= X->dims[k];
+    for (int k = mode + 1; k < X->order; ++k) C *= X->dims[k];
+    return split_mode_cuda(X->data, X->dtype, A, X->dims[mode], C, parts, dst, (cudaStream_t)stream);
 }
 
 rbki_status rbki_sample_units(uint64_t seed, int32_t mode, int64_t n_units, int64_t kept, int32_t* units,

@@ -191,7 +191,85 @@ __global__ void k_reduce_parts(const double* __restrict__ part, int nsplit, int6
 template <typename T>
 const T* as(const void* p) { return static_cast<const T*>(p); }
 
+// Gram matrix of a short mode (I <= IM): part[block][i][j] = sum over the block's columns of
+// X_(n)[i][col] X_(n)[j][col].  One thread per column at a time (coalesced in c when C > 1),
+// the I(I+1)/2 products in registers, then a fixed-order CTA reduction: an HBM-bound single
+// pass for the Gram path of modes such as a video's colour mode.
+template <typename T, typename Acc, int IM>
+__global__ void __launch_bounds__(256) k_gram_small(const T* __restrict__ X, int64_t A, int I, int64_t C,
+                                                    int64_t cols_per_block, double* __restrict__ part) {
+    constexpr int NP = IM * (IM + 1) / 2;
+    __shared__ Acc red[8][NP];
+    Acc acc[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) acc[k] = 0;
+    const int64_t d = A * C;
+    const int64_t lo = (int64_t)blockIdx.x * cols_per_block;
+    const int64_t hi = lo + cols_per_block < d ? lo + cols_per_block : d;
+    int64_t col = lo + threadIdx.x;
+    int64_t a = col / C, c = col - a * C;
+    const int64_t step_a = (int64_t)blockDim.x / C, step_c = (int64_t)blockDim.x - step_a * C;
+    for (; col < hi; col += blockDim.x) {
+        Acc x[IM];
+#pragma unroll
+        for (int i = 0; i < IM; ++i) x[i] = i < I ? ld_acc<Acc>(X + (a * I + i) * C + c) : (Acc)0;
+        int k = 0;
+#pragma unroll
+        for (int i = 0; i < IM; ++i)
+#pragma unroll
+            for (int j = i; j < IM; ++j) acc[k++] += x[i] * x[j];
+        c += step_c;
+        a += step_a;
+        if (c >= C) { c -= C; ++a; }
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        const Acc v = warp_sum(acc[k]);
+        if (lane == 0) red[w][k] = v;
+    }
+    __syncthreads();
+    double* out = part + (int64_t)blockIdx.x * I * I;
+    for (int e = threadIdx.x; e < NP; e += blockDim.x) {
+        double v = 0.0;
+        for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) v += (double)red[ww][e];
+        int i = 0, rem = e;                        // e -> (i, j), j >= i, row-major upper triangle
+        while (rem >= IM - i) { rem -= IM - i; ++i; }
+        const int j = i + rem;
+        if (i < I && j < I) {
+            out[i * I + j] = v;
+            out[j * I + i] = v;
+        }
+    }
+}
+
 }  // namespace
+
+rbki_status gram_small_cuda(const View& x, bool acc32, double* part, int nblocks, double* out, int64_t ld,
+                            cudaStream_t st) {
+    if (x.I > 8) return set_error(RBKI_E_UNSUPPORTED, "gram_small: I > 8");
+    const int64_t d = x.A * x.C;
+    const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(nblocks, cdiv(d, 256)));
+    const int64_t cpb = cdiv(d, nb);
+#define GS_L(T, ACC, IM) k_gram_small<T, ACC, IM><<<nb, 256, 0, st>>>(as<T>(x.data), x.A, (int)x.I, x.C, cpb, part)
+#define GS_I(T, ACC) if (x.I <= 4) { GS_L(T, ACC, 4); } else { GS_L(T, ACC, 8); }
+#define GS_D(T) if (acc32) { GS_I(T, float) } else { GS_I(T, double) }
+    switch (x.dtype) {
+        case RBKI_F64: GS_D(double); break;
+        case RBKI_F32: GS_D(float); break;
+        case RBKI_BF16: GS_D(__nv_bfloat16); break;
+        case RBKI_F16: GS_D(__half); break;
+        default: return set_error(RBKI_E_INVAL, "gram_small: dtype");
+    }
+#undef GS_D
+#undef GS_I
+#undef GS_L
+    RBKI_LAUNCH_CHECK("k_gram_small");
+    const int64_t n = x.I * x.I;
+    k_reduce_parts<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(part, nb, x.I, (int)x.I, out, ld, nullptr, 0);
+    RBKI_LAUNCH_CHECK("k_reduce_parts");
+    return RBKI_OK;
+}
 
 rbki_status ttm_cuda(const View& x, const double* M, int64_t ldm, int S, void* Y, int y_dtype,
                      bool acc32, cudaStream_t st) {

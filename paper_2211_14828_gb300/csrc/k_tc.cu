@@ -324,7 +324,22 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_stream_tc(const __grid_constant
                     tc_fence_before();
                     mbar_arrive(b_yready + 8 * b);
                     const int64_t t = blockIdx.x + k * gridDim.x;
-                    if (!IFAST) {
+                    if (p.yimg_out) {
+                        // Y as the tile's operand image for a later SKETCH pass: element (c, n)
+                        // at (n/8)*1024 + c*8 + n%8; zero past Sh and for columns outside X
+                        const bool valid = !IFAST ? (t % p.ctiles) * 128 + row < p.C : t * 128 + row < p.A;
+                        for (int s = 0; s < N; ++s)
+                            if (!valid || s >= Sh) v[s] = 0.f;
+                        uint16_t* base = (uint16_t*)p.yimg_out + (size_t)t * 128 * N;
+                        for (int g = 0; g < N / 8; ++g) {
+                            uint4 w;
+                            w.x = pack2(v[8 * g + 0], v[8 * g + 1], fp16);
+                            w.y = pack2(v[8 * g + 2], v[8 * g + 3], fp16);
+                            w.z = pack2(v[8 * g + 4], v[8 * g + 5], fp16);
+                            w.w = pack2(v[8 * g + 6], v[8 * g + 7], fp16);
+                            *reinterpret_cast<uint4*>(base + g * 1024 + row * 8) = w;
+                        }
+                    } else if (!IFAST) {
                         const int64_t a = t / p.ctiles, c = (t % p.ctiles) * 128 + row;
                         if (c < p.C)
                             for (int s = 0; s < Sh; ++s) p.yout[(a * Sh + s) * p.C + c] = v[s];
@@ -566,7 +581,7 @@ rbki_status omega_images(uint64_t seed, int mode, const View& v, int S, int N, b
 }
 
 rbki_status stream_tc(int mode, const View& v, int N, int Sh, bool split, const void* qimg, const void* omg,
-                      float* part, float* yout, int* err, cudaStream_t st) {
+                      float* part, float* yout, int* err, cudaStream_t st, void* yimg_out) {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return set_error(RBKI_E_CUDA, "cuTensorMapEncodeTiled unavailable");
     const bool ifast = v.C == 1;
@@ -600,6 +615,7 @@ rbki_status stream_tc(int mode, const View& v, int N, int Sh, bool split, const 
     p.qimg_bytes = mode == SKETCH ? 0 : (uint32_t)image_bytes_skinny(v, N);
     p.yimg_bytes = (uint32_t)(128 * N * 2);
     p.part = part; p.yout = yout; p.err = err;
+    p.yimg_out = mode == TTM ? yimg_out : nullptr;
     p.fp16 = v.dtype == RBKI_F16 ? 1 : 0;
     uint32_t tm = (uint32_t)((mode == TTM ? 0 : p.NS * N) + (mode == SKETCH ? 0 : 2 * N));
     uint32_t cols = 32;

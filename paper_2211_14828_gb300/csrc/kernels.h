@@ -21,7 +21,16 @@ rbki_status sample_units_cuda(uint64_t seed, int mode, int64_t nu, int64_t kept,
 rbki_status gather_units_cuda(const void* x, int dtype, int64_t A, int64_t I, int64_t C, const int32_t* units,
                               int64_t kept, void* y, cudaStream_t st);
 
+// ---- divide-and-conquer split (k_split.cu) ----
+// dst[k] (dense [A][I_k][C]) = X[:, floor(k I / parts) : floor((k+1) I / parts), :]
+rbki_status split_mode_cuda(const void* x, int dtype, int64_t A, int64_t I, int64_t C, int parts, void* const* dst,
+                            cudaStream_t st);
+
 // ---- FP64/FP32 CUDA-core streaming products (k_stream.cu) ----
+// Gram path of a short mode (I <= 8): out (I x I, ld) = X_(n) X_(n)^T, one pass, partials
+// [nblocks][I][I] in `part`, fixed-order reduce
+rbki_status gram_small_cuda(const View& x, bool acc32, double* part, int nblocks, double* out, int64_t ld,
+                            cudaStream_t st);
 // TTM: Y[a][s][c] = sum_i M[i*ldm + s] X[a][i][c],  s < S.  Y is [A][S][C] (Tout).
 // `acc32` = accumulate in FP32 (mixed path), else FP64.
 // Y (FP64, [A][S][C]) = X x_n M^T for S <= 32 (F64/F32 input): the small core-chain products

@@ -30,6 +30,8 @@ struct ModePlan {
     int32_t* kept = nullptr;
     // tensor-core path (mixed precision)
     bool tc = false;               // sketch + Krylov steps on tcgen05
+    bool tc2 = false;              // tcgen05 too, Krylov step in two passes (Y = X^T Q to images,
+                                   // then P = X Y): I_n too large for the fused step
     int N = 0;                     // MMA width (includes the lo half when split)
     void* qimg = nullptr;          // BF16 operand image of Q_j
     void* omg = nullptr;           // per-tile Omega images

@@ -24,6 +24,8 @@ struct Params {
     uint32_t yimg_bytes;    // 128 * N * 2
     float* part;            // [grid][I][N] partial products (KRYLOV, SKETCH)
     float* yout;            // [A][Sh][C] TTM output
+    void* yimg_out;         // TTM alternative output: per-tile BF16/FP16 images of Y in the
+                            // layout SKETCH consumes (the first pass of a two-pass Krylov step)
     int* err;               // error word (bounded wait expired)
     int fp16;
 };
@@ -38,7 +40,7 @@ rbki_status skinny_image(const double* M, int64_t ldm, int64_t rows, int S, int 
 rbki_status omega_images(uint64_t seed, int mode, const View& v, int S, int N, bool split, void* img,
                          cudaStream_t st);
 rbki_status stream_tc(int mode, const View& v, int N, int Sh, bool split, const void* qimg, const void* omg,
-                      float* part, float* yout, int* err, cudaStream_t st);
+                      float* part, float* yout, int* err, cudaStream_t st, void* yimg_out = nullptr);
 rbki_status reduce_parts(const float* part, int nb, int64_t I, int N, int Sh, bool split, double* out,
                          int64_t ld, double* out2, int64_t ld2, cudaStream_t st);
 

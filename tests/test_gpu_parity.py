@@ -228,3 +228,34 @@ def test_krylov_product_tensor_core(rb, dims, s):
         rel = np.linalg.norm(p - want) / np.linalg.norm(want)
         assert rel < 2e-3, (mode, rel)
         assert np.linalg.norm(p - exact) / np.linalg.norm(exact) < 1e-2
+
+
+@pytest.mark.parametrize("dims,mode", [((1024, 96, 40), 0), ((40, 1024, 48), 1), ((48, 40, 1024), 2),
+                                       ((1000, 64, 24), 0)])
+@pytest.mark.parametrize("s", [12, 50])
+def test_krylov_product_two_pass(rb, dims, mode, s):
+    """I_n > 640: the fused tensor-core step does not fit, so the step runs in two passes
+    (Y = X^T Q written as BF16 operand images, then P = X Y on the sketch kernel); same
+    rounding as the fused plain-BF16 step."""
+    g = np.random.default_rng(sum(dims) + s)
+    x = g.standard_normal(dims).astype(np.float32)
+    xt = torch.from_numpy(x).cuda()
+    xb = _bf16(x)
+    q = g.standard_normal((dims[mode], s))
+    p = rb.rbki_krylov_product(xt, mode, torch.from_numpy(q).cuda(), prec="bf16").cpu().numpy()
+    xn = unfold(xb, mode)
+    want = xn @ _bf16(xn.T @ _bf16(q))
+    assert np.linalg.norm(p - want) / np.linalg.norm(want) < 2e-3
+
+
+@pytest.mark.parametrize("dims,core", [((3, 40, 50), (2, 5, 6)), ((40, 50, 5), (5, 6, 3)),
+                                       ((30, 8, 20, 7), (4, 3, 4, 2))])
+def test_tucker_short_gram_modes(rb, dims, core):
+    """Gram-path modes with I_n <= 8 run on the one-pass short-mode Gram kernel (both
+    layouts: C > 1 and the last mode); FP64 bar, and the mixed path within 1%."""
+    wl = synth.config_small_fp64(mc=12, dims=dims, core=core, p=3, q=1)
+    _, ref = _check_fp64(rb, wl)
+    e_ref = np.sqrt(max(ref["x_norm2"] - ref["core_norm2"], 0.0))
+    out = rb.rbki_tucker(torch.from_numpy(wl.x.astype(np.float32)).cuda(), wl.ranks, wl.p, wl.q, wl.seed,
+                         prec="bf16")
+    assert abs(_err_from_norms(out["norms"]) - e_ref) <= 0.01 * e_ref
