@@ -445,7 +445,7 @@ rbki_status mode_factor(const Plan& pl, const ModePlan& m, double* U, double* ei
         // b >= I: Z = X_(n) X_(n)^T, Q = I (reading c7)
         View v = mode_view(pl, m);
         int tok = prof_begin(RBKI_PROF_GRAM, st);
-        if (m.I <= 8)
+        if (m.I <= (pl.mixed ? 16 : 8))
             RBKI_TRY(gram_small_cuda(v, pl.mixed, m.part, m.nsplit, m.Z, m.I, st));
         else
             RBKI_TRY(contract_cuda(v, pl.xstream, pl.stream_dtype, (int)m.I, pl.mixed, m.part,

@@ -247,13 +247,14 @@ __global__ void __launch_bounds__(256) k_gram_small(const T* __restrict__ X, int
 
 rbki_status gram_small_cuda(const View& x, bool acc32, double* part, int nblocks, double* out, int64_t ld,
                             cudaStream_t st) {
-    if (x.I > 8) return set_error(RBKI_E_UNSUPPORTED, "gram_small: I > 8");
+    if (x.I > (acc32 ? 16 : 8)) return set_error(RBKI_E_UNSUPPORTED, "gram_small: I too large");
     const int64_t d = x.A * x.C;
     const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(nblocks, cdiv(d, 256)));
     const int64_t cpb = cdiv(d, nb);
 #define GS_L(T, ACC, IM) k_gram_small<T, ACC, IM><<<nb, 256, 0, st>>>(as<T>(x.data), x.A, (int)x.I, x.C, cpb, part)
+// FP32 accumulation up to I = 16 (136 accumulators fit in registers), FP64 up to I = 8
 #define GS_I(T, ACC) if (x.I <= 4) { GS_L(T, ACC, 4); } else { GS_L(T, ACC, 8); }
-#define GS_D(T) if (acc32) { GS_I(T, float) } else { GS_I(T, double) }
+#define GS_D(T) if (acc32) { if (x.I > 8) { GS_L(T, float, 16); } else { GS_I(T, float) } } else { GS_I(T, double) }
     switch (x.dtype) {
         case RBKI_F64: GS_D(double); break;
         case RBKI_F32: GS_D(float); break;

@@ -27,7 +27,7 @@ rbki_status split_mode_cuda(const void* x, int dtype, int64_t A, int64_t I, int6
                             cudaStream_t st);
 
 // ---- FP64/FP32 CUDA-core streaming products (k_stream.cu) ----
-// Gram path of a short mode (I <= 8): out (I x I, ld) = X_(n) X_(n)^T, one pass, partials
+// Gram path of a short mode (I <= 8; I <= 16 with FP32 accumulation): out (I x I, ld) = X_(n) X_(n)^T, one pass, partials
 // [nblocks][I][I] in `part`, fixed-order reduce
 rbki_status gram_small_cuda(const View& x, bool acc32, double* part, int nblocks, double* out, int64_t ld,
                             cudaStream_t st);

@@ -249,10 +249,10 @@ def test_krylov_product_two_pass(rb, dims, mode, s):
 
 
 @pytest.mark.parametrize("dims,core", [((3, 40, 50), (2, 5, 6)), ((40, 50, 5), (5, 6, 3)),
-                                       ((30, 8, 20, 7), (4, 3, 4, 2))])
+                                       ((30, 8, 20, 7), (4, 3, 4, 2)), ((16, 16, 16, 16), (8, 8, 8, 8))])
 def test_tucker_short_gram_modes(rb, dims, core):
-    """Gram-path modes with I_n <= 8 run on the one-pass short-mode Gram kernel (both
-    layouts: C > 1 and the last mode); FP64 bar, and the mixed path within 1%."""
+    """Gram-path modes with I_n <= 8 (<= 16 on the mixed path) run on the one-pass short-mode
+    Gram kernel (both layouts: C > 1 and the last mode); FP64 bar, and the mixed path within 1%."""
     wl = synth.config_small_fp64(mc=12, dims=dims, core=core, p=3, q=1)
     _, ref = _check_fp64(rb, wl)
     e_ref = np.sqrt(max(ref["x_norm2"] - ref["core_norm2"], 0.0))
