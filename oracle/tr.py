@@ -12,6 +12,10 @@ Readings (the design doc lists them):
        |Fit_t - Fit_{t-1}| <= tol, Fit measured as a fraction against G (Sec. 4 stopping
        rule, max 20 iterations, tol 1e-3).
 
+TR-SVD (`tr_svd`, reading c32) is pinned by exact recovery of a TR tensor whose unfolding
+ranks match, by the exact split of its error into the steps' truncation errors, and, for
+N = 2 with r_1 = 1, by the Eckart-Young truncated SVD.
+
 Parity: the LS update is pinned by monotone non-increasing residual (exact ALS) and by
 exact recovery of a noiseless TR tensor's ring from a nearby start; the contraction
 identity R[[Z_n x_2 U_n]] = R[[Z_n]] x_1 U_1 ... x_N U_N is pinned exactly.  Agreement
@@ -77,15 +81,52 @@ def tr_als(g: np.ndarray, init: Sequence[np.ndarray], maxit: int = 20, tol: floa
     return cores, fits
 
 
+def tr_svd(g: np.ndarray, ranks: Sequence[int]):
+    """TR-SVD (Zhao, Zhou, Xie, Zhang, Cichocki 2016), the alternative Algorithm 3 step 3
+    names, with fixed TR ranks (reading c32): core n has shape (r_{n-1}, S_n, r_n), r_{-1} =
+    r_{N-1}.
+      step 0:  C = G as S_1 x prod(rest); truncated SVD of rank r_{N-1} r_0; core 0 [a, i, b]
+               = U[i, a r_0 + b]; the remainder Sigma V^T, indexed (a, b, rest), is reordered
+               to (b, rest, a) and read as (r_0 S_2) x (prod(rest) r_{N-1} / S_2);
+      step n:  truncated SVD of rank r_n of C ((r_{n-1} S_n) x ...); core n = U as
+               (r_{n-1}, S_n, r_n); C <- Sigma V^T read as (r_n S_{n+1}) x ...;
+      last:    core N-1 = C as (r_{N-2}, S_N, r_{N-1}).
+    Returns (cores, squared truncation error of every step)."""
+    g = np.asarray(g, dtype=np.float64)
+    n = g.ndim
+    r = list(ranks)
+    cores = []
+    errs = []
+    c = g.reshape(g.shape[0], -1)
+    for k in range(n - 1):
+        rk = r[n - 1] * r[0] if k == 0 else r[k]
+        u, sv, vt = np.linalg.svd(c, full_matrices=False)
+        errs.append(float(np.sum(sv[rk:] ** 2)))
+        u, w = u[:, :rk], sv[:rk, None] * vt[:rk]
+        if k == 0:
+            cores.append(u.reshape(g.shape[0], r[n - 1], r[0]).transpose(1, 0, 2).copy())
+            w = w.reshape(r[n - 1], r[0], -1).transpose(1, 2, 0)          # (b, rest, a)
+            c = w.reshape(r[0] * g.shape[1], -1)
+        else:
+            cores.append(u.reshape(r[k - 1], g.shape[k], r[k]).copy())
+            c = w.reshape(r[k] * g.shape[k + 1], -1)
+    cores.append(c.reshape(r[n - 2], g.shape[n - 1], r[n - 1]).copy())
+    return cores, errs
+
+
 def contract_factor(core: np.ndarray, u: np.ndarray) -> np.ndarray:
     """Algorithm 3 step 4: X_n = G_n x_2 U^(n):  X_n[a, i, b] = sum_s U[i, s] G_n[a, s, b]."""
     return np.einsum("is,asb->aib", u, core)
 
 
 def rbki_tk_tr(x: np.ndarray, tucker_ranks: Sequence[int], p: int, q: int, seed: int,
-               tr_init: Sequence[np.ndarray], maxit: int = 20, tol: float = 1e-3):
-    """Algorithm 3 (rBKI-TK-TR)."""
+               tr_init: Sequence[np.ndarray], maxit: int = 20, tol: float = 1e-3, tr_ranks=None):
+    """Algorithm 3 (rBKI-TK-TR).  tr_init None: TR-SVD with ranks tr_ranks instead of TR-ALS."""
     tk = rbki_tucker(x, tucker_ranks, p, q, seed)
-    cores, fits = tr_als(tk["core"], tr_init, maxit, tol)
+    if tr_init is None:
+        cores, _ = tr_svd(tk["core"], tr_ranks)
+        fits = [tr_fit(tk["core"], cores)]
+    else:
+        cores, fits = tr_als(tk["core"], tr_init, maxit, tol)
     tr_cores = [contract_factor(c, u) for c, u in zip(cores, tk["factors"])]
     return dict(tucker=tk, small_cores=cores, fits=fits, cores=tr_cores)
