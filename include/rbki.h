@@ -76,6 +76,12 @@ enum {
                                       Q_{j+1} = orth(X X^T Q_j) replaces the block instead of
                                       extending it; the basis is Q_q alone (width S_n); a mode
                                       takes the Gram path when S_n >= I_n */
+    RBKI_FLAG_TR_SVD = 64u,        /* rbki_htr: TR-SVD (Zhao et al. 2016) on the core instead of
+                                      TR-ALS (the alternative Algorithm 3 step 3 names): fixed
+                                      ranks, sequential truncated SVDs, the first splitting the
+                                      rank product r_{N-1} r_0; tr_init is not read (may be
+                                      NULL); fits[0] = the ring's fit to G, the rest NaN.
+                                      Unfolding rows r_{n-1} S_n must be <= 256 */
     RBKI_FLAG_ADAPTIVE_Q = 32u     /* adaptive Krylov depth: q is the bound; after block j the
                                       mode's fit F_j = 1 - sqrt(|X|^2 - sum of its R_n Ritz
                                       values)/|X| is evaluated, and the mode stops at the first

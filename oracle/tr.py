@@ -28,7 +28,7 @@ from typing import List, Sequence
 
 import numpy as np
 
-from .rbki import rbki_tucker
+from .rbki import rbki_tucker, sign_fix
 from .tensor import tr
 
 
@@ -91,6 +91,8 @@ def tr_svd(g: np.ndarray, ranks: Sequence[int]):
       step n:  truncated SVD of rank r_n of C ((r_{n-1} S_n) x ...); core n = U as
                (r_{n-1}, S_n, r_n); C <- Sigma V^T read as (r_n S_{n+1}) x ...;
       last:    core N-1 = C as (r_{N-2}, S_N, r_{N-1}).
+    Each U is sign-normalised (largest-|.| entry of every column positive, reading c5) before
+    use: the split of step 0 mixes bond indices, so the result depends on the signs.
     Returns (cores, squared truncation error of every step)."""
     g = np.asarray(g, dtype=np.float64)
     n = g.ndim
@@ -100,9 +102,10 @@ def tr_svd(g: np.ndarray, ranks: Sequence[int]):
     c = g.reshape(g.shape[0], -1)
     for k in range(n - 1):
         rk = r[n - 1] * r[0] if k == 0 else r[k]
-        u, sv, vt = np.linalg.svd(c, full_matrices=False)
+        u, sv, _ = np.linalg.svd(c, full_matrices=False)
         errs.append(float(np.sum(sv[rk:] ** 2)))
-        u, w = u[:, :rk], sv[:rk, None] * vt[:rk]
+        u = sign_fix(u[:, :rk])
+        w = u.T @ c                                                        # Sigma V^T, signs of u
         if k == 0:
             cores.append(u.reshape(g.shape[0], r[n - 1], r[0]).transpose(1, 0, 2).copy())
             w = w.reshape(r[n - 1], r[0], -1).transpose(1, 2, 0)          # (b, rest, a)

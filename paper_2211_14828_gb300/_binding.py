@@ -18,7 +18,8 @@ OK, PENDING, W_DEFLATED = 0, 1, 2
 E_INVAL, E_NOMEM, E_CUDA, E_UNSUPPORTED, E_TIMEOUT, E_BUSY, E_CANCELLED, E_NOTFOUND = range(-1, -9, -1)
 F64, F32, BF16, F16 = 0, 1, 2, 3
 PREC_FP64, PREC_BF16, PREC_FP16 = 0, 1, 2
-FLAG_HOST_IO, FLAG_SPLIT, FLAG_SERIAL_MODES, FLAG_SEQUENTIAL, FLAG_POWER, FLAG_ADAPTIVE_Q = 1, 2, 4, 8, 16, 32
+FLAG_HOST_IO, FLAG_SPLIT, FLAG_SERIAL_MODES, FLAG_SEQUENTIAL, FLAG_POWER, FLAG_ADAPTIVE_Q, FLAG_TR_SVD = \
+    1, 2, 4, 8, 16, 32, 64
 
 
 class rbki_tensor(C.Structure):
@@ -258,7 +259,8 @@ def rbki_divide_and_conquer(x, mode, parts, ranks, p, q, seed, prec="bf16", flag
 
 def rbki_htr(x, tucker_ranks, p, q, seed, tr_ranks, tr_init, maxit=20, tol=1e-3, prec="fp64", flags=0,
              workspace=None, tucker_out=None, stream=None, omega=0.0):
-    """rBKI-TK-TR (Algorithm 3).  tr_init: list of float64 CUDA tensors (r_{n-1}, R_n, r_n).
+    """rBKI-TK-TR (Algorithm 3).  tr_init: list of float64 CUDA tensors (r_{n-1}, R_n, r_n), or
+    None with FLAG_TR_SVD (TR-SVD instead of TR-ALS).
     Returns dict(cores=[(r_{n-1}, I_n, r_n)], fits=(maxit,) NaN after the stop, tucker=...)."""
     torch = _torch()
     N = x.dim()
@@ -268,8 +270,8 @@ def rbki_htr(x, tucker_ranks, p, q, seed, tr_ranks, tr_init, maxit=20, tol=1e-3,
     check(lib().rbki_htr_workspace(C.byref(t), C.byref(prm), trr, C.byref(need)), "rbki_htr_workspace")
     if workspace is None or workspace.numel() < need.value:
         workspace = torch.empty(int(need.value), dtype=torch.uint8, device=x.device)
-    init = [z.contiguous() for z in tr_init]
-    init_p = (C.c_void_p * 8)(*[z.data_ptr() for z in init])
+    init = [z.contiguous() for z in tr_init] if tr_init is not None else []
+    init_p = (C.c_void_p * 8)(*[z.data_ptr() for z in init]) if tr_init is not None else None
     cores = [torch.zeros((int(tr_ranks[(n + N - 1) % N]), int(x.shape[n]), int(tr_ranks[n])),
                          dtype=torch.float64, device=x.device) for n in range(N)]
     cores_p = (C.c_void_p * 8)(*[z.data_ptr() for z in cores])

@@ -1017,7 +1017,7 @@ static rbki_status htr_layout(const Plan& pl, const rbki_params* tk, const int32
     for (int n = 0; n < pl.N; ++n)
         L.trc[n] = take((size_t)tr[(n + pl.N - 1) % pl.N] * tk->ranks[n] * tr[n] * 8);
     L.table = take(RBKI_MAX_ORDER * sizeof(double*));
-    L.trws = take(tr_workspace_doubles_for(pl.N, cdims, tr) * 8);
+    L.trws = take(std::max(tr_workspace_doubles_for(pl.N, cdims, tr), trsvd_workspace_doubles(pl.N, cdims, tr)) * 8);
     L.total = off + 256;
     return RBKI_OK;
 }
@@ -1052,9 +1052,11 @@ rbki_status rbki_htr(const rbki_tensor* X, const rbki_params* tk, const int32_t*
                      void* stream) {
     Plan pl;
     RBKI_TRY(htr_validate(X, tk, tr_ranks, pl));
-    if (!tr_init || !tr_cores || tr_maxit < 1) return set_error(RBKI_E_INVAL, "tr_init / tr_cores / tr_maxit");
+    const bool trsvd = (tk->flags & RBKI_FLAG_TR_SVD) != 0;
+    if ((!trsvd && !tr_init) || !tr_cores || tr_maxit < 1)
+        return set_error(RBKI_E_INVAL, "tr_init / tr_cores / tr_maxit");
     for (int n = 0; n < pl.N; ++n)
-        if (!tr_init[n] || !tr_cores[n]) return set_error(RBKI_E_INVAL, "NULL TR core pointer");
+        if ((!trsvd && !tr_init[n]) || !tr_cores[n]) return set_error(RBKI_E_INVAL, "NULL TR core pointer");
     HtrLayout L;
     RBKI_TRY(htr_layout(pl, tk, tr_ranks, L));
     if (!workspace || workspace_bytes < L.total) return set_error(RBKI_E_NOMEM, "workspace too small");
@@ -1077,6 +1079,20 @@ rbki_status rbki_htr(const rbki_tensor* X, const rbki_params* tk, const int32_t*
     // working TR cores (initial values copied in) and their pointer table
     double* cores[RBKI_MAX_ORDER];
     int64_t cdims[RBKI_MAX_ORDER];
+    if (trsvd) {
+        // TR-SVD instead of TR-ALS: no initial cores, no host synchronisation; fits[0] is the
+        // fit of the ring to G, the rest NaN
+        for (int n = 0; n < pl.N; ++n) {
+            cores[n] = reinterpret_cast<double*>(base + L.trc[n]);
+            cdims[n] = tk->ranks[n];
+        }
+        RBKI_TRY(tr_svd_cuda(pl.N, cdims, tr_ranks, o.core, cores, reinterpret_cast<double*>(base + L.trws), fits,
+                             tr_maxit, st));
+        for (int n = 0; n < pl.N; ++n)
+            RBKI_TRY(tr_contract_cuda(cores[n], o.factors[n], tr_ranks[(n + pl.N - 1) % pl.N], tk->ranks[n],
+                                      tr_ranks[n], pl.dims[n], tr_cores[n], st));
+        return RBKI_OK;
+    }
     for (int n = 0; n < pl.N; ++n) {
         cores[n] = reinterpret_cast<double*>(base + L.trc[n]);
         cdims[n] = tk->ranks[n];

@@ -389,6 +389,133 @@ rbki_status tr_run(int N, const int64_t* core_dims, const int32_t* ranks, const 
     return tr_als_cuda(p, G, g_norm2, cores_dev, cores_table_dev, maxit, tol, ws, fits_host, sweeps, st);
 }
 
+// ---- TR-SVD (the alternative step 3 of Algorithm 3; Zhao et al. 2016) ----------------
+// Step n takes the truncated SVD of C_n ((r_{n-1} S_n) x rest; S_1 x rest for n = 0) from
+// the Gram matrix C_n C_n^T: U = its leading r eigenvectors (the FP64-refined eigensolver),
+// sign-normalised,
+// the remainder U^T C_n = Sigma V^T by a TTM, and the step's squared truncation error
+// trace(C C^T) - sum of the r eigenvalues.  Step 0 splits the rank product r_{N-1} r_0:
+// core 0 [a][i][b] = U[i][a r_0 + b], and the remainder is reordered (a, b, rest) ->
+// (b, rest, a).  The last core is the remaining C_{N-1}.
+namespace {
+
+// core0[a][i][b] = U[i][a * r0 + b]
+__global__ void k_trsvd_core0(const double* __restrict__ U, int64_t S, int ra, int r0, double* __restrict__ Z) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t tot = (int64_t)ra * S * r0;
+    if (e >= tot) return;
+    const int b = (int)(e % r0);
+    const int64_t i = (e / r0) % S;
+    const int a = (int)(e / (r0 * S));
+    Z[e] = U[i * ((int64_t)ra * r0) + (int64_t)a * r0 + b];
+}
+
+// out[b][c][a] = W[a * r0 + b][c]  (W: (ra r0) x ncol)
+__global__ void k_trsvd_reorder(const double* __restrict__ W, int ra, int r0, int64_t ncol, double* __restrict__ out) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t tot = (int64_t)ra * r0 * ncol;
+    if (e >= tot) return;
+    const int a = (int)(e % ra);
+    const int64_t c = (e / ra) % ncol;
+    const int b = (int)(e / (ra * ncol));
+    out[e] = W[((int64_t)a * r0 + b) * ncol + c];
+}
+
+// err2 += trace(Gram) - sum_{k<r} w[k]; step 0 also records |G|^2 = trace
+__global__ void k_trsvd_err(const double* __restrict__ gram, int m, const double* __restrict__ w, int r,
+                            double* __restrict__ acc, int first) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double tr = 0.0, top = 0.0;
+    for (int i = 0; i < m; ++i) tr += gram[(int64_t)i * m + i];
+    for (int k = 0; k < r; ++k) top += w[k];
+    if (first) {
+        acc[0] = tr;
+        acc[1] = 0.0;
+    }
+    acc[1] += tr - top;
+}
+
+__global__ void k_trsvd_fit(const double* __restrict__ acc, double* __restrict__ fits, int nfits) {
+    const int i = threadIdx.x;
+    if (i >= nfits) return;
+    if (i == 0) {
+        const double g2 = acc[0], e2 = acc[1] > 0.0 ? acc[1] : 0.0;
+        fits[0] = g2 > 0.0 ? 1.0 - sqrt(e2 / g2) : 1.0;
+    } else {
+        fits[i] = __longlong_as_double(0x7ff8000000000000LL);
+    }
+}
+
+constexpr int TRSVD_SPLIT = 8;   // split-K partials of the Gram contraction
+
+}  // namespace
+
+size_t trsvd_workspace_doubles(int N, const int64_t* S, const int32_t* r) {
+    int64_t numel = 1;
+    for (int n = 0; n < N; ++n) numel *= S[n];
+    return 2 * (size_t)rup(numel, 32) + 256 * 256 + 256 + 256 * 256 + syev_scratch_doubles(256) +
+           (size_t)TRSVD_SPLIT * 256 * 256 + 64;
+}
+
+rbki_status tr_svd_cuda(int N, const int64_t* S, const int32_t* r, const double* G, double* const* cores,
+                        double* ws, double* fits, int nfits, cudaStream_t st) {
+    if (N < 2) return set_error(RBKI_E_INVAL, "TR-SVD needs order >= 2");
+    int64_t numel = 1;
+    for (int n = 0; n < N; ++n) numel *= S[n];
+    double* buf[2] = {ws, ws + rup(numel, 32)};
+    double* gram = buf[1] + rup(numel, 32);
+    double* w = gram + 256 * 256;
+    double* V = w + 256;
+    double* eig_ws = V + 256 * 256;
+    double* part = eig_ws + syev_scratch_doubles(256);
+    double* acc = part + (size_t)TRSVD_SPLIT * 256 * 256;
+    const double* C = G;
+    int64_t rows = S[0], cols = numel / S[0];
+    for (int n = 0; n + 1 < N; ++n) {
+        const int rk = n == 0 ? r[N - 1] * r[0] : r[n];
+        if (rows > 256) return set_error(RBKI_E_UNSUPPORTED, "TR-SVD: unfolding rows > 256");
+        if (rk > rows || rk > cols) return set_error(RBKI_E_INVAL, "TR-SVD: rank exceeds the unfolding");
+        const View v{C, RBKI_F64, 1, rows, cols};
+        const int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(TRSVD_SPLIT, cdiv(cols, 256)));
+        RBKI_TRY(contract_cuda(v, C, RBKI_F64, (int)rows, false, part, nsplit, gram, rows, nullptr, 0, st));
+        RBKI_TRY(symmetrize_cuda(gram, (int)rows, st));
+        RBKI_TRY(syev_top_cuda(gram, (int)rows, rk, w, V, eig_ws, st));
+        k_trsvd_err<<<1, 32, 0, st>>>(gram, (int)rows, w, rk, acc, n == 0);
+        RBKI_LAUNCH_CHECK("k_trsvd_err");
+        // U = the leading eigenvectors, each column's largest-|.| entry made positive (the
+        // split of step 0 mixes bond indices, so the result depends on the signs); the Gram
+        // matrix is no longer needed, U takes its place
+        double* U = gram;
+        RBKI_TRY(form_factor_cuda(nullptr, 0, rows, V, (int)rows, rk, rk, U, st));
+        double* W = C == buf[0] ? buf[1] : buf[0];                     // never the buffer C is in
+        RBKI_TRY(ttm_cuda(v, U, rk, rk, W, RBKI_F64, false, st));       // W = U^T C, rk x cols
+        if (n == 0) {
+            const int64_t tot = (int64_t)r[N - 1] * S[0] * r[0];
+            k_trsvd_core0<<<(unsigned)cdiv(tot, 256), 256, 0, st>>>(U, S[0], r[N - 1], r[0], cores[0]);
+            RBKI_LAUNCH_CHECK("k_trsvd_core0");
+            double* R = buf[1];                                          // W is buf[0] here
+            k_trsvd_reorder<<<(unsigned)cdiv((int64_t)rk * cols, 256), 256, 0, st>>>(W, r[N - 1], r[0], cols, R);
+            RBKI_LAUNCH_CHECK("k_trsvd_reorder");
+            C = R;
+            rows = (int64_t)r[0] * S[1];
+            cols = (int64_t)cols * r[N - 1] / S[1];
+        } else {
+            RBKI_CUDA_TRY(cudaMemcpyAsync(cores[n], U, (size_t)rows * rk * sizeof(double), cudaMemcpyDeviceToDevice,
+                                          st));
+            C = W;
+            rows = (int64_t)r[n] * S[n + 1];
+            cols = (int64_t)rk * cols / rows;
+        }
+    }
+    RBKI_CUDA_TRY(cudaMemcpyAsync(cores[N - 1], C, (size_t)r[N - 2] * S[N - 1] * r[N - 1] * sizeof(double),
+                                  cudaMemcpyDeviceToDevice, st));
+    if (fits && nfits > 0) {
+        k_trsvd_fit<<<1, 1024, 0, st>>>(acc, fits, nfits > 1024 ? 1024 : nfits);
+        RBKI_LAUNCH_CHECK("k_trsvd_fit");
+    }
+    return RBKI_OK;
+}
+
 rbki_status tr_contract_cuda(const double* Z, const double* U, int r0, int64_t Rn, int r1, int64_t In, double* X,
                              cudaStream_t st) {
     const int64_t tot = (int64_t)r0 * In * r1;

@@ -77,6 +77,10 @@ rbki_status tr_run(int N, const int64_t* core_dims, const int32_t* ranks, const 
                    double* ws, double* fits_host, int* sweeps, cudaStream_t st);
 rbki_status tr_contract_cuda(const double* Z, const double* U, int r0, int64_t Rn, int r1, int64_t In, double* X,
                              cudaStream_t st);
+size_t trsvd_workspace_doubles(int N, const int64_t* S, const int32_t* r);
+rbki_status tr_svd_cuda(int N, const int64_t* S, const int32_t* r, const double* G, double* const* cores,
+                        double* ws, double* fits, int nfits, cudaStream_t st);
+rbki_status symmetrize_cuda(double* Z, int n, cudaStream_t st);
 
 size_t dtype_size(int dt);
 rbki_status validate_tensor(const rbki_tensor* X);

@@ -108,3 +108,28 @@ def test_htr_rejects_bad_ranks(rb):
     init = [torch.zeros((9, 4, 9), dtype=torch.float64, device="cuda") for _ in range(3)]
     with pytest.raises(rb.RbkiError):
         rb.rbki_htr(x, (4, 4, 4), 1, 1, 0, (9, 9, 9), init)
+
+
+@pytest.mark.parametrize("case", [
+    # dims, tucker ranks, p, q, TR ranks
+    ((24, 24, 24, 24), (6, 6, 6, 6), 2, 1, (2, 3, 3, 2)),
+    ((20, 25, 30), (8, 6, 7), 2, 1, (2, 3, 4)),
+    ((16,) * 6, (10,) * 6, 5, 2, (3, 3, 3, 3, 3, 3)),
+])
+def test_htr_tr_svd_matches_oracle(rb, case):
+    """TR-SVD instead of TR-ALS (RBKI_FLAG_TR_SVD): the ring's fit and its full
+    reconstruction against the oracle's TR-SVD of the oracle's Tucker core (the cores
+    themselves are fixed only up to rotations of each bond)."""
+    dims, tk, p, q, trr = case
+    x = _tr_tensor(dims, max(trr), 15.0, seed=sum(dims) + 1)
+    want = otr.rbki_tk_tr(x, tk, p, q, 42, None, tr_ranks=trr)
+    got = rb.rbki_htr(torch.from_numpy(x).cuda(), tk, p, q, 42, trr, None, maxit=4, prec="fp64",
+                      flags=rb.FLAG_TR_SVD)
+    torch.cuda.synchronize()
+    fits = got["fits"].cpu().numpy()
+    assert abs(fits[0] - want["fits"][0]) <= 1e-9 and np.all(np.isnan(fits[1:]))
+    cores = [c.cpu().numpy() for c in got["cores"]]
+    for c, w in zip(cores, want["cores"]):
+        assert c.shape == w.shape
+    a, b = tr_full(cores), tr_full(want["cores"])
+    assert np.linalg.norm(a - b) <= 1e-8 * np.linalg.norm(b)
