@@ -103,14 +103,15 @@ __device__ __forceinline__ void omega_pair_f64(uint64_t seed, uint32_t mode, uin
     z1 = rho * s;
 }
 
-// Single-precision evaluation of the same Gaussian (used to feed BF16/FP16 operands).
+// Single-precision evaluation of the same Gaussian (used to feed BF16/FP16 operands): the
+// two 53-bit uniforms are formed in FP32 directly (high word scaled by 2^-27 plus the low
+// word by 2^-53), so the image generation never touches the FP64 pipe.
 __device__ __forceinline__ void omega_pair_f32(uint64_t seed, uint32_t mode, uint64_t col,
                                                uint32_t pair, float& z0, float& z1) {
     U4 c{pair, mode, (uint32_t)(col & 0xffffffffu), (uint32_t)(col >> 32)};
     U4 r = philox4x32_10(c, (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32));
-    double u1d = ((double)(r.x >> 5) * 67108864.0 + (double)(r.y >> 6) + 1.0) * 0x1p-53;
-    double u2d = ((double)(r.z >> 5) * 67108864.0 + (double)(r.w >> 6)) * 0x1p-53;
-    float u1 = (float)u1d, u2 = (float)u2d;
+    const float u1 = fmaf((float)(r.x >> 5), 0x1p-27f, (float)((r.y >> 6) + 1u) * 0x1p-53f);
+    const float u2 = fmaf((float)(r.z >> 5), 0x1p-27f, (float)(r.w >> 6) * 0x1p-53f);
     float rho = sqrtf(-2.0f * logf(u1));
     float s, co;
     sincospif(2.0f * u2, &s, &co);

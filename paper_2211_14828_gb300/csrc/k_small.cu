@@ -58,8 +58,16 @@ __global__ void k_atb_reduce(const double* __restrict__ part, int nchunk, int ma
                              double* __restrict__ out, int64_t ldo) {
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= ma * mb) return;
+    // four independent loads in flight per step; fixed summation order
+    const int64_t stride = (int64_t)ma * mb;
     double acc = 0.0;
-    for (int c = 0; c < nchunk; ++c) acc += part[(int64_t)c * ma * mb + e];
+    int c = 0;
+    for (; c + 3 < nchunk; c += 4) {
+        const double v0 = part[c * stride + e], v1 = part[(c + 1) * stride + e];
+        const double v2 = part[(c + 2) * stride + e], v3 = part[(c + 3) * stride + e];
+        acc += (v0 + v1) + (v2 + v3);
+    }
+    for (; c < nchunk; ++c) acc += part[c * stride + e];
     out[(int64_t)(e / mb) * ldo + e % mb] = acc;
 }
 
@@ -399,8 +407,15 @@ __global__ void k_gemm_reduce(const double* __restrict__ part, int nchunk, int M
                               int64_t ldc, double beta) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= M * N) return;
+    const int64_t stride = (int64_t)M * N;
     double acc = 0.0;
-    for (int c = 0; c < nchunk; ++c) acc += part[(int64_t)c * M * N + e];
+    int c = 0;
+    for (; c + 3 < nchunk; c += 4) {
+        const double v0 = part[c * stride + e], v1 = part[(c + 1) * stride + e];
+        const double v2 = part[(c + 2) * stride + e], v3 = part[(c + 3) * stride + e];
+        acc += (v0 + v1) + (v2 + v3);
+    }
+    for (; c < nchunk; ++c) acc += part[c * stride + e];
     double* cp = C + (int64_t)(e / N) * ldc + e % N;
     *cp = beta != 0.0 ? acc + beta * *cp : acc;
 }

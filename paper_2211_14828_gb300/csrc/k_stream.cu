@@ -181,8 +181,15 @@ __global__ void k_reduce_parts(const double* __restrict__ part, int nsplit, int6
                                int64_t ld2) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= I * S) return;
+    const int64_t stride = I * S;
     double acc = 0.0;
-    for (int k = 0; k < nsplit; ++k) acc += part[(int64_t)k * I * S + e];
+    int k = 0;
+    for (; k + 3 < nsplit; k += 4) {
+        const double v0 = part[k * stride + e], v1 = part[(k + 1) * stride + e];
+        const double v2 = part[(k + 2) * stride + e], v3 = part[(k + 3) * stride + e];
+        acc += (v0 + v1) + (v2 + v3);
+    }
+    for (; k < nsplit; ++k) acc += part[k * stride + e];
     int64_t i = e / S, s = e % S;
     out[i * ld + s] = acc;
     if (out2) out2[i * ld2 + s] = acc;

@@ -426,54 +426,65 @@ __global__ void k_skinny_image(const double* __restrict__ M, int64_t ldm, int64_
 
 // Per-tile Omega images for SKETCH: tile t covers 128 unfolding columns; element (c, n) of
 // tile t at t*128*N + (n/8)*1024 + c*8 + n%8 (elements).  Columns outside the tensor are 0.
-__global__ void k_omega_images(uint64_t seed, int mode, int64_t A, int64_t C, int ifast, int64_t ctiles,
-                               int64_t tiles, int S, int N, int split, int fp16, uint16_t* __restrict__ img) {
-    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // (tile, c, pair)
-    const int npair = (S + 1) / 2;
-    if (e >= tiles * 128 * npair) return;
-    int pair = (int)(e % npair);
-    int64_t tc_ = e / npair;
-    int c = (int)(tc_ % 128);
-    int64_t t = tc_ / 128;
+__global__ void __launch_bounds__(256) k_omega_images(uint64_t seed, int mode, int64_t A, int64_t C, int ifast,
+                                                      int64_t ctiles, int64_t tiles, int S, int N, int split,
+                                                      int fp16, uint16_t* __restrict__ img) {
+    // one thread per (tile, column c, group of 8 image columns): the group is written as one
+    // 16-byte vector, zeros included, so the image needs no clearing beforehand
+    const int G = N / 8;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= tiles * 128 * G) return;
+    const int g = (int)(e % G);
+    const int64_t tc_ = e / G;
+    const int c = (int)(tc_ & 127);
+    const int64_t t = tc_ >> 7;
     int64_t col;
     bool valid;
     if (!ifast) {
-        int64_t a = t / ctiles, cc = (t % ctiles) * 128 + c;
+        const int64_t a = t / ctiles, cc = (t % ctiles) * 128 + c;
         valid = cc < C;
         col = a * C + cc;
     } else {
-        int64_t a = t * 128 + c;
+        const int64_t a = t * 128 + c;
         valid = a < A;
         col = a;
     }
+    float vals[8];
+    int have_pair = -1;
     float z[2] = {0.f, 0.f};
-    if (valid) omega_pair_f32(seed, (uint32_t)mode, (uint64_t)col, (uint32_t)pair, z[0], z[1]);
-    uint16_t* base = img + (size_t)t * 128 * N;
-    for (int u = 0; u < 2; ++u) {
-        int s = 2 * pair + u;
-        if (s >= S) break;
-        const float x = z[u];
-        float hi = fp16 ? __half2float(__float2half_rn(x)) : __bfloat162float(__float2bfloat16_rn(x));
-        float lo = x - hi;
-        int ns[2] = {s, split ? S + s : -1};
-        float vs[2] = {hi, lo};
-        for (int w = 0; w < 2; ++w) {
-            int n = ns[w];
-            if (n < 0) continue;
-            uint16_t bits;
-            if (fp16) { __half h = __float2half_rn(vs[w]); bits = *reinterpret_cast<uint16_t*>(&h); }
-            else { __nv_bfloat16 h = __float2bfloat16_rn(vs[w]); bits = *reinterpret_cast<uint16_t*>(&h); }
-            base[(n / 8) * 1024 + c * 8 + n % 8] = bits;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const int n = 8 * g + u;
+        const bool lo = split && n >= S;
+        const int s = lo ? n - S : n;
+        float v = 0.f;
+        if (valid && s < S && (!lo || n < 2 * S)) {
+            if (s / 2 != have_pair) {
+                omega_pair_f32(seed, (uint32_t)mode, (uint64_t)col, (uint32_t)(s / 2), z[0], z[1]);
+                have_pair = s / 2;
+            }
+            const float x = z[s & 1];
+            const float hi = fp16 ? __half2float(__float2half_rn(x)) : __bfloat162float(__float2bfloat16_rn(x));
+            v = lo ? x - hi : hi;
         }
+        vals[u] = v;
     }
+    uint4 w;
+    w.x = pack2(vals[0], vals[1], fp16 != 0);
+    w.y = pack2(vals[2], vals[3], fp16 != 0);
+    w.z = pack2(vals[4], vals[5], fp16 != 0);
+    w.w = pack2(vals[6], vals[7], fp16 != 0);
+    *reinterpret_cast<uint4*>(img + (size_t)t * 128 * N + (size_t)g * 1024 + c * 8) = w;
 }
 
-// out[i*ld + s] = sum_b (part[b][i][s] + split * part[b][i][Sh + s]), FP64, fixed order:
-// 32 outputs per CTA; warp w sums partials b = w, w+8, ...; warps combined in order.
-__global__ void __launch_bounds__(256) k_reduce_tc(const float* __restrict__ part, int nb, int64_t I, int N, int Sh,
-                                                   int split, double* __restrict__ out, int64_t ld,
-                                                   double* __restrict__ out2, int64_t ld2) {
-    __shared__ double acc_sh[8][33];
+// out[i*ld + s] = sum over the nb CTA partials (+ the lo half when split), FP64.  A CTA
+// owns 32 outputs; its 8 warps take the partials b = w, w + 8, ..., four at a time with
+// independent loads, and the 8 warp sums are added in a fixed order (deterministic).
+constexpr int RED_WARPS = 8;
+__global__ void __launch_bounds__(32 * RED_WARPS) k_reduce_tc(const float* __restrict__ part, int nb, int64_t I,
+                                                             int N, int Sh, int split, double* __restrict__ out,
+                                                             int64_t ld, double* __restrict__ out2, int64_t ld2) {
+    __shared__ double acc_sh[RED_WARPS][33];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t e = (int64_t)blockIdx.x * 32 + lane;
     const int64_t tot = I * Sh;
@@ -481,17 +492,30 @@ __global__ void __launch_bounds__(256) k_reduce_tc(const float* __restrict__ par
     if (e < tot) {
         const int64_t i = e / Sh;
         const int s = (int)(e % Sh);
-        for (int b = w; b < nb; b += 8) {
-            const float* pb = part + ((size_t)b * I + i) * N;
-            acc += (double)pb[s];
-            if (split) acc += (double)pb[Sh + s];
+        const float* p0 = part + i * N + s;
+        const size_t stride = (size_t)I * N;
+        int b = w;
+        for (; b + 3 * RED_WARPS < nb; b += 4 * RED_WARPS) {
+            float v[4], u[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) v[t] = p0[(size_t)(b + t * RED_WARPS) * stride];
+            if (split) {
+#pragma unroll
+                for (int t = 0; t < 4; ++t) u[t] = p0[(size_t)(b + t * RED_WARPS) * stride + Sh];
+            }
+#pragma unroll
+            for (int t = 0; t < 4; ++t) acc += (double)v[t] + (double)u[t];
+        }
+        for (; b < nb; b += RED_WARPS) {
+            acc += (double)p0[(size_t)b * stride];
+            if (split) acc += (double)p0[(size_t)b * stride + Sh];
         }
     }
     acc_sh[w][lane] = acc;
     __syncthreads();
     if (w == 0 && e < tot) {
         double t = 0.0;
-        for (int k = 0; k < 8; ++k) t += acc_sh[k][lane];
+        for (int k = 0; k < RED_WARPS; ++k) t += acc_sh[k][lane];
         const int64_t i = e / Sh;
         const int s = (int)(e % Sh);
         out[i * ld + s] = t;
@@ -571,8 +595,7 @@ rbki_status omega_images(uint64_t seed, int mode, const View& v, int S, int N, b
     const bool ifast = v.C == 1;
     int64_t ctiles = ifast ? 1 : cdiv(v.C, 128);
     int64_t tiles = num_tiles(v);
-    RBKI_CUDA_TRY(cudaMemsetAsync(img, 0, image_bytes_omega(v, N), st));
-    int64_t tot = tiles * 128 * ((S + 1) / 2);
+    int64_t tot = tiles * 128 * (N / 8);
     k_omega_images<<<(unsigned)cdiv(tot, 256), 256, 0, st>>>(seed, mode, v.A, v.C, ifast ? 1 : 0, ctiles, tiles, S,
                                                              N, split ? 1 : 0, v.dtype == RBKI_F16 ? 1 : 0,
                                                              (uint16_t*)img);
@@ -652,7 +675,8 @@ rbki_status stream_tc(int mode, const View& v, int N, int Sh, bool split, const 
 rbki_status reduce_parts(const float* part, int nb, int64_t I, int N, int Sh, bool split, double* out, int64_t ld,
                          double* out2, int64_t ld2, cudaStream_t st) {
     int64_t tot = I * Sh;
-    k_reduce_tc<<<(unsigned)cdiv(tot, 32), 256, 0, st>>>(part, nb, I, N, Sh, split ? 1 : 0, out, ld, out2, ld2);
+    k_reduce_tc<<<(unsigned)cdiv(tot, 32), 32 * RED_WARPS, 0, st>>>(part, nb, I, N, Sh, split ? 1 : 0, out, ld, out2,
+                                                                  ld2);
     RBKI_LAUNCH_CHECK("k_reduce_tc");
     return RBKI_OK;
 }

@@ -7,6 +7,7 @@
 * the mixed path: error within 1% of the oracle's sampled decomposition;
 * sampling composes with the sequential reading, at 512^3 too."""
 import numpy as np
+from parity_bars import err_matches
 import pytest
 
 import synth
@@ -60,7 +61,7 @@ def _check_fp64(rb, x, ranks, p, q, seed, omega, sequential=False):
         np.testing.assert_allclose(out["eigvals"][n].cpu().numpy(), ref["eigvals"][n], rtol=1e-11,
                                    atol=1e-12 * ref["eigvals"][n][0])
     e_ref = np.sqrt(max(ref["x_norm2"] - ref["core_norm2"], 0.0))
-    assert abs(_err(out["norms"]) - e_ref) <= 1e-12 * e_ref + 1e-13 * np.sqrt(ref["x_norm2"])
+    assert err_matches(_err(out["norms"]), e_ref, ref["x_norm2"])
     return out, ref
 
 

@@ -4,6 +4,7 @@ requests refused at submission; and parity of served results with the oracle."""
 import time
 
 import numpy as np
+from parity_bars import err_matches
 import pytest
 
 import synth
@@ -96,7 +97,7 @@ def test_served_results_match_the_oracle(rb):
         if prec == "fp64":
             for k, u in enumerate(out["factors"]):
                 assert max_principal_sine(ref["factors"][k], u.cpu().numpy()) <= 1e-10
-            assert abs(e - e_ref) <= 1e-12 * e_ref + 1e-13 * np.sqrt(ref["x_norm2"])
+            assert err_matches(e, e_ref, ref["x_norm2"])
         else:
             assert abs(e - e_ref) <= 0.01 * e_ref
 

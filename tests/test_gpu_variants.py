@@ -7,6 +7,7 @@ FP64 bar: principal-angle sines <= 1e-10, Ritz values to 1e-11, the reconstructi
 the same fit formula; the cases are checked not to be borderline).  Mixed bar: the error
 within 1% of the oracle's, a depth within the bound."""
 import numpy as np
+from parity_bars import err_matches
 import pytest
 
 import synth
@@ -50,7 +51,7 @@ def _check(rb, x, ranks, p, q, seed, flags, ref, sequential=False):
         np.testing.assert_allclose(out["eigvals"][n].cpu().numpy(), ref["eigvals"][n], rtol=1e-11,
                                    atol=1e-12 * ref["eigvals"][n][0])
     e_ref = np.sqrt(max(ref["x_norm2"] - ref["core_norm2"], 0.0))
-    assert abs(_err(out["norms"]) - e_ref) <= 1e-12 * e_ref + 1e-13 * np.sqrt(ref["x_norm2"])
+    assert err_matches(_err(out["norms"]), e_ref, ref["x_norm2"])
     return out
 
 
@@ -117,7 +118,7 @@ def test_adaptive_q_mixed_and_host_io(rb):
     host = rb.rbki_tucker(torch.from_numpy(wl.x).pin_memory(), wl.ranks, wl.p, wl.q, wl.seed, prec="fp64",
                           flags=rb.FLAG_ADAPTIVE_Q | rb.FLAG_HOST_IO, q_tol=tol)
     assert list(host["q_used"].numpy()) == ref["q_used"]
-    assert abs(_err(host["norms"]) - e_ref) <= 1e-12 * e_ref + 1e-13 * np.sqrt(ref["x_norm2"])
+    assert err_matches(_err(host["norms"]), e_ref, ref["x_norm2"])
 
 
 def test_variant_flag_validation(rb):
