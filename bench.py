@@ -79,7 +79,7 @@ def make_workload(name, mc, size=0):
 # ncu capture summarised in profiles/k_stream_tc_krylov_448cube_bf16.md (183.4 MB for
 # 448^3 elements); traffic grows in proportion to the elements streamed.  Set to None when
 # k_stream_tc changes until a new capture is taken.
-KRYLOV_TC_DRAM_BYTES_PER_ELEM = (179.947776e6 + 3.468032e6) / 448 ** 3
+KRYLOV_TC_DRAM_BYTES_PER_ELEM = (179.941376e6 + 3.524096e6) / 448 ** 3
 
 
 def plan_passes(dims, ranks, p, q):
@@ -380,7 +380,9 @@ def run_ours(args):
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
+    th0 = time.perf_counter()
     run_steps(args.steps)
+    host_ms = (time.perf_counter() - th0) * 1e3 / args.steps      # host time to enqueue a step
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier(world)
@@ -499,6 +501,7 @@ def run_ours(args):
                                    + (f", adaptive q (q_tol={args.q_tol}, depths "
                                       f"{out['q_used'].cpu().numpy().tolist()})" if args.q_tol is not None else ""),
                        "inflight": K, "single_decomposition_ms": round(single_ms, 4),
+                       "host_enqueue_ms_per_step": round(host_ms, 4),
                        "passes_per_step": passes, "krylov_steps_per_step": krylov_steps,
                        "bytes_per_step": step_bytes, "l2": "inputs larger than L2 (no flush)",
                        "parallelism": f"replicas x{world}"},
