@@ -76,6 +76,11 @@ enum {
                                       Q_{j+1} = orth(X X^T Q_j) replaces the block instead of
                                       extending it; the basis is Q_q alone (width S_n); a mode
                                       takes the Gram path when S_n >= I_n */
+    RBKI_FLAG_ASYNC = 128u,        /* with RBKI_FLAG_HOST_IO: return without waiting for the
+                                      stream; the host outputs are valid once `stream` has
+                                      completed, and X and the outputs must be pinned host memory
+                                      (calls on different streams then overlap their copies with
+                                      each other's computation) */
     RBKI_FLAG_TR_SVD = 64u,        /* rbki_htr: TR-SVD (Zhao et al. 2016) on the core instead of
                                       TR-ALS (the alternative Algorithm 3 step 3 names): fixed
                                       ranks, sequential truncated SVDs, the first splitting the

@@ -18,8 +18,8 @@ OK, PENDING, W_DEFLATED = 0, 1, 2
 E_INVAL, E_NOMEM, E_CUDA, E_UNSUPPORTED, E_TIMEOUT, E_BUSY, E_CANCELLED, E_NOTFOUND = range(-1, -9, -1)
 F64, F32, BF16, F16 = 0, 1, 2, 3
 PREC_FP64, PREC_BF16, PREC_FP16 = 0, 1, 2
-FLAG_HOST_IO, FLAG_SPLIT, FLAG_SERIAL_MODES, FLAG_SEQUENTIAL, FLAG_POWER, FLAG_ADAPTIVE_Q, FLAG_TR_SVD = \
-    1, 2, 4, 8, 16, 32, 64
+FLAG_HOST_IO, FLAG_SPLIT, FLAG_SERIAL_MODES, FLAG_SEQUENTIAL, FLAG_POWER, FLAG_ADAPTIVE_Q, FLAG_TR_SVD, FLAG_ASYNC = \
+    1, 2, 4, 8, 16, 32, 64, 128
 
 
 class rbki_tensor(C.Structure):

@@ -1,6 +1,7 @@
 // RBKI_FLAG_HOST_IO: end-to-end call with X and the outputs in host memory.  The input is
 // copied into the tail of the caller's workspace, the decomposition runs on the device and
-// the outputs are copied back; the call returns after the stream has drained.
+// the outputs are copied back; the call returns after the stream has drained, or at once with
+// RBKI_FLAG_ASYNC (calls on different streams then overlap their copies with computation).
 #include "plan.h"
 
 namespace rbki {
@@ -68,7 +69,7 @@ rbki_status run_tucker_host_io(Plan& pl, const rbki_tensor* X, const rbki_tucker
         RBKI_CUDA_TRY(cudaMemcpyAsync(out->info, dout.info, (2 * pl.N + 1) * 4, cudaMemcpyDeviceToHost, st));
     if (out->q_used)
         RBKI_CUDA_TRY(cudaMemcpyAsync(out->q_used, dout.q_used, pl.N * 4, cudaMemcpyDeviceToHost, st));
-    RBKI_CUDA_TRY(cudaStreamSynchronize(st));
+    if (!(pl.flags & RBKI_FLAG_ASYNC)) RBKI_CUDA_TRY(cudaStreamSynchronize(st));
     return RBKI_OK;
 }
 

@@ -259,3 +259,20 @@ def test_tucker_short_gram_modes(rb, dims, core):
     out = rb.rbki_tucker(torch.from_numpy(wl.x.astype(np.float32)).cuda(), wl.ranks, wl.p, wl.q, wl.seed,
                          prec="bf16")
     assert abs(_err_from_norms(out["norms"]) - e_ref) <= 0.01 * e_ref
+
+
+def test_host_io_async_in_flight(rb):
+    """RBKI_FLAG_HOST_IO | RBKI_FLAG_ASYNC: calls on separate streams return at once and
+    overlap; after a synchronisation every host output equals the synchronous call's."""
+    wl = synth.config_small_fp64(mc=13, dims=(48, 40, 56), core=(5, 4, 6), p=3, q=2)
+    xh = torch.from_numpy(wl.x).pin_memory()
+    ref = rb.rbki_tucker(xh, wl.ranks, wl.p, wl.q, wl.seed, prec="fp64", flags=rb.FLAG_HOST_IO)
+    streams = [torch.cuda.Stream() for _ in range(3)]
+    outs = [rb.rbki_tucker(xh, wl.ranks, wl.p, wl.q, wl.seed, prec="fp64", flags=rb.FLAG_HOST_IO | rb.FLAG_ASYNC,
+                           stream=s) for s in streams]
+    torch.cuda.synchronize()
+    for o in outs:
+        assert torch.equal(o["core"], ref["core"])
+        for a, b in zip(o["factors"], ref["factors"]):
+            assert torch.equal(a, b)
+        assert torch.equal(o["norms"], ref["norms"])
