@@ -479,9 +479,8 @@ __global__ void __launch_bounds__(256) k_omega_images(uint64_t seed, int mode, i
     *reinterpret_cast<uint4*>(img + (size_t)t * 128 * N + (size_t)g * 1024 + c * 8) = w;
 }
 
-// out[i*ld + s] = sum over the nb CTA partials (+ the lo half when split), FP64.  A CTA
-// owns 32 outputs; its 8 warps take the partials b = w, w + 8, ..., four at a time with
-// independent loads, and the 8 warp sums are added in a fixed order (deterministic).
+// out[i*ld + s] = sum_b (part[b][i][s] + split * part[b][i][Sh + s]), FP64, fixed order:
+// 32 outputs per CTA; warp w sums partials b = w, w+8, ...; warps combined in order.
 constexpr int RED_WARPS = 8;
 __global__ void __launch_bounds__(32 * RED_WARPS) k_reduce_tc(const float* __restrict__ part, int nb, int64_t I,
                                                              int N, int Sh, int split, double* __restrict__ out,
@@ -494,23 +493,10 @@ __global__ void __launch_bounds__(32 * RED_WARPS) k_reduce_tc(const float* __res
     if (e < tot) {
         const int64_t i = e / Sh;
         const int s = (int)(e % Sh);
-        const float* p0 = part + i * N + s;
-        const size_t stride = (size_t)I * N;
-        int b = w;
-        for (; b + 3 * RED_WARPS < nb; b += 4 * RED_WARPS) {
-            float v[4], u[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-            for (int t = 0; t < 4; ++t) v[t] = p0[(size_t)(b + t * RED_WARPS) * stride];
-            if (split) {
-#pragma unroll
-                for (int t = 0; t < 4; ++t) u[t] = p0[(size_t)(b + t * RED_WARPS) * stride + Sh];
-            }
-#pragma unroll
-            for (int t = 0; t < 4; ++t) acc += (double)v[t] + (double)u[t];
-        }
-        for (; b < nb; b += RED_WARPS) {
-            acc += (double)p0[(size_t)b * stride];
-            if (split) acc += (double)p0[(size_t)b * stride + Sh];
+        for (int b = w; b < nb; b += RED_WARPS) {
+            const float* pb = part + ((size_t)b * I + i) * N;
+            acc += (double)pb[s];
+            if (split) acc += (double)pb[Sh + s];
         }
     }
     acc_sh[w][lane] = acc;
