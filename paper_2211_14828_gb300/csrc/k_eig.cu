@@ -401,6 +401,21 @@ __device__ __forceinline__ bool tied(const float* shift, int k) {
     return k > 0 && fabsf(shift[k] - shift[k - 1]) <= TIE_EPS * EPS32;
 }
 
+// Long runs (more than RUN_SERIAL members tied in FP32) get FP64 eigenvalues (k_run_shift64)
+// and FP64 inverse-iteration vectors (k_run_vec64), member by member in parallel; only members
+// still tied in FP64 (|mu_k - mu_{k-1}| <= TIE64 eps64 |T|: a numerically multiple eigenvalue)
+// are left to the serial run kernel.  mu64[k] is NaN outside long runs.
+constexpr int RUN_SERIAL = 8;
+constexpr double TIE64 = 16.0;
+constexpr double EPS64 = 1.1102230246251565e-16;
+__device__ __forceinline__ bool tied2(const float* shift, const double* mu64, double tn, int k) {
+    if (!tied(shift, k)) return false;
+    if (!mu64) return true;
+    const double a = mu64[k], b = mu64[k - 1];
+    if (isnan(a) || isnan(b)) return true;
+    return fabs(a - b) <= TIE64 * EPS64 * tn;
+}
+
 template <typename T>
 __device__ T tri_norm(const T* d, const T* e, int n) {
     T t = 0;
@@ -485,11 +500,16 @@ __global__ void __launch_bounds__(64) k_tri_vec(const T* __restrict__ d, const T
 // serial tridiagonal solve runs on thread 0.
 template <typename T>
 __global__ void __launch_bounds__(256) k_tri_runs(const T* __restrict__ d, const T* __restrict__ e, int n,
-                                                  int nwant, const float* __restrict__ shift, T* __restrict__ Y) {
+                                                  int nwant, const float* __restrict__ shift,
+                                                  const double* __restrict__ mu64, T* __restrict__ Y) {
     const int L = blockIdx.x;
-    if (L >= nwant || tied(shift, L) || L + 1 >= nwant || !tied(shift, L + 1)) return;
+    __shared__ T tn0;
+    if (threadIdx.x == 0) tn0 = tri_norm(d, e, n);
+    __syncthreads();
+    const double tnd = (double)tn0;
+    if (L >= nwant || tied2(shift, mu64, tnd, L) || L + 1 >= nwant || !tied2(shift, mu64, tnd, L + 1)) return;
     int end = L + 1;
-    while (end < nwant && tied(shift, end)) ++end;   // members L .. end-1
+    while (end < nwant && tied2(shift, mu64, tnd, end)) ++end;   // members L .. end-1
     __shared__ T y[256], c[256], rdd[256], du[256], du2[256];
     __shared__ T red[33];
     __shared__ T tn_sh;
@@ -525,7 +545,7 @@ __global__ void __launch_bounds__(256) k_tri_runs(const T* __restrict__ d, const
     for (int k = L + 1; k < end; ++k) {
         if (tid == 0) invit_start<T>(n, k, y, 1);
         __syncthreads();
-        const T mu = (T)shift[k] * tnorm;
+        const T mu = (mu64 && !isnan(mu64[k])) ? (T)mu64[k] : (T)shift[k] * tnorm;
         for (int sweep = 0; sweep < 3; ++sweep) {
             cgs2(k);
             if (tid == 0) invit_solve<T>(d, e, n, mu, tiny, rdd, du, du2, y, 1, 1);
@@ -535,6 +555,104 @@ __global__ void __launch_bounds__(256) k_tri_runs(const T* __restrict__ d, const
         for (int i = tid; i < n; i += nt) Y[(size_t)i * ld + k] = y[i];
         __syncthreads();
     }
+}
+
+__device__ int sturm_count64(const double* d, const double* e2, int n, double x, double pivmin) {
+    int c = 0;
+    double q = d[0] - x;
+    if (fabs(q) < pivmin) q = -pivmin;
+    if (q < 0.0) ++c;
+    for (int i = 1; i < n; ++i) {
+        q = (d[i] - x) - e2[i - 1] / q;
+        if (fabs(q) < pivmin) q = -pivmin;
+        if (q < 0.0) ++c;
+    }
+    return c;
+}
+
+constexpr int R64_WARPS = 8;
+
+// FP64 eigenvalue of every member of a long run: one warp per member, multisection (32 FP64
+// Sturm counts per round) from the run's FP32 bracket widened by 16 FP32 ulps of |T| (the
+// Gershgorin interval when the counts do not bracket the index), down to 4 eps64 |T|.
+template <typename T>
+__global__ void __launch_bounds__(32 * R64_WARPS) k_run_shift64(const T* __restrict__ d, const T* __restrict__ e,
+                                                               int n, int nwant, const float* __restrict__ shift,
+                                                               double* __restrict__ mu64) {
+    __shared__ double d64[256], e2[256];
+    __shared__ double tn_sh;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    for (int i = tid; i < n; i += blockDim.x) {
+        d64[i] = (double)d[i];
+        e2[i] = i + 1 < n ? (double)e[i] * (double)e[i] : 0.0;
+    }
+    if (tid == 0) tn_sh = (double)tri_norm(d, e, n);
+    __syncthreads();
+    const int k = blockIdx.x * R64_WARPS + w;
+    if (k >= nwant) return;
+    int L = k, end = k + 1;
+    while (L > 0 && tied(shift, L)) --L;
+    while (end < nwant && tied(shift, end)) ++end;
+    if (end - L <= RUN_SERIAL) {
+        if (lane == 0) mu64[k] = __longlong_as_double(0x7ff8000000000000LL);
+        return;
+    }
+    const double tn = tn_sh;
+    const double pivmin = 1e-300 + EPS64 * EPS64 * tn;
+    const int idx = n - 1 - k;                                     // index from below
+    double lo = (double)shift[end - 1] * tn - 16.0 * (double)EPS32 * tn;
+    double hi = (double)shift[L] * tn + 16.0 * (double)EPS32 * tn;
+    const int clo = lane == 0 ? sturm_count64(d64, e2, n, lo, pivmin) : 0;
+    const int chi = lane == 1 ? sturm_count64(d64, e2, n, hi, pivmin) : 0;
+    const int c0 = __shfl_sync(0xffffffffu, clo, 0), c1 = __shfl_sync(0xffffffffu, chi, 1);
+    if (!(c0 <= idx && c1 > idx)) {
+        lo = -1.001 * tn;
+        hi = 1.001 * tn;
+    }
+    for (int round = 0; round < 24; ++round) {
+        const double h = (hi - lo) * (1.0 / 33.0);
+        const double pt = lo + h * (double)(lane + 1);
+        const unsigned above = __ballot_sync(0xffffffffu, sturm_count64(d64, e2, n, pt, pivmin) > idx);
+        const int first = above ? __ffs(above) - 1 : 32;
+        const double nlo = first == 0 ? lo : lo + h * (double)first;
+        const double nhi = first == 32 ? hi : lo + h * (double)(first + 1);
+        if (!(nhi - nlo < hi - lo)) break;
+        lo = nlo;
+        hi = nhi;
+        if (hi - lo <= 4.0 * EPS64 * tn) break;
+    }
+    if (lane == 0) mu64[k] = 0.5 * (lo + hi);
+}
+
+// FP64 inverse iteration (three solves) for the long-run members that are not tied in FP64
+// to their predecessor; lane 0 of the member's warp runs the serial solve, the vector is
+// stored back in the working precision.  Factor rows and the iterate live in shared memory.
+template <typename T>
+__global__ void __launch_bounds__(32 * R64_WARPS) k_run_vec64(const T* __restrict__ d, const T* __restrict__ e, int n,
+                                                             int nwant, const double* __restrict__ mu64,
+                                                             T* __restrict__ Y) {
+    extern __shared__ __align__(16) unsigned char rv_raw[];
+    __shared__ double d64[256], e64[256];
+    __shared__ double tn_sh;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    for (int i = tid; i < n; i += blockDim.x) {
+        d64[i] = (double)d[i];
+        e64[i] = i + 1 < n ? (double)e[i] : 0.0;
+    }
+    if (tid == 0) tn_sh = (double)tri_norm(d, e, n);
+    __syncthreads();
+    const int k = blockIdx.x * R64_WARPS + w;
+    if (k >= nwant) return;
+    const double mu = mu64[k];
+    if (isnan(mu)) return;
+    const double tn = tn_sh;
+    if (k > 0 && !isnan(mu64[k - 1]) && fabs(mu - mu64[k - 1]) <= TIE64 * EPS64 * tn) return;
+    double* base = reinterpret_cast<double*>(rv_raw) + (size_t)w * 4 * n;
+    double *rdd = base, *du = base + n, *du2 = base + 2 * n, *y = base + 3 * n;
+    if (lane == 0) invit_one<double>(d64, e64, n, mu, tn, k, rdd, du, du2, y, 1, 3, 0, 1);
+    __syncwarp();
+    const int ld = nwant + 1;
+    for (int i = lane; i < n; i += 32) Y[(size_t)i * ld + k] = (T)y[i];
 }
 
 // Orthonormalise the inverse-iteration vectors by one Cholesky QR of the whole block
@@ -845,7 +963,7 @@ __global__ void k_copy_cols(const double* __restrict__ src, int lds, double* __r
 
 struct EigLayout {
     float *work, *refl, *d, *e, *lam, *shift, *Yt, *iiw;
-    double *X, *ZX1, *G, *S, *E, *T1, *lam_all, *lam1, *part;
+    double *X, *ZX1, *G, *S, *E, *T1, *lam_all, *lam1, *mu64, *part;
     size_t doubles;
 };
 
@@ -879,6 +997,7 @@ EigLayout eig_layout(double* base, int n) {
     L.T1 = db(nn);
     L.lam_all = db(n);
     L.lam1 = db(n);
+    L.mu64 = db(n);
     L.part = db(gemm_part_doubles(n, n, n));
     L.doubles = off + 64;
     return L;
@@ -920,7 +1039,17 @@ rbki_status syev_top_cuda(const double* A, int n, int nwant, double* w, double* 
     RBKI_LAUNCH_CHECK("k_tri_shift");
     k_tri_vec<float><<<(unsigned)cdiv(n, vthr), vthr, vsm, st>>>(L.d, L.e, n, n, L.shift, L.Yt);
     RBKI_LAUNCH_CHECK("k_tri_vec");
-    k_tri_runs<float><<<(unsigned)n, 256, 0, st>>>(L.d, L.e, n, n, L.shift, L.Yt);
+    k_run_shift64<float><<<(unsigned)cdiv(n, R64_WARPS), 32 * R64_WARPS, 0, st>>>(L.d, L.e, n, n, L.shift, L.mu64);
+    RBKI_LAUNCH_CHECK("k_run_shift64");
+    {
+        static size_t rvmax = 0;
+        if (!rvmax) rvmax = max_dyn_smem(k_run_vec64<float>);
+        const size_t rvsm = (size_t)R64_WARPS * 4 * n * sizeof(double);
+        if (rvsm > rvmax) return set_error(RBKI_E_UNSUPPORTED, "syev: FP64 run vectors exceed shared memory");
+        k_run_vec64<float><<<(unsigned)cdiv(n, R64_WARPS), 32 * R64_WARPS, rvsm, st>>>(L.d, L.e, n, n, L.mu64, L.Yt);
+        RBKI_LAUNCH_CHECK("k_run_vec64");
+    }
+    k_tri_runs<float><<<(unsigned)n, 256, 0, st>>>(L.d, L.e, n, n, L.shift, L.mu64, L.Yt);
     RBKI_LAUNCH_CHECK("k_tri_runs");
     const size_t rsm = (2 * (size_t)n * (n + 1) + n) * sizeof(float);
     if (n <= 128) {
