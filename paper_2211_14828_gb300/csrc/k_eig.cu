@@ -305,9 +305,26 @@ __host__ __device__ void invit_start(int n, int k, T* y, int ystride) {
     }
 }
 
+// FP64 reciprocal on a serial chain: an FP32 estimate refined by two Newton-Raphson steps
+// y <- y (2 - a y) (each doubles the correct bits: 24 -> 48 -> 96), a short dependent chain
+// instead of an FP64 division; IEEE division outside the FP32 exponent range (and on the host)
+__host__ __device__ __forceinline__ double rcp64_nr(double a) {
+#ifdef __CUDA_ARCH__
+    const double m = fabs(a);
+    if (!(m > 1e-30 && m < 1e30)) return 1.0 / a;
+    double y = (double)__frcp_rn((float)a);
+    y = y * (2.0 - a * y);
+    y = y * (2.0 - a * y);
+    return y;
+#else
+    return 1.0 / a;
+#endif
+}
+
 // reciprocal on the serial elimination chain: the hardware reciprocal for FP32 (this
-// stage only needs FP32 accuracy), IEEE division otherwise
+// stage only needs FP32 accuracy), the Newton-refined one for FP64
 template <typename T> __host__ __device__ __forceinline__ T chain_rcp(T a) { return (T)1 / a; }
+template <> __host__ __device__ __forceinline__ double chain_rcp<double>(double a) { return rcp64_nr(a); }
 #ifdef __CUDA_ARCH__
 template <> __device__ __forceinline__ float chain_rcp<float>(float a) { return __frcp_rn(a); }
 #endif
@@ -405,15 +422,19 @@ __device__ __forceinline__ bool tied(const float* shift, int k) {
 // and FP64 inverse-iteration vectors (k_run_vec64), member by member in parallel; only members
 // still tied in FP64 (|mu_k - mu_{k-1}| <= TIE64 eps64 |T|: a numerically multiple eigenvalue)
 // are left to the serial run kernel.  mu64[k] is NaN outside long runs.
+// The FP64 eigenvalues are resolved to RES64 |T| (enough for inverse iteration: shifts a
+// thousand times closer than the eigenvalue gaps they must separate); members whose values
+// agree within twice that are tied in FP64.
 constexpr int RUN_SERIAL = 8;
-constexpr double TIE64 = 16.0;
+constexpr double RES64 = 1e-12;
 constexpr double EPS64 = 1.1102230246251565e-16;
+__device__ __forceinline__ bool tied64(double a, double b, double tn) { return fabs(a - b) <= 2.0 * RES64 * tn; }
 __device__ __forceinline__ bool tied2(const float* shift, const double* mu64, double tn, int k) {
     if (!tied(shift, k)) return false;
     if (!mu64) return true;
     const double a = mu64[k], b = mu64[k - 1];
     if (isnan(a) || isnan(b)) return true;
-    return fabs(a - b) <= TIE64 * EPS64 * tn;
+    return tied64(a, b, tn);
 }
 
 template <typename T>
@@ -563,18 +584,20 @@ __device__ int sturm_count64(const double* d, const double* e2, int n, double x,
     if (fabs(q) < pivmin) q = -pivmin;
     if (q < 0.0) ++c;
     for (int i = 1; i < n; ++i) {
-        q = (d[i] - x) - e2[i - 1] / q;
+        q = (d[i] - x) - e2[i - 1] * rcp64_nr(q);
         if (fabs(q) < pivmin) q = -pivmin;
         if (q < 0.0) ++c;
     }
     return c;
 }
 
-constexpr int R64_WARPS = 8;
+// one warp per CTA: every lane of a member's warp runs an FP64 chain, and GB300 issues two
+// FP64 operations per clock per SM, so members are spread over as many SMs as possible
+constexpr int R64_WARPS = 1;
 
 // FP64 eigenvalue of every member of a long run: one warp per member, multisection (32 FP64
 // Sturm counts per round) from the run's FP32 bracket widened by 16 FP32 ulps of |T| (the
-// Gershgorin interval when the counts do not bracket the index), down to 4 eps64 |T|.
+// Gershgorin interval when the counts do not bracket the index), down to RES64 |T|.
 template <typename T>
 __global__ void __launch_bounds__(32 * R64_WARPS) k_run_shift64(const T* __restrict__ d, const T* __restrict__ e,
                                                                int n, int nwant, const float* __restrict__ shift,
@@ -619,7 +642,7 @@ __global__ void __launch_bounds__(32 * R64_WARPS) k_run_shift64(const T* __restr
         if (!(nhi - nlo < hi - lo)) break;
         lo = nlo;
         hi = nhi;
-        if (hi - lo <= 4.0 * EPS64 * tn) break;
+        if (hi - lo <= RES64 * tn) break;
     }
     if (lane == 0) mu64[k] = 0.5 * (lo + hi);
 }
@@ -646,7 +669,7 @@ __global__ void __launch_bounds__(32 * R64_WARPS) k_run_vec64(const T* __restric
     const double mu = mu64[k];
     if (isnan(mu)) return;
     const double tn = tn_sh;
-    if (k > 0 && !isnan(mu64[k - 1]) && fabs(mu - mu64[k - 1]) <= TIE64 * EPS64 * tn) return;
+    if (k > 0 && !isnan(mu64[k - 1]) && tied64(mu, mu64[k - 1], tn)) return;
     double* base = reinterpret_cast<double*>(rv_raw) + (size_t)w * 4 * n;
     double *rdd = base, *du = base + n, *du2 = base + 2 * n, *y = base + 3 * n;
     if (lane == 0) invit_one<double>(d64, e64, n, mu, tn, k, rdd, du, du2, y, 1, 3, 0, 1);
