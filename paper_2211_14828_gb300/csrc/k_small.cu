@@ -326,7 +326,7 @@ rbki_status orth_pass_cuda(double* Q, int64_t ldq, int64_t rows, int m, int S, d
     static size_t smax = 0;
     if (!smax) smax = max_dyn_smem(k_chol_deflate);
     if (sm > smax) return set_error(RBKI_E_UNSUPPORTED, "orth: block too wide for shared memory");
-    k_chol_deflate<<<1, 128, sm, st>>>(Gp, nu2, S, tau, Rinv, kept);
+    k_chol_deflate<<<1, 256, sm, st>>>(Gp, nu2, S, tau, Rinv, kept);
     RBKI_LAUNCH_CHECK("k_chol_deflate");
     k_orth_apply<<<(unsigned)cdiv(rows, ORTH_ROWS), 32 * ORTH_ROWS, ORTH_ROWS * S * sizeof(double), st>>>(
         Q, ldq, rows, m, S, M, Rinv);
