@@ -142,6 +142,89 @@ __global__ void __launch_bounds__(512) k_tridiag(const double* __restrict__ A, i
     }
 }
 
+// Shared-memory variant for n where the full n x (n+1) FP32 matrix no longer fits (n > 237):
+// the lower triangle, packed row by row (element (i, j), j <= i, at i (i + 1) / 2 + j: 126 KB
+// for n = 256), with the same Householder steps as k_tridiag.  u = B v takes row i's
+// stored part (j <= i, contiguous) and its mirrored part (j > i, read down column i); the
+// rank-2 update touches the lower triangle only.
+template <typename T>
+__global__ void __launch_bounds__(512) k_tridiag_packed(const double* __restrict__ A, int n, T* __restrict__ d,
+                                                        T* __restrict__ e, T* __restrict__ refl) {
+    extern __shared__ __align__(16) unsigned char tp_raw[];
+    T* a = reinterpret_cast<T*>(tp_raw);
+    auto at = [&](int i, int j) -> T& { return a[(size_t)i * (i + 1) / 2 + j]; };   // j <= i
+    __shared__ T v[256], u[256];
+    __shared__ T part_a[16], part_b[16];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+    for (int t = tid; t < n * n; t += nt) {
+        const int i = t / n, j = t % n;
+        if (j <= i) at(i, j) = (T)A[t];
+    }
+    for (int t = tid; t < n * n; t += nt) refl[t] = (T)0;
+    __syncthreads();
+    for (int k = 0; k + 2 < n; ++k) {
+        const int m = n - k - 1;
+        const int o = k + 1;
+        const T x0 = at(o, k);
+        T s1 = 0;
+        for (int i = 1 + tid; i < m; i += nt) {
+            const T x = at(o + i, k);
+            s1 += x * x;
+        }
+        T* part = (k & 1) ? part_b : part_a;
+        s1 = block_sum1(s1, part, nw);
+        if (tid == 0) d[k] = at(k, k);
+        if (s1 == (T)0) {
+            if (tid == 0) e[k] = x0;
+            __syncthreads();
+            continue;
+        }
+        const T nrm = sqrt(x0 * x0 + s1);
+        const T alpha = x0 >= (T)0 ? -nrm : nrm;
+        const T v0 = x0 - alpha;
+        const T inv = (T)1 / sqrt(v0 * v0 + s1);
+        for (int i = tid; i < m; i += nt) {
+            const T vi = (i == 0 ? v0 : at(o + i, k)) * inv;
+            v[i] = vi;
+            refl[(size_t)k * n + o + i] = vi;
+        }
+        if (tid == 0) e[k] = alpha;
+        __syncthreads();
+        // u = B v: warp per row, lanes over the row's stored and mirrored parts
+        T gp = 0;
+        for (int i = wid; i < m; i += nw) {
+            T acc = 0;
+            const T* row = a + (size_t)(o + i) * (o + i + 1) / 2 + o;
+            for (int j = lane; j <= i; j += 32) acc += row[j] * v[j];
+            for (int j = i + 1 + lane; j < m; j += 32) acc += at(o + j, o + i) * v[j];
+            acc = warp_sum(acc);
+            if (lane == 0) {
+                u[i] = acc;
+                gp += acc * v[i];
+            }
+        }
+        part = (k & 1) ? part_a : part_b;
+        const T g = block_sum1(gp, part, nw);
+        for (int i = tid; i < m; i += nt) u[i] = (T)2 * u[i] - (T)2 * g * v[i];   // w
+        __syncthreads();
+        // B -= v w^T + w v^T on the lower triangle
+        for (int i = wid; i < m; i += nw) {
+            const T vi = v[i], wi = u[i];
+            T* row = a + (size_t)(o + i) * (o + i + 1) / 2 + o;
+            for (int j = lane; j <= i; j += 32) row[j] -= vi * u[j] + wi * v[j];
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        if (n >= 2) {
+            d[n - 2] = at(n - 2, n - 2);
+            e[n - 2] = at(n - 1, n - 2);
+        }
+        d[n - 1] = at(n - 1, n - 1);
+    }
+}
+
 // Register-resident variant for n <= 32 * NC (and n <= 16 * NR): the working matrix is
 // distributed over 16 warps, element (i, j) held by warp i % 16 (slot i / 16) and lane
 // j % 32 (slot j / 32).  Per Householder step: the owners of column k publish it through
@@ -1046,11 +1129,17 @@ rbki_status syev_top_cuda(const double* A, int n, int nwant, double* w, double* 
     } else if (n <= 192) {
         k_tridiag_reg<12, 6><<<1, 512, 0, st>>>(A, n, L.d, L.e, L.refl);
     } else {
-        static size_t tmax = 0;
+        static size_t tmax = 0, pmax = 0;
         if (!tmax) tmax = max_dyn_smem(k_tridiag<float>);
+        if (!pmax) pmax = max_dyn_smem(k_tridiag_packed<float>);
         const size_t tsm = (size_t)(n + 1) * n * sizeof(float);
-        const int t_smem = tsm <= tmax;
-        k_tridiag<float><<<1, 512, t_smem ? tsm : 0, st>>>(A, n, L.work, t_smem, L.d, L.e, L.refl);
+        const size_t psm = (size_t)n * (n + 1) / 2 * sizeof(float);
+        if (tsm <= tmax)
+            k_tridiag<float><<<1, 512, tsm, st>>>(A, n, L.work, 1, L.d, L.e, L.refl);
+        else if (psm <= pmax)
+            k_tridiag_packed<float><<<1, 512, psm, st>>>(A, n, L.d, L.e, L.refl);
+        else
+            k_tridiag<float><<<1, 512, 0, st>>>(A, n, L.work, 0, L.d, L.e, L.refl);
     }
     RBKI_LAUNCH_CHECK("k_tridiag");
     static size_t vmax = 0;

@@ -60,7 +60,7 @@ def test_krylov_product_bf16_cuda_cores(rb, dims):
     assert rel < 2e-5
 
 
-@pytest.mark.parametrize("n", [1, 2, 5, 36, 48, 97, 120])
+@pytest.mark.parametrize("n", [1, 2, 5, 36, 48, 97, 120, 200, 250, 256])
 def test_syev(rb, n):
     g = np.random.default_rng(n)
     a = g.standard_normal((n, n))
