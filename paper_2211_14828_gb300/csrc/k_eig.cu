@@ -847,6 +847,78 @@ __global__ void __launch_bounds__(256) k_tri_orth(T* __restrict__ Yg, int n, int
     for (int t = tid; t < n * ld; t += blockDim.x) Yg[t] = ys[t];
 }
 
+// Variant of k_tri_orth for n whose working set does not fit in shared memory: Y stays in
+// global memory (L2-resident, at most 257 KB) and is updated in place; R lives in shared
+// memory as the packed upper triangle (row p from column p: n (n + 1) / 2 floats, 128 KB for
+// n = 256).  Same Gram tiles, Cholesky with the same pivot guard, and row solves.
+template <typename T>
+__global__ void __launch_bounds__(256) k_tri_orth_packed(T* __restrict__ Yg, int n, int nwant) {
+    extern __shared__ __align__(16) unsigned char op_raw[];
+    T* Gp = reinterpret_cast<T*>(op_raw);
+    T* Ri = Gp + (size_t)nwant * (nwant + 1) / 2;
+    auto G = [&](int p, int q) -> T& { return Gp[(size_t)p * nwant - (size_t)p * (p - 1) / 2 + (q - p)]; };
+    const int tid = threadIdx.x;
+    const int ld = nwant + 1;
+    T* ys = Yg;
+    const int nt4 = (nwant + 3) / 4;
+    for (int t = tid; t < nt4 * nt4; t += blockDim.x) {
+        const int pb = (t / nt4) * 4, qb = (t % nt4) * 4;
+        if (qb + 3 < pb) continue;
+        T acc[4][4] = {};
+        for (int i = 0; i < n; ++i) {
+            const T* yi = ys + (size_t)i * ld;
+            T yp[4], yq[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                yp[u] = pb + u < nwant ? yi[pb + u] : (T)0;
+                yq[u] = qb + u < nwant ? yi[qb + u] : (T)0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v2 = 0; v2 < 4; ++v2) acc[u][v2] += yp[u] * yq[v2];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v2 = 0; v2 < 4; ++v2) {
+                const int pp = pb + u, qq = qb + v2;
+                if (pp < nwant && qq < nwant && qq >= pp) G(pp, qq) = acc[u][v2];
+            }
+    }
+    __syncthreads();
+    const int lane = tid & 31, wid = tid >> 5, nwp = blockDim.x >> 5;
+    for (int k = 0; k < nwant; ++k) {
+        const T dk = G(k, k);
+        const T ri = dk > (T)1e-6 ? (T)1 / sqrt(dk) : (T)1;
+        if (tid == 0) Ri[k] = ri;
+        const T r2 = ri * ri;
+        for (int i = k + 1 + wid; i < nwant; i += nwp) {
+            const T gki = G(k, i) * r2;
+            for (int j = i + lane; j < nwant; j += 32) G(i, j) -= gki * G(k, j);
+        }
+        __syncthreads();
+    }
+    for (int t = tid; t < nwant * nwant; t += blockDim.x) {
+        const int p = t / nwant, q = t % nwant;
+        if (q >= p) G(p, q) *= Ri[p];
+    }
+    __syncthreads();
+    for (int i = tid; i < n; i += blockDim.x) {
+        T* yi = ys + (size_t)i * ld;
+        for (int q = 0; q < nwant; ++q) {
+            T a0 = yi[q], a1 = 0;
+            int p = 0;
+            for (; p + 1 < q; p += 2) {
+                a0 -= yi[p] * G(p, q);
+                a1 -= yi[p + 1] * G(p + 1, q);
+            }
+            for (; p < q; ++p) a0 -= yi[p] * G(p, q);
+            yi[q] = (a0 + a1) * Ri[q];
+        }
+    }
+}
+
 // Cholesky QR of the eigenvector block for n <= 32 * NC (n <= 16 * NR), 512 threads.
 // Y (n x n, ld n+1) is staged in shared memory; G = Y^T Y is accumulated into the same
 // register distribution as k_tridiag_reg; the right-looking Cholesky publishes row k
@@ -1177,11 +1249,17 @@ rbki_status syev_top_cuda(const double* A, int n, int nwant, double* w, double* 
             k_tri_orth_reg<8, 4><<<1, 512, rsm, st>>>(L.Yt, n);
         }
     } else {
-        static size_t omax = 0;
+        static size_t omax = 0, opmax = 0;
         if (!omax) omax = max_dyn_smem(k_tri_orth<float>);
+        if (!opmax) opmax = max_dyn_smem(k_tri_orth_packed<float>);
         const size_t osm = (size_t)(n + 2 * n) * (n + 1) * sizeof(float);
-        const int o_smem = osm <= omax;
-        k_tri_orth<float><<<1, 256, o_smem ? osm : 0, st>>>(L.Yt, n, n, L.iiw, o_smem);
+        const size_t opsm = ((size_t)n * (n + 1) / 2 + n) * sizeof(float);
+        if (osm <= omax)
+            k_tri_orth<float><<<1, 256, osm, st>>>(L.Yt, n, n, L.iiw, 1);
+        else if (opsm <= opmax)
+            k_tri_orth_packed<float><<<1, 256, opsm, st>>>(L.Yt, n, n);
+        else
+            k_tri_orth<float><<<1, 256, 0, st>>>(L.Yt, n, n, L.iiw, 0);
     }
     RBKI_LAUNCH_CHECK("k_tri_orth");
     k_tri_rq<float><<<(unsigned)cdiv(n, 64), 64, 0, st>>>(L.d, L.e, n, n, L.Yt, L.lam);
