@@ -567,12 +567,22 @@ static rbki_status run_modes_adaptive(const Plan& pl, const rbki_tucker_out* out
 }
 
 // step 6: G = X x_1 U^(1)T ... x_N U^(N)T, largest shrink first
-rbki_status core_chain(const Plan& pl, double* const* factors, double* core, cudaStream_t st) {
+// Steps t_begin .. t_end-1 of the chain; the state before t_begin (dims, source buffer and
+// its dtype) follows from the plan, so the first product can run on its mode's stream as
+// soon as that factor exists and the rest after the join.
+rbki_status core_chain(const Plan& pl, double* const* factors, double* core, cudaStream_t st, int t_begin = 0,
+                       int t_end = -1) {
+    if (t_end < 0) t_end = pl.N;
     int64_t cur[RBKI_MAX_ORDER];
     for (int n = 0; n < pl.N; ++n) cur[n] = pl.dims[n];
     const void* src = pl.xstream;
     int src_dtype = pl.stream_dtype;
-    for (int t = 0; t < pl.N; ++t) {
+    for (int t = 0; t < t_begin; ++t) {
+        cur[pl.order[t]] = pl.mode[pl.order[t]].R;
+        src = pl.tbuf[t & 1];
+        src_dtype = (t == 0 && pl.ttm_tc && pl.N > 1) ? RBKI_F32 : RBKI_F64;
+    }
+    for (int t = t_begin; t < t_end; ++t) {
         int m = pl.order[t];
         int64_t A = 1, C = 1;
         for (int k = 0; k < m; ++k) A *= cur[k];
@@ -756,6 +766,7 @@ rbki_status run_tucker(Plan& pl, const rbki_tucker_out* out, cudaStream_t st, co
     }
     prof_end(tok, st);
     const bool concurrent = pl.N > 1 && !(pl.flags & RBKI_FLAG_SERIAL_MODES);
+    int chain_from = 0;   // core-chain steps already enqueued on a mode stream
     int32_t q_used[RBKI_MAX_ORDER];
     for (int n = 0; n < pl.N; ++n) q_used[n] = pl.mode[n].gram ? 0 : pl.mode[n].q;
     if (pl.flags & RBKI_FLAG_ADAPTIVE_Q) {
@@ -793,6 +804,11 @@ rbki_status run_tucker(Plan& pl, const rbki_tucker_out* out, cudaStream_t st, co
             RBKI_CUDA_TRY(cudaEventCreateWithFlags(&join[n], cudaEventDisableTiming));
             RBKI_CUDA_TRY(cudaStreamWaitEvent(ms[n], fork, 0));
             if (rs >= 0) rs = mode_factor(pl, pl.mode[n], out->factors[n], out->eigvals[n], out->info, ms[n]);
+            // the first core product needs only this mode's factor: start it on this stream
+            if (rs >= 0 && n == pl.order[0]) {
+                rs = core_chain(pl, out->factors, out->core, ms[n], 0, 1);
+                chain_from = 1;
+            }
             RBKI_CUDA_TRY(cudaEventRecord(join[n], ms[n]));
             RBKI_CUDA_TRY(cudaStreamWaitEvent(st, join[n], 0));
         }
@@ -805,7 +821,7 @@ rbki_status run_tucker(Plan& pl, const rbki_tucker_out* out, cudaStream_t st, co
     }
     if (out->q_used)
         for (int n = 0; n < pl.N; ++n) RBKI_TRY(fill_i32_cuda(out->q_used + n, q_used[n], 1, st));
-    RBKI_TRY(core_chain(pl, out->factors, out->core, st));
+    RBKI_TRY(core_chain(pl, out->factors, out->core, st, chain_from));
     RBKI_TRY(sumsq_cuda(out->core, RBKI_F64, pl.ranks_numel, pl.scal + 64, norms + 1, st));
     if (out->info)
         RBKI_CUDA_TRY(cudaMemcpyAsync(out->info + 2 * pl.N, pl.err, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
