@@ -848,43 +848,55 @@ __global__ void __launch_bounds__(256) k_tri_orth(T* __restrict__ Yg, int n, int
 }
 
 // Variant of k_tri_orth for n whose working set does not fit in shared memory: Y stays in
-// global memory (L2-resident, at most 257 KB) and is updated in place; R lives in shared
-// memory as the packed upper triangle (row p from column p: n (n + 1) / 2 floats, 128 KB for
-// n = 256).  Same Gram tiles, Cholesky with the same pivot guard, and row solves.
+// global memory (L2-resident, at most 257 KB) and is updated in place, staged through
+// shared memory 64 rows at a time for the Gram matrix; R lives in shared memory as the packed
+// upper triangle (row p from column p: n (n + 1) / 2 floats, 128 KB for n = 256).  Same
+// Gram tiles, Cholesky with the same pivot guard, and row solves.
+constexpr int ORTH_CH = 64;   // rows of Y staged per pass of the Gram accumulation
 template <typename T>
 __global__ void __launch_bounds__(256) k_tri_orth_packed(T* __restrict__ Yg, int n, int nwant) {
     extern __shared__ __align__(16) unsigned char op_raw[];
     T* Gp = reinterpret_cast<T*>(op_raw);
     T* Ri = Gp + (size_t)nwant * (nwant + 1) / 2;
+    T* Yc = Ri + nwant;                                    // ORTH_CH x ld staged rows of Y
     auto G = [&](int p, int q) -> T& { return Gp[(size_t)p * nwant - (size_t)p * (p - 1) / 2 + (q - p)]; };
     const int tid = threadIdx.x;
     const int ld = nwant + 1;
     T* ys = Yg;
+    for (int t = tid; t < nwant * (nwant + 1) / 2; t += blockDim.x) Gp[t] = (T)0;
+    // G = Y^T Y over chunks of ORTH_CH rows staged in shared memory; each thread adds its own
+    // 4 x 4 tiles' partial sums into G, so no two threads touch the same entry
     const int nt4 = (nwant + 3) / 4;
-    for (int t = tid; t < nt4 * nt4; t += blockDim.x) {
-        const int pb = (t / nt4) * 4, qb = (t % nt4) * 4;
-        if (qb + 3 < pb) continue;
-        T acc[4][4] = {};
-        for (int i = 0; i < n; ++i) {
-            const T* yi = ys + (size_t)i * ld;
-            T yp[4], yq[4];
+    for (int r0 = 0; r0 < n; r0 += ORTH_CH) {
+        const int rows = n - r0 < ORTH_CH ? n - r0 : ORTH_CH;
+        __syncthreads();
+        for (int t = tid; t < rows * ld; t += blockDim.x) Yc[t] = ys[(size_t)r0 * ld + t];
+        __syncthreads();
+        for (int t = tid; t < nt4 * nt4; t += blockDim.x) {
+            const int pb = (t / nt4) * 4, qb = (t % nt4) * 4;
+            if (qb + 3 < pb) continue;
+            T acc[4][4] = {};
+            for (int i = 0; i < rows; ++i) {
+                const T* yi = Yc + (size_t)i * ld;
+                T yp[4], yq[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                yp[u] = pb + u < nwant ? yi[pb + u] : (T)0;
-                yq[u] = qb + u < nwant ? yi[qb + u] : (T)0;
+                for (int u = 0; u < 4; ++u) {
+                    yp[u] = pb + u < nwant ? yi[pb + u] : (T)0;
+                    yq[u] = qb + u < nwant ? yi[qb + u] : (T)0;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v2 = 0; v2 < 4; ++v2) acc[u][v2] += yp[u] * yq[v2];
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
-                for (int v2 = 0; v2 < 4; ++v2) acc[u][v2] += yp[u] * yq[v2];
+                for (int v2 = 0; v2 < 4; ++v2) {
+                    const int pp = pb + u, qq = qb + v2;
+                    if (pp < nwant && qq < nwant && qq >= pp) G(pp, qq) += acc[u][v2];
+                }
         }
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int v2 = 0; v2 < 4; ++v2) {
-                const int pp = pb + u, qq = qb + v2;
-                if (pp < nwant && qq < nwant && qq >= pp) G(pp, qq) = acc[u][v2];
-            }
     }
     __syncthreads();
     const int lane = tid & 31, wid = tid >> 5, nwp = blockDim.x >> 5;
@@ -1253,7 +1265,7 @@ rbki_status syev_top_cuda(const double* A, int n, int nwant, double* w, double* 
         if (!omax) omax = max_dyn_smem(k_tri_orth<float>);
         if (!opmax) opmax = max_dyn_smem(k_tri_orth_packed<float>);
         const size_t osm = (size_t)(n + 2 * n) * (n + 1) * sizeof(float);
-        const size_t opsm = ((size_t)n * (n + 1) / 2 + n) * sizeof(float);
+        const size_t opsm = ((size_t)n * (n + 1) / 2 + n + (size_t)ORTH_CH * (n + 1)) * sizeof(float);
         if (osm <= omax)
             k_tri_orth<float><<<1, 256, osm, st>>>(L.Yt, n, n, L.iiw, 1);
         else if (opsm <= opmax)
