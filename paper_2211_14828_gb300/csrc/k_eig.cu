@@ -1213,9 +1213,8 @@ rbki_status syev_top_cuda(const double* A, int n, int nwant, double* w, double* 
     } else if (n <= 192) {
         k_tridiag_reg<12, 6><<<1, 512, 0, st>>>(A, n, L.d, L.e, L.refl);
     } else {
-        static size_t tmax = 0, pmax = 0;
-        if (!tmax) tmax = max_dyn_smem(k_tridiag<float>);
-        if (!pmax) pmax = max_dyn_smem(k_tridiag_packed<float>);
+        static const size_t tmax = max_dyn_smem(k_tridiag<float>);          // thread-safe, once
+        static const size_t pmax = max_dyn_smem(k_tridiag_packed<float>);
         const size_t tsm = (size_t)(n + 1) * n * sizeof(float);
         const size_t psm = (size_t)n * (n + 1) / 2 * sizeof(float);
         if (tsm <= tmax)
@@ -1226,8 +1225,7 @@ rbki_status syev_top_cuda(const double* A, int n, int nwant, double* w, double* 
             k_tridiag<float><<<1, 512, 0, st>>>(A, n, L.work, 0, L.d, L.e, L.refl);
     }
     RBKI_LAUNCH_CHECK("k_tridiag");
-    static size_t vmax = 0;
-    if (!vmax) vmax = max_dyn_smem(k_tri_vec<float>);
+    static const size_t vmax = max_dyn_smem(k_tri_vec<float>);
     const int vthr = 32;
     const size_t vsm = 3 * (size_t)n * vthr * sizeof(float);
     if (vsm > vmax) return set_error(RBKI_E_UNSUPPORTED, "syev: inverse-iteration rows exceed shared memory");
@@ -1238,8 +1236,7 @@ rbki_status syev_top_cuda(const double* A, int n, int nwant, double* w, double* 
     k_run_shift64<float><<<(unsigned)cdiv(n, R64_WARPS), 32 * R64_WARPS, 0, st>>>(L.d, L.e, n, n, L.shift, L.mu64);
     RBKI_LAUNCH_CHECK("k_run_shift64");
     {
-        static size_t rvmax = 0;
-        if (!rvmax) rvmax = max_dyn_smem(k_run_vec64<float>);
+        static const size_t rvmax = max_dyn_smem(k_run_vec64<float>);
         const size_t rvsm = (size_t)R64_WARPS * 4 * n * sizeof(double);
         if (rvsm > rvmax) return set_error(RBKI_E_UNSUPPORTED, "syev: FP64 run vectors exceed shared memory");
         k_run_vec64<float><<<(unsigned)cdiv(n, R64_WARPS), 32 * R64_WARPS, rvsm, st>>>(L.d, L.e, n, n, L.mu64, L.Yt);
@@ -1249,21 +1246,23 @@ rbki_status syev_top_cuda(const double* A, int n, int nwant, double* w, double* 
     RBKI_LAUNCH_CHECK("k_tri_runs");
     const size_t rsm = (2 * (size_t)n * (n + 1) + n) * sizeof(float);
     if (n <= 128) {
-        static size_t rmax[3] = {0, 0, 0};
+        // opt-in to large dynamic shared memory once per variant (thread-safe statics)
         if (n <= 32) {
-            if (!rmax[0]) rmax[0] = max_dyn_smem(k_tri_orth_reg<2, 1>);
+            static const size_t r0 = max_dyn_smem(k_tri_orth_reg<2, 1>);
+            (void)r0;
             k_tri_orth_reg<2, 1><<<1, 512, rsm, st>>>(L.Yt, n);
         } else if (n <= 64) {
-            if (!rmax[1]) rmax[1] = max_dyn_smem(k_tri_orth_reg<4, 2>);
+            static const size_t r1 = max_dyn_smem(k_tri_orth_reg<4, 2>);
+            (void)r1;
             k_tri_orth_reg<4, 2><<<1, 512, rsm, st>>>(L.Yt, n);
         } else {
-            if (!rmax[2]) rmax[2] = max_dyn_smem(k_tri_orth_reg<8, 4>);
+            static const size_t r2 = max_dyn_smem(k_tri_orth_reg<8, 4>);
+            (void)r2;
             k_tri_orth_reg<8, 4><<<1, 512, rsm, st>>>(L.Yt, n);
         }
     } else {
-        static size_t omax = 0, opmax = 0;
-        if (!omax) omax = max_dyn_smem(k_tri_orth<float>);
-        if (!opmax) opmax = max_dyn_smem(k_tri_orth_packed<float>);
+        static const size_t omax = max_dyn_smem(k_tri_orth<float>);
+        static const size_t opmax = max_dyn_smem(k_tri_orth_packed<float>);
         const size_t osm = (size_t)(n + 2 * n) * (n + 1) * sizeof(float);
         const size_t opsm = ((size_t)n * (n + 1) / 2 + n + (size_t)ORTH_CH * (n + 1)) * sizeof(float);
         if (osm <= omax)
@@ -1276,8 +1275,7 @@ rbki_status syev_top_cuda(const double* A, int n, int nwant, double* w, double* 
     RBKI_LAUNCH_CHECK("k_tri_orth");
     k_tri_rq<float><<<(unsigned)cdiv(n, 64), 64, 0, st>>>(L.d, L.e, n, n, L.Yt, L.lam);
     RBKI_LAUNCH_CHECK("k_tri_rq");
-    static size_t bmax = 0;
-    if (!bmax) bmax = max_dyn_smem(k_backtransform<float>);
+    static const size_t bmax = max_dyn_smem(k_backtransform<float>);
     const size_t bsm = (size_t)n * n * sizeof(float);
     const int b_smem = bsm <= bmax;
     k_backtransform<float><<<(unsigned)cdiv(n, BT_WARPS), 32 * BT_WARPS, b_smem ? bsm : 0, st>>>(

@@ -323,8 +323,7 @@ rbki_status orth_pass_cuda(double* Q, int64_t ldq, int64_t rows, int m, int S, d
     k_gprime<<<S, 128, 0, st>>>(M, m, S, Gp, nu2);
     RBKI_LAUNCH_CHECK("k_gprime");
     size_t sm = ((size_t)S * S + 2 * S) * sizeof(double);   // W | L^{-1}, 1/d, 1/sqrt(d)
-    static size_t smax = 0;
-    if (!smax) smax = max_dyn_smem(k_chol_deflate);
+    static const size_t smax = max_dyn_smem(k_chol_deflate);   // thread-safe, once
     if (sm > smax) return set_error(RBKI_E_UNSUPPORTED, "orth: block too wide for shared memory");
     k_chol_deflate<<<1, 256, sm, st>>>(Gp, nu2, S, tau, Rinv, kept);
     RBKI_LAUNCH_CHECK("k_chol_deflate");

@@ -516,22 +516,21 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 EncodeTiledFn encode_fn() {
-    static EncodeTiledFn fn = nullptr;
-    if (!fn) {
+    static const EncodeTiledFn fn = [] {   // looked up once, thread-safe
         void* ptr = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
                 cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            fn = (EncodeTiledFn)ptr;
-    }
+            return (EncodeTiledFn)ptr;
+        return (EncodeTiledFn) nullptr;
+    }();
     return fn;
 }
 
 template <int MODE, bool IFAST>
 size_t smem_limit() {
-    static size_t mx = 0;
-    if (!mx) mx = max_dyn_smem(k_stream_tc<MODE, IFAST>);
+    static const size_t mx = max_dyn_smem(k_stream_tc<MODE, IFAST>);   // thread-safe, once
     return mx;
 }
 
@@ -562,15 +561,14 @@ size_t image_bytes_omega(const View& v, int N) { return (size_t)num_tiles(v) * 1
 // decompositions in flight, single-CTA kernels of other streams may hold an SM's shared
 // memory, and a persistent CTA that cannot start there delays its whole launch.
 int grid_size(const View& v) {
-    static int sms = 0;
-    if (!sms) {
+    static const int sms = [] {
         int dev = 0, n = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
         int reserve = 0;
         if (const char* e = std::getenv("RBKI_TC_SM_RESERVE")) reserve = std::atoi(e);
-        sms = std::max(1, n - std::max(0, std::min(reserve, n - 1)));
-    }
+        return std::max(1, n - std::max(0, std::min(reserve, n - 1)));
+    }();
     return (int)std::min<int64_t>(num_tiles(v), sms);
 }
 

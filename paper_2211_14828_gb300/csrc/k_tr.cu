@@ -324,8 +324,7 @@ rbki_status tr_als_cuda(const TrPlan& p, const double* G, double g_norm2, double
     Meta* dmeta = reinterpret_cast<Meta*>(meta);
     RBKI_CUDA_TRY(cudaMemcpyAsync(dmeta, host_meta, N * sizeof(Meta), cudaMemcpyHostToDevice, st));
     RBKI_CUDA_TRY(cudaStreamSynchronize(st));
-    static size_t smax = 0;
-    if (!smax) smax = max_dyn_smem(k_tr_solve);
+    static const size_t smax = max_dyn_smem(k_tr_solve);   // thread-safe, once
     const size_t smem = 4 * (size_t)TR_RMAX * TR_RMAX * TR_RMAX * TR_RMAX * sizeof(double);
     if (smem > smax) return set_error(RBKI_E_UNSUPPORTED, "TR-ALS: ranks too large");
     double prev = -1.0;
