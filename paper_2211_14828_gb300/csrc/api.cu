@@ -319,10 +319,15 @@ void carve(Plan& pl, void* ws) {
         const ModePlan& m = pl.mode[m0];
         // the first core product streams all of X (not a mode's column sample)
         View v{nullptr, pl.stream_dtype, m.sampled ? m.A0 : m.A, m.I, m.sampled ? m.C0 : m.C};
-        // the core carries the reconstruction error |X|^2 - |G|^2: always hi + lo operands
+        // the core carries the reconstruction error |X|^2 - |G|^2: always hi + lo operands,
+        // in one pass (2R columns) when they fit the MMA width, else in two (R columns each)
         pl.ttm_N = (int)rup(2 * m.R, 16);
         pl.ttm_tc = pl.mixed && m.R <= 32 && tc::supported(v, tc::TTM, pl.ttm_N);
-        if (pl.ttm_tc) pl.ttm_img = c.take<char>(tc::image_bytes_skinny(v, pl.ttm_N));
+        if (!pl.ttm_tc && pl.mixed && m.R <= 64 && tc::supported(v, tc::TTM, (int)rup(m.R, 16))) {
+            pl.ttm_tc2 = true;
+            pl.ttm_N = (int)rup(m.R, 16);
+        }
+        if (pl.ttm_tc || pl.ttm_tc2) pl.ttm_img = c.take<char>(tc::image_bytes_skinny(v, pl.ttm_N));
     }
     pl.ws_bytes = c.off + 256;
 }
@@ -341,6 +346,18 @@ __global__ void k_symmetrize(double* Z, int n) {
         Z[i * n + j] = v;
         Z[j * n + i] = v;
     }
+}
+
+__global__ void k_add_f32(float* __restrict__ y, const float* __restrict__ x, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] += x[i];
+}
+
+rbki_status add_f32_cuda(float* y, const float* x, int64_t n, cudaStream_t st) {
+    if (n <= 0) return RBKI_OK;
+    k_add_f32<<<(unsigned)std::min<int64_t>(cdiv(n, 256), 152 * 8), 256, 0, st>>>(y, x, n);
+    RBKI_LAUNCH_CHECK("k_add_f32");
+    return RBKI_OK;
 }
 
 rbki_status symmetrize_cuda(double* Z, int n, cudaStream_t st) {
@@ -580,7 +597,7 @@ rbki_status core_chain(const Plan& pl, double* const* factors, double* core, cud
     for (int t = 0; t < t_begin; ++t) {
         cur[pl.order[t]] = pl.mode[pl.order[t]].R;
         src = pl.tbuf[t & 1];
-        src_dtype = (t == 0 && pl.ttm_tc && pl.N > 1) ? RBKI_F32 : RBKI_F64;
+        src_dtype = (t == 0 && (pl.ttm_tc || pl.ttm_tc2) && pl.N > 1) ? RBKI_F32 : RBKI_F64;
     }
     for (int t = t_begin; t < t_end; ++t) {
         int m = pl.order[t];
@@ -597,6 +614,23 @@ rbki_status core_chain(const Plan& pl, double* const* factors, double* core, cud
                                       pl.ttm_img, st));
             RBKI_TRY(tc::stream_tc(tc::TTM, v, pl.ttm_N, R, true, pl.ttm_img, nullptr, nullptr, (float*)dst,
                                    pl.err, st));
+            prof_end(tok, st);
+            cur[m] = R;
+            src = dst;
+            src_dtype = RBKI_F32;
+            continue;
+        }
+        if (t == 0 && pl.ttm_tc2 && t != pl.N - 1) {
+            // R > 32: the hi part of the factor into dst, the lo part into the other ping-pong
+            // buffer (free until step 1), then summed: the split product in two passes
+            float* lo = reinterpret_cast<float*>(pl.tbuf[1]);
+            const bool f16 = pl.stream_dtype == RBKI_F16;
+            RBKI_TRY(tc::skinny_image(factors[m], R, cur[m], R, pl.ttm_N, 0, f16, pl.ttm_img, st));
+            RBKI_TRY(tc::stream_tc(tc::TTM, v, pl.ttm_N, R, false, pl.ttm_img, nullptr, nullptr, (float*)dst,
+                                   pl.err, st));
+            RBKI_TRY(tc::skinny_image(factors[m], R, cur[m], R, pl.ttm_N, 2, f16, pl.ttm_img, st));
+            RBKI_TRY(tc::stream_tc(tc::TTM, v, pl.ttm_N, R, false, pl.ttm_img, nullptr, nullptr, lo, pl.err, st));
+            RBKI_TRY(add_f32_cuda((float*)dst, lo, A * R * C, st));
             prof_end(tok, st);
             cur[m] = R;
             src = dst;

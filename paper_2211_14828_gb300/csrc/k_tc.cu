@@ -405,7 +405,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_stream_tc(const __grid_constant
 // ---- operand images ----
 // B image of a skinny FP64 matrix M (rows x S, ld ldm) for GEMM1: MN-major no-swizzle,
 // element (i, n) at (i/8)*(N/8)*128 + (n/8)*128 + (i%8)*16 + (n%8)*2; rows padded to
-// rows_pad; columns n < S hold hi (or the value), S <= n < 2S the lo part when split.
+// rows_pad; columns n < S hold hi (or the value), S <= n < 2S the lo part when split == 1;
+// split == 2 puts the lo parts alone in columns n < S.
 __global__ void k_skinny_image(const double* __restrict__ M, int64_t ldm, int64_t rows, int S,
                                int64_t rows_pad, int N, int split, int fp16, uint16_t* __restrict__ img) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -413,11 +414,11 @@ __global__ void k_skinny_image(const double* __restrict__ M, int64_t ldm, int64_
     int64_t i = e / N;
     int n = (int)(e % N);
     float val = 0.f;
-    int s = (split && n >= S) ? n - S : n;
+    int s = (split == 1 && n >= S) ? n - S : n;
     if (i < rows && s < S) {
         double x = M[i * ldm + s];
         float hi = fp16 ? __half2float(__double2half(x)) : __bfloat162float(__double2bfloat16(x));
-        val = (split && n >= S) ? (float)(x - (double)hi) : hi;
+        val = ((split == 1 && n >= S) || split == 2) ? (float)(x - (double)hi) : hi;
     }
     uint16_t bits;
     if (fp16) { __half h = __float2half_rn(val); bits = *reinterpret_cast<uint16_t*>(&h); }
@@ -572,11 +573,11 @@ int grid_size(const View& v) {
     return (int)std::min<int64_t>(num_tiles(v), sms);
 }
 
-rbki_status skinny_image(const double* M, int64_t ldm, int64_t rows, int S, int N, bool split, bool fp16,
+rbki_status skinny_image(const double* M, int64_t ldm, int64_t rows, int S, int N, int split, bool fp16,
                          void* img, cudaStream_t st) {
     int64_t rows_pad = cdiv(rows, 128) * 128;
     int64_t tot = rows_pad * N;
-    k_skinny_image<<<(unsigned)cdiv(tot, 256), 256, 0, st>>>(M, ldm, rows, S, rows_pad, N, split ? 1 : 0,
+    k_skinny_image<<<(unsigned)cdiv(tot, 256), 256, 0, st>>>(M, ldm, rows, S, rows_pad, N, split,
                                                              fp16 ? 1 : 0, (uint16_t*)img);
     RBKI_LAUNCH_CHECK("k_skinny_image");
     return RBKI_OK;

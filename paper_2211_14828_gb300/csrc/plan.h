@@ -53,7 +53,8 @@ struct Plan {
     char* xs = nullptr;            // staged low-precision copy of X
     double* tbuf[2] = {nullptr, nullptr};
     int32_t* err = nullptr;        // device error word (bounded waits)
-    bool ttm_tc = false;           // first core TTM on tcgen05
+    bool ttm_tc = false;           // first core TTM on tcgen05 (split factor, 2R <= 64)
+    bool ttm_tc2 = false;          // ... as two plain passes (hi, then lo; 32 < R <= 64)
     int ttm_N = 0;
     void* ttm_img = nullptr;
     size_t ws_bytes = 0;

@@ -35,7 +35,9 @@ int64_t num_tiles(const View& v);
 int grid_size(const View& v);
 size_t image_bytes_skinny(const View& v, int N);
 size_t image_bytes_omega(const View& v, int N);
-rbki_status skinny_image(const double* M, int64_t ldm, int64_t rows, int S, int N, bool split, bool fp16,
+// split: 0 the values (rounded), 1 hi in columns < S and lo = value - hi in columns S..2S-1,
+// 2 the lo parts alone in columns < S
+rbki_status skinny_image(const double* M, int64_t ldm, int64_t rows, int S, int N, int split, bool fp16,
                          void* img, cudaStream_t st);
 rbki_status omega_images(uint64_t seed, int mode, const View& v, int S, int N, bool split, void* img,
                          cudaStream_t st);

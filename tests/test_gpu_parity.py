@@ -276,3 +276,20 @@ def test_host_io_async_in_flight(rb):
         for a, b in zip(o["factors"], ref["factors"]):
             assert torch.equal(a, b)
         assert torch.equal(o["norms"], ref["norms"])
+
+
+def test_first_core_product_rank_above_32(rb):
+    """R = 40 on the first contracted mode: the split (hi + lo) factor no longer fits one
+    tensor-core pass, so the product runs as two plain passes summed; the mixed result's
+    error stays within 1% of the oracle's and within 1e-3 of the FP64 path's."""
+    wl = synth.config_small_fp64(mc=14, dims=(256, 64, 48), core=(40, 16, 16), p=4, q=1)
+    ref = rbki.rbki_tucker(wl.x, wl.ranks, wl.p, wl.q, wl.seed)
+    e_ref = np.sqrt(max(ref["x_norm2"] - ref["core_norm2"], 0.0))
+    x = torch.from_numpy(wl.x.astype(np.float32)).cuda()
+    mixed = rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec="bf16")
+    f64 = rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec="fp64")
+    torch.cuda.synchronize()
+    em, e64 = _err_from_norms(mixed["norms"]), _err_from_norms(f64["norms"])
+    assert abs(em - e_ref) <= 0.01 * e_ref
+    assert abs(em - e64) <= 1e-3 * e64
+    assert mixed["info"].cpu().numpy()[6] == 0
