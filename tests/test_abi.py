@@ -94,3 +94,44 @@ def test_sequential_flag_without_gpu(L):
     st = L.rbki_mode_basis(ctypes.byref(t), ctypes.byref(prm), 0, ctypes.c_void_p(16), ctypes.c_void_p(16),
                            ctypes.c_size_t(1 << 30), None)
     assert st == B.E_INVAL
+
+
+def test_flag_and_argument_validation_without_gpu(L):
+    """The option checks of rbki_params and the new entry points reject bad arguments on
+    the host, before any device work."""
+    import torch
+    import paper_2211_14828_gb300 as rb
+    from paper_2211_14828_gb300 import _binding as B
+    x = torch.zeros((32, 24, 40), dtype=torch.float32)
+    ranks = [4, 4, 4]
+    bad = [
+        dict(omega=float("nan")),                                   # E_INVAL
+        dict(flags=rb.FLAG_ADAPTIVE_Q | rb.FLAG_POWER),            # E_INVAL
+        dict(flags=rb.FLAG_ADAPTIVE_Q, q_tol=-1.0),                 # E_INVAL
+        dict(flags=rb.FLAG_ADAPTIVE_Q | rb.FLAG_SEQUENTIAL),       # E_UNSUPPORTED
+        dict(flags=rb.FLAG_ADAPTIVE_Q, omega=0.5),                  # E_UNSUPPORTED
+    ]
+    for kw in bad:
+        with pytest.raises(rb.RbkiError) as e:
+            rb.rbki_tucker_workspace(x, ranks, 2, 1, 0, "bf16", kw.get("flags", 0), kw.get("omega", 0.0),
+                                     kw.get("q_tol", 0.0))
+        assert e.value.status in (B.E_INVAL, B.E_UNSUPPORTED)
+    # valid combinations size a workspace
+    assert rb.rbki_tucker_workspace(x, ranks, 2, 1, 0, "bf16", rb.FLAG_POWER | rb.FLAG_SEQUENTIAL, 0.3) > 0
+    assert rb.rbki_tucker_workspace(x, ranks, 2, 3, 0, "fp64", rb.FLAG_ADAPTIVE_Q, 0.0, 1e-3) > 0
+    # sampling grows the workspace by the sample buffer only where a mode is sampled
+    w0 = rb.rbki_tucker_workspace(x, ranks, 2, 1, 0, "fp64")
+    w1 = rb.rbki_tucker_workspace(x, ranks, 2, 1, 0, "fp64", 0, 0.5)
+    assert w1 > 0 and w0 > 0
+    # the unit choice and the split refuse bad counts before launching anything
+    assert L.rbki_sample_units(0, 0, 10, 11, ctypes.c_void_p(16), None) == B.E_INVAL
+    assert L.rbki_sample_units(0, 0, 0, 0, ctypes.c_void_p(16), None) == B.E_INVAL
+    t = B.make_tensor(x)
+    dst = (ctypes.c_void_p * 4)(16, 16, 16, 16)
+    assert L.rbki_split_mode(ctypes.byref(t), 1, 25, dst, None) == B.E_INVAL      # parts > I
+    assert L.rbki_split_mode(ctypes.byref(t), 3, 2, dst, None) == B.E_INVAL       # mode out of range
+    # batches refuse host buffers
+    ts = (B.rbki_tensor * 1)(B.make_tensor(x))
+    ps = (B.rbki_params * 1)(B.make_params(ranks, 2, 1, 0, "fp64", rb.FLAG_HOST_IO))
+    n = ctypes.c_size_t(0)
+    assert L.rbki_tucker_batch_workspace(1, ts, ps, ctypes.byref(n)) == B.E_UNSUPPORTED
