@@ -119,7 +119,8 @@ typedef struct {
                                         0x53414D50), key = seed); Z = Q^T Y Y^T Q on the
                                         sampled Y; the core uses all of X.  <= 0 or >= 1:
                                         no sampling.  Must be finite. */
-    double q_tol;                    /* RBKI_FLAG_ADAPTIVE_Q: fit-change threshold, >= 0 */
+    double q_tol;                    /* RBKI_FLAG_ADAPTIVE_Q: fit-change threshold, >= 0
+                                        (+inf: stop every mode at its first check, q = 1) */
 } rbki_params;
 
 /* Algorithm 2 outputs (caller-owned). */

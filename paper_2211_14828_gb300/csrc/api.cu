@@ -86,7 +86,8 @@ rbki_status validate_params(const rbki_tensor* X, const rbki_params* prm) {
         return set_error(RBKI_E_INVAL, "unknown precision");
     if (!std::isfinite(prm->omega)) return set_error(RBKI_E_INVAL, "omega must be finite");
     if (prm->flags & RBKI_FLAG_ADAPTIVE_Q) {
-        if (!std::isfinite(prm->q_tol) || prm->q_tol < 0.0) return set_error(RBKI_E_INVAL, "q_tol must be >= 0");
+        // +inf is allowed: every mode then stops at its first check (q = 1)
+        if (std::isnan(prm->q_tol) || prm->q_tol < 0.0) return set_error(RBKI_E_INVAL, "q_tol must be >= 0");
         if (prm->flags & RBKI_FLAG_POWER)
             return set_error(RBKI_E_INVAL, "adaptive q applies to the block Krylov space, not power iteration");
         if (prm->flags & RBKI_FLAG_SEQUENTIAL)
