@@ -1,5 +1,9 @@
 // C ABI of librbki: argument validation, planning, workspace carving and the per-mode
-// pipeline of Algorithms 1-2 (rBKI-TK) on the caller's stream.
+// pipeline of Algorithms 1-2 (rBKI-TK) on the caller's stream, with its variants: the
+// sequentially truncated reading (step plans on the contracted tensor), partial column
+// sampling (Sec. 3.2), the power-iteration baseline and the adaptive Krylov depth; batches
+// of independent decompositions and the divide-and-conquer split; Algorithm 3 (TR-ALS or
+// TR-SVD on the core) and the step-level entry points the tests call.
 #include <atomic>
 #include <cmath>
 #include <cstdio>
