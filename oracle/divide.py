@@ -6,7 +6,7 @@ The paper splits the frame mode of a video into consecutive subsets (250 frames 
 of 50) and decomposes each subset with the same rank-to-size ratio (rank 50 of 250 frames
 one-pass, 10 of 50 per subset).
 
-Readings (each is listed in DESIGN.md):
+Readings (where the paper is silent):
   c29 part k of K along mode n covers indices [floor(k I_n / K), floor((k+1) I_n / K)), so
       every part is non-empty when K <= I_n and sizes differ by at most one.
   c30 part k is decomposed by rBKI-TK (Algorithm 2) with seed + k, so the parts draw

@@ -14,7 +14,7 @@ Steps follow the paper's order and notation:
     step 5  U^(n) = Q U~(:, 1:R_n)
     step 6  G = X x_1 U^(1)T ... x_N U^(N)T            (HOSVD reading c1, Eq. tensorsketch)
 
-Readings (where the paper is silent; each is listed in the design doc):
+Readings (where the paper is silent):
   c2  K is orthonormalised block by block: block j+1 = orth((X X^T) Q_j) against all
       earlier blocks.  In exact arithmetic this spans exactly the space of Eq. BKspace.
   c3  deflation: a new direction is dropped when the norm of its component orthogonal

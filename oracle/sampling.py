@@ -6,7 +6,7 @@ The paper shortens X_(n) (I_n x d_n, d_n large) to Y (I_n x m, m = omega d_n) by
 column sampling and builds the block Krylov space from Y instead of X_(n); omega is the
 sampling rate (Fig. 5 sweeps omega = 0.1 .. 1; the hall video uses omega = 0.5).
 
-Readings (each is listed in DESIGN.md):
+Readings (where the paper is silent):
   c20 Algorithm 2 steps 3-5 use the products of the sampled construction (Remark 1 on Y):
       Z = Q^T Y Y^T Q, U = Q * leading eigenvectors of Z.  The core (step 6) uses all of X.
   c21 the sampling unit is a tile of 128 unfolding columns, not a single column:

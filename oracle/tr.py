@@ -4,7 +4,7 @@ Algorithm 3: (1) rBKI-TK compresses X to [[G; U^(1..N)]]; (3) TR-ALS fits a tens
 ring to the small core G; (4) each TR core is contracted with its factor over the
 physical mode: X_n = G_n x_2 U^(n) in R^{R_{n-1} x I_n x R_n}.
 
-Readings (the design doc lists them):
+Readings (where the paper is silent):
   c9   TR-ALS runs once on G and yields all N cores; ring closed by r_0 = r_N.
   c10  the initial cores are inputs (seeded, from `synth.tr_init_cores`); a sweep
        updates cores 1..N in order; each update is the exact least-squares solution of
