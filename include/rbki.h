@@ -221,8 +221,10 @@ rbki_status rbki_server_destroy(rbki_server* s);
 /* Krylov step of Algorithm 1 / Eq. BKspace on mode n: P = X_(n) (X_(n)^T Q),
  * Q: I_n x s row-major FP64 (device), P: I_n x s row-major FP64 (device).
  * prec = RBKI_PREC_*; a negative value -RBKI_PREC_BF16 / -RBKI_PREC_FP16 selects the split
- * (hi + lo) operand variant.  BF16/FP16 run on the tensor-core kernel when the shape allows
- * (contiguous extent a multiple of 8, I_n <= 512 for s <= 32), else on CUDA cores. */
+ * (hi + lo) operand variant.  BF16/FP16 run on the tensor-core kernels when the shape allows
+ * (contiguous extent a multiple of 8; I_n <= 640 at s <= 32, I_n <= 512 with the split
+ * variant; larger I_n with plain operands in two passes), else on CUDA cores.  If a bounded
+ * wait inside a tensor-core kernel expires, every entry of P is NaN. */
 rbki_status rbki_krylov_product(const rbki_tensor* X, int32_t mode, int32_t prec,
                                 const double* Q, int32_t s, double* P,
                                 void* workspace, size_t workspace_bytes, void* stream);
@@ -242,14 +244,33 @@ rbki_status rbki_krylov_product_workspace(const rbki_tensor* X, int32_t mode, in
  *   X: device, already stored in the product precision (RBKI_BF16 for RBKI_PREC_BF16,
  *      RBKI_F16 for RBKI_PREC_FP16); prec < 0 selects the split (hi + lo) variant.
  *   Q: I_n x s row-major FP64 (device), 1 <= s <= 32;  P: I_n x s row-major FP64 (device).
- * Shapes the tensor-core kernel takes (contiguous extent a multiple of 8, I_n <= 512) fit
- * the array on GB300; RBKI_E_UNSUPPORTED is returned for other shapes and RBKI_E_NOMEM if a
- * shape would ever need more scratch than the array holds.  It allocates nothing.
+ * Scratch needed: 256 + the operand image (ceil(I_n/128) 128 N 2 bytes) + the partial
+ * products (G I_n N 4 bytes), with N = s (2s when split) rounded up to 16 and G = the kernel's
+ * grid, at most the GPU's SM count.  The largest shape the kernel takes (I_n = 512, split,
+ * s = 32: N = 64) needs 19.99 MB at G = 152 (GB300), inside the array; GPUs with more than 159
+ * SMs get RBKI_E_NOMEM for it.  Shapes the tensor-core kernels do not take (contiguous extent
+ * not a multiple of 8; I_n beyond the fused step's limits) return RBKI_E_UNSUPPORTED.  It
+ * allocates nothing.  Results are bit-identical to rbki_krylov_product's (same kernels).
+ * If a bounded wait inside the kernel expires, every entry of P is NaN.
  * All calls share the array: calls that overlap on the GPU race on it and must be ordered
- * by the caller.  The first call on a device looks up the array's address
- * (cudaGetSymbolAddress, once per device); make that call before any stream capture. */
+ * by the caller.  Each call looks up the array's address on the current device
+ * (cudaGetSymbolAddress, nothing cached); the first call on a device may load the library's
+ * device code, so make it before any stream capture. */
 rbki_status rbki_krylov_product_noalloc(const rbki_tensor* X, int32_t mode, int32_t prec,
                                         const double* Q, int32_t s, double* P, void* stream);
+
+/* Diagnostics of the bounded device waits (no counterpart in the paper): the Krylov step of
+ * rbki_krylov_product (BF16/FP16 tensor-core shapes only, else RBKI_E_UNSUPPORTED) with a
+ * planted stall - the MMA-issuing thread first waits on a barrier that nothing arrives at,
+ * giving up after wait_us microseconds - so the kernel's abort path runs: every role leaves its
+ * loop, the copies and MMAs already issued are waited for (bounded), tensor memory is freed
+ * and the error word is set.  Nothing faults or hangs.  Synchronises `stream`, then returns
+ * RBKI_E_TIMEOUT when the error word is set (the expected outcome; P is then all NaN) or
+ * RBKI_OK.  Workspace as rbki_krylov_product_workspace. */
+rbki_status rbki_diag_krylov_stall(const rbki_tensor* X, int32_t mode, int32_t prec,
+                                   const double* Q, int32_t s, double* P,
+                                   void* workspace, size_t workspace_bytes,
+                                   uint32_t wait_us, void* stream);
 
 /* Algorithm 1 for one mode: the orthonormal Krylov basis Q = [Q_0..Q_q] (I_n x b,
  * row-major FP64, deflated columns are zero), b = S(q+1), S = min(R_n+p, I_n). */

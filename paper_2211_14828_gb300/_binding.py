@@ -73,6 +73,8 @@ def lib():
             "rbki_krylov_product_workspace": (st, [vp, C.c_int32, C.c_int32, C.c_int32, sz]),
             "rbki_mode_basis": (st, [vp, vp, C.c_int32, vp, vp, C.c_size_t, vp]),
             "rbki_krylov_product_noalloc": (st, [vp, C.c_int32, C.c_int32, vp, C.c_int32, vp, vp]),
+            "rbki_diag_krylov_stall": (st, [vp, C.c_int32, C.c_int32, vp, C.c_int32, vp, vp, C.c_size_t,
+                                            C.c_uint32, vp]),
             "rbki_syev": (st, [vp, C.c_int32, vp, vp, vp, C.c_size_t, vp]),
             "rbki_syev_workspace": (st, [C.c_int32, sz]),
             "rbki_sample_units": (st, [C.c_uint64, C.c_int32, C.c_int64, C.c_int64, vp, vp]),
@@ -301,6 +303,25 @@ def rbki_krylov_product(x, mode: int, q_mat, prec="fp64", workspace=None, stream
                                     C.c_void_p(P.data_ptr()), C.c_void_p(workspace.data_ptr()),
                                     C.c_size_t(workspace.numel()), stream_ptr(stream)), "rbki_krylov_product")
     return P
+
+
+def rbki_diag_krylov_stall(x, mode: int, q_mat, prec="bf16", wait_us: int = 2000, stream=None):
+    """The Krylov step with a planted stall that nothing releases (bounded by wait_us):
+    exercises the kernels' abort path.  Returns (status, P); the expected status is E_TIMEOUT
+    with P all NaN."""
+    torch = _torch()
+    t = make_tensor(x)
+    s = int(q_mat.shape[1])
+    need = C.c_size_t(0)
+    check(lib().rbki_krylov_product_workspace(C.byref(t), mode, prec_code(prec), s, C.byref(need)),
+          "rbki_krylov_product_workspace")
+    workspace = torch.empty(int(need.value), dtype=torch.uint8, device=x.device)
+    P = torch.empty((x.shape[mode], s), dtype=torch.float64, device=x.device)
+    q_c = q_mat.contiguous()
+    status = lib().rbki_diag_krylov_stall(C.byref(t), mode, prec_code(prec), C.c_void_p(q_c.data_ptr()), s,
+                                          C.c_void_p(P.data_ptr()), C.c_void_p(workspace.data_ptr()),
+                                          C.c_size_t(workspace.numel()), C.c_uint32(wait_us), stream_ptr(stream))
+    return int(status), P
 
 
 def rbki_krylov_product_noalloc(x, mode: int, q_mat, prec="bf16", stream=None):

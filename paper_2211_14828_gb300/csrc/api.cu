@@ -290,15 +290,18 @@ void carve(Plan& pl, void* ws) {
                 orth = std::max(orth, orth_scratch_doubles(m.I, j * m.S, m.S));
             m.small = c.take<double>(orth);
             m.N = (int)rup(pl.split ? 2 * m.S : m.S, 16);
-            const bool kr = tc::supported(v, tc::KRYLOV, m.N), sk = tc::supported(v, tc::SKETCH, m.N);
+            const bool kp = tc::krylov_supported(v, m.N);
+            const bool kr = kp || tc::supported(v, tc::KRYLOV, m.N), sk = tc::supported(v, tc::SKETCH, m.N);
             m.tc = pl.mixed && kr && sk;
             // two-pass Krylov step when the fused one does not fit (I_n > 640); plain operands
             m.tc2 = pl.mixed && !m.tc && !pl.split && sk && tc::supported(v, tc::TTM, m.N);
             if (m.tc || m.tc2) {
                 m.tgrid = tc::grid_size(v);
+                m.kp = m.tc && kp;
+                m.kgrid = m.kp ? tc::krylov_grid(v) : m.tgrid;
                 m.qimg = c.take<char>(tc::image_bytes_skinny(v, m.N));
                 m.omg = c.take<char>(tc::image_bytes_omega(v, m.N));
-                m.tpart = c.take<float>((size_t)m.tgrid * m.I * m.N);
+                m.tpart = c.take<float>((size_t)std::max(m.tgrid, m.kgrid) * m.I * m.N);
             } else {
                 m.Y = c.take<double>((size_t)d * m.S);
             }
@@ -396,14 +399,21 @@ rbki_status krylov_step(const Plan& pl, const ModePlan& m, const double* Q, int6
         RBKI_TRY(tc::stream_tc(tc::TTM, v, m.N, S, false, m.qimg, nullptr, nullptr, nullptr, pl.err, st, m.omg));
         RBKI_TRY(tc::stream_tc(tc::SKETCH, v, m.N, S, false, nullptr, m.omg, m.tpart, nullptr, pl.err, st));
         prof_end(tok, st);
-        return tc::reduce_parts(m.tpart, m.tgrid, m.I, m.N, S, false, out, ldo, out2, ldo2, st);
+        return tc::reduce_parts(m.tpart, m.tgrid, m.I, m.N, S, false, out, ldo, out2, ldo2, pl.err, st);
+    }
+    if (m.tc && m.kp) {
+        RBKI_TRY(tc::skinny_image(Q, ldq, m.I, S, m.N, pl.split, pl.stream_dtype == RBKI_F16, m.qimg, st));
+        int tok = prof_begin(RBKI_PROF_KRYLOV, st);
+        RBKI_TRY(tc::krylov_tc(v, m.N, S, pl.split, m.qimg, m.tpart, pl.err, st));
+        prof_end(tok, st);
+        return tc::reduce_parts(m.tpart, m.kgrid, m.I, m.N, S, pl.split, out, ldo, out2, ldo2, pl.err, st);
     }
     if (m.tc) {
         RBKI_TRY(tc::skinny_image(Q, ldq, m.I, S, m.N, pl.split, pl.stream_dtype == RBKI_F16, m.qimg, st));
         int tok = prof_begin(RBKI_PROF_KRYLOV, st);
         RBKI_TRY(tc::stream_tc(tc::KRYLOV, v, m.N, S, pl.split, m.qimg, nullptr, m.tpart, nullptr, pl.err, st));
         prof_end(tok, st);
-        return tc::reduce_parts(m.tpart, m.tgrid, m.I, m.N, S, pl.split, out, ldo, out2, ldo2, st);
+        return tc::reduce_parts(m.tpart, m.tgrid, m.I, m.N, S, pl.split, out, ldo, out2, ldo2, pl.err, st);
     }
     int tok = prof_begin(RBKI_PROF_KRYLOV, st);
     RBKI_TRY(ttm_cuda(v, Q, ldq, S, m.Y, RBKI_F64, pl.mixed, st));
@@ -427,7 +437,7 @@ rbki_status mode_basis(const Plan& pl, const ModePlan& m, int32_t* kept, cudaStr
         int tok = prof_begin(RBKI_PROF_SKETCH, st);
         RBKI_TRY(tc::stream_tc(tc::SKETCH, v, m.N, m.S, pl.split, nullptr, m.omg, m.tpart, nullptr, pl.err, st));
         prof_end(tok, st);
-        RBKI_TRY(tc::reduce_parts(m.tpart, m.tgrid, m.I, m.N, m.S, pl.split, m.Qall, m.b, nullptr, 0, st));
+        RBKI_TRY(tc::reduce_parts(m.tpart, m.tgrid, m.I, m.N, m.S, pl.split, m.Qall, m.b, nullptr, 0, pl.err, st));
     } else {
         int tok = prof_begin(RBKI_PROF_SKETCH, st);
         RBKI_TRY(omega_f64_cuda(pl.seed, m.n, m.A, m.C, m.S, m.Y, st));
@@ -523,7 +533,7 @@ static rbki_status run_modes_adaptive(const Plan& pl, const rbki_tucker_out* out
             int tok = prof_begin(RBKI_PROF_SKETCH, ms[n]);
             RBKI_TRY(tc::stream_tc(tc::SKETCH, v, m.N, m.S, pl.split, nullptr, m.omg, m.tpart, nullptr, pl.err, ms[n]));
             prof_end(tok, ms[n]);
-            RBKI_TRY(tc::reduce_parts(m.tpart, m.tgrid, m.I, m.N, m.S, pl.split, m.Qall, m.b, nullptr, 0, ms[n]));
+            RBKI_TRY(tc::reduce_parts(m.tpart, m.tgrid, m.I, m.N, m.S, pl.split, m.Qall, m.b, nullptr, 0, pl.err, ms[n]));
         } else {
             int tok = prof_begin(RBKI_PROF_SKETCH, ms[n]);
             RBKI_TRY(omega_f64_cuda(pl.seed, m.n, m.A, m.C, m.S, m.Y, ms[n]));
@@ -967,12 +977,14 @@ static rbki_status krylov_product_plan(const rbki_tensor* X, int32_t mode, int32
     if (pl.stage) pl.xs = c.take<char>((size_t)pl.numel * dtype_size(pl.stream_dtype));
     View v{nullptr, pl.stream_dtype, m.A, m.I, m.C};
     m.N = (int)rup(pl.split ? 2 * s : s, 16);
-    m.tc = pl.mixed && tc::supported(v, tc::KRYLOV, m.N);
+    m.tc = pl.mixed && (tc::krylov_supported(v, m.N) || tc::supported(v, tc::KRYLOV, m.N));
     m.tc2 = pl.mixed && !m.tc && !pl.split && tc::supported(v, tc::SKETCH, m.N) && tc::supported(v, tc::TTM, m.N);
     if (m.tc || m.tc2) {
         m.tgrid = tc::grid_size(v);
+        m.kp = m.tc && tc::krylov_supported(v, m.N);
+        m.kgrid = m.kp ? tc::krylov_grid(v) : m.tgrid;
         m.qimg = c.take<char>(tc::image_bytes_skinny(v, m.N));
-        m.tpart = c.take<float>((size_t)m.tgrid * m.I * m.N);
+        m.tpart = c.take<float>((size_t)std::max(m.tgrid, m.kgrid) * m.I * m.N);
         if (m.tc2) m.omg = c.take<char>(tc::image_bytes_omega(v, m.N));
     } else {
         m.nsplit = contract_nsplit(v);
@@ -1015,6 +1027,57 @@ rbki_status rbki_krylov_product(const rbki_tensor* X, int32_t mode, int32_t prec
         pl.xstream = X->data;
     }
     return krylov_step(pl, m, Q, s, s, P, s, nullptr, 0, st);
+}
+
+// Diagnostics of the bounded waits: the Krylov step of rbki_krylov_product with a planted
+// stall (the MMA issuer first waits on a barrier nothing arrives at, for wait_us microseconds),
+// so the abort path runs: every role leaves its loop, the copies and MMAs already issued
+// are drained, tensor memory is freed and the error word set.  Synchronises the stream and
+// reads the error word back.
+rbki_status rbki_diag_krylov_stall(const rbki_tensor* X, int32_t mode, int32_t prec, const double* Q, int32_t s,
+                                   double* P, void* workspace, size_t workspace_bytes, uint32_t wait_us,
+                                   void* stream) {
+    size_t need = 0;
+    Plan pl;
+    ModePlan m;
+    uint32_t flags = prec < 0 ? RBKI_FLAG_SPLIT : 0u;
+    int32_t pr = prec < 0 ? -prec : prec;
+    RBKI_TRY(krylov_product_plan(X, mode, pr, s, flags, pl, m, nullptr, &need));
+    if (!Q || !P) return set_error(RBKI_E_INVAL, "Q/P NULL");
+    if (wait_us == 0) return set_error(RBKI_E_INVAL, "wait_us must be positive");
+    if (!workspace || workspace_bytes < need) return set_error(RBKI_E_NOMEM, "workspace too small");
+    RBKI_TRY(krylov_product_plan(X, mode, pr, s, flags, pl, m, workspace, nullptr));
+    if (!(m.tc || m.tc2)) return set_error(RBKI_E_UNSUPPORTED, "diag stall: not a tensor-core shape");
+    cudaStream_t st = (cudaStream_t)stream;
+    RBKI_CUDA_TRY(cudaMemsetAsync(pl.err, 0, sizeof(int32_t), st));
+    if (pl.stage) {
+        RBKI_TRY(stage_cuda(X->data, X->dtype, pl.numel, pl.xs, pl.stream_dtype, pl.scal + 64, pl.scal, st));
+        pl.xstream = pl.xs;
+    } else {
+        pl.xstream = X->data;
+    }
+    const View v = mode_view(pl, m);
+    const bool f16 = pl.stream_dtype == RBKI_F16;
+    if (m.tc2) {
+        RBKI_TRY(tc::skinny_image(Q, s, m.I, s, m.N, false, f16, m.qimg, st));
+        RBKI_TRY(tc::stream_tc(tc::TTM, v, m.N, s, false, m.qimg, nullptr, nullptr, nullptr, pl.err, st, m.omg,
+                               wait_us, 1));
+        RBKI_TRY(tc::stream_tc(tc::SKETCH, v, m.N, s, false, nullptr, m.omg, m.tpart, nullptr, pl.err, st));
+        RBKI_TRY(tc::reduce_parts(m.tpart, m.tgrid, m.I, m.N, s, false, P, s, nullptr, 0, pl.err, st));
+    } else {
+        RBKI_TRY(tc::skinny_image(Q, s, m.I, s, m.N, pl.split, f16, m.qimg, st));
+        if (m.kp)
+            RBKI_TRY(tc::krylov_tc(v, m.N, s, pl.split, m.qimg, m.tpart, pl.err, st, wait_us, 1));
+        else
+            RBKI_TRY(tc::stream_tc(tc::KRYLOV, v, m.N, s, pl.split, m.qimg, nullptr, m.tpart, nullptr, pl.err, st,
+                                   nullptr, wait_us, 1));
+        RBKI_TRY(tc::reduce_parts(m.tpart, m.kp ? m.kgrid : m.tgrid, m.I, m.N, s, pl.split, P, s, nullptr, 0,
+                                  pl.err, st));
+    }
+    int32_t h = 0;
+    RBKI_CUDA_TRY(cudaMemcpyAsync(&h, pl.err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    RBKI_CUDA_TRY(cudaStreamSynchronize(st));
+    return h ? set_error(RBKI_E_TIMEOUT, "a bounded device wait expired (planted stall)") : RBKI_OK;
 }
 
 rbki_status rbki_mode_basis(const rbki_tensor* X, const rbki_params* prm, int32_t mode, double* Q,

@@ -16,14 +16,14 @@
 //        X as a K-major operand;  C == 1 ("IFAST", rows contiguous): the roles swap.
 // Warp roles (192 threads): warp 0 TMA producer, warp 1 MMA issuer + TMEM owner, warps 2-5
 // epilogue (TMEM -> registers -> BF16 operand image in shared memory / global stores).
-// Every mbarrier wait is bounded; on expiry the CTA sets an abort flag, drains, frees its
-// TMEM and reports through an error word.
+// Every mbarrier wait is bounded; on expiry the CTA raises an abort flag, every role leaves
+// its loop, the producer waits (bounded) for each copy it issued and the MMA issuer for every
+// MMA it issued, and only then is tensor memory freed; the error word is set.
 #include <cuda.h>
 
 #include "kernels.h"
 #include "tc.h"
-
-#include <cstdlib>
+#include "tc_ptx.cuh"
 
 namespace rbki {
 namespace tc {
@@ -32,130 +32,6 @@ namespace {
 constexpr int SLAB_BYTES = 32768;
 constexpr int BOX_BYTES = 16384;
 constexpr int NTHREADS = 192;
-constexpr uint32_t WAIT_LIMIT = 1u << 25;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t a) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
-}
-__device__ __forceinline__ uint32_t mbar_try(uint32_t a, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(a), "r"(parity)
-        : "memory");
-    return ok;
-}
-// bounded wait: false on timeout (abort raised) or when another role already aborted
-__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort_flag) {
-    for (uint32_t it = 0; it < WAIT_LIMIT; ++it) {
-        if (mbar_try(a, parity)) return true;
-        if (*abort_flag) return false;
-    }
-    *abort_flag = 1;
-    return false;
-}
-
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t mbar, int c0,
-                                            int c1, int c2) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
-        "l"(map), "r"(mbar), "r"(c0), "r"(c1), "r"(c2)
-        : "memory");
-}
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t mbar, int c0, int c1) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
-        "l"(map), "r"(mbar), "r"(c0), "r"(c1)
-        : "memory");
-}
-__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(mbar)
-                 : "memory");
-}
-
-__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
-                 : "memory");
-}
-__device__ __forceinline__ void tmem_relinquish() {
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-__device__ __forceinline__ void umma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
-}
-__device__ __forceinline__ void umma_commit(uint32_t mbar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
-                 : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-// 32 consecutive FP32 columns of this thread's TMEM lane
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr)
-        : "memory");
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// shared-memory matrix descriptor (sm_100 family): start, leading / stride byte offsets,
-// version 1, layout type in bits 61-63 (0 = no swizzle, 2 = 128-byte swizzle)
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo, uint32_t layout) {
-    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | ((uint64_t)layout << 61);
-}
-constexpr uint32_t LAYOUT_SW128 = 2, LAYOUT_NONE = 0;
-
-// instruction descriptor of kind::f16: D = F32, A = B = BF16 (or F16), M = 128, N
-__device__ __forceinline__ uint32_t idesc_f16(int N, bool a_mn, bool b_mn, bool fp16) {
-    const uint32_t fmt = fp16 ? 0u : 1u;
-    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((a_mn ? 1u : 0u) << 15) | ((b_mn ? 1u : 0u) << 16) |
-           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-}
-
-__device__ __forceinline__ uint32_t pack2(float a, float b, bool fp16) {
-    if (fp16) {
-        __half2 h = __floats2half2_rn(a, b);
-        return *reinterpret_cast<uint32_t*>(&h);
-    }
-    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-    return *reinterpret_cast<uint32_t*>(&h);
-}
-__device__ __forceinline__ float round_lo(float v, bool fp16) {
-    return fp16 ? __half2float(__float2half_rn(v)) : __bfloat162float(__float2bfloat16_rn(v));
-}
 
 template <int MODE, bool IFAST>
 __global__ void __launch_bounds__(NTHREADS, 1) k_stream_tc(const __grid_constant__ CUtensorMap tmap, const Params p) {
@@ -168,7 +44,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_stream_tc(const __grid_constant
     const uint32_t b_full = smem_u32(bars), b_empty = b_full + 8 * nslot;
     const uint32_t b_yfull = b_empty + 8 * nslot, b_yready = b_yfull + 16, b_ysfree = b_yready + 16;
     const uint32_t b_omfull = b_ysfree + 16, b_qfull = b_omfull + 16, b_pdone = b_qfull + 8;
-    uint32_t* tmem_slot = (uint32_t*)(bars + 2 * nslot + 10);
+    const uint32_t b_drain = b_pdone + 8, b_never = b_drain + 8;
+    uint32_t* tmem_slot = (uint32_t*)(bars + 2 * nslot + 12);
+    const uint32_t lim = p.wait_us;
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
     if (threadIdx.x == 0) {
@@ -184,6 +62,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_stream_tc(const __grid_constant
         }
         mbar_init(b_qfull, 1);
         mbar_init(b_pdone, 1);
+        mbar_init(b_drain, 1);
+        mbar_init(b_never, 1);   // nothing ever arrives: the planted stall of the timeout test
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_async_smem();
@@ -203,6 +83,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_stream_tc(const __grid_constant
     if (warp == 0) {
         // ------------------------------ TMA producer ------------------------------
         if (lane == 0) {
+            // parity of the last load issued into each slot / Omega buffer, to drain them
+            uint32_t issued = 0, par = 0, om_issued = 0, om_par = 0;
             if (MODE != SKETCH) {
                 mbar_expect_tx(b_qfull, p.qimg_bytes);
                 for (uint32_t off = 0; off < p.qimg_bytes; off += 32768) {
@@ -222,13 +104,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_stream_tc(const __grid_constant
                 }
                 if (MODE == SKETCH) {
                     const int b = (int)(k & 1);
-                    if (k >= 2 && !mbar_wait(b_ysfree + 8 * b, (uint32_t)(((k - 2) >> 1) & 1), abort_flag)) break;
+                    if (k >= 2 && !mbar_wait(b_ysfree + 8 * b, (uint32_t)(((k - 2) >> 1) & 1), abort_flag, lim)) break;
                     mbar_expect_tx(b_omfull + 8 * b, p.yimg_bytes);
                     bulk_load(Y0 + b * p.yimg_bytes, (const uint8_t*)p.omg + (size_t)t * p.yimg_bytes, p.yimg_bytes,
                               b_omfull + 8 * b);
+                    om_issued |= 1u << b;
+                    om_par = (om_par & ~(1u << b)) | ((uint32_t)((k >> 1) & 1) << b);
                 }
                 for (int s = 0; s < NS; ++s) {
-                    if (!mbar_wait(b_empty + 8 * slot, phase ^ 1, abort_flag)) break;
+                    if (!mbar_wait(b_empty + 8 * slot, phase ^ 1, abort_flag, lim)) break;
                     mbar_expect_tx(b_full + 8 * slot, SLAB_BYTES);
                     const uint32_t dst = X0 + slot * SLAB_BYTES;
                     if (!IFAST) {
@@ -238,36 +122,55 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_stream_tc(const __grid_constant
                         tma_load_2d(dst, &tmap, b_full + 8 * slot, 128 * s, ca);
                         tma_load_2d(dst + BOX_BYTES, &tmap, b_full + 8 * slot, 128 * s + 64, ca);
                     }
+                    issued |= 1u << slot;
+                    par = (par & ~(1u << slot)) | (phase << slot);
                     if (++slot == (uint32_t)nslot) { slot = 0; phase ^= 1; }
                 }
             }
+            // drain: every copy issued into this CTA's shared memory lands before it exits
+            if (MODE != SKETCH) mbar_drain(b_qfull, 0, lim);
+            for (int i = 0; i < nslot; ++i)
+                if (issued >> i & 1) mbar_drain(b_full + 8 * i, par >> i & 1, lim);
+            for (int i = 0; i < 2; ++i)
+                if (om_issued >> i & 1) mbar_drain(b_omfull + 8 * i, om_par >> i & 1, lim);
         }
     } else if (warp == 1) {
         // ------------------------------ MMA issuer ------------------------------
+        // Shared-memory descriptors are built once: a slab's or a K-step's descriptor is
+        // the base descriptor plus its byte offset in 16-byte units (shared addresses stay
+        // below 2^18, so the 14-bit address field never carries).  The issue loop then costs
+        // a few independent adds per MMA instead of a dependent chain of shifts and masks.
         if (lane == 0) {
-            const uint32_t id1 = idesc_f16(N, /*a_mn=*/!IFAST, /*b_mn=*/true, fp16);   // Y = X^T Q
-            const uint32_t id2 = idesc_f16(N, /*a_mn=*/IFAST, /*b_mn=*/true, fp16);    // P += X Y
+            const uint32_t id1 = idesc_f16(128, N, /*a_mn=*/!IFAST, /*b_mn=*/true, fp16);   // Y = X^T Q
+            const uint32_t id2 = idesc_f16(128, N, /*a_mn=*/IFAST, /*b_mn=*/true, fp16);    // P += X Y
             const uint32_t qlbo = (uint32_t)(N / 8) * 128u;
+            const uint64_t dx1 = IFAST ? sdesc(X0, 16, 1024, LAYOUT_SW128) : sdesc(X0, BOX_BYTES, 1024, LAYOUT_SW128);
+            const uint64_t dx2 = IFAST ? sdesc(X0, BOX_BYTES, 1024, LAYOUT_SW128) : sdesc(X0, 16, 1024, LAYOUT_SW128);
+            const uint64_t dq = sdesc(Q0, qlbo, 128, LAYOUT_NONE);
+            const uint64_t dy = sdesc(Y0, 128, 2048, LAYOUT_NONE);
+            const uint32_t qstep = (2u * qlbo) >> 4;     // one K = 16 step of the Q image
             bool ok = true;
-            if (MODE != SKETCH) ok = mbar_wait(b_qfull, 0, abort_flag);
+            if (p.stall) ok = mbar_wait(b_never, 0, abort_flag, lim);   // expires by design
+            if (ok && MODE != SKETCH) ok = mbar_wait(b_qfull, 0, abort_flag, lim);
             uint32_t slot = 0, phase = 0;
             for (int64_t k = 0; ok && k < my_tiles; ++k) {
                 const int b = (int)(k & 1);
                 const uint32_t slot0 = slot, phase0 = phase;
                 if (MODE != SKETCH) {
-                    if (MODE == TTM && k >= 2 && !mbar_wait(b_yready + 8 * b, (uint32_t)(((k - 2) >> 1) & 1), abort_flag)) { ok = false; break; }
+                    if (MODE == TTM && k >= 2 && !mbar_wait(b_yready + 8 * b, (uint32_t)(((k - 2) >> 1) & 1), abort_flag, lim)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t ytm = tbase + ycol0 + (uint32_t)(b * N);
                     for (int s = 0; s < NS && ok; ++s) {
-                        if (!mbar_wait(b_full + 8 * slot, phase, abort_flag)) { ok = false; break; }
+                        if (!mbar_wait(b_full + 8 * slot, phase, abort_flag, lim)) { ok = false; break; }
                         tc_fence_after();
-                        const uint32_t xs = X0 + slot * SLAB_BYTES;
+                        const uint64_t a0 = dx1 + ((slot * SLAB_BYTES) >> 4);
+                        const uint64_t b0 = dq + (uint64_t)(s * 8) * qstep;
+                        umma_f16(ytm, a0, b0, id1, s != 0 ? 1u : 0u);
 #pragma unroll
-                        for (int kk = 0; kk < 8; ++kk) {
-                            const uint64_t ad = IFAST ? sdesc(xs + (kk >> 2) * BOX_BYTES + (kk & 3) * 32, 16, 1024, LAYOUT_SW128)
-                                                      : sdesc(xs + kk * 2048, BOX_BYTES, 1024, LAYOUT_SW128);
-                            const uint64_t bd = sdesc(Q0 + (uint32_t)(s * 8 + kk) * 2u * qlbo, qlbo, 128, LAYOUT_NONE);
-                            umma_f16(ytm, ad, bd, id1, (s | kk) != 0 ? 1u : 0u);
+                        for (int kk = 1; kk < 8; ++kk) {
+                            const uint32_t ko = IFAST ? (uint32_t)(((kk >> 2) * BOX_BYTES + (kk & 3) * 32) >> 4)
+                                                      : (uint32_t)((kk * 2048) >> 4);
+                            umma_f16(ytm, a0 + ko, b0 + (uint64_t)kk * qstep, id1, 1u);
                         }
                         if (MODE == TTM) umma_commit(b_empty + 8 * slot);
                         if (++slot == (uint32_t)nslot) { slot = 0; phase ^= 1; }
@@ -277,23 +180,23 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_stream_tc(const __grid_constant
                 }
                 if (MODE != TTM) {
                     const uint32_t rb = (MODE == KRYLOV) ? b_yready + 8 * b : b_omfull + 8 * b;
-                    if (!mbar_wait(rb, (uint32_t)((k >> 1) & 1), abort_flag)) { ok = false; break; }
+                    if (!mbar_wait(rb, (uint32_t)((k >> 1) & 1), abort_flag, lim)) { ok = false; break; }
                     tc_fence_after();
-                    const uint32_t yimg = Y0 + (uint32_t)b * p.yimg_bytes;
+                    const uint64_t y0 = dy + (uint64_t)((b * p.yimg_bytes) >> 4);
                     uint32_t sl = slot0, ph = phase0;
                     for (int s = 0; s < NS; ++s) {
                         if (MODE == SKETCH) {
-                            if (!mbar_wait(b_full + 8 * sl, ph, abort_flag)) { ok = false; break; }
+                            if (!mbar_wait(b_full + 8 * sl, ph, abort_flag, lim)) { ok = false; break; }
                             tc_fence_after();
                         }
-                        const uint32_t xs = X0 + sl * SLAB_BYTES;
+                        const uint64_t a0 = dx2 + ((sl * SLAB_BYTES) >> 4);
                         const uint32_t ptm = tbase + (uint32_t)(s * N);
+                        umma_f16(ptm, a0, y0, id2, k > 0 ? 1u : 0u);
 #pragma unroll
-                        for (int kk = 0; kk < 8; ++kk) {
-                            const uint64_t ad = IFAST ? sdesc(xs + kk * 2048, BOX_BYTES, 1024, LAYOUT_SW128)
-                                                      : sdesc(xs + (kk >> 2) * BOX_BYTES + (kk & 3) * 32, 16, 1024, LAYOUT_SW128);
-                            const uint64_t bd = sdesc(yimg + kk * 256, 128, 2048, LAYOUT_NONE);
-                            umma_f16(ptm, ad, bd, id2, (k > 0 || kk > 0) ? 1u : 0u);
+                        for (int kk = 1; kk < 8; ++kk) {
+                            const uint32_t ko = IFAST ? (uint32_t)((kk * 2048) >> 4)
+                                                      : (uint32_t)(((kk >> 2) * BOX_BYTES + (kk & 3) * 32) >> 4);
+                            umma_f16(ptm, a0 + ko, y0 + (uint64_t)(kk * 16), id2, 1u);
                         }
                         umma_commit(b_empty + 8 * sl);
                         if (++sl == (uint32_t)nslot) { sl = 0; ph ^= 1; }
@@ -303,7 +206,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_stream_tc(const __grid_constant
                     if (MODE == SKETCH) { slot = sl; phase = ph; }
                 }
             }
-            if (MODE != TTM) umma_commit(b_pdone);
+            if (MODE != TTM && ok) umma_commit(b_pdone);
+            // drain: every MMA this thread issued completes before tensor memory is freed
+            umma_commit(b_drain);
+            if (!mbar_drain(b_drain, 0, lim)) *abort_flag = 1;
         }
     } else {
         // ------------------------------ epilogue (warps 2-5) ------------------------------
@@ -314,14 +220,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_stream_tc(const __grid_constant
         if (MODE != SKETCH) {
             for (int64_t k = 0; k < my_tiles; ++k) {
                 const int b = (int)(k & 1);
-                if (!mbar_wait(b_yfull + 8 * b, (uint32_t)((k >> 1) & 1), abort_flag)) break;
+                if (!mbar_wait(b_yfull + 8 * b, (uint32_t)((k >> 1) & 1), abort_flag, lim)) break;
                 tc_fence_after();
                 const uint32_t ytm = tbase + ycol0 + (uint32_t)(b * N) + lane_off;
                 tmem_ld32(ytm, v);
                 if (N > 32) tmem_ld32(ytm + 32, v + 32);
                 const int Sh = p.Sh;
                 if (p.split)
-                    for (int s = 0; s < Sh; ++s) v[s] += v[Sh + s];
+                    for (int s = 0; s < Sh; ++s) v[s] += v[N / 2 + s];
                 if (MODE == TTM) {
                     tc_fence_before();
                     mbar_arrive(b_yready + 8 * b);
@@ -351,14 +257,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_stream_tc(const __grid_constant
                             for (int s = 0; s < Sh; ++s) p.yout[a * Sh + s] = v[s];
                     }
                 } else {
-                    if (k >= 2 && !mbar_wait(b_ysfree + 8 * b, (uint32_t)(((k - 2) >> 1) & 1), abort_flag)) break;
+                    if (k >= 2 && !mbar_wait(b_ysfree + 8 * b, (uint32_t)(((k - 2) >> 1) & 1), abort_flag, lim)) break;
                     // BF16 operand image of Y (MN-major, no swizzle): element (c, n) at
                     // (n/8)*2048 + c*16 + (n%8)*2
                     uint8_t* img = smem + p.smem_y + (size_t)b * p.yimg_bytes;
                     if (p.split) {
                         for (int s = 0; s < Sh; ++s) {
                             float hi = round_lo(v[s], fp16);
-                            v[Sh + s] = v[s] - hi;
+                            v[N / 2 + s] = v[s] - hi;
                             v[s] = hi;
                         }
                     }
@@ -377,7 +283,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_stream_tc(const __grid_constant
             }
         }
         if (MODE != TTM) {
-            if (mbar_wait(b_pdone, 0, abort_flag)) {
+            if (mbar_wait(b_pdone, 0, abort_flag, lim)) {
                 tc_fence_after();
                 float* out = p.part + (size_t)blockIdx.x * p.I * N;
                 for (int s = 0; s < NS; ++s) {
@@ -405,8 +311,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_stream_tc(const __grid_constant
 // ---- operand images ----
 // B image of a skinny FP64 matrix M (rows x S, ld ldm) for GEMM1: MN-major no-swizzle,
 // element (i, n) at (i/8)*(N/8)*128 + (n/8)*128 + (i%8)*16 + (n%8)*2; rows padded to
-// rows_pad; columns n < S hold hi (or the value), S <= n < 2S the lo part when split == 1;
-// split == 2 puts the lo parts alone in columns n < S.
+// rows_pad; columns n < S hold hi (or the value), N/2 <= n < N/2 + S the lo part when
+// split == 1 (S <= N/2); split == 2 puts the lo parts alone in columns n < S.
 __global__ void k_skinny_image(const double* __restrict__ M, int64_t ldm, int64_t rows, int S,
                                int64_t rows_pad, int N, int split, int fp16, uint16_t* __restrict__ img) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -414,11 +320,12 @@ __global__ void k_skinny_image(const double* __restrict__ M, int64_t ldm, int64_
     int64_t i = e / N;
     int n = (int)(e % N);
     float val = 0.f;
-    int s = (split == 1 && n >= S) ? n - S : n;
+    const bool lo_half = split == 1 && n >= N / 2;
+    int s = lo_half ? n - N / 2 : n;
     if (i < rows && s < S) {
         double x = M[i * ldm + s];
         float hi = fp16 ? __half2float(__double2half(x)) : __bfloat162float(__double2bfloat16(x));
-        val = ((split == 1 && n >= S) || split == 2) ? (float)(x - (double)hi) : hi;
+        val = (lo_half || split == 2) ? (float)(x - (double)hi) : hi;
     }
     uint16_t bits;
     if (fp16) { __half h = __float2half_rn(val); bits = *reinterpret_cast<uint16_t*>(&h); }
@@ -429,6 +336,8 @@ __global__ void k_skinny_image(const double* __restrict__ M, int64_t ldm, int64_
 
 // Per-tile Omega images for SKETCH: tile t covers 128 unfolding columns; element (c, n) of
 // tile t at t*128*N + (n/8)*1024 + c*8 + n%8 (elements).  Columns outside the tensor are 0.
+// With `split`, image column n < S holds the hi part of Omega's column n and N/2 + s the lo
+// part of column s.
 __global__ void __launch_bounds__(256) k_omega_images(uint64_t seed, int mode, int64_t A, int64_t C, int ifast,
                                                       int64_t ctiles, int64_t tiles, int S, int N, int split,
                                                       int fp16, uint16_t* __restrict__ img) {
@@ -458,10 +367,10 @@ __global__ void __launch_bounds__(256) k_omega_images(uint64_t seed, int mode, i
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
         const int n = 8 * g + u;
-        const bool lo = split && n >= S;
-        const int s = lo ? n - S : n;
+        const bool lo = split && n >= N / 2;
+        const int s = lo ? n - N / 2 : n;
         float v = 0.f;
-        if (valid && s < S && (!lo || n < 2 * S)) {
+        if (valid && s < S) {
             if (s / 2 != have_pair) {
                 omega_pair_f32(seed, (uint32_t)mode, (uint64_t)col, (uint32_t)(s / 2), z[0], z[1]);
                 have_pair = s / 2;
@@ -480,12 +389,15 @@ __global__ void __launch_bounds__(256) k_omega_images(uint64_t seed, int mode, i
     *reinterpret_cast<uint4*>(img + (size_t)t * 128 * N + (size_t)g * 1024 + c * 8) = w;
 }
 
-// out[i*ld + s] = sum_b (part[b][i][s] + split * part[b][i][Sh + s]), FP64, fixed order:
+// out[i*ld + s] = sum_b (part[b][i][s] + split * part[b][i][N/2 + s]), FP64, fixed order:
 // 32 outputs per CTA; warp w sums partials b = w, w+8, ...; warps combined in order.
+// When the producing kernel reported an expired wait (*err != 0) its partials are
+// incomplete, and every output is NaN instead, so the result cannot pass for a valid one.
 constexpr int RED_WARPS = 8;
 __global__ void __launch_bounds__(32 * RED_WARPS) k_reduce_tc(const float* __restrict__ part, int nb, int64_t I,
                                                              int N, int Sh, int split, double* __restrict__ out,
-                                                             int64_t ld, double* __restrict__ out2, int64_t ld2) {
+                                                             int64_t ld, double* __restrict__ out2, int64_t ld2,
+                                                             const int* __restrict__ err) {
     __shared__ double acc_sh[RED_WARPS][33];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t e = (int64_t)blockIdx.x * 32 + lane;
@@ -497,7 +409,7 @@ __global__ void __launch_bounds__(32 * RED_WARPS) k_reduce_tc(const float* __res
         for (int b = w; b < nb; b += RED_WARPS) {
             const float* pb = part + ((size_t)b * I + i) * N;
             acc += (double)pb[s];
-            if (split) acc += (double)pb[Sh + s];
+            if (split) acc += (double)pb[N / 2 + s];
         }
     }
     acc_sh[w][lane] = acc;
@@ -505,6 +417,7 @@ __global__ void __launch_bounds__(32 * RED_WARPS) k_reduce_tc(const float* __res
     if (w == 0 && e < tot) {
         double t = 0.0;
         for (int k = 0; k < RED_WARPS; ++k) t += acc_sh[k][lane];
+        if (err && *err) t = __longlong_as_double(0x7ff8000000000000LL);
         const int64_t i = e / Sh;
         const int s = (int)(e % Sh);
         out[i * ld + s] = t;
@@ -597,7 +510,8 @@ rbki_status omega_images(uint64_t seed, int mode, const View& v, int S, int N, b
 }
 
 rbki_status stream_tc(int mode, const View& v, int N, int Sh, bool split, const void* qimg, const void* omg,
-                      float* part, float* yout, int* err, cudaStream_t st, void* yimg_out) {
+                      float* part, float* yout, int* err, cudaStream_t st, void* yimg_out, uint32_t wait_us,
+                      int stall) {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return set_error(RBKI_E_CUDA, "cuTensorMapEncodeTiled unavailable");
     const bool ifast = v.C == 1;
@@ -633,6 +547,8 @@ rbki_status stream_tc(int mode, const View& v, int N, int Sh, bool split, const 
     p.part = part; p.yout = yout; p.err = err;
     p.yimg_out = mode == TTM ? yimg_out : nullptr;
     p.fp16 = v.dtype == RBKI_F16 ? 1 : 0;
+    p.wait_us = wait_us ? wait_us : WAIT_US_DEFAULT;
+    p.stall = stall;
     uint32_t tm = (uint32_t)((mode == TTM ? 0 : p.NS * N) + (mode == SKETCH ? 0 : 2 * N));
     uint32_t cols = 32;
     while (cols < tm) cols <<= 1;
@@ -666,10 +582,10 @@ rbki_status stream_tc(int mode, const View& v, int N, int Sh, bool split, const 
 }
 
 rbki_status reduce_parts(const float* part, int nb, int64_t I, int N, int Sh, bool split, double* out, int64_t ld,
-                         double* out2, int64_t ld2, cudaStream_t st) {
+                         double* out2, int64_t ld2, const int* err, cudaStream_t st) {
     int64_t tot = I * Sh;
     k_reduce_tc<<<(unsigned)cdiv(tot, 32), 32 * RED_WARPS, 0, st>>>(part, nb, I, N, Sh, split ? 1 : 0, out, ld, out2,
-                                                                  ld2);
+                                                                  ld2, err);
     RBKI_LAUNCH_CHECK("k_reduce_tc");
     return RBKI_OK;
 }

@@ -12,11 +12,12 @@
 //     for this array until the process exits;
 //   * all calls share the one array: calls that overlap on the GPU (different streams,
 //     or threads without ordering) race on it; serialise them;
-//   * the first call on a device looks up the array's device address with
-//     cudaGetSymbolAddress (once per device, with that device current); make that first
-//     call before any stream capture starts.
-#include <mutex>
-
+//   * each call looks up the array's device address on the current device with
+//     cudaGetSymbolAddress (no allocation; nothing is cached, so a device reset or a new
+//     primary context leaves no stale address behind); the first call on a device may load
+//     the library's device code, so make it before any stream capture starts;
+//   * the error word is cleared at the start of each call; if a bounded wait inside the
+//     kernel expires, every entry of P is set to NaN (the partial products are incomplete).
 #include "plan.h"
 #include "tc.h"
 
@@ -26,22 +27,12 @@ namespace {
 constexpr size_t kScratchBytes = (size_t)RBKI_NOALLOC_SCRATCH_BYTES;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-std::mutex g_scratch_mu;
-void* g_scratch_dev[64] = {nullptr};
-
-// Device address of g_noalloc_scratch on the current device (looked up once per device).
+// Device address of g_noalloc_scratch on the current device.
 rbki_status scratch_address(void** out) {
-    int dev = 0;
-    RBKI_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return set_error(RBKI_E_UNSUPPORTED, "device index");
-    std::lock_guard<std::mutex> lk(g_scratch_mu);
-    if (!g_scratch_dev[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) return set_cuda_error(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
-        g_scratch_dev[dev] = p;
-    }
-    *out = g_scratch_dev[dev];
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return set_cuda_error(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+    *out = p;
     return RBKI_OK;
 }
 
@@ -67,11 +58,13 @@ extern "C" rbki_status rbki_krylov_product_noalloc(const rbki_tensor* X, int32_t
     for (int k = mode + 1; k < X->order; ++k) C *= X->dims[k];
     const View v{X->data, X->dtype, A, X->dims[mode], C};
     const int N = (int)rup(split ? 2 * s : s, 16);
-    if (!tc::supported(v, tc::KRYLOV, N))
+    // the same kernel choice as rbki_krylov_product, so the results are bit-identical
+    const bool kp = tc::krylov_supported(v, N);
+    if (!kp && !tc::supported(v, tc::KRYLOV, N))
         return set_error(RBKI_E_UNSUPPORTED, "noalloc Krylov step: shape not supported by the tensor-core kernel");
-    // scratch layout: error word | operand image | partial products
+    // scratch layout: error word | operand image | partial products (grid x I x N FP32)
     const size_t img_bytes = tc::image_bytes_skinny(v, N);
-    const int grid = tc::grid_size(v);
+    const int grid = kp ? tc::krylov_grid(v) : tc::grid_size(v);
     const size_t part_bytes = (size_t)grid * (size_t)v.I * N * sizeof(float);
     const size_t off_img = 256, off_part = rup(off_img + img_bytes, 256);
     if (off_part + part_bytes > kScratchBytes)
@@ -86,6 +79,9 @@ extern "C" rbki_status rbki_krylov_product_noalloc(const rbki_tensor* X, int32_t
     cudaStream_t st = (cudaStream_t)stream;
     RBKI_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
     RBKI_TRY(tc::skinny_image(Q, s, v.I, s, N, split, X->dtype == RBKI_F16, img, st));
-    RBKI_TRY(tc::stream_tc(tc::KRYLOV, v, N, s, split, img, nullptr, part, nullptr, err, st));
-    return tc::reduce_parts(part, grid, v.I, N, s, split, P, s, nullptr, 0, st);
+    if (kp)
+        RBKI_TRY(tc::krylov_tc(v, N, s, split, img, part, err, st));
+    else
+        RBKI_TRY(tc::stream_tc(tc::KRYLOV, v, N, s, split, img, nullptr, part, nullptr, err, st));
+    return tc::reduce_parts(part, grid, v.I, N, s, split, P, s, nullptr, 0, err, st);
 }

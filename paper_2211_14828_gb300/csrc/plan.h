@@ -35,8 +35,10 @@ struct ModePlan {
     int N = 0;                     // MMA width (includes the lo half when split)
     void* qimg = nullptr;          // BF16 operand image of Q_j
     void* omg = nullptr;           // per-tile Omega images
-    float* tpart = nullptr;        // [grid][I][N] partials
-    int tgrid = 0;
+    float* tpart = nullptr;        // [grid][I][N] partials (sized for the larger grid)
+    int tgrid = 0;                 // grid of k_stream_tc (sketch, two-pass step)
+    bool kp = false;               // fused Krylov step on the pipelined 64-column kernel
+    int kgrid = 0;                 // its grid
 };
 
 struct Plan {

@@ -28,6 +28,9 @@ struct Params {
                             // layout SKETCH consumes (the first pass of a two-pass Krylov step)
     int* err;               // error word (bounded wait expired)
     int fp16;
+    uint32_t wait_us;       // microseconds before a bounded mbarrier wait gives up
+    int stall;              // nonzero: the MMA issuer first waits on a barrier nothing arrives at
+                            // (the planted stall that exercises the timeout path)
 };
 
 bool supported(const View& v, int mode, int N);
@@ -35,16 +38,29 @@ int64_t num_tiles(const View& v);
 int grid_size(const View& v);
 size_t image_bytes_skinny(const View& v, int N);
 size_t image_bytes_omega(const View& v, int N);
-// split: 0 the values (rounded), 1 hi in columns < S and lo = value - hi in columns S..2S-1,
-// 2 the lo parts alone in columns < S
+// split: 0 the values (rounded), 1 hi in columns < S and lo = value - hi in columns
+// N/2 .. N/2+S-1 (S <= N/2), 2 the lo parts alone in columns < S
 rbki_status skinny_image(const double* M, int64_t ldm, int64_t rows, int S, int N, int split, bool fp16,
                          void* img, cudaStream_t st);
 rbki_status omega_images(uint64_t seed, int mode, const View& v, int S, int N, bool split, void* img,
                          cudaStream_t st);
 rbki_status stream_tc(int mode, const View& v, int N, int Sh, bool split, const void* qimg, const void* omg,
-                      float* part, float* yout, int* err, cudaStream_t st, void* yimg_out = nullptr);
+                      float* part, float* yout, int* err, cudaStream_t st, void* yimg_out = nullptr,
+                      uint32_t wait_us = 0, int stall = 0);
+// Fused Krylov step on the pipelined kernel (k_krylov.cu): 64-column tiles, two tiles
+// resident, GEMM1 of the next tile overlapping the epilogue of the current one.
+bool krylov_supported(const View& v, int N);
+int64_t krylov_tiles(const View& v);
+int krylov_grid(const View& v);
+// part: [krylov_grid(v)][I][N] FP32 partial products of P = X_(n) (X_(n)^T Q); reduce with
+// reduce_parts(part, krylov_grid(v), ...).  wait_us 0 = default; stall = planted stall.
+rbki_status krylov_tc(const View& v, int N, int Sh, bool split, const void* qimg, float* part, int* err,
+                      cudaStream_t st, uint32_t wait_us = 0, int stall = 0);
+// out (ld) [and out2 (ld2)] = sum of the grid's partial products, FP64, fixed order; NaN
+// everywhere when *err is nonzero (a bounded wait of the producing kernel expired, so the
+// partials are incomplete)
 rbki_status reduce_parts(const float* part, int nb, int64_t I, int N, int Sh, bool split, double* out,
-                         int64_t ld, double* out2, int64_t ld2, cudaStream_t st);
+                         int64_t ld, double* out2, int64_t ld2, const int* err, cudaStream_t st);
 
 }  // namespace tc
 }  // namespace rbki
