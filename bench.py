@@ -52,11 +52,14 @@ def parse_args():
     ap.add_argument("--parts", type=int, default=0,
                     help="divide-and-conquer: split the last mode into this many parts, decompose them as a batch")
     ap.add_argument("--power", action="store_true", help="power-iteration baseline instead of block Krylov")
+    ap.add_argument("--refine", action="store_true", help="FP32 Rayleigh-Ritz refinement of the mixed factors")
     ap.add_argument("--q-tol", type=float, default=None,
                     help="adaptive Krylov depth: stop a mode when its fit changes by at most this (q is the bound)")
     ap.add_argument("--omega", type=float, default=0.0,
                     help="column sampling rate of the Krylov construction (0 < omega < 1)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serve-compare", action="store_true",
+                    help="skip the bounded served-stream measurement of the default line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
     return ap.parse_args()
@@ -293,6 +296,8 @@ def run_ours(args):
     flags = rb.FLAG_SEQUENTIAL if args.sequential else 0
     if args.power:
         flags |= rb.FLAG_POWER
+    if args.refine:
+        flags |= rb.FLAG_REFINE_FP32
     if args.q_tol is not None:
         flags |= rb.FLAG_ADAPTIVE_Q
     qtol = args.q_tol or 0.0
@@ -469,6 +474,29 @@ def run_ours(args):
         rel64 = float(np.sqrt(max(n64[0] - n64[1], 0.0) / n64[0]))
         fp64_cmp = {"ms_per_step": round(t64 * 1e3, 2), "rel_err": rel64,
                     "mixed_rel_err": rel_err, "mixed_vs_fp64": (rel_err - rel64) / rel64}
+        if not (flags & rb.FLAG_REFINE_FP32) and args.q_tol is None:
+            # the FP32 Rayleigh-Ritz refinement of the mixed factors: the Ritz values against the
+            # FP64 path's (largest deviation relative to lambda_1, over every Krylov-path mode)
+            # with and without it, its reconstruction error and one refined decomposition alone
+            orf = rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec=prec, flags=flags | rb.FLAG_REFINE_FP32,
+                                 omega=args.omega)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec=prec, flags=flags | rb.FLAG_REFINE_FP32,
+                           omega=args.omega, workspace=orf["workspace"], out=orf)
+            torch.cuda.synchronize()
+            trf = time.perf_counter() - t0
+            nrf = orf["norms"].cpu().numpy()
+            dev_plain, dev_ref = 0.0, 0.0
+            for n in range(len(dims)):
+                l64 = o64["eigvals"][n].cpu().numpy()
+                dev_plain = max(dev_plain, float(np.max(np.abs(out["eigvals"][n].cpu().numpy() - l64)) / l64[0]))
+                dev_ref = max(dev_ref, float(np.max(np.abs(orf["eigvals"][n].cpu().numpy() - l64)) / l64[0]))
+            fp64_cmp["refine_fp32"] = {"single_decomposition_ms": round(trf * 1e3, 4),
+                                       "rel_err": float(np.sqrt(max(nrf[0] - nrf[1], 0.0) / nrf[0])),
+                                       "ritz_dev_vs_fp64_unrefined": dev_plain,
+                                       "ritz_dev_vs_fp64_refined": dev_ref}
+            del orf
         del o64
 
     seq_cmp = None
@@ -491,6 +519,14 @@ def run_ours(args):
                    "rel_err": float(np.sqrt(max(nsq[0] - nsq[1], 0.0) / nsq[0])),
                    "bytes_per_decomposition": sq_bytes}
         del osq
+
+    serve_cmp = None
+    if rank == 0 and world == 1 and not args.no_serve_compare and args.workload == "tucker512" and not args.size:
+        # the served-stream half of the metric, bounded: 1024 requests of the stream
+        res, _ = serve_measure(1024, args.slots, 128, (0.8,))
+        serve_cmp = {k: res[k] for k in ("requests", "slots", "solves_per_s", "launches_per_request",
+                                          "x_pass_gbs", "latency", "fp64_compare", "rel_err_mixed")}
+        serve_cmp["unit"] = "solves/s"
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -516,7 +552,7 @@ def run_ours(args):
                        "bytes_per_step": step_bytes, "l2": "inputs larger than L2 (no flush)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roof, "breakdown": breakdown, "rel_err": rel_err, "fp64_compare": fp64_cmp,
-            "sequential_compare": seq_cmp,
+            "sequential_compare": seq_cmp, "serve_compare": serve_cmp,
             "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "cpu_baseline": cpu,
         }
         print(json.dumps(line))
@@ -751,21 +787,19 @@ def run_divide(args):
         }))
 
 
-def run_serve(args):
-    """Served stream: --requests rBKI-TK requests (3rd order, dims in [32, 256], ranks in
-    [4, 32], q in {1, 2, 3}, p = 5, SNR in [5, 25] dB, BF16 products) through the server.
-    value = closed-loop solves/s; p50/p99 latency under Poisson arrivals at 0.5/0.8/0.95 of
-    that rate; the FP64 GPU path on a prefix of the same stream for the matched-error check."""
+def serve_measure(n_requests, slots, fp64_prefix, rhos, warmup=1):
+    """The served stream (Sec. 4 workloads as a request stream): n_requests rBKI-TK requests
+    (3rd order, dims in [32, 256], ranks in [4, 32], q in {1, 2, 3}, p = 5, SNR in [5, 25] dB,
+    BF16 products) through the server.  Closed-loop solves/s (every request submitted at
+    once); p50/p99 latency under Poisson arrivals at rho x that rate; the FP64 GPU path on a
+    prefix of the same stream, with the largest relative deviation of the mixed path's
+    reconstruction error from the FP64 path's (matched error: <= 1%)."""
     import numpy as np
     import torch
     import synth
     import paper_2211_14828_gb300 as rb
     from paper_2211_14828_gb300 import _binding as B
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    if world > 1:
-        raise SystemExit("--workload serve runs on one GPU")
-    torch.cuda.set_device(0)
-    reqs = synth.serve_stream(n_requests=args.requests, seed=5000)
+    reqs = synth.serve_stream(n_requests=n_requests, seed=5000)
     items, outs, x32 = [], [], []
     numel_passes = 0
     for i, r in enumerate(reqs):
@@ -773,22 +807,22 @@ def run_serve(args):
         items.append((x, rk, p, q, sd))
         outs.append(B.alloc_outputs(x.shape, rk, x.device))
         numel_passes += serve_passes(x.shape, rk, p, q) * x.numel()
-        if i < args.fp64_requests:
+        if i < fp64_prefix:
             x32.append(x.float())
     torch.cuda.synchronize()
     budget = 8 << 30
-    launches0 = rb.rbki_kernel_launches()
-    with rb.RbkiServer(0, mem_budget=budget, max_slots=args.slots) as srv:
-        nw = min(len(items), max(args.warmup, 1) * args.slots)
+    res = {}
+    with rb.RbkiServer(0, mem_budget=budget, max_slots=slots) as srv:
+        nw = min(len(items), max(warmup, 1) * slots)
         _serve_closed_loop(rb, srv, items[:nw], outs[:nw], "bf16")
         clocks = ClockSampler()
         clocks.start()
-        launches0 = rb.rbki_kernel_launches()
         torch.cuda.synchronize()
+        launches0 = rb.rbki_kernel_launches()
         secs, lat, status = _serve_closed_loop(rb, srv, items, outs, "bf16")
         torch.cuda.synchronize()
         launches = rb.rbki_kernel_launches() - launches0
-        clk = clocks.stop()
+        res["clocks"] = clocks.stop()
         assert all(s == 0 for s in status), "served request failed"
         sat = len(items) / secs
         errs_mixed = []
@@ -797,46 +831,68 @@ def run_serve(args):
             errs_mixed.append(float(np.sqrt(max(n[0] - n[1], 0.0) / n[0])))
         latency = {"closed_loop": {"p50_ms": round(1e3 * float(np.percentile(lat, 50)), 3),
                                    "p99_ms": round(1e3 * float(np.percentile(lat, 99)), 3)}}
-        for rho in (0.5, 0.8, 0.95):
+        for rho in rhos:
             t, l = _serve_poisson(rb, srv, items, outs, "bf16", rho * sat, seed=int(rho * 1000))
             latency[f"poisson_rho_{rho}"] = {"offered_per_s": round(rho * sat, 1),
                                              "achieved_per_s": round(len(items) / t, 1),
                                              "p50_ms": round(1e3 * float(np.percentile(l, 50)), 3),
                                              "p99_ms": round(1e3 * float(np.percentile(l, 99)), 3)}
-        # FP64 GPU path on a prefix of the same stream
         f64 = None
         if x32:
             its = [(x32[i],) + items[i][1:] for i in range(len(x32))]
             o64 = [B.alloc_outputs(x.shape, it[1], x.device) for x, it in zip(x32, its)]
             secs64, lat64, st64 = _serve_closed_loop(rb, srv, its, o64, "fp64")
+            assert all(s == 0 for s in st64), "served FP64 request failed"
             e64 = []
             for o in o64:
                 n = o["norms"].cpu().numpy()
                 e64.append(float(np.sqrt(max(n[0] - n[1], 0.0) / n[0])))
             dev = [abs(a - b) / b for a, b in zip(errs_mixed[:len(e64)], e64)]
-            f64 = {"requests": len(its), "solves_per_s": round(len(its) / secs64, 1),
-                   "p50_ms": round(1e3 * float(np.percentile(lat64, 50)), 3),
-                   "p99_ms": round(1e3 * float(np.percentile(lat64, 99)), 3),
-                   "mixed_solves_per_s_same_prefix": None,
+            secs_m, lat_m, _ = _serve_closed_loop(rb, srv, items[:len(its)], outs[:len(its)], "bf16")
+            f64 = {"requests": len(its), "fp64_solves_per_s": round(len(its) / secs64, 1),
+                   "fp64_p50_ms": round(1e3 * float(np.percentile(lat64, 50)), 3),
+                   "fp64_p99_ms": round(1e3 * float(np.percentile(lat64, 99)), 3),
+                   "mixed_solves_per_s": round(len(its) / secs_m, 1),
+                   "mixed_p50_ms": round(1e3 * float(np.percentile(lat_m, 50)), 3),
+                   "mixed_p99_ms": round(1e3 * float(np.percentile(lat_m, 99)), 3),
                    "max_rel_err_dev_mixed_vs_fp64": max(dev), "all_within_1pct": bool(max(dev) <= 0.01)}
-            secs_m, _, _ = _serve_closed_loop(rb, srv, items[:len(its)], outs[:len(its)], "bf16")
-            f64["mixed_solves_per_s_same_prefix"] = round(len(its) / secs_m, 1)
+    res.update({
+        "requests": len(items), "slots": slots, "budget_bytes": budget,
+        "solves_per_s": round(sat, 2), "closed_loop_s": round(secs, 4),
+        "x_pass_bytes": int(2 * numel_passes), "x_pass_gbs": round(2 * numel_passes / secs / 1e9, 2),
+        "launches_per_request": round(launches / len(items), 1), "gpu_launches": int(launches),
+        "latency": latency, "fp64_compare": f64,
+        "rel_err_mixed": {"median": float(np.median(errs_mixed)), "max": float(np.max(errs_mixed))},
+    })
+    return res, reqs
+
+
+def run_serve(args):
+    """Served stream: --requests requests through the server (see serve_measure).  value =
+    closed-loop solves/s; p50/p99 latency under Poisson arrivals at 0.5/0.8/0.95 of that rate;
+    the FP64 GPU path on a prefix of the same stream for the matched-error check."""
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:
+        raise SystemExit("--workload serve runs on one GPU")
+    torch.cuda.set_device(0)
+    res, reqs = serve_measure(args.requests, args.slots, args.fp64_requests, (0.5, 0.8, 0.95), args.warmup)
     cpu = None
     if not args.no_cpu_baseline:
         cpu = serve_cpu_baseline(reqs)
     line = {
         "metric": "served rBKI-TK solves/s (closed loop; p50/p99 latency under Poisson arrivals)",
-        "value": round(sat, 2), "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": args.warmup,
-        "ms_per_step": round(secs * 1e3, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16", "data": "synthetic",
-        "config": {"workload": f"serve: {len(items)} requests, dims U[32,256]^3, ranks U[4,32], p=5, q in {{1,2,3}}, "
-                               f"SNR U[5,25] dB, BF16 products", "slots": args.slots, "budget_bytes": budget,
-                   "x_pass_bytes": int(2 * numel_passes),
-                   "x_pass_gbs": round(2 * numel_passes / secs / 1e9, 2),
+        "value": res["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": args.warmup,
+        "ms_per_step": round(res["closed_loop_s"] * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": f"serve: {res['requests']} requests, dims U[32,256]^3, ranks U[4,32], p=5, "
+                               f"q in {{1,2,3}}, SNR U[5,25] dB, BF16 products", "slots": args.slots,
+                   "budget_bytes": res["budget_bytes"], "x_pass_bytes": res["x_pass_bytes"],
+                   "x_pass_gbs": res["x_pass_gbs"],
                    "l2": "requests are mostly smaller than L2; throughput is latency-bound"},
-        "latency": latency, "fp64_compare": f64,
-        "rel_err_mixed": {"median": float(np.median(errs_mixed)), "max": float(np.max(errs_mixed))},
-        "e2e": None, "gpu_launches": int(launches), "clocks": clk, "cpu_baseline": cpu,
+        "latency": res["latency"], "fp64_compare": res["fp64_compare"], "rel_err_mixed": res["rel_err_mixed"],
+        "launches_per_request": res["launches_per_request"],
+        "e2e": None, "gpu_launches": res["gpu_launches"], "clocks": res["clocks"], "cpu_baseline": cpu,
     }
     print(json.dumps(line))
 

@@ -87,6 +87,16 @@ enum {
                                       rank product r_{N-1} r_0; tr_init is not read (may be
                                       NULL); fits[0] = the ring's fit to G, the rest NaN.
                                       Unfolding rows r_{n-1} S_n must be <= 256 */
+    RBKI_FLAG_REFINE_FP32 = 256u,  /* Rayleigh-Ritz refinement of every Krylov-path factor: one
+                                      more pass of width R, P = X_(n) X_(n)^T U with FP32-accurate
+                                      products (the split hi + lo operand on the tensor cores, or
+                                      FP32-accumulating CUDA cores when the shape does not fit),
+                                      then Z_r = U^T P (FP64), its eigenvectors W and U <- U W,
+                                      eigvals <- the refined Ritz values.  U keeps its span, so
+                                      the core's norm and the reconstruction error do not change;
+                                      the Ritz values and the individual factor columns lose the
+                                      BF16 rounding of the Krylov products.  Not with
+                                      RBKI_FLAG_ADAPTIVE_Q */
     RBKI_FLAG_ADAPTIVE_Q = 32u     /* adaptive Krylov depth: q is the bound; after block j the
                                       mode's fit F_j = 1 - sqrt(|X|^2 - sum of its R_n Ritz
                                       values)/|X| is evaluated, and the mode stops at the first

@@ -171,11 +171,27 @@ def rayleigh_ritz(xn: np.ndarray, q_basis: np.ndarray, r: int):
     return sign_fix(u), lam[:r], z
 
 
+def refine_rr(a: np.ndarray, u: np.ndarray):
+    """Rayleigh-Ritz refinement of a factor (the precision pattern's final step, reading c17):
+    Z_r = U^T A A^T U from a fresh product with the unfolding A, its eigenvectors W
+    (descending), U' = U W with the sign rule, and the Ritz values lambda'.  U' spans the
+    same space as U, so the projector U U^T (and the reconstruction error) is unchanged; in
+    exact arithmetic, when U already holds eigenvectors of the mode's Rayleigh quotient, Z_r
+    is diagonal and U' = U.  A path whose Z carries product rounding gets its Ritz values
+    and vectors recomputed from accurate products."""
+    y = u.T @ a
+    zr = y @ y.T
+    lam, vec = np.linalg.eigh(zr)
+    order = np.argsort(-lam, kind="stable")
+    return sign_fix(u @ vec[:, order]), lam[order]
+
+
 def krylov_mode(xn: np.ndarray, x: np.ndarray, n: int, s: int, r: int, q: int, seed: int, omega: float,
-                tau: float = TAU_DEFLATE, variant: str = "krylov", q_tol=None):
+                tau: float = TAU_DEFLATE, variant: str = "krylov", q_tol=None, refine: bool = False):
     """Algorithms 1-2 for a Krylov-path mode of tensor x (unfolding xn): (U, lambda, kept, q used).
     0 < omega < 1: the Krylov space and Z come from the sampled Y (oracle.sampling).
-    variant "power": the power-iteration basis; q_tol: adaptive depth with q as the bound."""
+    variant "power": the power-iteration basis; q_tol: adaptive depth with q as the bound;
+    refine: the Rayleigh-Ritz refinement of U on the same data (refine_rr)."""
     if 0.0 < omega < 1.0:
         if q_tol is not None:
             raise ValueError("adaptive q with column sampling is not defined")
@@ -192,14 +208,18 @@ def krylov_mode(xn: np.ndarray, x: np.ndarray, n: int, s: int, r: int, q: int, s
         return u, lam, k, qu
     qb = power_basis(a, om, q, tau) if variant == "power" else np.concatenate(rbki(a, om, q, tau), axis=1)
     u, lam, _ = rayleigh_ritz(a, qb, r)
+    if refine:
+        u, lam = refine_rr(a, u)
     return u, lam, qb.shape[1], q
 
 
 def rbki_tucker(x: np.ndarray, ranks: Sequence[int], p: int, q: int, seed: int,
-                tau: float = TAU_DEFLATE, omega: float = 1.0, variant: str = "krylov", q_tol=None) -> Dict:
+                tau: float = TAU_DEFLATE, omega: float = 1.0, variant: str = "krylov", q_tol=None,
+                refine: bool = False) -> Dict:
     """Algorithm 2 (rBKI-TK), HOSVD reading: every mode sketches the original X.
     0 < omega < 1: partial column sampling of the Krylov construction (oracle.sampling).
-    variant "power": the power-iteration baseline; q_tol: adaptive depth, q the bound."""
+    variant "power": the power-iteration baseline; q_tol: adaptive depth, q the bound;
+    refine: Rayleigh-Ritz refinement of each Krylov-path factor (refine_rr)."""
     x = np.asarray(x, dtype=np.float64)
     plan = sketch_plan(x.shape, ranks, p, q, variant)
     factors, eigvals, kept, paths, q_used = [], [], [], [], []
@@ -213,7 +233,7 @@ def rbki_tucker(x: np.ndarray, ranks: Sequence[int], p: int, q: int, seed: int,
             kept.append(x.shape[n])
             q_used.append(0)
         else:
-            u, lam, k, qu = krylov_mode(xn, x, n, s, ranks[n], q, seed, omega, tau, variant, q_tol)
+            u, lam, k, qu = krylov_mode(xn, x, n, s, ranks[n], q, seed, omega, tau, variant, q_tol, refine)
             kept.append(k)
             q_used.append(qu)
         factors.append(u)

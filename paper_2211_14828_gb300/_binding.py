@@ -20,6 +20,7 @@ F64, F32, BF16, F16 = 0, 1, 2, 3
 PREC_FP64, PREC_BF16, PREC_FP16 = 0, 1, 2
 FLAG_HOST_IO, FLAG_SPLIT, FLAG_SERIAL_MODES, FLAG_SEQUENTIAL, FLAG_POWER, FLAG_ADAPTIVE_Q, FLAG_TR_SVD, FLAG_ASYNC = \
     1, 2, 4, 8, 16, 32, 64, 128
+FLAG_REFINE_FP32 = 256
 
 
 class rbki_tensor(C.Structure):

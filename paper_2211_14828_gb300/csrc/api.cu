@@ -98,6 +98,8 @@ rbki_status validate_params(const rbki_tensor* X, const rbki_params* prm) {
             return set_error(RBKI_E_UNSUPPORTED, "adaptive q with the sequential reading");
         if (prm->omega > 0.0 && prm->omega < 1.0)
             return set_error(RBKI_E_UNSUPPORTED, "adaptive q with column sampling");
+        if (prm->flags & RBKI_FLAG_REFINE_FP32)
+            return set_error(RBKI_E_UNSUPPORTED, "refinement with adaptive q");
     }
     for (int n = 0; n < X->order; ++n) {
         if (prm->ranks[n] < 1 || prm->ranks[n] > X->dims[n])
@@ -305,6 +307,28 @@ void carve(Plan& pl, void* ws) {
             } else {
                 m.Y = c.take<double>((size_t)d * m.S);
             }
+            if (pl.flags & RBKI_FLAG_REFINE_FP32) {
+                const size_t IR = (size_t)m.I * m.R;
+                m.refine = true;
+                m.U0 = c.take<double>(IR);
+                m.Pr = c.take<double>(IR);
+                m.Zr = c.take<double>((size_t)m.R * m.R);
+                m.Wr = c.take<double>((size_t)m.R * m.R);
+                m.lamr = c.take<double>((size_t)m.R);
+                m.rsyev = c.take<double>(syev_scratch_doubles(m.R));
+                m.rN = (int)rup(2 * m.R, 16);
+                m.rkp = pl.mixed && tc::krylov_supported(v, m.rN);
+                m.rtc = m.rkp || (pl.mixed && tc::supported(v, tc::KRYLOV, m.rN));
+                if (m.rtc) {
+                    m.rgrid = m.rkp ? tc::krylov_grid(v) : tc::grid_size(v);
+                    m.rimg = c.take<char>(tc::image_bytes_skinny(v, m.rN));
+                    m.rpart = c.take<float>((size_t)m.rgrid * m.I * m.rN);
+                } else {
+                    m.rnsplit = contract_nsplit(v);
+                    m.rY = c.take<double>((size_t)d * m.R);
+                    m.rsplit = c.take<double>((size_t)m.rnsplit * m.I * m.R);
+                }
+            }
         }
     }
     // core chain ping-pong buffers (FP64)
@@ -469,6 +493,33 @@ rbki_status mode_basis(const Plan& pl, const ModePlan& m, int32_t* kept, cudaStr
     return RBKI_OK;
 }
 
+// Rayleigh-Ritz refinement of a Krylov-path factor (RBKI_FLAG_REFINE_FP32): P = X X^T U0 at
+// width R with FP32-accurate products, Z_r = U0^T P in FP64, its eigenvectors W (descending),
+// U = U0 W with the sign rule; the refined Ritz values land in m.lamr.
+static rbki_status refine_factor(const Plan& pl, const ModePlan& m, double* U, cudaStream_t st) {
+    const View v = mode_view(pl, m);
+    const int R = m.R;
+    RBKI_TRY(copy_f64_cuda(U, m.U0, (int64_t)m.I * R, st));
+    int tok = prof_begin(RBKI_PROF_KRYLOV, st);
+    if (m.rtc) {
+        RBKI_TRY(tc::skinny_image(m.U0, R, m.I, R, m.rN, 1, pl.stream_dtype == RBKI_F16, m.rimg, st));
+        if (m.rkp)
+            RBKI_TRY(tc::krylov_tc(v, m.rN, R, true, m.rimg, m.rpart, pl.err, st));
+        else
+            RBKI_TRY(tc::stream_tc(tc::KRYLOV, v, m.rN, R, true, m.rimg, nullptr, m.rpart, nullptr, pl.err, st));
+        prof_end(tok, st);
+        RBKI_TRY(tc::reduce_parts(m.rpart, m.rgrid, m.I, m.rN, R, true, m.Pr, R, nullptr, 0, pl.err, st));
+    } else {
+        RBKI_TRY(ttm_cuda(v, m.U0, R, R, m.rY, RBKI_F64, pl.mixed, st));
+        RBKI_TRY(contract_cuda(v, m.rY, RBKI_F64, R, pl.mixed, m.rsplit, m.rnsplit, m.Pr, R, nullptr, 0, st));
+        prof_end(tok, st);
+    }
+    RBKI_TRY(atb_cuda(m.U0, R, R, m.Pr, R, R, m.I, m.part, m.Zr, R, st));
+    RBKI_TRY(symmetrize_cuda(m.Zr, R, st));
+    RBKI_TRY(syev_top_cuda(m.Zr, R, R, m.lamr, m.Wr, m.rsyev, st));
+    return form_factor_cuda(m.U0, R, m.I, m.Wr, R, R, R, U, st);
+}
+
 // Algorithm 2 steps 2-5 for mode n: U^(n) and its Ritz values
 rbki_status mode_factor(const Plan& pl, const ModePlan& m, double* U, double* eigvals,
                         int32_t* info, cudaStream_t st) {
@@ -497,8 +548,9 @@ rbki_status mode_factor(const Plan& pl, const ModePlan& m, double* U, double* ei
         // step 4: leading eigenvectors of Z; step 5: U = Q U~(:, 1:R)
         RBKI_TRY(syev_top_cuda(m.Z, m.b, m.R, m.eval, m.evec, m.syev_ws, st));
         RBKI_TRY(form_factor_cuda(m.Qall, m.b, m.I, m.evec, m.b, m.R, m.R, U, st));
+        if (m.refine) RBKI_TRY(refine_factor(pl, m, U, st));
     }
-    if (eigvals) RBKI_TRY(copy_f64_cuda(m.eval, eigvals, m.R, st));
+    if (eigvals) RBKI_TRY(copy_f64_cuda(m.refine ? m.lamr : m.eval, eigvals, m.R, st));
     if (info) RBKI_TRY(fill_i32_cuda(info + pl.N + m.n, m.gram ? 1 : 0, 1, st));
     return RBKI_OK;
 }

@@ -413,13 +413,18 @@ template <> __device__ __forceinline__ float chain_rcp<float>(float a) { return 
 #endif
 
 // One inverse-iteration solve y <- (T - mu I)^{-1} y, unnormalised; returns |y|^2.
+// When both pivot candidates of a step are below `tiny` (a decoupled block: T's off-diagonal
+// is negligible there), the diagonal one is clamped to +-tiny instead of pivoting on the
+// negligible off-diagonal entry, so no multiplier exceeds 1 and no reciprocal 1 / tiny.  If
+// several clamped pivots in a row still overflow the sum of squares, y is rescaled by its
+// largest entry (a power-of-two factor of it) and the sum taken again.
 template <typename T>
 __host__ __device__ T invit_solve(const T* d, const T* e, int n, T mu, T tiny, T* rdd, T* du, T* du2, T* y,
-                                  int stride, int ystride) {
+                                       int stride, int ystride) {
     T a = d[0] - mu, b = n > 1 ? e[0] : (T)0, yi = y[0];
     for (int i = 0; i + 1 < n; ++i) {
         const T c = e[i], dn = d[i + 1] - mu, f = (i + 2 < n) ? e[i + 1] : (T)0, yn = y[(i + 1) * ystride];
-        if (fabs(a) >= fabs(c)) {
+        if (fabs(a) >= fabs(c) || fabs(c) < tiny) {
             if (fabs(a) < tiny) a = a >= (T)0 ? tiny : -tiny;
             const T r = chain_rcp(a), m = c * r;
             rdd[i * stride] = r; du[i * stride] = b; du2[i * stride] = 0; y[i * ystride] = yi;
@@ -440,6 +445,20 @@ __host__ __device__ T invit_solve(const T* d, const T* e, int n, T mu, T tiny, T
         ss += vv * vv;
         y2 = y1;
         y1 = vv;
+    }
+    const T big = sizeof(T) == 8 ? (T)1e300 : (T)1e36;
+    if (!(ss <= big)) {
+        T m = 0;
+        for (int i = 0; i < n; ++i) m = fmax(m, fabs(y[i * ystride]));
+        int ex = 0;
+        frexp(m, &ex);
+        const T sc = ldexp((T)1, -ex);   // exact power-of-two scaling: |y| <= 1 afterwards
+        ss = 0;
+        for (int i = 0; i < n; ++i) {
+            const T v = y[i * ystride] * sc;
+            y[i * ystride] = v;
+            ss += v * v;
+        }
     }
     return ss;
 }

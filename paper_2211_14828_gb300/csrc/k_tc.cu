@@ -471,17 +471,13 @@ int64_t num_tiles(const View& v) { return v.C > 1 ? v.A * cdiv(v.C, 128) : cdiv(
 
 size_t image_bytes_skinny(const View& v, int N) { return (size_t)cdiv(v.I, 128) * 128 * N * 2; }
 size_t image_bytes_omega(const View& v, int N) { return (size_t)num_tiles(v) * 128 * N * 2; }
-// One persistent CTA per SM, less RBKI_TC_SM_RESERVE SMs (environment, default 0): with
-// decompositions in flight, single-CTA kernels of other streams may hold an SM's shared
-// memory, and a persistent CTA that cannot start there delays its whole launch.
+// One persistent CTA per SM.
 int grid_size(const View& v) {
     static const int sms = [] {
         int dev = 0, n = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        int reserve = 0;
-        if (const char* e = std::getenv("RBKI_TC_SM_RESERVE")) reserve = std::atoi(e);
-        return std::max(1, n - std::max(0, std::min(reserve, n - 1)));
+        return std::max(1, n);
     }();
     return (int)std::min<int64_t>(num_tiles(v), sms);
 }

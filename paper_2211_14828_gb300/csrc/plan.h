@@ -39,6 +39,21 @@ struct ModePlan {
     int tgrid = 0;                 // grid of k_stream_tc (sketch, two-pass step)
     bool kp = false;               // fused Krylov step on the pipelined 64-column kernel
     int kgrid = 0;                 // its grid
+    // Rayleigh-Ritz refinement of U (RBKI_FLAG_REFINE_FP32)
+    bool refine = false;
+    bool rtc = false, rkp = false; // refinement product on the tensor cores (split operand) / on
+                                   // the pipelined kernel
+    int rN = 0, rgrid = 0, rnsplit = 1;
+    double* U0 = nullptr;          // I x R: the unrefined factor
+    double* Pr = nullptr;          // I x R: X X^T U0
+    double* Zr = nullptr;          // R x R
+    double* Wr = nullptr;          // R x R eigenvectors of Zr
+    double* lamr = nullptr;        // R refined Ritz values
+    double* rsyev = nullptr;       // eigensolver scratch for R
+    void* rimg = nullptr;          // split operand image of U0 (tensor cores)
+    float* rpart = nullptr;        // [rgrid][I][rN] partials (tensor cores)
+    double* rY = nullptr;          // [A][R][C] X x_n U0^T (CUDA cores)
+    double* rsplit = nullptr;      // [rnsplit][I][R] partials (CUDA cores)
 };
 
 struct Plan {

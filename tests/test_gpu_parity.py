@@ -73,6 +73,26 @@ def test_syev(rb, n):
     np.testing.assert_allclose(V.T @ V, np.eye(n), atol=1e-13)
 
 
+@pytest.mark.parametrize("n", [8, 20, 120])
+@pytest.mark.parametrize("off", [0.0, 1e-20, 1e-16, 1e-13, 1e-6])
+def test_syev_near_diagonal(rb, n, off):
+    """A diagonal matrix plus a symmetric perturbation of size `off`: the shape of a Rayleigh
+    quotient on vectors that are already Ritz vectors.  The FP32 tridiagonal then splits into
+    blocks decoupled by negligible off-diagonal entries, where inverse iteration meets a pair
+    of pivot candidates both below its tiny threshold."""
+    g = np.random.default_rng(n)
+    lam = np.sort(g.uniform(1, 100, n))[::-1]
+    e = g.standard_normal((n, n)) * off
+    a = np.diag(lam) + (e + e.T) / 2
+    w, V = rb.rbki_syev(torch.from_numpy(a).cuda())
+    w, V = w.cpu().numpy(), V.cpu().numpy()
+    assert np.all(np.isfinite(w)) and np.all(np.isfinite(V))
+    wr = np.sort(np.linalg.eigvalsh(a))[::-1]
+    np.testing.assert_allclose(w, wr, rtol=1e-12, atol=1e-12 * wr[0])
+    np.testing.assert_allclose(a @ V, V * w[None, :], atol=1e-11 * wr[0])
+    np.testing.assert_allclose(V.T @ V, np.eye(n), atol=1e-13)
+
+
 def _sym_with_spectrum(lam, seed):
     g = np.random.default_rng(seed)
     q, r = np.linalg.qr(g.standard_normal((len(lam), len(lam))))
