@@ -78,11 +78,11 @@ def make_workload(name, mc, size=0):
     raise ValueError(name)
 
 
-# DRAM bytes (read + write) per X element of one tensor-core Krylov-step launch, from the
-# ncu capture summarised in profiles/k_stream_tc_krylov_448cube_bf16.md (183.4 MB for
-# 448^3 elements); traffic grows in proportion to the elements streamed.  Set to None when
-# k_stream_tc changes until a new capture is taken.
-KRYLOV_TC_DRAM_BYTES_PER_ELEM = (179.941376e6 + 3.524096e6) / 448 ** 3
+# DRAM bytes (read + write) of one tensor-core Krylov-step launch on the 512^3 workload
+# (k_krylov_tc, mode 0), from the single-pass ncu capture summarised in
+# profiles/k_krylov_tc_448cube_bf16.md: 268.5 MB read + 2.7 MB written.  Set to None when
+# k_krylov_tc changes until a new capture is taken.
+KRYLOV_TC_DRAM_BYTES_512 = 268510720 + 2740224
 
 
 def plan_passes(dims, ranks, p, q):
@@ -408,10 +408,10 @@ def run_ours(args):
         ach = krylov_bytes * args.steps / (kms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(ach / peak, 4),
-                "traffic": (round(KRYLOV_TC_DRAM_BYTES_PER_ELEM * numel) if prec == "bf16"
-                            and KRYLOV_TC_DRAM_BYTES_PER_ELEM and not args.sequential
+                "traffic": (KRYLOV_TC_DRAM_BYTES_512 if prec == "bf16" and KRYLOV_TC_DRAM_BYTES_512
+                            and numel == 512 ** 3 and not args.sequential
                             and args.omega <= 0 and args.q_tol is None else None),
-                "traffic_unit": "bytes per launch (ncu at 448^3, scaled by elements)",
+                "traffic_unit": "bytes per launch (ncu, one 512^3 launch)",
                 "kernel": "krylov_step",
                 "avg_launch_ms": round(avg, 4), "launches": kcount, "peak_kind": peak_kind}
     breakdown = {}
