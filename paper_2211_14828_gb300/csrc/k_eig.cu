@@ -343,6 +343,111 @@ __global__ void __launch_bounds__(512) k_tridiag_reg(const double* __restrict__ 
         }
 }
 
+// Row-parallel variant for n <= 128 (512 threads): the working matrix B is in shared memory
+// (FP32, row stride tr_ld(n) = 4 mod 32, so the 8 rows x 4 phases of a warp hit 32 distinct
+// banks) and row i belongs to the four threads 4i..4i+3, which walk its
+// columns j = k+1+t, k+5+t, ...  Per Householder step k only the active block (rows and
+// columns > k) is touched, so the work shrinks as k grows:
+//   A  the owner (t = 0) of row i > k reads B[i][k] (written by that same thread in the
+//      previous update) and contributes its square; barrier 1;
+//   B  every thread forms the reflector v = (x - alpha e_1) / |x - alpha e_1| from the
+//      column and the sum of squares;
+//   C  u_i = sum_j B[i][j] v_j (four partial sums, two shuffles) and g = v^T u; barrier 2;
+//   D  B -= v w^T + w v^T with w = 2u - 2 g v, each thread its own row slice.
+// Column k+1 of the next step and the diagonal entry d[k+1] are owned by the t = 0 thread of
+// their row, which also wrote them in D, so no third barrier is needed; the column, the
+// partial sums and u are double-buffered by k.
+constexpr int TR_TPR = 4;
+__host__ __device__ inline int tr_ld(int n) { return ((n + 31) / 32) * 32 + 4; }
+__global__ void __launch_bounds__(512) k_tridiag_rows(const double* __restrict__ A, int n, float* __restrict__ d,
+                                                      float* __restrict__ e, float* __restrict__ refl) {
+    extern __shared__ float trs[];                  // B: n x tr_ld(n)
+    __shared__ float xs[2][128], us[2][128];
+    __shared__ float part[2][16], part2[2][16];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int gi = tid / TR_TPR, t = tid % TR_TPR;  // row gi, column phase t
+    const int ld = tr_ld(n);
+    for (int q = tid; q < n * n; q += blockDim.x) {
+        const int i = q / n, j = q % n;
+        trs[i * ld + j] = (float)A[q];
+    }
+    for (int q = tid; q < n * n; q += blockDim.x) refl[q] = 0.f;
+    __syncthreads();
+    const bool rowok = gi < n;
+    float* Bi = trs + (size_t)(rowok ? gi : 0) * ld;
+    for (int k = 0; k + 2 < n; ++k) {
+        const int kb = k & 1;
+        // ---- A: column k below the diagonal, sum of squares below the subdiagonal ----
+        float sq = 0.f;
+        if (rowok && t == 0) {
+            if (gi == k) d[k] = Bi[k];
+            if (gi > k) {
+                const float xv = Bi[k];
+                xs[kb][gi] = xv;
+                if (gi > k + 1) sq = xv * xv;
+            }
+        }
+        sq = warp_sum(sq);
+        if (lane == 0) part[kb][w] = sq;
+        __syncthreads();
+        float s1 = part[kb][lane & 15];      // lanes 16..31 mirror 0..15: every lane, same sum
+#pragma unroll
+        for (int o = 8; o; o >>= 1) s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        const float x0 = xs[kb][k + 1];
+        if (s1 == 0.f) {                 // already reduced: no reflector (uniform)
+            if (tid == 0) e[k] = x0;
+            continue;
+        }
+        // ---- B: the reflector ----
+        const float nrm = sqrtf(x0 * x0 + s1);
+        const float alpha = x0 >= 0.f ? -nrm : nrm;
+        const float v0 = x0 - alpha;
+        const float inv = 1.f / sqrtf(v0 * v0 + s1);
+        if (tid == 0) e[k] = alpha;
+        const float* xk = xs[kb];
+        auto vval = [&](int j) -> float { return (j == k + 1 ? v0 : xk[j]) * inv; };
+        const bool act = rowok && gi > k;
+        // ---- C: u = B v over the active block, g = v^T u ----
+        float ui = 0.f;
+        if (act)
+            for (int j = k + 1 + t; j < n; j += TR_TPR) ui += Bi[j] * vval(j);
+        ui += __shfl_xor_sync(0xffffffffu, ui, 1);
+        ui += __shfl_xor_sync(0xffffffffu, ui, 2);
+        const float vi = act ? vval(gi) : 0.f;
+        if (act && t == 0) {
+            us[kb][gi] = ui;
+            refl[(size_t)k * n + gi] = vi;
+        }
+        float gp = (t == 0) ? vi * ui : 0.f;
+        gp = warp_sum(gp);
+        if (lane == 0) part2[kb][w] = gp;
+        __syncthreads();
+        float g = part2[kb][lane & 15];
+#pragma unroll
+        for (int o = 8; o; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+        // ---- D: rank-2 update of this thread's row slice ----
+        if (act) {
+            const float wi = 2.f * ui - 2.f * g * vi;
+            const float* uk = us[kb];
+            for (int j = k + 1 + t; j < n; j += TR_TPR) {
+                const float vj = vval(j);
+                const float wj = 2.f * uk[j] - 2.f * g * vj;
+                Bi[j] -= vi * wj + wi * vj;
+            }
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        if (n >= 2) {
+            d[n - 2] = trs[(n - 2) * ld + (n - 2)];
+            e[n - 2] = trs[(n - 1) * ld + (n - 2)];
+            d[n - 1] = trs[(n - 1) * ld + (n - 1)];
+        } else {
+            d[0] = trs[0];
+        }
+    }
+}
+
 }  // namespace
 
 // number of eigenvalues of T (d, e) below x, FP32 Sturm sequence
@@ -1223,12 +1328,11 @@ rbki_status syev_top_cuda(const double* A, int n, int nwant, double* w, double* 
     const EigLayout L = eig_layout(scratch, n);
     const size_t nn = (size_t)n * n;
     // ---- 1. FP32 eigendecomposition ----
-    if (n <= 32) {
-        k_tridiag_reg<2, 1><<<1, 512, 0, st>>>(A, n, L.d, L.e, L.refl);
-    } else if (n <= 64) {
-        k_tridiag_reg<4, 2><<<1, 512, 0, st>>>(A, n, L.d, L.e, L.refl);
-    } else if (n <= 128) {
-        k_tridiag_reg<8, 4><<<1, 512, 0, st>>>(A, n, L.d, L.e, L.refl);
+    if (n <= 128) {
+        static const size_t rmax = max_dyn_smem(k_tridiag_rows);   // thread-safe, once
+        const size_t rsm_t = (size_t)n * tr_ld(n) * sizeof(float);
+        if (rsm_t > rmax) return set_error(RBKI_E_CUDA, "syev: tridiagonalisation shared memory");
+        k_tridiag_rows<<<1, 512, rsm_t, st>>>(A, n, L.d, L.e, L.refl);
     } else if (n <= 192) {
         k_tridiag_reg<12, 6><<<1, 512, 0, st>>>(A, n, L.d, L.e, L.refl);
     } else {
