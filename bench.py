@@ -41,6 +41,9 @@ def parse_args():
                     help="decompositions in flight on separate streams (throughput mode); 1 = one at a time")
     ap.add_argument("--requests", type=int, default=4096, help="served stream length (--workload serve)")
     ap.add_argument("--slots", type=int, default=16, help="server slots (--workload serve)")
+    ap.add_argument("--wave-threads", type=int, default=4,
+                    help="server workers of the batched path (0: every request on a slot)")
+    ap.add_argument("--wave-max", type=int, default=32, help="requests per wave of the batched path")
     ap.add_argument("--fp64-requests", type=int, default=256,
                     help="prefix of the served stream also run on the FP64 GPU path (--workload serve)")
     ap.add_argument("--prec", choices=["bf16", "fp64"], default="bf16")
@@ -523,8 +526,9 @@ def run_ours(args):
     serve_cmp = None
     if rank == 0 and world == 1 and not args.no_serve_compare and args.workload == "tucker512" and not args.size:
         # the served-stream half of the metric, bounded: 1024 requests of the stream
-        res, _ = serve_measure(1024, args.slots, 128, (0.8,))
-        serve_cmp = {k: res[k] for k in ("requests", "slots", "solves_per_s", "launches_per_request",
+        res, _ = serve_measure(1024, args.slots, 128, (0.8,), 1, args.wave_threads, args.wave_max)
+        serve_cmp = {k: res[k] for k in ("requests", "slots", "wave_threads", "wave_max", "solves_per_s",
+                                          "launches_per_request",
                                           "x_pass_gbs", "latency", "fp64_compare", "rel_err_mixed")}
         serve_cmp["unit"] = "solves/s"
 
@@ -787,7 +791,7 @@ def run_divide(args):
         }))
 
 
-def serve_measure(n_requests, slots, fp64_prefix, rhos, warmup=1):
+def serve_measure(n_requests, slots, fp64_prefix, rhos, warmup=1, wave_threads=4, wave_max=32):
     """The served stream (Sec. 4 workloads as a request stream): n_requests rBKI-TK requests
     (3rd order, dims in [32, 256], ranks in [4, 32], q in {1, 2, 3}, p = 5, SNR in [5, 25] dB,
     BF16 products) through the server.  Closed-loop solves/s (every request submitted at
@@ -812,8 +816,8 @@ def serve_measure(n_requests, slots, fp64_prefix, rhos, warmup=1):
     torch.cuda.synchronize()
     budget = 8 << 30
     res = {}
-    with rb.RbkiServer(0, mem_budget=budget, max_slots=slots) as srv:
-        nw = min(len(items), max(warmup, 1) * slots)
+    with rb.RbkiServer(0, mem_budget=budget, max_slots=slots, wave_threads=wave_threads, wave_max=wave_max) as srv:
+        nw = min(len(items), max(warmup, 1) * max(slots, wave_max if wave_threads else 0))
         _serve_closed_loop(rb, srv, items[:nw], outs[:nw], "bf16")
         clocks = ClockSampler()
         clocks.start()
@@ -857,7 +861,8 @@ def serve_measure(n_requests, slots, fp64_prefix, rhos, warmup=1):
                    "mixed_p99_ms": round(1e3 * float(np.percentile(lat_m, 99)), 3),
                    "max_rel_err_dev_mixed_vs_fp64": max(dev), "all_within_1pct": bool(max(dev) <= 0.01)}
     res.update({
-        "requests": len(items), "slots": slots, "budget_bytes": budget,
+        "requests": len(items), "slots": slots, "wave_threads": wave_threads, "wave_max": wave_max,
+        "budget_bytes": budget,
         "solves_per_s": round(sat, 2), "closed_loop_s": round(secs, 4),
         "x_pass_bytes": int(2 * numel_passes), "x_pass_gbs": round(2 * numel_passes / secs / 1e9, 2),
         "launches_per_request": round(launches / len(items), 1), "gpu_launches": int(launches),
@@ -876,7 +881,8 @@ def run_serve(args):
     if world > 1:
         raise SystemExit("--workload serve runs on one GPU")
     torch.cuda.set_device(0)
-    res, reqs = serve_measure(args.requests, args.slots, args.fp64_requests, (0.5, 0.8, 0.95), args.warmup)
+    res, reqs = serve_measure(args.requests, args.slots, args.fp64_requests, (0.5, 0.8, 0.95), args.warmup,
+                              args.wave_threads, args.wave_max)
     cpu = None
     if not args.no_cpu_baseline:
         cpu = serve_cpu_baseline(reqs)
@@ -887,6 +893,7 @@ def run_serve(args):
         "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": f"serve: {res['requests']} requests, dims U[32,256]^3, ranks U[4,32], p=5, "
                                f"q in {{1,2,3}}, SNR U[5,25] dB, BF16 products", "slots": args.slots,
+                   "wave_threads": args.wave_threads, "wave_max": args.wave_max,
                    "budget_bytes": res["budget_bytes"], "x_pass_bytes": res["x_pass_bytes"],
                    "x_pass_gbs": res["x_pass_gbs"],
                    "l2": "requests are mostly smaller than L2; throughput is latency-bound"},

@@ -178,6 +178,29 @@ rbki_status rbki_tucker_batch_workspace(int32_t count, const rbki_tensor* X, con
 rbki_status rbki_tucker_batch(int32_t count, const rbki_tensor* X, const rbki_params* prm,
                               void* workspace, size_t workspace_bytes, const rbki_tucker_out* out,
                               void* stream);
+/* ---- batched small decompositions (continuous batching pattern) --------------------- */
+/* Workspace of rbki_tucker_batched for these items (bytes, 256-byte aligned pieces). */
+rbki_status rbki_tucker_batched_workspace(int32_t count, const rbki_tensor* X, const rbki_params* prm,
+                                          size_t* bytes);
+/* `count` independent rBKI-TK decompositions (Algorithm 2, HOSVD reading, the same outputs
+ * as rbki_tucker) run as ONE wave on `stream`: every stage of Algorithms 1-2 is one launch
+ * for all modes of all items (about 75 launches for a wave of q = 3 requests, whatever its
+ * size), so many small requests cost what one costs in launches.
+ *   - X passes (sketch, Krylov step, Gram, the core's mode products) on CUDA cores: FP32
+ *     products of the BF16/FP16 value of each X entry (X rounded as it is read when its
+ *     storage dtype is wider), FP32 Omega and Q, FP32 accumulation within a run of 64-column
+ *     tiles and FP64 across runs, fixed order.
+ *   - Orthonormalisation, Z = Q^T P, the eigensolver and U = Q U~ in FP64 with the kernels
+ *     of rbki_tucker (their batched forms: the same per-item arithmetic).
+ * Each item's result depends only on the item (and the work-queue granularity table, see
+ * rbki_wave_autotune), not on the other items of the wave.  Requires: prec BF16 or FP16,
+ * flags 0 or RBKI_FLAG_SERIAL_MODES (no effect here), no column sampling, order >= 2,
+ * every I_n <= 256, R_n + p <= 64, the eigenproblem (S(q+1), or I_n on the Gram path)
+ * <= 192, fewer than 2^31 entries; otherwise RBKI_E_UNSUPPORTED.  Device buffers only;
+ * outputs as rbki_tucker (info[2N] is always 0: the wave's kernels have no device waits). */
+rbki_status rbki_tucker_batched(int32_t count, const rbki_tensor* X, const rbki_params* prm,
+                                void* workspace, size_t workspace_bytes, const rbki_tucker_out* out,
+                                void* stream);
 /* Divide-and-conquer split: dst[k] (device, dense C-order, dims of X with I_mode replaced by
  * hi_k - lo_k) = X restricted to mode indices [lo_k, hi_k), lo_k = floor(k I_mode / parts),
  * hi_k = floor((k+1) I_mode / parts); 1 <= parts <= I_mode.  Same dtype as X. */
@@ -204,10 +227,22 @@ rbki_status rbki_htr(const rbki_tensor* X, const rbki_params* tk, const int32_t*
 typedef struct rbki_server rbki_server;
 
 /* Creates a server on `device` that admits requests while their workspace fits in
- * mem_budget bytes and fewer than max_slots are in flight.  The server allocates its
- * own device memory pool of mem_budget bytes once, here. */
+ * mem_budget bytes.  Requests rbki_tucker_batched supports are served in waves
+ * (rbki_server_create_ex with RBKI_SERVER_WAVE_THREADS workers, waves of at most
+ * RBKI_SERVER_WAVE_MAX requests); every other request runs on one of max_slots slots
+ * (rbki_tucker each).  The server allocates its own device memory pool of mem_budget bytes
+ * once, here. */
+#define RBKI_SERVER_WAVE_THREADS 4
+#define RBKI_SERVER_WAVE_MAX 32
 rbki_status rbki_server_create(int32_t device, size_t mem_budget, int32_t max_slots,
                                rbki_server** out);
+/* As rbki_server_create with the batched path configured: wave_threads host workers (0..8;
+ * 0 = every request on the slots) each run waves of up to wave_max (1..1024) requests: the
+ * longest FIFO prefix of the waiting batched-path requests whose workspaces fit in the pool
+ * together.  A wave item's outputs are bitwise those of rbki_tucker_batched on that request
+ * alone; a slot request's those of rbki_tucker. */
+rbki_status rbki_server_create_ex(int32_t device, size_t mem_budget, int32_t max_slots,
+                                  int32_t wave_threads, int32_t wave_max, rbki_server** out);
 /* Queues one rBKI-TK request (device buffers; RBKI_FLAG_HOST_IO is refused).  X and out
  * must stay valid until a terminal poll.  The server runs requests on its own streams: work
  * already queued on `after_stream` (a cudaStream_t as void*, typically the stream that

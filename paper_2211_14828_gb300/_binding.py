@@ -21,6 +21,7 @@ PREC_FP64, PREC_BF16, PREC_FP16 = 0, 1, 2
 FLAG_HOST_IO, FLAG_SPLIT, FLAG_SERIAL_MODES, FLAG_SEQUENTIAL, FLAG_POWER, FLAG_ADAPTIVE_Q, FLAG_TR_SVD, FLAG_ASYNC = \
     1, 2, 4, 8, 16, 32, 64, 128
 FLAG_REFINE_FP32 = 256
+SERVER_WAVE_THREADS, SERVER_WAVE_MAX = 4, 32   # rbki_server_create's batched-path workers and wave size
 
 
 class rbki_tensor(C.Structure):
@@ -65,6 +66,7 @@ def lib():
             "rbki_htr_workspace": (st, [vp, vp, vp, sz]),
             "rbki_htr": (st, [vp, vp, vp, vp, C.c_int32, C.c_double, vp, vp, vp, vp, C.c_size_t, vp]),
             "rbki_server_create": (st, [C.c_int32, C.c_size_t, C.c_int32, C.POINTER(vp)]),
+            "rbki_server_create_ex": (st, [C.c_int32, C.c_size_t, C.c_int32, C.c_int32, C.c_int32, C.POINTER(vp)]),
             "rbki_submit": (st, [vp, vp, vp, vp, vp, C.POINTER(C.c_uint64)]),
             "rbki_poll": (st, [vp, C.c_uint64, C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
             "rbki_cancel": (st, [vp, C.c_uint64]),
@@ -81,6 +83,8 @@ def lib():
             "rbki_sample_units": (st, [C.c_uint64, C.c_int32, C.c_int64, C.c_int64, vp, vp]),
             "rbki_tucker_batch_workspace": (st, [C.c_int32, vp, vp, sz]),
             "rbki_tucker_batch": (st, [C.c_int32, vp, vp, vp, C.c_size_t, vp, vp]),
+            "rbki_tucker_batched_workspace": (st, [C.c_int32, vp, vp, sz]),
+            "rbki_tucker_batched": (st, [C.c_int32, vp, vp, vp, C.c_size_t, vp, vp]),
             "rbki_split_mode": (st, [vp, C.c_int32, C.c_int32, vp, vp]),
             "rbki_status_str": (C.c_char_p, [C.c_int32]),
             "rbki_last_error": (C.c_char_p, []),
@@ -251,6 +255,40 @@ def rbki_tucker_batch(xs, ranks, p, q, seeds, prec="bf16", flags=0, omega=0.0, q
     return outs
 
 
+def rbki_tucker_batched_workspace(xs, ranks, p, qs, seeds, prec="bf16", flags=0) -> int:
+    """Workspace bytes of rbki_tucker_batched for these items."""
+    n = len(xs)
+    qv = [int(qs)] * n if isinstance(qs, int) else [int(v) for v in qs]
+    ts = (rbki_tensor * n)(*[make_tensor(x) for x in xs])
+    ps = (rbki_params * n)(*[make_params(ranks[k], p, qv[k], seeds[k], prec, flags) for k in range(n)])
+    need = C.c_size_t(0)
+    check(lib().rbki_tucker_batched_workspace(n, ts, ps, C.byref(need)), "rbki_tucker_batched_workspace")
+    return int(need.value)
+
+
+def rbki_tucker_batched(xs, ranks, p, qs, seeds, prec="bf16", flags=0, workspace=None, outs=None,
+                        stream=None):
+    """Many small rBKI-TK decompositions as one wave (rbki_tucker_batched): ranks[k], qs[k]
+    (an int applies to all), seeds[k] per item.  Returns the list of output dicts (the first
+    also holds the workspace)."""
+    torch = _torch()
+    n = len(xs)
+    qv = [int(qs)] * n if isinstance(qs, int) else [int(v) for v in qs]
+    ts = (rbki_tensor * n)(*[make_tensor(x) for x in xs])
+    ps = (rbki_params * n)(*[make_params(ranks[k], p, qv[k], seeds[k], prec, flags) for k in range(n)])
+    need = C.c_size_t(0)
+    check(lib().rbki_tucker_batched_workspace(n, ts, ps, C.byref(need)), "rbki_tucker_batched_workspace")
+    if workspace is None or workspace.numel() < need.value:
+        workspace = torch.empty(max(int(need.value), 1), dtype=torch.uint8, device=xs[0].device)
+    if outs is None:
+        outs = [alloc_outputs(x.shape, ranks[k], x.device) for k, x in enumerate(xs)]
+    os_ = (rbki_tucker_out * n)(*[make_out(o) for o in outs])
+    check(lib().rbki_tucker_batched(n, ts, ps, C.c_void_p(workspace.data_ptr()), C.c_size_t(workspace.numel()),
+                                    os_, stream_ptr(stream)), "rbki_tucker_batched")
+    outs[0]["workspace"] = workspace
+    return outs
+
+
 def rbki_divide_and_conquer(x, mode, parts, ranks, p, q, seed, prec="bf16", flags=0, stream=None):
     """Divide-and-conquer decomposition along `mode`: split into `parts` consecutive parts,
     decompose them as one batch (part k with ranks[k] and seed + k).  Returns (parts, outs)."""
@@ -386,10 +424,13 @@ class RbkiServer:
     """Served stream (rbki_server_*): continuous batching with device-memory admission.
     Holds references to each request's input and outputs until its terminal poll."""
 
-    def __init__(self, device: int = 0, mem_budget: int = 1 << 30, max_slots: int = 4):
+    def __init__(self, device: int = 0, mem_budget: int = 1 << 30, max_slots: int = 4,
+                 wave_threads: int = SERVER_WAVE_THREADS, wave_max: int = SERVER_WAVE_MAX):
+        """wave_threads workers serve the requests rbki_tucker_batched supports in waves of up
+        to wave_max (0 workers: every request on the max_slots slots, one rbki_tucker each)."""
         h = C.c_void_p()
-        check(lib().rbki_server_create(int(device), C.c_size_t(int(mem_budget)), int(max_slots), C.byref(h)),
-              "rbki_server_create")
+        check(lib().rbki_server_create_ex(int(device), C.c_size_t(int(mem_budget)), int(max_slots), int(wave_threads),
+                                          int(wave_max), C.byref(h)), "rbki_server_create_ex")
         self._h = h
         self._live = {}
 

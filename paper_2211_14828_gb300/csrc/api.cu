@@ -367,7 +367,6 @@ void carve(Plan& pl, void* ws) {
 // ---------------------------------------------------------------------------------
 // per-mode pipeline
 // ---------------------------------------------------------------------------------
-static const double TAU_DEFLATE = 1e-6;
 
 __global__ void k_symmetrize(double* Z, int n) {
     int e = blockIdx.x * blockDim.x + threadIdx.x;

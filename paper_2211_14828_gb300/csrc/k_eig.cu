@@ -233,8 +233,8 @@ __global__ void __launch_bounds__(512) k_tridiag_packed(const double* __restrict
 // (barrier 2); the rank-2 update B -= v w^T + w v^T, w = 2u - 2 g v, runs in registers.
 // Entries in rows or columns <= k are dead: v and w are zero there.
 template <int NR, int NC>
-__global__ void __launch_bounds__(512) k_tridiag_reg(const double* __restrict__ A, int n, float* __restrict__ d,
-                                                     float* __restrict__ e, float* __restrict__ refl) {
+__device__ __forceinline__ void tridiag_reg_dev(const double* __restrict__ A, int n, float* __restrict__ d,
+                                                float* __restrict__ e, float* __restrict__ refl) {
     constexpr int NW = 16;
     __shared__ float xv[2][NR * NW];   // column k below the diagonal, double-buffered by k
     __shared__ float uv[NR * NW];
@@ -343,6 +343,30 @@ __global__ void __launch_bounds__(512) k_tridiag_reg(const double* __restrict__ 
         }
 }
 
+template <int NR, int NC>
+__global__ void __launch_bounds__(512) k_tridiag_reg(const double* __restrict__ A, int n, float* __restrict__ d,
+                                                     float* __restrict__ e, float* __restrict__ refl) {
+    tridiag_reg_dev<NR, NC>(A, n, d, e, refl);
+}
+
+struct tridiag_reg_rec {
+    const double* A;
+    int n;
+    float* d;
+    float* e;
+    float* refl;
+    int gx, gy, gz;
+};
+
+template <int NR, int NC>
+__global__ void __launch_bounds__(512) k_tridiag_reg_b(const __grid_constant__ BPack<tridiag_reg_rec> p) {
+    const tridiag_reg_rec& r = p.r[blockIdx.y];
+    int bx, by, bz;
+    if (!bat_block(r, bx, by, bz)) return;
+    tridiag_reg_dev<NR, NC>(r.A, r.n, r.d, r.e, r.refl);
+}
+
+
 // Row-parallel variant for n <= 128 (512 threads): the working matrix B is in shared memory
 // (FP32, row stride tr_ld(n) = 4 mod 32, so the 8 rows x 4 phases of a warp hit 32 distinct
 // banks) and row i belongs to the four threads 4i..4i+3, which walk its
@@ -359,8 +383,8 @@ __global__ void __launch_bounds__(512) k_tridiag_reg(const double* __restrict__ 
 // partial sums and u are double-buffered by k.
 constexpr int TR_TPR = 4;
 __host__ __device__ inline int tr_ld(int n) { return ((n + 31) / 32) * 32 + 4; }
-__global__ void __launch_bounds__(512) k_tridiag_rows(const double* __restrict__ A, int n, float* __restrict__ d,
-                                                      float* __restrict__ e, float* __restrict__ refl) {
+__device__ __forceinline__ void tridiag_rows_dev(const double* __restrict__ A, int n, float* __restrict__ d,
+                                                 float* __restrict__ e, float* __restrict__ refl) {
     extern __shared__ float trs[];                  // B: n x tr_ld(n)
     __shared__ float xs[2][128], us[2][128];
     __shared__ float part[2][16], part2[2][16];
@@ -447,6 +471,28 @@ __global__ void __launch_bounds__(512) k_tridiag_rows(const double* __restrict__
         }
     }
 }
+
+__global__ void __launch_bounds__(512) k_tridiag_rows(const double* __restrict__ A, int n, float* __restrict__ d,
+                                                      float* __restrict__ e, float* __restrict__ refl) {
+    tridiag_rows_dev(A, n, d, e, refl);
+}
+
+struct tridiag_rows_rec {
+    const double* A;
+    int n;
+    float* d;
+    float* e;
+    float* refl;
+    int gx, gy, gz;
+};
+
+__global__ void __launch_bounds__(512) k_tridiag_rows_b(const __grid_constant__ BPack<tridiag_rows_rec> p) {
+    const tridiag_rows_rec& r = p.r[blockIdx.y];
+    int bx, by, bz;
+    if (!bat_block(r, bx, by, bz)) return;
+    tridiag_rows_dev(r.A, r.n, r.d, r.e, r.refl);
+}
+
 
 }  // namespace
 
@@ -657,8 +703,8 @@ __device__ T tri_norm(const T* d, const T* e, int n) {
 // per lane) and keeps the sub-interval where the count crosses the eigenvalue's index.
 constexpr int SHIFT_WARPS = 8;
 template <typename T>
-__global__ void __launch_bounds__(32 * SHIFT_WARPS) k_tri_shift(const T* __restrict__ d, const T* __restrict__ e,
-                                                                int n, int nwant, float* __restrict__ shift_out) {
+__device__ __forceinline__ void tri_shift_dev(const T* __restrict__ d, const T* __restrict__ e,
+                                              int n, int nwant, float* __restrict__ shift_out, int bx) {
     __shared__ float df[256], e2f[256];
     __shared__ float bounds[2];
     __shared__ T tn_sh;
@@ -682,7 +728,7 @@ __global__ void __launch_bounds__(32 * SHIFT_WARPS) k_tri_shift(const T* __restr
         bounds[1] = hi + 1e-5f;
     }
     __syncthreads();
-    const int k = blockIdx.x * SHIFT_WARPS + (tid >> 5);
+    const int k = bx * SHIFT_WARPS + (tid >> 5);
     if (k >= nwant) return;
     const int j = n - 1 - k;                    // index from below
     float lo = bounds[0], hi = bounds[1];
@@ -700,17 +746,42 @@ __global__ void __launch_bounds__(32 * SHIFT_WARPS) k_tri_shift(const T* __restr
     if (lane == 0) shift_out[k] = 0.5f * (lo + hi);
 }
 
+template <typename T>
+__global__ void __launch_bounds__(32 * SHIFT_WARPS) k_tri_shift(const T* __restrict__ d, const T* __restrict__ e,
+                                                                int n, int nwant, float* __restrict__ shift_out) {
+    tri_shift_dev<T>(d, e, n, nwant, shift_out, (int)blockIdx.x);
+}
+
+template <typename T>
+struct tri_shift_rec {
+    const T* d;
+    const T* e;
+    int n;
+    int nwant;
+    float* shift_out;
+    int gx, gy, gz;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(32 * SHIFT_WARPS) k_tri_shift_b(const __grid_constant__ BPack<tri_shift_rec<T>> p) {
+    const tri_shift_rec<T>& r = p.r[blockIdx.y];
+    int bx, by, bz;
+    if (!bat_block(r, bx, by, bz)) return;
+    tri_shift_dev<T>(r.d, r.e, r.n, r.nwant, r.shift_out, bx);
+}
+
+
 // fixed-shift inverse iteration (3 solves) for every eigenvalue that does not continue a run
 template <typename T>
-__global__ void __launch_bounds__(64) k_tri_vec(const T* __restrict__ d, const T* __restrict__ e, int n, int nwant,
-                                                const float* __restrict__ shift, T* __restrict__ Y) {
+__device__ __forceinline__ void tri_vec_dev(const T* __restrict__ d, const T* __restrict__ e, int n, int nwant,
+                                            const float* __restrict__ shift, T* __restrict__ Y, int bx) {
     __shared__ T tn_sh;
     const int tid = threadIdx.x;
     if (tid == 0) tn_sh = tri_norm(d, e, n);
     __syncthreads();
     const T tnorm = tn_sh;
     const int ld = nwant + 1;
-    const int k = blockIdx.x * blockDim.x + tid;
+    const int k = bx * blockDim.x + tid;
     if (k >= nwant || tied(shift, k)) return;
     // elimination rows of this thread in shared memory ([i][thread], conflict-free)
     extern __shared__ __align__(16) unsigned char vsm_raw[];
@@ -723,14 +794,40 @@ __global__ void __launch_bounds__(64) k_tri_vec(const T* __restrict__ d, const T
     invit_one<T>(d, e, n, mu, tnorm, k, rdd + tid, du + tid, du2 + tid, Y + k, (int)blockDim.x, 3, 0, ld);
 }
 
+template <typename T>
+__global__ void __launch_bounds__(64) k_tri_vec(const T* __restrict__ d, const T* __restrict__ e, int n, int nwant,
+                                                const float* __restrict__ shift, T* __restrict__ Y) {
+    tri_vec_dev<T>(d, e, n, nwant, shift, Y, (int)blockIdx.x);
+}
+
+template <typename T>
+struct tri_vec_rec {
+    const T* d;
+    const T* e;
+    int n;
+    int nwant;
+    const float* shift;
+    T* Y;
+    int gx, gy, gz;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(64) k_tri_vec_b(const __grid_constant__ BPack<tri_vec_rec<T>> p) {
+    const tri_vec_rec<T>& r = p.r[blockIdx.y];
+    int bx, by, bz;
+    if (!bat_block(r, bx, by, bz)) return;
+    tri_vec_dev<T>(r.d, r.e, r.n, r.nwant, r.shift, r.Y, bx);
+}
+
+
 // One CTA per run of tied shifts starting at column blockIdx.x (CTAs whose column does not
 // start a run with at least one follower return at once).  y lives in shared memory; the
 // serial tridiagonal solve runs on thread 0.
 template <typename T>
-__global__ void __launch_bounds__(256) k_tri_runs(const T* __restrict__ d, const T* __restrict__ e, int n,
-                                                  int nwant, const float* __restrict__ shift,
-                                                  const double* __restrict__ mu64, T* __restrict__ Y) {
-    const int L = blockIdx.x;
+__device__ __forceinline__ void tri_runs_dev(const T* __restrict__ d, const T* __restrict__ e, int n,
+                                             int nwant, const float* __restrict__ shift,
+                                             const double* __restrict__ mu64, T* __restrict__ Y, int bx) {
+    const int L = bx;
     __shared__ T tn0;
     if (threadIdx.x == 0) tn0 = tri_norm(d, e, n);
     __syncthreads();
@@ -785,6 +882,34 @@ __global__ void __launch_bounds__(256) k_tri_runs(const T* __restrict__ d, const
     }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) k_tri_runs(const T* __restrict__ d, const T* __restrict__ e, int n,
+                                                  int nwant, const float* __restrict__ shift,
+                                                  const double* __restrict__ mu64, T* __restrict__ Y) {
+    tri_runs_dev<T>(d, e, n, nwant, shift, mu64, Y, (int)blockIdx.x);
+}
+
+template <typename T>
+struct tri_runs_rec {
+    const T* d;
+    const T* e;
+    int n;
+    int nwant;
+    const float* shift;
+    const double* mu64;
+    T* Y;
+    int gx, gy, gz;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_tri_runs_b(const __grid_constant__ BPack<tri_runs_rec<T>> p) {
+    const tri_runs_rec<T>& r = p.r[blockIdx.y];
+    int bx, by, bz;
+    if (!bat_block(r, bx, by, bz)) return;
+    tri_runs_dev<T>(r.d, r.e, r.n, r.nwant, r.shift, r.mu64, r.Y, bx);
+}
+
+
 __device__ int sturm_count64(const double* d, const double* e2, int n, double x, double pivmin) {
     int c = 0;
     double q = d[0] - x;
@@ -806,9 +931,9 @@ constexpr int R64_WARPS = 1;
 // Sturm counts per round) from the run's FP32 bracket widened by 16 FP32 ulps of |T| (the
 // Gershgorin interval when the counts do not bracket the index), down to RES64 |T|.
 template <typename T>
-__global__ void __launch_bounds__(32 * R64_WARPS) k_run_shift64(const T* __restrict__ d, const T* __restrict__ e,
-                                                               int n, int nwant, const float* __restrict__ shift,
-                                                               double* __restrict__ mu64) {
+__device__ __forceinline__ void run_shift64_dev(const T* __restrict__ d, const T* __restrict__ e,
+                                                int n, int nwant, const float* __restrict__ shift,
+                                                double* __restrict__ mu64, int bx) {
     __shared__ double d64[256], e2[256];
     __shared__ double tn_sh;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -818,7 +943,7 @@ __global__ void __launch_bounds__(32 * R64_WARPS) k_run_shift64(const T* __restr
     }
     if (tid == 0) tn_sh = (double)tri_norm(d, e, n);
     __syncthreads();
-    const int k = blockIdx.x * R64_WARPS + w;
+    const int k = bx * R64_WARPS + w;
     if (k >= nwant) return;
     int L = k, end = k + 1;
     while (L > 0 && tied(shift, L)) --L;
@@ -854,13 +979,40 @@ __global__ void __launch_bounds__(32 * R64_WARPS) k_run_shift64(const T* __restr
     if (lane == 0) mu64[k] = 0.5 * (lo + hi);
 }
 
+template <typename T>
+__global__ void __launch_bounds__(32 * R64_WARPS) k_run_shift64(const T* __restrict__ d, const T* __restrict__ e,
+                                                               int n, int nwant, const float* __restrict__ shift,
+                                                               double* __restrict__ mu64) {
+    run_shift64_dev<T>(d, e, n, nwant, shift, mu64, (int)blockIdx.x);
+}
+
+template <typename T>
+struct run_shift64_rec {
+    const T* d;
+    const T* e;
+    int n;
+    int nwant;
+    const float* shift;
+    double* mu64;
+    int gx, gy, gz;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(32 * R64_WARPS) k_run_shift64_b(const __grid_constant__ BPack<run_shift64_rec<T>> p) {
+    const run_shift64_rec<T>& r = p.r[blockIdx.y];
+    int bx, by, bz;
+    if (!bat_block(r, bx, by, bz)) return;
+    run_shift64_dev<T>(r.d, r.e, r.n, r.nwant, r.shift, r.mu64, bx);
+}
+
+
 // FP64 inverse iteration (three solves) for the long-run members that are not tied in FP64
 // to their predecessor; lane 0 of the member's warp runs the serial solve, the vector is
 // stored back in the working precision.  Factor rows and the iterate live in shared memory.
 template <typename T>
-__global__ void __launch_bounds__(32 * R64_WARPS) k_run_vec64(const T* __restrict__ d, const T* __restrict__ e, int n,
-                                                             int nwant, const double* __restrict__ mu64,
-                                                             T* __restrict__ Y) {
+__device__ __forceinline__ void run_vec64_dev(const T* __restrict__ d, const T* __restrict__ e, int n,
+                                              int nwant, const double* __restrict__ mu64,
+                                              T* __restrict__ Y, int bx) {
     extern __shared__ __align__(16) unsigned char rv_raw[];
     __shared__ double d64[256], e64[256];
     __shared__ double tn_sh;
@@ -871,7 +1023,7 @@ __global__ void __launch_bounds__(32 * R64_WARPS) k_run_vec64(const T* __restric
     }
     if (tid == 0) tn_sh = (double)tri_norm(d, e, n);
     __syncthreads();
-    const int k = blockIdx.x * R64_WARPS + w;
+    const int k = bx * R64_WARPS + w;
     if (k >= nwant) return;
     const double mu = mu64[k];
     if (isnan(mu)) return;
@@ -885,6 +1037,33 @@ __global__ void __launch_bounds__(32 * R64_WARPS) k_run_vec64(const T* __restric
     for (int i = lane; i < n; i += 32) Y[(size_t)i * ld + k] = (T)y[i];
 }
 
+template <typename T>
+__global__ void __launch_bounds__(32 * R64_WARPS) k_run_vec64(const T* __restrict__ d, const T* __restrict__ e, int n,
+                                                             int nwant, const double* __restrict__ mu64,
+                                                             T* __restrict__ Y) {
+    run_vec64_dev<T>(d, e, n, nwant, mu64, Y, (int)blockIdx.x);
+}
+
+template <typename T>
+struct run_vec64_rec {
+    const T* d;
+    const T* e;
+    int n;
+    int nwant;
+    const double* mu64;
+    T* Y;
+    int gx, gy, gz;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(32 * R64_WARPS) k_run_vec64_b(const __grid_constant__ BPack<run_vec64_rec<T>> p) {
+    const run_vec64_rec<T>& r = p.r[blockIdx.y];
+    int bx, by, bz;
+    if (!bat_block(r, bx, by, bz)) return;
+    run_vec64_dev<T>(r.d, r.e, r.n, r.nwant, r.mu64, r.Y, bx);
+}
+
+
 // Orthonormalise the inverse-iteration vectors by one Cholesky QR of the whole block
 // (FP32): fixed-shift inverse iteration leaves the vectors of a cluster of (near-)equal
 // eigenvalues independent but not orthogonal, and the noise part of Z forms large clusters
@@ -893,8 +1072,8 @@ __global__ void __launch_bounds__(32 * R64_WARPS) k_run_vec64(const T* __restric
 // whole CTA; the factorisation and the triangular inverse run on warp 0 with warp-level
 // synchronisation only.  Y (n x nwant, ld nwant+1) is processed in shared memory.
 template <typename T>
-__global__ void __launch_bounds__(256) k_tri_orth(T* __restrict__ Yg, int n, int nwant, T* __restrict__ scratch,
-                                                  int use_smem) {
+__device__ __forceinline__ void tri_orth_dev(T* __restrict__ Yg, int n, int nwant, T* __restrict__ scratch,
+                                             int use_smem) {
     extern __shared__ __align__(16) unsigned char osm_raw[];
     const int tid = threadIdx.x;
     const int ld = nwant + 1;
@@ -971,6 +1150,31 @@ __global__ void __launch_bounds__(256) k_tri_orth(T* __restrict__ Yg, int n, int
     for (int t = tid; t < n * ld; t += blockDim.x) Yg[t] = ys[t];
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) k_tri_orth(T* __restrict__ Yg, int n, int nwant, T* __restrict__ scratch,
+                                                  int use_smem) {
+    tri_orth_dev<T>(Yg, n, nwant, scratch, use_smem);
+}
+
+template <typename T>
+struct tri_orth_rec {
+    T* Yg;
+    int n;
+    int nwant;
+    T* scratch;
+    int use_smem;
+    int gx, gy, gz;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_tri_orth_b(const __grid_constant__ BPack<tri_orth_rec<T>> p) {
+    const tri_orth_rec<T>& r = p.r[blockIdx.y];
+    int bx, by, bz;
+    if (!bat_block(r, bx, by, bz)) return;
+    tri_orth_dev<T>(r.Yg, r.n, r.nwant, r.scratch, r.use_smem);
+}
+
+
 // Variant of k_tri_orth for n whose working set does not fit in shared memory: Y stays in
 // global memory (L2-resident, at most 257 KB) and is updated in place, staged through
 // shared memory 64 rows at a time for the Gram matrix; R lives in shared memory as the packed
@@ -978,7 +1182,7 @@ __global__ void __launch_bounds__(256) k_tri_orth(T* __restrict__ Yg, int n, int
 // Gram tiles, Cholesky with the same pivot guard, and row solves.
 constexpr int ORTH_CH = 64;   // rows of Y staged per pass of the Gram accumulation
 template <typename T>
-__global__ void __launch_bounds__(256) k_tri_orth_packed(T* __restrict__ Yg, int n, int nwant) {
+__device__ __forceinline__ void tri_orth_packed_dev(T* __restrict__ Yg, int n, int nwant) {
     extern __shared__ __align__(16) unsigned char op_raw[];
     T* Gp = reinterpret_cast<T*>(op_raw);
     T* Ri = Gp + (size_t)nwant * (nwant + 1) / 2;
@@ -1055,6 +1259,28 @@ __global__ void __launch_bounds__(256) k_tri_orth_packed(T* __restrict__ Yg, int
     }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) k_tri_orth_packed(T* __restrict__ Yg, int n, int nwant) {
+    tri_orth_packed_dev<T>(Yg, n, nwant);
+}
+
+template <typename T>
+struct tri_orth_packed_rec {
+    T* Yg;
+    int n;
+    int nwant;
+    int gx, gy, gz;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_tri_orth_packed_b(const __grid_constant__ BPack<tri_orth_packed_rec<T>> p) {
+    const tri_orth_packed_rec<T>& r = p.r[blockIdx.y];
+    int bx, by, bz;
+    if (!bat_block(r, bx, by, bz)) return;
+    tri_orth_packed_dev<T>(r.Yg, r.n, r.nwant);
+}
+
+
 // Cholesky QR of the eigenvector block for n <= 32 * NC (n <= 16 * NR), 512 threads.
 // Y (n x n, ld n+1) is staged in shared memory; G = Y^T Y is accumulated into the same
 // register distribution as k_tridiag_reg; the right-looking Cholesky publishes row k
@@ -1063,7 +1289,7 @@ __global__ void __launch_bounds__(256) k_tri_orth_packed(T* __restrict__ Yg, int
 // column).  Same pivot guard as k_tri_orth: a pivot <= 1e-6 (the columns are unit
 // vectors) leaves its column unscaled.
 template <int NR, int NC>
-__global__ void __launch_bounds__(512) k_tri_orth_reg(float* __restrict__ Yg, int n) {
+__device__ __forceinline__ void tri_orth_reg_dev(float* __restrict__ Yg, int n) {
     constexpr int NW = 16;
     extern __shared__ __align__(16) unsigned char or_raw[];
     const int ld = n + 1;
@@ -1147,10 +1373,30 @@ __global__ void __launch_bounds__(512) k_tri_orth_reg(float* __restrict__ Yg, in
     for (int t = tid; t < n * ld; t += blockDim.x) Yg[t] = ys[t];
 }
 
+template <int NR, int NC>
+__global__ void __launch_bounds__(512) k_tri_orth_reg(float* __restrict__ Yg, int n) {
+    tri_orth_reg_dev<NR, NC>(Yg, n);
+}
+
+struct tri_orth_reg_rec {
+    float* Yg;
+    int n;
+    int gx, gy, gz;
+};
+
+template <int NR, int NC>
+__global__ void __launch_bounds__(512) k_tri_orth_reg_b(const __grid_constant__ BPack<tri_orth_reg_rec> p) {
+    const tri_orth_reg_rec& r = p.r[blockIdx.y];
+    int bx, by, bz;
+    if (!bat_block(r, bx, by, bz)) return;
+    tri_orth_reg_dev<NR, NC>(r.Yg, r.n);
+}
+
+
 template <typename T>
-__global__ void k_tri_rq(const T* __restrict__ d, const T* __restrict__ e, int n, int nwant,
-                         const T* __restrict__ Y, T* __restrict__ w) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void tri_rq_dev(const T* __restrict__ d, const T* __restrict__ e, int n, int nwant,
+                                           const T* __restrict__ Y, T* __restrict__ w, int bx) {
+    const int k = bx * blockDim.x + threadIdx.x;
     if (k >= nwant) return;
     const int ld = nwant + 1;
     T num = 0;
@@ -1163,15 +1409,41 @@ __global__ void k_tri_rq(const T* __restrict__ d, const T* __restrict__ e, int n
     w[k] = num;
 }
 
+template <typename T>
+__global__ void k_tri_rq(const T* __restrict__ d, const T* __restrict__ e, int n, int nwant,
+                         const T* __restrict__ Y, T* __restrict__ w) {
+    tri_rq_dev<T>(d, e, n, nwant, Y, w, (int)blockIdx.x);
+}
+
+template <typename T>
+struct tri_rq_rec {
+    const T* d;
+    const T* e;
+    int n;
+    int nwant;
+    const T* Y;
+    T* w;
+    int gx, gy, gz;
+};
+
+template <typename T>
+__global__ void k_tri_rq_b(const __grid_constant__ BPack<tri_rq_rec<T>> p) {
+    const tri_rq_rec<T>& r = p.r[blockIdx.y];
+    int bx, by, bz;
+    if (!bat_block(r, bx, by, bz)) return;
+    tri_rq_dev<T>(r.d, r.e, r.n, r.nwant, r.Y, r.w, bx);
+}
+
+
 // z = H_0 H_1 ... H_{n-3} y for eigenvector column k, one warp per eigenvector (z held in
 // registers, 8 entries per lane); output widened to FP64 (ld ldv).  BT_WARPS eigenvectors
 // per CTA; the reflectors are staged once per CTA in shared memory when they fit
 // (use_smem), otherwise read from global memory.
 constexpr int BT_WARPS = 16;
 template <typename T>
-__global__ void __launch_bounds__(32 * BT_WARPS) k_backtransform(const T* __restrict__ refl, int n, int nwant,
-                                                                 const T* __restrict__ Y, double* __restrict__ V,
-                                                                 int ldv, int use_smem) {
+__device__ __forceinline__ void backtransform_dev(const T* __restrict__ refl, int n, int nwant,
+                                                  const T* __restrict__ Y, double* __restrict__ V,
+                                                  int ldv, int use_smem, int bx) {
     extern __shared__ __align__(16) unsigned char bt_raw[];
     const T* rf = refl;
     if (use_smem) {
@@ -1181,7 +1453,7 @@ __global__ void __launch_bounds__(32 * BT_WARPS) k_backtransform(const T* __rest
         rf = s;
     }
     const int lane = threadIdx.x & 31;
-    const int k = blockIdx.x * BT_WARPS + (threadIdx.x >> 5);
+    const int k = bx * BT_WARPS + (threadIdx.x >> 5);
     if (k >= nwant) return;
     T z[8];
 #pragma unroll
@@ -1210,11 +1482,39 @@ __global__ void __launch_bounds__(32 * BT_WARPS) k_backtransform(const T* __rest
     }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(32 * BT_WARPS) k_backtransform(const T* __restrict__ refl, int n, int nwant,
+                                                                 const T* __restrict__ Y, double* __restrict__ V,
+                                                                 int ldv, int use_smem) {
+    backtransform_dev<T>(refl, n, nwant, Y, V, ldv, use_smem, (int)blockIdx.x);
+}
+
+template <typename T>
+struct backtransform_rec {
+    const T* refl;
+    int n;
+    int nwant;
+    const T* Y;
+    double* V;
+    int ldv;
+    int use_smem;
+    int gx, gy, gz;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(32 * BT_WARPS) k_backtransform_b(const __grid_constant__ BPack<backtransform_rec<T>> p) {
+    const backtransform_rec<T>& r = p.r[blockIdx.y];
+    int bx, by, bz;
+    if (!bat_block(r, bx, by, bz)) return;
+    backtransform_dev<T>(r.refl, r.n, r.nwant, r.Y, r.V, r.ldv, r.use_smem, bx);
+}
+
+
 // Ogita-Aishima correction for the leading R columns: E (n x R), refined eigenvalues lam1.
 // G = X^T X1, S = X^T Z X1 (n x R each), lam_all: approximate eigenvalues of every column.
-__global__ void k_oa_update(const double* __restrict__ G, const double* __restrict__ S,
-                            const double* __restrict__ lam_all, int n, int R, double* __restrict__ E,
-                            double* __restrict__ lam1) {
+__device__ __forceinline__ void oa_update_dev(const double* __restrict__ G, const double* __restrict__ S,
+                                              const double* __restrict__ lam_all, int n, int R, double* __restrict__ E,
+                                              double* __restrict__ lam1) {
     __shared__ double lt[256];
     for (int j = threadIdx.x; j < R; j += blockDim.x) {
         const double rjj = 1.0 - G[(size_t)j * R + j];
@@ -1239,9 +1539,34 @@ __global__ void k_oa_update(const double* __restrict__ G, const double* __restri
     for (int j = threadIdx.x; j < R; j += blockDim.x) lam1[j] = lt[j];
 }
 
+__global__ void k_oa_update(const double* __restrict__ G, const double* __restrict__ S,
+                            const double* __restrict__ lam_all, int n, int R, double* __restrict__ E,
+                            double* __restrict__ lam1) {
+    oa_update_dev(G, S, lam_all, n, R, E, lam1);
+}
+
+struct oa_update_rec {
+    const double* G;
+    const double* S;
+    const double* lam_all;
+    int n;
+    int R;
+    double* E;
+    double* lam1;
+    int gx, gy, gz;
+};
+
+__global__ void k_oa_update_b(const __grid_constant__ BPack<oa_update_rec> p) {
+    const oa_update_rec& r = p.r[blockIdx.y];
+    int bx, by, bz;
+    if (!bat_block(r, bx, by, bz)) return;
+    oa_update_dev(r.G, r.S, r.lam_all, r.n, r.R, r.E, r.lam1);
+}
+
+
 // descending order of the R refined pairs: w[rank] = lam[j], V[:, rank] = X1[:, j]
-__global__ void k_sort_top(const double* __restrict__ lam, const double* __restrict__ X1, int n, int ldx, int R,
-                           double* __restrict__ w, double* __restrict__ V) {
+__device__ __forceinline__ void sort_top_dev(const double* __restrict__ lam, const double* __restrict__ X1, int n, int ldx, int R,
+                                             double* __restrict__ w, double* __restrict__ V) {
     __shared__ int rank_of[256];
     for (int j = threadIdx.x; j < R; j += blockDim.x) {
         int r = 0;
@@ -1256,24 +1581,109 @@ __global__ void k_sort_top(const double* __restrict__ lam, const double* __restr
     }
 }
 
+__global__ void k_sort_top(const double* __restrict__ lam, const double* __restrict__ X1, int n, int ldx, int R,
+                           double* __restrict__ w, double* __restrict__ V) {
+    sort_top_dev(lam, X1, n, ldx, R, w, V);
+}
+
+struct sort_top_rec {
+    const double* lam;
+    const double* X1;
+    int n;
+    int ldx;
+    int R;
+    double* w;
+    double* V;
+    int gx, gy, gz;
+};
+
+__global__ void k_sort_top_b(const __grid_constant__ BPack<sort_top_rec> p) {
+    const sort_top_rec& r = p.r[blockIdx.y];
+    int bx, by, bz;
+    if (!bat_block(r, bx, by, bz)) return;
+    sort_top_dev(r.lam, r.X1, r.n, r.ldx, r.R, r.w, r.V);
+}
+
+
 // M = (3 I - G) / 2: one second-order step towards orthonormal columns (X1 <- X1 M)
-__global__ void k_halfstep(const double* __restrict__ G, int R, double* __restrict__ M) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void halfstep_dev(const double* __restrict__ G, int R, double* __restrict__ M, int bx) {
+    int t = bx * blockDim.x + threadIdx.x;
     if (t >= R * R) return;
     M[t] = ((t / R == t % R) ? 1.5 : 0.0) - 0.5 * G[t];
 }
 
-__global__ void k_f32_to_f64(const float* __restrict__ s, double* __restrict__ d, int n) {
-    int e = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_halfstep(const double* __restrict__ G, int R, double* __restrict__ M) {
+    halfstep_dev(G, R, M, (int)blockIdx.x);
+}
+
+struct halfstep_rec {
+    const double* G;
+    int R;
+    double* M;
+    int gx, gy, gz;
+};
+
+__global__ void k_halfstep_b(const __grid_constant__ BPack<halfstep_rec> p) {
+    const halfstep_rec& r = p.r[blockIdx.y];
+    int bx, by, bz;
+    if (!bat_block(r, bx, by, bz)) return;
+    halfstep_dev(r.G, r.R, r.M, bx);
+}
+
+
+__device__ __forceinline__ void f32_to_f64_dev(const float* __restrict__ s, double* __restrict__ d, int n, int bx) {
+    int e = bx * blockDim.x + threadIdx.x;
     if (e < n) d[e] = (double)s[e];
+}
+
+__global__ void k_f32_to_f64(const float* __restrict__ s, double* __restrict__ d, int n) {
+    f32_to_f64_dev(s, d, n, (int)blockIdx.x);
+}
+
+struct f32_to_f64_rec {
+    const float* s;
+    double* d;
+    int n;
+    int gx, gy, gz;
+};
+
+__global__ void k_f32_to_f64_b(const __grid_constant__ BPack<f32_to_f64_rec> p) {
+    const f32_to_f64_rec& r = p.r[blockIdx.y];
+    int bx, by, bz;
+    if (!bat_block(r, bx, by, bz)) return;
+    f32_to_f64_dev(r.s, r.d, r.n, bx);
+}
+
+
+__device__ __forceinline__ void copy_cols_dev(const double* __restrict__ src, int lds, double* __restrict__ dst, int ldd, int n,
+                                              int R, int bx) {
+    int t = bx * blockDim.x + threadIdx.x;
+    if (t >= n * R) return;
+    dst[(size_t)(t / R) * ldd + t % R] = src[(size_t)(t / R) * lds + t % R];
 }
 
 __global__ void k_copy_cols(const double* __restrict__ src, int lds, double* __restrict__ dst, int ldd, int n,
                             int R) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n * R) return;
-    dst[(size_t)(t / R) * ldd + t % R] = src[(size_t)(t / R) * lds + t % R];
+    copy_cols_dev(src, lds, dst, ldd, n, R, (int)blockIdx.x);
 }
+
+struct copy_cols_rec {
+    const double* src;
+    int lds;
+    double* dst;
+    int ldd;
+    int n;
+    int R;
+    int gx, gy, gz;
+};
+
+__global__ void k_copy_cols_b(const __grid_constant__ BPack<copy_cols_rec> p) {
+    const copy_cols_rec& r = p.r[blockIdx.y];
+    int bx, by, bz;
+    if (!bat_block(r, bx, by, bz)) return;
+    copy_cols_dev(r.src, r.lds, r.dst, r.ldd, r.n, r.R, bx);
+}
+
 
 struct EigLayout {
     float *work, *refl, *d, *e, *lam, *shift, *Yt, *iiw;
@@ -1437,6 +1847,214 @@ rbki_status syev_top_cuda(const double* A, int n, int nwant, double* w, double* 
 
 rbki_status syev_cuda(const double* A, int n, double* w, double* V, double* scratch, cudaStream_t st) {
     return syev_top_cuda(A, n, n, w, V, scratch, st);
+}
+
+}  // namespace rbki
+
+// ---- batched form: the same stages for many independent matrices, one launch per stage and
+// variant (items take exactly the kernels and shared-memory choices of syev_top_cuda) ----
+namespace rbki {
+
+rbki_status syev_top_batched(const EigItem* it, int cnt, cudaStream_t st) {
+    if (cnt <= 0) return RBKI_OK;
+    std::vector<EigLayout> L(cnt);
+    int nmax = 0;
+    for (int k = 0; k < cnt; ++k) {
+        const int n = it[k].n, nw = it[k].nwant;
+        if (n > 192 || nw > n || nw < 1) return set_error(RBKI_E_UNSUPPORTED, "batched syev: n > 192");
+        L[k] = eig_layout(it[k].scratch, n);
+        nmax = std::max(nmax, n);
+    }
+    // ---- 1. FP32 eigendecomposition ----
+    {
+        std::vector<tridiag_rows_rec> rows;
+        std::vector<tridiag_reg_rec> reg;
+        size_t rsm = 0;
+        for (int k = 0; k < cnt; ++k) {
+            const int n = it[k].n;
+            if (n <= 128) {
+                rows.push_back(tridiag_rows_rec{it[k].A, n, L[k].d, L[k].e, L[k].refl, 1, 1, 1});
+                rsm = std::max(rsm, (size_t)n * tr_ld(n) * sizeof(float));
+            } else {
+                reg.push_back(tridiag_reg_rec{it[k].A, n, L[k].d, L[k].e, L[k].refl, 1, 1, 1});
+            }
+        }
+        static const size_t rmax = max_dyn_smem(k_tridiag_rows_b);
+        if (rsm > rmax) return set_error(RBKI_E_CUDA, "syev: tridiagonalisation shared memory");
+        RBKI_TRY(bat_launch(k_tridiag_rows_b, rows.data(), (int)rows.size(), 512, rsm, st, "k_tridiag_rows_b"));
+        RBKI_TRY(bat_launch(k_tridiag_reg_b<12, 6>, reg.data(), (int)reg.size(), 512, 0, st, "k_tridiag_reg_b"));
+    }
+    {
+        const int vthr = 32;
+        static const size_t vmax = max_dyn_smem(k_tri_vec_b<float>);
+        static const size_t rvmax = max_dyn_smem(k_run_vec64_b<float>);
+        const size_t vsm = 3 * (size_t)nmax * vthr * sizeof(float);
+        const size_t rvsm = (size_t)R64_WARPS * 4 * nmax * sizeof(double);
+        if (vsm > vmax || rvsm > rvmax) return set_error(RBKI_E_UNSUPPORTED, "syev: inverse-iteration rows exceed shared memory");
+        std::vector<tri_shift_rec<float>> sh(cnt);
+        std::vector<tri_vec_rec<float>> vc(cnt);
+        std::vector<run_shift64_rec<float>> rs(cnt);
+        std::vector<run_vec64_rec<float>> rv(cnt);
+        std::vector<tri_runs_rec<float>> ru(cnt);
+        for (int k = 0; k < cnt; ++k) {
+            const int n = it[k].n;
+            const EigLayout& l = L[k];
+            sh[k] = tri_shift_rec<float>{l.d, l.e, n, n, l.shift, (int)cdiv(n, SHIFT_WARPS), 1, 1};
+            vc[k] = tri_vec_rec<float>{l.d, l.e, n, n, l.shift, l.Yt, (int)cdiv(n, vthr), 1, 1};
+            rs[k] = run_shift64_rec<float>{l.d, l.e, n, n, l.shift, l.mu64, (int)cdiv(n, R64_WARPS), 1, 1};
+            rv[k] = run_vec64_rec<float>{l.d, l.e, n, n, l.mu64, l.Yt, (int)cdiv(n, R64_WARPS), 1, 1};
+            ru[k] = tri_runs_rec<float>{l.d, l.e, n, n, l.shift, l.mu64, l.Yt, n, 1, 1};
+        }
+        RBKI_TRY(bat_launch(k_tri_shift_b<float>, sh.data(), cnt, 32 * SHIFT_WARPS, 0, st, "k_tri_shift_b"));
+        RBKI_TRY(bat_launch(k_tri_vec_b<float>, vc.data(), cnt, vthr, vsm, st, "k_tri_vec_b"));
+        RBKI_TRY(bat_launch(k_run_shift64_b<float>, rs.data(), cnt, 32 * R64_WARPS, 0, st, "k_run_shift64_b"));
+        RBKI_TRY(bat_launch(k_run_vec64_b<float>, rv.data(), cnt, 32 * R64_WARPS, rvsm, st, "k_run_vec64_b"));
+        RBKI_TRY(bat_launch(k_tri_runs_b<float>, ru.data(), cnt, 256, 0, st, "k_tri_runs_b"));
+    }
+    {
+        // Cholesky QR of the inverse-iteration vectors: the variant of syev_top_cuda per item
+        std::vector<tri_orth_reg_rec> o1, o2, o3;
+        std::vector<tri_orth_rec<float>> og0, og1;
+        std::vector<tri_orth_packed_rec<float>> op;
+        size_t s1 = 0, s2 = 0, s3 = 0, sg1 = 0, spk = 0;
+        static const size_t r0 = max_dyn_smem(k_tri_orth_reg_b<2, 1>);
+        static const size_t r1 = max_dyn_smem(k_tri_orth_reg_b<4, 2>);
+        static const size_t r2 = max_dyn_smem(k_tri_orth_reg_b<8, 4>);
+        static const size_t omax = max_dyn_smem(k_tri_orth_b<float>);
+        static const size_t opmax = max_dyn_smem(k_tri_orth_packed_b<float>);
+        for (int k = 0; k < cnt; ++k) {
+            const int n = it[k].n;
+            const size_t rsm = (2 * (size_t)n * (n + 1) + n) * sizeof(float);
+            if (n <= 32) {
+                o1.push_back(tri_orth_reg_rec{L[k].Yt, n, 1, 1, 1});
+                s1 = std::max(s1, rsm);
+            } else if (n <= 64) {
+                o2.push_back(tri_orth_reg_rec{L[k].Yt, n, 1, 1, 1});
+                s2 = std::max(s2, rsm);
+            } else if (n <= 128) {
+                o3.push_back(tri_orth_reg_rec{L[k].Yt, n, 1, 1, 1});
+                s3 = std::max(s3, rsm);
+            } else {
+                const size_t osm = (size_t)(n + 2 * n) * (n + 1) * sizeof(float);
+                const size_t opsm = ((size_t)n * (n + 1) / 2 + n + (size_t)ORTH_CH * (n + 1)) * sizeof(float);
+                if (osm <= omax) {
+                    og1.push_back(tri_orth_rec<float>{L[k].Yt, n, n, L[k].iiw, 1, 1, 1, 1});
+                    sg1 = std::max(sg1, osm);
+                } else if (opsm <= opmax) {
+                    op.push_back(tri_orth_packed_rec<float>{L[k].Yt, n, n, 1, 1, 1});
+                    spk = std::max(spk, opsm);
+                } else {
+                    og0.push_back(tri_orth_rec<float>{L[k].Yt, n, n, L[k].iiw, 0, 1, 1, 1});
+                }
+            }
+        }
+        if (s1 > r0 || s2 > r1 || s3 > r2) return set_error(RBKI_E_CUDA, "syev: orthonormalisation shared memory");
+        RBKI_TRY(bat_launch(k_tri_orth_reg_b<2, 1>, o1.data(), (int)o1.size(), 512, s1, st, "k_tri_orth_reg_b"));
+        RBKI_TRY(bat_launch(k_tri_orth_reg_b<4, 2>, o2.data(), (int)o2.size(), 512, s2, st, "k_tri_orth_reg_b"));
+        RBKI_TRY(bat_launch(k_tri_orth_reg_b<8, 4>, o3.data(), (int)o3.size(), 512, s3, st, "k_tri_orth_reg_b"));
+        RBKI_TRY(bat_launch(k_tri_orth_b<float>, og1.data(), (int)og1.size(), 256, sg1, st, "k_tri_orth_b"));
+        RBKI_TRY(bat_launch(k_tri_orth_packed_b<float>, op.data(), (int)op.size(), 256, spk, st,
+                            "k_tri_orth_packed_b"));
+        RBKI_TRY(bat_launch(k_tri_orth_b<float>, og0.data(), (int)og0.size(), 256, 0, st, "k_tri_orth_b"));
+    }
+    {
+        static const size_t bmax = max_dyn_smem(k_backtransform_b<float>);
+        std::vector<tri_rq_rec<float>> rq(cnt);
+        std::vector<backtransform_rec<float>> bs, bg;
+        std::vector<f32_to_f64_rec> cv(cnt);
+        size_t bsm_max = 0;
+        for (int k = 0; k < cnt; ++k) {
+            const int n = it[k].n;
+            const EigLayout& l = L[k];
+            rq[k] = tri_rq_rec<float>{l.d, l.e, n, n, l.Yt, l.lam, (int)cdiv(n, 64), 1, 1};
+            const size_t bsm = (size_t)n * n * sizeof(float);
+            const int b_smem = bsm <= bmax;
+            (b_smem ? bs : bg).push_back(backtransform_rec<float>{l.refl, n, n, l.Yt, l.X, n, b_smem,
+                                                                   (int)cdiv(n, BT_WARPS), 1, 1});
+            if (b_smem) bsm_max = std::max(bsm_max, bsm);
+            cv[k] = f32_to_f64_rec{l.lam, l.lam_all, n, (int)cdiv(n, 256), 1, 1};
+        }
+        RBKI_TRY(bat_launch(k_tri_rq_b<float>, rq.data(), cnt, 64, 0, st, "k_tri_rq_b"));
+        RBKI_TRY(bat_launch(k_backtransform_b<float>, bs.data(), (int)bs.size(), 32 * BT_WARPS, bsm_max, st,
+                            "k_backtransform_b"));
+        RBKI_TRY(bat_launch(k_backtransform_b<float>, bg.data(), (int)bg.size(), 32 * BT_WARPS, 0, st,
+                            "k_backtransform_b"));
+        RBKI_TRY(bat_launch(k_f32_to_f64_b, cv.data(), cnt, 256, 0, st, "k_f32_to_f64_b"));
+    }
+    // ---- 2. FP64 refinement of the leading nwant columns (sweeps per item as in syev_top_cuda) ----
+    int max_sweeps = 0;
+    for (int k = 0; k < cnt; ++k) max_sweeps = std::max(max_sweeps, it[k].nwant == it[k].n ? 5 : 2);
+    std::vector<GemmItem> g;
+    std::vector<oa_update_rec> ou;
+    std::vector<copy_cols_rec> c1, c2;
+    std::vector<CopyItem> cl;
+    for (int sw = 0; sw < max_sweeps; ++sw) {
+        std::vector<int> act;
+        for (int k = 0; k < cnt; ++k)
+            if (sw < (it[k].nwant == it[k].n ? 5 : 2)) act.push_back(k);
+        const int na = (int)act.size();
+        auto gemms = [&](auto make) -> rbki_status {
+            g.clear();
+            for (int k : act) g.push_back(make(k));
+            return gemm_f64_batched(g.data(), na, st);
+        };
+        RBKI_TRY(gemms([&](int k) {   // Z X1
+            const int n = it[k].n, R = it[k].nwant;
+            return GemmItem{false, n, R, n, it[k].A, n, L[k].X, n, L[k].ZX1, R, 0.0, L[k].part};
+        }));
+        RBKI_TRY(gemms([&](int k) {   // X^T Z X1
+            const int n = it[k].n, R = it[k].nwant;
+            return GemmItem{true, n, R, n, L[k].X, n, L[k].ZX1, R, L[k].S, R, 0.0, L[k].part};
+        }));
+        RBKI_TRY(gemms([&](int k) {   // X^T X1
+            const int n = it[k].n, R = it[k].nwant;
+            return GemmItem{true, n, R, n, L[k].X, n, L[k].X, n, L[k].G, R, 0.0, L[k].part};
+        }));
+        ou.clear();
+        c1.clear();
+        c2.clear();
+        cl.clear();
+        for (int k : act) {
+            const int n = it[k].n, R = it[k].nwant;
+            const EigLayout& l = L[k];
+            ou.push_back(oa_update_rec{l.G, l.S, l.lam_all, n, R, l.E, l.lam1, 1, 1, 1});
+            const int gc = (int)cdiv((int64_t)n * R, 256);
+            c1.push_back(copy_cols_rec{l.X, n, l.T1, R, n, R, gc, 1, 1});
+            c2.push_back(copy_cols_rec{l.T1, R, l.X, n, n, R, gc, 1, 1});
+            cl.push_back(CopyItem{l.lam1, l.lam_all, R});
+        }
+        RBKI_TRY(bat_launch(k_oa_update_b, ou.data(), na, 256, 0, st, "k_oa_update_b"));
+        RBKI_TRY(bat_launch(k_copy_cols_b, c1.data(), na, 256, 0, st, "k_copy_cols_b"));
+        RBKI_TRY(gemms([&](int k) {   // X1 + X E
+            const int n = it[k].n, R = it[k].nwant;
+            return GemmItem{false, n, R, n, L[k].X, n, L[k].E, R, L[k].T1, R, 1.0, L[k].part};
+        }));
+        RBKI_TRY(bat_launch(k_copy_cols_b, c2.data(), na, 256, 0, st, "k_copy_cols_b"));
+        RBKI_TRY(copy_f64_batched(cl.data(), na, st));
+    }
+    // X1 <- X1 (3I - X1^T X1) / 2
+    g.clear();
+    for (int k = 0; k < cnt; ++k) {
+        const int n = it[k].n, R = it[k].nwant;
+        g.push_back(GemmItem{true, R, R, n, L[k].X, n, L[k].X, n, L[k].G, R, 0.0, L[k].part});
+    }
+    RBKI_TRY(gemm_f64_batched(g.data(), cnt, st));
+    std::vector<halfstep_rec> hs(cnt);
+    std::vector<copy_cols_rec> cb(cnt);
+    std::vector<sort_top_rec> so(cnt);
+    g.clear();
+    for (int k = 0; k < cnt; ++k) {
+        const int n = it[k].n, R = it[k].nwant;
+        const EigLayout& l = L[k];
+        hs[k] = halfstep_rec{l.G, R, l.S, (int)cdiv((int64_t)R * R, 256), 1, 1};
+        g.push_back(GemmItem{false, n, R, R, l.X, n, l.S, R, l.T1, R, 0.0, l.part});
+        cb[k] = copy_cols_rec{l.T1, R, l.X, n, n, R, (int)cdiv((int64_t)n * R, 256), 1, 1};
+        so[k] = sort_top_rec{l.lam1, l.X, n, n, R, it[k].w, it[k].V, 1, 1, 1};
+    }
+    RBKI_TRY(bat_launch(k_halfstep_b, hs.data(), cnt, 256, 0, st, "k_halfstep_b"));
+    RBKI_TRY(gemm_f64_batched(g.data(), cnt, st));
+    RBKI_TRY(bat_launch(k_copy_cols_b, cb.data(), cnt, 256, 0, st, "k_copy_cols_b"));
+    return bat_launch(k_sort_top_b, so.data(), cnt, 256, 0, st, "k_sort_top_b");
 }
 
 }  // namespace rbki

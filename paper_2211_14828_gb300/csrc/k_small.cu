@@ -14,16 +14,16 @@ constexpr int AT_T = 32;    // output tile
 constexpr int AT_K = 16;    // rows per sub-chunk
 
 // part[chunk][k][l] = sum_{r in chunk} A[r][k] B[r][l]
-__global__ void __launch_bounds__(256) k_atb_part(const double* __restrict__ A, int64_t lda, int ma,
-                                                  const double* __restrict__ B, int64_t ldb, int mb,
-                                                  int64_t rows, int64_t rows_per_chunk,
-                                                  double* __restrict__ part) {
+__device__ __forceinline__ void atb_part_dev(const double* __restrict__ A, int64_t lda, int ma,
+                                             const double* __restrict__ B, int64_t ldb, int mb,
+                                             int64_t rows, int64_t rows_per_chunk,
+                                             double* __restrict__ part, int bx, int by, int bz) {
     __shared__ double as[AT_K][AT_T + 1];
     __shared__ double bs[AT_K][AT_T + 1];
     const int tid = threadIdx.x;
     const int tk = tid / 16, tl = tid % 16;          // 2 x 2 outputs per thread
-    const int k0 = blockIdx.x * AT_T, l0 = blockIdx.y * AT_T;
-    const int64_t r_lo = (int64_t)blockIdx.z * rows_per_chunk;
+    const int k0 = bx * AT_T, l0 = by * AT_T;
+    const int64_t r_lo = (int64_t)bz * rows_per_chunk;
     const int64_t r_hi = min(rows, r_lo + rows_per_chunk);
     double acc[2][2] = {{0, 0}, {0, 0}};
     for (int64_t r0 = r_lo; r0 < r_hi; r0 += AT_K) {
@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(256) k_atb_part(const double* __restrict__ A, 
         }
         __syncthreads();
     }
-    double* out = part + (int64_t)blockIdx.z * ma * mb;
+    double* out = part + (int64_t)bz * ma * mb;
 #pragma unroll
     for (int u = 0; u < 2; ++u)
 #pragma unroll
@@ -54,9 +54,37 @@ __global__ void __launch_bounds__(256) k_atb_part(const double* __restrict__ A, 
         }
 }
 
-__global__ void k_atb_reduce(const double* __restrict__ part, int nchunk, int ma, int mb,
-                             double* __restrict__ out, int64_t ldo) {
-    int e = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256) k_atb_part(const double* __restrict__ A, int64_t lda, int ma,
+                                                  const double* __restrict__ B, int64_t ldb, int mb,
+                                                  int64_t rows, int64_t rows_per_chunk,
+                                                  double* __restrict__ part) {
+    atb_part_dev(A, lda, ma, B, ldb, mb, rows, rows_per_chunk, part, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z);
+}
+
+struct atb_part_rec {
+    const double* A;
+    int64_t lda;
+    int ma;
+    const double* B;
+    int64_t ldb;
+    int mb;
+    int64_t rows;
+    int64_t rows_per_chunk;
+    double* part;
+    int gx, gy, gz;
+};
+
+__global__ void __launch_bounds__(256) k_atb_part_b(const __grid_constant__ BPack<atb_part_rec> p) {
+    const atb_part_rec& r = p.r[blockIdx.y];
+    int bx, by, bz;
+    if (!bat_block(r, bx, by, bz)) return;
+    atb_part_dev(r.A, r.lda, r.ma, r.B, r.ldb, r.mb, r.rows, r.rows_per_chunk, r.part, bx, by, bz);
+}
+
+
+__device__ __forceinline__ void atb_reduce_dev(const double* __restrict__ part, int nchunk, int ma, int mb,
+                                               double* __restrict__ out, int64_t ldo, int bx) {
+    int e = bx * blockDim.x + threadIdx.x;
     if (e >= ma * mb) return;
     // four independent loads in flight per step; fixed summation order
     const int64_t stride = (int64_t)ma * mb;
@@ -71,11 +99,34 @@ __global__ void k_atb_reduce(const double* __restrict__ part, int nchunk, int ma
     out[(int64_t)(e / mb) * ldo + e % mb] = acc;
 }
 
+__global__ void k_atb_reduce(const double* __restrict__ part, int nchunk, int ma, int mb,
+                             double* __restrict__ out, int64_t ldo) {
+    atb_reduce_dev(part, nchunk, ma, mb, out, ldo, (int)blockIdx.x);
+}
+
+struct atb_reduce_rec {
+    const double* part;
+    int nchunk;
+    int ma;
+    int mb;
+    double* out;
+    int64_t ldo;
+    int gx, gy, gz;
+};
+
+__global__ void k_atb_reduce_b(const __grid_constant__ BPack<atb_reduce_rec> p) {
+    const atb_reduce_rec& r = p.r[blockIdx.y];
+    int bx, by, bz;
+    if (!bat_block(r, bx, by, bz)) return;
+    atb_reduce_dev(r.part, r.nchunk, r.ma, r.mb, r.out, r.ldo, bx);
+}
+
+
 // G'[k][l] = M[m+k][l] - sum_{r<m} M[r][k] M[r][l]  (Pythagorean Gram of the projected block)
 // nu2[k] = M[m+k][k] (squared column norms before projection).  One CTA per column l.
-__global__ void k_gprime(const double* __restrict__ M, int m, int S, double* __restrict__ Gp,
-                         double* __restrict__ nu2) {
-    int l = blockIdx.x, k = threadIdx.x;
+__device__ __forceinline__ void gprime_dev(const double* __restrict__ M, int m, int S, double* __restrict__ Gp,
+                                           double* __restrict__ nu2, int bx) {
+    int l = bx, k = threadIdx.x;
     if (k >= S) return;
     double g = M[(int64_t)(m + k) * S + l];
     double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
@@ -90,6 +141,28 @@ __global__ void k_gprime(const double* __restrict__ M, int m, int S, double* __r
     Gp[k * S + l] = g - ((a0 + a1) + (a2 + a3));
     if (k == l) nu2[k] = g;
 }
+
+__global__ void k_gprime(const double* __restrict__ M, int m, int S, double* __restrict__ Gp,
+                         double* __restrict__ nu2) {
+    gprime_dev(M, m, S, Gp, nu2, (int)blockIdx.x);
+}
+
+struct gprime_rec {
+    const double* M;
+    int m;
+    int S;
+    double* Gp;
+    double* nu2;
+    int gx, gy, gz;
+};
+
+__global__ void k_gprime_b(const __grid_constant__ BPack<gprime_rec> p) {
+    const gprime_rec& r = p.r[blockIdx.y];
+    int bx, by, bz;
+    if (!bat_block(r, bx, by, bz)) return;
+    gprime_dev(r.M, r.m, r.S, r.Gp, r.nu2, bx);
+}
+
 
 // Cholesky G' = R^T R with pivot deflation, and Rinv (upper, zero rows/columns for
 // deflated directions).  Column k is deflated when nu2[k] == 0 or its pivot (squared norm
@@ -118,9 +191,9 @@ __device__ __forceinline__ double rcp_f64(double d) {
     return y;
 }
 
-__global__ void k_chol_deflate(const double* __restrict__ Gp, const double* __restrict__ nu2,
-                               int S, double tau, double* __restrict__ Rinv,
-                               int32_t* __restrict__ kept) {
+__device__ __forceinline__ void chol_deflate_dev(const double* __restrict__ Gp, const double* __restrict__ nu2,
+                                                 int S, double tau, double* __restrict__ Rinv,
+                                                 int32_t* __restrict__ kept) {
     // one S x S array holds both factors: the upper triangle (with the diagonal) is W, row k
     // = d_k L_{:,k}^T after step k; the strict lower triangle is L^{-1} (unit diagonal
     // implied).  Keeping the shared memory small (S = 30: 7.5 KB) lets this kernel share an
@@ -182,13 +255,37 @@ __global__ void k_chol_deflate(const double* __restrict__ Gp, const double* __re
     }
 }
 
+__global__ void k_chol_deflate(const double* __restrict__ Gp, const double* __restrict__ nu2,
+                               int S, double tau, double* __restrict__ Rinv,
+                               int32_t* __restrict__ kept) {
+    chol_deflate_dev(Gp, nu2, S, tau, Rinv, kept);
+}
+
+struct chol_deflate_rec {
+    const double* Gp;
+    const double* nu2;
+    int S;
+    double tau;
+    double* Rinv;
+    int32_t* kept;
+    int gx, gy, gz;
+};
+
+__global__ void k_chol_deflate_b(const __grid_constant__ BPack<chol_deflate_rec> p) {
+    const chol_deflate_rec& r = p.r[blockIdx.y];
+    int bx, by, bz;
+    if (!bat_block(r, bx, by, bz)) return;
+    chol_deflate_dev(r.Gp, r.nu2, r.S, r.tau, r.Rinv, r.kept);
+}
+
+
 // Q[i][m+s] = sum_t (Q[i][m+t] - sum_{r<m} Q[i][r] M[r][t]) Rinv[t][s]; ORTH_ROWS rows per CTA
 constexpr int ORTH_ROWS = 4;
-__global__ void __launch_bounds__(128) k_orth_apply(double* __restrict__ Q, int64_t ldq, int64_t rows, int m,
-                                                    int S, const double* __restrict__ M,
-                                                    const double* __restrict__ Rinv) {
+__device__ __forceinline__ void orth_apply_dev(double* __restrict__ Q, int64_t ldq, int64_t rows, int m,
+                                               int S, const double* __restrict__ M,
+                                               const double* __restrict__ Rinv, int bx) {
     extern __shared__ double tmp[];   // ORTH_ROWS x S
-    const int64_t i0 = (int64_t)blockIdx.x * ORTH_ROWS;
+    const int64_t i0 = (int64_t)bx * ORTH_ROWS;
     for (int e = threadIdx.x; e < ORTH_ROWS * S; e += blockDim.x) {
         int rr = e / S, s = e % S;
         int64_t i = i0 + rr;
@@ -226,10 +323,35 @@ __global__ void __launch_bounds__(128) k_orth_apply(double* __restrict__ Q, int6
     }
 }
 
+__global__ void __launch_bounds__(128) k_orth_apply(double* __restrict__ Q, int64_t ldq, int64_t rows, int m,
+                                                    int S, const double* __restrict__ M,
+                                                    const double* __restrict__ Rinv) {
+    orth_apply_dev(Q, ldq, rows, m, S, M, Rinv, (int)blockIdx.x);
+}
+
+struct orth_apply_rec {
+    double* Q;
+    int64_t ldq;
+    int64_t rows;
+    int m;
+    int S;
+    const double* M;
+    const double* Rinv;
+    int gx, gy, gz;
+};
+
+__global__ void __launch_bounds__(128) k_orth_apply_b(const __grid_constant__ BPack<orth_apply_rec> p) {
+    const orth_apply_rec& r = p.r[blockIdx.y];
+    int bx, by, bz;
+    if (!bat_block(r, bx, by, bz)) return;
+    orth_apply_dev(r.Q, r.ldq, r.rows, r.m, r.S, r.M, r.Rinv, bx);
+}
+
+
 // U[i][k] = sum_t Q[i][t] V[t][k]  (or V[i][k] when Q == nullptr)
-__global__ void k_form_u(const double* __restrict__ Q, int64_t ldq, int64_t rows,
-                         const double* __restrict__ V, int n, int ldv, int R, double* __restrict__ U) {
-    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void form_u_dev(const double* __restrict__ Q, int64_t ldq, int64_t rows,
+                                           const double* __restrict__ V, int n, int ldv, int R, double* __restrict__ U, int bx) {
+    int64_t e = (int64_t)bx * blockDim.x + threadIdx.x;
     if (e >= rows * R) return;
     int64_t i = e / R;
     int k = (int)(e % R);
@@ -244,9 +366,34 @@ __global__ void k_form_u(const double* __restrict__ Q, int64_t ldq, int64_t rows
     U[e] = acc;
 }
 
+__global__ void k_form_u(const double* __restrict__ Q, int64_t ldq, int64_t rows,
+                         const double* __restrict__ V, int n, int ldv, int R, double* __restrict__ U) {
+    form_u_dev(Q, ldq, rows, V, n, ldv, R, U, (int)blockIdx.x);
+}
+
+struct form_u_rec {
+    const double* Q;
+    int64_t ldq;
+    int64_t rows;
+    const double* V;
+    int n;
+    int ldv;
+    int R;
+    double* U;
+    int gx, gy, gz;
+};
+
+__global__ void k_form_u_b(const __grid_constant__ BPack<form_u_rec> p) {
+    const form_u_rec& r = p.r[blockIdx.y];
+    int bx, by, bz;
+    if (!bat_block(r, bx, by, bz)) return;
+    form_u_dev(r.Q, r.ldq, r.rows, r.V, r.n, r.ldv, r.R, r.U, bx);
+}
+
+
 // largest-|.| entry of column k made positive (lowest row index on ties); one CTA per column
-__global__ void k_sign_fix(double* __restrict__ U, int64_t rows, int R) {
-    const int k = blockIdx.x;
+__device__ __forceinline__ void sign_fix_dev(double* __restrict__ U, int64_t rows, int R, int bx) {
+    const int k = bx;
     double best = -1.0;
     int64_t bi = 0x7fffffffffffffffLL;
     for (int64_t i = threadIdx.x; i < rows; i += blockDim.x) {
@@ -277,10 +424,48 @@ __global__ void k_sign_fix(double* __restrict__ U, int64_t rows, int R) {
         for (int64_t i = threadIdx.x; i < rows; i += blockDim.x) U[i * R + k] = -U[i * R + k];
 }
 
-__global__ void k_copy(const double* __restrict__ s, double* __restrict__ d, int64_t n) {
-    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_sign_fix(double* __restrict__ U, int64_t rows, int R) {
+    sign_fix_dev(U, rows, R, (int)blockIdx.x);
+}
+
+struct sign_fix_rec {
+    double* U;
+    int64_t rows;
+    int R;
+    int gx, gy, gz;
+};
+
+__global__ void k_sign_fix_b(const __grid_constant__ BPack<sign_fix_rec> p) {
+    const sign_fix_rec& r = p.r[blockIdx.y];
+    int bx, by, bz;
+    if (!bat_block(r, bx, by, bz)) return;
+    sign_fix_dev(r.U, r.rows, r.R, bx);
+}
+
+
+__device__ __forceinline__ void copy_dev(const double* __restrict__ s, double* __restrict__ d, int64_t n, int bx) {
+    int64_t e = (int64_t)bx * blockDim.x + threadIdx.x;
     if (e < n) d[e] = s[e];
 }
+
+__global__ void k_copy(const double* __restrict__ s, double* __restrict__ d, int64_t n) {
+    copy_dev(s, d, n, (int)blockIdx.x);
+}
+
+struct copy_rec {
+    const double* s;
+    double* d;
+    int64_t n;
+    int gx, gy, gz;
+};
+
+__global__ void k_copy_b(const __grid_constant__ BPack<copy_rec> p) {
+    const copy_rec& r = p.r[blockIdx.y];
+    int bx, by, bz;
+    if (!bat_block(r, bx, by, bz)) return;
+    copy_dev(r.s, r.d, r.n, bx);
+}
+
 __global__ void k_fill_i32(int32_t* d, int32_t v, int n) {
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e < n) d[e] = v;
@@ -357,6 +542,80 @@ rbki_status fill_i32_cuda(int32_t* dst, int32_t v, int n, cudaStream_t st) {
     return RBKI_OK;
 }
 
+// ---- batched forms: one launch per kernel for all items (see bat_launch) ----
+rbki_status atb_batched(const AtbItem* it, int n, cudaStream_t st) {
+    if (n <= 0) return RBKI_OK;
+    std::vector<atb_part_rec> ap(n);
+    std::vector<atb_reduce_rec> ar(n);
+    for (int k = 0; k < n; ++k) {
+        const AtbItem& a = it[k];
+        const int nch = atb_nchunks(a.rows);
+        ap[k] = atb_part_rec{a.A, a.lda, a.ma, a.B, a.ldb, a.mb, a.rows, cdiv(a.rows, nch), a.part,
+                             (int)cdiv(a.ma, AT_T), (int)cdiv(a.mb, AT_T), nch};
+        ar[k] = atb_reduce_rec{a.part, nch, a.ma, a.mb, a.out, a.ldo, (int)cdiv((int64_t)a.ma * a.mb, 256), 1, 1};
+    }
+    RBKI_TRY(bat_launch(k_atb_part_b, ap.data(), n, 256, 0, st, "k_atb_part_b"));
+    return bat_launch(k_atb_reduce_b, ar.data(), n, 256, 0, st, "k_atb_reduce_b");
+}
+
+rbki_status orth_pass_batched(const OrthItem* it, int n, double tau, cudaStream_t st) {
+    if (n <= 0) return RBKI_OK;
+    std::vector<atb_part_rec> ap(n);
+    std::vector<atb_reduce_rec> ar(n);
+    std::vector<gprime_rec> gp(n);
+    std::vector<chol_deflate_rec> cd(n);
+    std::vector<orth_apply_rec> oa(n);
+    int smax = 0;
+    for (int k = 0; k < n; ++k) {
+        const OrthItem& o = it[k];
+        if (o.S > 128) return set_error(RBKI_E_UNSUPPORTED, "orth: block width > 128");
+        const int S = o.S, ma = o.m + S;
+        const size_t mp = (size_t)ma * S;
+        const int nch = atb_nchunks(o.rows);
+        double* part = o.scratch;
+        double* M = part + (size_t)nch * mp;
+        double* Gp = M + mp;
+        double* Rinv = Gp + (size_t)S * S;
+        double* nu2 = Rinv + (size_t)S * S;
+        ap[k] = atb_part_rec{o.Q, o.ldq, ma, o.Q + o.m, o.ldq, S, o.rows, cdiv(o.rows, nch), part,
+                             (int)cdiv(ma, AT_T), (int)cdiv(S, AT_T), nch};
+        ar[k] = atb_reduce_rec{part, nch, ma, S, M, S, (int)cdiv((int64_t)ma * S, 256), 1, 1};
+        gp[k] = gprime_rec{M, o.m, S, Gp, nu2, S, 1, 1};
+        cd[k] = chol_deflate_rec{Gp, nu2, S, tau, Rinv, o.kept, 1, 1, 1};
+        oa[k] = orth_apply_rec{o.Q, o.ldq, o.rows, o.m, S, M, Rinv, (int)cdiv(o.rows, ORTH_ROWS), 1, 1};
+        smax = std::max(smax, S);
+    }
+    const size_t sm = ((size_t)smax * smax + 2 * smax) * sizeof(double);
+    static const size_t cmax = max_dyn_smem(k_chol_deflate_b);   // thread-safe, once
+    if (sm > cmax) return set_error(RBKI_E_UNSUPPORTED, "orth: block too wide for shared memory");
+    RBKI_TRY(bat_launch(k_atb_part_b, ap.data(), n, 256, 0, st, "k_atb_part_b"));
+    RBKI_TRY(bat_launch(k_atb_reduce_b, ar.data(), n, 256, 0, st, "k_atb_reduce_b"));
+    RBKI_TRY(bat_launch(k_gprime_b, gp.data(), n, 128, 0, st, "k_gprime_b"));
+    RBKI_TRY(bat_launch(k_chol_deflate_b, cd.data(), n, 256, sm, st, "k_chol_deflate_b"));
+    return bat_launch(k_orth_apply_b, oa.data(), n, 32 * ORTH_ROWS, (size_t)ORTH_ROWS * smax * sizeof(double), st,
+                      "k_orth_apply_b");
+}
+
+rbki_status form_factor_batched(const FormItem* it, int n, cudaStream_t st) {
+    if (n <= 0) return RBKI_OK;
+    std::vector<form_u_rec> fu(n);
+    std::vector<sign_fix_rec> sf(n);
+    for (int k = 0; k < n; ++k) {
+        const FormItem& f = it[k];
+        fu[k] = form_u_rec{f.Q, f.ldq, f.rows, f.V, f.n, f.ldv, f.R, f.U, (int)cdiv(f.rows * f.R, 256), 1, 1};
+        sf[k] = sign_fix_rec{f.U, f.rows, f.R, f.R, 1, 1};
+    }
+    RBKI_TRY(bat_launch(k_form_u_b, fu.data(), n, 256, 0, st, "k_form_u_b"));
+    return bat_launch(k_sign_fix_b, sf.data(), n, 256, 0, st, "k_sign_fix_b");
+}
+
+rbki_status copy_f64_batched(const CopyItem* it, int n, cudaStream_t st) {
+    std::vector<copy_rec> cp;
+    for (int k = 0; k < n; ++k)
+        if (it[k].n > 0) cp.push_back(copy_rec{it[k].src, it[k].dst, it[k].n, (int)cdiv(it[k].n, 256), 1, 1});
+    return bat_launch(k_copy_b, cp.data(), (int)cp.size(), 256, 0, st, "k_copy_b");
+}
+
 }  // namespace rbki
 
 // ---- general small FP64 GEMM: C = op(A) B + beta C with a split over K ----
@@ -364,15 +623,15 @@ namespace rbki {
 namespace {
 
 template <bool TRANSA>
-__global__ void __launch_bounds__(256) k_gemm_part(const double* __restrict__ A, int64_t lda,
-                                                   const double* __restrict__ B, int64_t ldb, int M, int N, int K,
-                                                   int kpc, double* __restrict__ part) {
+__device__ __forceinline__ void gemm_part_dev(const double* __restrict__ A, int64_t lda,
+                                              const double* __restrict__ B, int64_t ldb, int M, int N, int K,
+                                              int kpc, double* __restrict__ part, int bx, int by, int bz) {
     __shared__ double as[AT_K][AT_T + 1];
     __shared__ double bs[AT_K][AT_T + 1];
     const int tid = threadIdx.x;
     const int tk = tid / 16, tl = tid % 16;
-    const int m0 = blockIdx.x * AT_T, n0 = blockIdx.y * AT_T;
-    const int k_lo = blockIdx.z * kpc, k_hi = min(K, k_lo + kpc);
+    const int m0 = bx * AT_T, n0 = by * AT_T;
+    const int k_lo = bz * kpc, k_hi = min(K, k_lo + kpc);
     double acc[2][2] = {{0, 0}, {0, 0}};
     for (int k0 = k_lo; k0 < k_hi; k0 += AT_K) {
         for (int e = tid; e < AT_K * AT_T; e += 256) {
@@ -392,7 +651,7 @@ __global__ void __launch_bounds__(256) k_gemm_part(const double* __restrict__ A,
         }
         __syncthreads();
     }
-    double* out = part + (int64_t)blockIdx.z * M * N;
+    double* out = part + (int64_t)bz * M * N;
 #pragma unroll
     for (int u = 0; u < 2; ++u)
 #pragma unroll
@@ -402,9 +661,38 @@ __global__ void __launch_bounds__(256) k_gemm_part(const double* __restrict__ A,
         }
 }
 
-__global__ void k_gemm_reduce(const double* __restrict__ part, int nchunk, int M, int N, double* __restrict__ C,
-                              int64_t ldc, double beta) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+template <bool TRANSA>
+__global__ void __launch_bounds__(256) k_gemm_part(const double* __restrict__ A, int64_t lda,
+                                                   const double* __restrict__ B, int64_t ldb, int M, int N, int K,
+                                                   int kpc, double* __restrict__ part) {
+    gemm_part_dev<TRANSA>(A, lda, B, ldb, M, N, K, kpc, part, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z);
+}
+
+struct gemm_part_rec {
+    const double* A;
+    int64_t lda;
+    const double* B;
+    int64_t ldb;
+    int M;
+    int N;
+    int K;
+    int kpc;
+    double* part;
+    int gx, gy, gz;
+};
+
+template <bool TRANSA>
+__global__ void __launch_bounds__(256) k_gemm_part_b(const __grid_constant__ BPack<gemm_part_rec> p) {
+    const gemm_part_rec& r = p.r[blockIdx.y];
+    int bx, by, bz;
+    if (!bat_block(r, bx, by, bz)) return;
+    gemm_part_dev<TRANSA>(r.A, r.lda, r.B, r.ldb, r.M, r.N, r.K, r.kpc, r.part, bx, by, bz);
+}
+
+
+__device__ __forceinline__ void gemm_reduce_dev(const double* __restrict__ part, int nchunk, int M, int N, double* __restrict__ C,
+                                                int64_t ldc, double beta, int bx) {
+    const int e = bx * blockDim.x + threadIdx.x;
     if (e >= M * N) return;
     const int64_t stride = (int64_t)M * N;
     double acc = 0.0;
@@ -418,6 +706,30 @@ __global__ void k_gemm_reduce(const double* __restrict__ part, int nchunk, int M
     double* cp = C + (int64_t)(e / N) * ldc + e % N;
     *cp = beta != 0.0 ? acc + beta * *cp : acc;
 }
+
+__global__ void k_gemm_reduce(const double* __restrict__ part, int nchunk, int M, int N, double* __restrict__ C,
+                              int64_t ldc, double beta) {
+    gemm_reduce_dev(part, nchunk, M, N, C, ldc, beta, (int)blockIdx.x);
+}
+
+struct gemm_reduce_rec {
+    const double* part;
+    int nchunk;
+    int M;
+    int N;
+    double* C;
+    int64_t ldc;
+    double beta;
+    int gx, gy, gz;
+};
+
+__global__ void k_gemm_reduce_b(const __grid_constant__ BPack<gemm_reduce_rec> p) {
+    const gemm_reduce_rec& r = p.r[blockIdx.y];
+    int bx, by, bz;
+    if (!bat_block(r, bx, by, bz)) return;
+    gemm_reduce_dev(r.part, r.nchunk, r.M, r.N, r.C, r.ldc, r.beta, bx);
+}
+
 
 int gemm_nchunk(int M, int N, int K) {
     const int tiles = (int)(cdiv(M, AT_T) * cdiv(N, AT_T));
@@ -441,6 +753,24 @@ rbki_status gemm_f64_cuda(bool transA, int M, int N, int K, const double* A, int
     k_gemm_reduce<<<(unsigned)cdiv((int64_t)M * N, 256), 256, 0, st>>>(part, nch, M, N, C, ldc, beta);
     RBKI_LAUNCH_CHECK("k_gemm_reduce");
     return RBKI_OK;
+}
+
+rbki_status gemm_f64_batched(const GemmItem* it, int n, cudaStream_t st) {
+    if (n <= 0) return RBKI_OK;
+    std::vector<gemm_part_rec> pt, pn;
+    std::vector<gemm_reduce_rec> rd(n);
+    for (int k = 0; k < n; ++k) {
+        const GemmItem& g = it[k];
+        const int nch = gemm_nchunk(g.M, g.N, g.K);
+        const int kpc = (int)rup(cdiv(g.K, nch), AT_K);
+        const gemm_part_rec r{g.A, g.lda, g.B, g.ldb, g.M, g.N, g.K, kpc, g.part,
+                              (int)cdiv(g.M, AT_T), (int)cdiv(g.N, AT_T), nch};
+        (g.transA ? pt : pn).push_back(r);
+        rd[k] = gemm_reduce_rec{g.part, nch, g.M, g.N, g.C, g.ldc, g.beta, (int)cdiv((int64_t)g.M * g.N, 256), 1, 1};
+    }
+    RBKI_TRY(bat_launch(k_gemm_part_b<true>, pt.data(), (int)pt.size(), 256, 0, st, "k_gemm_part_b"));
+    RBKI_TRY(bat_launch(k_gemm_part_b<false>, pn.data(), (int)pn.size(), 256, 0, st, "k_gemm_part_b"));
+    return bat_launch(k_gemm_reduce_b, rd.data(), n, 256, 0, st, "k_gemm_reduce_b");
 }
 
 }  // namespace rbki

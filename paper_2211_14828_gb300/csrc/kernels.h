@@ -1,6 +1,8 @@
 // Internal launch wrappers of librbki (host side).  Not part of the C ABI.
 #pragma once
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace rbki {
@@ -101,6 +103,82 @@ inline size_t max_dyn_smem(K kernel) {
         return 0;
     return mx;
 }
+
+// deflation threshold of the block orthonormalisation (reading c3): a column is dropped when
+// its norm orthogonal to the accepted ones is <= tau times its norm before projection
+constexpr double TAU_DEFLATE = 1e-6;
+
+// ---- batched launches ----
+// The batched twin `k_x_b` of a kernel `k_x` runs one launch for up to BMAX independent
+// items.  The items' arguments travel as records in the kernel parameter buffer (sm_90 and
+// later accept 32 KB of parameters, so no copy precedes the launch); blockIdx.y selects the
+// record and blockIdx.x is the item's own block index, flattened over the item's grid
+// (gx, gy, gz).  Both kernels call the same device body, so every item does exactly the
+// arithmetic, in the same order, of its single launch, whatever else shares the launch.
+constexpr int BMAX = 128;
+template <class R>
+struct BPack {
+    static_assert(sizeof(R) * BMAX <= 32000, "record too large for the kernel parameter buffer");
+    R r[BMAX];
+};
+template <class R>
+__device__ __forceinline__ bool bat_block(const R& r, int& bx, int& by, int& bz) {
+    const int b = (int)blockIdx.x;
+    if (b >= r.gx * r.gy * r.gz) return false;
+    bx = b % r.gx;
+    by = (b / r.gx) % r.gy;
+    bz = b / (r.gx * r.gy);
+    return true;
+}
+// Launches kernel(pack) over recs[0..n) in packs of BMAX; grid.x = the largest item grid.
+template <class R, class K>
+rbki_status bat_launch(K kernel, const R* recs, int n, int threads, size_t smem, cudaStream_t st,
+                       const char* where) {
+    static thread_local BPack<R> pack;
+    for (int i0 = 0; i0 < n; i0 += BMAX) {
+        const int cnt = std::min(BMAX, n - i0);
+        int gmax = 0;
+        for (int i = 0; i < cnt; ++i) {
+            pack.r[i] = recs[i0 + i];
+            gmax = std::max(gmax, recs[i0 + i].gx * recs[i0 + i].gy * recs[i0 + i].gz);
+        }
+        if (gmax == 0) continue;
+        kernel<<<dim3((unsigned)gmax, (unsigned)cnt), threads, smem, st>>>(pack);
+        RBKI_LAUNCH_CHECK(where);
+    }
+    return RBKI_OK;
+}
+
+// batched forms of the small FP64 stages (k_small.cu): item k of each array is independent
+struct AtbItem {
+    const double* A; int64_t lda; int ma;
+    const double* B; int64_t ldb; int mb;
+    int64_t rows; double* part; double* out; int64_t ldo;
+};
+rbki_status atb_batched(const AtbItem* it, int n, cudaStream_t st);
+struct OrthItem {
+    double* Q; int64_t ldq; int64_t rows; int m; int S; double* scratch; int32_t* kept;
+};
+rbki_status orth_pass_batched(const OrthItem* it, int n, double tau, cudaStream_t st);
+struct GemmItem {
+    bool transA; int M, N, K;
+    const double* A; int64_t lda; const double* B; int64_t ldb;
+    double* C; int64_t ldc; double beta; double* part;
+};
+rbki_status gemm_f64_batched(const GemmItem* it, int n, cudaStream_t st);
+struct FormItem {
+    const double* Q; int64_t ldq; int64_t rows; const double* V; int n; int ldv; int R; double* U;
+};
+rbki_status form_factor_batched(const FormItem* it, int n, cudaStream_t st);
+struct CopyItem {
+    const double* src; double* dst; int64_t n;
+};
+rbki_status copy_f64_batched(const CopyItem* it, int n, cudaStream_t st);
+// eigensolver (k_eig.cu): the leading nwant eigenpairs of each item's A
+struct EigItem {
+    const double* A; int n; int nwant; double* w; double* V; double* scratch;
+};
+rbki_status syev_top_batched(const EigItem* it, int n, cudaStream_t st);
 
 // profiling hook (api.cu): returns a token for prof_end, or -1 when profiling is off
 int prof_begin(int cls, cudaStream_t st);

@@ -64,12 +64,21 @@ def _same(a, b):
         assert torch.equal(ea, eb)
 
 
-def test_results_in_the_mix_equal_results_alone(rb):
+def _alone(rb, x, wl, prec, waves=True):
+    """The request alone through the path the server gives it: the batched path (a wave of
+    one) for BF16 requests when waves are on, rbki_tucker otherwise."""
+    if waves and prec != "fp64":
+        return rb.rbki_tucker_batched([x], [wl.ranks], wl.p, wl.q, [wl.seed], prec=prec)[0]
+    return rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec=prec)
+
+
+@pytest.mark.parametrize("wave_threads", [2, 0])
+def test_results_in_the_mix_equal_results_alone(rb, wave_threads):
     reqs = _requests()
     xs = [_device_input(wl, prec) for wl, prec in reqs]
-    alone = [rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec=prec) for x, (wl, prec) in zip(xs, reqs)]
+    alone = [_alone(rb, x, wl, prec, wave_threads > 0) for x, (wl, prec) in zip(xs, reqs)]
     torch.cuda.synchronize()
-    with rb.RbkiServer(0, mem_budget=1 << 30, max_slots=4) as srv:
+    with rb.RbkiServer(0, mem_budget=1 << 30, max_slots=4, wave_threads=wave_threads) as srv:
         tickets, outs = [], []
         for x, (wl, prec) in zip(xs, reqs):
             t, o = srv.submit(x, wl.ranks, wl.p, wl.q, wl.seed, prec=prec)
@@ -108,9 +117,11 @@ def test_admission_under_a_small_budget(rb):
     refused at submission."""
     reqs = _requests(n=6, seed=5)
     xs = [_device_input(wl, prec) for wl, prec in reqs]
-    need = [rb.rbki_tucker_workspace(x, wl.ranks, wl.p, wl.q, wl.seed, prec) for x, (wl, prec) in zip(xs, reqs)]
+    need = [rb.rbki_tucker_workspace(x, wl.ranks, wl.p, wl.q, wl.seed, prec) if prec == "fp64" else
+            rb.rbki_tucker_batched_workspace([x], [wl.ranks], wl.p, wl.q, [wl.seed], prec)
+            for x, (wl, prec) in zip(xs, reqs)]
     budget = int(max(need) * 1.2)
-    alone = [rb.rbki_tucker(x, wl.ranks, wl.p, wl.q, wl.seed, prec=prec) for x, (wl, prec) in zip(xs, reqs)]
+    alone = [_alone(rb, x, wl, prec) for x, (wl, prec) in zip(xs, reqs)]
     torch.cuda.synchronize()
     with rb.RbkiServer(0, mem_budget=budget, max_slots=4) as srv:
         subs = [srv.submit(x, wl.ranks, wl.p, wl.q, wl.seed, prec=prec) for x, (wl, prec) in zip(xs, reqs)]
