@@ -184,15 +184,18 @@ rbki_status rbki_tucker_batched_workspace(int32_t count, const rbki_tensor* X, c
                                           size_t* bytes);
 /* `count` independent rBKI-TK decompositions (Algorithm 2, HOSVD reading, the same outputs
  * as rbki_tucker) run as ONE wave on `stream`: every stage of Algorithms 1-2 is one launch
- * for all modes of all items (about 75 launches for a wave of q = 3 requests, whatever its
+ * for all modes of all items (about 100 launches for a wave of q <= 3 requests, whatever its
  * size), so many small requests cost what one costs in launches.
- *   - X passes (sketch, Krylov step, Gram, the core's mode products) on CUDA cores: FP32
- *     products of the BF16/FP16 value of each X entry (X rounded as it is read when its
- *     storage dtype is wider), FP32 Omega and Q, FP32 accumulation within a run of 64-column
- *     tiles and FP64 across runs, fixed order.
+ *   - X is read once per mode (I_n <= 256): one pass forms X_(n) X_(n)^T and, on Krylov-path
+ *     modes, the sketch W = X_(n) Omega (Omega as in rbki_tucker); the Krylov products are
+ *     P_j = (X_(n) X_(n)^T) Q_j in FP64 - the Krylov space of Eq. BKspace, the product
+ *     associated the other way.  X products are FP32 products of the BF16/FP16 value of each
+ *     entry (X rounded as read when stored wider), FP32 Omega, FP32 accumulation within a
+ *     unit of 32-column steps, FP64 across units, fixed order.  The core's mode products
+ *     likewise (FP32 intermediates).
  *   - Orthonormalisation, Z = Q^T P, the eigensolver and U = Q U~ in FP64 with the kernels
  *     of rbki_tucker (their batched forms: the same per-item arithmetic).
- * Each item's result depends only on the item (and the work-queue granularity table, see
+ * Each item's result depends only on the item (and the work-granularity table, see
  * rbki_wave_autotune), not on the other items of the wave.  Requires: prec BF16 or FP16,
  * flags 0 or RBKI_FLAG_SERIAL_MODES (no effect here), no column sampling, order >= 2,
  * every I_n <= 256, R_n + p <= 64, the eigenproblem (S(q+1), or I_n on the Gram path)

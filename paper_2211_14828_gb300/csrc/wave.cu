@@ -5,16 +5,21 @@
 // launches, not by HBM: one decomposition is ~250 small launches, and the host issues about
 // 200k launches/s however many threads it uses.  Here a stage is one launch whatever the
 // number of requests:
-//   * the X passes (sketch W = X_(n) Omega, Krylov step P = X_(n) (X_(n)^T Q), Gram
-//     X_(n) X_(n)^T, the core's mode products) of all items share one work-queue kernel
-//     (k_xpass_b): block (x, y) of the launch is unit x of item y, a run of 64-column tiles of
-//     X_(n) whose products it accumulates in registers; a fixed-order reduction follows;
-//   * the FP64 stages (block orthonormalisation, Z = Q^T P, the eigensolver, U = Q U~) are the
-//     batched twins of the single-call kernels (bat_launch): the same device code and the
-//     same per-item grids, so each item's result does not depend on what shares its wave.
-// The products run on CUDA cores in FP32 from BF16/FP16 values of X (X rounded to the
-// requested precision as it is read; FP32 Omega and Q), with FP32 accumulation per tile run
-// and FP64 accumulation across runs.  Orthonormalisation and the eigensolver stay FP64.
+//   * X is read once per mode: a work-queue kernel (k_gram_b) forms X_(n) X_(n)^T for every
+//     mode of every item (I_n <= 256, so the matrix is small) and, on the Krylov-path modes,
+//     the sketch W = X_(n) Omega from the same staged columns; block (x, y) of the launch is
+//     unit x of item y, a block pair of the Gram matrix over a run of 32-column steps.  The
+//     Krylov products are then P_j = (X_(n) X_(n)^T) Q_j in FP64, without touching X (the
+//     same Krylov space as X_(n) (X_(n)^T Q_j), associated the other way);
+//   * the core's mode products share a second work-queue kernel (k_ttm_b);
+//   * the FP64 stages (block orthonormalisation, Z = Q^T P, the eigensolver, U = Q U~, the
+//     Krylov products) are the batched twins of the single-call kernels (bat_launch): the
+//     same device code and the same per-item grids.
+// Every per-item partition (units, steps per unit) depends only on the item's shape and the
+// reductions have a fixed order, so each item's result does not depend on its wave.
+// Products with X are FP32 products of the BF16/FP16 value of each entry of X (rounded as it
+// is read when the storage is wider) with FP32 Omega / U, FP32 accumulation within a unit and
+// FP64 across units; orthonormalisation, the Krylov products and the eigensolver are FP64.
 #include "kernels.h"
 #include "plan.h"
 
@@ -25,9 +30,11 @@
 namespace rbki {
 namespace {
 
-enum XOp { XO_SKETCH = 0, XO_KRYLOV = 1, XO_GRAM = 2, XO_TTM = 3 };
-constexpr int XT = 64;          // columns of X_(n) per tile
-constexpr int XTHREADS = 256;   // 8 warps
+constexpr int GB = 64;          // rows of a block of X_(n) X_(n)^T
+constexpr int KT = 32;          // columns of X_(n) per step of the Gram pass
+constexpr int GP = GB + 4;      // shared-memory pitch of a staged block (16-byte rows)
+constexpr int TT = 64;          // columns of X_(n) per tile of a mode product
+constexpr int NTHREADS = 256;   // 8 warps
 
 __device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
 __device__ __forceinline__ float to_f32(__half v) { return __half2float(v); }
@@ -39,109 +46,270 @@ __device__ __forceinline__ float round_to(float v, int rnd) {
     return v;
 }
 
-// XTs[t][i] = X_(n)[i][col0 + t] for the tile's 64 columns (colb[t] = offset of X[a][0][c],
-// -1 past the end); coalesced along c (C > 1) or along i (C == 1), loads unrolled by 4
+// column offsets of X_(n): colb[k] = offset of X[a][0][c] for column col0 + k, -1 past the end
+__device__ __forceinline__ void column_bases(int64_t col0, int ncol, int64_t J, int I, int64_t C, int64_t* colb) {
+    for (int k = threadIdx.x; k < ncol; k += NTHREADS) {
+        const int64_t col = col0 + k;
+        colb[k] = col < J ? (col / C) * I * C + col % C : -1;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Gram pass: G = X_(n) X_(n)^T (and W = X_(n) Omega) for I_n <= 256, one pass over X.
+// Block pair (bi <= bj) of 64 x 64 rows of G, unit u = a run of 32-column steps: the two row
+// blocks of the step are staged transposed (As[k][r], pitch 68), each thread accumulates a
+// 4 x 4 tile (two 16-byte loads per 16 FMAs).  The diagonal pairs of a Krylov-path item also
+// accumulate W's rows of their block: Omega's 32 x S entries are generated in place (Philox
+// keyed by (seed, mode, column, pair)) and each thread holds S8/4 columns of one row.
+// ---------------------------------------------------------------------------------------
+struct gram_rec {
+    const void* x;       // the item's tensor, viewed as [A][I][C]
+    int dtype, rnd;      // storage dtype; rounding applied as values are read (0: none)
+    int A, I, C;
+    int nb, npair;       // row blocks of 64; block pairs bi <= bj
+    int ksteps, kpu;     // 32-column steps of X_(n); steps per unit
+    int S;               // sketch width (0: no sketch)
+    uint64_t seed;
+    int mode;
+    float* gpart;        // [unit][I][I]: block pairs (diagonal blocks in full)
+    float* wpart;        // [unit][I][S]
+    int gx, gy, gz;      // npair * units, 1, 1
+};
+
+template <typename T>
+__device__ __forceinline__ void stage_rows(const T* __restrict__ x, const int64_t* colb, int row0, int I, int64_t C,
+                                           int rnd, float* As) {
+    if (C == 1) {
+        // columns are contiguous along i
+#pragma unroll 4
+        for (int e = threadIdx.x; e < KT * GB; e += NTHREADS) {
+            const int k = e / GB, rr = e % GB, i = row0 + rr;
+            const int64_t cb = colb[k];
+            As[k * GP + rr] = (cb >= 0 && i < I) ? round_to(to_f32(x[cb + i]), rnd) : 0.f;
+        }
+    } else {
+        // consecutive columns are contiguous along c
+#pragma unroll 4
+        for (int e = threadIdx.x; e < KT * GB; e += NTHREADS) {
+            const int rr = e / KT, k = e % KT, i = row0 + rr;
+            const int64_t cb = colb[k];
+            As[k * GP + rr] = (cb >= 0 && i < I) ? round_to(to_f32(x[cb + (int64_t)i * C]), rnd) : 0.f;
+        }
+    }
+}
+
+__device__ __forceinline__ void gram_dev(const gram_rec& r, int bx) {
+    extern __shared__ __align__(16) float gsm[];
+    const int pair = bx % r.npair, unit = bx / r.npair;
+    int bi = 0, bj = 0;
+    for (int p = pair, b = 0; b < r.nb; ++b) {
+        if (p < r.nb - b) {
+            bi = b;
+            bj = b + p;
+            break;
+        }
+        p -= r.nb - b;
+    }
+    const bool diag = bi == bj, sk = diag && r.S > 0;
+    const int S8 = (r.S + 7) & ~7, wn = S8 / 4;   // sketch columns per thread
+    float* As = gsm;
+    float* Bs = As + KT * GP;
+    float* Om = Bs + KT * GP;
+    int64_t* colb = reinterpret_cast<int64_t*>(Om + KT * 64);
+    const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
+    const int rr = tid % 64, cg = tid / 64;
+    const int64_t C = r.C, J = (int64_t)r.A * r.C;
+    float acc[4][4], wacc[16];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) wacc[c] = 0.f;
+    const int k_lo = unit * r.kpu, k_hi = min(r.ksteps, k_lo + r.kpu);
+    for (int t = k_lo; t < k_hi; ++t) {
+        const int64_t col0 = (int64_t)t * KT;
+        __syncthreads();   // the previous step is consumed
+        column_bases(col0, KT, J, r.I, C, colb);
+        __syncthreads();
+        switch (r.dtype) {
+            case RBKI_BF16:
+                stage_rows(static_cast<const __nv_bfloat16*>(r.x), colb, bi * GB, r.I, C, r.rnd, As);
+                if (!diag) stage_rows(static_cast<const __nv_bfloat16*>(r.x), colb, bj * GB, r.I, C, r.rnd, Bs);
+                break;
+            case RBKI_F16:
+                stage_rows(static_cast<const __half*>(r.x), colb, bi * GB, r.I, C, r.rnd, As);
+                if (!diag) stage_rows(static_cast<const __half*>(r.x), colb, bj * GB, r.I, C, r.rnd, Bs);
+                break;
+            case RBKI_F32:
+                stage_rows(static_cast<const float*>(r.x), colb, bi * GB, r.I, C, r.rnd, As);
+                if (!diag) stage_rows(static_cast<const float*>(r.x), colb, bj * GB, r.I, C, r.rnd, Bs);
+                break;
+            default:
+                stage_rows(static_cast<const double*>(r.x), colb, bi * GB, r.I, C, r.rnd, As);
+                if (!diag) stage_rows(static_cast<const double*>(r.x), colb, bj * GB, r.I, C, r.rnd, Bs);
+                break;
+        }
+        if (sk) {
+            const int np = S8 / 2;
+            for (int e = tid; e < KT * np; e += NTHREADS) {
+                const int k = e / np, pr = e % np, s = 2 * pr;
+                float z0 = 0.f, z1 = 0.f;
+                if (colb[k] >= 0 && s < r.S)
+                    omega_pair_f32(r.seed, (uint32_t)r.mode, (uint64_t)(col0 + k), (uint32_t)pr, z0, z1);
+                Om[k * 64 + s] = z0;
+                Om[k * 64 + s + 1] = s + 1 < r.S ? z1 : 0.f;
+            }
+        }
+        __syncthreads();
+        const float* Bsrc = diag ? As : Bs;
+#pragma unroll 4
+        for (int k = 0; k < KT; ++k) {
+            const float4 a4 = *reinterpret_cast<const float4*>(As + k * GP + ty * 4);
+            const float4 b4 = *reinterpret_cast<const float4*>(Bsrc + k * GP + tx * 4);
+            const float av[4] = {a4.x, a4.y, a4.z, a4.w}, bv[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
+        }
+        if (sk) {
+            for (int k = 0; k < KT; ++k) {
+                const float a = As[k * GP + rr];
+#pragma unroll
+                for (int c = 0; c < 16; ++c)
+                    if (c < wn) wacc[c] = fmaf(a, Om[k * 64 + cg * wn + c], wacc[c]);
+            }
+        }
+    }
+    float* g = r.gpart + (int64_t)unit * r.I * r.I;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int i = bi * GB + ty * 4 + a;
+        if (i >= r.I) continue;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int j = bj * GB + tx * 4 + b;
+            if (j < r.I) g[(int64_t)i * r.I + j] = acc[a][b];
+        }
+    }
+    if (sk) {
+        const int i = bi * GB + rr;
+        if (i < r.I) {
+            float* w = r.wpart + ((int64_t)unit * r.I + i) * r.S;
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+                const int s = cg * wn + c;
+                if (c < wn && s < r.S) w[s] = wacc[c];
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(NTHREADS) k_gram_b(const __grid_constant__ BPack<gram_rec> p) {
+    const gram_rec& r = p.r[blockIdx.y];
+    int bx, by, bz;
+    if (!bat_block(r, bx, by, bz)) return;
+    gram_dev(r, bx);
+}
+
+constexpr size_t GRAM_SMEM = (2 * KT * GP + KT * 64) * sizeof(float) + KT * sizeof(int64_t);
+
+// G (FP64, I x I) = sum over units of the block pairs, in unit order; the lower blocks mirror
+// the upper ones, the diagonal blocks are symmetrised: G is exactly symmetric.
+struct greduce_rec {
+    const float* gpart;
+    int units, I;
+    double* G;
+    int gx, gy, gz;
+};
+
+__global__ void __launch_bounds__(256) k_greduce_b(const __grid_constant__ BPack<greduce_rec> p) {
+    const greduce_rec& r = p.r[blockIdx.y];
+    int bx, by, bz;
+    if (!bat_block(r, bx, by, bz)) return;
+    const int e = bx * 256 + threadIdx.x;
+    if (e >= r.I * r.I) return;
+    const int i = e / r.I, j = e % r.I, bi = i / GB, bj = j / GB;
+    const int64_t us = (int64_t)r.I * r.I;
+    auto sum = [&](int a, int b) {
+        double v = 0.0;
+        for (int u = 0; u < r.units; ++u) v += (double)r.gpart[u * us + (int64_t)a * r.I + b];
+        return v;
+    };
+    r.G[e] = bi < bj ? sum(i, j) : bi > bj ? sum(j, i) : 0.5 * (sum(i, j) + sum(j, i));
+}
+
+// ---------------------------------------------------------------------------------------
+// Mode product of the core chain: T[a][s][c] = sum_i X[a][i][c] U[i][s] (S = R_n <= 64).
+// Unit = a run of 64-column tiles of X_(n): the tile is staged transposed (XT[t][i], odd
+// pitch); warp (g, h) of the product owns columns 8g..8g+7 of U and the share h of the rows
+// i, the shares meet in shared memory in a fixed order; results are written along c.
+// ---------------------------------------------------------------------------------------
+struct ttm_rec {
+    const void* x;
+    int dtype, rnd;
+    int A, I, C, S;
+    int tiles, tpu;
+    const double* U;     // I x S, ld ldu
+    int ldu;
+    void* out;           // [A][S][C], FP32 or FP64 (odt)
+    int odt;
+    int gx, gy, gz;
+};
+
+__host__ __device__ inline int ttm_ip(int I) { return I | 1; }
+__host__ __device__ inline int s8_of(int S) { return (S + 7) & ~7; }
+size_t ttm_smem(const ttm_rec& r) {
+    const int S8 = s8_of(r.S), ns = 8 / (S8 / 8);
+    return ((size_t)TT * ttm_ip(r.I) + (size_t)r.I * S8 + (size_t)TT * S8 + (ns > 1 ? (size_t)ns * TT * S8 : 0)) *
+               sizeof(float) + TT * sizeof(int64_t);
+}
+
 template <typename T>
 __device__ __forceinline__ void stage_tile(const T* __restrict__ x, const int64_t* colb, int I, int Ip, int64_t C,
                                            int rnd, float* XTs) {
-    const int n = 64 * I;
+    const int n = TT * I;
     if (C == 1) {
 #pragma unroll 4
-        for (int e = threadIdx.x; e < n; e += 256) {
+        for (int e = threadIdx.x; e < n; e += NTHREADS) {
             const int tt = e / I, i = e - tt * I;
             const int64_t cb = colb[tt];
             XTs[tt * Ip + i] = cb >= 0 ? round_to(to_f32(x[cb + i]), rnd) : 0.f;
         }
     } else {
 #pragma unroll 4
-        for (int e = threadIdx.x; e < n; e += 256) {
-            const int i = e >> 6, tt = e & 63;
+        for (int e = threadIdx.x; e < n; e += NTHREADS) {
+            const int i = e / TT, tt = e % TT;
             const int64_t cb = colb[tt];
             XTs[tt * Ip + i] = cb >= 0 ? round_to(to_f32(x[cb + (int64_t)i * C]), rnd) : 0.f;
         }
     }
 }
 
-struct xpass_rec {
-    const void* x;          // the item's tensor, viewed as [A][I][C] for its mode
-    int dtype, rnd;         // storage dtype; rounding applied as values are read (0: none)
-    int A, I, C;
-    int op, S;              // XOp; product width (<= 64; Gram: I, in column blocks of 64)
-    int tiles, tpu;         // 64-column tiles of X_(n); tiles per unit
-    const double* Q;        // KRYLOV / TTM operand, I x S (ld ldq)
-    int ldq;
-    uint64_t seed;          // SKETCH: Omega^(mode) (Philox4x32-10 + Box-Muller)
-    int mode;
-    float* part;            // SKETCH / KRYLOV / GRAM: [unit][I][ldp] partial sums
-    int ldp;
-    void* tout;             // TTM: [A][S][C] result, FP32 or FP64 (tdt)
-    int tdt;
-    int gx, gy, gz;         // units, Gram column blocks, 1
-};
-
-__host__ __device__ inline int xp_ip(int I) { return I | 1; }   // odd pitch: conflict-free columns
-__host__ __device__ inline int xp_s8(int S) { return (S + 7) & ~7; }
-size_t xpass_smem(const xpass_rec& r) {
-    const int S = r.op == XO_GRAM ? std::min(64, r.I) : r.S;
-    const int S8 = xp_s8(S);
-    const bool q = r.op == XO_KRYLOV || r.op == XO_TTM;
-    const int ns1 = 8 / (S8 / 8);
-    return ((size_t)XT * xp_ip(r.I) + (q ? (size_t)r.I * S8 : 0) + (size_t)XT * S8 +
-            (q && ns1 > 1 ? (size_t)ns1 * XT * S8 : 0)) * sizeof(float) +
-           XT * sizeof(int64_t);
-}
-
-// Unit `unit` of one item: tiles [unit * tpu, (unit + 1) * tpu).  Per tile the X tile is
-// staged transposed (XT[t][i], odd pitch), then
-//   SKETCH:  Y[t][s] = Omega(col t, s)                      (generated in place)
-//   KRYLOV:  Y = X_tile^T Q                                  (GEMM 1: warp w -> 8 columns)
-//   TTM:     Y = X_tile^T U, written out as [A][S][C]
-//   GRAM:    Y[t][s] = X[sb + s][t]                          (the tile itself)
-// and, except for TTM, P += X_tile Y (GEMM 2: warp w -> 8 columns x a share of the rows,
-// registers across all tiles of the unit).  MR bounds the 32-row groups a thread of GEMM 2
-// accumulates (ceil(ceil(I/32) / warps per column group)): launches are split by MR so that
-// small items run with fewer registers and less shared memory, hence more CTAs per SM.
-template <int MR>
-__device__ __forceinline__ void xpass_dev(const xpass_rec& r, int unit, int blk) {
-    extern __shared__ __align__(16) float xsm[];
-    const int I = r.I, Ip = xp_ip(I);
-    const int sb = r.op == XO_GRAM ? blk * 64 : 0;
-    const int S = r.op == XO_GRAM ? min(64, I - sb) : r.S;
-    const int S8 = xp_s8(S);
-    const bool useq = r.op == XO_KRYLOV || r.op == XO_TTM;
-    const int G = S8 / 8;
-    const int ns1 = 8 / G;                    // GEMM 1: warps per column group (row shares)
-    const int ns2 = 8 / G;                    // GEMM 2: warps per column group (row split)
-    float* XTs = xsm;
-    float* Qs = XTs + XT * Ip;
-    float* Ys = Qs + (useq ? I * S8 : 0);
-    float* Yp = Ys + XT * S8;                 // GEMM 1 row-share partials (ns1 > 1)
-    int64_t* colb = reinterpret_cast<int64_t*>(Yp + (useq && ns1 > 1 ? ns1 * XT * S8 : 0));
+__device__ __forceinline__ void ttm_dev(const ttm_rec& r, int unit) {
+    extern __shared__ __align__(16) float tsm[];
+    const int I = r.I, Ip = ttm_ip(I), S = r.S, S8 = s8_of(S);
+    const int G = S8 / 8, ns = 8 / G;
+    float* XTs = tsm;
+    float* Us = XTs + TT * Ip;
+    float* Ys = Us + I * S8;
+    float* Yp = Ys + TT * S8;
+    int64_t* colb = reinterpret_cast<int64_t*>(Yp + (ns > 1 ? ns * TT * S8 : 0));
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int64_t C = r.C, J = (int64_t)r.A * r.C;
-    if (useq)
-        for (int e = tid; e < I * S8; e += XTHREADS) {
-            const int i = e / S8, s = e % S8;
-            Qs[e] = s < S ? (float)r.Q[(int64_t)i * r.ldq + s] : 0.f;
-        }
-    const bool act1 = w < G * ns1;
-    const int g1 = w % G, h1 = w / G;
-    const bool act2 = w < G * ns2;
-    const int g2 = w % G, h2 = w / G;
-    const int nr32 = (I + 31) / 32;
-    float acc[MR][8];
-#pragma unroll
-    for (int k = 0; k < MR; ++k)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[k][j] = 0.f;
+    for (int e = tid; e < I * S8; e += NTHREADS) {
+        const int i = e / S8, s = e % S8;
+        Us[e] = s < S ? (float)r.U[(int64_t)i * r.ldu + s] : 0.f;
+    }
+    const bool act = w < G * ns;
+    const int g = w % G, h = w / G;
+    const int il = (I + ns - 1) / ns, i_lo = h * il, i_hi = min(I, i_lo + il);
     const int t_lo = unit * r.tpu, t_hi = min(r.tiles, t_lo + r.tpu);
     for (int t = t_lo; t < t_hi; ++t) {
-        const int64_t col0 = (int64_t)t * XT;
-        __syncthreads();   // the previous tile is consumed
-        if (tid < XT) {
-            const int64_t col = col0 + tid;
-            colb[tid] = col < J ? (col / C) * I * C + col % C : -1;
-        }
+        const int64_t col0 = (int64_t)t * TT;
+        __syncthreads();
+        column_bases(col0, TT, J, I, C, colb);
         __syncthreads();
         switch (r.dtype) {
             case RBKI_BF16: stage_tile(static_cast<const __nv_bfloat16*>(r.x), colb, I, Ip, C, r.rnd, XTs); break;
@@ -149,130 +317,83 @@ __device__ __forceinline__ void xpass_dev(const xpass_rec& r, int unit, int blk)
             case RBKI_F32: stage_tile(static_cast<const float*>(r.x), colb, I, Ip, C, r.rnd, XTs); break;
             default: stage_tile(static_cast<const double*>(r.x), colb, I, Ip, C, r.rnd, XTs); break;
         }
-        if (r.op == XO_SKETCH) {
-            const int np = S8 / 2;
-            for (int e = tid; e < XT * np; e += XTHREADS) {
-                const int tt = e / np, pr = e % np, s = 2 * pr;
-                float z0 = 0.f, z1 = 0.f;
-                if (colb[tt] >= 0 && s < S)
-                    omega_pair_f32(r.seed, (uint32_t)r.mode, (uint64_t)(col0 + tt), (uint32_t)pr, z0, z1);
-                Ys[tt * S8 + s] = z0;
-                Ys[tt * S8 + s + 1] = s + 1 < S ? z1 : 0.f;
+        __syncthreads();
+        if (act) {
+            const int s0 = 8 * g;
+            float a1[2][8];
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) a1[u][j] = 0.f;
+            for (int i = i_lo; i < i_hi; ++i) {
+                const float4 qa = *reinterpret_cast<const float4*>(Us + i * S8 + s0);
+                const float4 qb = *reinterpret_cast<const float4*>(Us + i * S8 + s0 + 4);
+                const float qv[8] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z, qb.w};
+                const float x0 = XTs[lane * Ip + i], x1 = XTs[(lane + 32) * Ip + i];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    a1[0][j] = fmaf(x0, qv[j], a1[0][j]);
+                    a1[1][j] = fmaf(x1, qv[j], a1[1][j]);
+                }
+            }
+            float* dst = ns == 1 ? Ys : Yp + h * TT * S8;
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) dst[(lane + 32 * u) * S8 + s0 + j] = a1[u][j];
+        }
+        if (ns > 1) {
+            __syncthreads();
+            for (int e = tid; e < TT * S8; e += NTHREADS) {
+                float v = 0.f;
+                for (int hh = 0; hh < ns; ++hh) v += Yp[hh * TT * S8 + e];
+                Ys[e] = v;
             }
         }
         __syncthreads();
-        if (useq) {
-            // GEMM 1, Y = X_tile^T Q: warp (g, h) owns columns 8g..8g+7 and rows i of its share
-            // [h*il, (h+1)*il) for both 32-column halves; the ns1 shares meet in Yp
-            if (act1) {
-                const int s0 = 8 * g1;
-                const int il = (I + ns1 - 1) / ns1, i_lo = h1 * il, i_hi = min(I, i_lo + il);
-                float a1[2][8];
-#pragma unroll
-                for (int u = 0; u < 2; ++u)
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) a1[u][j] = 0.f;
-                for (int i = i_lo; i < i_hi; ++i) {
-                    const float4 qa = *reinterpret_cast<const float4*>(Qs + i * S8 + s0);
-                    const float4 qb = *reinterpret_cast<const float4*>(Qs + i * S8 + s0 + 4);
-                    const float qv[8] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z, qb.w};
-                    const float x0 = XTs[lane * Ip + i], x1 = XTs[(lane + 32) * Ip + i];
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        a1[0][j] = fmaf(x0, qv[j], a1[0][j]);
-                        a1[1][j] = fmaf(x1, qv[j], a1[1][j]);
-                    }
-                }
-                float* dst = ns1 == 1 ? Ys : Yp + h1 * XT * S8;
-#pragma unroll
-                for (int u = 0; u < 2; ++u)
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) dst[(lane + 32 * u) * S8 + s0 + j] = a1[u][j];
-            }
-            if (ns1 > 1) {
-                __syncthreads();
-                for (int e = tid; e < XT * S8; e += XTHREADS) {
-                    float v = 0.f;
-                    for (int h = 0; h < ns1; ++h) v += Yp[h * XT * S8 + e];
-                    Ys[e] = v;
-                }
-            }
-            __syncthreads();
-            if (r.op == XO_TTM) {
-                // T[a][s][c] for the tile's valid columns (coalesced along c)
-                for (int e = tid; e < XT * S; e += XTHREADS) {
-                    const int s = e / XT, tt = e % XT;
-                    const int64_t col = col0 + tt;
-                    if (col >= J) continue;
-                    const int64_t a = col / C, c = col % C;
-                    const int64_t o = (a * S + s) * C + c;
-                    const float v = Ys[tt * S8 + s];
-                    if (r.tdt == RBKI_F64) static_cast<double*>(r.tout)[o] = (double)v;
-                    else static_cast<float*>(r.tout)[o] = v;
-                }
-                continue;
-            }
+        for (int e = tid; e < TT * S; e += NTHREADS) {
+            const int s = e / TT, tt = e % TT;
+            const int64_t col = col0 + tt;
+            if (col >= J) continue;
+            const int64_t a = col / C, c = col % C;
+            const int64_t o = (a * S + s) * C + c;
+            const float v = Ys[tt * S8 + s];
+            if (r.odt == RBKI_F64) static_cast<double*>(r.out)[o] = (double)v;
+            else static_cast<float*>(r.out)[o] = v;
         }
-        if (act2) {
-            const int s0 = 8 * g2;
-            for (int tt = 0; tt < XT; ++tt) {
-                float yv[8];
-                if (r.op == XO_GRAM) {
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) yv[j] = s0 + j < S ? XTs[tt * Ip + sb + s0 + j] : 0.f;
-                } else {
-                    const float4 ya = *reinterpret_cast<const float4*>(Ys + tt * S8 + s0);
-                    const float4 yb = *reinterpret_cast<const float4*>(Ys + tt * S8 + s0 + 4);
-                    yv[0] = ya.x; yv[1] = ya.y; yv[2] = ya.z; yv[3] = ya.w;
-                    yv[4] = yb.x; yv[5] = yb.y; yv[6] = yb.z; yv[7] = yb.w;
-                }
-#pragma unroll
-                for (int k = 0; k < MR; ++k) {
-                    const int m = h2 + k * ns2;
-                    if (m >= nr32) break;
-                    const int i = lane + 32 * m;
-                    const float xv = i < I ? XTs[tt * Ip + i] : 0.f;
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) acc[k][j] = fmaf(xv, yv[j], acc[k][j]);
-                }
-            }
-        }
-    }
-    if (r.op == XO_TTM || !act2) return;
-    float* out = r.part + (int64_t)unit * I * r.ldp + sb;
-    const int s0 = 8 * g2;
-#pragma unroll
-    for (int k = 0; k < MR; ++k) {
-        const int m = h2 + k * ns2;
-        if (m >= nr32) break;
-        const int i = lane + 32 * m;
-        if (i >= I) continue;
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-            if (s0 + j < S) out[(int64_t)i * r.ldp + s0 + j] = acc[k][j];
     }
 }
 
-template <int MR>
-__global__ void __launch_bounds__(XTHREADS, MR <= 2 ? 3 : 2) k_xpass_b(const __grid_constant__ BPack<xpass_rec> p) {
-    const xpass_rec& r = p.r[blockIdx.y];
+__global__ void __launch_bounds__(NTHREADS, 2) k_ttm_b(const __grid_constant__ BPack<ttm_rec> p) {
+    const ttm_rec& r = p.r[blockIdx.y];
     int bx, by, bz;
     if (!bat_block(r, bx, by, bz)) return;
-    xpass_dev<MR>(r, bx, by);
+    ttm_dev(r, bx);
 }
 
-// row groups per GEMM-2 thread of a record (GEMM 2 only runs for SKETCH / KRYLOV / GRAM)
-int xpass_mr(const xpass_rec& r) {
-    const int S = r.op == XO_GRAM ? std::min(64, r.I) : r.S;
-    const int G = xp_s8(S) / 8, ns2 = 8 / G, nr32 = (r.I + 31) / 32;
-    return (nr32 + ns2 - 1) / ns2;
+// dst[i][s] = src[i][s] for i < rows, s < cols (strided blocks: Q_{j+1} <- P_j)
+struct blkcopy_rec {
+    const double* src;
+    int lds;
+    double* dst;
+    int ldd, rows, cols;
+    int gx, gy, gz;
+};
+
+__global__ void __launch_bounds__(256) k_blkcopy_b(const __grid_constant__ BPack<blkcopy_rec> p) {
+    const blkcopy_rec& r = p.r[blockIdx.y];
+    int bx, by, bz;
+    if (!bat_block(r, bx, by, bz)) return;
+    const int e = bx * 256 + threadIdx.x;
+    if (e >= r.rows * r.cols) return;
+    const int i = e / r.cols, s = e % r.cols;
+    r.dst[(int64_t)i * r.ldd + s] = r.src[(int64_t)i * r.lds + s];
 }
 
-// out1[i][s] (= out2[i][s]) = sum over units of part[u][i][s], in unit order, FP64;
-// sym: 0.5 (G[i][s] + G[s][i]) (the Gram path's Z, symmetric by construction)
+// out1[i][s] (= out2[i][s]) = sum over units of part[u][i][s], in unit order, FP64
 struct xreduce_rec {
     const float* part;
-    int units, I, S, ldp, sym;
+    int units, I, S, ldp;
     double* out1;
     int ld1;
     double* out2;
@@ -290,11 +411,6 @@ __global__ void __launch_bounds__(256) k_xreduce_b(const __grid_constant__ BPack
     const int64_t us = (int64_t)r.I * r.ldp;
     double a = 0.0;
     for (int u = 0; u < r.units; ++u) a += (double)r.part[u * us + (int64_t)i * r.ldp + s];
-    if (r.sym) {
-        double b = 0.0;
-        for (int u = 0; u < r.units; ++u) b += (double)r.part[u * us + (int64_t)s * r.ldp + i];
-        a = 0.5 * (a + b);
-    }
     r.out1[(int64_t)i * r.ld1 + s] = a;
     if (r.out2) r.out2[(int64_t)i * r.ld2 + s] = a;
 }
@@ -411,36 +527,31 @@ __global__ void k_info_b(const __grid_constant__ BPack<info_rec> p) {
 }  // namespace rbki
 
 // ---------------------------------------------------------------------------------------
-// Work-queue granularity: tiles per unit of an item.  A unit is one CTA; smaller units spread
-// an item over more SMs, larger ones leave fewer partial sums to reduce.  The work per unit
-// comes from a table by (op, I_n, S) bucket: a default, or the values measured by
-// rbki_wave_autotune / read by rbki_wave_tune_load.
+// Work-queue granularity: steps (Gram pass) or tiles (mode products) per unit of an item.  A
+// unit is one CTA: smaller units spread an item over more SMs, larger ones leave fewer
+// partial sums to reduce.  The table holds the target steps per unit by (kind, I_n) bucket:
+// a default, or the values measured by rbki_wave_autotune / read by rbki_wave_tune_load.
 // ---------------------------------------------------------------------------------------
 namespace rbki {
 namespace {
 
-constexpr int TUNE_OPS = 4, TUNE_IB = 8, TUNE_SB = 8;   // I_n in 32-buckets, S in 8-buckets
-constexpr double DEFAULT_WORK = 49152.0;                 // ~10 tiles of a 144 x 24 item
+constexpr int TUNE_KINDS = 2, TUNE_IB = 8;   // kind 0 Gram pass, 1 mode product; I_n in 32-buckets
+constexpr int DEFAULT_STEPS[TUNE_KINDS] = {16, 4};
+constexpr int MAX_UNITS = 32;                // bounds the partial sums of one item
 std::mutex g_tune_mu;
-double g_tune_work[TUNE_OPS][TUNE_IB][TUNE_SB];          // work per unit; 0 = default
-bool g_tune_init = false;
-
+int g_tune_steps[TUNE_KINDS][TUNE_IB];       // 0 = default
 int tune_ib(int I) { return std::min(TUNE_IB - 1, std::max(0, (I - 1) / 32)); }
-int tune_sb(int S) { return std::min(TUNE_SB - 1, std::max(0, (S - 1) / 8)); }
-// cost model of one tile: the two products (I x S8 each way) and the staging of I x 64 values
-double tile_cost(int I, int S) { return (double)I * (xp_s8(std::min(S, 64)) + 8); }
 
-double tuned_work(int op, int I, int S) {
+int tuned_steps(int kind, int I) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    const double w = g_tune_init ? g_tune_work[op][tune_ib(I)][tune_sb(S)] : 0.0;
-    return w > 0.0 ? w : DEFAULT_WORK;
+    const int v = g_tune_steps[kind][tune_ib(I)];
+    return v > 0 ? v : DEFAULT_STEPS[kind];
 }
 
-// tiles per unit of an item: about a fixed amount of work per unit (CTA), so that large and
-// small items of one wave finish their units together; depends only on the item's shape
-int wave_tpu(int op, int I, int S, int tiles) {
-    const double t = tuned_work(op, I, S) / tile_cost(I, S);
-    return (int)std::min<double>(std::max(1.0, std::floor(t)), std::max(1, tiles));
+// steps per unit of an item with `steps` steps: depends only on the item's shape
+int per_unit(int kind, int I, int steps) {
+    const int want = tuned_steps(kind, I);
+    return std::max(want, (int)cdiv(steps, MAX_UNITS));
 }
 
 }  // namespace
@@ -454,16 +565,14 @@ namespace {
 
 constexpr size_t WAVE_ALIGN = 256;
 
-int wave_units(int tiles, int tpu) { return (int)cdiv(tiles, std::max(1, tpu)); }
-
 struct WaveMode {
-    int n = 0;
     const ModePlan* m = nullptr;
+    double* G = nullptr;             // X_(n) X_(n)^T (I x I); the Gram path's Z
     double *Qall = nullptr, *Pall = nullptr, *Z = nullptr, *evec = nullptr, *eval = nullptr;
-    double *syev_ws = nullptr, *orth_ws = nullptr, *atb_part = nullptr;
+    double *syev_ws = nullptr, *orth_ws = nullptr, *atb_part = nullptr, *gemm_part = nullptr;
     int32_t* kept = nullptr;
-    float* xpart = nullptr;
-    int tiles = 0, tpu = 1, units = 1;
+    float *gpart = nullptr, *wpart = nullptr;
+    int ksteps = 0, kpu = 1, units = 1;
 };
 
 struct WaveReq {
@@ -475,8 +584,7 @@ struct WaveReq {
     int64_t tmax = 0;           // largest intermediate of the core chain (elements)
     double* sq_part = nullptr;
     double* norms = nullptr;    // out.norms or workspace
-    int rnd = 0;                // RBKI_BF16 / RBKI_F16: rounding of X as it is read
-    int ttm_tpu[RBKI_MAX_ORDER] = {0};
+    int rnd = 0;                // rounding of X as it is read (RBKI_BF16 / RBKI_F16, 0: none)
 };
 
 rbki_status wave_check(const rbki_tensor* X, const rbki_params* prm, Plan& pl) {
@@ -520,27 +628,28 @@ void wave_carve(WaveReq& q, Carve& cv) {
     for (int n = 0; n < pl.N; ++n) {
         const ModePlan& m = pl.mode[n];
         WaveMode& w = q.mode[n];
-        w.n = n;
         w.m = &m;
-        const int64_t J = m.A * m.C;
-        w.tiles = (int)cdiv(J, XT);
-        w.tpu = wave_tpu(m.gram ? 2 : 1, (int)m.I, m.gram ? (int)m.I : m.S, w.tiles);
-        w.units = wave_units(w.tiles, w.tpu);
-        const int b = m.b;
-        const int ev = m.gram ? (int)m.I : b;
+        const int I = (int)m.I;
+        w.ksteps = (int)cdiv(m.A * m.C, KT);
+        w.kpu = per_unit(0, I, w.ksteps);
+        w.units = (int)cdiv(w.ksteps, w.kpu);
+        w.gpart = cv.take<float>((size_t)w.units * I * I);
+        const int ev = m.gram ? I : m.b;
         w.Z = cv.take<double>((size_t)ev * ev);
         w.evec = cv.take<double>((size_t)ev * m.R);
         w.eval = cv.take<double>((size_t)ev);
         w.syev_ws = cv.take<double>(syev_scratch_doubles(ev));
         w.kept = cv.take<int32_t>(1);
         if (m.gram) {
-            w.xpart = cv.take<float>((size_t)w.units * m.I * m.I);
+            w.G = w.Z;
         } else {
-            w.Qall = cv.take<double>((size_t)m.I * b);
-            w.Pall = cv.take<double>((size_t)m.I * b);
-            w.orth_ws = cv.take<double>(orth_scratch_doubles(m.I, b - m.S, m.S));
-            w.atb_part = cv.take<double>((size_t)atb_nchunks(m.I) * b * b);
-            w.xpart = cv.take<float>((size_t)w.units * m.I * m.S);
+            w.G = cv.take<double>((size_t)I * I);
+            w.wpart = cv.take<float>((size_t)w.units * I * m.S);
+            w.Qall = cv.take<double>((size_t)I * m.b);
+            w.Pall = cv.take<double>((size_t)I * m.b);
+            w.orth_ws = cv.take<double>(orth_scratch_doubles(I, m.b - m.S, m.S));
+            w.atb_part = cv.take<double>((size_t)atb_nchunks(I) * m.b * m.b);
+            w.gemm_part = cv.take<double>(gemm_part_doubles(I, m.S, I));
         }
     }
     q.tbuf[0] = cv.take<float>((size_t)q.tmax);
@@ -549,92 +658,76 @@ void wave_carve(WaveReq& q, Carve& cv) {
     q.norms = cv.take<double>(2);
 }
 
-template <int MR>
-rbki_status launch_xpass_class(const std::vector<xpass_rec>& recs, cudaStream_t st) {
+rbki_status launch_ttm(const std::vector<ttm_rec>& recs, cudaStream_t st) {
     if (recs.empty()) return RBKI_OK;
     size_t sm = 0;
-    for (const auto& r : recs) sm = std::max(sm, xpass_smem(r));
-    static const size_t smax = max_dyn_smem(k_xpass_b<MR>);   // thread-safe, once per MR
-    if (sm > smax) return set_error(RBKI_E_UNSUPPORTED, "batched X pass: shared memory");
-    return bat_launch(k_xpass_b<MR>, recs.data(), (int)recs.size(), XTHREADS, sm, st, "k_xpass_b");
+    for (const auto& r : recs) sm = std::max(sm, ttm_smem(r));
+    static const size_t smax = max_dyn_smem(k_ttm_b);   // thread-safe, once
+    if (sm > smax) return set_error(RBKI_E_UNSUPPORTED, "batched mode product: shared memory");
+    return bat_launch(k_ttm_b, recs.data(), (int)recs.size(), NTHREADS, sm, st, "k_ttm_b");
 }
 
-// one launch per register class (a TTM runs no GEMM 2: the smallest class)
-rbki_status launch_xpass(const std::vector<xpass_rec>& recs, cudaStream_t st) {
-    std::vector<xpass_rec> c2, c4, c8;
-    for (const auto& r : recs) {
-        const int mr = r.op == XO_TTM ? 1 : xpass_mr(r);
-        (mr <= 2 ? c2 : mr <= 4 ? c4 : c8).push_back(r);
-    }
-    RBKI_TRY(launch_xpass_class<2>(c2, st));
-    RBKI_TRY(launch_xpass_class<4>(c4, st));
-    return launch_xpass_class<8>(c8, st);
-}
-
-xpass_rec xrec(const WaveReq& q, const WaveMode& w, int op) {
-    const ModePlan& m = *w.m;
-    xpass_rec r{};
-    r.x = q.X.data;
-    r.dtype = q.X.dtype;
-    r.rnd = q.X.dtype == q.pl.stream_dtype ? 0 : q.rnd;
-    r.A = (int)m.A;
-    r.I = (int)m.I;
-    r.C = (int)m.C;
-    r.op = op;
-    r.S = op == XO_GRAM ? (int)m.I : m.S;
-    r.tiles = w.tiles;
-    r.tpu = w.tpu;
-    r.part = w.xpart;
-    r.ldp = r.S;
-    r.seed = q.pl.seed;
-    r.mode = m.n;
-    r.gx = w.units;
-    r.gy = op == XO_GRAM ? (int)cdiv(m.I, 64) : 1;
-    r.gz = 1;
-    return r;
-}
-
-xreduce_rec rrec(const WaveMode& w, double* out1, int ld1, double* out2, int ld2) {
-    const ModePlan& m = *w.m;
-    const int S = m.gram ? (int)m.I : m.S;
-    return xreduce_rec{w.xpart, w.units, (int)m.I, S, S, m.gram ? 1 : 0, out1, ld1, out2, ld2,
-                       (int)cdiv((int64_t)m.I * S, 256), 1, 1};
-}
-
-// Algorithms 1-2 for every request of the wave, stage by stage.
+// Algorithms 1-2 for every request of the wave, stage by stage.  Per Krylov-path mode the
+// Krylov products are P_j = (X_(n) X_(n)^T) Q_j with X_(n) X_(n)^T formed once (I_n <= 256):
+// one pass over X instead of q + 1, and FP64 products on the small matrix.
 rbki_status run_wave(std::vector<WaveReq>& Q, cudaStream_t st) {
     const int nq = (int)Q.size();
     // ---- |X|^2 ----
     {
         std::vector<sumsq_rec> sq;
         for (auto& q : Q)
-            sq.push_back(sumsq_rec{q.X.data, q.X.dtype, q.pl.numel, q.sq_part, q.norms, (int)cdiv(q.pl.numel, SQ_CHUNK), 1, 1});
+            sq.push_back(sumsq_rec{q.X.data, q.X.dtype, q.pl.numel, q.sq_part, q.norms,
+                                   (int)cdiv(q.pl.numel, SQ_CHUNK), 1, 1});
         RBKI_TRY(bat_launch(k_sumsq_part_b, sq.data(), nq, 256, 0, st, "k_sumsq_part_b"));
         for (auto& r : sq) r.gx = 1;
         RBKI_TRY(bat_launch(k_sumsq_fin_b, sq.data(), nq, 32, 0, st, "k_sumsq_fin_b"));
     }
-    // ---- Algorithm 1 steps 1-2 (sketch) on Krylov modes; Z = X_(n) X_(n)^T on Gram modes ----
+    // ---- one pass per mode: X_(n) X_(n)^T, and W = X_(n) Omega (Algorithm 1 steps 1-2) on
+    // Krylov-path modes; the Gram path's Z is X_(n) X_(n)^T itself ----
     int qmax = 0;
     {
-        std::vector<xpass_rec> xp;
-        std::vector<xreduce_rec> xr;
+        std::vector<gram_rec> gr;
+        std::vector<greduce_rec> gd;
+        std::vector<xreduce_rec> wd;
         std::vector<fill_rec> fk;
         for (auto& q : Q)
             for (int n = 0; n < q.pl.N; ++n) {
                 WaveMode& w = q.mode[n];
-                if (w.m->gram) {
-                    xp.push_back(xrec(q, w, XO_GRAM));
-                    xr.push_back(rrec(w, w.Z, (int)w.m->I, nullptr, 0));
-                } else {
-                    xp.push_back(xrec(q, w, XO_SKETCH));
-                    xr.push_back(rrec(w, w.Qall, w.m->b, nullptr, 0));
-                    qmax = std::max(qmax, w.m->q);
+                const ModePlan& m = *w.m;
+                const int I = (int)m.I, nb = (int)cdiv(I, GB), npair = nb * (nb + 1) / 2;
+                gram_rec r{};
+                r.x = q.X.data;
+                r.dtype = q.X.dtype;
+                r.rnd = q.X.dtype == q.pl.stream_dtype ? 0 : q.rnd;
+                r.A = (int)m.A;
+                r.I = I;
+                r.C = (int)m.C;
+                r.nb = nb;
+                r.npair = npair;
+                r.ksteps = w.ksteps;
+                r.kpu = w.kpu;
+                r.S = m.gram ? 0 : m.S;
+                r.seed = q.pl.seed;
+                r.mode = n;
+                r.gpart = w.gpart;
+                r.wpart = w.wpart;
+                r.gx = npair * w.units;
+                r.gy = r.gz = 1;
+                gr.push_back(r);
+                gd.push_back(greduce_rec{w.gpart, w.units, I, w.G, (int)cdiv((int64_t)I * I, 256), 1, 1});
+                if (!m.gram) {
+                    wd.push_back(xreduce_rec{w.wpart, w.units, I, m.S, m.S, w.Qall, m.b, nullptr, 0,
+                                             (int)cdiv((int64_t)I * m.S, 256), 1, 1});
                     fk.push_back(fill_rec{w.kept, 0, 1, 1, 1});
+                    qmax = std::max(qmax, m.q);
                 }
             }
+        static const size_t gmax = max_dyn_smem(k_gram_b);
+        if (GRAM_SMEM > gmax) return set_error(RBKI_E_CUDA, "batched Gram pass: shared memory");
         RBKI_TRY(bat_launch(k_fill_b, fk.data(), (int)fk.size(), 32, 0, st, "k_fill_b"));
-        RBKI_TRY(launch_xpass(xp, st));
-        RBKI_TRY(bat_launch(k_xreduce_b, xr.data(), (int)xr.size(), 256, 0, st, "k_xreduce_b"));
+        RBKI_TRY(bat_launch(k_gram_b, gr.data(), (int)gr.size(), NTHREADS, GRAM_SMEM, st, "k_gram_b"));
+        RBKI_TRY(bat_launch(k_greduce_b, gd.data(), (int)gd.size(), 256, 0, st, "k_greduce_b"));
+        RBKI_TRY(bat_launch(k_xreduce_b, wd.data(), (int)wd.size(), 256, 0, st, "k_xreduce_b"));
     }
     // BCGS2 on block col0 of every listed item (two passes; the second counts kept columns)
     auto orth2 = [&](const std::vector<WaveMode*>& ws, const std::vector<int>& col0) -> rbki_status {
@@ -658,10 +751,10 @@ rbki_status run_wave(std::vector<WaveReq>& Q, cudaStream_t st) {
                 }
         RBKI_TRY(orth2(ws, c0));
     }
-    // ---- step 3: K = [W, A W, ..., A^q W], block by block ----
+    // ---- step 3: K = [W, A W, ..., A^q W], block by block: P_j = (X X^T) Q_j (FP64) ----
     for (int j = 0; j <= qmax; ++j) {
-        std::vector<xpass_rec> xp;
-        std::vector<xreduce_rec> xr;
+        std::vector<GemmItem> gm;
+        std::vector<blkcopy_rec> cp;
         std::vector<WaveMode*> ws;
         std::vector<int> c0;
         for (auto& q : Q)
@@ -669,19 +762,18 @@ rbki_status run_wave(std::vector<WaveReq>& Q, cudaStream_t st) {
                 WaveMode& w = q.mode[n];
                 const ModePlan& m = *w.m;
                 if (m.gram || j > m.q) continue;
-                xpass_rec r = xrec(q, w, XO_KRYLOV);
-                r.Q = w.Qall + j * m.S;
-                r.ldq = m.b;
-                xp.push_back(r);
-                const bool more = j < m.q;
-                xr.push_back(rrec(w, w.Pall + j * m.S, m.b, more ? w.Qall + (j + 1) * m.S : nullptr, m.b));
-                if (more) {
+                const int I = (int)m.I;
+                gm.push_back(GemmItem{false, I, m.S, I, w.G, I, w.Qall + j * m.S, m.b, w.Pall + j * m.S, m.b, 0.0,
+                                      w.gemm_part});
+                if (j < m.q) {
+                    cp.push_back(blkcopy_rec{w.Pall + j * m.S, m.b, w.Qall + (j + 1) * m.S, m.b, I, m.S,
+                                             (int)cdiv((int64_t)I * m.S, 256), 1, 1});
                     ws.push_back(&w);
                     c0.push_back((j + 1) * m.S);
                 }
             }
-        RBKI_TRY(launch_xpass(xp, st));
-        RBKI_TRY(bat_launch(k_xreduce_b, xr.data(), (int)xr.size(), 256, 0, st, "k_xreduce_b"));
+        RBKI_TRY(gemm_f64_batched(gm.data(), (int)gm.size(), st));
+        RBKI_TRY(bat_launch(k_blkcopy_b, cp.data(), (int)cp.size(), 256, 0, st, "k_blkcopy_b"));
         if (!ws.empty()) RBKI_TRY(orth2(ws, c0));
     }
     // ---- Remark 1: Z = Q^T [P_0 .. P_q]; steps 4-5: eigenvectors, U = Q U~(:, 1:R) ----
@@ -718,7 +810,7 @@ rbki_status run_wave(std::vector<WaveReq>& Q, cudaStream_t st) {
     for (int k = 0; k < nq; ++k)
         for (int n = 0; n < Q[k].pl.N; ++n) cur[k * RBKI_MAX_ORDER + n] = Q[k].pl.dims[n];
     for (int t = 0; t < Nmax; ++t) {
-        std::vector<xpass_rec> xp;
+        std::vector<ttm_rec> tr;
         for (int k = 0; k < nq; ++k) {
             WaveReq& q = Q[k];
             const Plan& pl = q.pl;
@@ -726,31 +818,30 @@ rbki_status run_wave(std::vector<WaveReq>& Q, cudaStream_t st) {
             int64_t* c = &cur[k * RBKI_MAX_ORDER];
             const int md = pl.order[t];
             const ModePlan& m = pl.mode[md];
-            int64_t A = 1, C = 1;
+            int64_t A = 1, Cc = 1;
             for (int i = 0; i < md; ++i) A *= c[i];
-            for (int i = md + 1; i < pl.N; ++i) C *= c[i];
-            xpass_rec r{};
+            for (int i = md + 1; i < pl.N; ++i) Cc *= c[i];
+            ttm_rec r{};
             r.x = t == 0 ? q.X.data : q.tbuf[(t - 1) & 1];
             r.dtype = t == 0 ? q.X.dtype : RBKI_F32;
             r.rnd = t == 0 && q.X.dtype != pl.stream_dtype ? q.rnd : 0;
             r.A = (int)A;
             r.I = (int)c[md];
-            r.C = (int)C;
-            r.op = XO_TTM;
+            r.C = (int)Cc;
             r.S = m.R;
-            r.tiles = (int)cdiv(A * C, XT);
-            r.tpu = wave_tpu(3, r.I, m.R, r.tiles);
-            r.Q = q.out.factors[md];
-            r.ldq = m.R;
+            r.tiles = (int)cdiv(A * Cc, TT);
+            r.tpu = per_unit(1, r.I, r.tiles);
+            r.U = q.out.factors[md];
+            r.ldu = m.R;
             const bool last = t == pl.N - 1;
-            r.tout = last ? (void*)q.out.core : (void*)q.tbuf[t & 1];
-            r.tdt = last ? RBKI_F64 : RBKI_F32;
-            r.gx = wave_units(r.tiles, r.tpu);
+            r.out = last ? (void*)q.out.core : (void*)q.tbuf[t & 1];
+            r.odt = last ? RBKI_F64 : RBKI_F32;
+            r.gx = (int)cdiv(r.tiles, r.tpu);
             r.gy = r.gz = 1;
-            xp.push_back(r);
+            tr.push_back(r);
             c[md] = m.R;
         }
-        RBKI_TRY(launch_xpass(xp, st));
+        RBKI_TRY(launch_ttm(tr, st));
     }
     // ---- |G|^2, info, q_used ----
     {
