@@ -44,6 +44,9 @@ def parse_args():
     ap.add_argument("--wave-threads", type=int, default=4,
                     help="server workers of the batched path (0: every request on a slot)")
     ap.add_argument("--wave-max", type=int, default=32, help="requests per wave of the batched path")
+    ap.add_argument("--tune-cache", default=None,
+                    help="work-granularity table of the batched path: loaded if the file exists, else "
+                         "measured (rbki_wave_autotune) and written there; default: measured, not kept")
     ap.add_argument("--fp64-requests", type=int, default=256,
                     help="prefix of the served stream also run on the FP64 GPU path (--workload serve)")
     ap.add_argument("--prec", choices=["bf16", "fp64"], default="bf16")
@@ -526,8 +529,9 @@ def run_ours(args):
     serve_cmp = None
     if rank == 0 and world == 1 and not args.no_serve_compare and args.workload == "tucker512" and not args.size:
         # the served-stream half of the metric, bounded: 1024 requests of the stream
-        res, _ = serve_measure(1024, args.slots, 128, (0.8,), 1, args.wave_threads, args.wave_max)
-        serve_cmp = {k: res[k] for k in ("requests", "slots", "wave_threads", "wave_max", "solves_per_s",
+        res, _ = serve_measure(1024, args.slots, 128, (0.8,), 1, args.wave_threads, args.wave_max, args.tune_cache)
+        serve_cmp = {k: res[k] for k in ("requests", "slots", "wave_threads", "wave_max", "tuning", "solves_per_s",
+                                          "graph_replay",
                                           "launches_per_request",
                                           "x_pass_gbs", "latency", "fp64_compare", "rel_err_mixed")}
         serve_cmp["unit"] = "solves/s"
@@ -791,7 +795,20 @@ def run_divide(args):
         }))
 
 
-def serve_measure(n_requests, slots, fp64_prefix, rhos, warmup=1, wave_threads=4, wave_max=32):
+def wave_tuning(rb, cache):
+    """Autotuned work granularity of the batched path (from `cache` when it exists)."""
+    if cache and os.path.exists(cache):
+        rb.rbki_wave_tune_load(cache)
+        return {"source": "file", "table": rb.rbki_wave_tune_table()}
+    t0 = time.perf_counter()
+    rb.rbki_wave_autotune()
+    secs = time.perf_counter() - t0
+    if cache:
+        rb.rbki_wave_tune_save(cache)
+    return {"source": "measured", "seconds": round(secs, 3), "table": rb.rbki_wave_tune_table()}
+
+
+def serve_measure(n_requests, slots, fp64_prefix, rhos, warmup=1, wave_threads=4, wave_max=32, tune_cache=None):
     """The served stream (Sec. 4 workloads as a request stream): n_requests rBKI-TK requests
     (3rd order, dims in [32, 256], ranks in [4, 32], q in {1, 2, 3}, p = 5, SNR in [5, 25] dB,
     BF16 products) through the server.  Closed-loop solves/s (every request submitted at
@@ -815,7 +832,7 @@ def serve_measure(n_requests, slots, fp64_prefix, rhos, warmup=1, wave_threads=4
             x32.append(x.float())
     torch.cuda.synchronize()
     budget = 8 << 30
-    res = {}
+    res = {"tuning": wave_tuning(rb, tune_cache) if wave_threads else None}
     with rb.RbkiServer(0, mem_budget=budget, max_slots=slots, wave_threads=wave_threads, wave_max=wave_max) as srv:
         nw = min(len(items), max(warmup, 1) * max(slots, wave_max if wave_threads else 0))
         _serve_closed_loop(rb, srv, items[:nw], outs[:nw], "bf16")
@@ -841,6 +858,30 @@ def serve_measure(n_requests, slots, fp64_prefix, rhos, warmup=1, wave_threads=4
                                              "achieved_per_s": round(len(items) / t, 1),
                                              "p50_ms": round(1e3 * float(np.percentile(l, 50)), 3),
                                              "p99_ms": round(1e3 * float(np.percentile(l, 99)), 3)}
+        # the graph pattern: a fixed batch (the stream's first wave_max requests, in their own
+        # buffers) captured once and replayed per batch
+        replay = None
+        if wave_threads:
+            nb = min(len(items), wave_max)
+            plan = rb.BatchedPlan([it[0] for it in items[:nb]], [it[1] for it in items[:nb]], items[0][2],
+                                  [it[3] for it in items[:nb]], [it[4] for it in items[:nb]])
+            for _ in range(3):
+                plan.launch()
+            torch.cuda.synchronize()
+            reps = 20
+            l0 = rb.rbki_kernel_launches()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                plan.launch()
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            replay = {"requests_per_batch": nb, "batches": reps, "ms_per_batch": round(ms, 3),
+                      "solves_per_s": round(nb / (ms * 1e-3), 1),
+                      "kernels_per_batch": int((rb.rbki_kernel_launches() - l0) / reps), "graph_launches_per_batch": 1}
+            plan.close()
+        res["graph_replay"] = replay
         f64 = None
         if x32:
             its = [(x32[i],) + items[i][1:] for i in range(len(x32))]
@@ -882,7 +923,7 @@ def run_serve(args):
         raise SystemExit("--workload serve runs on one GPU")
     torch.cuda.set_device(0)
     res, reqs = serve_measure(args.requests, args.slots, args.fp64_requests, (0.5, 0.8, 0.95), args.warmup,
-                              args.wave_threads, args.wave_max)
+                              args.wave_threads, args.wave_max, args.tune_cache)
     cpu = None
     if not args.no_cpu_baseline:
         cpu = serve_cpu_baseline(reqs)
@@ -898,7 +939,8 @@ def run_serve(args):
                    "x_pass_gbs": res["x_pass_gbs"],
                    "l2": "requests are mostly smaller than L2; throughput is latency-bound"},
         "latency": res["latency"], "fp64_compare": res["fp64_compare"], "rel_err_mixed": res["rel_err_mixed"],
-        "launches_per_request": res["launches_per_request"],
+        "launches_per_request": res["launches_per_request"], "tuning": res["tuning"],
+        "graph_replay": res["graph_replay"],
         "e2e": None, "gpu_launches": res["gpu_launches"], "clocks": res["clocks"], "cpu_baseline": cpu,
     }
     print(json.dumps(line))

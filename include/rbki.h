@@ -204,6 +204,32 @@ rbki_status rbki_tucker_batched_workspace(int32_t count, const rbki_tensor* X, c
 rbki_status rbki_tucker_batched(int32_t count, const rbki_tensor* X, const rbki_params* prm,
                                 void* workspace, size_t workspace_bytes, const rbki_tucker_out* out,
                                 void* stream);
+/* A wave captured once as a CUDA graph and replayed: for repeated batches of the same shapes
+ * in the same buffers (fixed-shape request slots, frames of a stream).  _create validates
+ * like rbki_tucker_batched, runs the wave once on `stream` (valid outputs), then captures its
+ * launches on a private stream; X, prm, workspace and out are bound into the plan (their
+ * pointers and shapes), so the caller refills X in place and calls _launch: one graph launch
+ * per batch, bitwise the results of rbki_tucker_batched on the same data.  rbki_kernel_launches
+ * counts a replay's kernel nodes. */
+typedef struct rbki_batched_plan rbki_batched_plan;
+rbki_status rbki_batched_plan_create(int32_t count, const rbki_tensor* X, const rbki_params* prm,
+                                     void* workspace, size_t workspace_bytes, const rbki_tucker_out* out,
+                                     void* stream, rbki_batched_plan** plan);
+rbki_status rbki_batched_plan_launch(rbki_batched_plan* plan, void* stream);
+rbki_status rbki_batched_plan_destroy(rbki_batched_plan* plan);
+/* Work-granularity table of rbki_tucker_batched: steps of its two work-queue kernels per CTA
+ * (kind 0: the Gram pass, 32-column steps; kind 1: the core's mode products, 64-column
+ * tiles) for each I_n bucket b (I_n in (32b, 32(b+1)], b = 0..7).  The summation order of an
+ * item depends on these values, so results are reproducible bit for bit under one table.
+ * rbki_wave_autotune times the candidates {2, 4, 8, 16, 32, 64} on a synthetic batch
+ * (48 items of 128 x I x 128 BF16) on `stream` and keeps the fastest (about a second; needs
+ * ~500 MB of device memory for its own buffers); _save / _load write and read the table
+ * as text ("<gram|ttm> <b> <steps>" lines), _reset restores the defaults. */
+rbki_status rbki_wave_autotune(void* stream);
+rbki_status rbki_wave_tune_get(int32_t kind, int32_t bucket, int32_t* steps);
+rbki_status rbki_wave_tune_reset(void);
+rbki_status rbki_wave_tune_save(const char* path);
+rbki_status rbki_wave_tune_load(const char* path);
 /* Divide-and-conquer split: dst[k] (device, dense C-order, dims of X with I_mode replaced by
  * hi_k - lo_k) = X restricted to mode indices [lo_k, hi_k), lo_k = floor(k I_mode / parts),
  * hi_k = floor((k+1) I_mode / parts); 1 <= parts <= I_mode.  Same dtype as X. */

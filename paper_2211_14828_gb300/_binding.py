@@ -84,6 +84,14 @@ def lib():
             "rbki_tucker_batch_workspace": (st, [C.c_int32, vp, vp, sz]),
             "rbki_tucker_batch": (st, [C.c_int32, vp, vp, vp, C.c_size_t, vp, vp]),
             "rbki_tucker_batched_workspace": (st, [C.c_int32, vp, vp, sz]),
+            "rbki_wave_autotune": (st, [vp]),
+            "rbki_batched_plan_create": (st, [C.c_int32, vp, vp, vp, C.c_size_t, vp, vp, C.POINTER(vp)]),
+            "rbki_batched_plan_launch": (st, [vp, vp]),
+            "rbki_batched_plan_destroy": (st, [vp]),
+            "rbki_wave_tune_get": (st, [C.c_int32, C.c_int32, C.POINTER(C.c_int32)]),
+            "rbki_wave_tune_reset": (st, []),
+            "rbki_wave_tune_save": (st, [C.c_char_p]),
+            "rbki_wave_tune_load": (st, [C.c_char_p]),
             "rbki_tucker_batched": (st, [C.c_int32, vp, vp, vp, C.c_size_t, vp, vp]),
             "rbki_split_mode": (st, [vp, C.c_int32, C.c_int32, vp, vp]),
             "rbki_status_str": (C.c_char_p, [C.c_int32]),
@@ -253,6 +261,75 @@ def rbki_tucker_batch(xs, ranks, p, q, seeds, prec="bf16", flags=0, omega=0.0, q
                                   os_, stream_ptr(stream)), "rbki_tucker_batch")
     outs[0]["workspace"] = workspace
     return outs
+
+
+class BatchedPlan:
+    """A wave captured as a CUDA graph (rbki_batched_plan_*): refill the inputs in place and
+    call launch(); the outputs land in `outs`.  Holds references to the inputs, outputs and
+    workspace it is bound to."""
+
+    def __init__(self, xs, ranks, p, qs, seeds, prec="bf16", flags=0, stream=None):
+        torch = _torch()
+        n = len(xs)
+        qv = [int(qs)] * n if isinstance(qs, int) else [int(v) for v in qs]
+        self.xs = xs
+        ts = (rbki_tensor * n)(*[make_tensor(x) for x in xs])
+        ps = (rbki_params * n)(*[make_params(ranks[k], p, qv[k], seeds[k], prec, flags) for k in range(n)])
+        need = C.c_size_t(0)
+        check(lib().rbki_tucker_batched_workspace(n, ts, ps, C.byref(need)), "rbki_tucker_batched_workspace")
+        self.workspace = torch.empty(max(int(need.value), 1), dtype=torch.uint8, device=xs[0].device)
+        self.outs = [alloc_outputs(x.shape, ranks[k], x.device) for k, x in enumerate(xs)]
+        os_ = (rbki_tucker_out * n)(*[make_out(o) for o in self.outs])
+        h = C.c_void_p()
+        check(lib().rbki_batched_plan_create(n, ts, ps, C.c_void_p(self.workspace.data_ptr()),
+                                             C.c_size_t(self.workspace.numel()), os_, stream_ptr(stream),
+                                             C.byref(h)), "rbki_batched_plan_create")
+        self._h = h
+
+    def launch(self, stream=None):
+        check(lib().rbki_batched_plan_launch(self._h, stream_ptr(stream)), "rbki_batched_plan_launch")
+        return self.outs
+
+    def close(self):
+        if self._h:
+            lib().rbki_batched_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rbki_wave_autotune(stream=None):
+    """Measures the batched path's work granularity on the device and keeps the fastest."""
+    check(lib().rbki_wave_autotune(stream_ptr(stream)), "rbki_wave_autotune")
+
+
+def rbki_wave_tune_table():
+    """The current table: {"gram": [steps per bucket], "ttm": [...]} (buckets of 32 rows)."""
+    out = {}
+    for kind, name in enumerate(("gram", "ttm")):
+        row = []
+        for b in range(8):
+            v = C.c_int32(0)
+            check(lib().rbki_wave_tune_get(kind, b, C.byref(v)), "rbki_wave_tune_get")
+            row.append(int(v.value))
+        out[name] = row
+    return out
+
+
+def rbki_wave_tune_save(path):
+    check(lib().rbki_wave_tune_save(str(path).encode()), "rbki_wave_tune_save")
+
+
+def rbki_wave_tune_load(path):
+    check(lib().rbki_wave_tune_load(str(path).encode()), "rbki_wave_tune_load")
+
+
+def rbki_wave_tune_reset():
+    check(lib().rbki_wave_tune_reset(), "rbki_wave_tune_reset")
 
 
 def rbki_tucker_batched_workspace(xs, ranks, p, qs, seeds, prec="bf16", flags=0) -> int:

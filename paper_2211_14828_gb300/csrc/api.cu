@@ -22,6 +22,8 @@ static std::atomic<uint64_t> g_launches{0};
 static thread_local std::string g_err;
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void add_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+void drop_launches(uint64_t n) { g_launches.fetch_sub(n, std::memory_order_relaxed); }
 
 rbki_status set_cuda_error(cudaError_t e, const char* where) {
     g_err = std::string(where) + ": " + cudaGetErrorString(e);

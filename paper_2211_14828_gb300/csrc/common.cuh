@@ -14,6 +14,8 @@ namespace rbki {
 
 // launch accounting (rbki_kernel_launches) and error capture
 void note_launch();
+void add_launches(uint64_t n);    // kernels launched through a CUDA graph replay
+void drop_launches(uint64_t n);   // kernels recorded by a stream capture (not launched)
 rbki_status set_cuda_error(cudaError_t e, const char* where);
 rbki_status set_error(rbki_status s, const char* msg);
 

@@ -24,6 +24,7 @@
 #include "plan.h"
 
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <mutex>
 
@@ -541,6 +542,7 @@ constexpr int MAX_UNITS = 32;                // bounds the partial sums of one i
 std::mutex g_tune_mu;
 int g_tune_steps[TUNE_KINDS][TUNE_IB];       // 0 = default
 int tune_ib(int I) { return std::min(TUNE_IB - 1, std::max(0, (I - 1) / 32)); }
+const char* const TUNE_NAMES[TUNE_KINDS] = {"gram", "ttm"};
 
 int tuned_steps(int kind, int I) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -897,6 +899,122 @@ rbki_status wave_prepare(int32_t count, const rbki_tensor* X, const rbki_params*
     return RBKI_OK;
 }
 
+// ---- autotuner: the steps per unit of each kernel and I_n bucket, measured on the device ----
+// A synthetic batch of 48 items (3rd-order BF16 tensors 128 x I x 128, mode 1: 16384 columns)
+// runs each candidate after a warm-up launch; its time is the fastest of three timed runs of
+// two launches (CUDA events on `st`); the fastest candidate wins.
+rbki_status autotune(cudaStream_t st, int* table) {
+    const int cand[] = {2, 4, 8, 16, 32, 64};
+    const int items = 48, A = 128, Cc = 128, Imax = 256, S = 32;
+    const int64_t numel = (int64_t)A * Imax * Cc;
+    void* x = nullptr;
+    double* U = nullptr;
+    float *part = nullptr, *tout = nullptr;
+    const int ksteps = (int)cdiv((int64_t)A * Cc, KT), tiles = (int)cdiv((int64_t)A * Cc, TT);
+    const size_t part_n = (size_t)MAX_UNITS * Imax * (Imax + S);   // one item's partials (units <= MAX_UNITS)
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    rbki_status rs = RBKI_OK;
+    auto fail = [&](cudaError_t e, const char* w) { rs = set_cuda_error(e, w); };
+    cudaError_t e;
+    if ((e = cudaMalloc(&x, numel * 2)) != cudaSuccess) fail(e, "autotune: tensor");
+    if (rs == RBKI_OK && (e = cudaMalloc(&U, (size_t)Imax * S * sizeof(double))) != cudaSuccess) fail(e, "autotune: U");
+    if (rs == RBKI_OK && (e = cudaMalloc(&part, items * part_n * sizeof(float))) != cudaSuccess)
+        fail(e, "autotune: partials");
+    if (rs == RBKI_OK && (e = cudaMalloc(&tout, (size_t)items * A * S * Cc * sizeof(float))) != cudaSuccess)
+        fail(e, "autotune: output");
+    if (rs == RBKI_OK && (e = cudaMemsetAsync(x, 0x3f, numel * 2, st)) != cudaSuccess) fail(e, "autotune: fill");
+    if (rs == RBKI_OK && (e = cudaMemsetAsync(U, 0, (size_t)Imax * S * sizeof(double), st)) != cudaSuccess)
+        fail(e, "autotune: fill");
+    if (rs == RBKI_OK && (e = cudaEventCreate(&e0)) != cudaSuccess) fail(e, "autotune: event");
+    if (rs == RBKI_OK && (e = cudaEventCreate(&e1)) != cudaSuccess) fail(e, "autotune: event");
+    static const size_t gmax = max_dyn_smem(k_gram_b);
+    static const size_t tmax = max_dyn_smem(k_ttm_b);
+    for (int kind = 0; kind < TUNE_KINDS && rs == RBKI_OK; ++kind) {
+        for (int b = 0; b < TUNE_IB && rs == RBKI_OK; ++b) {
+            const int I = 32 * (b + 1), nb = (int)cdiv(I, GB);
+            float best = 1e30f;
+            int arg = DEFAULT_STEPS[kind];
+            for (int c : cand) {
+                const int steps = kind == 0 ? ksteps : tiles;
+                const int kpu = std::max(c, (int)cdiv(steps, MAX_UNITS)), units = (int)cdiv(steps, kpu);
+                std::vector<gram_rec> gr;
+                std::vector<ttm_rec> tr;
+                for (int k = 0; k < items; ++k) {
+                    if (kind == 0) {
+                        gram_rec r{};
+                        r.x = x;
+                        r.dtype = RBKI_BF16;
+                        r.A = A;
+                        r.I = I;
+                        r.C = Cc;
+                        r.nb = nb;
+                        r.npair = nb * (nb + 1) / 2;
+                        r.ksteps = ksteps;
+                        r.kpu = kpu;
+                        r.S = S;
+                        r.gpart = part + (size_t)k * part_n;
+                        r.wpart = part + (size_t)k * part_n + (size_t)units * I * I;
+                        r.gx = r.npair * units;
+                        r.gy = r.gz = 1;
+                        gr.push_back(r);
+                    } else {
+                        ttm_rec r{};
+                        r.x = x;
+                        r.dtype = RBKI_BF16;
+                        r.A = A;
+                        r.I = I;
+                        r.C = Cc;
+                        r.S = S;
+                        r.tiles = tiles;
+                        r.tpu = kpu;
+                        r.U = U;
+                        r.ldu = S;
+                        r.out = tout + (size_t)k * A * S * Cc;
+                        r.odt = RBKI_F32;
+                        r.gx = units;
+                        r.gy = r.gz = 1;
+                        tr.push_back(r);
+                    }
+                }
+                // a warm-up launch, then the fastest of 3 timed runs of 2 launches
+                auto launch = [&]() -> rbki_status {
+                    if (kind == 0) {
+                        if (GRAM_SMEM > gmax) return set_error(RBKI_E_CUDA, "autotune: Gram shared memory");
+                        return bat_launch(k_gram_b, gr.data(), items, NTHREADS, GRAM_SMEM, st, "k_gram_b");
+                    }
+                    const size_t sm = ttm_smem(tr[0]);
+                    if (sm > tmax) return set_error(RBKI_E_CUDA, "autotune: mode-product shared memory");
+                    return bat_launch(k_ttm_b, tr.data(), items, NTHREADS, sm, st, "k_ttm_b");
+                };
+                float ms = 1e30f;
+                rs = launch();
+                for (int run = 0; run < 3 && rs == RBKI_OK; ++run) {
+                    if ((e = cudaEventRecord(e0, st)) != cudaSuccess) fail(e, "autotune: record");
+                    for (int l = 0; l < 2 && rs == RBKI_OK; ++l) rs = launch();
+                    if (rs == RBKI_OK && (e = cudaEventRecord(e1, st)) != cudaSuccess) fail(e, "autotune: record");
+                    if (rs == RBKI_OK && (e = cudaEventSynchronize(e1)) != cudaSuccess) fail(e, "autotune: sync");
+                    float t = 0.f;
+                    if (rs == RBKI_OK && (e = cudaEventElapsedTime(&t, e0, e1)) != cudaSuccess) fail(e, "autotune: time");
+                    ms = std::min(ms, t);
+                }
+                if (rs == RBKI_OK && ms < best) {
+                    best = ms;
+                    arg = c;
+                }
+            }
+            table[kind * TUNE_IB + b] = arg;
+        }
+    }
+    cudaStreamSynchronize(st);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(x);
+    cudaFree(U);
+    cudaFree(part);
+    cudaFree(tout);
+    return rs;
+}
+
 }  // namespace
 }  // namespace rbki
 
@@ -904,11 +1022,154 @@ using namespace rbki;
 
 extern "C" {
 
+rbki_status rbki_wave_autotune(void* stream) {
+    int table[TUNE_KINDS * TUNE_IB];
+    RBKI_TRY(autotune(static_cast<cudaStream_t>(stream), table));
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (int k = 0; k < TUNE_KINDS; ++k)
+        for (int b = 0; b < TUNE_IB; ++b) g_tune_steps[k][b] = table[k * TUNE_IB + b];
+    return RBKI_OK;
+}
+
+rbki_status rbki_wave_tune_get(int32_t kind, int32_t bucket, int32_t* steps) {
+    if (kind < 0 || kind >= TUNE_KINDS || bucket < 0 || bucket >= TUNE_IB || !steps)
+        return set_error(RBKI_E_INVAL, "kind / bucket out of range or steps is NULL");
+    *steps = tuned_steps(kind, 32 * (bucket + 1));
+    return RBKI_OK;
+}
+
+rbki_status rbki_wave_tune_reset(void) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (auto& row : g_tune_steps)
+        for (int& v : row) v = 0;
+    return RBKI_OK;
+}
+
+rbki_status rbki_wave_tune_save(const char* path) {
+    if (!path) return set_error(RBKI_E_INVAL, "path is NULL");
+    FILE* f = std::fopen(path, "w");
+    if (!f) return set_error(RBKI_E_INVAL, "cannot open the tuning file for writing");
+    std::fprintf(f, "# rbki wave tuning table v1: kind I_n-bucket(32*(b+1)) steps-per-unit\n");
+    for (int k = 0; k < TUNE_KINDS; ++k)
+        for (int b = 0; b < TUNE_IB; ++b) std::fprintf(f, "%s %d %d\n", TUNE_NAMES[k], b, tuned_steps(k, 32 * (b + 1)));
+    const bool ok = std::fclose(f) == 0;
+    return ok ? RBKI_OK : set_error(RBKI_E_INVAL, "writing the tuning file failed");
+}
+
+rbki_status rbki_wave_tune_load(const char* path) {
+    if (!path) return set_error(RBKI_E_INVAL, "path is NULL");
+    FILE* f = std::fopen(path, "r");
+    if (!f) return set_error(RBKI_E_NOTFOUND, "cannot open the tuning file");
+    int table[TUNE_KINDS][TUNE_IB] = {};
+    char line[256];
+    rbki_status rs = RBKI_OK;
+    while (std::fgets(line, sizeof line, f)) {
+        if (line[0] == '#' || line[0] == '\n') continue;
+        char name[16];
+        int b = -1, v = 0;
+        if (std::sscanf(line, "%15s %d %d", name, &b, &v) != 3 || b < 0 || b >= TUNE_IB || v < 1 || v > 4096) {
+            rs = set_error(RBKI_E_INVAL, "malformed line in the tuning file");
+            break;
+        }
+        int k = -1;
+        for (int i = 0; i < TUNE_KINDS; ++i)
+            if (std::strcmp(name, TUNE_NAMES[i]) == 0) k = i;
+        if (k < 0) {
+            rs = set_error(RBKI_E_INVAL, "unknown kernel kind in the tuning file");
+            break;
+        }
+        table[k][b] = v;
+    }
+    std::fclose(f);
+    if (rs < 0) return rs;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (int k = 0; k < TUNE_KINDS; ++k)
+        for (int b = 0; b < TUNE_IB; ++b) g_tune_steps[k][b] = table[k][b];
+    return RBKI_OK;
+}
+
 rbki_status rbki_tucker_batched_workspace(int32_t count, const rbki_tensor* X, const rbki_params* prm,
                                           size_t* bytes) {
     if (!bytes) return set_error(RBKI_E_INVAL, "bytes is NULL");
     std::vector<WaveReq> Q;
     return wave_prepare(count, X, prm, nullptr, nullptr, Q, bytes);
+}
+
+// ---- captured waves: the whole schedule of one wave as a CUDA graph, replayed per batch ----
+struct rbki_batched_plan {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t kernels = 0;   // kernel nodes per replay
+};
+
+rbki_status rbki_batched_plan_create(int32_t count, const rbki_tensor* X, const rbki_params* prm, void* workspace,
+                                     size_t workspace_bytes, const rbki_tucker_out* out, void* stream,
+                                     rbki_batched_plan** plan) {
+    if (!plan) return set_error(RBKI_E_INVAL, "plan is NULL");
+    *plan = nullptr;
+    if (count < 1) return set_error(RBKI_E_INVAL, "count must be >= 1");
+    if (!out) return set_error(RBKI_E_INVAL, "out is NULL");
+    size_t need = 0;
+    std::vector<WaveReq> Q;
+    RBKI_TRY(wave_prepare(count, X, prm, out, nullptr, Q, &need));
+    if (!workspace || workspace_bytes < need) return set_error(RBKI_E_NOMEM, "workspace too small");
+    RBKI_TRY(wave_prepare(count, X, prm, out, workspace, Q, &need));
+    for (const auto& q : Q)
+        if (!q.X.data) return set_error(RBKI_E_INVAL, "X->data is NULL");
+    cudaStream_t user = static_cast<cudaStream_t>(stream);
+    // one eager run sets up every kernel's shared-memory opt-in before the capture (and
+    // leaves valid outputs); the capture runs on a private stream ordered after `stream`
+    RBKI_TRY(run_wave(Q, user));
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev = nullptr;
+    RBKI_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    auto cleanup = [&] {
+        if (ev) cudaEventDestroy(ev);
+        cudaStreamDestroy(cs);
+    };
+    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ev, user);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev, 0);
+    if (e != cudaSuccess) {
+        cleanup();
+        return set_cuda_error(e, "batched plan: ordering");
+    }
+    rbki_batched_plan* p = new rbki_batched_plan();
+    const uint64_t l0 = rbki_kernel_launches();
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    rbki_status rs = e == cudaSuccess ? run_wave(Q, cs) : set_cuda_error(e, "batched plan: begin capture");
+    if (e == cudaSuccess) {
+        const cudaError_t e2 = cudaStreamEndCapture(cs, &p->graph);
+        if (rs >= 0 && e2 != cudaSuccess) rs = set_cuda_error(e2, "batched plan: end capture");
+    }
+    p->kernels = rbki_kernel_launches() - l0;
+    drop_launches(p->kernels);   // recorded into the graph, not launched
+    if (rs >= 0) {
+        e = cudaGraphInstantiate(&p->exec, p->graph, 0);
+        if (e != cudaSuccess) rs = set_cuda_error(e, "batched plan: instantiate");
+    }
+    cleanup();
+    if (rs < 0) {
+        rbki_batched_plan_destroy(p);
+        return rs;
+    }
+    *plan = p;
+    return RBKI_OK;
+}
+
+rbki_status rbki_batched_plan_launch(rbki_batched_plan* plan, void* stream) {
+    if (!plan || !plan->exec) return set_error(RBKI_E_INVAL, "plan is NULL");
+    RBKI_CUDA_TRY(cudaGraphLaunch(plan->exec, static_cast<cudaStream_t>(stream)));
+    add_launches(plan->kernels);
+    return RBKI_OK;
+}
+
+rbki_status rbki_batched_plan_destroy(rbki_batched_plan* plan) {
+    if (!plan) return set_error(RBKI_E_INVAL, "plan is NULL");
+    if (plan->exec) cudaGraphExecDestroy(plan->exec);
+    if (plan->graph) cudaGraphDestroy(plan->graph);
+    delete plan;
+    return RBKI_OK;
 }
 
 rbki_status rbki_tucker_batched(int32_t count, const rbki_tensor* X, const rbki_params* prm, void* workspace,

@@ -146,3 +146,55 @@ def test_batched_refuses_unsupported(rb):
     with pytest.raises(rb.RbkiError) as e:
         rb.rbki_tucker_batched([big], [[4, 4, 4]], 2, 1, [1])
     assert e.value.status == B.E_UNSUPPORTED
+
+
+def test_autotuned_table_keeps_parity_and_independence(rb, tmp_path):
+    cand = {2, 4, 8, 16, 32, 64}
+    try:
+        rb.rbki_wave_autotune()
+        t = rb.rbki_wave_tune_table()
+        assert set(t["gram"]) <= cand and set(t["ttm"]) <= cand
+        rb.rbki_wave_tune_save(tmp_path / "tune.txt")
+        reqs = _reqs(6, 77, dim_lo=8, dim_hi=64, rank_lo=2, rank_hi=8)
+        wls = [synth.serve_request_tensor(r, dtype=np.float64) for r in reqs]
+        xs = [torch.from_numpy(wl.x).cuda().bfloat16() for wl in wls]
+        wave = _run(rb, xs, reqs)
+        alone = [_run(rb, [x], [r])[0] for x, r in zip(xs, reqs)]
+        torch.cuda.synchronize()
+        for wl, x, a, b in zip(wls, xs, wave, alone):
+            assert torch.equal(a["core"], b["core"]) and torch.equal(a["norms"], b["norms"])
+            ref = rbki.rbki_tucker(np.asarray(x.double().cpu().numpy()), wl.ranks, wl.p, wl.q, wl.seed)
+            e, _ = _err(a)
+            e_ref = float(np.sqrt(max(ref["x_norm2"] - ref["core_norm2"], 0.0)))
+            assert abs(e - e_ref) <= 0.01 * e_ref
+        # the saved table reproduces the tuned one
+        rb.rbki_wave_tune_reset()
+        rb.rbki_wave_tune_load(tmp_path / "tune.txt")
+        assert rb.rbki_wave_tune_table() == t
+    finally:
+        rb.rbki_wave_tune_reset()
+
+
+def test_captured_wave_replays(rb):
+    reqs = _reqs(8, 55, dim_lo=16, dim_hi=80, rank_lo=3, rank_hi=10)
+    xs = [synth.serve_request_device(r)[0] for r in reqs]
+    ranks, qs, seeds = [r["ranks"] for r in reqs], [r["q"] for r in reqs], [r["seed"] + 17 for r in reqs]
+    plan = rb.BatchedPlan(xs, ranks, 5, qs, seeds)
+    try:
+        for scale in (1.0, -0.5):
+            with torch.no_grad():
+                for x in xs:
+                    x.mul_(scale)               # refilled in place: the plan reads the same buffers
+            l0 = rb.rbki_kernel_launches()
+            outs = plan.launch()
+            l1 = rb.rbki_kernel_launches()
+            ref = rb.rbki_tucker_batched(xs, ranks, 5, qs, seeds)
+            torch.cuda.synchronize()
+            assert 50 <= l1 - l0 <= 150          # one graph launch carries the whole wave
+            for a, b in zip(outs, ref):
+                for k in ("core", "norms", "info"):
+                    assert torch.equal(a[k], b[k]), k
+                for fa, fb in zip(a["factors"], b["factors"]):
+                    assert torch.equal(fa, fb)
+    finally:
+        plan.close()
