@@ -36,7 +36,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["tucker512", "tucker64", "video", "htr", "serve"], default="tucker512")
+    ap.add_argument("--workload", choices=["tucker512", "tucker64", "video", "htr", "serve", "waves"],
+                    default="tucker512")
     ap.add_argument("--inflight", type=int, default=3,
                     help="decompositions in flight on separate streams (throughput mode); 1 = one at a time")
     ap.add_argument("--requests", type=int, default=4096, help="served stream length (--workload serve)")
@@ -965,12 +966,70 @@ def serve_cpu_baseline(reqs, max_seconds=20.0):
                       f"tensors of the same recipe)"}
 
 
+def run_waves(args):
+    """Batched path alone: the served stream's first --requests requests as waves of
+    --wave-max through rbki_tucker_batched, one after another on one stream (no server, no
+    arrivals).  A step is one pass over all the requests; value = requests / step time."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_2211_14828_gb300 as rb
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        raise SystemExit("--workload waves runs on one GPU")
+    torch.cuda.set_device(0)
+    reqs = synth.serve_stream(n_requests=args.requests, seed=5000)
+    items = [synth.serve_request_device(r) for r in reqs]
+    W = max(1, args.wave_max)
+    waves = [items[i:i + W] for i in range(0, len(items), W)]
+    outs = [None] * len(waves)
+
+    def step():
+        for k, wv in enumerate(waves):
+            o = rb.rbki_tucker_batched([t[0] for t in wv], [t[1] for t in wv], wv[0][2], [t[3] for t in wv],
+                                       [t[4] for t in wv], workspace=outs[k][0]["workspace"] if outs[k] else None,
+                                       outs=outs[k])
+            outs[k] = o
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler()
+    clocks.start()
+    l0 = rb.rbki_kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    launches = rb.rbki_kernel_launches() - l0
+    ms = e0.elapsed_time(e1) / args.steps
+    errs = []
+    for wv, o in zip(waves, outs):
+        for out in o:
+            n = out["norms"].cpu().numpy()
+            errs.append(float(np.sqrt(max(n[0] - n[1], 0.0) / n[0])))
+    print(json.dumps({
+        "metric": "batched rBKI-TK solves/s (waves through rbki_tucker_batched, one stream)",
+        "value": round(len(items) / (ms * 1e-3), 2), "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": f"waves: the first {len(items)} requests of the served stream in waves of {W}",
+                   "l2": "requests are mostly smaller than L2; latency-bound small stages"},
+        "rel_err_mixed": {"median": float(np.median(errs)), "max": float(np.max(errs))},
+        "launches_per_request": round(launches / args.steps / len(items), 2),
+        "e2e": None, "gpu_launches": int(launches), "clocks": clocks.stop(), "cpu_baseline": None,
+    }))
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "waves":
+        run_waves(args)
     elif args.parts > 1:
         run_divide(args)
     else:

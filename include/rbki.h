@@ -222,7 +222,8 @@ rbki_status rbki_batched_plan_destroy(rbki_batched_plan* plan);
  * tiles) for each I_n bucket b (I_n in (32b, 32(b+1)], b = 0..7).  The summation order of an
  * item depends on these values, so results are reproducible bit for bit under one table.
  * rbki_wave_autotune times the candidates {2, 4, 8, 16, 32, 64} on a synthetic batch
- * (48 items of 128 x I x 128 BF16) on `stream` and keeps the fastest (about a second; needs
+ * (48 items of 128 x I x 128 BF16) on `stream` and keeps the fastest when it beats the
+ * default by at least 5% (about a second; needs
  * ~500 MB of device memory for its own buffers); _save / _load write and read the table
  * as text ("<gram|ttm> <b> <steps>" lines), _reset restores the defaults. */
 rbki_status rbki_wave_autotune(void* stream);
