@@ -22,6 +22,7 @@
 // FP64 across units; orthonormalisation, the Krylov products and the eigensolver are FP64.
 #include "kernels.h"
 #include "plan.h"
+#include "tc_ptx.cuh"
 
 #include <cmath>
 #include <cstdio>
@@ -215,6 +216,277 @@ __global__ void __launch_bounds__(NTHREADS) k_gram_b(const __grid_constant__ BPa
 }
 
 constexpr size_t GRAM_SMEM = (2 * KT * GP + KT * 64) * sizeof(float) + KT * sizeof(int64_t);
+
+// ---------------------------------------------------------------------------------------
+// Gram pass on the tensor cores (tcgen05, BF16/FP16 X stored in the products' format).
+// CTA = (item, row block rb of 128 rows, unit of 64-column steps).  Per step the CTA stages
+// X_(n)'s 64 columns for all rows (padded to whole 128-row blocks, zeros outside X) in one
+// of two shared-memory buffers and one thread issues, per K = 16:
+//   G[rb rows, 0:Npad] += X[rb rows, k] X[:, k]^T     (M = 128, N = Npad <= 256)
+//   W[rb rows, 0:S16]  += X[rb rows, k] Omega[k, :]    (M = 128, N = S16 <= 64; Krylov path)
+// with the FP32 accumulators in tensor memory.  Layouts: C > 1 (consecutive columns
+// contiguous): K-major, 128-byte swizzle (row r at r*128 B, 16-byte chunk q at q ^ (r & 7));
+// C == 1 (rows contiguous): MN-major without swizzle (element (r, k) at (r/8)*1024 + k*16 +
+// (r%8)*2 B).  Omega's tile (BF16/FP16, from the same Philox definition) is K-major,
+// 128-byte swizzle.  A buffer is refilled once the MMAs that read it have committed.  Every
+// mbarrier wait is bounded (tc::mbar_wait); on expiry the CTA drains its MMAs, frees tensor
+// memory, sets the error word and writes no partials.
+// ---------------------------------------------------------------------------------------
+constexpr int TCK = 64;                    // columns of X_(n) per step
+constexpr uint32_t TC_TILE_MAX = 2 * 16384; // two 128-row blocks x 64 columns x 2 B
+constexpr uint32_t TC_OM_BYTES = 8192;     // Omega tile: up to 64 rows x 128 B
+constexpr uint32_t TC_BUF = TC_TILE_MAX + TC_OM_BYTES;
+constexpr size_t GRAM_TC_SMEM = 1024 + 2 * (size_t)TC_BUF + 64 + TCK * sizeof(int64_t);
+
+struct gramtc_rec {
+    const void* x;       // BF16 (fp16 = 0) or FP16 (fp16 = 1) storage, [A][I][C]
+    int fp16;
+    int A, I, C;
+    int nrb, npad;       // 128-row blocks (1 or 2); Gram columns padded to 16
+    int ksteps, kpu;     // 64-column steps of X_(n); steps per unit
+    int S, S16;          // sketch width and its padding to 16 (0: no sketch)
+    uint64_t seed;
+    int mode;
+    float* gpart;        // [unit][I][I]: full rows of the CTA's row block
+    float* wpart;        // [unit][I][S]
+    int32_t* err;        // set when a bounded wait expires
+    uint32_t tcols;      // tensor-memory columns allocated (256 or 512)
+    uint32_t wait_us;
+    int gx, gy, gz;      // nrb * units, 1, 1
+};
+
+__device__ __forceinline__ uint32_t swz128(int r, int k) {
+    return (uint32_t)r * 128u + ((uint32_t)(((k >> 3) ^ (r & 7))) << 4) + (uint32_t)(k & 7) * 2u;
+}
+
+constexpr int TCT = 256;          // threads of the tensor-core Gram pass
+constexpr int TCB = 16;           // loads a thread issues before its stores (memory parallelism)
+
+// Stages the step's 64 columns: work item e of n (e = tid + TCT u) is loaded by load(e) into a
+// register and stored by store(e, v); TCB loads are in flight before the first store.
+template <typename V, typename L, typename S>
+__device__ __forceinline__ void stage_batched(int n, L load, S store) {
+    for (int e0 = threadIdx.x; e0 < n; e0 += TCT * TCB) {
+        V v[TCB];
+#pragma unroll
+        for (int u = 0; u < TCB; ++u) {
+            const int e = e0 + u * TCT;
+            v[u] = e < n ? load(e) : V{};
+        }
+#pragma unroll
+        for (int u = 0; u < TCB; ++u) {
+            const int e = e0 + u * TCT;
+            if (e < n) store(e, v[u]);
+        }
+    }
+}
+
+template <bool IFAST>
+__device__ __forceinline__ void gramtc_stage(const gramtc_rec& r, int64_t col0, const int64_t* colb, uint8_t* tile,
+                                             uint8_t* om) {
+    const uint16_t* x = static_cast<const uint16_t*>(r.x);
+    const int rows = r.nrb * 128, I = r.I;
+    const int64_t C = r.C, J = (int64_t)r.A * r.C;
+    const int tid = threadIdx.x;
+    if (!IFAST) {
+        // colb[k] = offset of X[a][0][c] of column col0 + k (-1 past the end)
+        if (C % 8 == 0) {
+            // 16-byte chunks: 8 consecutive columns of one row (col0 is a multiple of 64 and C of
+            // 8, so a chunk never crosses a slab of X_(n)'s columns and is 16-byte aligned)
+            stage_batched<uint4>(
+                rows * 8,
+                [&](int e) {
+                    const int rr = e >> 3;
+                    const int64_t cb = colb[8 * (e & 7)];
+                    return (rr < I && cb >= 0) ? __ldg(reinterpret_cast<const uint4*>(x + cb + (int64_t)rr * C))
+                                               : make_uint4(0u, 0u, 0u, 0u);
+                },
+                [&](int e, uint4 v) { *reinterpret_cast<uint4*>(tile + swz128(e >> 3, 8 * (e & 7))) = v; });
+        } else {
+            // element by element, a warp reading 32 consecutive columns of one row
+            stage_batched<uint16_t>(
+                rows * TCK,
+                [&](int e) {
+                    const int rr = e / TCK;
+                    const int64_t cb = colb[e % TCK];
+                    return (rr < I && cb >= 0) ? x[cb + (int64_t)rr * C] : (uint16_t)0;
+                },
+                [&](int e, uint16_t v) { *reinterpret_cast<uint16_t*>(tile + swz128(e / TCK, e % TCK)) = v; });
+        }
+    } else {
+        if (I % 8 == 0) {
+            // 16-byte chunks: 8 consecutive rows of one column
+            stage_batched<uint4>(
+                (rows / 8) * TCK,
+                [&](int e) {
+                    const int k = e % TCK, r8 = e / TCK;
+                    const int64_t col = col0 + k;
+                    return (8 * r8 < I && col < J) ? __ldg(reinterpret_cast<const uint4*>(x + col * I + 8 * r8))
+                                                   : make_uint4(0u, 0u, 0u, 0u);
+                },
+                [&](int e, uint4 v) { *reinterpret_cast<uint4*>(tile + (e / TCK) * 1024 + (e % TCK) * 16) = v; });
+        } else {
+            const int rsh = rows == 128 ? 7 : 8;
+            stage_batched<uint16_t>(
+                rows * TCK,
+                [&](int e) {
+                    const int k = e >> rsh, rr = e & (rows - 1);
+                    const int64_t col = col0 + k;
+                    return (rr < I && col < J) ? x[col * I + rr] : (uint16_t)0;
+                },
+                [&](int e, uint16_t v) {
+                    const int k = e >> rsh, rr = e & (rows - 1);
+                    *reinterpret_cast<uint16_t*>(tile + (rr >> 3) * 1024 + k * 16 + (rr & 7) * 2) = v;
+                });
+        }
+    }
+    if (r.S16 > 0) {
+        // Omega[col0 + k][s] for s < S16 (zeros past S and past X_(n)'s columns), rounded to the
+        // products' format, stored K-major with the 128-byte swizzle (row s, column k)
+        const int np = r.S16 / 2;
+        for (int e = tid; e < TCK * np; e += TCT) {
+            const int k = e / np, pr = e % np, s = 2 * pr;
+            float z0 = 0.f, z1 = 0.f;
+            if (col0 + k < J && s < r.S)
+                omega_pair_f32(r.seed, (uint32_t)r.mode, (uint64_t)(col0 + k), (uint32_t)pr, z0, z1);
+            if (s + 1 >= r.S) z1 = 0.f;
+            uint16_t h0, h1;
+            if (r.fp16) {
+                __half a = __float2half_rn(z0), b = __float2half_rn(z1);
+                h0 = *reinterpret_cast<uint16_t*>(&a);
+                h1 = *reinterpret_cast<uint16_t*>(&b);
+            } else {
+                __nv_bfloat16 a = __float2bfloat16_rn(z0), b = __float2bfloat16_rn(z1);
+                h0 = *reinterpret_cast<uint16_t*>(&a);
+                h1 = *reinterpret_cast<uint16_t*>(&b);
+            }
+            *reinterpret_cast<uint16_t*>(om + swz128(s, k)) = h0;
+            *reinterpret_cast<uint16_t*>(om + swz128(s + 1, k)) = h1;
+        }
+    }
+}
+
+template <bool IFAST>
+__device__ __forceinline__ void gramtc_dev(const gramtc_rec& r, int bx) {
+    using namespace tc;
+    extern __shared__ __align__(1024) uint8_t tcsm[];
+    uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tcsm) + 1023) & ~uintptr_t(1023));
+    uint8_t* buf[2] = {base, base + TC_BUF};
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base + 2 * TC_BUF);   // [0..1] MMA done, [2] drain
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 3);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 4);
+    int64_t* colb = reinterpret_cast<int64_t*>(bars + 8);          // the step's column offsets
+    const int rb = bx % r.nrb, unit = bx / r.nrb;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t lim = r.wait_us;
+    if (warp == 0) {
+        tmem_alloc(smem_u32(tslot), r.tcols);
+        tmem_relinquish();
+    }
+    if (tid == 0) {
+        mbar_init(smem_u32(&bars[0]), 1);
+        mbar_init(smem_u32(&bars[1]), 1);
+        mbar_init(smem_u32(&bars[2]), 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tslot;
+    const uint32_t wcol = (uint32_t)((r.npad + 31) & ~31);   // W's first accumulator column
+    const int k_lo = unit * r.kpu, k_hi = min(r.ksteps, k_lo + r.kpu);
+    const uint32_t idg = idesc_f16(128, r.npad, IFAST, IFAST, r.fp16 != 0);
+    const uint32_t idw = idesc_f16(128, r.S16 > 0 ? r.S16 : 16, IFAST, false, r.fp16 != 0);
+    uint32_t committed = 0;   // MMA groups committed per buffer (phase bookkeeping)
+    bool ok = true;
+    for (int t = k_lo; t < k_hi; ++t) {
+        const int n = t - k_lo, b = n & 1;
+        // buffer b was last read by the MMAs of step n - 2
+        if (n >= 2) {
+            bool w = mbar_wait(smem_u32(&bars[b]), (uint32_t)(((n - 2) >> 1) & 1), abort_flag, lim);
+            __syncthreads();
+            if (!w || *abort_flag) {
+                ok = false;
+                break;
+            }
+        }
+        if (!IFAST && tid < TCK) {
+            const int64_t col = (int64_t)t * TCK + tid;
+            colb[tid] = col < (int64_t)r.A * r.C ? (col / r.C) * r.I * r.C + col % r.C : -1;
+        }
+        __syncthreads();
+        gramtc_stage<IFAST>(r, (int64_t)t * TCK, colb, buf[b], buf[b] + TC_TILE_MAX);
+        fence_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t tb = smem_u32(buf[b]), to = tb + TC_TILE_MAX;
+            const uint64_t da = IFAST ? sdesc(tb + (uint32_t)rb * 16384u, 128, 1024, LAYOUT_NONE)
+                                      : sdesc(tb + (uint32_t)rb * 16384u, 16, 1024, LAYOUT_SW128);
+            const uint64_t db = IFAST ? sdesc(tb, 128, 1024, LAYOUT_NONE) : sdesc(tb, 16, 1024, LAYOUT_SW128);
+            const uint64_t dom = sdesc(to, 16, 1024, LAYOUT_SW128);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const uint64_t ka = IFAST ? (uint64_t)(16 * kk) : (uint64_t)(2 * kk);   // K = 16 step
+                const uint32_t acc = (n > 0 || kk > 0) ? 1u : 0u;
+                umma_f16(tbase, da + ka, db + ka, idg, acc);
+                if (r.S16 > 0) umma_f16(tbase + wcol, da + ka, dom + (uint64_t)(2 * kk), idw, acc);
+            }
+            umma_commit(smem_u32(&bars[b]));
+        }
+        ++committed;
+    }
+    // the last one or two groups: wait for their commits (bounded), also on the abort path
+    if (tid == 0) {
+        umma_commit(smem_u32(&bars[2]));
+        if (!mbar_drain(smem_u32(&bars[2]), 0, lim)) *abort_flag = 1;
+    }
+    __syncthreads();
+    tc_fence_after();
+    if (ok && !*abort_flag && k_hi > k_lo) {
+        // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 = rows 128 rb + 32 (w % 4)
+        // + lane; the two warps of a sub-partition take alternate 32-column groups
+        const int q = warp & 3, half = warp >> 2;
+        const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+        const int row = rb * 128 + q * 32 + lane;
+        float v[32];
+        float* g = r.gpart + ((int64_t)unit * r.I + row) * r.I;
+        for (int c0 = 32 * half; c0 < r.npad; c0 += 64) {
+            tmem_ld32(tbase + lane_off + (uint32_t)c0, v);
+            if (row < r.I)
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    if (c0 + j < r.I) g[c0 + j] = v[j];
+        }
+        if (r.S16 > 0) {
+            float* w = r.wpart + ((int64_t)unit * r.I + row) * r.S;
+            for (int c0 = 32 * half; c0 < r.S16; c0 += 64) {
+                tmem_ld32(tbase + lane_off + wcol + (uint32_t)c0, v);
+                if (row < r.I)
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (c0 + j < r.S) w[c0 + j] = v[j];
+            }
+        }
+    }
+    if ((!ok || *abort_flag) && tid == 0) atomicExch(r.err, 1);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tbase, r.tcols);
+    }
+    (void)committed;
+}
+
+template <bool IFAST>
+__global__ void __launch_bounds__(TCT) k_gram_tc_b(const __grid_constant__ BPack<gramtc_rec> p) {
+    const gramtc_rec& r = p.r[blockIdx.y];
+    int bx, by, bz;
+    if (!bat_block(r, bx, by, bz)) return;
+    gramtc_dev<IFAST>(r, bx);
+}
 
 // G (FP64, I x I) = sum over units of the block pairs, in unit order; the lower blocks mirror
 // the upper ones, the diagonal blocks are symmetrised: G is exactly symmetric.
@@ -499,10 +771,12 @@ __global__ void k_fill_b(const __grid_constant__ BPack<fill_rec> p) {
 }
 
 // info[n] = kept Krylov width (Krylov path) or I_n (Gram path); info[N+n] = path;
-// info[2N] = 0 (the wave's kernels have no device waits); q_used[n] = q or 0
+// info[2N] = the request's error word (nonzero: a bounded wait of the tensor-core Gram pass
+// expired); q_used[n] = q or 0
 struct info_rec {
     int32_t* info;
     int32_t* q_used;
+    const int32_t* err;
     int N, q;
     int32_t gram[RBKI_MAX_ORDER];
     int32_t dim[RBKI_MAX_ORDER];
@@ -519,7 +793,7 @@ __global__ void k_info_b(const __grid_constant__ BPack<info_rec> p) {
     if (r.info) {
         r.info[n] = r.gram[n] ? r.dim[n] : *r.kept[n];
         r.info[r.N + n] = r.gram[n];
-        if (n == 0) r.info[2 * r.N] = 0;
+        if (n == 0) r.info[2 * r.N] = *r.err;
     }
     if (r.q_used) r.q_used[n] = r.gram[n] ? 0 : r.q;
 }
@@ -575,6 +849,7 @@ struct WaveMode {
     int32_t* kept = nullptr;
     float *gpart = nullptr, *wpart = nullptr;
     int ksteps = 0, kpu = 1, units = 1;
+    bool tc = false;                 // Gram pass on the tensor cores (64-column steps)
 };
 
 struct WaveReq {
@@ -586,6 +861,7 @@ struct WaveReq {
     int64_t tmax = 0;           // largest intermediate of the core chain (elements)
     double* sq_part = nullptr;
     double* norms = nullptr;    // out.norms or workspace
+    int32_t* err = nullptr;     // device error word of the request's bounded waits
     int rnd = 0;                // rounding of X as it is read (RBKI_BF16 / RBKI_F16, 0: none)
 };
 
@@ -632,7 +908,10 @@ void wave_carve(WaveReq& q, Carve& cv) {
         WaveMode& w = q.mode[n];
         w.m = &m;
         const int I = (int)m.I;
-        w.ksteps = (int)cdiv(m.A * m.C, KT);
+        // the tensor-core Gram pass reads X in its storage format, so it needs X stored as the
+        // products' 16-bit type; otherwise the CUDA-core pass rounds as it reads
+        w.tc = q.X.dtype == pl.stream_dtype && (q.X.dtype == RBKI_BF16 || q.X.dtype == RBKI_F16);
+        w.ksteps = (int)cdiv(m.A * m.C, w.tc ? TCK : KT);
         w.kpu = per_unit(0, I, w.ksteps);
         w.units = (int)cdiv(w.ksteps, w.kpu);
         w.gpart = cv.take<float>((size_t)w.units * I * I);
@@ -658,6 +937,7 @@ void wave_carve(WaveReq& q, Carve& cv) {
     q.tbuf[1] = cv.take<float>((size_t)q.tmax);
     q.sq_part = cv.take<double>((size_t)cdiv(std::max(pl.numel, pl.ranks_numel), SQ_CHUNK));
     q.norms = cv.take<double>(2);
+    q.err = cv.take<int32_t>(1);
 }
 
 rbki_status launch_ttm(const std::vector<ttm_rec>& recs, cudaStream_t st) {
@@ -689,33 +969,63 @@ rbki_status run_wave(std::vector<WaveReq>& Q, cudaStream_t st) {
     int qmax = 0;
     {
         std::vector<gram_rec> gr;
+        std::vector<gramtc_rec> gt[2];   // [C == 1]
         std::vector<greduce_rec> gd;
         std::vector<xreduce_rec> wd;
         std::vector<fill_rec> fk;
-        for (auto& q : Q)
+        for (auto& q : Q) {
+            fk.push_back(fill_rec{q.err, 0, 1, 1, 1});
             for (int n = 0; n < q.pl.N; ++n) {
                 WaveMode& w = q.mode[n];
                 const ModePlan& m = *w.m;
-                const int I = (int)m.I, nb = (int)cdiv(I, GB), npair = nb * (nb + 1) / 2;
-                gram_rec r{};
-                r.x = q.X.data;
-                r.dtype = q.X.dtype;
-                r.rnd = q.X.dtype == q.pl.stream_dtype ? 0 : q.rnd;
-                r.A = (int)m.A;
-                r.I = I;
-                r.C = (int)m.C;
-                r.nb = nb;
-                r.npair = npair;
-                r.ksteps = w.ksteps;
-                r.kpu = w.kpu;
-                r.S = m.gram ? 0 : m.S;
-                r.seed = q.pl.seed;
-                r.mode = n;
-                r.gpart = w.gpart;
-                r.wpart = w.wpart;
-                r.gx = npair * w.units;
-                r.gy = r.gz = 1;
-                gr.push_back(r);
+                const int I = (int)m.I;
+                if (w.tc) {
+                    gramtc_rec r{};
+                    r.x = q.X.data;
+                    r.fp16 = q.X.dtype == RBKI_F16 ? 1 : 0;
+                    r.A = (int)m.A;
+                    r.I = I;
+                    r.C = (int)m.C;
+                    r.nrb = (int)cdiv(I, 128);
+                    r.npad = (int)rup(I, 16);
+                    r.ksteps = w.ksteps;
+                    r.kpu = w.kpu;
+                    r.S = m.gram ? 0 : m.S;
+                    r.S16 = m.gram ? 0 : (int)rup(m.S, 16);
+                    r.seed = q.pl.seed;
+                    r.mode = n;
+                    r.gpart = w.gpart;
+                    r.wpart = w.wpart;
+                    r.err = q.err;
+                    // G in columns [0, npad), W from rup(npad, 32); the epilogue reads whole
+                    // 32-column groups, so both are counted rounded up to 32
+                    r.tcols = (uint32_t)(rup(r.npad, 32) + rup(r.S16, 32) <= 256 ? 256 : 512);
+                    r.wait_us = tc::WAIT_US_DEFAULT;
+                    r.gx = r.nrb * w.units;
+                    r.gy = r.gz = 1;
+                    gt[m.C == 1 ? 1 : 0].push_back(r);
+                } else {
+                    const int nb = (int)cdiv(I, GB), npair = nb * (nb + 1) / 2;
+                    gram_rec r{};
+                    r.x = q.X.data;
+                    r.dtype = q.X.dtype;
+                    r.rnd = q.X.dtype == q.pl.stream_dtype ? 0 : q.rnd;
+                    r.A = (int)m.A;
+                    r.I = I;
+                    r.C = (int)m.C;
+                    r.nb = nb;
+                    r.npair = npair;
+                    r.ksteps = w.ksteps;
+                    r.kpu = w.kpu;
+                    r.S = m.gram ? 0 : m.S;
+                    r.seed = q.pl.seed;
+                    r.mode = n;
+                    r.gpart = w.gpart;
+                    r.wpart = w.wpart;
+                    r.gx = npair * w.units;
+                    r.gy = r.gz = 1;
+                    gr.push_back(r);
+                }
                 gd.push_back(greduce_rec{w.gpart, w.units, I, w.G, (int)cdiv((int64_t)I * I, 256), 1, 1});
                 if (!m.gram) {
                     wd.push_back(xreduce_rec{w.wpart, w.units, I, m.S, m.S, w.Qall, m.b, nullptr, 0,
@@ -724,9 +1034,17 @@ rbki_status run_wave(std::vector<WaveReq>& Q, cudaStream_t st) {
                     qmax = std::max(qmax, m.q);
                 }
             }
+        }
         static const size_t gmax = max_dyn_smem(k_gram_b);
-        if (GRAM_SMEM > gmax) return set_error(RBKI_E_CUDA, "batched Gram pass: shared memory");
+        static const size_t tmax0 = max_dyn_smem(k_gram_tc_b<false>);
+        static const size_t tmax1 = max_dyn_smem(k_gram_tc_b<true>);
+        if (GRAM_SMEM > gmax || GRAM_TC_SMEM > tmax0 || GRAM_TC_SMEM > tmax1)
+            return set_error(RBKI_E_CUDA, "batched Gram pass: shared memory");
         RBKI_TRY(bat_launch(k_fill_b, fk.data(), (int)fk.size(), 32, 0, st, "k_fill_b"));
+        RBKI_TRY(bat_launch(k_gram_tc_b<false>, gt[0].data(), (int)gt[0].size(), TCT, GRAM_TC_SMEM, st,
+                            "k_gram_tc_b"));
+        RBKI_TRY(bat_launch(k_gram_tc_b<true>, gt[1].data(), (int)gt[1].size(), TCT, GRAM_TC_SMEM, st,
+                            "k_gram_tc_b"));
         RBKI_TRY(bat_launch(k_gram_b, gr.data(), (int)gr.size(), NTHREADS, GRAM_SMEM, st, "k_gram_b"));
         RBKI_TRY(bat_launch(k_greduce_b, gd.data(), (int)gd.size(), 256, 0, st, "k_greduce_b"));
         RBKI_TRY(bat_launch(k_xreduce_b, wd.data(), (int)wd.size(), 256, 0, st, "k_xreduce_b"));
@@ -860,6 +1178,7 @@ rbki_status run_wave(std::vector<WaveReq>& Q, cudaStream_t st) {
                 r.q = q.pl.prm.q;
                 for (int n = 0; n < q.pl.N; ++n) {
                     r.gram[n] = q.mode[n].m->gram ? 1 : 0;
+                    r.err = q.err;
                     r.dim[n] = (int32_t)q.pl.dims[n];
                     r.kept[n] = q.mode[n].kept;
                 }
