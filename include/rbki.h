@@ -347,6 +347,17 @@ rbki_status rbki_diag_krylov_stall(const rbki_tensor* X, int32_t mode, int32_t p
                                    void* workspace, size_t workspace_bytes,
                                    uint32_t wait_us, void* stream);
 
+/* The same for the tensor-core Gram pass of rbki_tucker_batched: the wave runs with every
+ * Gram-pass CTA first waiting on a barrier that nothing completes, giving up after wait_us
+ * (1 .. 2e6) microseconds; the CTA then drains its MMAs, frees tensor memory, writes no
+ * partials and sets its request's error word (info[2N]).  Synchronises `stream` and returns
+ * RBKI_E_TIMEOUT when any item's error word is set (the expected outcome when an item takes
+ * the tensor-core pass; the outputs are then not valid), else RBKI_OK.  Arguments otherwise
+ * as rbki_tucker_batched. */
+rbki_status rbki_diag_batched_stall(int32_t count, const rbki_tensor* X, const rbki_params* prm,
+                                    void* workspace, size_t workspace_bytes, const rbki_tucker_out* out,
+                                    uint32_t wait_us, void* stream);
+
 /* Algorithm 1 for one mode: the orthonormal Krylov basis Q = [Q_0..Q_q] (I_n x b,
  * row-major FP64, deflated columns are zero), b = S(q+1), S = min(R_n+p, I_n). */
 rbki_status rbki_mode_basis(const rbki_tensor* X, const rbki_params* prm, int32_t mode,

@@ -2,7 +2,7 @@
 C ABI in include/rbki.h, with a thin ctypes binding."""
 from ._binding import (  # noqa: F401
     LIB_PATH, RbkiError, lib, rbki_kernel_launches, rbki_krylov_product, rbki_krylov_product_noalloc, rbki_mode_basis,
-    rbki_diag_krylov_stall,
+    rbki_diag_krylov_stall, rbki_diag_batched_stall,
     rbki_syev, rbki_tucker, rbki_htr, RbkiServer, rbki_tucker_workspace, rbki_profile_enable, rbki_profile_reset,
     rbki_profile_read, PROF_KRYLOV, PROF_SKETCH, PROF_GRAM, PROF_TTM, PROF_STAGE, PROF_SAMPLE,
     rbki_sample_units, rbki_split_mode, rbki_tucker_batch, rbki_tucker_batched, rbki_tucker_batched_workspace,

@@ -85,6 +85,7 @@ def lib():
             "rbki_tucker_batch": (st, [C.c_int32, vp, vp, vp, C.c_size_t, vp, vp]),
             "rbki_tucker_batched_workspace": (st, [C.c_int32, vp, vp, sz]),
             "rbki_wave_autotune": (st, [vp]),
+            "rbki_diag_batched_stall": (st, [C.c_int32, vp, vp, vp, C.c_size_t, vp, C.c_uint32, vp]),
             "rbki_batched_plan_create": (st, [C.c_int32, vp, vp, vp, C.c_size_t, vp, vp, C.POINTER(vp)]),
             "rbki_batched_plan_launch": (st, [vp, vp]),
             "rbki_batched_plan_destroy": (st, [vp]),
@@ -438,6 +439,26 @@ def rbki_diag_krylov_stall(x, mode: int, q_mat, prec="bf16", wait_us: int = 2000
                                           C.c_void_p(P.data_ptr()), C.c_void_p(workspace.data_ptr()),
                                           C.c_size_t(workspace.numel()), C.c_uint32(wait_us), stream_ptr(stream))
     return int(status), P
+
+
+def rbki_diag_batched_stall(xs, ranks, p, qs, seeds, prec="bf16", wait_us: int = 2000, stream=None):
+    """A wave with a planted stall in its tensor-core Gram pass (bounded by wait_us): exercises
+    that kernel's abort path.  Returns (status, outs); the expected status is E_TIMEOUT with
+    info[2N] set on the items that took the tensor-core pass."""
+    torch = _torch()
+    n = len(xs)
+    qv = [int(qs)] * n if isinstance(qs, int) else [int(v) for v in qs]
+    ts = (rbki_tensor * n)(*[make_tensor(x) for x in xs])
+    ps = (rbki_params * n)(*[make_params(ranks[k], p, qv[k], seeds[k], prec, 0) for k in range(n)])
+    need = C.c_size_t(0)
+    check(lib().rbki_tucker_batched_workspace(n, ts, ps, C.byref(need)), "rbki_tucker_batched_workspace")
+    workspace = torch.empty(max(int(need.value), 1), dtype=torch.uint8, device=xs[0].device)
+    outs = [alloc_outputs(x.shape, ranks[k], x.device) for k, x in enumerate(xs)]
+    os_ = (rbki_tucker_out * n)(*[make_out(o) for o in outs])
+    status = lib().rbki_diag_batched_stall(n, ts, ps, C.c_void_p(workspace.data_ptr()),
+                                           C.c_size_t(workspace.numel()), os_, C.c_uint32(wait_us),
+                                           stream_ptr(stream))
+    return int(status), outs
 
 
 def rbki_krylov_product_noalloc(x, mode: int, q_mat, prec="bf16", stream=None):

@@ -216,6 +216,14 @@ rbki_status run_wave_requests(rbki_server* s, Slot& slot, const std::vector<Requ
     return rs;
 }
 
+// A wave item whose bounded wait expired (info[2N] != 0; requests without info cannot tell)
+bool wave_item_timed_out(const Request* r) {
+    if (!r->out.info) return false;
+    int32_t e = 0;
+    if (cudaMemcpy(&e, r->out.info + 2 * r->X.order, sizeof(e), cudaMemcpyDeviceToHost) != cudaSuccess) return false;
+    return e != 0;
+}
+
 void wave_main(rbki_server* s, int id) {
     cudaSetDevice(s->device);
     Slot& slot = s->wslots[id];
@@ -236,13 +244,17 @@ void wave_main(rbki_server* s, int id) {
         s->running += k;
         lk.unlock();
         const rbki_status rs = run_wave_requests(s, slot, w, off);
+        std::vector<bool> timed_out(w.size(), false);
+        if (rs >= 0)
+            for (size_t i = 0; i < w.size(); ++i) timed_out[i] = wave_item_timed_out(w[i]);
         const double t = now_s();
         lk.lock();
         s->arena->release(off);
         s->running -= k;
-        for (Request* r : w) {
+        for (size_t i = 0; i < w.size(); ++i) {
+            Request* r = w[i];
             r->t_done = t;
-            r->result = r->cancel ? RBKI_E_CANCELLED : rs;
+            r->result = r->cancel ? RBKI_E_CANCELLED : (timed_out[i] ? RBKI_E_TIMEOUT : rs);
             r->state = State::DONE;
         }
         s->cv_work.notify_all();

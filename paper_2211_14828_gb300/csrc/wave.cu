@@ -252,6 +252,7 @@ struct gramtc_rec {
     int32_t* err;        // set when a bounded wait expires
     uint32_t tcols;      // tensor-memory columns allocated (256 or 512)
     uint32_t wait_us;
+    int stall;           // diagnostics: first wait on a barrier nothing completes (expires)
     int gx, gy, gz;      // nrb * units, 1, 1
 };
 
@@ -373,8 +374,9 @@ __device__ __forceinline__ void gramtc_dev(const gramtc_rec& r, int bx) {
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tcsm) + 1023) & ~uintptr_t(1023));
     uint8_t* buf[2] = {base, base + TC_BUF};
     uint64_t* bars = reinterpret_cast<uint64_t*>(base + 2 * TC_BUF);   // [0..1] MMA done, [2] drain
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 3);
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 4);
+    uint64_t* never = bars + 3;                                        // never completed
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 4);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 5);
     int64_t* colb = reinterpret_cast<int64_t*>(bars + 8);          // the step's column offsets
     const int rb = bx % r.nrb, unit = bx / r.nrb;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -387,6 +389,7 @@ __device__ __forceinline__ void gramtc_dev(const gramtc_rec& r, int bx) {
         mbar_init(smem_u32(&bars[0]), 1);
         mbar_init(smem_u32(&bars[1]), 1);
         mbar_init(smem_u32(&bars[2]), 1);
+        mbar_init(smem_u32(never), 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -398,9 +401,14 @@ __device__ __forceinline__ void gramtc_dev(const gramtc_rec& r, int bx) {
     const int k_lo = unit * r.kpu, k_hi = min(r.ksteps, k_lo + r.kpu);
     const uint32_t idg = idesc_f16(128, r.npad, IFAST, IFAST, r.fp16 != 0);
     const uint32_t idw = idesc_f16(128, r.S16 > 0 ? r.S16 : 16, IFAST, false, r.fp16 != 0);
-    uint32_t committed = 0;   // MMA groups committed per buffer (phase bookkeeping)
     bool ok = true;
-    for (int t = k_lo; t < k_hi; ++t) {
+    if (r.stall) {
+        // a planted stall (diagnostics): every thread's wait runs out, the CTA aborts
+        mbar_wait(smem_u32(never), 0, abort_flag, lim);
+        __syncthreads();
+        ok = !*abort_flag;
+    }
+    for (int t = k_lo; ok && t < k_hi; ++t) {
         const int n = t - k_lo, b = n & 1;
         // buffer b was last read by the MMAs of step n - 2
         if (n >= 2) {
@@ -435,7 +443,6 @@ __device__ __forceinline__ void gramtc_dev(const gramtc_rec& r, int bx) {
             }
             umma_commit(smem_u32(&bars[b]));
         }
-        ++committed;
     }
     // the last one or two groups: wait for their commits (bounded), also on the abort path
     if (tid == 0) {
@@ -477,7 +484,6 @@ __device__ __forceinline__ void gramtc_dev(const gramtc_rec& r, int bx) {
         tc_fence_after();
         tmem_dealloc(tbase, r.tcols);
     }
-    (void)committed;
 }
 
 template <bool IFAST>
@@ -952,7 +958,8 @@ rbki_status launch_ttm(const std::vector<ttm_rec>& recs, cudaStream_t st) {
 // Algorithms 1-2 for every request of the wave, stage by stage.  Per Krylov-path mode the
 // Krylov products are P_j = (X_(n) X_(n)^T) Q_j with X_(n) X_(n)^T formed once (I_n <= 256):
 // one pass over X instead of q + 1, and FP64 products on the small matrix.
-rbki_status run_wave(std::vector<WaveReq>& Q, cudaStream_t st) {
+rbki_status run_wave(std::vector<WaveReq>& Q, cudaStream_t st, uint32_t wait_us = tc::WAIT_US_DEFAULT,
+                     int stall = 0) {
     const int nq = (int)Q.size();
     // ---- |X|^2 ----
     {
@@ -1000,7 +1007,8 @@ rbki_status run_wave(std::vector<WaveReq>& Q, cudaStream_t st) {
                     // G in columns [0, npad), W from rup(npad, 32); the epilogue reads whole
                     // 32-column groups, so both are counted rounded up to 32
                     r.tcols = (uint32_t)(rup(r.npad, 32) + rup(r.S16, 32) <= 256 ? 256 : 512);
-                    r.wait_us = tc::WAIT_US_DEFAULT;
+                    r.wait_us = wait_us;
+                    r.stall = stall;
                     r.gx = r.nrb * w.units;
                     r.gy = r.gz = 1;
                     gt[m.C == 1 ? 1 : 0].push_back(r);
@@ -1492,6 +1500,28 @@ rbki_status rbki_batched_plan_destroy(rbki_batched_plan* plan) {
     if (plan->graph) cudaGraphDestroy(plan->graph);
     delete plan;
     return RBKI_OK;
+}
+
+rbki_status rbki_diag_batched_stall(int32_t count, const rbki_tensor* X, const rbki_params* prm, void* workspace,
+                                   size_t workspace_bytes, const rbki_tucker_out* out, uint32_t wait_us,
+                                   void* stream) {
+    if (count < 1 || !out) return set_error(RBKI_E_INVAL, "count must be >= 1 and out non-NULL");
+    if (wait_us < 1 || wait_us > tc::WAIT_US_DEFAULT) return set_error(RBKI_E_INVAL, "wait_us out of range");
+    size_t need = 0;
+    std::vector<WaveReq> Q;
+    RBKI_TRY(wave_prepare(count, X, prm, out, nullptr, Q, &need));
+    if (!workspace || workspace_bytes < need) return set_error(RBKI_E_NOMEM, "workspace too small");
+    RBKI_TRY(wave_prepare(count, X, prm, out, workspace, Q, &need));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    RBKI_TRY(run_wave(Q, st, wait_us, 1));
+    RBKI_CUDA_TRY(cudaStreamSynchronize(st));
+    int any = 0;
+    for (const auto& q : Q) {
+        int32_t e = 0;
+        RBKI_CUDA_TRY(cudaMemcpy(&e, q.err, sizeof(e), cudaMemcpyDeviceToHost));
+        any |= e;
+    }
+    return any ? set_error(RBKI_E_TIMEOUT, "a bounded wait inside the Gram pass expired") : RBKI_OK;
 }
 
 rbki_status rbki_tucker_batched(int32_t count, const rbki_tensor* X, const rbki_params* prm, void* workspace,

@@ -50,3 +50,28 @@ def test_expired_wait_reports_timeout_and_next_call_succeeds(rb, dims, mode, s, 
         # Y = X^T Q is rounded to BF16 before the second product (unit roundoff 2^-8); the
         # split variant carries it as hi + lo (about 2^-16)
         assert float((p2 - want).norm() / want.norm()) <= (2.0 ** -8 if prec == "bf16" else 2e-5)
+
+
+def test_batched_gram_pass_expired_wait_reports_timeout(rb):
+    """The tensor-core Gram pass of rbki_tucker_batched: every CTA's planted wait runs out,
+    the wave reports E_TIMEOUT with info[2N] set per item, and the next wave on the same
+    context is correct and bitwise equal to a wave run before the stall."""
+    import synth
+    from paper_2211_14828_gb300 import _binding as B
+    reqs = synth.serve_stream(n_requests=4, seed=808, dim_lo=24, dim_hi=96, rank_lo=3, rank_hi=10)
+    xs = [synth.serve_request_device(r)[0] for r in reqs]           # BF16: the tensor-core pass
+    ranks, qs, seeds = [r["ranks"] for r in reqs], [r["q"] for r in reqs], [r["seed"] for r in reqs]
+    before = rb.rbki_tucker_batched(xs, ranks, 5, qs, seeds)
+    torch.cuda.synchronize()
+    status, outs = rb.rbki_diag_batched_stall(xs, ranks, 5, qs, seeds, wait_us=2000)
+    assert status == B.E_TIMEOUT
+    for o, x in zip(outs, xs):
+        assert int(o["info"].cpu()[2 * x.dim()]) == 1
+    for _ in range(2):
+        after = rb.rbki_tucker_batched(xs, ranks, 5, qs, seeds)
+        torch.cuda.synchronize()
+        for a, b, x in zip(before, after, xs):
+            assert int(b["info"].cpu()[2 * x.dim()]) == 0
+            assert torch.equal(a["core"], b["core"]) and torch.equal(a["norms"], b["norms"])
+            for fa, fb in zip(a["factors"], b["factors"]):
+                assert torch.equal(fa, fb)
