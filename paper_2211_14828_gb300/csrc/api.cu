@@ -453,10 +453,10 @@ rbki_status orth2(const ModePlan& m, int col0, int32_t* kept, cudaStream_t st) {
     return RBKI_OK;
 }
 
-// Algorithm 1 for mode n: Q = [Q_0 .. Q_q] in m.Qall, P_j = A Q_j in m.Pall
-rbki_status mode_basis(const Plan& pl, const ModePlan& m, int32_t* kept, cudaStream_t st) {
+// Algorithm 1 steps 1-2 for mode n: W = X_(n) Omega into block 0 of m.Qall (Omega generated
+// per tile in the tensor-core images, or in the [A][S][C] layout on the CUDA-core path)
+static rbki_status sketch_mode(const Plan& pl, const ModePlan& m, cudaStream_t st) {
     View v = mode_view(pl, m);
-    // step 1-2: W = X_(n) Omega  (Omega generated in the [A][S][C] layout)
     if (m.tc || m.tc2) {
         RBKI_TRY(tc::omega_images(pl.seed, m.n, v, m.S, m.N, pl.split, m.omg, st));
         int tok = prof_begin(RBKI_PROF_SKETCH, st);
@@ -470,6 +470,12 @@ rbki_status mode_basis(const Plan& pl, const ModePlan& m, int32_t* kept, cudaStr
                                nullptr, 0, st));
         prof_end(tok, st);
     }
+    return RBKI_OK;
+}
+
+// Algorithm 1 for mode n: Q = [Q_0 .. Q_q] in m.Qall, P_j = A Q_j in m.Pall
+rbki_status mode_basis(const Plan& pl, const ModePlan& m, int32_t* kept, cudaStream_t st) {
+    RBKI_TRY(sketch_mode(pl, m, st));
     if (pl.flags & RBKI_FLAG_POWER) {
         // power iteration: each product replaces the block, orthonormalised on its own
         RBKI_TRY(orth2(m, 0, kept, st));
@@ -553,6 +559,75 @@ rbki_status mode_factor(const Plan& pl, const ModePlan& m, double* U, double* ei
     }
     if (eigvals) RBKI_TRY(copy_f64_cuda(m.refine ? m.lamr : m.eval, eigvals, m.R, st));
     if (info) RBKI_TRY(fill_i32_cuda(info + pl.N + m.n, m.gram ? 1 : 0, 1, st));
+    return RBKI_OK;
+}
+
+// Lockstep modes: whether the call's Krylov-path modes can run Algorithms 1-2 in lockstep with
+// one batched launch per FP64 stage (the batched eigensolver takes b <= 192; adaptive depth,
+// power iteration, sampling, refinement and the sequential reading have their own drivers).
+static bool lockstep_ok(const Plan& pl) {
+    const uint32_t own = RBKI_FLAG_ADAPTIVE_Q | RBKI_FLAG_POWER | RBKI_FLAG_REFINE_FP32 | RBKI_FLAG_SEQUENTIAL;
+    if (pl.flags & own) return false;
+    int krylov = 0;
+    for (int n = 0; n < pl.N; ++n) {
+        const ModePlan& m = pl.mode[n];
+        if (m.gram) continue;
+        if (m.sampled || m.b > 192) return false;
+        ++krylov;
+    }
+    return krylov >= 2;
+}
+
+// Algorithms 1-2 for every mode on one stream, stage by stage: the X passes per mode (the
+// tensor-core kernels take one tensor per launch), each FP64 stage (block orthonormalisation,
+// Z = Q^T P, the eigensolver, U = Q U~) as one batched launch for all Krylov-path modes.  The
+// batched kernels run each mode through the same device code and grids as the per-mode
+// calls, so the results equal the concurrent per-mode chains bit for bit; the modes' FP64
+// stages share launches instead of queueing on three streams.
+static rbki_status run_modes_lockstep(const Plan& pl, const rbki_tucker_out* out, cudaStream_t st) {
+    std::vector<const ModePlan*> K;
+    for (int n = 0; n < pl.N; ++n) {
+        const ModePlan& m = pl.mode[n];
+        if (m.gram) RBKI_TRY(mode_factor(pl, m, out->factors[n], out->eigvals[n], out->info, st));
+        else K.push_back(&m);
+    }
+    auto kept = [&](const ModePlan& m) { return out->info ? out->info + m.n : m.kept; };
+    for (const ModePlan* m : K) {
+        if (out->info) RBKI_TRY(fill_i32_cuda(out->info + m->n, 0, 1, st));
+        RBKI_TRY(sketch_mode(pl, *m, st));
+    }
+    auto orth2 = [&](int j) -> rbki_status {
+        std::vector<OrthItem> oi;
+        for (const ModePlan* m : K)
+            oi.push_back(OrthItem{m->Qall, m->b, m->I, j * m->S, m->S, m->small, nullptr});
+        RBKI_TRY(orth_pass_batched(oi.data(), (int)oi.size(), TAU_DEFLATE, st));
+        for (size_t k = 0; k < K.size(); ++k) oi[k].kept = kept(*K[k]);
+        return orth_pass_batched(oi.data(), (int)oi.size(), TAU_DEFLATE, st);
+    };
+    RBKI_TRY(orth2(0));
+    const int q = K[0]->q;
+    for (int j = 0; j <= q; ++j) {
+        for (const ModePlan* m : K)
+            RBKI_TRY(krylov_step(pl, *m, m->Qall + j * m->S, m->b, m->S, m->Pall + j * m->S, m->b,
+                                 j < q ? m->Qall + (j + 1) * m->S : nullptr, m->b, st));
+        if (j < q) RBKI_TRY(orth2(j + 1));
+    }
+    std::vector<AtbItem> ab;
+    std::vector<EigItem> ei;
+    std::vector<FormItem> fi;
+    for (const ModePlan* m : K) {
+        ab.push_back(AtbItem{m->Qall, m->b, m->b, m->Pall, m->b, m->b, m->I, m->part, m->Z, m->b});
+        ei.push_back(EigItem{m->Z, m->b, m->R, m->eval, m->evec, m->syev_ws});
+        fi.push_back(FormItem{m->Qall, m->b, m->I, m->evec, m->b, m->R, m->R, out->factors[m->n]});
+    }
+    RBKI_TRY(atb_batched(ab.data(), (int)ab.size(), st));
+    for (const ModePlan* m : K) RBKI_TRY(symmetrize_cuda(m->Z, m->b, st));
+    RBKI_TRY(syev_top_batched(ei.data(), (int)ei.size(), st));
+    RBKI_TRY(form_factor_batched(fi.data(), (int)fi.size(), st));
+    for (const ModePlan* m : K) {
+        if (out->eigvals[m->n]) RBKI_TRY(copy_f64_cuda(m->eval, out->eigvals[m->n], m->R, st));
+        if (out->info) RBKI_TRY(fill_i32_cuda(out->info + pl.N + m->n, 0, 1, st));
+    }
     return RBKI_OK;
 }
 
@@ -891,6 +966,8 @@ rbki_status run_tucker(Plan& pl, const rbki_tucker_out* out, cudaStream_t st, co
         }
         cudaEventDestroy(ev);
         if (rs < 0) return rs;
+    } else if (lockstep_ok(pl)) {
+        RBKI_TRY(run_modes_lockstep(pl, out, st));
     } else if (concurrent) {
         cudaStream_t ms[RBKI_MAX_ORDER];
         if (mode_streams) {
