@@ -38,7 +38,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["tucker512", "tucker64", "video", "htr", "serve", "waves"],
                     default="tucker512")
-    ap.add_argument("--inflight", type=int, default=3,
+    ap.add_argument("--inflight", type=int, default=8,
                     help="decompositions in flight on separate streams (throughput mode); 1 = one at a time")
     ap.add_argument("--requests", type=int, default=4096, help="served stream length (--workload serve)")
     ap.add_argument("--slots", type=int, default=16, help="server slots (--workload serve)")

@@ -592,9 +592,29 @@ static rbki_status run_modes_lockstep(const Plan& pl, const rbki_tucker_out* out
         else K.push_back(&m);
     }
     auto kept = [&](const ModePlan& m) { return out->info ? out->info + m.n : m.kept; };
-    for (const ModePlan* m : K) {
-        if (out->info) RBKI_TRY(fill_i32_cuda(out->info + m->n, 0, 1, st));
-        RBKI_TRY(sketch_mode(pl, *m, st));
+    const bool f16 = pl.stream_dtype == RBKI_F16;
+    // Algorithm 1 steps 1-2: the tensor-core modes' Omega images and reductions batched
+    {
+        std::vector<tc::OmegaItem> om;
+        std::vector<tc::ReduceItem> rd;
+        for (const ModePlan* m : K) {
+            if (out->info) RBKI_TRY(fill_i32_cuda(out->info + m->n, 0, 1, st));
+            if (m->tc || m->tc2) om.push_back(tc::OmegaItem{pl.seed, m->n, mode_view(pl, *m), m->S, m->N, pl.split, m->omg});
+        }
+        RBKI_TRY(tc::omega_images_batched(om.data(), (int)om.size(), st));
+        for (const ModePlan* m : K) {
+            if (!(m->tc || m->tc2)) {
+                RBKI_TRY(sketch_mode(pl, *m, st));
+                continue;
+            }
+            int tok = prof_begin(RBKI_PROF_SKETCH, st);
+            RBKI_TRY(tc::stream_tc(tc::SKETCH, mode_view(pl, *m), m->N, m->S, pl.split, nullptr, m->omg, m->tpart,
+                                   nullptr, pl.err, st));
+            prof_end(tok, st);
+            rd.push_back(tc::ReduceItem{m->tpart, m->tgrid, m->I, m->N, m->S, pl.split, m->Qall, m->b, nullptr, 0,
+                                        pl.err});
+        }
+        RBKI_TRY(tc::reduce_parts_batched(rd.data(), (int)rd.size(), st));
     }
     auto orth2 = [&](int j) -> rbki_status {
         std::vector<OrthItem> oi;
@@ -607,9 +627,32 @@ static rbki_status run_modes_lockstep(const Plan& pl, const rbki_tucker_out* out
     RBKI_TRY(orth2(0));
     const int q = K[0]->q;
     for (int j = 0; j <= q; ++j) {
+        // P_j = X_(n) (X_(n)^T Q_j): single-pass tensor-core modes share the Q-image and
+        // reduction launches; two-pass and CUDA-core modes take krylov_step as they are
+        std::vector<tc::SkinnyItem> im;
+        std::vector<tc::ReduceItem> rd;
         for (const ModePlan* m : K)
-            RBKI_TRY(krylov_step(pl, *m, m->Qall + j * m->S, m->b, m->S, m->Pall + j * m->S, m->b,
-                                 j < q ? m->Qall + (j + 1) * m->S : nullptr, m->b, st));
+            if (m->tc && !m->tc2)
+                im.push_back(tc::SkinnyItem{m->Qall + j * m->S, m->b, m->I, m->S, m->N, pl.split ? 1 : 0, f16,
+                                            m->qimg});
+        RBKI_TRY(tc::skinny_image_batched(im.data(), (int)im.size(), st));
+        for (const ModePlan* m : K) {
+            double* P = m->Pall + j * m->S;
+            double* Qn = j < q ? m->Qall + (j + 1) * m->S : nullptr;
+            if (!(m->tc && !m->tc2)) {
+                RBKI_TRY(krylov_step(pl, *m, m->Qall + j * m->S, m->b, m->S, P, m->b, Qn, m->b, st));
+                continue;
+            }
+            const View v = mode_view(pl, *m);
+            int tok = prof_begin(RBKI_PROF_KRYLOV, st);
+            if (m->kp) RBKI_TRY(tc::krylov_tc(v, m->N, m->S, pl.split, m->qimg, m->tpart, pl.err, st));
+            else RBKI_TRY(tc::stream_tc(tc::KRYLOV, v, m->N, m->S, pl.split, m->qimg, nullptr, m->tpart, nullptr,
+                                        pl.err, st));
+            prof_end(tok, st);
+            rd.push_back(tc::ReduceItem{m->tpart, m->kp ? m->kgrid : m->tgrid, m->I, m->N, m->S, pl.split, P, m->b,
+                                        Qn, m->b, pl.err});
+        }
+        RBKI_TRY(tc::reduce_parts_batched(rd.data(), (int)rd.size(), st));
         if (j < q) RBKI_TRY(orth2(j + 1));
     }
     std::vector<AtbItem> ab;
@@ -624,11 +667,12 @@ static rbki_status run_modes_lockstep(const Plan& pl, const rbki_tucker_out* out
     for (const ModePlan* m : K) RBKI_TRY(symmetrize_cuda(m->Z, m->b, st));
     RBKI_TRY(syev_top_batched(ei.data(), (int)ei.size(), st));
     RBKI_TRY(form_factor_batched(fi.data(), (int)fi.size(), st));
+    std::vector<CopyItem> ci;
     for (const ModePlan* m : K) {
-        if (out->eigvals[m->n]) RBKI_TRY(copy_f64_cuda(m->eval, out->eigvals[m->n], m->R, st));
+        if (out->eigvals[m->n]) ci.push_back(CopyItem{m->eval, out->eigvals[m->n], m->R});
         if (out->info) RBKI_TRY(fill_i32_cuda(out->info + pl.N + m->n, 0, 1, st));
     }
-    return RBKI_OK;
+    return copy_f64_batched(ci.data(), (int)ci.size(), st);
 }
 
 // Adaptive Krylov depth (RBKI_FLAG_ADAPTIVE_Q): the Krylov-path modes advance block by

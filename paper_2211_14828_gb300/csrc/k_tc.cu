@@ -313,9 +313,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_stream_tc(const __grid_constant
 // element (i, n) at (i/8)*(N/8)*128 + (n/8)*128 + (i%8)*16 + (n%8)*2; rows padded to
 // rows_pad; columns n < S hold hi (or the value), N/2 <= n < N/2 + S the lo part when
 // split == 1 (S <= N/2); split == 2 puts the lo parts alone in columns n < S.
-__global__ void k_skinny_image(const double* __restrict__ M, int64_t ldm, int64_t rows, int S,
-                               int64_t rows_pad, int N, int split, int fp16, uint16_t* __restrict__ img) {
-    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void skinny_image_dev(const double* __restrict__ M, int64_t ldm, int64_t rows, int S,
+                                                 int64_t rows_pad, int N, int split, int fp16, uint16_t* __restrict__ img, int bx) {
+    int64_t e = (int64_t)bx * blockDim.x + threadIdx.x;
     if (e >= rows_pad * N) return;
     int64_t i = e / N;
     int n = (int)(e % N);
@@ -334,17 +334,43 @@ __global__ void k_skinny_image(const double* __restrict__ M, int64_t ldm, int64_
     img[off] = bits;
 }
 
+__global__ void k_skinny_image(const double* __restrict__ M, int64_t ldm, int64_t rows, int S,
+                               int64_t rows_pad, int N, int split, int fp16, uint16_t* __restrict__ img) {
+    skinny_image_dev(M, ldm, rows, S, rows_pad, N, split, fp16, img, (int)blockIdx.x);
+}
+
+struct skinny_image_rec {
+    const double* M;
+    int64_t ldm;
+    int64_t rows;
+    int S;
+    int64_t rows_pad;
+    int N;
+    int split;
+    int fp16;
+    uint16_t* img;
+    int gx, gy, gz;
+};
+
+__global__ void k_skinny_image_b(const __grid_constant__ BPack<skinny_image_rec> p) {
+    const skinny_image_rec& r = p.r[blockIdx.y];
+    int bx, by, bz;
+    if (!bat_block(r, bx, by, bz)) return;
+    skinny_image_dev(r.M, r.ldm, r.rows, r.S, r.rows_pad, r.N, r.split, r.fp16, r.img, bx);
+}
+
+
 // Per-tile Omega images for SKETCH: tile t covers 128 unfolding columns; element (c, n) of
 // tile t at t*128*N + (n/8)*1024 + c*8 + n%8 (elements).  Columns outside the tensor are 0.
 // With `split`, image column n < S holds the hi part of Omega's column n and N/2 + s the lo
 // part of column s.
-__global__ void __launch_bounds__(256) k_omega_images(uint64_t seed, int mode, int64_t A, int64_t C, int ifast,
-                                                      int64_t ctiles, int64_t tiles, int S, int N, int split,
-                                                      int fp16, uint16_t* __restrict__ img) {
+__device__ __forceinline__ void omega_images_dev(uint64_t seed, int mode, int64_t A, int64_t C, int ifast,
+                                                 int64_t ctiles, int64_t tiles, int S, int N, int split,
+                                                 int fp16, uint16_t* __restrict__ img, int bx) {
     // one thread per (tile, column c, group of 8 image columns): the group is written as one
     // 16-byte vector, zeros included, so the image needs no clearing beforehand
     const int G = N / 8;
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t e = (int64_t)bx * blockDim.x + threadIdx.x;
     if (e >= tiles * 128 * G) return;
     const int g = (int)(e % G);
     const int64_t tc_ = e / G;
@@ -389,18 +415,48 @@ __global__ void __launch_bounds__(256) k_omega_images(uint64_t seed, int mode, i
     *reinterpret_cast<uint4*>(img + (size_t)t * 128 * N + (size_t)g * 1024 + c * 8) = w;
 }
 
+__global__ void __launch_bounds__(256) k_omega_images(uint64_t seed, int mode, int64_t A, int64_t C, int ifast,
+                                                      int64_t ctiles, int64_t tiles, int S, int N, int split,
+                                                      int fp16, uint16_t* __restrict__ img) {
+    omega_images_dev(seed, mode, A, C, ifast, ctiles, tiles, S, N, split, fp16, img, (int)blockIdx.x);
+}
+
+struct omega_images_rec {
+    uint64_t seed;
+    int mode;
+    int64_t A;
+    int64_t C;
+    int ifast;
+    int64_t ctiles;
+    int64_t tiles;
+    int S;
+    int N;
+    int split;
+    int fp16;
+    uint16_t* img;
+    int gx, gy, gz;
+};
+
+__global__ void __launch_bounds__(256) k_omega_images_b(const __grid_constant__ BPack<omega_images_rec> p) {
+    const omega_images_rec& r = p.r[blockIdx.y];
+    int bx, by, bz;
+    if (!bat_block(r, bx, by, bz)) return;
+    omega_images_dev(r.seed, r.mode, r.A, r.C, r.ifast, r.ctiles, r.tiles, r.S, r.N, r.split, r.fp16, r.img, bx);
+}
+
+
 // out[i*ld + s] = sum_b (part[b][i][s] + split * part[b][i][N/2 + s]), FP64, fixed order:
 // 32 outputs per CTA; warp w sums partials b = w, w+8, ...; warps combined in order.
 // When the producing kernel reported an expired wait (*err != 0) its partials are
 // incomplete, and every output is NaN instead, so the result cannot pass for a valid one.
 constexpr int RED_WARPS = 8;
-__global__ void __launch_bounds__(32 * RED_WARPS) k_reduce_tc(const float* __restrict__ part, int nb, int64_t I,
-                                                             int N, int Sh, int split, double* __restrict__ out,
-                                                             int64_t ld, double* __restrict__ out2, int64_t ld2,
-                                                             const int* __restrict__ err) {
+__device__ __forceinline__ void reduce_tc_dev(const float* __restrict__ part, int nb, int64_t I,
+                                              int N, int Sh, int split, double* __restrict__ out,
+                                              int64_t ld, double* __restrict__ out2, int64_t ld2,
+                                              const int* __restrict__ err, int bx) {
     __shared__ double acc_sh[RED_WARPS][33];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t e = (int64_t)blockIdx.x * 32 + lane;
+    const int64_t e = (int64_t)bx * 32 + lane;
     const int64_t tot = I * Sh;
     double acc = 0.0;
     if (e < tot) {
@@ -424,6 +480,36 @@ __global__ void __launch_bounds__(32 * RED_WARPS) k_reduce_tc(const float* __res
         if (out2) out2[i * ld2 + s] = t;
     }
 }
+
+__global__ void __launch_bounds__(32 * RED_WARPS) k_reduce_tc(const float* __restrict__ part, int nb, int64_t I,
+                                                             int N, int Sh, int split, double* __restrict__ out,
+                                                             int64_t ld, double* __restrict__ out2, int64_t ld2,
+                                                             const int* __restrict__ err) {
+    reduce_tc_dev(part, nb, I, N, Sh, split, out, ld, out2, ld2, err, (int)blockIdx.x);
+}
+
+struct reduce_tc_rec {
+    const float* part;
+    int nb;
+    int64_t I;
+    int N;
+    int Sh;
+    int split;
+    double* out;
+    int64_t ld;
+    double* out2;
+    int64_t ld2;
+    const int* err;
+    int gx, gy, gz;
+};
+
+__global__ void __launch_bounds__(32 * RED_WARPS) k_reduce_tc_b(const __grid_constant__ BPack<reduce_tc_rec> p) {
+    const reduce_tc_rec& r = p.r[blockIdx.y];
+    int bx, by, bz;
+    if (!bat_block(r, bx, by, bz)) return;
+    reduce_tc_dev(r.part, r.nb, r.I, r.N, r.Sh, r.split, r.out, r.ld, r.out2, r.ld2, r.err, bx);
+}
+
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -584,6 +670,41 @@ rbki_status reduce_parts(const float* part, int nb, int64_t I, int N, int Sh, bo
                                                                   ld2, err);
     RBKI_LAUNCH_CHECK("k_reduce_tc");
     return RBKI_OK;
+}
+
+// ---- batched forms (one launch for the items of a lockstep stage; see bat_launch) ----
+rbki_status skinny_image_batched(const SkinnyItem* it, int n, cudaStream_t st) {
+    std::vector<skinny_image_rec> r;
+    for (int k = 0; k < n; ++k) {
+        const SkinnyItem& a = it[k];
+        const int64_t rows_pad = cdiv(a.rows, 128) * 128;
+        r.push_back(skinny_image_rec{a.M, a.ldm, a.rows, a.S, rows_pad, a.N, a.split, a.fp16 ? 1 : 0,
+                                     (uint16_t*)a.img, (int)cdiv(rows_pad * a.N, 256), 1, 1});
+    }
+    return bat_launch(k_skinny_image_b, r.data(), (int)r.size(), 256, 0, st, "k_skinny_image_b");
+}
+
+rbki_status omega_images_batched(const OmegaItem* it, int n, cudaStream_t st) {
+    std::vector<omega_images_rec> r;
+    for (int k = 0; k < n; ++k) {
+        const OmegaItem& a = it[k];
+        const bool ifast = a.v.C == 1;
+        const int64_t ctiles = ifast ? 1 : cdiv(a.v.C, 128), tiles = num_tiles(a.v);
+        r.push_back(omega_images_rec{a.seed, a.mode, a.v.A, a.v.C, ifast ? 1 : 0, ctiles, tiles, a.S, a.N,
+                                     a.split ? 1 : 0, a.v.dtype == RBKI_F16 ? 1 : 0, (uint16_t*)a.img,
+                                     (int)cdiv(tiles * 128 * (a.N / 8), 256), 1, 1});
+    }
+    return bat_launch(k_omega_images_b, r.data(), (int)r.size(), 256, 0, st, "k_omega_images_b");
+}
+
+rbki_status reduce_parts_batched(const ReduceItem* it, int n, cudaStream_t st) {
+    std::vector<reduce_tc_rec> r;
+    for (int k = 0; k < n; ++k) {
+        const ReduceItem& a = it[k];
+        r.push_back(reduce_tc_rec{a.part, a.nb, a.I, a.N, a.Sh, a.split ? 1 : 0, a.out, a.ld, a.out2, a.ld2, a.err,
+                                  (int)cdiv(a.I * a.Sh, 32), 1, 1});
+    }
+    return bat_launch(k_reduce_tc_b, r.data(), (int)r.size(), 32 * RED_WARPS, 0, st, "k_reduce_tc_b");
 }
 
 }  // namespace tc

@@ -62,5 +62,20 @@ rbki_status krylov_tc(const View& v, int N, int Sh, bool split, const void* qimg
 rbki_status reduce_parts(const float* part, int nb, int64_t I, int N, int Sh, bool split, double* out,
                          int64_t ld, double* out2, int64_t ld2, const int* err, cudaStream_t st);
 
+// batched forms of the operand-image and reduction launches (one launch for many items)
+struct SkinnyItem {
+    const double* M; int64_t ldm, rows; int S, N, split; bool fp16; void* img;
+};
+rbki_status skinny_image_batched(const SkinnyItem* it, int n, cudaStream_t st);
+struct OmegaItem {
+    uint64_t seed; int mode; View v; int S, N; bool split; void* img;
+};
+rbki_status omega_images_batched(const OmegaItem* it, int n, cudaStream_t st);
+struct ReduceItem {
+    const float* part; int nb; int64_t I; int N, Sh; bool split;
+    double* out; int64_t ld; double* out2; int64_t ld2; const int* err;
+};
+rbki_status reduce_parts_batched(const ReduceItem* it, int n, cudaStream_t st);
+
 }  // namespace tc
 }  // namespace rbki
