@@ -433,6 +433,33 @@ def run_ours(args):
     norms = out["norms"].cpu().numpy()
     rel_err = float(np.sqrt(max(norms[0] - norms[1], 0.0) / norms[0]))
 
+    # the same Krylov-step kernel timed by itself (nothing else on the GPU): one mode's step
+    # P = X_(0) (X_(0)^T Q) through the public rbki_krylov_product on the BF16 tensor
+    roof_alone = None
+    if roof is not None and prec == "bf16" and not args.sequential and args.omega <= 0:
+        xb = x.to(torch.bfloat16)
+        s_w = min(wl.ranks[0] + wl.p, dims[0])
+        qm = torch.linalg.qr(torch.randn(dims[0], s_w, dtype=torch.float64, device="cuda"))[0].contiguous()
+        for _ in range(3):
+            rb.rbki_krylov_product(xb, 0, qm, prec="bf16")
+        torch.cuda.synchronize()
+        rb.rbki_profile_reset()
+        rb.rbki_profile_enable(True)
+        for _ in range(10):
+            rb.rbki_krylov_product(xb, 0, qm, prec="bf16")
+        torch.cuda.synchronize()
+        rb.rbki_profile_enable(False)
+        ac, ams = rb.rbki_profile_read(rb.PROF_KRYLOV)
+        rb.rbki_profile_reset()
+        if ac:
+            a_ms = ams / ac
+            a_gbs = numel * ELEM_BYTES / (a_ms * 1e-3) / 1e9
+            roof_alone = {"bound": "hbm", "achieved": round(a_gbs, 1), "peak": peak, "unit": "GB/s",
+                          "frac": round(a_gbs / peak, 4), "kernel": "krylov_step", "avg_launch_ms": round(a_ms, 4),
+                          "launches": ac, "peak_kind": peak_kind,
+                          "note": "the same kernel timed alone after the timed region (mode 0 of the same tensor)"}
+        del xb
+
     e2e = None
     if not args.no_e2e:
         # through the public call with host buffers (RBKI_FLAG_HOST_IO): every step copies X
@@ -560,7 +587,8 @@ def run_ours(args):
                        "passes_per_step": passes, "krylov_steps_per_step": krylov_steps,
                        "bytes_per_step": step_bytes, "l2": "inputs larger than L2 (no flush)",
                        "parallelism": f"replicas x{world}"},
-            "roofline": roof, "breakdown": breakdown, "rel_err": rel_err, "fp64_compare": fp64_cmp,
+            "roofline": roof, "roofline_alone": roof_alone, "breakdown": breakdown, "rel_err": rel_err,
+            "fp64_compare": fp64_cmp,
             "sequential_compare": seq_cmp, "serve_compare": serve_cmp,
             "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "cpu_baseline": cpu,
         }
