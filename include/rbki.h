@@ -67,7 +67,11 @@ enum {
     RBKI_FLAG_HOST_IO = 1u,        /* X and outputs in host memory (end-to-end call) */
     RBKI_FLAG_SPLIT = 2u,          /* mixed path: carry the skinny operands (Q, Y, Omega, U) as
                                       hi + lo BF16 pairs: ~FP32-accurate products, 2x MMA work */
-    RBKI_FLAG_SERIAL_MODES = 4u,   /* run modes one after another on `stream` */
+    RBKI_FLAG_SERIAL_MODES = 4u,   /* run modes one after another on `stream`, each through the
+                                      per-mode kernels.  Without it, two or more Krylov-path modes
+                                      with b <= 192 run in lockstep (each FP64 stage one batched
+                                      launch for all modes), with the same results bit for bit;
+                                      otherwise each mode runs on a stream of its own */
     RBKI_FLAG_SEQUENTIAL = 8u,     /* sequentially truncated reading of Algorithm 2 (ST-HOSVD):
                                       mode n is sketched on Y_n = X x_1 U^(1)T .. x_{n-1} U^(n-1)T,
                                       modes in the order 1..N; the default (HOSVD reading)

@@ -564,9 +564,11 @@ rbki_status mode_factor(const Plan& pl, const ModePlan& m, double* U, double* ei
 
 // Lockstep modes: whether the call's Krylov-path modes can run Algorithms 1-2 in lockstep with
 // one batched launch per FP64 stage (the batched eigensolver takes b <= 192; adaptive depth,
-// power iteration, sampling, refinement and the sequential reading have their own drivers).
+// power iteration, sampling, refinement and the sequential reading have their own drivers;
+// RBKI_FLAG_SERIAL_MODES asks for the per-mode kernels, one mode after another).
 static bool lockstep_ok(const Plan& pl) {
-    const uint32_t own = RBKI_FLAG_ADAPTIVE_Q | RBKI_FLAG_POWER | RBKI_FLAG_REFINE_FP32 | RBKI_FLAG_SEQUENTIAL;
+    const uint32_t own = RBKI_FLAG_ADAPTIVE_Q | RBKI_FLAG_POWER | RBKI_FLAG_REFINE_FP32 | RBKI_FLAG_SEQUENTIAL |
+                         RBKI_FLAG_SERIAL_MODES;
     if (pl.flags & own) return false;
     int krylov = 0;
     for (int n = 0; n < pl.N; ++n) {
@@ -586,6 +588,20 @@ static bool lockstep_ok(const Plan& pl) {
 // stages share launches instead of queueing on three streams.
 static rbki_status run_modes_lockstep(const Plan& pl, const rbki_tucker_out* out, cudaStream_t st) {
     std::vector<const ModePlan*> K;
+    // one launch for the scalar outputs known up front (q_used; the Krylov-path modes' kept
+    // counters and path words) and the orthonormalisation tickets
+    std::vector<FillItem> fills;
+    for (int n = 0; n < pl.N; ++n) {
+        const ModePlan& m = pl.mode[n];
+        if (out->q_used) fills.push_back(FillItem{out->q_used + n, m.gram ? 0 : m.q});
+        if (m.gram) continue;
+        if (out->info) {
+            fills.push_back(FillItem{out->info + n, 0});
+            fills.push_back(FillItem{out->info + pl.N + n, 0});
+        }
+        fills.push_back(FillItem{orth_ticket(m.small), 0});
+    }
+    RBKI_TRY(fill_i32_batched(fills.data(), (int)fills.size(), st));
     for (int n = 0; n < pl.N; ++n) {
         const ModePlan& m = pl.mode[n];
         if (m.gram) RBKI_TRY(mode_factor(pl, m, out->factors[n], out->eigvals[n], out->info, st));
@@ -598,7 +614,6 @@ static rbki_status run_modes_lockstep(const Plan& pl, const rbki_tucker_out* out
         std::vector<tc::OmegaItem> om;
         std::vector<tc::ReduceItem> rd;
         for (const ModePlan* m : K) {
-            if (out->info) RBKI_TRY(fill_i32_cuda(out->info + m->n, 0, 1, st));
             if (m->tc || m->tc2) om.push_back(tc::OmegaItem{pl.seed, m->n, mode_view(pl, *m), m->S, m->N, pl.split, m->omg});
         }
         RBKI_TRY(tc::omega_images_batched(om.data(), (int)om.size(), st));
@@ -659,19 +674,17 @@ static rbki_status run_modes_lockstep(const Plan& pl, const rbki_tucker_out* out
     std::vector<EigItem> ei;
     std::vector<FormItem> fi;
     for (const ModePlan* m : K) {
-        ab.push_back(AtbItem{m->Qall, m->b, m->b, m->Pall, m->b, m->b, m->I, m->part, m->Z, m->b});
+        // Z = Q^T P with its symmetrisation (Z + Z^T) / 2 folded into the reduction
+        ab.push_back(AtbItem{m->Qall, m->b, m->b, m->Pall, m->b, m->b, m->I, m->part, m->Z, m->b, 1});
         ei.push_back(EigItem{m->Z, m->b, m->R, m->eval, m->evec, m->syev_ws});
         fi.push_back(FormItem{m->Qall, m->b, m->I, m->evec, m->b, m->R, m->R, out->factors[m->n]});
     }
     RBKI_TRY(atb_batched(ab.data(), (int)ab.size(), st));
-    for (const ModePlan* m : K) RBKI_TRY(symmetrize_cuda(m->Z, m->b, st));
     RBKI_TRY(syev_top_batched(ei.data(), (int)ei.size(), st));
     RBKI_TRY(form_factor_batched(fi.data(), (int)fi.size(), st));
     std::vector<CopyItem> ci;
-    for (const ModePlan* m : K) {
+    for (const ModePlan* m : K)
         if (out->eigvals[m->n]) ci.push_back(CopyItem{m->eval, out->eigvals[m->n], m->R});
-        if (out->info) RBKI_TRY(fill_i32_cuda(out->info + pl.N + m->n, 0, 1, st));
-    }
     return copy_f64_batched(ci.data(), (int)ci.size(), st);
 }
 
@@ -987,6 +1000,7 @@ rbki_status run_tucker(Plan& pl, const rbki_tucker_out* out, cudaStream_t st, co
     }
     prof_end(tok, st);
     const bool concurrent = pl.N > 1 && !(pl.flags & RBKI_FLAG_SERIAL_MODES);
+    const bool lockstep = !(pl.flags & RBKI_FLAG_ADAPTIVE_Q) && lockstep_ok(pl);
     int chain_from = 0;   // core-chain steps already enqueued on a mode stream
     int32_t q_used[RBKI_MAX_ORDER];
     for (int n = 0; n < pl.N; ++n) q_used[n] = pl.mode[n].gram ? 0 : pl.mode[n].q;
@@ -1010,7 +1024,7 @@ rbki_status run_tucker(Plan& pl, const rbki_tucker_out* out, cudaStream_t st, co
         }
         cudaEventDestroy(ev);
         if (rs < 0) return rs;
-    } else if (lockstep_ok(pl)) {
+    } else if (lockstep) {
         RBKI_TRY(run_modes_lockstep(pl, out, st));
     } else if (concurrent) {
         cudaStream_t ms[RBKI_MAX_ORDER];
@@ -1042,7 +1056,7 @@ rbki_status run_tucker(Plan& pl, const rbki_tucker_out* out, cudaStream_t st, co
         for (int n = 0; n < pl.N; ++n)
             RBKI_TRY(mode_factor(pl, pl.mode[n], out->factors[n], out->eigvals[n], out->info, st));
     }
-    if (out->q_used)
+    if (out->q_used && !lockstep)   // the lockstep driver writes q_used with its first launch
         for (int n = 0; n < pl.N; ++n) RBKI_TRY(fill_i32_cuda(out->q_used + n, q_used[n], 1, st));
     RBKI_TRY(core_chain(pl, out->factors, out->core, st, chain_from));
     RBKI_TRY(sumsq_cuda(out->core, RBKI_F64, pl.ranks_numel, pl.scal + 64, norms + 1, st));

@@ -82,12 +82,9 @@ __global__ void __launch_bounds__(256) k_atb_part_b(const __grid_constant__ BPac
 }
 
 
-__device__ __forceinline__ void atb_reduce_dev(const double* __restrict__ part, int nchunk, int ma, int mb,
-                                               double* __restrict__ out, int64_t ldo, int bx) {
-    int e = bx * blockDim.x + threadIdx.x;
-    if (e >= ma * mb) return;
-    // four independent loads in flight per step; fixed summation order
-    const int64_t stride = (int64_t)ma * mb;
+// sum over the chunks of element e of the partials: four independent loads in flight per
+// step; fixed summation order
+__device__ __forceinline__ double atb_sum_elem(const double* __restrict__ part, int nchunk, int64_t stride, int e) {
     double acc = 0.0;
     int c = 0;
     for (; c + 3 < nchunk; c += 4) {
@@ -96,7 +93,20 @@ __device__ __forceinline__ void atb_reduce_dev(const double* __restrict__ part, 
         acc += (v0 + v1) + (v2 + v3);
     }
     for (; c < nchunk; ++c) acc += part[c * stride + e];
-    out[(int64_t)(e / mb) * ldo + e % mb] = acc;
+    return acc;
+}
+
+// out = sum of the partials; sym (ma == mb): out[k][l] = (sum_kl + sum_lk) / 2, the reduction
+// followed by the symmetrisation (Z + Z^T) / 2 of k_symmetrize, bit for bit
+__device__ __forceinline__ void atb_reduce_dev(const double* __restrict__ part, int nchunk, int ma, int mb,
+                                               double* __restrict__ out, int64_t ldo, int bx, int sym = 0) {
+    int e = bx * blockDim.x + threadIdx.x;
+    if (e >= ma * mb) return;
+    const int64_t stride = (int64_t)ma * mb;
+    const int k = e / mb, l = e % mb;
+    double acc = atb_sum_elem(part, nchunk, stride, e);
+    if (sym && k != l) acc = 0.5 * (acc + atb_sum_elem(part, nchunk, stride, l * mb + k));
+    out[(int64_t)k * ldo + l] = acc;
 }
 
 __global__ void k_atb_reduce(const double* __restrict__ part, int nchunk, int ma, int mb,
@@ -111,6 +121,7 @@ struct atb_reduce_rec {
     int mb;
     double* out;
     int64_t ldo;
+    int sym;
     int gx, gy, gz;
 };
 
@@ -118,16 +129,14 @@ __global__ void k_atb_reduce_b(const __grid_constant__ BPack<atb_reduce_rec> p) 
     const atb_reduce_rec& r = p.r[blockIdx.y];
     int bx, by, bz;
     if (!bat_block(r, bx, by, bz)) return;
-    atb_reduce_dev(r.part, r.nchunk, r.ma, r.mb, r.out, r.ldo, bx);
+    atb_reduce_dev(r.part, r.nchunk, r.ma, r.mb, r.out, r.ldo, bx, r.sym);
 }
 
 
 // G'[k][l] = M[m+k][l] - sum_{r<m} M[r][k] M[r][l]  (Pythagorean Gram of the projected block)
 // nu2[k] = M[m+k][k] (squared column norms before projection).  One CTA per column l.
-__device__ __forceinline__ void gprime_dev(const double* __restrict__ M, int m, int S, double* __restrict__ Gp,
-                                           double* __restrict__ nu2, int bx) {
-    int l = bx, k = threadIdx.x;
-    if (k >= S) return;
+__device__ __forceinline__ void gprime_elem(const double* __restrict__ M, int m, int S, double* __restrict__ Gp,
+                                            double* __restrict__ nu2, int k, int l) {
     double g = M[(int64_t)(m + k) * S + l];
     double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
     int r = 0;
@@ -140,6 +149,11 @@ __device__ __forceinline__ void gprime_dev(const double* __restrict__ M, int m, 
     for (; r < m; ++r) a0 += M[(int64_t)r * S + k] * M[(int64_t)r * S + l];
     Gp[k * S + l] = g - ((a0 + a1) + (a2 + a3));
     if (k == l) nu2[k] = g;
+}
+
+__device__ __forceinline__ void gprime_dev(const double* __restrict__ M, int m, int S, double* __restrict__ Gp,
+                                           double* __restrict__ nu2, int bx) {
+    if ((int)threadIdx.x < S) gprime_elem(M, m, S, Gp, nu2, (int)threadIdx.x, bx);
 }
 
 __global__ void k_gprime(const double* __restrict__ M, int m, int S, double* __restrict__ Gp,
@@ -278,6 +292,54 @@ __global__ void k_chol_deflate_b(const __grid_constant__ BPack<chol_deflate_rec>
     chol_deflate_dev(r.Gp, r.nu2, r.S, r.tau, r.Rinv, r.kept);
 }
 
+
+// The head of one orthonormalisation pass in one launch: every CTA computes its tile of the
+// chunk partials of M = [Q_{<m} Q_m]^T Q_m (k_atb_part); the CTA that finishes last (a ticket
+// counter, no CTA waits for another) sums the partials (k_atb_reduce), forms the Pythagorean
+// Gram G' and nu2 (k_gprime) and factors it with deflation (k_chol_deflate), with the same
+// arithmetic in the same order as those three kernels, then resets the ticket to 0.  The
+// ticket must be 0 before the first pass.
+struct orth_head_rec {
+    const double* Q;
+    int64_t ldq;
+    int m;
+    int S;
+    int64_t rows;
+    int64_t rows_per_chunk;
+    int nchunk;
+    double* part;
+    double* M;
+    double* Gp;
+    double* Rinv;
+    double* nu2;
+    double tau;
+    int32_t* kept;
+    int32_t* ticket;
+    int gx, gy, gz;
+};
+
+__global__ void __launch_bounds__(256) k_orth_head_b(const __grid_constant__ BPack<orth_head_rec> p) {
+    const orth_head_rec& r = p.r[blockIdx.y];
+    int bx, by, bz;
+    if (!bat_block(r, bx, by, bz)) return;
+    const int ma = r.m + r.S;
+    atb_part_dev(r.Q, r.ldq, ma, r.Q + r.m, r.ldq, r.S, r.rows, r.rows_per_chunk, r.part, bx, by, bz);
+    __shared__ int last;
+    __threadfence();                   // this CTA's partials before its ticket
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(r.ticket, 1) == r.gx * r.gy * r.gz - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();                   // every other CTA's partials are visible from here
+    const int mp = ma * r.S;
+    for (int e = threadIdx.x; e < mp; e += blockDim.x)
+        r.M[e] = atb_sum_elem(r.part, r.nchunk, (int64_t)mp, e);
+    __syncthreads();
+    for (int e = threadIdx.x; e < r.S * r.S; e += blockDim.x) gprime_elem(r.M, r.m, r.S, r.Gp, r.nu2, e % r.S, e / r.S);
+    __syncthreads();
+    chol_deflate_dev(r.Gp, r.nu2, r.S, r.tau, r.Rinv, r.kept);
+    if (threadIdx.x == 0) *r.ticket = 0;
+}
 
 // Q[i][m+s] = sum_t (Q[i][m+t] - sum_{r<m} Q[i][r] M[r][t]) Rinv[t][s]; ORTH_ROWS rows per CTA
 constexpr int ORTH_ROWS = 4;
@@ -471,6 +533,19 @@ __global__ void k_fill_i32(int32_t* d, int32_t v, int n) {
     if (e < n) d[e] = v;
 }
 
+struct fill_i32_rec {
+    int32_t* d;
+    int32_t v;
+    int gx, gy, gz;
+};
+
+__global__ void k_fill_i32_b(const __grid_constant__ BPack<fill_i32_rec> p) {
+    const fill_i32_rec& r = p.r[blockIdx.y];
+    int bx, by, bz;
+    if (!bat_block(r, bx, by, bz) || threadIdx.x) return;
+    *r.d = r.v;
+}
+
 }  // namespace
 
 int atb_nchunks(int64_t rows) {
@@ -490,16 +565,19 @@ rbki_status atb_cuda(const double* A, int64_t lda, int ma, const double* B, int6
     return RBKI_OK;
 }
 
+// scratch: [ticket (8 doubles)] [chunk partials] [M] [G'] [Rinv] [nu2]
 size_t orth_scratch_doubles(int64_t rows, int m, int S) {
     size_t mp = (size_t)(m + S) * S;
-    return (size_t)atb_nchunks(rows) * mp + mp + 2 * (size_t)S * S + S + 64;
+    return ORTH_TICKET_DOUBLES + (size_t)atb_nchunks(rows) * mp + mp + 2 * (size_t)S * S + S + 64;
 }
+
+int32_t* orth_ticket(double* scratch) { return reinterpret_cast<int32_t*>(scratch); }
 
 rbki_status orth_pass_cuda(double* Q, int64_t ldq, int64_t rows, int m, int S, double tau,
                            double* scratch, int32_t* kept, cudaStream_t st) {
     if (S > 128) return set_error(RBKI_E_UNSUPPORTED, "orth: block width > 128");
     size_t mp = (size_t)(m + S) * S;
-    double* part = scratch;
+    double* part = scratch + ORTH_TICKET_DOUBLES;
     double* M = part + (size_t)atb_nchunks(rows) * mp;
     double* Gp = M + mp;
     double* Rinv = Gp + (size_t)S * S;
@@ -552,18 +630,19 @@ rbki_status atb_batched(const AtbItem* it, int n, cudaStream_t st) {
         const int nch = atb_nchunks(a.rows);
         ap[k] = atb_part_rec{a.A, a.lda, a.ma, a.B, a.ldb, a.mb, a.rows, cdiv(a.rows, nch), a.part,
                              (int)cdiv(a.ma, AT_T), (int)cdiv(a.mb, AT_T), nch};
-        ar[k] = atb_reduce_rec{a.part, nch, a.ma, a.mb, a.out, a.ldo, (int)cdiv((int64_t)a.ma * a.mb, 256), 1, 1};
+        if (a.sym && a.ma != a.mb) return set_error(RBKI_E_INVAL, "atb_batched: symmetric output of a non-square product");
+        ar[k] = atb_reduce_rec{a.part, nch, a.ma, a.mb, a.out, a.ldo, a.sym, (int)cdiv((int64_t)a.ma * a.mb, 256), 1, 1};
     }
     RBKI_TRY(bat_launch(k_atb_part_b, ap.data(), n, 256, 0, st, "k_atb_part_b"));
     return bat_launch(k_atb_reduce_b, ar.data(), n, 256, 0, st, "k_atb_reduce_b");
 }
 
+// Two launches per pass: the fused head (partials, reduction, G', Cholesky with deflation)
+// and the update of the block; the same arithmetic as orth_pass_cuda's five kernels.  Each
+// item's ticket (orth_ticket(scratch)) must be 0 before the first pass.
 rbki_status orth_pass_batched(const OrthItem* it, int n, double tau, cudaStream_t st) {
     if (n <= 0) return RBKI_OK;
-    std::vector<atb_part_rec> ap(n);
-    std::vector<atb_reduce_rec> ar(n);
-    std::vector<gprime_rec> gp(n);
-    std::vector<chol_deflate_rec> cd(n);
+    std::vector<orth_head_rec> oh(n);
     std::vector<orth_apply_rec> oa(n);
     int smax = 0;
     for (int k = 0; k < n; ++k) {
@@ -572,26 +651,20 @@ rbki_status orth_pass_batched(const OrthItem* it, int n, double tau, cudaStream_
         const int S = o.S, ma = o.m + S;
         const size_t mp = (size_t)ma * S;
         const int nch = atb_nchunks(o.rows);
-        double* part = o.scratch;
+        double* part = o.scratch + ORTH_TICKET_DOUBLES;
         double* M = part + (size_t)nch * mp;
         double* Gp = M + mp;
         double* Rinv = Gp + (size_t)S * S;
         double* nu2 = Rinv + (size_t)S * S;
-        ap[k] = atb_part_rec{o.Q, o.ldq, ma, o.Q + o.m, o.ldq, S, o.rows, cdiv(o.rows, nch), part,
-                             (int)cdiv(ma, AT_T), (int)cdiv(S, AT_T), nch};
-        ar[k] = atb_reduce_rec{part, nch, ma, S, M, S, (int)cdiv((int64_t)ma * S, 256), 1, 1};
-        gp[k] = gprime_rec{M, o.m, S, Gp, nu2, S, 1, 1};
-        cd[k] = chol_deflate_rec{Gp, nu2, S, tau, Rinv, o.kept, 1, 1, 1};
+        oh[k] = orth_head_rec{o.Q, o.ldq, o.m, S, o.rows, cdiv(o.rows, nch), nch, part, M, Gp, Rinv, nu2, tau, o.kept,
+                              orth_ticket(o.scratch), (int)cdiv(ma, AT_T), (int)cdiv(S, AT_T), nch};
         oa[k] = orth_apply_rec{o.Q, o.ldq, o.rows, o.m, S, M, Rinv, (int)cdiv(o.rows, ORTH_ROWS), 1, 1};
         smax = std::max(smax, S);
     }
     const size_t sm = ((size_t)smax * smax + 2 * smax) * sizeof(double);
-    static const size_t cmax = max_dyn_smem(k_chol_deflate_b);   // thread-safe, once
-    if (sm > cmax) return set_error(RBKI_E_UNSUPPORTED, "orth: block too wide for shared memory");
-    RBKI_TRY(bat_launch(k_atb_part_b, ap.data(), n, 256, 0, st, "k_atb_part_b"));
-    RBKI_TRY(bat_launch(k_atb_reduce_b, ar.data(), n, 256, 0, st, "k_atb_reduce_b"));
-    RBKI_TRY(bat_launch(k_gprime_b, gp.data(), n, 128, 0, st, "k_gprime_b"));
-    RBKI_TRY(bat_launch(k_chol_deflate_b, cd.data(), n, 256, sm, st, "k_chol_deflate_b"));
+    static const size_t hmax = max_dyn_smem(k_orth_head_b);   // thread-safe, once
+    if (sm > hmax) return set_error(RBKI_E_UNSUPPORTED, "orth: block too wide for shared memory");
+    RBKI_TRY(bat_launch(k_orth_head_b, oh.data(), n, 256, sm, st, "k_orth_head_b"));
     return bat_launch(k_orth_apply_b, oa.data(), n, 32 * ORTH_ROWS, (size_t)ORTH_ROWS * smax * sizeof(double), st,
                       "k_orth_apply_b");
 }
@@ -607,6 +680,13 @@ rbki_status form_factor_batched(const FormItem* it, int n, cudaStream_t st) {
     }
     RBKI_TRY(bat_launch(k_form_u_b, fu.data(), n, 256, 0, st, "k_form_u_b"));
     return bat_launch(k_sign_fix_b, sf.data(), n, 256, 0, st, "k_sign_fix_b");
+}
+
+rbki_status fill_i32_batched(const FillItem* it, int n, cudaStream_t st) {
+    std::vector<fill_i32_rec> fr;
+    for (int k = 0; k < n; ++k)
+        if (it[k].dst) fr.push_back(fill_i32_rec{it[k].dst, it[k].v, 1, 1, 1});
+    return bat_launch(k_fill_i32_b, fr.data(), (int)fr.size(), 32, 0, st, "k_fill_i32_b");
 }
 
 rbki_status copy_f64_batched(const CopyItem* it, int n, cudaStream_t st) {

@@ -70,6 +70,10 @@ rbki_status atb_cuda(const double* A, int64_t lda, int ma, const double* B, int6
 rbki_status orth_pass_cuda(double* Q, int64_t ldq, int64_t rows, int m, int S, double tau,
                            double* scratch, int32_t* kept, cudaStream_t st);
 size_t orth_scratch_doubles(int64_t rows, int m, int S);
+// the first ORTH_TICKET_DOUBLES of an orthonormalisation scratch hold the batched pass's
+// ticket counter (orth_ticket), which must be 0 before the first orth_pass_batched on it
+constexpr size_t ORTH_TICKET_DOUBLES = 8;
+int32_t* orth_ticket(double* scratch);
 // C (M x N, ld ldc) = op(A) B + beta C; op(A) = A^T (A: K x M, ld lda) when transA, else A
 // (M x K); B: K x N (ld ldb).  Split over K into `part` (gemm_part_doubles), fixed-order reduce.
 size_t gemm_part_doubles(int M, int N, int K);
@@ -154,12 +158,15 @@ struct AtbItem {
     const double* A; int64_t lda; int ma;
     const double* B; int64_t ldb; int mb;
     int64_t rows; double* part; double* out; int64_t ldo;
+    int sym = 0;   // ma == mb: out = (A^T B + B^T A) / 2, the product and its symmetrisation
 };
 rbki_status atb_batched(const AtbItem* it, int n, cudaStream_t st);
 struct OrthItem {
     double* Q; int64_t ldq; int64_t rows; int m; int S; double* scratch; int32_t* kept;
 };
 rbki_status orth_pass_batched(const OrthItem* it, int n, double tau, cudaStream_t st);
+struct FillItem { int32_t* dst; int32_t v; };   // *dst = v (dst == nullptr: skipped)
+rbki_status fill_i32_batched(const FillItem* it, int n, cudaStream_t st);
 struct GemmItem {
     bool transA; int M, N, K;
     const double* A; int64_t lda; const double* B; int64_t ldb;

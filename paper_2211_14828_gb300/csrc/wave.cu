@@ -1039,6 +1039,7 @@ rbki_status run_wave(std::vector<WaveReq>& Q, cudaStream_t st, uint32_t wait_us 
                     wd.push_back(xreduce_rec{w.wpart, w.units, I, m.S, m.S, w.Qall, m.b, nullptr, 0,
                                              (int)cdiv((int64_t)I * m.S, 256), 1, 1});
                     fk.push_back(fill_rec{w.kept, 0, 1, 1, 1});
+                    fk.push_back(fill_rec{orth_ticket(w.orth_ws), 0, 1, 1, 1});   // batched BCGS tickets
                     qmax = std::max(qmax, m.q);
                 }
             }
