@@ -439,7 +439,9 @@ def run_ours(args):
     if roof is not None and prec == "bf16" and not args.sequential and args.omega <= 0:
         xb = x.to(torch.bfloat16)
         s_w = min(wl.ranks[0] + wl.p, dims[0])
-        qm = torch.linalg.qr(torch.randn(dims[0], s_w, dtype=torch.float64, device="cuda"))[0].contiguous()
+        # an orthonormal Q (host QR: keeps torch's device linear-algebra library out of the run)
+        qh = np.linalg.qr(np.random.default_rng(11).standard_normal((dims[0], s_w)))[0]
+        qm = torch.from_numpy(np.ascontiguousarray(qh)).cuda()
         for _ in range(3):
             rb.rbki_krylov_product(xb, 0, qm, prec="bf16")
         torch.cuda.synchronize()

@@ -445,11 +445,22 @@ __global__ void __launch_bounds__(256) k_omega_images_b(const __grid_constant__ 
 }
 
 
-// out[i*ld + s] = sum_b (part[b][i][s] + split * part[b][i][N/2 + s]), FP64, fixed order:
-// 32 outputs per CTA; warp w sums partials b = w, w+8, ...; warps combined in order.
+// out[i*ld + s] = sum_b (part[b][i][s] + split * part[b][i][N/2 + s]) in a fixed order:
+// 32 outputs per CTA; warp w sums partials b = w, w+8, ... by compensated summation in FP32
+// (Knuth's TwoSum: the running sum hi and the sum lo of its exact rounding errors; Ogita,
+// Rump & Oishi 2005, Sum2), then the warps' hi + lo are added in order in FP64.  The
+// result is as accurate as an FP64 sum of the terms up to about n^2 u32^2 sum |x| (u32 =
+// 2^-24) and keeps GB300's FP64 pipe (2 operations per clock per SM) out of the loop.
 // When the producing kernel reported an expired wait (*err != 0) its partials are
 // incomplete, and every output is NaN instead, so the result cannot pass for a valid one.
 constexpr int RED_WARPS = 8;
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
+    const float s = __fadd_rn(hi, x);
+    const float bp = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+}
 __device__ __forceinline__ void reduce_tc_dev(const float* __restrict__ part, int nb, int64_t I,
                                               int N, int Sh, int split, double* __restrict__ out,
                                               int64_t ld, double* __restrict__ out2, int64_t ld2,
@@ -458,17 +469,17 @@ __device__ __forceinline__ void reduce_tc_dev(const float* __restrict__ part, in
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t e = (int64_t)bx * 32 + lane;
     const int64_t tot = I * Sh;
-    double acc = 0.0;
+    float hi = 0.f, lo = 0.f;
     if (e < tot) {
         const int64_t i = e / Sh;
         const int s = (int)(e % Sh);
         for (int b = w; b < nb; b += RED_WARPS) {
             const float* pb = part + ((size_t)b * I + i) * N;
-            acc += (double)pb[s];
-            if (split) acc += (double)pb[N / 2 + s];
+            two_sum_acc(hi, lo, pb[s]);
+            if (split) two_sum_acc(hi, lo, pb[N / 2 + s]);
         }
     }
-    acc_sh[w][lane] = acc;
+    acc_sh[w][lane] = (double)hi + (double)lo;
     __syncthreads();
     if (w == 0 && e < tot) {
         double t = 0.0;
