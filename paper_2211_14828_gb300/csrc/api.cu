@@ -550,7 +550,7 @@ rbki_status mode_factor(const Plan& pl, const ModePlan& m, double* U, double* ei
         if (m.sampled) RBKI_TRY(sample_mode(pl, m, st));
         RBKI_TRY(mode_basis(pl, m, kept, st));
         // step 3 (Remark 1): Z = Q^T X X^T Q = Q^T [P_0 .. P_q]
-        RBKI_TRY(atb_cuda(m.Qall, m.b, m.b, m.Pall, m.b, m.b, m.I, m.part, m.Z, m.b, st));
+        RBKI_TRY(atb_cuda(m.Qall, m.b, m.b, m.Pall, m.b, m.b, m.I, m.part, m.Z, m.b, st, pl.mixed));
         RBKI_TRY(symmetrize_cuda(m.Z, m.b, st));
         // step 4: leading eigenvectors of Z; step 5: U = Q U~(:, 1:R)
         RBKI_TRY(syev_top_cuda(m.Z, m.b, m.R, m.eval, m.evec, m.syev_ws, st));
@@ -599,7 +599,7 @@ static rbki_status run_modes_lockstep(const Plan& pl, const rbki_tucker_out* out
             fills.push_back(FillItem{out->info + n, 0});
             fills.push_back(FillItem{out->info + pl.N + n, 0});
         }
-        fills.push_back(FillItem{orth_ticket(m.small), 0});
+        fills.push_back(FillItem{orth_ticket(m.small), 0, ORTH_TICKETS});
     }
     RBKI_TRY(fill_i32_batched(fills.data(), (int)fills.size(), st));
     for (int n = 0; n < pl.N; ++n) {
@@ -675,7 +675,8 @@ static rbki_status run_modes_lockstep(const Plan& pl, const rbki_tucker_out* out
     std::vector<FormItem> fi;
     for (const ModePlan* m : K) {
         // Z = Q^T P with its symmetrisation (Z + Z^T) / 2 folded into the reduction
-        ab.push_back(AtbItem{m->Qall, m->b, m->b, m->Pall, m->b, m->b, m->I, m->part, m->Z, m->b, 1});
+        ab.push_back(AtbItem{m->Qall, m->b, m->b, m->Pall, m->b, m->b, m->I, m->part, m->Z, m->b, 1,
+                             pl.mixed ? 1 : 0});
         ei.push_back(EigItem{m->Z, m->b, m->R, m->eval, m->evec, m->syev_ws});
         fi.push_back(FormItem{m->Qall, m->b, m->I, m->evec, m->b, m->R, m->R, out->factors[m->n]});
     }
@@ -740,7 +741,7 @@ static rbki_status run_modes_adaptive(const Plan& pl, const rbki_tucker_out* out
             const int bj = (j + 1) * m.S;
             RBKI_TRY(krylov_step(pl, m, m.Qall + j * m.S, m.b, m.S, m.Pall + j * m.S, m.b,
                                  j < m.q ? m.Qall + (j + 1) * m.S : nullptr, m.b, ms[n]));
-            RBKI_TRY(atb_cuda(m.Qall, m.b, bj, m.Pall, m.b, bj, m.I, m.part, m.Z, bj, ms[n]));
+            RBKI_TRY(atb_cuda(m.Qall, m.b, bj, m.Pall, m.b, bj, m.I, m.part, m.Z, bj, ms[n], pl.mixed));
             RBKI_TRY(symmetrize_cuda(m.Z, bj, ms[n]));
             RBKI_TRY(syev_top_cuda(m.Z, bj, m.R, m.eval, m.evec, m.syev_ws, ms[n]));
         }

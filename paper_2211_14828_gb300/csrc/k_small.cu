@@ -6,6 +6,7 @@
 //     deflation (reading c3); two passes give BCGS2 / CholQR2
 //   * factor formation U = Q U~(:, 1:R) with the sign convention (Algorithm 2 step 5).
 #include "kernels.h"
+#include "dfloat.cuh"
 
 namespace rbki {
 namespace {
@@ -81,6 +82,66 @@ __global__ void __launch_bounds__(256) k_atb_part_b(const __grid_constant__ BPac
     atb_part_dev(r.A, r.lda, r.ma, r.B, r.ldb, r.mb, r.rows, r.rows_per_chunk, r.part, bx, by, bz);
 }
 
+// The same partials with the operands rounded to FP32 and FP32 accumulation within a chunk of
+// rows (the chunks are then summed in FP64 by k_atb_reduce): for the mixed path's Z = Q^T P,
+// whose P already carries the BF16 rounding of the tensor-core products (relative 2^-9), so
+// the FP32 chunk sums (error <= rows_per_chunk * 2^-24 * sum |q p|) add nothing visible, and
+// the products leave GB300's FP64 pipe (2 per clock per SM) for the FP32 pipes.
+__device__ __forceinline__ void atb_part32_dev(const double* __restrict__ A, int64_t lda, int ma,
+                                               const double* __restrict__ B, int64_t ldb, int mb,
+                                               int64_t rows, int64_t rows_per_chunk,
+                                               double* __restrict__ part, int bx, int by, int bz) {
+    __shared__ float as[AT_K][AT_T + 1];
+    __shared__ float bs[AT_K][AT_T + 1];
+    const int tid = threadIdx.x;
+    const int tk = tid / 16, tl = tid % 16;          // 2 x 2 outputs per thread
+    const int k0 = bx * AT_T, l0 = by * AT_T;
+    const int64_t r_lo = (int64_t)bz * rows_per_chunk;
+    const int64_t r_hi = min(rows, r_lo + rows_per_chunk);
+    float acc[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+    for (int64_t r0 = r_lo; r0 < r_hi; r0 += AT_K) {
+        for (int e = tid; e < AT_K * AT_T; e += 256) {
+            int rr = e / AT_T, cc = e % AT_T;
+            int64_t r = r0 + rr;
+            bool ok = r < r_hi;
+            as[rr][cc] = (ok && k0 + cc < ma) ? __double2float_rn(A[r * lda + k0 + cc]) : 0.f;
+            bs[rr][cc] = (ok && l0 + cc < mb) ? __double2float_rn(B[r * ldb + l0 + cc]) : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int rr = 0; rr < AT_K; ++rr) {
+            const float a0 = as[rr][tk], a1 = as[rr][tk + 16];
+            const float b0 = bs[rr][tl], b1 = bs[rr][tl + 16];
+            acc[0][0] = fmaf(a0, b0, acc[0][0]); acc[0][1] = fmaf(a0, b1, acc[0][1]);
+            acc[1][0] = fmaf(a1, b0, acc[1][0]); acc[1][1] = fmaf(a1, b1, acc[1][1]);
+        }
+        __syncthreads();
+    }
+    double* out = part + (int64_t)bz * ma * mb;
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+            int k = k0 + tk + 16 * u, l = l0 + tl + 16 * v;
+            if (k < ma && l < mb) out[(int64_t)k * mb + l] = (double)acc[u][v];
+        }
+}
+
+__global__ void __launch_bounds__(256) k_atb_part32(const double* __restrict__ A, int64_t lda, int ma,
+                                                    const double* __restrict__ B, int64_t ldb, int mb,
+                                                    int64_t rows, int64_t rows_per_chunk,
+                                                    double* __restrict__ part) {
+    atb_part32_dev(A, lda, ma, B, ldb, mb, rows, rows_per_chunk, part, (int)blockIdx.x, (int)blockIdx.y,
+                   (int)blockIdx.z);
+}
+
+__global__ void __launch_bounds__(256) k_atb_part32_b(const __grid_constant__ BPack<atb_part_rec> p) {
+    const atb_part_rec& r = p.r[blockIdx.y];
+    int bx, by, bz;
+    if (!bat_block(r, bx, by, bz)) return;
+    atb_part32_dev(r.A, r.lda, r.ma, r.B, r.ldb, r.mb, r.rows, r.rows_per_chunk, r.part, bx, by, bz);
+}
+
 
 // sum over the chunks of element e of the partials: four independent loads in flight per
 // step; fixed summation order
@@ -88,11 +149,11 @@ __device__ __forceinline__ double atb_sum_elem(const double* __restrict__ part, 
     double acc = 0.0;
     int c = 0;
     for (; c + 3 < nchunk; c += 4) {
-        const double v0 = part[c * stride + e], v1 = part[(c + 1) * stride + e];
-        const double v2 = part[(c + 2) * stride + e], v3 = part[(c + 3) * stride + e];
+        const double v0 = __ldcg(part + c * stride + e), v1 = __ldcg(part + (c + 1) * stride + e);
+        const double v2 = __ldcg(part + (c + 2) * stride + e), v3 = __ldcg(part + (c + 3) * stride + e);
         acc += (v0 + v1) + (v2 + v3);
     }
-    for (; c < nchunk; ++c) acc += part[c * stride + e];
+    for (; c < nchunk; ++c) acc += __ldcg(part + c * stride + e);
     return acc;
 }
 
@@ -134,26 +195,49 @@ __global__ void k_atb_reduce_b(const __grid_constant__ BPack<atb_reduce_rec> p) 
 
 
 // G'[k][l] = M[m+k][l] - sum_{r<m} M[r][k] M[r][l]  (Pythagorean Gram of the projected block)
-// nu2[k] = M[m+k][k] (squared column norms before projection).  One CTA per column l.
-__device__ __forceinline__ void gprime_elem(const double* __restrict__ M, int m, int S, double* __restrict__ Gp,
-                                            double* __restrict__ nu2, int k, int l) {
-    double g = M[(int64_t)(m + k) * S + l];
+// nu2[k] = M[m+k][k] (squared column norms before projection).
+// Summation order (fixed, shared by every form): the rows r < m in tiles of GP_TILE; within a
+// tile four interleaved accumulators, combined as (a0 + a1) + (a2 + a3); the tiles' sums
+// added in tile order.  The batched pass computes each tile's sum on its own CTA.
+constexpr int GP_TILE = 32;
+// the tile's sum from its nr rows, row q at Mt + q * S (global memory or a shared copy)
+template <bool SHARED>
+__device__ __forceinline__ double gprime_tile_rows(const double* __restrict__ Mt, int nr, int S, int k, int l) {
+    auto ld = [&](int q, int c) { return SHARED ? Mt[q * S + c] : __ldcg(Mt + (int64_t)q * S + c); };
     double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-    int r = 0;
-    for (; r + 3 < m; r += 4) {
-        a0 += M[(int64_t)r * S + k] * M[(int64_t)r * S + l];
-        a1 += M[(int64_t)(r + 1) * S + k] * M[(int64_t)(r + 1) * S + l];
-        a2 += M[(int64_t)(r + 2) * S + k] * M[(int64_t)(r + 2) * S + l];
-        a3 += M[(int64_t)(r + 3) * S + k] * M[(int64_t)(r + 3) * S + l];
+    int q = 0;
+    for (; q + 3 < nr; q += 4) {
+        a0 += ld(q, k) * ld(q, l);
+        a1 += ld(q + 1, k) * ld(q + 1, l);
+        a2 += ld(q + 2, k) * ld(q + 2, l);
+        a3 += ld(q + 3, k) * ld(q + 3, l);
     }
-    for (; r < m; ++r) a0 += M[(int64_t)r * S + k] * M[(int64_t)r * S + l];
-    Gp[k * S + l] = g - ((a0 + a1) + (a2 + a3));
+    for (; q < nr; ++q) a0 += ld(q, k) * ld(q, l);
+    return (a0 + a1) + (a2 + a3);
+}
+__device__ __forceinline__ double gprime_tile(const double* __restrict__ M, int m, int S, int k, int l, int t) {
+    const int r0 = t * GP_TILE, r1 = min(m, r0 + GP_TILE);
+    return gprime_tile_rows<false>(M + (int64_t)r0 * S, r1 - r0, S, k, l);
+}
+
+__device__ __forceinline__ void gprime_finish(const double* __restrict__ M, int m, int S, double acc,
+                                              double* __restrict__ Gp, double* __restrict__ nu2, int k, int l) {
+    const double g = __ldcg(M + (int64_t)(m + k) * S + l);
+    Gp[k * S + l] = g - acc;
     if (k == l) nu2[k] = g;
 }
 
+__device__ __forceinline__ void gprime_elem(const double* __restrict__ M, int m, int S, double* __restrict__ Gp,
+                                            double* __restrict__ nu2, int k, int l) {
+    double acc = 0.0;
+    for (int t = 0; t * GP_TILE < m; ++t) acc += gprime_tile(M, m, S, k, l, t);
+    gprime_finish(M, m, S, acc, Gp, nu2, k, l);
+}
+
+// one CTA per column l; only the upper triangle k <= l (what the Cholesky reads)
 __device__ __forceinline__ void gprime_dev(const double* __restrict__ M, int m, int S, double* __restrict__ Gp,
                                            double* __restrict__ nu2, int bx) {
-    if ((int)threadIdx.x < S) gprime_elem(M, m, S, Gp, nu2, (int)threadIdx.x, bx);
+    if ((int)threadIdx.x <= bx && (int)threadIdx.x < S) gprime_elem(M, m, S, Gp, nu2, (int)threadIdx.x, bx);
 }
 
 __global__ void k_gprime(const double* __restrict__ M, int m, int S, double* __restrict__ Gp,
@@ -161,50 +245,22 @@ __global__ void k_gprime(const double* __restrict__ M, int m, int S, double* __r
     gprime_dev(M, m, S, Gp, nu2, (int)blockIdx.x);
 }
 
-struct gprime_rec {
-    const double* M;
-    int m;
-    int S;
-    double* Gp;
-    double* nu2;
-    int gx, gy, gz;
-};
-
-__global__ void k_gprime_b(const __grid_constant__ BPack<gprime_rec> p) {
-    const gprime_rec& r = p.r[blockIdx.y];
-    int bx, by, bz;
-    if (!bat_block(r, bx, by, bz)) return;
-    gprime_dev(r.M, r.m, r.S, r.Gp, r.nu2, bx);
-}
-
-
 // Cholesky G' = R^T R with pivot deflation, and Rinv (upper, zero rows/columns for
 // deflated directions).  Column k is deflated when nu2[k] == 0 or its pivot (squared norm
 // orthogonal to everything accepted) <= tau^2 nu2[k].  Single CTA.
 //
 // G' = L D L^T by elimination without square roots, carrying M = L^{-1} along (the same row
 // operations applied to an identity), so that R = D^{1/2} L^T and Rinv = M^T D^{-1/2} come
-// out of one loop with one barrier per step.  FP64 on GB300 has 64 cycles of dependent
-// latency and 2 FMA/clk/SM, so the serial chain is kept short and the FP64 instructions
-// full:
-//   * thread 0 updates d_{k+1} first and computes 1 / d_{k+1} (FP32 estimate + two FP64
-//     Newton steps) while the other threads update the rest (lookahead);
+// out of one loop with one barrier per step.  The elimination is a serial chain of S steps,
+// so it runs in double-float (dfloat.cuh, about 2^-48 relative) on the FP32 pipes: on GB300
+// a dependent FP64 instruction waits tens of cycles and the SM retires two a clock, which
+// made the FP64 form take about 1.7 us per step at S = 30.  G' and the thresholds are scaled
+// by an exact power of 4 (the largest nu2 into [1, 4)) so that every entry sits well inside
+// FP32's range; a column whose nu2 is below about 2^-100 of the largest is treated as zero.
+//   * thread 0 updates d_{k+1} first and computes 1 / d_{k+1} while the other threads update
+//     the rest (lookahead);
 //   * the trailing upper triangle and the rows of M are walked as one packed index list;
-//   * 1 / sqrt(d_k) for all k in parallel afterwards.
-__device__ __forceinline__ double rsqrt_f64(double d) {
-    // FP32 estimate + two FP64 Newton steps: full FP64 accuracy with a short dependent chain
-    double y = (double)rsqrtf((float)d);
-    y = y * (1.5 - 0.5 * d * y * y);
-    y = y * (1.5 - 0.5 * d * y * y);
-    return y;
-}
-__device__ __forceinline__ double rcp_f64(double d) {
-    double y = (double)__frcp_rn((float)d);
-    y = y * (2.0 - d * y);
-    y = y * (2.0 - d * y);
-    return y;
-}
-
+//   * 1 / sqrt(d_k) for all k in parallel afterwards; Rinv is written in FP64.
 __device__ __forceinline__ void chol_deflate_dev(const double* __restrict__ Gp, const double* __restrict__ nu2,
                                                  int S, double tau, double* __restrict__ Rinv,
                                                  int32_t* __restrict__ kept) {
@@ -213,58 +269,78 @@ __device__ __forceinline__ void chol_deflate_dev(const double* __restrict__ Gp, 
     // implied).  Keeping the shared memory small (S = 30: 7.5 KB) lets this kernel share an
     // SM with the tensor-core streaming kernel running on another stream.
     extern __shared__ double sm[];
-    double* W = sm;
-    double* inv_d = W + S * S;        // S: 1 / d_k, 0 when deflated
-    double* rinv = inv_d + S;         // S: 1 / sqrt(d_k), 0 when deflated
+    dfl* W = reinterpret_cast<dfl*>(sm);
+    dfl* inv_d = W + S * S;           // S: 1 / d_k, 0 when deflated
+    dfl* aux = inv_d + S;             // S: deflation thresholds, then 1 / sqrt(d_k)
+    __shared__ int p_sh;
     const int tid = threadIdx.x, nt = blockDim.x;
-    for (int e = tid; e < S * S; e += nt) W[e] = (e % S >= e / S) ? Gp[e] : 0.0;
+    const int tx = tid & 15, ty = tid >> 4, ny = nt >> 4;
+    // p = floor(e / 2) for the largest nu2 in [2^e, 2^(e+1)): nu2 * 4^-p lies in [1, 4)
+    if (tid < 32) {
+        unsigned long long mx = 0;
+        for (int k = tid; k < S; k += 32) {
+            const unsigned long long b = (unsigned long long)__double_as_longlong(nu2[k]);
+            mx = b > mx ? b : mx;   // nu2 >= 0: the bit patterns order like the values
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            const unsigned long long v = __shfl_xor_sync(0xffffffffu, mx, o);
+            mx = v > mx ? v : mx;
+        }
+        if (tid == 0) {
+            const int e = (int)((mx >> 52) & 0x7ff) - 1023;
+            const int pe = mx == 0 ? 0 : (e >= 0 ? e / 2 : -((1 - e) / 2));
+            p_sh = pe < -500 ? -500 : (pe > 500 ? 500 : pe);   // keeps 4^-p and 2^-p normal
+        }
+    }
+    __syncthreads();
+    const int p = p_sh;
+    const double sc = __longlong_as_double((long long)(1023 - 2 * p) << 52);     // 4^-p
+    const double unsc = __longlong_as_double((long long)(1023 - p) << 52);       // 2^-p
+    for (int e = tid; e < S * S; e += nt) W[e] = (e % S >= e / S) ? df_from_double(Gp[e] * sc) : dfl{0.f, 0.f};
+    for (int k = tid; k < S; k += nt)
+        aux[k] = nu2[k] > 0.0 ? df_from_double(tau * tau * nu2[k] * sc) : dfl{__int_as_float(0x7f800000), 0.f};
     __syncthreads();
     auto pivot = [&](int k) {
-        const double d = W[k * S + k], nu = nu2[k];
-        inv_d[k] = (nu > 0.0 && d > tau * tau * nu) ? rcp_f64(d) : 0.0;
+        const dfl d = W[k * S + k];
+        inv_d[k] = df_gt(d, aux[k]) ? df_rcp(d) : dfl{0.f, 0.f};
     };
     if (tid == 0) pivot(0);
     __syncthreads();
     for (int k = 0; k < S; ++k) {
-        const double ik = inv_d[k];
+        const dfl ik = inv_d[k];
         const int mm = S - k - 1;
-        if (ik != 0.0) {                       // uniform: a deflated column eliminates nothing
+        if (ik.hi != 0.f) {                    // uniform: a deflated column eliminates nothing
             if (tid == 0 && mm > 0) {          // d_{k+1} first, then its reciprocal
-                const double wk = W[k * S + k + 1];
-                W[(k + 1) * S + k + 1] -= wk * wk * ik;
+                const dfl wk = W[k * S + k + 1];
+                W[(k + 1) * S + k + 1] = df_fms(W[(k + 1) * S + k + 1], df_mul(wk, ik), wk);
             }
-            const int ntri = mm * (mm + 1) / 2;      // trailing upper triangle (a <= b)
-            const int nm = mm * (k + 1);             // rows k+1.. of L^{-1}, columns 0..k
-            for (int t = tid + 1; t < ntri + nm; t += nt) {
-                if (t < ntri) {
-                    // t = b (b + 1) / 2 + a, 0 <= a <= b < mm
-                    int bb = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
-                    if ((bb + 1) * (bb + 2) / 2 <= t) ++bb;
-                    if (bb * (bb + 1) / 2 > t) --bb;
-                    const int aa = t - bb * (bb + 1) / 2;
-                    const int i = k + 1 + aa, j = k + 1 + bb;
-                    W[i * S + j] -= W[k * S + i] * W[k * S + j] * ik;
-                } else {
-                    const int u = t - ntri;
-                    const int i = k + 1 + u / (k + 1), c = u % (k + 1);
-                    const double mkc = c == k ? 1.0 : W[k * S + c];   // L^{-1}[k][c]
-                    W[i * S + c] -= (W[k * S + i] * ik) * mkc;
+            // rows i > k on a 16-wide grid of threads (no index division): the trailing
+            // upper triangle j >= i (d_{k+1} done above) and the row of L^{-1}, columns 0..k
+            for (int i = k + 1 + ty; i < S; i += ny) {
+                const dfl li = df_mul(W[k * S + i], ik);
+                for (int j = k + 1 + tx; j < S; j += 16)
+                    if (j >= i && (i != k + 1 || j != k + 1)) W[i * S + j] = df_fms(W[i * S + j], li, W[k * S + j]);
+                for (int c = tx; c <= k; c += 16) {
+                    const dfl mkc = c == k ? dfl{1.f, 0.f} : W[k * S + c];   // L^{-1}[k][c]
+                    W[i * S + c] = df_fms(W[i * S + c], li, mkc);
                 }
             }
         }
         if (tid == 0 && mm > 0) pivot(k + 1);
         __syncthreads();
     }
-    for (int k = tid; k < S; k += nt) rinv[k] = inv_d[k] != 0.0 ? rsqrt_f64(W[k * S + k]) : 0.0;
+    for (int k = tid; k < S; k += nt) aux[k] = inv_d[k].hi != 0.f ? df_rsqrt(W[k * S + k]) : dfl{0.f, 0.f};
     __syncthreads();
-    // Rinv[t][c] = L^{-1}[c][t] / sqrt(d_c) for t <= c
+    // Rinv[t][c] = L^{-1}[c][t] / sqrt(d_c) for t <= c, scaled back by 2^-p
     for (int e = tid; e < S * S; e += nt) {
         const int t = e / S, c = e % S;
-        Rinv[e] = t < c ? W[c * S + t] * rinv[c] : (t == c ? rinv[c] : 0.0);
+        Rinv[e] = t < c ? df_to_double(df_mul(W[c * S + t], aux[c])) * unsc
+                        : (t == c ? df_to_double(aux[c]) * unsc : 0.0);
     }
     if (tid == 0 && kept) {
         int nk = 0;
-        for (int k = 0; k < S; ++k) nk += inv_d[k] != 0.0 ? 1 : 0;
+        for (int k = 0; k < S; ++k) nk += inv_d[k].hi != 0.f ? 1 : 0;
         atomicAdd(kept, nk);
     }
 }
@@ -275,30 +351,17 @@ __global__ void k_chol_deflate(const double* __restrict__ Gp, const double* __re
     chol_deflate_dev(Gp, nu2, S, tau, Rinv, kept);
 }
 
-struct chol_deflate_rec {
-    const double* Gp;
-    const double* nu2;
-    int S;
-    double tau;
-    double* Rinv;
-    int32_t* kept;
-    int gx, gy, gz;
-};
-
-__global__ void k_chol_deflate_b(const __grid_constant__ BPack<chol_deflate_rec> p) {
-    const chol_deflate_rec& r = p.r[blockIdx.y];
-    int bx, by, bz;
-    if (!bat_block(r, bx, by, bz)) return;
-    chol_deflate_dev(r.Gp, r.nu2, r.S, r.tau, r.Rinv, r.kept);
-}
-
-
-// The head of one orthonormalisation pass in one launch: every CTA computes its tile of the
-// chunk partials of M = [Q_{<m} Q_m]^T Q_m (k_atb_part); the CTA that finishes last (a ticket
-// counter, no CTA waits for another) sums the partials (k_atb_reduce), forms the Pythagorean
-// Gram G' and nu2 (k_gprime) and factors it with deflation (k_chol_deflate), with the same
-// arithmetic in the same order as those three kernels, then resets the ticket to 0.  The
-// ticket must be 0 before the first pass.
+// The head of one orthonormalisation pass in one launch, finished by ticket counters (no CTA
+// waits for another):
+//   1. every CTA computes its tile of the chunk partials of M = [Q_{<m} Q_m]^T Q_m (k_atb_part);
+//   2. the CTA that finishes last among those of a 32-row tile of M sums that tile's partials
+//      (k_atb_reduce) and, for the rows r < m it holds, the tile's sums of the Pythagorean
+//      correction sum_r M[r][k] M[r][l] (gprime_tile);
+//   3. the tile that finishes last adds the tiles' sums in tile order, forms G' and nu2
+//      (k_gprime) and factors G' with deflation (k_chol_deflate).
+// Same arithmetic in the same order as those kernels.  ticket[0] counts finished tiles and
+// ticket[1 + t] the finished CTAs of tile t; the last CTA puts them back to 0.  The tickets
+// must be 0 before the first pass.
 struct orth_head_rec {
     const double* Q;
     int64_t ldq;
@@ -309,12 +372,13 @@ struct orth_head_rec {
     int nchunk;
     double* part;
     double* M;
+    double* gpart;     // [tile][S][S] sums of the Pythagorean correction per 32-row tile
     double* Gp;
     double* Rinv;
     double* nu2;
     double tau;
     int32_t* kept;
-    int32_t* ticket;
+    int32_t* ticket;   // 1 + gx counters
     int gx, gy, gz;
 };
 
@@ -322,23 +386,48 @@ __global__ void __launch_bounds__(256) k_orth_head_b(const __grid_constant__ BPa
     const orth_head_rec& r = p.r[blockIdx.y];
     int bx, by, bz;
     if (!bat_block(r, bx, by, bz)) return;
-    const int ma = r.m + r.S;
-    atb_part_dev(r.Q, r.ldq, ma, r.Q + r.m, r.ldq, r.S, r.rows, r.rows_per_chunk, r.part, bx, by, bz);
+    const int ma = r.m + r.S, S = r.S;
+    atb_part_dev(r.Q, r.ldq, ma, r.Q + r.m, r.ldq, S, r.rows, r.rows_per_chunk, r.part, bx, by, bz);
     __shared__ int last;
     __threadfence();                   // this CTA's partials before its ticket
     __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(r.ticket, 1) == r.gx * r.gy * r.gz - 1;
+    if (threadIdx.x == 0) last = atomicAdd(r.ticket + 1 + bx, 1) == r.gy * r.gz - 1;
     __syncthreads();
     if (!last) return;
-    __threadfence();                   // every other CTA's partials are visible from here
-    const int mp = ma * r.S;
-    for (int e = threadIdx.x; e < mp; e += blockDim.x)
-        r.M[e] = atb_sum_elem(r.part, r.nchunk, (int64_t)mp, e);
+    __threadfence();                   // the partials of this row tile are visible from here
+    const int mp = ma * S;
+    const int r0 = bx * AT_T, nr = min(AT_T, ma - r0);
+    extern __shared__ double oh_sm[];  // this tile's rows of M (then the Cholesky's arrays)
+    for (int e = threadIdx.x; e < nr * S; e += blockDim.x) {
+        const double v = atb_sum_elem(r.part, r.nchunk, (int64_t)mp, r0 * S + e);
+        r.M[(int64_t)r0 * S + e] = v;
+        oh_sm[e] = v;
+    }
+    __syncthreads();                   // this tile's rows of M, for the tile sums below
+    if (r0 < r.m) {
+        const int nb = min(r.m, r0 + GP_TILE) - r0;
+        for (int e = threadIdx.x; e < S * S; e += blockDim.x) {
+            const int k = e / S, l = e % S;
+            if (k <= l) r.gpart[(int64_t)bx * S * S + e] = gprime_tile_rows<true>(oh_sm, nb, S, k, l);
+        }
+    }
+    __syncthreads();                   // the shared rows are reused by the Cholesky
+    __threadfence();                   // this tile's M rows and sums before its ticket
     __syncthreads();
-    for (int e = threadIdx.x; e < r.S * r.S; e += blockDim.x) gprime_elem(r.M, r.m, r.S, r.Gp, r.nu2, e % r.S, e / r.S);
+    if (threadIdx.x == 0) last = atomicAdd(r.ticket, 1) == r.gx - 1;
     __syncthreads();
-    chol_deflate_dev(r.Gp, r.nu2, r.S, r.tau, r.Rinv, r.kept);
-    if (threadIdx.x == 0) *r.ticket = 0;
+    if (!last) return;
+    __threadfence();                   // every tile's M rows and sums are visible from here
+    for (int e = threadIdx.x; e < S * S; e += blockDim.x) {
+        if (e / S > e % S) continue;   // the Cholesky reads the upper triangle only
+        double acc = 0.0;
+        for (int t = 0; t * GP_TILE < r.m; ++t) acc += __ldcg(r.gpart + (int64_t)t * S * S + e);
+        gprime_finish(r.M, r.m, S, acc, r.Gp, r.nu2, e / S, e % S);
+    }
+    __syncthreads();
+    chol_deflate_dev(r.Gp, r.nu2, S, r.tau, r.Rinv, r.kept);
+    if (threadIdx.x == 0)
+        for (int t = 0; t <= r.gx; ++t) r.ticket[t] = 0;
 }
 
 // Q[i][m+s] = sum_t (Q[i][m+t] - sum_{r<m} Q[i][r] M[r][t]) Rinv[t][s]; ORTH_ROWS rows per CTA
@@ -536,14 +625,15 @@ __global__ void k_fill_i32(int32_t* d, int32_t v, int n) {
 struct fill_i32_rec {
     int32_t* d;
     int32_t v;
+    int n;
     int gx, gy, gz;
 };
 
 __global__ void k_fill_i32_b(const __grid_constant__ BPack<fill_i32_rec> p) {
     const fill_i32_rec& r = p.r[blockIdx.y];
     int bx, by, bz;
-    if (!bat_block(r, bx, by, bz) || threadIdx.x) return;
-    *r.d = r.v;
+    if (!bat_block(r, bx, by, bz)) return;
+    for (int e = threadIdx.x; e < r.n; e += blockDim.x) r.d[e] = r.v;
 }
 
 }  // namespace
@@ -554,21 +644,24 @@ int atb_nchunks(int64_t rows) {
 }
 
 rbki_status atb_cuda(const double* A, int64_t lda, int ma, const double* B, int64_t ldb, int mb,
-                     int64_t rows, double* part, double* out, int64_t ldo, cudaStream_t st) {
+                     int64_t rows, double* part, double* out, int64_t ldo, cudaStream_t st, bool f32) {
     int nch = atb_nchunks(rows);
     int64_t rpc = cdiv(rows, nch);
     dim3 grid((unsigned)cdiv(ma, AT_T), (unsigned)cdiv(mb, AT_T), (unsigned)nch);
-    k_atb_part<<<grid, 256, 0, st>>>(A, lda, ma, B, ldb, mb, rows, rpc, part);
+    if (f32) k_atb_part32<<<grid, 256, 0, st>>>(A, lda, ma, B, ldb, mb, rows, rpc, part);
+    else k_atb_part<<<grid, 256, 0, st>>>(A, lda, ma, B, ldb, mb, rows, rpc, part);
     RBKI_LAUNCH_CHECK("k_atb_part");
     k_atb_reduce<<<(unsigned)cdiv((int64_t)ma * mb, 256), 256, 0, st>>>(part, nch, ma, mb, out, ldo);
     RBKI_LAUNCH_CHECK("k_atb_reduce");
     return RBKI_OK;
 }
 
-// scratch: [ticket (8 doubles)] [chunk partials] [M] [G'] [Rinv] [nu2]
+// scratch: [tickets (8 doubles)] [chunk partials] [M] [G'] [Rinv] [nu2] [per-tile sums of the
+// Pythagorean correction]
 size_t orth_scratch_doubles(int64_t rows, int m, int S) {
     size_t mp = (size_t)(m + S) * S;
-    return ORTH_TICKET_DOUBLES + (size_t)atb_nchunks(rows) * mp + mp + 2 * (size_t)S * S + S + 64;
+    return ORTH_TICKET_DOUBLES + (size_t)atb_nchunks(rows) * mp + mp + 2 * (size_t)S * S + S +
+           (size_t)cdiv(m + S, AT_T) * S * S + 64;
 }
 
 int32_t* orth_ticket(double* scratch) { return reinterpret_cast<int32_t*>(scratch); }
@@ -623,17 +716,18 @@ rbki_status fill_i32_cuda(int32_t* dst, int32_t v, int n, cudaStream_t st) {
 // ---- batched forms: one launch per kernel for all items (see bat_launch) ----
 rbki_status atb_batched(const AtbItem* it, int n, cudaStream_t st) {
     if (n <= 0) return RBKI_OK;
-    std::vector<atb_part_rec> ap(n);
+    std::vector<atb_part_rec> ap, ap32;
     std::vector<atb_reduce_rec> ar(n);
     for (int k = 0; k < n; ++k) {
         const AtbItem& a = it[k];
         const int nch = atb_nchunks(a.rows);
-        ap[k] = atb_part_rec{a.A, a.lda, a.ma, a.B, a.ldb, a.mb, a.rows, cdiv(a.rows, nch), a.part,
-                             (int)cdiv(a.ma, AT_T), (int)cdiv(a.mb, AT_T), nch};
+        (a.f32 ? ap32 : ap).push_back(atb_part_rec{a.A, a.lda, a.ma, a.B, a.ldb, a.mb, a.rows, cdiv(a.rows, nch),
+                                                   a.part, (int)cdiv(a.ma, AT_T), (int)cdiv(a.mb, AT_T), nch});
         if (a.sym && a.ma != a.mb) return set_error(RBKI_E_INVAL, "atb_batched: symmetric output of a non-square product");
         ar[k] = atb_reduce_rec{a.part, nch, a.ma, a.mb, a.out, a.ldo, a.sym, (int)cdiv((int64_t)a.ma * a.mb, 256), 1, 1};
     }
-    RBKI_TRY(bat_launch(k_atb_part_b, ap.data(), n, 256, 0, st, "k_atb_part_b"));
+    RBKI_TRY(bat_launch(k_atb_part_b, ap.data(), (int)ap.size(), 256, 0, st, "k_atb_part_b"));
+    RBKI_TRY(bat_launch(k_atb_part32_b, ap32.data(), (int)ap32.size(), 256, 0, st, "k_atb_part32_b"));
     return bat_launch(k_atb_reduce_b, ar.data(), n, 256, 0, st, "k_atb_reduce_b");
 }
 
@@ -656,12 +750,16 @@ rbki_status orth_pass_batched(const OrthItem* it, int n, double tau, cudaStream_
         double* Gp = M + mp;
         double* Rinv = Gp + (size_t)S * S;
         double* nu2 = Rinv + (size_t)S * S;
-        oh[k] = orth_head_rec{o.Q, o.ldq, o.m, S, o.rows, cdiv(o.rows, nch), nch, part, M, Gp, Rinv, nu2, tau, o.kept,
-                              orth_ticket(o.scratch), (int)cdiv(ma, AT_T), (int)cdiv(S, AT_T), nch};
+        double* gpart = nu2 + S;
+        if (cdiv(ma, AT_T) + 1 > (int64_t)(ORTH_TICKET_DOUBLES * 2))
+            return set_error(RBKI_E_UNSUPPORTED, "orth: more row tiles than tickets");
+        oh[k] = orth_head_rec{o.Q, o.ldq, o.m, S, o.rows, cdiv(o.rows, nch), nch, part, M, gpart, Gp, Rinv, nu2, tau,
+                              o.kept, orth_ticket(o.scratch), (int)cdiv(ma, AT_T), (int)cdiv(S, AT_T), nch};
         oa[k] = orth_apply_rec{o.Q, o.ldq, o.rows, o.m, S, M, Rinv, (int)cdiv(o.rows, ORTH_ROWS), 1, 1};
         smax = std::max(smax, S);
     }
-    const size_t sm = ((size_t)smax * smax + 2 * smax) * sizeof(double);
+    // the Cholesky's arrays, or one 32-row tile of M for the tile sums
+    const size_t sm = std::max((size_t)smax * smax + 2 * smax, (size_t)AT_T * smax) * sizeof(double);
     static const size_t hmax = max_dyn_smem(k_orth_head_b);   // thread-safe, once
     if (sm > hmax) return set_error(RBKI_E_UNSUPPORTED, "orth: block too wide for shared memory");
     RBKI_TRY(bat_launch(k_orth_head_b, oh.data(), n, 256, sm, st, "k_orth_head_b"));
@@ -685,7 +783,7 @@ rbki_status form_factor_batched(const FormItem* it, int n, cudaStream_t st) {
 rbki_status fill_i32_batched(const FillItem* it, int n, cudaStream_t st) {
     std::vector<fill_i32_rec> fr;
     for (int k = 0; k < n; ++k)
-        if (it[k].dst) fr.push_back(fill_i32_rec{it[k].dst, it[k].v, 1, 1, 1});
+        if (it[k].dst && it[k].n > 0) fr.push_back(fill_i32_rec{it[k].dst, it[k].v, it[k].n, 1, 1, 1});
     return bat_launch(k_fill_i32_b, fr.data(), (int)fr.size(), 32, 0, st, "k_fill_i32_b");
 }
 

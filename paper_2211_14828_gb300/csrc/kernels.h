@@ -61,9 +61,11 @@ rbki_status stage_cuda(const void* x, int dtype, int64_t n, void* dst, int dst_d
 
 // ---- small dense FP64 kernels (k_small.cu) ----
 // out (ma x mb, ld ldo) = A^T B over `rows` rows; A: rows x ma (lda), B: rows x mb (ldb).
+// Partial sums over chunks of rows, summed in FP64 in a fixed order; f32: the operands
+// rounded to FP32 and FP32 sums within a chunk (the mixed path's Z = Q^T P).
 int atb_nchunks(int64_t rows);
 rbki_status atb_cuda(const double* A, int64_t lda, int ma, const double* B, int64_t ldb, int mb,
-                     int64_t rows, double* part, double* out, int64_t ldo, cudaStream_t st);
+                     int64_t rows, double* part, double* out, int64_t ldo, cudaStream_t st, bool f32 = false);
 // One pass of block orthonormalisation (Pythagorean-inner-product block Gram-Schmidt
 // followed by Cholesky QR with pivot deflation).  Q: rows x ldq, block = columns
 // [m, m+S); earlier columns [0, m) are orthonormal.  In place.
@@ -73,6 +75,7 @@ size_t orth_scratch_doubles(int64_t rows, int m, int S);
 // the first ORTH_TICKET_DOUBLES of an orthonormalisation scratch hold the batched pass's
 // ticket counter (orth_ticket), which must be 0 before the first orth_pass_batched on it
 constexpr size_t ORTH_TICKET_DOUBLES = 8;
+constexpr int ORTH_TICKETS = (int)(ORTH_TICKET_DOUBLES * 2);   // int32 words to zero
 int32_t* orth_ticket(double* scratch);
 // C (M x N, ld ldc) = op(A) B + beta C; op(A) = A^T (A: K x M, ld lda) when transA, else A
 // (M x K); B: K x N (ld ldb).  Split over K into `part` (gemm_part_doubles), fixed-order reduce.
@@ -159,13 +162,14 @@ struct AtbItem {
     const double* B; int64_t ldb; int mb;
     int64_t rows; double* part; double* out; int64_t ldo;
     int sym = 0;   // ma == mb: out = (A^T B + B^T A) / 2, the product and its symmetrisation
+    int f32 = 0;   // operands rounded to FP32, FP32 sums within a chunk of rows (atb_cuda's f32)
 };
 rbki_status atb_batched(const AtbItem* it, int n, cudaStream_t st);
 struct OrthItem {
     double* Q; int64_t ldq; int64_t rows; int m; int S; double* scratch; int32_t* kept;
 };
 rbki_status orth_pass_batched(const OrthItem* it, int n, double tau, cudaStream_t st);
-struct FillItem { int32_t* dst; int32_t v; };   // *dst = v (dst == nullptr: skipped)
+struct FillItem { int32_t* dst; int32_t v; int n = 1; };   // dst[0..n) = v (dst == nullptr: skipped)
 rbki_status fill_i32_batched(const FillItem* it, int n, cudaStream_t st);
 struct GemmItem {
     bool transA; int M, N, K;

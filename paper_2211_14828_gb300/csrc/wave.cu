@@ -762,18 +762,20 @@ __global__ void k_sumsq_fin_b(const __grid_constant__ BPack<sumsq_rec> p) {
     *r.out = t;
 }
 
-// *p = v for every record (the Krylov-path kept counters of a wave in one launch)
+// p[0..n) = v for every record (the error words, kept counters and orthonormalisation
+// tickets of a wave in one launch)
 struct fill_rec {
     int32_t* p;
     int32_t v;
+    int n;
     int gx, gy, gz;
 };
 
 __global__ void k_fill_b(const __grid_constant__ BPack<fill_rec> p) {
     const fill_rec& r = p.r[blockIdx.y];
     int bx, by, bz;
-    if (!bat_block(r, bx, by, bz) || threadIdx.x) return;
-    *r.p = r.v;
+    if (!bat_block(r, bx, by, bz)) return;
+    for (int e = threadIdx.x; e < r.n; e += blockDim.x) r.p[e] = r.v;
 }
 
 // info[n] = kept Krylov width (Krylov path) or I_n (Gram path); info[N+n] = path;
@@ -981,7 +983,7 @@ rbki_status run_wave(std::vector<WaveReq>& Q, cudaStream_t st, uint32_t wait_us 
         std::vector<xreduce_rec> wd;
         std::vector<fill_rec> fk;
         for (auto& q : Q) {
-            fk.push_back(fill_rec{q.err, 0, 1, 1, 1});
+            fk.push_back(fill_rec{q.err, 0, 1, 1, 1, 1});
             for (int n = 0; n < q.pl.N; ++n) {
                 WaveMode& w = q.mode[n];
                 const ModePlan& m = *w.m;
@@ -1038,8 +1040,8 @@ rbki_status run_wave(std::vector<WaveReq>& Q, cudaStream_t st, uint32_t wait_us 
                 if (!m.gram) {
                     wd.push_back(xreduce_rec{w.wpart, w.units, I, m.S, m.S, w.Qall, m.b, nullptr, 0,
                                              (int)cdiv((int64_t)I * m.S, 256), 1, 1});
-                    fk.push_back(fill_rec{w.kept, 0, 1, 1, 1});
-                    fk.push_back(fill_rec{orth_ticket(w.orth_ws), 0, 1, 1, 1});   // batched BCGS tickets
+                    fk.push_back(fill_rec{w.kept, 0, 1, 1, 1, 1});
+                    fk.push_back(fill_rec{orth_ticket(w.orth_ws), 0, ORTH_TICKETS, 1, 1, 1});   // batched BCGS tickets
                     qmax = std::max(qmax, m.q);
                 }
             }
