@@ -307,17 +307,22 @@ rbki_status ttm_cuda(const View& x, const double* M, int64_t ldm, int S, void* Y
 // Small mode products (the core chain after the first contraction): Y = X x_n M^T with
 // S <= NSB <= 32 outputs per column.  M is staged in shared memory in chunks of TS_MI rows,
 // converted to the accumulation type once.
-//   C > 1: one thread per (a, c) column with NSB accumulators; X reads coalesced over c.
+//   C > 1: a CTA takes 32 columns c of one a; its 8 warps split the rows i (warp g takes
+//          i = g mod 8), each lane keeps NSB accumulators for its column, and the 8 partial
+//          sums are added in warp order through shared memory.  X reads coalesced over c.
 //   C = 1: one warp per a, lanes over i, butterfly reduction of the NSB partial sums.
 constexpr int TS_MI = 128;
+constexpr int TS_G = 8;      // row groups (warps) per CTA of the C > 1 form
 template <typename T, typename Acc, int NSB>
 __global__ void __launch_bounds__(256) k_ttm_small_c(const T* __restrict__ X, int64_t A, int64_t I, int64_t C,
                                                      const double* __restrict__ M, int64_t ldm, int S,
                                                      double* __restrict__ Y) {
-    __shared__ __align__(16) Acc ms[TS_MI][NSB];
-    const int64_t cblocks = cdiv(C, (int64_t)blockDim.x);
+    static_assert(TS_G * (NSB / 2) * 32 <= TS_MI * NSB, "reduction buffer");
+    __shared__ __align__(16) Acc buf[TS_MI * NSB];   // M chunk, then the reduction
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int64_t cblocks = cdiv(C, (int64_t)32);
     const int64_t a = blockIdx.x / cblocks;
-    const int64_t c = (blockIdx.x % cblocks) * blockDim.x + threadIdx.x;
+    const int64_t c = (blockIdx.x % cblocks) * 32 + lane;
     Acc acc[NSB];
 #pragma unroll
     for (int q = 0; q < NSB; ++q) acc[q] = 0;
@@ -326,35 +331,60 @@ __global__ void __launch_bounds__(256) k_ttm_small_c(const T* __restrict__ X, in
         __syncthreads();
         for (int e = threadIdx.x; e < TS_MI * NSB; e += blockDim.x) {
             const int ii = e / NSB, q = e % NSB;
-            ms[ii][q] = (ii < ni && q < S) ? (Acc)M[(i0 + ii) * ldm + q] : (Acc)0;
+            buf[e] = (ii < ni && q < S) ? (Acc)M[(i0 + ii) * ldm + q] : (Acc)0;
         }
         __syncthreads();
         if (c < C) {
             const T* xp = X + (a * I + i0) * C + c;
-            for (int ii = 0; ii < ni; ++ii) {
-                const Acc x = ld_acc<Acc>(xp + (int64_t)ii * C);
-                // the row of M is the same for every lane: 16-byte broadcast reads
-                const uint4* mr = reinterpret_cast<const uint4*>(&ms[ii][0]);
+            // four rows' loads in flight per warp, then their products in row order
+            for (int ib = g; ib < ni; ib += 4 * TS_G) {
+                Acc xs[4];
 #pragma unroll
-                for (int v = 0; v < NSB * (int)sizeof(Acc) / 16; ++v) {
-                    const uint4 u = mr[v];
-                    if constexpr (sizeof(Acc) == 4) {
-                        acc[4 * v + 0] += x * __uint_as_float(u.x);
-                        acc[4 * v + 1] += x * __uint_as_float(u.y);
-                        acc[4 * v + 2] += x * __uint_as_float(u.z);
-                        acc[4 * v + 3] += x * __uint_as_float(u.w);
-                    } else {
-                        acc[2 * v + 0] += x * __hiloint2double((int)u.y, (int)u.x);
-                        acc[2 * v + 1] += x * __hiloint2double((int)u.w, (int)u.z);
+                for (int u4 = 0; u4 < 4; ++u4) {
+                    const int ii = ib + u4 * TS_G;
+                    xs[u4] = ii < ni ? ld_acc<Acc>(xp + (int64_t)ii * C) : (Acc)0;
+                }
+#pragma unroll
+                for (int u4 = 0; u4 < 4; ++u4) {
+                    const int ii = ib + u4 * TS_G;
+                    if (ii >= ni) break;
+                    const Acc x = xs[u4];
+                    // the row of M is the same for every lane: 16-byte broadcast reads
+                    const uint4* mr = reinterpret_cast<const uint4*>(&buf[ii * NSB]);
+#pragma unroll
+                    for (int v = 0; v < NSB * (int)sizeof(Acc) / 16; ++v) {
+                        const uint4 u = mr[v];
+                        if constexpr (sizeof(Acc) == 4) {
+                            acc[4 * v + 0] += x * __uint_as_float(u.x);
+                            acc[4 * v + 1] += x * __uint_as_float(u.y);
+                            acc[4 * v + 2] += x * __uint_as_float(u.z);
+                            acc[4 * v + 3] += x * __uint_as_float(u.w);
+                        } else {
+                            acc[2 * v + 0] += x * __hiloint2double((int)u.y, (int)u.x);
+                            acc[2 * v + 1] += x * __hiloint2double((int)u.w, (int)u.z);
+                        }
                     }
                 }
             }
         }
     }
-    if (c < C)
+    // the groups' sums, added in group order, half of the outputs at a time
+    Acc* red = buf;   // [TS_G][NSB / 2][32]
 #pragma unroll
-        for (int q = 0; q < NSB; ++q)
-            if (q < S) Y[(a * S + q) * C + c] = (double)acc[q];
+    for (int h = 0; h < 2; ++h) {
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < NSB / 2; ++q) red[(g * (NSB / 2) + q) * 32 + lane] = acc[h * (NSB / 2) + q];
+        __syncthreads();
+        for (int e = threadIdx.x; e < (NSB / 2) * 32; e += blockDim.x) {
+            const int q = e / 32, l = e % 32;
+            const int qq = h * (NSB / 2) + q;
+            const int64_t cc = (blockIdx.x % cblocks) * 32 + l;
+            Acc t = 0;
+            for (int gg = 0; gg < TS_G; ++gg) t += red[(gg * (NSB / 2) + q) * 32 + l];
+            if (cc < C && qq < S) Y[(a * S + qq) * C + cc] = (double)t;
+        }
+    }
 }
 
 template <typename T, typename Acc, int NSB>
@@ -395,13 +425,14 @@ rbki_status ttm_small_cuda(const View& x, const double* M, int64_t ldm, int S, d
     if (S < 1 || S > 32) return set_error(RBKI_E_UNSUPPORTED, "ttm_small: S > 32");
     if (x.dtype != RBKI_F64 && x.dtype != RBKI_F32) return set_error(RBKI_E_UNSUPPORTED, "ttm_small: dtype");
     const bool ifast = x.C == 1;
-    const int64_t blocks = ifast ? cdiv(x.A, (int64_t)8) : x.A * cdiv(x.C, (int64_t)256);
+    const int64_t blocks = ifast ? cdiv(x.A, (int64_t)8) : x.A * cdiv(x.C, (int64_t)32);
     if (blocks > 0x7fffffff) return set_error(RBKI_E_UNSUPPORTED, "ttm_small: too many blocks");
 #define TS_L(T, ACC, NSB)                                                                              \
     if (ifast) k_ttm_small_i<T, ACC, NSB><<<(unsigned)blocks, 256, 0, st>>>(as<T>(x.data), x.A, x.I, M, ldm, S, Y); \
-    else k_ttm_small_c<T, ACC, NSB><<<(unsigned)blocks, 256, 0, st>>>(as<T>(x.data), x.A, x.I, x.C, M, ldm, S, Y)
+    else k_ttm_small_c<T, ACC, NSB><<<(unsigned)blocks, 32 * TS_G, 0, st>>>(as<T>(x.data), x.A, x.I, x.C, M, ldm, S, Y)
 #define TS_B(T, ACC)                                                                                   \
-    if (S <= 8) { TS_L(T, ACC, 8); } else if (S <= 16) { TS_L(T, ACC, 16); } else { TS_L(T, ACC, 32); }
+    if (S <= 8) { TS_L(T, ACC, 8); } else if (S <= 16) { TS_L(T, ACC, 16); } else if (S <= 24) { TS_L(T, ACC, 24); } \
+    else { TS_L(T, ACC, 32); }
     if (x.dtype == RBKI_F64) {
         if (acc32) { TS_B(double, float) } else { TS_B(double, double) }
     } else {
