@@ -307,27 +307,62 @@ __device__ __forceinline__ void chol_deflate_dev(const double* __restrict__ Gp, 
     };
     if (tid == 0) pivot(0);
     __syncthreads();
+    const bool small = S <= 32 && ny == 16;   // 256 threads: rows ty and ty + 16 cover every i > k
     for (int k = 0; k < S; ++k) {
         const dfl ik = inv_d[k];
         const int mm = S - k - 1;
         if (ik.hi != 0.f) {                    // uniform: a deflated column eliminates nothing
-            if (tid == 0 && mm > 0) {          // d_{k+1} first, then its reciprocal
+            if (tid == 0 && mm > 0) {          // d_{k+1} and its reciprocal first (lookahead)
                 const dfl wk = W[k * S + k + 1];
                 W[(k + 1) * S + k + 1] = df_fms(W[(k + 1) * S + k + 1], df_mul(wk, ik), wk);
+                pivot(k + 1);
             }
             // rows i > k on a 16-wide grid of threads (no index division): the trailing
             // upper triangle j >= i (d_{k+1} done above) and the row of L^{-1}, columns 0..k
-            for (int i = k + 1 + ty; i < S; i += ny) {
-                const dfl li = df_mul(W[k * S + i], ik);
-                for (int j = k + 1 + tx; j < S; j += 16)
-                    if (j >= i && (i != k + 1 || j != k + 1)) W[i * S + j] = df_fms(W[i * S + j], li, W[k * S + j]);
-                for (int c = tx; c <= k; c += 16) {
-                    const dfl mkc = c == k ? dfl{1.f, 0.f} : W[k * S + c];   // L^{-1}[k][c]
-                    W[i * S + c] = df_fms(W[i * S + c], li, mkc);
+            if (small) {
+                // at most 2 rows x (2 trailing + 2 L^{-1} columns) per thread: every operand
+                // is loaded before any update, so the eight double-float chains overlap
+                dfl wv[8], mv[8], lv[2];
+                int at[8];
+                bool on[8];
+#pragma unroll
+                for (int a = 0; a < 2; ++a) {
+                    const int i = k + 1 + ty + 16 * a;
+                    const bool rok = i < S;
+                    lv[a] = rok ? df_mul(W[k * S + i], ik) : dfl{0.f, 0.f};
+#pragma unroll
+                    for (int b = 0; b < 2; ++b) {
+                        const int j = k + 1 + tx + 16 * b, c = tx + 16 * b;
+                        const int q = 4 * a + b, q2 = 4 * a + 2 + b;
+                        on[q] = rok && j < S && j >= i && (i != k + 1 || j != k + 1);
+                        on[q2] = rok && c <= k;
+                        at[q] = i * S + j;
+                        at[q2] = i * S + c;
+                        wv[q] = on[q] ? W[at[q]] : dfl{0.f, 0.f};
+                        mv[q] = on[q] ? W[k * S + j] : dfl{0.f, 0.f};
+                        wv[q2] = on[q2] ? W[at[q2]] : dfl{0.f, 0.f};
+                        mv[q2] = on[q2] ? (c == k ? dfl{1.f, 0.f} : W[k * S + c]) : dfl{0.f, 0.f};
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 8; ++q) wv[q] = df_fms(wv[q], lv[q / 4], mv[q]);
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    if (on[q]) W[at[q]] = wv[q];
+            } else {
+                for (int i = k + 1 + ty; i < S; i += ny) {
+                    const dfl li = df_mul(W[k * S + i], ik);
+                    for (int j = k + 1 + tx; j < S; j += 16)
+                        if (j >= i && (i != k + 1 || j != k + 1)) W[i * S + j] = df_fms(W[i * S + j], li, W[k * S + j]);
+                    for (int c = tx; c <= k; c += 16) {
+                        const dfl mkc = c == k ? dfl{1.f, 0.f} : W[k * S + c];   // L^{-1}[k][c]
+                        W[i * S + c] = df_fms(W[i * S + c], li, mkc);
+                    }
                 }
             }
+        } else if (tid == 0 && mm > 0) {
+            pivot(k + 1);
         }
-        if (tid == 0 && mm > 0) pivot(k + 1);
         __syncthreads();
     }
     for (int k = tid; k < S; k += nt) aux[k] = inv_d[k].hi != 0.f ? df_rsqrt(W[k * S + k]) : dfl{0.f, 0.f};
