@@ -677,6 +677,7 @@ struct xreduce_rec {
     int ld1;
     double* out2;
     int ld2;
+    int32_t* ticket;   // the item's orthonormalisation tickets, zeroed here (or nullptr)
     int gx, gy, gz;
 };
 
@@ -684,6 +685,7 @@ __global__ void __launch_bounds__(256) k_xreduce_b(const __grid_constant__ BPack
     const xreduce_rec& r = p.r[blockIdx.y];
     int bx, by, bz;
     if (!bat_block(r, bx, by, bz)) return;
+    if (bx == 0 && r.ticket && (int)threadIdx.x < ORTH_TICKETS) r.ticket[threadIdx.x] = 0;
     const int e = bx * 256 + threadIdx.x;
     if (e >= r.I * r.S) return;
     const int i = e / r.S, s = e % r.S;
@@ -1039,9 +1041,8 @@ rbki_status run_wave(std::vector<WaveReq>& Q, cudaStream_t st, uint32_t wait_us 
                 gd.push_back(greduce_rec{w.gpart, w.units, I, w.G, (int)cdiv((int64_t)I * I, 256), 1, 1});
                 if (!m.gram) {
                     wd.push_back(xreduce_rec{w.wpart, w.units, I, m.S, m.S, w.Qall, m.b, nullptr, 0,
-                                             (int)cdiv((int64_t)I * m.S, 256), 1, 1});
+                                             orth_ticket(w.orth_ws), (int)cdiv((int64_t)I * m.S, 256), 1, 1});
                     fk.push_back(fill_rec{w.kept, 0, 1, 1, 1, 1});
-                    fk.push_back(fill_rec{orth_ticket(w.orth_ws), 0, ORTH_TICKETS, 1, 1, 1});   // batched BCGS tickets
                     qmax = std::max(qmax, m.q);
                 }
             }
