@@ -473,10 +473,26 @@ __device__ __forceinline__ void reduce_tc_dev(const float* __restrict__ part, in
     if (e < tot) {
         const int64_t i = e / Sh;
         const int s = (int)(e % Sh);
-        for (int b = w; b < nb; b += RED_WARPS) {
-            const float* pb = part + ((size_t)b * I + i) * N;
-            two_sum_acc(hi, lo, pb[s]);
-            if (split) two_sum_acc(hi, lo, pb[N / 2 + s]);
+        // four partials' loads in flight, then summed in partial order
+        const size_t step = (size_t)RED_WARPS * I * N;
+        const float* pb = part + ((size_t)w * I + i) * N + s;
+        int b = w;
+        for (; b + 3 * RED_WARPS < nb; b += 4 * RED_WARPS, pb += 4 * step) {
+            float x[4], y[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                x[u] = pb[u * step];
+                y[u] = split ? pb[u * step + N / 2] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                two_sum_acc(hi, lo, x[u]);
+                if (split) two_sum_acc(hi, lo, y[u]);
+            }
+        }
+        for (; b < nb; b += RED_WARPS, pb += step) {
+            two_sum_acc(hi, lo, pb[0]);
+            if (split) two_sum_acc(hi, lo, pb[N / 2]);
         }
     }
     acc_sh[w][lane] = (double)hi + (double)lo;
