@@ -1,5 +1,6 @@
 // Sketching matrix generation (Algorithm 1 step 1), norms, precision staging.
 #include "kernels.h"
+#include "dfloat.cuh"
 
 namespace rbki {
 namespace {
@@ -82,15 +83,20 @@ __global__ void k_stage(const T* __restrict__ x, int64_t n, TD* __restrict__ dst
     }
 }
 
-// float4-vectorised fp32 -> bf16 staging (the common case), n % 4 == 0, 16-byte aligned
+// float4-vectorised fp32 -> bf16 staging (the common case), n % 4 == 0, 16-byte aligned.
+// The squares of four elements are summed in FP32 and accumulated per thread by compensated
+// FP32 summation (TwoSum: the running sum and the sum of its rounding errors, about 2^-48
+// relative); the threads' sums are combined in FP64.  An FP64 accumulator here cost two FP64
+// operations per 16 bytes read, about as long as the HBM traffic itself on GB300.
 __global__ void k_stage_f32_bf16_v4(const float4* __restrict__ x, int64_t n4,
                                     uint2* __restrict__ dst, double* __restrict__ part) {
-    double acc = 0.0;
+    float hi = 0.f, lo = 0.f;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
          i += (int64_t)gridDim.x * blockDim.x) {
         float4 v = __ldcs(x + i);
-        // FP32 square-sum of the four elements, FP64 accumulation across the stream
-        acc += (double)(v.x * v.x + v.y * v.y + v.z * v.z + v.w * v.w);
+        const dfl sq = df_two_sum(hi, v.x * v.x + v.y * v.y + v.z * v.z + v.w * v.w);
+        hi = sq.hi;
+        lo = __fadd_rn(lo, sq.lo);
         __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y);
         __nv_bfloat162 b = __floats2bfloat162_rn(v.z, v.w);
         uint2 o;
@@ -98,6 +104,7 @@ __global__ void k_stage_f32_bf16_v4(const float4* __restrict__ x, int64_t n4,
         o.y = *reinterpret_cast<uint32_t*>(&b);
         dst[i] = o;
     }
+    double acc = (double)hi + (double)lo;
     __shared__ double red[32];
     acc = warp_sum(acc);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
