@@ -586,7 +586,8 @@ static bool lockstep_ok(const Plan& pl) {
 // batched kernels run each mode through the same device code and grids as the per-mode
 // calls, so the results equal the concurrent per-mode chains bit for bit; the modes' FP64
 // stages share launches instead of queueing on three streams.
-static rbki_status run_modes_lockstep(const Plan& pl, const rbki_tucker_out* out, cudaStream_t st) {
+static rbki_status run_modes_lockstep(const Plan& pl, const rbki_tucker_out* out, cudaStream_t st,
+                                      bool omega_done) {
     std::vector<const ModePlan*> K;
     // one launch for the scalar outputs known up front (q_used; the Krylov-path modes' kept
     // counters and path words) and the orthonormalisation tickets
@@ -616,7 +617,7 @@ static rbki_status run_modes_lockstep(const Plan& pl, const rbki_tucker_out* out
         for (const ModePlan* m : K) {
             if (m->tc || m->tc2) om.push_back(tc::OmegaItem{pl.seed, m->n, mode_view(pl, *m), m->S, m->N, pl.split, m->omg});
         }
-        RBKI_TRY(tc::omega_images_batched(om.data(), (int)om.size(), st));
+        if (!omega_done) RBKI_TRY(tc::omega_images_batched(om.data(), (int)om.size(), st));
         for (const ModePlan* m : K) {
             if (!(m->tc || m->tc2)) {
                 RBKI_TRY(sketch_mode(pl, *m, st));
@@ -990,8 +991,30 @@ rbki_status run_tucker(Plan& pl, const rbki_tucker_out* out, cudaStream_t st, co
     if (pl.sequential) return run_sequential(pl, out, st);
     double* norms = out->norms ? out->norms : pl.scal;
     RBKI_CUDA_TRY(cudaMemsetAsync(pl.err, 0, sizeof(int32_t), st));
+    const bool concurrent = pl.N > 1 && !(pl.flags & RBKI_FLAG_SERIAL_MODES);
+    const bool lockstep = !(pl.flags & RBKI_FLAG_ADAPTIVE_Q) && lockstep_ok(pl);
+    // FP32 -> BF16 staging (every path, so that |X|^2 is summed in one order): the cast and,
+    // for lockstep calls, the modes' Omega images in one launch
+    std::vector<tc::OmegaItem> om;
+    const bool fused = pl.stage && pl.dtype == RBKI_F32 && pl.stream_dtype == RBKI_BF16 && pl.numel % 4 == 0 &&
+                       (uintptr_t)pl.xin % 16 == 0 && (uintptr_t)pl.xs % 8 == 0 &&
+                       tc::stage_omega_grid() <= 4096 - 64;
+    if (fused) {
+        pl.xstream = pl.xs;
+        for (int n = 0; n < pl.N && lockstep; ++n) {
+            const ModePlan& m = pl.mode[n];
+            if (!m.gram && (m.tc || m.tc2))
+                om.push_back(tc::OmegaItem{pl.seed, m.n, mode_view(pl, m), m.S, m.N, pl.split, m.omg});
+        }
+        if (om.size() > 8) om.clear();
+    }
+    const bool omega_done = !om.empty();
     int tok = prof_begin(RBKI_PROF_STAGE, st);
-    if (pl.stage) {
+    if (fused) {
+        RBKI_TRY(tc::stage_omega_batched(static_cast<const float*>(pl.xin), pl.numel, pl.xs, pl.scal + 64, om.data(),
+                                         (int)om.size(), st));
+        RBKI_TRY(sum_parts_cuda(pl.scal + 64, tc::stage_omega_grid(), norms, st));
+    } else if (pl.stage) {
         RBKI_TRY(stage_cuda(pl.xin, pl.dtype, pl.numel, pl.xs, pl.stream_dtype, pl.scal + 64,
                             norms, st));
         pl.xstream = pl.xs;
@@ -1000,8 +1023,6 @@ rbki_status run_tucker(Plan& pl, const rbki_tucker_out* out, cudaStream_t st, co
         RBKI_TRY(sumsq_cuda(pl.xin, pl.dtype, pl.numel, pl.scal + 64, norms, st));
     }
     prof_end(tok, st);
-    const bool concurrent = pl.N > 1 && !(pl.flags & RBKI_FLAG_SERIAL_MODES);
-    const bool lockstep = !(pl.flags & RBKI_FLAG_ADAPTIVE_Q) && lockstep_ok(pl);
     int chain_from = 0;   // core-chain steps already enqueued on a mode stream
     int32_t q_used[RBKI_MAX_ORDER];
     for (int n = 0; n < pl.N; ++n) q_used[n] = pl.mode[n].gram ? 0 : pl.mode[n].q;
@@ -1026,7 +1047,7 @@ rbki_status run_tucker(Plan& pl, const rbki_tucker_out* out, cudaStream_t st, co
         cudaEventDestroy(ev);
         if (rs < 0) return rs;
     } else if (lockstep) {
-        RBKI_TRY(run_modes_lockstep(pl, out, st));
+        RBKI_TRY(run_modes_lockstep(pl, out, st, omega_done));
     } else if (concurrent) {
         cudaStream_t ms[RBKI_MAX_ORDER];
         if (mode_streams) {

@@ -144,6 +144,12 @@ rbki_status sumsq_cuda(const void* x, int dtype, int64_t n, double* part, double
     return RBKI_OK;
 }
 
+rbki_status sum_parts_cuda(const double* part, int nparts, double* out, cudaStream_t st) {
+    k_sum_parts<<<1, 256, 0, st>>>(part, nparts, out);
+    RBKI_LAUNCH_CHECK("k_sum_parts");
+    return RBKI_OK;
+}
+
 rbki_status stage_cuda(const void* x, int dtype, int64_t n, void* dst, int dst_dtype,
                        double* part, double* norm2, cudaStream_t st) {
     int blocks = (int)std::min<int64_t>(NORM_BLOCKS, std::max<int64_t>(1, cdiv(n, 256)));

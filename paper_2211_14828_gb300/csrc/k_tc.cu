@@ -23,6 +23,7 @@
 
 #include "kernels.h"
 #include "tc.h"
+#include "dfloat.cuh"
 #include "tc_ptx.cuh"
 
 namespace rbki {
@@ -364,14 +365,12 @@ __global__ void k_skinny_image_b(const __grid_constant__ BPack<skinny_image_rec>
 // tile t at t*128*N + (n/8)*1024 + c*8 + n%8 (elements).  Columns outside the tensor are 0.
 // With `split`, image column n < S holds the hi part of Omega's column n and N/2 + s the lo
 // part of column s.
-__device__ __forceinline__ void omega_images_dev(uint64_t seed, int mode, int64_t A, int64_t C, int ifast,
-                                                 int64_t ctiles, int64_t tiles, int S, int N, int split,
-                                                 int fp16, uint16_t* __restrict__ img, int bx) {
-    // one thread per (tile, column c, group of 8 image columns): the group is written as one
-    // 16-byte vector, zeros included, so the image needs no clearing beforehand
+// element e = (tile, column c, group of 8 image columns), 0 <= e < tiles * 128 * N / 8: the
+// group is written as one 16-byte vector, zeros included, so the image needs no clearing
+__device__ __forceinline__ void omega_image_elem(uint64_t seed, int mode, int64_t A, int64_t C, int ifast,
+                                                 int64_t ctiles, int S, int N, int split, int fp16,
+                                                 uint16_t* __restrict__ img, int64_t e) {
     const int G = N / 8;
-    const int64_t e = (int64_t)bx * blockDim.x + threadIdx.x;
-    if (e >= tiles * 128 * G) return;
     const int g = (int)(e % G);
     const int64_t tc_ = e / G;
     const int c = (int)(tc_ & 127);
@@ -415,6 +414,15 @@ __device__ __forceinline__ void omega_images_dev(uint64_t seed, int mode, int64_
     *reinterpret_cast<uint4*>(img + (size_t)t * 128 * N + (size_t)g * 1024 + c * 8) = w;
 }
 
+// one thread per element
+__device__ __forceinline__ void omega_images_dev(uint64_t seed, int mode, int64_t A, int64_t C, int ifast,
+                                                 int64_t ctiles, int64_t tiles, int S, int N, int split,
+                                                 int fp16, uint16_t* __restrict__ img, int bx) {
+    const int64_t e = (int64_t)bx * blockDim.x + threadIdx.x;
+    if (e >= tiles * 128 * (N / 8)) return;
+    omega_image_elem(seed, mode, A, C, ifast, ctiles, S, N, split, fp16, img, e);
+}
+
 __global__ void __launch_bounds__(256) k_omega_images(uint64_t seed, int mode, int64_t A, int64_t C, int ifast,
                                                       int64_t ctiles, int64_t tiles, int S, int N, int split,
                                                       int fp16, uint16_t* __restrict__ img) {
@@ -442,6 +450,72 @@ __global__ void __launch_bounds__(256) k_omega_images_b(const __grid_constant__ 
     int bx, by, bz;
     if (!bat_block(r, bx, by, bz)) return;
     omega_images_dev(r.seed, r.mode, r.A, r.C, r.ifast, r.ctiles, r.tiles, r.S, r.N, r.split, r.fp16, r.img, bx);
+}
+
+
+// The staging cast of X (FP32 -> BF16, with the sum of squares) and the Omega images of every
+// mode in one persistent launch: in each CTA warps 0-3 stream the cast (HBM-bound, the ALUs
+// mostly idle) while warps 4-7 generate images (Philox and Box-Muller: integer- and
+// FP32-ALU-bound), so the two share the SMs instead of running one after the other.  The
+// staged values and the images are those of k_stage_f32_bf16_v4 and k_omega_images; the sum
+// of squares is accumulated per thread by compensated FP32 summation and per CTA in FP64.
+constexpr int SO_MAXREC = 8;
+struct StageOmegaParams {
+    const float4* x;
+    int64_t n4;
+    uint2* dst;
+    double* part;          // one partial sum of squares per CTA
+    int nrec;
+    int64_t first[SO_MAXREC + 1];   // element offsets of the records' images
+    omega_images_rec rec[SO_MAXREC];
+};
+
+__global__ void __launch_bounds__(256) k_stage_omega(const __grid_constant__ StageOmegaParams p) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __shared__ double red[4];
+    if (w < 4) {
+        // warp-contiguous 32-float4 chunks, four chunks' loads in flight per thread
+        const int64_t nw = (int64_t)gridDim.x * 4;
+        float hi = 0.f, lo = 0.f;
+        for (int64_t ch = (int64_t)blockIdx.x * 4 + w; ch * 32 < p.n4; ch += 4 * nw) {
+            float4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t i = (ch + u * nw) * 32 + lane;
+                v[u] = i < p.n4 ? __ldcs(p.x + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t i = (ch + u * nw) * 32 + lane;
+                if (i >= p.n4) continue;
+                const dfl sq = df_two_sum(hi, v[u].x * v[u].x + v[u].y * v[u].y + v[u].z * v[u].z + v[u].w * v[u].w);
+                hi = sq.hi;
+                lo = __fadd_rn(lo, sq.lo);
+                __nv_bfloat162 a = __floats2bfloat162_rn(v[u].x, v[u].y);
+                __nv_bfloat162 b = __floats2bfloat162_rn(v[u].z, v[u].w);
+                uint2 o;
+                o.x = *reinterpret_cast<uint32_t*>(&a);
+                o.y = *reinterpret_cast<uint32_t*>(&b);
+                p.dst[i] = o;
+            }
+        }
+        double acc = (double)hi + (double)lo;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) red[w] = acc;
+    } else {
+        const int64_t nt = (int64_t)gridDim.x * 128;
+        const int64_t total = p.first[p.nrec];
+        int r = 0;
+        for (int64_t e = ((int64_t)blockIdx.x * 4 + (w - 4)) * 32 + lane; e < total; e += nt) {
+            while (e >= p.first[r + 1]) ++r;   // e only grows: the record index only grows
+            const omega_images_rec& q = p.rec[r];
+            omega_image_elem(q.seed, q.mode, q.A, q.C, q.ifast, q.ctiles, q.S, q.N, q.split, q.fp16, q.img,
+                             e - p.first[r]);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) p.part[blockIdx.x] = ((red[0] + red[1]) + red[2]) + red[3];
 }
 
 
@@ -722,6 +796,40 @@ rbki_status omega_images_batched(const OmegaItem* it, int n, cudaStream_t st) {
                                      (int)cdiv(tiles * 128 * (a.N / 8), 256), 1, 1});
     }
     return bat_launch(k_omega_images_b, r.data(), (int)r.size(), 256, 0, st, "k_omega_images_b");
+}
+
+int stage_omega_grid() {
+    static const int g = [] {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        return std::max(1, sms) * 4;
+    }();
+    return g;
+}
+
+rbki_status stage_omega_batched(const float* x, int64_t n, void* dst, double* part, const OmegaItem* it, int n_items,
+                                cudaStream_t st) {
+    if (n % 4 || ((uintptr_t)x % 16) || ((uintptr_t)dst % 8)) return set_error(RBKI_E_INVAL, "stage_omega: layout");
+    if (n_items < 0 || n_items > SO_MAXREC) return set_error(RBKI_E_INVAL, "stage_omega: records");
+    StageOmegaParams p{};
+    p.x = reinterpret_cast<const float4*>(x);
+    p.n4 = n / 4;
+    p.dst = reinterpret_cast<uint2*>(dst);
+    p.part = part;
+    p.nrec = n_items;
+    p.first[0] = 0;
+    for (int k = 0; k < n_items; ++k) {
+        const OmegaItem& a = it[k];
+        const bool ifast = a.v.C == 1;
+        const int64_t ctiles = ifast ? 1 : cdiv(a.v.C, 128), tiles = num_tiles(a.v);
+        p.rec[k] = omega_images_rec{a.seed, a.mode, a.v.A, a.v.C, ifast ? 1 : 0, ctiles, tiles, a.S, a.N,
+                                    a.split ? 1 : 0, a.v.dtype == RBKI_F16 ? 1 : 0, (uint16_t*)a.img, 0, 1, 1};
+        p.first[k + 1] = p.first[k] + tiles * 128 * (a.N / 8);
+    }
+    k_stage_omega<<<stage_omega_grid(), 256, 0, st>>>(p);
+    RBKI_LAUNCH_CHECK("k_stage_omega");
+    return RBKI_OK;
 }
 
 rbki_status reduce_parts_batched(const ReduceItem* it, int n, cudaStream_t st) {

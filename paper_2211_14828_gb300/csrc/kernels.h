@@ -56,6 +56,8 @@ rbki_status omega_f64_cuda(uint64_t seed, int mode, int64_t A, int64_t C, int S,
 rbki_status sumsq_cuda(const void* x, int dtype, int64_t n, double* part, double* out,
                        cudaStream_t st);
 // cast to bf16/f16 (dst_dtype) + sum of squares of the source
+// *out = the fixed-order sum of part[0 .. nparts)
+rbki_status sum_parts_cuda(const double* part, int nparts, double* out, cudaStream_t st);
 rbki_status stage_cuda(const void* x, int dtype, int64_t n, void* dst, int dst_dtype,
                        double* part, double* norm2, cudaStream_t st);
 

@@ -71,6 +71,13 @@ struct OmegaItem {
     uint64_t seed; int mode; View v; int S, N; bool split; void* img;
 };
 rbki_status omega_images_batched(const OmegaItem* it, int n, cudaStream_t st);
+// The FP32 -> BF16 staging of X (n elements, n % 4 == 0, x 16-byte and dst 8-byte aligned)
+// with per-CTA partial sums of squares in part[0 .. stage_omega_grid()), and the Omega images
+// of up to 8 items (0: the cast alone), in one launch (the two jobs share the SMs).  Same staged values and images
+// as stage_cuda and omega_images_batched.
+int stage_omega_grid();
+rbki_status stage_omega_batched(const float* x, int64_t n, void* dst, double* part, const OmegaItem* it, int n_items,
+                                cudaStream_t st);
 struct ReduceItem {
     const float* part; int nb; int64_t I; int N, Sh; bool split;
     double* out; int64_t ld; double* out2; int64_t ld2; const int* err;
